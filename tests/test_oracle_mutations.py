@@ -1,0 +1,73 @@
+"""Planted mistakes in the oracle (CPU only) must be caught by its pins.
+
+Each case patches one plausible slip into a copy of an oracle routine -- a dropped
+term, a wrong sign, a transposed operand -- and checks that the corresponding pin
+fails on it.  This shows the pins are sharp enough to trust."""
+import math
+
+import numpy as np
+import scipy.fft as sfft
+
+import oracle.dtn as dtn
+from oracle.coefficients import order1
+from oracle.lattice import Box
+from oracle.propagate import System
+from paper_1908_02456_gb300 import inputs
+
+
+def test_dropped_taylor_term_is_caught(monkeypatch):
+    def taylor3(self, op, phi, f, V, dt):
+        out_p, tp, tf = phi.copy(), phi, f
+        for k in range(1, 4):                          # quartic term dropped
+            tp, tf = op(tp, tf, V)
+            out_p = out_p + dt ** k / math.factorial(k) * tp
+        return out_p, None
+    monkeypatch.setattr(System, "taylor", taylor3)
+    dims, h, dt, n = (5, 4, 6), 0.5, 0.02, 10
+    box = Box(dims, h)
+    phi0 = inputs.random_state(dims, 1, np.random.default_rng(0))
+    phi, _, _ = System(box).run(phi0.reshape(1, -1), dt, n)
+    lam = np.zeros(box.shape)
+    for ax, N in zip((2, 1, 0), dims):
+        shp = [1, 1, 1]
+        shp[ax] = N
+        lam = lam + ((1 - np.cos(np.pi * np.arange(1, N + 1) / (N + 1))) / h ** 2).reshape(shp)
+    P = sum((-1j * dt * lam) ** k / math.factorial(k) for k in range(5))
+    ref = sfft.idstn(sfft.dstn(phi0[0], type=1, norm="ortho") * P ** n, type=1, norm="ortho")
+    assert np.linalg.norm(phi[0] - ref.reshape(-1)) / np.linalg.norm(ref) > 1e-8
+
+
+def test_wrong_sign_of_shift_is_caught(monkeypatch):
+    orig = dtn.FreeGreen.__init__
+
+    def flipped(self, d, h, R, s, max_offset, P=None):
+        orig(self, d, h, R, -s, max_offset, P)        # +is instead of -is
+    monkeypatch.setattr(dtn.FreeGreen, "__init__", flipped)
+    K = dtn.dtn_eval(Box((4, 5, 4), 0.5), 1.0)
+    assert np.linalg.eigvalsh((K - K.conj().T) / 2j).max() > 0   # Im K <= 0 pin fails
+
+
+def test_transposed_b_is_caught():
+    box = Box((5, 4, 6), 0.5)
+    co = order1(box, 1.0)
+    A, B, K1 = co["A"], co["B"], co["K1"]
+    n = len(A)
+    bad = np.linalg.solve(np.eye(n) - B.T, A)
+    assert np.abs(bad - K1).max() > 1e-6 * np.abs(K1).max()
+
+
+def test_dropped_boundary_forcing_is_caught(monkeypatch):
+    orig_L = System.L
+
+    def L_no_forcing(self, phi, f, V):
+        dphi, df = orig_L(self, phi, f, V)
+        if self.order == 1:
+            dphi = dphi + 1j * self.ET(f, phi.shape[1])   # removes -i E^T f
+        return dphi, df
+    monkeypatch.setattr(System, "L", L_no_forcing)
+    N, h = 8, 0.5
+    box = Box((N,) * 3, h)
+    psi = inputs.gaussian_packet((N,) * 3, h, (0, 0, 0), (3.0, 0.5, 0), 1.0).reshape(1, -1)
+    _, _, d = System(box, coeffs=order1(box, 1.0)).run(psi, 0.01, 100, diag_every=1)
+    W = np.concatenate([[1.0], d[:, 0, 1]])
+    assert not np.all(W[1:] <= W[:-1] * (1 + 1e-12))              # Lyapunov pin fails

@@ -1,0 +1,180 @@
+"""Pins of the oracle's reduced dynamics and Taylor propagator (eq:dynamics0/1, eq:21)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.fft as sfft
+
+from oracle.coefficients import order0, order1
+from oracle.lattice import Box
+from oracle.propagate import System
+from paper_1908_02456_gb300 import inputs
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def taylor4(z):
+    return sum(z ** k / math.factorial(k) for k in range(5))
+
+
+def test_dirichlet_dst_exact():
+    """Zero Dirichlet, V = 0: the type-I DST diagonalises H_{I,I}, with eigenvalues
+    sum_axes (1 - cos(pi k/(N+1)))/h^2, so n steps of the Taylor propagator equal
+    DST^-1[P(-i dt lambda)^n DST phi0] exactly (P = degree-4 Taylor polynomial)."""
+    dims, h, dt, n = (6, 7, 5), 0.5, 0.02, 25
+    box = Box(dims, h)
+    rng = np.random.default_rng(1)
+    phi0 = inputs.random_state(dims, 2, rng)
+    sysd = System(box)
+    phi, _, _ = sysd.run(phi0.reshape(2, -1), dt, n)
+    lam = np.zeros(box.shape)
+    for ax, N in zip((2, 1, 0), dims):
+        k = np.arange(1, N + 1)
+        shp = [1, 1, 1]
+        shp[ax] = N
+        lam = lam + ((1 - np.cos(np.pi * k / (N + 1))) / h ** 2).reshape(shp)
+    ref = []
+    for j in range(2):
+        c = sfft.dstn(phi0[j], type=1, norm="ortho")
+        ref.append(sfft.idstn(c * taylor4(-1j * dt * lam) ** n, type=1, norm="ortho").reshape(-1))
+    ref = np.array(ref)
+    assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-13
+
+
+def closed_form_packet(X, t, center, k, sigma2):
+    """Free packet psi0 = exp(-|x-c|^2/(2 sigma^2) + i k.(x-c)) evolved by i psi_t = -Delta psi/2."""
+    d = len(X)
+    a = sigma2 + 1j * t
+    r2 = sum((X[i] - center[i] - k[i] * t) ** 2 for i in range(d))
+    kx = sum(k[i] * (X[i] - center[i]) for i in range(d))
+    k2 = sum(ki * ki for ki in k)
+    return (sigma2 / a) ** (d / 2) * np.exp(-r2 / (2 * a) + 1j * kx - 0.5j * k2 * t)
+
+
+def test_closed_form_is_papers_eq15():
+    """The test's closed form with sigma^2 = 1/2 is the paper's eq:15."""
+    g = GOLDEN["free_packet_3d"]
+    k0 = g["k0"]
+    rng = np.random.default_rng(2)
+    x = rng.uniform(-1, 1, size=(3, 20))
+    for t in (0.0, 0.05, 0.3):
+        printed = (1j / (1j - 2 * t)) ** 1.5 * np.exp(
+            (-1j * (x ** 2).sum(0) - k0 * x[0] + 0.5 * k0 ** 2 * t) / (1j - 2 * t))
+        mine = closed_form_packet(list(x), t, (0, 0, 0), (k0, 0, 0), g["sigma2"])
+        assert np.allclose(mine, printed, rtol=1e-13)
+
+
+def _packet_error(d, N, h, T, k, sigma2=0.5):
+    box = Box((N,) * d, h)
+    ax = (np.arange(N) - 0.5 * (N - 1)) * h
+    X = np.meshgrid(*([ax] * d), indexing="ij")[::-1] if d > 1 else [ax]
+    if d == 3:
+        X = list(np.meshgrid(ax, ax, ax, indexing="ij"))[::-1]
+    center = (0.0,) * d
+    kv = (k,) + (0.0,) * (d - 1)
+    phi0 = closed_form_packet(X, 0.0, center, kv, sigma2).reshape(1, -1)
+    dt = 0.2 * h * h
+    n = int(round(T / dt))
+    phi, _, _ = System(box).run(phi0, T / n, n)
+    ref = closed_form_packet(X, T, center, kv, sigma2).reshape(1, -1)
+    return np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+
+
+def test_free_packet_second_order_1d():
+    """Away from the boundary the discrete solution converges to the closed form with
+    order 2 in h (3-point stencil)."""
+    e1 = _packet_error(1, 401, 0.04, 0.5, 3.0)
+    e2 = _packet_error(1, 801, 0.02, 0.5, 3.0)
+    assert e2 < 0.02
+    assert 3.6 < e1 / e2 < 4.4
+
+
+@pytest.mark.slow
+def test_free_packet_3d_eq15():
+    """The paper's 3D packet (eq:15 with k0 = 1) in a box of half-width 4.4 (6 packet widths,
+    so the Dirichlet faces are invisible): second-order convergence in h."""
+    e1 = _packet_error(3, 45, 0.2, 0.1, 1.0)
+    e2 = _packet_error(3, 91, 0.1, 0.1, 1.0)
+    assert e2 < 0.02
+    assert 3.2 < e1 / e2 < 4.6
+
+
+def _packet_case(N=8, h=0.5, k=3.0):
+    box = Box((N, N, N), h)
+    psi = inputs.gaussian_packet((N, N, N), h, (0.0, 0.0, 0.0), (k, 0.5, 0.0), 1.0)
+    return box, psi.reshape(1, -1)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_lyapunov_non_increase(order):
+    """W = |phi|^2 (+ f^* Q f for order 1) never grows (Thm 3.1 / Thm 3.2); checked step
+    by step after time discretisation with a 1e-12 relative slack."""
+    box, phi0 = _packet_case()
+    co = order0(box, 1.0) if order == 0 else order1(box, 1.0)
+    sy = System(box, coeffs=co)
+    _, _, d = sy.run(phi0, 0.01, 150, diag_every=1)
+    W = d[:, 0, 1]
+    W = np.concatenate([[1.0], W])
+    assert np.all(W[1:] <= W[:-1] * (1 + 1e-12))
+    assert d[-1, 0, 0] < 0.7          # a large part has left the box
+
+
+def test_dirichlet_norm_conservation():
+    """Zero Dirichlet: H is Hermitian, so each step changes the norm only by the Taylor
+    truncation, |P(i theta)|^2 = 1 - theta^6/72 + O(theta^8)."""
+    box, phi0 = _packet_case()
+    sy = System(box)
+    dt = 0.01
+    _, _, d = sy.run(phi0, dt, 50, diag_every=1)
+    lam = 3 * 2 / box.h ** 2
+    bound = (dt * lam) ** 6 / 72 * 1.5
+    nr = np.concatenate([[1.0], d[:, 0, 0]])
+    assert np.all(np.abs(np.diff(nr)) <= bound * nr[:-1] + 1e-15)
+
+
+def test_reflection_against_large_box():
+    """The same packet on a large zero-Dirichlet box, restricted to the small box, is the
+    reflection-free reference (Sec. 4.3's test design).  The ABCs cut the error of the
+    Dirichlet box, order 1 more than order 0 (Sec. 4.1, Sec. 4.2)."""
+    N, h, Nb, T, dt = 10, 0.5, 42, 1.6, 0.01
+    k = (2.5, 0.0, 0.0)
+    small = Box((N,) * 3, h)
+    big = Box((Nb,) * 3, h)
+    p_s = inputs.gaussian_packet((N,) * 3, h, (0, 0, 0), k, 1.0).reshape(1, -1)
+    p_b = inputs.gaussian_packet((Nb,) * 3, h, (0, 0, 0), k, 1.0)
+    p_b = p_b * (np.linalg.norm(p_s) / np.linalg.norm(
+        p_b[(Nb - N) // 2:(Nb + N) // 2, (Nb - N) // 2:(Nb + N) // 2, (Nb - N) // 2:(Nb + N) // 2]))
+    n = int(round(T / dt))
+    ref, _, _ = System(big).run(p_b.reshape(1, -1), dt, n)
+    o = (Nb - N) // 2
+    ref = ref.reshape(Nb, Nb, Nb)[o:o + N, o:o + N, o:o + N].reshape(1, -1)
+    errs = {}
+    for name, co in (("dirichlet", None), ("order0", order0(small, 1.0)), ("order1", order1(small, 1.0))):
+        phi, _, _ = System(small, coeffs=co).run(p_s, dt, n)
+        errs[name] = np.linalg.norm(phi - ref) / np.linalg.norm(p_s)
+    # measured 0.63 / 0.47 / 0.23 at kh = 1.25 (a coarse, strongly dispersive case)
+    assert errs["order0"] < 0.85 * errs["dirichlet"]
+    assert errs["order1"] < 0.5 * errs["dirichlet"]
+    assert errs["order1"] < errs["order0"]
+
+
+def test_meanfield_keeps_orbitals_orthonormal():
+    """With zero Dirichlet the mean-field Hamiltonian is Hermitian (V real), so the
+    orbitals stay h^3-orthonormal up to the Taylor truncation; the density term must
+    also change the trajectory relative to the linear problem."""
+    N, h, b = 8, 0.5, 4
+    box = Box((N,) * 3, h)
+    rng = np.random.default_rng(5)
+    psi = inputs.orbital_set((N,) * 3, h, rng, b).reshape(b, -1)
+    mf = System(box, meanfield=(-30.0, 20.0, 1.0 / 6.0))
+    lin = System(box)
+    p1, _, _ = mf.run(psi, 0.005, 40)
+    p2, _, _ = lin.run(psi, 0.005, 40)
+    G = (p1.conj() @ p1.T) * h ** 3
+    assert np.abs(G - np.eye(b)).max() < 1e-8
+    assert np.linalg.norm(p1 - p2) / np.linalg.norm(p2) > 1e-3
+    zero = System(box, meanfield=(0.0, 0.0, 1.0 / 6.0))
+    p3, _, _ = zero.run(psi, 0.005, 40)
+    assert np.array_equal(p3, p2)
