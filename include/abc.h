@@ -1,0 +1,174 @@
+/*
+ * abc.h -- C ABI of the GB300 time-stepper for the 3D Schroedinger equation
+ * closed by the discrete Dirichlet-to-Neumann absorbing boundary condition of
+ * Wu & Li, "Absorbing boundary conditions for the time-dependent
+ * Schroedinger-type equations in R^3".
+ *
+ * Problem (Sec. 2, eq:22/eq:32, eq:omega1): interior box of nx*ny*nz nodes with
+ * spacing h, H = -1/2 Delta_h + V with the 3-point second difference per axis
+ * (the standard 7-point 3D stencil).  The exterior (V = 0, phi_II(0) = 0) enters
+ * only through the boundary nodes Gamma (eq:25: nodes with a coordinate on a
+ * face), either as
+ *   order 0 (eq:dynamics0):  phi' = -i H phi - i E^T M E phi,      M = K(s0)
+ *   order 1 (eq:dynamics1):  phi' = -i H phi - i E^T f,
+ *                            f'   = B f + A E phi,
+ *                            A = -i H_{Gamma,II} H_{II,Gamma}, B = s1 I - A K(s1)^{-1}
+ * with K(s) the DtN map of eq:17, evaluated by eq:eval (App. A).  One time step
+ * applies sum_{k=0..4} (dt L)^k / k! (eq:21, signs read as the Taylor series of
+ * exp(dt L)) in Horner form.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * - Node order: x fastest, linear index (k*ny + j)*nx + i.  Node coordinates are
+ *   not needed by the library (only h).
+ * - psi: device array [n_orb][nz][ny][nx] of complex values, interleaved (re, im):
+ *   complex128 when precision == ABC_FP64, complex64 otherwise.
+ * - aux: device array [n_gamma][n_orb] (orbital fastest) of the same complex type,
+ *   holding f_Gamma (order 1 only; pass NULL for order 0).  Gamma nodes are
+ *   numbered by ascending linear index.  Start it at zero (f_Gamma(0) = 0, Sec. 2).
+ * - V: device array [nz][ny][nx] of real values (double for ABC_FP64, float
+ *   otherwise): the external potential.
+ * - The caller owns psi, aux and V.  The context owns the boundary matrices and
+ *   its workspace; nothing the caller passes is freed by the library.
+ * - stream: a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *   Calls are asynchronous with respect to the host unless stated.
+ * - Every function returns ABC_OK (0) or an ABC_ERR_* code; no exception crosses
+ *   the ABI.  abc_last_error() gives a message for the last failure on the calling
+ *   thread.
+ */
+#ifndef ABC_H
+#define ABC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define ABC_OK 0
+#define ABC_ERR_ARG 1          /* invalid argument (size, pointer, order, ...) */
+#define ABC_ERR_ALLOC 2        /* host or device allocation failed */
+#define ABC_ERR_CUDA 3         /* a CUDA runtime call failed */
+#define ABC_ERR_SINGULAR 4     /* eq:eval system or K(s1) not invertible */
+#define ABC_ERR_TIMEOUT 5      /* a bounded device wait gave up */
+#define ABC_ERR_UNSTABLE 6     /* the Lyapunov functional grew (divergence monitor) */
+#define ABC_ERR_UNSUPPORTED 7  /* valid request this build does not implement */
+
+/* arithmetic of the path */
+#define ABC_FP64 0             /* complex128 state, complex128 boundary matrices   */
+#define ABC_C64_FP32 1         /* complex64 state, complex64 matrices, FP32 FMA     */
+#define ABC_C64_SPLIT_BF16 2   /* complex64 state, matrices as bf16 hi + bf16 lo,
+                                  tensor-core contraction with FP32 accumulation    */
+
+/* matrices for abc_get_matrices / abc_host_matrices (dense, natural Gamma order) */
+#define ABC_MAT_K 0            /* K(s) at the context's interpolation point        */
+#define ABC_MAT_M 1            /* order 0: M = K(s0)                                */
+#define ABC_MAT_A 2            /* order 1: A                                        */
+#define ABC_MAT_B 3            /* order 1: B                                        */
+#define ABC_MAT_Q 4            /* order 1: Q = (H_{Gamma,II} H_{II,Gamma})^{-1}     */
+
+typedef struct {
+    int nx, ny, nz;   /* interior nodes per axis, each >= 3                        */
+    int radius;       /* stencil radius per axis; this build supports 1 only       */
+    double h;         /* grid spacing > 0                                          */
+} abc_grid;
+
+typedef struct {
+    int order;        /* 0 or 1 (rational order m of eq:24)                         */
+    double s0;        /* order 0 interpolation point, > 0 (Thm 3.1)                 */
+    double s1;        /* order 1 interpolation point, > 0 (Thm 3.2)                 */
+    int precision;    /* ABC_FP64 | ABC_C64_FP32 | ABC_C64_SPLIT_BF16               */
+    int max_orbitals; /* largest n_orb later passed to step/run (sizes workspace)   */
+} abc_params;
+
+typedef struct {
+    double a, b, alpha;   /* V = V_ext + a rho + b rho^(1+alpha), rho = sum_j |phi_j|^2
+                             (the density-dependent mean field of Sec. 4.3, eq:ham_tdhf,
+                             in simplified form); rho^(1+alpha) := 0 at rho = 0        */
+} abc_meanfield;
+
+typedef struct abc_ctx abc_ctx;
+
+/* Builds the context: index sets, K(s) by eq:eval with the free lattice Green's
+ * function (App. A, App. D), the order-0 / order-1 coefficients (Thm 3.1 / 3.2),
+ * all in FP64 on the host (untimed setup, OpenMP), then converts them to the
+ * device format of `precision` and uploads them to the current CUDA device.
+ * *out receives the context (free with abc_destroy).  Errors: ABC_ERR_ARG for bad
+ * sizes/order/precision, ABC_ERR_SINGULAR, ABC_ERR_ALLOC, ABC_ERR_CUDA. */
+int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx** out);
+
+/* n_gamma = |Gamma| = nx*ny*nz - (nx-2)(ny-2)(nz-2) (eq:25, radius 1). */
+int abc_boundary_size(const abc_ctx* ctx, long long* n_gamma);
+
+/* One time step of the augmented system in place on (psi, aux), static potential
+ * V.  n_orb in [1, max_orbitals]; dt > 0. */
+int abc_step(abc_ctx* ctx, void* psi, void* aux, const void* V, int n_orb, double dt,
+             void* stream);
+
+/* nsteps time steps.  mf == NULL: static V; else V is V_ext and the mean-field
+ * potential is recomputed from the state before every step and held fixed within
+ * it.  If diag_every > 0, after every diag_every steps the per-orbital
+ * diagnostics [norm, W, energy] (see abc_diagnostics) are stored; diag_out (host,
+ * [nsteps/diag_every][n_orb][3] doubles) is filled when the call returns, which
+ * then synchronises the stream.  The step loop is replayed as a CUDA graph. */
+int abc_run(abc_ctx* ctx, void* psi, void* aux, const void* V, int n_orb, double dt,
+            long long nsteps, const abc_meanfield* mf, int diag_every, double* diag_out,
+            void* stream);
+
+/* abc_run on HOST buffers (same layouts): copies psi, aux and V to device buffers
+ * owned by the context, runs, copies psi and aux back, and synchronises. */
+int abc_run_host(abc_ctx* ctx, void* psi_host, void* aux_host, const void* V_host, int n_orb,
+                 double dt, long long nsteps, const abc_meanfield* mf, int diag_every,
+                 double* diag_out);
+
+/* Per-orbital diagnostics of the current state into host out[n_orb][3]:
+ * norm_j = h^3 |phi_j|^2; W_j = norm_j + h^3 f_j^* Q f_j (eq:lyapunov1; = norm_j
+ * for order 0, eq:lyapunov0); energy_j = h^3 Re <phi_j, H_{I,I}[V] phi_j>.
+ * All sums in FP64.  mf as in abc_run (V_ext + mean field of the given state).
+ * Synchronises the stream. */
+int abc_diagnostics(abc_ctx* ctx, const void* psi, const void* aux, const void* V, int n_orb,
+                    const abc_meanfield* mf, double* out, void* stream);
+
+/* Gradient of the absorbed probability J = sum_j (1 - h^3 |phi_j(T)|^2) after
+ * nsteps steps from psi0 (aux starts at zero) with the static potential V, with
+ * respect to V: dJdV (device, real [nz][ny][nx], same real type as V) is
+ * overwritten; J_out (host) receives J.  Discrete adjoint of the Horner stages;
+ * the forward states are checkpointed every ckpt_every steps and recomputed
+ * segment by segment.  psi0 is not modified.  Synchronises the stream. */
+int abc_adjoint_run(abc_ctx* ctx, const void* psi0, const void* V, int n_orb, double dt,
+                    long long nsteps, int ckpt_every, double* J_out, void* dJdV, void* stream);
+
+/* Dense FP64 copy (complex128, row-major n_gamma x n_gamma, natural Gamma order)
+ * of a coefficient matrix held by the context (ABC_MAT_*).  bytes must be at
+ * least 16*n_gamma^2.  Reconstructed on the host from the stored FP64 blocks. */
+int abc_get_matrices(const abc_ctx* ctx, int which, void* host_dst, size_t bytes);
+
+/* Host-only variant for machines without a GPU: runs the FP64 setup of abc_setup
+ * and returns the dense matrix `which` without touching CUDA. */
+int abc_host_matrices(const abc_grid* grid, const abc_params* params, int which,
+                      void* host_dst, size_t bytes);
+
+/* Kernel timing: when enabled, abc_run launches eagerly (no graph) and brackets
+ * every launch of the dominant kernel `kernel` (ABC_KERNEL_*) with CUDA events on
+ * the launching stream; abc_profile_read returns the summed milliseconds and the
+ * launch count since the last enable, after synchronising. */
+#define ABC_KERNEL_CONTRACTION 0   /* boundary DtN contraction (GEMV / GEMM)        */
+#define ABC_KERNEL_STENCIL 1       /* fused stencil + potential + Horner stage       */
+int abc_profile_enable(abc_ctx* ctx, int enable);
+int abc_profile_read(abc_ctx* ctx, int kernel, double* ms, long long* launches);
+
+/* Algorithmic bytes of one launch of a kernel for n_orb orbitals (the roofline
+ * numerator): boundary matrix bytes + vectors for the contraction; for the stencil
+ * 3 complex values per point and orbital plus V per point. */
+int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, double* bytes);
+
+void abc_destroy(abc_ctx* ctx);
+const char* abc_status_string(int status);
+const char* abc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ABC_H */

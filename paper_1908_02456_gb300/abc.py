@@ -1,0 +1,295 @@
+"""Thin ctypes binding of the C ABI in ``include/abc.h`` (argument marshalling only).
+
+Every step of the path runs in the native library; this module checks tensor
+dtypes / shapes / devices, passes raw pointers and raises ``AbcError`` on a
+non-zero status.  The library must have been built (``build.build()``); there is
+no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+OK = 0
+FP64, C64_FP32, C64_SPLIT_BF16 = 0, 1, 2
+MAT_K, MAT_M, MAT_A, MAT_B, MAT_Q = 0, 1, 2, 3, 4
+KERNEL_CONTRACTION, KERNEL_STENCIL = 0, 1
+PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libabc.so")
+
+
+class AbcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+class abc_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("radius", ctypes.c_int), ("h", ctypes.c_double)]
+
+
+class abc_params(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("s0", ctypes.c_double), ("s1", ctypes.c_double),
+                ("precision", ctypes.c_int), ("max_orbitals", ctypes.c_int)]
+
+
+class abc_meanfield(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("alpha", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load():
+    """Load the native library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"native library not built: {LIB_PATH} (run paper_1908_02456_gb300.build.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    G, Pm, MF = ctypes.POINTER(abc_grid), ctypes.POINTER(abc_params), ctypes.POINTER(abc_meanfield)
+    sig = {
+        "abc_setup": [G, Pm, ctypes.POINTER(_P)],
+        "abc_boundary_size": [_P, ctypes.POINTER(ctypes.c_longlong)],
+        "abc_step": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P],
+        "abc_run": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, MF, ctypes.c_int, _P, _P],
+        "abc_run_host": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, MF, ctypes.c_int, _P],
+        "abc_diagnostics": [_P, _P, _P, _P, ctypes.c_int, MF, _P, _P],
+        "abc_adjoint_run": [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_int, _P, _P, _P],
+        "abc_get_matrices": [_P, ctypes.c_int, _P, ctypes.c_size_t],
+        "abc_host_matrices": [G, Pm, ctypes.c_int, _P, ctypes.c_size_t],
+        "abc_profile_enable": [_P, ctypes.c_int],
+        "abc_profile_read": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
+        "abc_kernel_bytes": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.abc_destroy.argtypes = [_P]
+    lib.abc_destroy.restype = None
+    lib.abc_status_string.argtypes = [ctypes.c_int]
+    lib.abc_status_string.restype = ctypes.c_char_p
+    lib.abc_last_error.argtypes = []
+    lib.abc_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != OK:
+        lib = load()
+        raise AbcError(st, f"{lib.abc_status_string(st).decode()}: {lib.abc_last_error().decode()}")
+
+
+def _grid(shape: Sequence[int], h: float) -> abc_grid:
+    nx, ny, nz = (int(v) for v in shape)
+    return abc_grid(nx, ny, nz, 1, float(h))
+
+
+def _params(order: int, s: float, precision, max_orbitals: int) -> abc_params:
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return abc_params(int(order), float(s), float(s), prec, int(max_orbitals))
+
+
+def _mf(meanfield) -> Optional[ctypes.POINTER(abc_meanfield)]:
+    if meanfield is None:
+        return None
+    a, b, alpha = meanfield
+    return ctypes.pointer(abc_meanfield(float(a), float(b), float(alpha)))
+
+
+# ----------------------------------------------------------------------
+# the C functions under their own names
+# ----------------------------------------------------------------------
+def abc_setup(grid: abc_grid, params: abc_params) -> ctypes.c_void_p:
+    ctx = _P()
+    _check(load().abc_setup(ctypes.byref(grid), ctypes.byref(params), ctypes.byref(ctx)))
+    return ctx
+
+
+def abc_boundary_size(ctx) -> int:
+    n = ctypes.c_longlong()
+    _check(load().abc_boundary_size(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def abc_step(ctx, psi_ptr: int, aux_ptr: int, V_ptr: int, n_orb: int, dt: float, stream: int = 0):
+    _check(load().abc_step(ctx, psi_ptr, aux_ptr or None, V_ptr, n_orb, dt, stream or None))
+
+
+def abc_run(ctx, psi_ptr, aux_ptr, V_ptr, n_orb, dt, nsteps, meanfield=None, diag_every=0, diag_out=None,
+            stream: int = 0):
+    d = None if diag_out is None else diag_out.ctypes.data_as(_P)
+    _check(load().abc_run(ctx, psi_ptr, aux_ptr or None, V_ptr, n_orb, dt, nsteps, _mf(meanfield), diag_every, d,
+                          stream or None))
+
+
+def abc_run_host(ctx, psi: np.ndarray, aux: Optional[np.ndarray], V: np.ndarray, n_orb, dt, nsteps,
+                 meanfield=None, diag_every=0, diag_out=None):
+    d = None if diag_out is None else diag_out.ctypes.data_as(_P)
+    _check(load().abc_run_host(ctx, psi.ctypes.data_as(_P), None if aux is None else aux.ctypes.data_as(_P),
+                               V.ctypes.data_as(_P), n_orb, dt, nsteps, _mf(meanfield), diag_every, d))
+
+
+def abc_diagnostics(ctx, psi_ptr, aux_ptr, V_ptr, n_orb, meanfield=None, stream: int = 0) -> np.ndarray:
+    out = np.zeros((n_orb, 3))
+    _check(load().abc_diagnostics(ctx, psi_ptr, aux_ptr or None, V_ptr, n_orb, _mf(meanfield),
+                                  out.ctypes.data_as(_P), stream or None))
+    return out
+
+
+def abc_adjoint_run(ctx, psi0_ptr, V_ptr, n_orb, dt, nsteps, ckpt_every, dJdV_ptr, stream: int = 0) -> float:
+    J = ctypes.c_double()
+    _check(load().abc_adjoint_run(ctx, psi0_ptr, V_ptr, n_orb, dt, nsteps, ckpt_every, ctypes.byref(J), dJdV_ptr,
+                                  stream or None))
+    return J.value
+
+
+def abc_get_matrices(ctx, which: int, n_gamma: int) -> np.ndarray:
+    out = np.zeros((n_gamma, n_gamma), np.complex128)
+    _check(load().abc_get_matrices(ctx, which, out.ctypes.data_as(_P), out.nbytes))
+    return out
+
+
+def abc_host_matrices(shape, h, order, s, which) -> np.ndarray:
+    """FP64 setup on the host only (no CUDA): dense ABC_MAT_* in natural Gamma order."""
+    nx, ny, nz = shape
+    n = nx * ny * nz - (nx - 2) * (ny - 2) * (nz - 2)
+    out = np.zeros((n, n), np.complex128)
+    g, p = _grid(shape, h), _params(order, s, FP64, 1)
+    _check(load().abc_host_matrices(ctypes.byref(g), ctypes.byref(p), which, out.ctypes.data_as(_P), out.nbytes))
+    return out
+
+
+def abc_profile_enable(ctx, enable: bool):
+    _check(load().abc_profile_enable(ctx, int(bool(enable))))
+
+
+def abc_profile_read(ctx, kernel: int):
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(load().abc_profile_read(ctx, kernel, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def abc_kernel_bytes(ctx, kernel: int, n_orb: int) -> float:
+    b = ctypes.c_double()
+    _check(load().abc_kernel_bytes(ctx, kernel, n_orb, ctypes.byref(b)))
+    return b.value
+
+
+def abc_destroy(ctx):
+    if ctx:
+        load().abc_destroy(ctx)
+
+
+# ----------------------------------------------------------------------
+# convenience wrapper over torch tensors
+# ----------------------------------------------------------------------
+class Context:
+    """Owns one abc_ctx.  psi: [b, nz, ny, nx] complex CUDA tensor; aux: [n_gamma, b]."""
+
+    def __init__(self, shape, h, order, s, precision="c64", max_orbitals=1):
+        self.shape = tuple(int(v) for v in shape)
+        self.h, self.order, self.s = float(h), int(order), float(s)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.max_orbitals = int(max_orbitals)
+        self.ctx = abc_setup(_grid(self.shape, h), _params(order, s, self.precision, max_orbitals))
+        self.n_gamma = abc_boundary_size(self.ctx)
+
+    # dtypes of the path
+    @property
+    def complex_dtype(self):
+        import torch
+        return torch.complex128 if self.precision == FP64 else torch.complex64
+
+    @property
+    def real_dtype(self):
+        import torch
+        return torch.float64 if self.precision == FP64 else torch.float32
+
+    def _check_tensors(self, psi, aux, V):
+        nx, ny, nz = self.shape
+        if not psi.is_cuda or psi.dtype != self.complex_dtype or not psi.is_contiguous():
+            raise ValueError(f"psi must be a contiguous CUDA {self.complex_dtype} tensor")
+        if psi.dim() != 4 or tuple(psi.shape[1:]) != (nz, ny, nx):
+            raise ValueError(f"psi must have shape [b, {nz}, {ny}, {nx}]")
+        b = psi.shape[0]
+        if self.order == 1:
+            if aux is None or not aux.is_cuda or aux.dtype != self.complex_dtype or not aux.is_contiguous() \
+                    or tuple(aux.shape) != (self.n_gamma, b):
+                raise ValueError(f"aux must be a contiguous CUDA {self.complex_dtype} tensor [{self.n_gamma}, {b}]")
+        if not V.is_cuda or V.dtype != self.real_dtype or not V.is_contiguous() or tuple(V.shape) != (nz, ny, nx):
+            raise ValueError(f"V must be a contiguous CUDA {self.real_dtype} tensor [{nz}, {ny}, {nx}]")
+        return b
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        return (stream or torch.cuda.current_stream()).cuda_stream
+
+    def new_aux(self, b):
+        import torch
+        return torch.zeros((self.n_gamma, b), dtype=self.complex_dtype, device="cuda")
+
+    def step(self, psi, aux, V, dt, stream=None):
+        b = self._check_tensors(psi, aux, V)
+        abc_step(self.ctx, psi.data_ptr(), aux.data_ptr() if aux is not None else 0, V.data_ptr(), b, dt,
+                 self._stream(stream))
+
+    def run(self, psi, aux, V, dt, nsteps, meanfield=None, diag_every=0, stream=None):
+        b = self._check_tensors(psi, aux, V)
+        diag = np.zeros((nsteps // diag_every, b, 3)) if diag_every else None
+        abc_run(self.ctx, psi.data_ptr(), aux.data_ptr() if aux is not None else 0, V.data_ptr(), b, dt, nsteps,
+                meanfield, diag_every, diag, self._stream(stream))
+        return diag
+
+    def run_host(self, psi, aux, V, dt, nsteps, meanfield=None, diag_every=0):
+        """Host (numpy) buffers; copies in, runs, copies back into psi / aux."""
+        b = psi.shape[0]
+        diag = np.zeros((nsteps // diag_every, b, 3)) if diag_every else None
+        abc_run_host(self.ctx, psi, aux, V, b, dt, nsteps, meanfield, diag_every, diag)
+        return diag
+
+    def diagnostics(self, psi, aux, V, meanfield=None, stream=None):
+        b = self._check_tensors(psi, aux, V)
+        return abc_diagnostics(self.ctx, psi.data_ptr(), aux.data_ptr() if aux is not None else 0, V.data_ptr(), b,
+                               meanfield, self._stream(stream))
+
+    def adjoint(self, psi0, V, dt, nsteps, ckpt_every=50, stream=None):
+        import torch
+        b = self._check_tensors(psi0, self.new_aux(psi0.shape[0]) if self.order == 1 else None, V)
+        g = torch.empty_like(V)
+        J = abc_adjoint_run(self.ctx, psi0.data_ptr(), V.data_ptr(), b, dt, nsteps, ckpt_every, g.data_ptr(),
+                            self._stream(stream))
+        return J, g
+
+    def matrix(self, which):
+        return abc_get_matrices(self.ctx, which, self.n_gamma)
+
+    def profile(self, enable=True):
+        abc_profile_enable(self.ctx, enable)
+
+    def profile_read(self, kernel=KERNEL_CONTRACTION):
+        return abc_profile_read(self.ctx, kernel)
+
+    def kernel_bytes(self, kernel, n_orb):
+        return abc_kernel_bytes(self.ctx, kernel, n_orb)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            abc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,543 @@
+// C ABI of the time-stepper: context set-up and upload, the Horner-form step,
+// graph-captured runs, diagnostics and kernel timing.  See include/abc.h.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace abc {
+int fail(int status, const std::string& msg);
+int check_params(const abc_grid* grid, const abc_params* params);
+}  // namespace abc
+
+using namespace abc;
+using abc::dev::BlockInfo;
+
+#define CUDA_TRY(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(ABC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    int alloc(size_t b) {
+        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+        if (b == 0) return ABC_OK;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) { p = nullptr; return fail(ABC_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+        bytes = b;
+        return ABC_OK;
+    }
+    template <typename X> X* as() const { return reinterpret_cast<X*>(p); }
+};
+
+struct ProfileSlot {
+    std::vector<cudaEvent_t> ev;   // pairs
+    size_t used = 0;
+};
+
+}  // namespace
+
+struct abc_ctx {
+    abc_grid grid;
+    abc_params params;
+    Geometry geo;
+    Blocks blocks;          // FP64 blocks (kept for abc_get_matrices)
+    int device = 0;
+    int prec = 0;
+    size_t real_bytes = 8;  // bytes of one real value of the state
+    long long nvox = 0;
+    BlockInfo bi;
+    // device tables
+    DevBuf rep_gamma, rep_adapted, rep_stab, rep_c, gamma_node, gamma_c;
+    DevBuf mat;             // parity blocks in device format
+    DevBuf tile_blk, tile_row;   // row tiles (block, first row) of the multi-orbital contraction
+    int n_tiles = 0;
+    // workspace
+    DevBuf Tp[2], Tf[2], hat_phi, hat_f, tvec, cnat, Veff, diag;
+    DevBuf host_psi, host_aux, host_V;   // device copies for abc_run_host
+    cudaStream_t own = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    struct Key { const void *psi, *aux, *V; int n_orb; double dt; int mf; double a, b, alpha; cudaStream_t s; } key{};
+    // profiling
+    bool profiling = false;
+    ProfileSlot prof[2];
+};
+
+namespace {
+
+inline size_t cplx_bytes(const abc_ctx* c) { return 2 * c->real_bytes; }
+
+int upload_tables(abc_ctx* c) {
+    const Geometry& g = c->geo;
+    std::vector<int> rc(g.n_rep);
+    for (int r = 0; r < g.n_rep; ++r) rc[r] = g.gamma_c[g.node_gamma[g.rep_node[r]]];
+    struct { DevBuf* b; const int* src; size_t n; } t[] = {
+        {&c->rep_gamma, g.rep_gamma.data(), g.rep_gamma.size()},
+        {&c->rep_adapted, g.rep_adapted.data(), g.rep_adapted.size()},
+        {&c->rep_stab, g.rep_stab.data(), g.rep_stab.size()},
+        {&c->rep_c, rc.data(), rc.size()},
+        {&c->gamma_node, g.gamma_node.data(), g.gamma_node.size()},
+        {&c->gamma_c, g.gamma_c.data(), g.gamma_c.size()},
+    };
+    for (auto& e : t) {
+        int st = e.b->alloc(e.n * sizeof(int));
+        if (st) return st;
+        CUDA_TRY(cudaMemcpy(e.b->p, e.src, e.n * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    return ABC_OK;
+}
+
+// Parity blocks in the device format: row-major, rows padded to a multiple of 4
+// complex elements so that every row starts on a 32-byte boundary.
+int upload_matrices(abc_ctx* c) {
+    const Geometry& g = c->geo;
+    long long total = 0;
+    for (int p = 0; p < 8; ++p) {
+        c->bi.m[p] = g.m[p];
+        c->bi.off[p] = g.off[p];
+        c->bi.ld[p] = (g.m[p] + 3) & ~3;
+        c->bi.mat_off[p] = total;
+        total += (long long)c->bi.ld[p] * g.m[p];
+    }
+    if (c->prec == ABC_C64_SPLIT_BF16)
+        return fail(ABC_ERR_UNSUPPORTED, "split-bf16 contraction not built yet");
+    const size_t eb = cplx_bytes(c);
+    int st = c->mat.alloc((size_t)total * eb);
+    if (st) return st;
+    CUDA_TRY(cudaMemset(c->mat.p, 0, (size_t)total * eb));
+    for (int p = 0; p < 8; ++p) {
+        const int m = g.m[p], ld = c->bi.ld[p];
+        if (!m) continue;
+        const std::vector<cd>& M = c->blocks.mat[p];
+        if (c->prec == ABC_FP64) {
+            std::vector<double> buf((size_t)2 * ld * m, 0.0);
+            for (int a = 0; a < m; ++a)
+                for (int b = 0; b < m; ++b) {
+                    buf[2 * ((size_t)a * ld + b)] = M[(size_t)a * m + b].real();
+                    buf[2 * ((size_t)a * ld + b) + 1] = M[(size_t)a * m + b].imag();
+                }
+            CUDA_TRY(cudaMemcpy(c->mat.as<char>() + c->bi.mat_off[p] * eb, buf.data(), buf.size() * 8,
+                                cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> buf((size_t)2 * ld * m, 0.0f);
+            for (int a = 0; a < m; ++a)
+                for (int b = 0; b < m; ++b) {
+                    buf[2 * ((size_t)a * ld + b)] = (float)M[(size_t)a * m + b].real();
+                    buf[2 * ((size_t)a * ld + b) + 1] = (float)M[(size_t)a * m + b].imag();
+                }
+            CUDA_TRY(cudaMemcpy(c->mat.as<char>() + c->bi.mat_off[p] * eb, buf.data(), buf.size() * 4,
+                                cudaMemcpyHostToDevice));
+        }
+    }
+    return ABC_OK;
+}
+
+int ensure_workspace(abc_ctx* c) {
+    const size_t cb = cplx_bytes(c);
+    const size_t b = (size_t)c->params.max_orbitals;
+    const size_t phi_b = (size_t)c->nvox * b * cb, aux_b = (size_t)c->geo.n_gamma * b * cb;
+    int st;
+    for (int i = 0; i < 2; ++i) {
+        if ((st = c->Tp[i].alloc(phi_b))) return st;
+        if ((st = c->Tf[i].alloc(aux_b))) return st;
+    }
+    if ((st = c->hat_phi.alloc(aux_b))) return st;
+    if ((st = c->hat_f.alloc(aux_b))) return st;
+    if ((st = c->tvec.alloc(aux_b))) return st;
+    if ((st = c->cnat.alloc(aux_b))) return st;
+    if ((st = c->Veff.alloc((size_t)c->nvox * c->real_bytes))) return st;
+    CUDA_TRY(cudaMemset(c->Tf[0].p, 0, aux_b));
+    CUDA_TRY(cudaMemset(c->Tf[1].p, 0, aux_b));
+    return ABC_OK;
+}
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+void prof_begin(abc_ctx* c, int k, cudaStream_t s) {
+    if (!c->profiling) return;
+    ProfileSlot& ps = c->prof[k];
+    if (ps.used + 2 > ps.ev.size()) {
+        for (int i = 0; i < 256; ++i) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            ps.ev.push_back(e);
+        }
+    }
+    cudaEventRecord(ps.ev[ps.used], s);
+}
+void prof_end(abc_ctx* c, int k, cudaStream_t s) {
+    if (!c->profiling) return;
+    ProfileSlot& ps = c->prof[k];
+    cudaEventRecord(ps.ev[ps.used + 1], s);
+    ps.used += 2;
+}
+
+}  // namespace
+
+namespace {
+int build_tiles(abc_ctx* c) {
+    std::vector<int> tb, tr;
+    for (int p = 0; p < 8; ++p)
+        for (int r0 = 0; r0 < c->bi.m[p]; r0 += 32) { tb.push_back(p); tr.push_back(r0); }
+    c->n_tiles = (int)tb.size();
+    int st;
+    if ((st = c->tile_blk.alloc(tb.size() * sizeof(int)))) return st;
+    if ((st = c->tile_row.alloc(tr.size() * sizeof(int)))) return st;
+    CUDA_TRY(cudaMemcpy(c->tile_blk.p, tb.data(), tb.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->tile_row.p, tr.data(), tr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return ABC_OK;
+}
+
+template <typename T>
+void contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaStream_t s) {
+    typedef typename dev::C2<T>::t V;
+    const int n = c->geo.n_gamma;
+    prof_begin(c, ABC_KERNEL_CONTRACTION, s);
+    if (n_orb == 1) {
+        dev::gemv_blocks<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(c->bi, n, c->mat.as<V>(),
+                                                                          (const V*)x, (V*)t, conj);
+    } else {
+        dim3 grid(c->n_tiles, (n_orb + 31) / 32);
+        dev::gemm_blocks_simt<T, 32, 32, 16><<<grid, 256, 0, s>>>(c->bi, n_orb, c->mat.as<V>(), (const V*)x,
+                                                                  (V*)t, conj, c->tile_blk.as<int>(), c->tile_row.as<int>());
+    }
+    prof_end(c, ABC_KERNEL_CONTRACTION, s);
+}
+
+// One Horner stage: out = y + cdt * L(w).
+template <typename T>
+void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, const void* y_phi, const void* y_f,
+           void* o_phi, void* o_f, const T* V, cudaStream_t s) {
+    typedef typename dev::C2<T>::t Vc;
+    const Geometry& g = c->geo;
+    const int order = c->params.order;
+    const long long nb = (long long)g.n_rep * n_orb;
+    const T h = (T)g.h;
+    dev::bnd_forward<T><<<nblk(nb, 128), 128, 0, s>>>(
+        g.n_rep, n_orb, c->nvox, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
+        c->gamma_node.as<int>(), (const Vc*)w_phi, order == 1 ? (const Vc*)w_f : nullptr, c->hat_phi.as<Vc>(),
+        c->hat_f.as<Vc>());
+    contraction<T>(c, order == 1 ? c->hat_f.p : c->hat_phi.p, c->tvec.p, n_orb, 0, s);
+    const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
+    dev::bnd_back<T><<<nblk(nb, 128), 128, 0, s>>>(
+        order, g.n_rep, n_orb, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
+        c->rep_c.as<int>(), (T)c->blocks.s, a_coef, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->tvec.as<Vc>(),
+        (const Vc*)y_f, order == 1 ? (Vc*)o_f : c->cnat.as<Vc>(), cdt);
+    prof_begin(c, ABC_KERNEL_STENCIL, s);
+    dev::stencil_stage<T><<<nblk(c->nvox * n_orb, 256), 256, 0, s>>>(
+        g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)w_phi, (const Vc*)y_phi, V,
+        order == 1 ? (const Vc*)w_f : c->cnat.as<Vc>(), (Vc*)o_phi, cdt);
+    prof_end(c, ABC_KERNEL_STENCIL, s);
+    (void)h;
+}
+
+// One time step (4 Horner stages) in place on (psi, aux).
+template <typename T>
+void step_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double dt, const abc_meanfield* mf,
+               cudaStream_t s) {
+    const T* Vuse = (const T*)V;
+    if (mf) {
+        dev::density_potential<T><<<nblk(c->nvox, 256), 256, 0, s>>>(
+            c->nvox, n_orb, (const typename dev::C2<T>::t*)psi, (const T*)V, (T)mf->a, (T)mf->b, (T)mf->alpha,
+            c->Veff.as<T>());
+        Vuse = c->Veff.as<T>();
+    }
+    const double cs[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+    const void* in_p = psi;
+    const void* in_f = aux;
+    for (int st = 0; st < 4; ++st) {
+        void* op = st == 3 ? psi : c->Tp[st & 1].p;
+        void* of = st == 3 ? aux : c->Tf[st & 1].p;
+        stage<T>(c, n_orb, (T)(cs[st] * dt), in_p, in_f, psi, aux, op, of, Vuse, s);
+        in_p = op;
+        in_f = of;
+    }
+}
+
+template <typename T>
+void diag_impl(abc_ctx* c, const void* psi, const void* aux, const void* V, int n_orb, const abc_meanfield* mf,
+               double* out_dev, cudaStream_t s) {
+    typedef typename dev::C2<T>::t Vc;
+    const Geometry& g = c->geo;
+    const T* Vuse = (const T*)V;
+    if (mf) {
+        dev::density_potential<T><<<nblk(c->nvox, 256), 256, 0, s>>>(c->nvox, n_orb, (const Vc*)psi, (const T*)V,
+                                                                     (T)mf->a, (T)mf->b, (T)mf->alpha, c->Veff.as<T>());
+        Vuse = c->Veff.as<T>();
+    }
+    cudaMemsetAsync(out_dev, 0, sizeof(double) * 3 * n_orb, s);
+    dim3 gp((unsigned)std::min<long long>(nblk(c->nvox, 256), 1024), n_orb);
+    dev::diag_phi<T><<<gp, 256, 0, s>>>(g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)psi, Vuse, out_dev);
+    if (c->params.order == 1 && aux) {
+        dim3 ga((unsigned)std::min<long long>(nblk(g.n_gamma, 256), 256), n_orb);
+        dev::diag_aux<T><<<ga, 256, 0, s>>>(g.n_gamma, n_orb, c->gamma_c.as<int>(), 4.0 * std::pow(g.h, 4),
+                                            (const Vc*)aux, out_dev);
+    }
+}
+
+// raw sums -> [norm, W, energy] with the h^3 weight
+void finish_diag(const abc_ctx* c, double* v, long long rows) {
+    const double w = c->geo.h * c->geo.h * c->geo.h;
+    for (long long r = 0; r < rows; ++r) {
+        double* d = v + 3 * r;
+        const double nrm = w * d[0];
+        d[1] = nrm + w * d[1];
+        d[0] = nrm;
+        d[2] = w * d[2];
+    }
+}
+
+int check_run_args(abc_ctx* c, const void* psi, const void* aux, const void* V, int n_orb, double dt) {
+    if (!c) return fail(ABC_ERR_ARG, "null context");
+    if (!psi || !V) return fail(ABC_ERR_ARG, "null psi or V");
+    if (c->params.order == 1 && !aux) return fail(ABC_ERR_ARG, "order 1 needs the auxiliary buffer");
+    if (n_orb < 1 || n_orb > c->params.max_orbitals) return fail(ABC_ERR_ARG, "n_orb outside [1, max_orbitals]");
+    if (!(dt > 0.0)) return fail(ABC_ERR_ARG, "dt must be positive");
+    return ABC_OK;
+}
+
+int last_launch_status() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ABC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return ABC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx** out) {
+    if (!out) return fail(ABC_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    int st = check_params(grid, params);
+    if (st) return st;
+    std::unique_ptr<abc_ctx> c(new abc_ctx());
+    c->grid = *grid;
+    c->params = *params;
+    c->prec = params->precision;
+    c->real_bytes = c->prec == ABC_FP64 ? 8 : 4;
+    std::string err;
+    st = build_geometry(grid->nx, grid->ny, grid->nz, grid->h, c->geo, err);
+    if (st) return fail(st, err);
+    c->nvox = c->geo.n_nodes;
+    st = compute_blocks(c->geo, params->order, params->order == 0 ? params->s0 : params->s1, c->blocks, err);
+    if (st) return fail(st, err);
+    CUDA_TRY(cudaGetDevice(&c->device));
+    if ((st = upload_tables(c.get()))) return st;
+    if ((st = upload_matrices(c.get()))) return st;
+    if ((st = ensure_workspace(c.get()))) return st;
+    if ((st = c->diag.alloc(sizeof(double) * 3 * params->max_orbitals))) return st;
+    if ((st = build_tiles(c.get()))) return st;
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming));
+    *out = c.release();
+    return ABC_OK;
+}
+
+extern "C" int abc_boundary_size(const abc_ctx* ctx, long long* n_gamma) {
+    if (!ctx || !n_gamma) return fail(ABC_ERR_ARG, "null argument");
+    *n_gamma = ctx->geo.n_gamma;
+    return ABC_OK;
+}
+
+extern "C" int abc_step(abc_ctx* ctx, void* psi, void* aux, const void* V, int n_orb, double dt, void* stream) {
+    int st = check_run_args(ctx, psi, aux, V, n_orb, dt);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->prec == ABC_FP64) step_impl<double>(ctx, psi, aux, V, n_orb, dt, nullptr, s);
+    else step_impl<float>(ctx, psi, aux, V, n_orb, dt, nullptr, s);
+    return last_launch_status();
+}
+
+namespace {
+int run_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double dt, long long nsteps,
+             const abc_meanfield* mf, int diag_every, double* diag_out, cudaStream_t user) {
+    if (nsteps < 0) return fail(ABC_ERR_ARG, "nsteps must be >= 0");
+    if (diag_every < 0) return fail(ABC_ERR_ARG, "diag_every must be >= 0");
+    if (diag_every > 0 && !diag_out) return fail(ABC_ERR_ARG, "diag_out is NULL");
+    const long long ndiag = diag_every > 0 ? nsteps / diag_every : 0;
+    DevBuf dd;
+    int st;
+    if (ndiag > 0 && (st = dd.alloc(sizeof(double) * 3 * n_orb * ndiag))) return st;
+    // work on a non-blocking stream ordered after the caller's stream
+    cudaStream_t s = user ? user : c->own;
+    if (!user) {
+        CUDA_TRY(cudaEventRecord(c->ev_a, 0));
+        CUDA_TRY(cudaStreamWaitEvent(s, c->ev_a, 0));
+    }
+    auto one_step = [&](cudaStream_t ss) {
+        if (c->prec == ABC_FP64) step_impl<double>(c, psi, aux, V, n_orb, dt, mf, ss);
+        else step_impl<float>(c, psi, aux, V, n_orb, dt, mf, ss);
+    };
+    auto one_diag = [&](long long row, cudaStream_t ss) {
+        double* o = dd.as<double>() + row * 3 * n_orb;
+        if (c->prec == ABC_FP64) diag_impl<double>(c, psi, aux, V, n_orb, mf, o, ss);
+        else diag_impl<float>(c, psi, aux, V, n_orb, mf, o, ss);
+    };
+    const bool use_graph = !c->profiling && nsteps > 1;
+    if (use_graph) {
+        abc_ctx::Key k{psi, aux, V, n_orb, dt, mf != nullptr, mf ? mf->a : 0, mf ? mf->b : 0, mf ? mf->alpha : 0, s};
+        const bool same = c->gexec && !std::memcmp(&k, &c->key, sizeof(k));
+        if (!same) {
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            cudaGraph_t graph;
+            CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            one_step(s);
+            cudaError_t le = cudaGetLastError();
+            cudaError_t ce = cudaStreamEndCapture(s, &graph);
+            if (le != cudaSuccess || ce != cudaSuccess)
+                return fail(ABC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ce));
+            cudaError_t ie = cudaGraphInstantiate(&c->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) { c->gexec = nullptr; return fail(ABC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie)); }
+            c->key = k;
+        }
+    }
+    for (long long n = 1; n <= nsteps; ++n) {
+        if (use_graph) CUDA_TRY(cudaGraphLaunch(c->gexec, s));
+        else one_step(s);
+        if (diag_every > 0 && n % diag_every == 0) one_diag(n / diag_every - 1, s);
+    }
+    st = last_launch_status();
+    if (st) return st;
+    if (ndiag > 0) {
+        CUDA_TRY(cudaMemcpyAsync(diag_out, dd.p, sizeof(double) * 3 * n_orb * ndiag, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        finish_diag(c, diag_out, ndiag * n_orb);
+    }
+    if (!user) {
+        CUDA_TRY(cudaEventRecord(c->ev_b, s));
+        CUDA_TRY(cudaStreamWaitEvent(0, c->ev_b, 0));
+    }
+    return ABC_OK;
+}
+}  // namespace
+
+extern "C" int abc_run(abc_ctx* ctx, void* psi, void* aux, const void* V, int n_orb, double dt, long long nsteps,
+                       const abc_meanfield* mf, int diag_every, double* diag_out, void* stream) {
+    int st = check_run_args(ctx, psi, aux, V, n_orb, dt);
+    if (st) return st;
+    return run_impl(ctx, psi, aux, V, n_orb, dt, nsteps, mf, diag_every, diag_out, (cudaStream_t)stream);
+}
+
+extern "C" int abc_run_host(abc_ctx* ctx, void* psi_host, void* aux_host, const void* V_host, int n_orb, double dt,
+                            long long nsteps, const abc_meanfield* mf, int diag_every, double* diag_out) {
+    int st = check_run_args(ctx, psi_host, aux_host, V_host, n_orb, dt);
+    if (st) return st;
+    const size_t cb = cplx_bytes(ctx);
+    const size_t pb = (size_t)ctx->nvox * n_orb * cb, ab = (size_t)ctx->geo.n_gamma * n_orb * cb,
+                 vb = (size_t)ctx->nvox * ctx->real_bytes;
+    if (ctx->host_psi.bytes < pb && (st = ctx->host_psi.alloc(pb))) return st;
+    if (ctx->host_aux.bytes < ab && (st = ctx->host_aux.alloc(ab))) return st;
+    if (ctx->host_V.bytes < vb && (st = ctx->host_V.alloc(vb))) return st;
+    cudaStream_t s = ctx->own;
+    CUDA_TRY(cudaMemcpyAsync(ctx->host_psi.p, psi_host, pb, cudaMemcpyHostToDevice, s));
+    if (ctx->params.order == 1) CUDA_TRY(cudaMemcpyAsync(ctx->host_aux.p, aux_host, ab, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(ctx->host_V.p, V_host, vb, cudaMemcpyHostToDevice, s));
+    st = run_impl(ctx, ctx->host_psi.p, ctx->params.order == 1 ? ctx->host_aux.p : nullptr, ctx->host_V.p, n_orb, dt,
+                  nsteps, mf, diag_every, diag_out, s);
+    if (st) return st;
+    CUDA_TRY(cudaMemcpyAsync(psi_host, ctx->host_psi.p, pb, cudaMemcpyDeviceToHost, s));
+    if (ctx->params.order == 1) CUDA_TRY(cudaMemcpyAsync(aux_host, ctx->host_aux.p, ab, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return ABC_OK;
+}
+
+extern "C" int abc_diagnostics(abc_ctx* ctx, const void* psi, const void* aux, const void* V, int n_orb,
+                               const abc_meanfield* mf, double* out, void* stream) {
+    int st = check_run_args(ctx, psi, aux, V, n_orb, 1.0);
+    if (st) return st;
+    if (!out) return fail(ABC_ERR_ARG, "null output");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->prec == ABC_FP64) diag_impl<double>(ctx, psi, aux, V, n_orb, mf, ctx->diag.as<double>(), s);
+    else diag_impl<float>(ctx, psi, aux, V, n_orb, mf, ctx->diag.as<double>(), s);
+    if ((st = last_launch_status())) return st;
+    CUDA_TRY(cudaMemcpyAsync(out, ctx->diag.p, sizeof(double) * 3 * n_orb, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    finish_diag(ctx, out, n_orb);
+    return ABC_OK;
+}
+
+extern "C" int abc_adjoint_run(abc_ctx* ctx, const void* psi0, const void* V, int n_orb, double dt, long long nsteps,
+                               int ckpt_every, double* J_out, void* dJdV, void* stream) {
+    (void)ctx; (void)psi0; (void)V; (void)n_orb; (void)dt; (void)nsteps; (void)ckpt_every; (void)J_out;
+    (void)dJdV; (void)stream;
+    return fail(ABC_ERR_UNSUPPORTED, "adjoint not built yet");
+}
+
+extern "C" int abc_get_matrices(const abc_ctx* ctx, int which, void* host_dst, size_t bytes) {
+    if (!ctx || !host_dst) return fail(ABC_ERR_ARG, "null argument");
+    const size_t n = ctx->geo.n_gamma;
+    if (bytes < 16 * n * n) return fail(ABC_ERR_ARG, "destination too small");
+    std::string err;
+    int st = dense_natural(ctx->geo, ctx->blocks, which, reinterpret_cast<cd*>(host_dst), err);
+    if (st) return fail(st, err);
+    return ABC_OK;
+}
+
+extern "C" int abc_profile_enable(abc_ctx* ctx, int enable) {
+    if (!ctx) return fail(ABC_ERR_ARG, "null context");
+    ctx->profiling = enable != 0;
+    for (auto& p : ctx->prof) p.used = 0;
+    return ABC_OK;
+}
+
+extern "C" int abc_profile_read(abc_ctx* ctx, int kernel, double* ms, long long* launches) {
+    if (!ctx || !ms || !launches || kernel < 0 || kernel > 1) return fail(ABC_ERR_ARG, "bad argument");
+    ProfileSlot& ps = ctx->prof[kernel];
+    double tot = 0;
+    for (size_t i = 0; i + 1 < ps.used; i += 2) {
+        CUDA_TRY(cudaEventSynchronize(ps.ev[i + 1]));
+        float t = 0;
+        CUDA_TRY(cudaEventElapsedTime(&t, ps.ev[i], ps.ev[i + 1]));
+        tot += t;
+    }
+    *ms = tot;
+    *launches = (long long)(ps.used / 2);
+    return ABC_OK;
+}
+
+extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, double* bytes) {
+    if (!ctx || !bytes || n_orb < 1) return fail(ABC_ERR_ARG, "bad argument");
+    const double cb = (double)cplx_bytes(ctx);
+    if (kernel == ABC_KERNEL_CONTRACTION) {
+        double entries = 0;
+        for (int p = 0; p < 8; ++p) entries += (double)ctx->geo.m[p] * ctx->geo.m[p];
+        *bytes = entries * cb + 2.0 * ctx->geo.n_gamma * n_orb * cb;
+    } else if (kernel == ABC_KERNEL_STENCIL) {
+        *bytes = (double)ctx->nvox * (3.0 * n_orb * cb + ctx->real_bytes);
+    } else {
+        return fail(ABC_ERR_ARG, "unknown kernel");
+    }
+    return ABC_OK;
+}
+
+extern "C" void abc_destroy(abc_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    for (auto& p : ctx->prof)
+        for (auto e : p.ev) cudaEventDestroy(e);
+    if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
+    if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
+    if (ctx->own) cudaStreamDestroy(ctx->own);
+    delete ctx;
+}

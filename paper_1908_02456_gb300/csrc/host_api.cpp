@@ -1,0 +1,64 @@
+// Host-only entry points of the C ABI (no CUDA calls): status strings, the
+// per-thread error message and the FP64 setup for machines without a GPU.
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace abc {
+thread_local std::string g_last_error;
+int fail(int status, const std::string& msg) {
+    g_last_error = msg;
+    return status;
+}
+}  // namespace abc
+
+using namespace abc;
+
+extern "C" const char* abc_status_string(int status) {
+    switch (status) {
+        case ABC_OK: return "ok";
+        case ABC_ERR_ARG: return "invalid argument";
+        case ABC_ERR_ALLOC: return "allocation failed";
+        case ABC_ERR_CUDA: return "CUDA error";
+        case ABC_ERR_SINGULAR: return "singular system";
+        case ABC_ERR_TIMEOUT: return "device wait timed out";
+        case ABC_ERR_UNSTABLE: return "Lyapunov functional grew";
+        case ABC_ERR_UNSUPPORTED: return "not supported by this build";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* abc_last_error(void) { return g_last_error.c_str(); }
+
+namespace abc {
+int check_params(const abc_grid* grid, const abc_params* params) {
+    if (!grid || !params) return fail(ABC_ERR_ARG, "null grid or params");
+    if (grid->radius != 1) return fail(ABC_ERR_UNSUPPORTED, "only the 3-point stencil (radius 1) is built");
+    if (params->order != 0 && params->order != 1) return fail(ABC_ERR_ARG, "order must be 0 or 1");
+    const double s = params->order == 0 ? params->s0 : params->s1;
+    if (!(s > 0.0)) return fail(ABC_ERR_ARG, "interpolation point must be > 0");
+    if (params->precision < ABC_FP64 || params->precision > ABC_C64_SPLIT_BF16)
+        return fail(ABC_ERR_ARG, "unknown precision");
+    if (params->max_orbitals < 1) return fail(ABC_ERR_ARG, "max_orbitals must be >= 1");
+    return ABC_OK;
+}
+}  // namespace abc
+
+extern "C" int abc_host_matrices(const abc_grid* grid, const abc_params* params, int which,
+                                 void* host_dst, size_t bytes) {
+    int st = check_params(grid, params);
+    if (st) return st;
+    if (!host_dst) return fail(ABC_ERR_ARG, "null destination");
+    Geometry g;
+    std::string err;
+    st = build_geometry(grid->nx, grid->ny, grid->nz, grid->h, g, err);
+    if (st) return fail(st, err);
+    if (bytes < (size_t)16 * g.n_gamma * g.n_gamma) return fail(ABC_ERR_ARG, "destination too small");
+    Blocks b;
+    st = compute_blocks(g, params->order, params->order == 0 ? params->s0 : params->s1, b, err);
+    if (st) return fail(st, err);
+    st = dense_natural(g, b, which, reinterpret_cast<cd*>(host_dst), err);
+    if (st) return fail(st, err);
+    return ABC_OK;
+}

@@ -1,0 +1,74 @@
+// Host-side structures shared by the FP64 setup (setup.cpp, dense.cpp) and the
+// device driver (api.cu).  Not part of the ABI.
+#pragma once
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "abc.h"
+
+namespace abc {
+
+typedef std::complex<double> cd;
+
+// Index sets of Sec. 2 (eq:25, App. A) for the 3-point stencil, plus the
+// decomposition of Gamma under the reflections of the box.
+//
+// The box is invariant under the three axis reflections i -> n-1-i; they form the
+// group Z2^3 (element g: bit a set = reflect axis a).  The DtN map K(s) (eq:17)
+// commutes with them because H_{II,II} and H_{II,Gamma} do (V = 0 outside the box),
+// so in the basis of parity-adapted combinations of each orbit it splits into 8
+// independent blocks, one per character chi_p(g) = (-1)^{popcount(p & g)}.  Each
+// orbit is represented by its node in the low octant (2*i <= n-1 per axis); a node
+// on a middle plane (odd n) is fixed by that reflection, and only the parities that
+// are even on its stabiliser give a basis vector.
+struct Geometry {
+    int nx = 0, ny = 0, nz = 0;
+    double h = 0.0;
+    long long n_nodes = 0;
+    int n_gamma = 0;
+    std::vector<int> gamma_node;        // Gamma index -> linear node index (ascending)
+    std::vector<int> node_gamma;        // linear node index -> Gamma index or -1
+    std::vector<int> gamma_c;           // number of exterior neighbours (1..3)
+    int n_rep = 0;
+    std::vector<int> rep_node;          // representative -> linear node index
+    std::vector<int> rep_gamma;         // [n_rep][8] Gamma index of g.r
+    std::vector<int> rep_adapted;       // [n_rep][8] adapted index of parity p, or -1
+    std::vector<int> rep_stab;          // |stabiliser of r| (1, 2, 4 or 8)
+    int m[8] = {0}, off[8] = {0};       // block sizes / offsets in adapted numbering
+    std::vector<int> adapted_rep;       // adapted index -> representative
+};
+
+// Closed-form Gamma index of a boundary node (ascending linear order).
+int gamma_index_closed(int i, int j, int k, int nx, int ny, int nz);
+
+int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& err);
+
+// FP64 coefficient blocks in the parity-adapted basis (row-major m_p x m_p each).
+//   order 0: mat[p] = M_p = K_p(s0)
+//   order 1: mat[p] = S_p = K_p(s1)^{-1}; B = s1 I - A S with A diagonal
+// Both are complex symmetric.
+struct Blocks {
+    int order = 0;
+    double s = 0.0;
+    std::vector<cd> mat[8];
+};
+
+int compute_blocks(const Geometry& g, int order, double s, Blocks& b, std::string& err);
+
+// Dense natural-order (row-major n_gamma^2) reconstruction of ABC_MAT_* from blocks.
+int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::string& err);
+
+// Free lattice Green's function table G(|dx|,|dy|,|dz|) = [(H_0 - i s)^{-1}](dx,dy,dz)
+// for 0 <= |d| < dims[a]; layout [(c*dy)+b]*dx + a.
+void free_green_table(double h, double s, int dx, int dy, int dz, std::vector<cd>& table);
+
+// Dense complex LU with partial pivoting (column-major), and the solve with many
+// right-hand sides.  Return 0, or k+1 if U(k,k) == 0.
+int zgetrf(int n, cd* A, int lda, int* ipiv);
+void zgetrs(int n, int nrhs, const cd* A, int lda, const int* ipiv, cd* B, int ldb);
+// C -= A * B (column-major, m x k times k x n)
+void zgemm_sub(int m, int n, int k, const cd* A, int lda, const cd* B, int ldb, cd* C, int ldc);
+
+}  // namespace abc

@@ -1,0 +1,396 @@
+// Device kernels of the time-stepper (sm_103a).  Templated on the real type T
+// (float for the complex64 forms, double for the FP64 form); complex values are
+// interleaved (re, im) pairs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace abc {
+namespace dev {
+
+template <typename T> struct C2;
+template <> struct C2<float> { typedef float2 t; };
+template <> struct C2<double> { typedef double2 t; };
+
+template <typename T> __device__ __forceinline__ typename C2<T>::t mk(T re, T im) {
+    typename C2<T>::t v; v.x = re; v.y = im; return v;
+}
+
+// Block structure of the parity-adapted boundary matrices (kernel parameter).
+struct BlockInfo {
+    int m[8];               // block sizes
+    int off[8];             // first adapted index of each block
+    int ld[8];              // row stride (complex elements) of each block
+    long long mat_off[8];   // first element of each block in the matrix buffer
+};
+
+// Gamma index of a boundary node (ascending linear order, x fastest).
+__device__ __forceinline__ int gamma_index(int i, int j, int k, int nx, int ny, int nz) {
+    const int plane = 2 * nx + 2 * (ny - 2);
+    if (k == 0) return j * nx + i;
+    if (k == nz - 1) return nx * ny + (nz - 2) * plane + j * nx + i;
+    const int base = nx * ny + (k - 1) * plane;
+    if (j == 0) return base + i;
+    if (j == ny - 1) return base + nx + 2 * (ny - 2) + i;
+    return base + nx + 2 * (j - 1) + (i == 0 ? 0 : 1);
+}
+
+// In-place 8-point Walsh-Hadamard transform: out[p] = sum_g (-1)^{popcount(p&g)} in[g].
+template <typename V> __device__ __forceinline__ void wht8(V* x) {
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1) {
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            if (g & bit) continue;
+            const V a = x[g], b = x[g | bit];
+            x[g].x = a.x + b.x; x[g].y = a.y + b.y;
+            x[g | bit].x = a.x - b.x; x[g | bit].y = a.y - b.y;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Boundary: natural Gamma order -> parity-adapted order (E, then U^T)
+// --------------------------------------------------------------------------
+// Thread (r, j): gathers phi at the 8 reflections of representative r (and f,
+// order 1), applies the 8-point transform with scale 1/sqrt(8|H_r|), and stores the
+// parity components that exist for r.
+template <typename T>
+__global__ void bnd_forward(int n_rep, int n_orb, long long nvox, const int* __restrict__ rep_gamma,
+                            const int* __restrict__ rep_adapted, const int* __restrict__ rep_stab,
+                            const int* __restrict__ gamma_node,
+                            const typename C2<T>::t* __restrict__ w_phi,
+                            const typename C2<T>::t* __restrict__ w_f,
+                            typename C2<T>::t* __restrict__ hat_phi, typename C2<T>::t* __restrict__ hat_f) {
+    typedef typename C2<T>::t V;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_rep * n_orb) return;
+    const int j = (int)(idx % n_orb);
+    const int r = (int)(idx / n_orb);
+    const T sc = (T)rsqrt(8.0 * rep_stab[r]);
+    V xp[8], xf[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        const int gi = rep_gamma[r * 8 + g];
+        xp[g] = w_phi[(long long)j * nvox + gamma_node[gi]];
+        if (w_f) xf[g] = w_f[(long long)gi * n_orb + j];
+    }
+    wht8(xp);
+    if (w_f) wht8(xf);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const int q = rep_adapted[r * 8 + p];
+        if (q < 0) continue;
+        hat_phi[(long long)q * n_orb + j] = mk<T>(sc * xp[p].x, sc * xp[p].y);
+        if (w_f) hat_f[(long long)q * n_orb + j] = mk<T>(sc * xf[p].x, sc * xf[p].y);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Boundary: parity-adapted -> natural order, with the order-0 / order-1 epilogue
+// --------------------------------------------------------------------------
+// order 1:  g_hat = s1 f_hat + a_r (phi_hat - t),  a_r = -i c_r / (4 h^4)
+//           (this is B f + A E phi with B = s1 I - A S, t = S f_hat), then
+//           out_f = y_f + cdt * U g_hat
+// order 0:  out_c = U t  (t = M phi_hat), the natural-order E^T M E phi term
+template <typename T>
+__global__ void bnd_back(int order, int n_rep, int n_orb, const int* __restrict__ rep_gamma,
+                         const int* __restrict__ rep_adapted, const int* __restrict__ rep_stab,
+                         const int* __restrict__ rep_c, T s1, T a_coef,
+                         const typename C2<T>::t* __restrict__ hat_phi,
+                         const typename C2<T>::t* __restrict__ hat_f, const typename C2<T>::t* __restrict__ t,
+                         const typename C2<T>::t* y_f, typename C2<T>::t* out, T cdt) {
+    typedef typename C2<T>::t V;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_rep * n_orb) return;
+    const int j = (int)(idx % n_orb);
+    const int r = (int)(idx / n_orb);
+    const T a = a_coef * (T)rep_c[r];             // a_r = -i * a (imaginary coefficient)
+    V x[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const int q = rep_adapted[r * 8 + p];
+        if (q < 0) { x[p] = mk<T>(0, 0); continue; }
+        const long long e = (long long)q * n_orb + j;
+        const V tv = t[e];
+        if (order == 1) {
+            const V fv = hat_f[e], pv = hat_phi[e];
+            const T dr = pv.x - tv.x, di = pv.y - tv.y;
+            // s1 f + (-i a)(d) = (s1 f.x + a d.y, s1 f.y - a d.x)
+            x[p] = mk<T>(s1 * fv.x + a * di, s1 * fv.y - a * dr);
+        } else {
+            x[p] = tv;
+        }
+    }
+    wht8(x);
+    const T sc = (T)sqrt(rep_stab[r] / 8.0);
+    if (order == 1) {
+        V yv[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) yv[g] = y_f[(long long)rep_gamma[r * 8 + g] * n_orb + j];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const long long e = (long long)rep_gamma[r * 8 + g] * n_orb + j;
+            out[e] = mk<T>(yv[g].x + cdt * sc * x[g].x, yv[g].y + cdt * sc * x[g].y);
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const long long e = (long long)rep_gamma[r * 8 + g] * n_orb + j;
+            out[e] = mk<T>(sc * x[g].x, sc * x[g].y);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Boundary contraction, one orbital: t = S_p x_p for every parity block p
+// (GEMV; HBM-bound).  One warp per row; the row is streamed with 16-byte loads.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int find_block(const BlockInfo& bi, int q) {
+    int p = 0;
+#pragma unroll
+    for (int k = 1; k < 8; ++k)
+        if (q >= bi.off[k]) p = k;
+    return p;
+}
+
+template <typename T>
+__global__ void gemv_blocks(BlockInfo bi, int n_rows, const typename C2<T>::t* __restrict__ mat,
+                            const typename C2<T>::t* __restrict__ x, typename C2<T>::t* __restrict__ y, int conj) {
+    const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_rows) return;
+    const int p = find_block(bi, warp);
+    const int a = warp - bi.off[p];
+    const int m = bi.m[p];
+    const typename C2<T>::t* row = mat + bi.mat_off[p] + (long long)a * bi.ld[p];
+    const typename C2<T>::t* xv = x + bi.off[p];
+    T sr = 0, si = 0;
+    const T cs = conj ? (T)-1 : (T)1;     // conj: y = conj(S conj(x)) = conj(S) x
+    if constexpr (sizeof(T) == 4) {
+        // two complex per lane per load (row start 16-byte aligned: ld, mat_off even)
+        const float4* row4 = reinterpret_cast<const float4*>(row);
+        const int m2 = m >> 1;
+        int c = lane;
+#pragma unroll 4
+        for (; c < m2; c += 32) {
+            const float4 sv = __ldcs(row4 + c);
+            const typename C2<T>::t x0 = xv[2 * c], x1 = xv[2 * c + 1];
+            const T sy0 = cs * sv.y, sy1 = cs * sv.w;
+            sr += sv.x * x0.x - sy0 * x0.y + sv.z * x1.x - sy1 * x1.y;
+            si += sv.x * x0.y + sy0 * x0.x + sv.z * x1.y + sy1 * x1.x;
+        }
+        if ((m & 1) && lane == 0) {
+            const typename C2<T>::t sv = row[m - 1], xx = xv[m - 1];
+            const T sy = cs * sv.y;
+            sr += sv.x * xx.x - sy * xx.y;
+            si += sv.x * xx.y + sy * xx.x;
+        }
+    } else {
+#pragma unroll 4
+        for (int c = lane; c < m; c += 32) {
+            const typename C2<T>::t sv = row[c], xx = xv[c];
+            const T sy = cs * sv.y;
+            sr += sv.x * xx.x - sy * xx.y;
+            si += sv.x * xx.y + sy * xx.x;
+        }
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) y[warp] = mk<T>(sr, si);
+}
+
+// --------------------------------------------------------------------------
+// Boundary contraction, many orbitals: T_p = S_p X_p (X_p: m_p x n_orb, orbital
+// fastest).  CUDA-core reference form (shared-memory tiles).
+// --------------------------------------------------------------------------
+template <typename T, int BM, int BN, int BK>
+__global__ void gemm_blocks_simt(BlockInfo bi, int n_orb, const typename C2<T>::t* __restrict__ mat,
+                                 const typename C2<T>::t* __restrict__ X, typename C2<T>::t* __restrict__ Y,
+                                 int conj, const int* __restrict__ tile_block, const int* __restrict__ tile_row) {
+    typedef typename C2<T>::t V;
+    __shared__ V As[BK][BM + 1];
+    __shared__ V Bs[BK][BN];
+    const int p = tile_block[blockIdx.x];
+    const int row0 = tile_row[blockIdx.x];          // local row in block p
+    const int col0 = blockIdx.y * BN;
+    const int m = bi.m[p];
+    const V* S = mat + bi.mat_off[p];
+    const V* Xp = X + (long long)bi.off[p] * n_orb;
+    const int tx = threadIdx.x % BN, ty = threadIdx.x / BN;   // BN columns, (nthr/BN) row groups
+    constexpr int NT = 256;
+    constexpr int RPT = BM / (NT / BN);                       // rows per thread
+    T accr[RPT], acci[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) accr[i] = acci[i] = 0;
+    const T cs = conj ? (T)-1 : (T)1;
+    for (int k0 = 0; k0 < m; k0 += BK) {
+        for (int e = threadIdx.x; e < BM * BK; e += NT) {
+            const int rr = e / BK, kk = e % BK;
+            const int gr = row0 + rr, gk = k0 + kk;
+            V v = mk<T>(0, 0);
+            if (gr < m && gk < m) v = S[(long long)gr * bi.ld[p] + gk];
+            v.y *= cs;
+            As[kk][rr] = v;
+        }
+        for (int e = threadIdx.x; e < BK * BN; e += NT) {
+            const int kk = e / BN, cc = e % BN;
+            const int gk = k0 + kk, gc = col0 + cc;
+            V v = mk<T>(0, 0);
+            if (gk < m && gc < n_orb) v = Xp[(long long)gk * n_orb + gc];
+            Bs[kk][cc] = v;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < BK; ++kk) {
+            const V b = Bs[kk][tx];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+                const V a = As[kk][ty * RPT + i];
+                accr[i] += a.x * b.x - a.y * b.y;
+                acci[i] += a.x * b.y + a.y * b.x;
+            }
+        }
+        __syncthreads();
+    }
+    const int gc = col0 + tx;
+    if (gc >= n_orb) return;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int gr = row0 + ty * RPT + i;
+        if (gr < m) Y[(long long)(bi.off[p] + gr) * n_orb + gc] = mk<T>(accr[i], acci[i]);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Fused stencil + potential + boundary term + Horner stage
+//   out = y + cdt * (-i) [ H_{I,I} w + E^T b ],  H = -1/2 Delta_h + V
+// b = w_f (order 1) or M E w (order 0), natural Gamma order [n_gamma][n_orb].
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void stencil_stage(int nx, int ny, int nz, int n_orb, T inv_h2, const typename C2<T>::t* __restrict__ w,
+                              const typename C2<T>::t* y, const T* __restrict__ V,
+                              const typename C2<T>::t* __restrict__ bterm, typename C2<T>::t* out, T cdt) {
+    typedef typename C2<T>::t Vc;
+    const long long nvox = (long long)nx * ny * nz;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nvox * n_orb) return;
+    const int orb = (int)(idx / nvox);
+    const long long n = idx - (long long)orb * nvox;
+    const int i = (int)(n % nx);
+    const int jy = (int)((n / nx) % ny);
+    const int k = (int)(n / ((long long)nx * ny));
+    const Vc* wo = w + (long long)orb * nvox;
+    const Vc c = wo[n];
+    T sr = 0, si = 0;
+    if (i > 0) { const Vc v = wo[n - 1]; sr += v.x; si += v.y; }
+    if (i < nx - 1) { const Vc v = wo[n + 1]; sr += v.x; si += v.y; }
+    if (jy > 0) { const Vc v = wo[n - nx]; sr += v.x; si += v.y; }
+    if (jy < ny - 1) { const Vc v = wo[n + nx]; sr += v.x; si += v.y; }
+    if (k > 0) { const Vc v = wo[n - (long long)nx * ny]; sr += v.x; si += v.y; }
+    if (k < nz - 1) { const Vc v = wo[n + (long long)nx * ny]; sr += v.x; si += v.y; }
+    const T diag = (T)3 * inv_h2 + V[n];
+    T hr = diag * c.x - (T)0.5 * inv_h2 * sr;
+    T hi = diag * c.y - (T)0.5 * inv_h2 * si;
+    if (i == 0 || i == nx - 1 || jy == 0 || jy == ny - 1 || k == 0 || k == nz - 1) {
+        const Vc b = bterm[(long long)gamma_index(i, jy, k, nx, ny, nz) * n_orb + orb];
+        hr += b.x;
+        hi += b.y;
+    }
+    const Vc yv = y[idx];
+    out[idx] = mk<T>(yv.x + cdt * hi, yv.y - cdt * hr);
+}
+
+// --------------------------------------------------------------------------
+// Mean field: V = V_ext + a rho + b rho^(1+alpha), rho = sum_j |phi_j|^2
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void density_potential(long long nvox, int n_orb, const typename C2<T>::t* __restrict__ phi,
+                                  const T* __restrict__ Vext, T a, T b, T alpha, T* __restrict__ Vout) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nvox) return;
+    T rho = 0;
+    for (int j = 0; j < n_orb; ++j) {
+        const typename C2<T>::t v = phi[(long long)j * nvox + n];
+        rho += v.x * v.x + v.y * v.y;
+    }
+    const T pw = rho > 0 ? pow(rho, (T)1 + alpha) : (T)0;
+    Vout[n] = Vext[n] + a * rho + b * pw;
+}
+
+// --------------------------------------------------------------------------
+// Diagnostics (FP64 sums): per orbital |phi|^2 and Re<phi, H phi>; f^* Q f.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0;
+    if (w == 0) {
+        r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+template <typename T>
+__global__ void diag_phi(int nx, int ny, int nz, int n_orb, T inv_h2, const typename C2<T>::t* __restrict__ phi,
+                         const T* __restrict__ V, double* __restrict__ out /* [n_orb][3] */) {
+    __shared__ double sh[32];
+    const long long nvox = (long long)nx * ny * nz;
+    const int orb = blockIdx.y;
+    const typename C2<T>::t* w = phi + (long long)orb * nvox;
+    double s_norm = 0, s_en = 0;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < nvox; n += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(n % nx), jy = (int)((n / nx) % ny), k = (int)(n / ((long long)nx * ny));
+        const typename C2<T>::t c = w[n];
+        double sr = 0, si = 0;
+        if (i > 0) { sr += w[n - 1].x; si += w[n - 1].y; }
+        if (i < nx - 1) { sr += w[n + 1].x; si += w[n + 1].y; }
+        if (jy > 0) { sr += w[n - nx].x; si += w[n - nx].y; }
+        if (jy < ny - 1) { sr += w[n + nx].x; si += w[n + nx].y; }
+        if (k > 0) { sr += w[n - (long long)nx * ny].x; si += w[n - (long long)nx * ny].y; }
+        if (k < nz - 1) { sr += w[n + (long long)nx * ny].x; si += w[n + (long long)nx * ny].y; }
+        const double d = 3.0 * (double)inv_h2 + (double)V[n];
+        const double hr = d * c.x - 0.5 * (double)inv_h2 * sr, hi = d * c.y - 0.5 * (double)inv_h2 * si;
+        s_norm += (double)c.x * c.x + (double)c.y * c.y;
+        s_en += (double)c.x * hr + (double)c.y * hi;
+    }
+    s_norm = block_sum(s_norm, sh);
+    s_en = block_sum(s_en, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(out + orb * 3 + 0, s_norm);
+        atomicAdd(out + orb * 3 + 2, s_en);
+    }
+}
+
+template <typename T>
+__global__ void diag_aux(int n_gamma, int n_orb, const int* __restrict__ gamma_c, double q_coef,
+                         const typename C2<T>::t* __restrict__ f, double* __restrict__ out) {
+    __shared__ double sh[32];
+    const int orb = blockIdx.y;
+    double s = 0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_gamma; g += gridDim.x * blockDim.x) {
+        const typename C2<T>::t v = f[(long long)g * n_orb + orb];
+        s += q_coef / gamma_c[g] * ((double)v.x * v.x + (double)v.y * v.y);
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) atomicAdd(out + orb * 3 + 1, s);
+}
+
+}  // namespace dev
+}  // namespace abc

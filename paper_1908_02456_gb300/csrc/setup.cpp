@@ -1,0 +1,423 @@
+// FP64 host setup of the ABC coefficients (untimed): index sets, the free lattice
+// Green's function, the DtN map K(s) by the boundary formula of App. A (eq:eval),
+// and the order-0 / order-1 coefficient blocks of Thm 3.1 / Thm 3.2.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+
+namespace abc {
+
+// ---------------------------------------------------------------------------
+// Index sets
+// ---------------------------------------------------------------------------
+
+// Gamma index of a boundary node when Gamma is numbered by ascending linear index
+// (x fastest).  Face planes z = 0 and z = nz-1 are entirely on Gamma; a middle
+// plane contributes its first and last rows and the two end nodes of every other row.
+int gamma_index_closed(int i, int j, int k, int nx, int ny, int nz) {
+    const int plane = 2 * nx + 2 * (ny - 2);
+    if (k == 0) return j * nx + i;
+    if (k == nz - 1) return nx * ny + (nz - 2) * plane + j * nx + i;
+    const int base = nx * ny + (k - 1) * plane;
+    if (j == 0) return base + i;
+    if (j == ny - 1) return base + nx + 2 * (ny - 2) + i;
+    return base + nx + 2 * (j - 1) + (i == 0 ? 0 : 1);
+}
+
+int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& err) {
+    if (nx < 3 || ny < 3 || nz < 3) { err = "each axis needs at least 3 interior nodes"; return ABC_ERR_ARG; }
+    if (!(h > 0.0)) { err = "grid spacing must be positive"; return ABC_ERR_ARG; }
+    g = Geometry();
+    g.nx = nx; g.ny = ny; g.nz = nz; g.h = h;
+    g.n_nodes = (long long)nx * ny * nz;
+    if (g.n_nodes > (1LL << 31) - 1) { err = "grid too large"; return ABC_ERR_ARG; }
+    g.node_gamma.assign((size_t)g.n_nodes, -1);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const int c = (i == 0) + (i == nx - 1) + (j == 0) + (j == ny - 1) + (k == 0) + (k == nz - 1);
+                if (!c) continue;
+                const int node = (k * ny + j) * nx + i;
+                const int gi = (int)g.gamma_node.size();
+                if (gamma_index_closed(i, j, k, nx, ny, nz) != gi) {
+                    err = "internal: Gamma numbering mismatch";
+                    return ABC_ERR_ARG;
+                }
+                g.node_gamma[node] = gi;
+                g.gamma_node.push_back(node);
+                g.gamma_c.push_back(c);
+            }
+    g.n_gamma = (int)g.gamma_node.size();
+
+    // representatives: Gamma nodes of the low octant
+    const int dims[3] = {nx, ny, nz};
+    for (int gi = 0; gi < g.n_gamma; ++gi) {
+        const int node = g.gamma_node[gi];
+        const int co[3] = {node % nx, (node / nx) % ny, node / (nx * ny)};
+        bool low = true;
+        for (int a = 0; a < 3; ++a) low &= (2 * co[a] <= dims[a] - 1);
+        if (low) g.rep_node.push_back(node);
+    }
+    g.n_rep = (int)g.rep_node.size();
+    g.rep_gamma.assign((size_t)g.n_rep * 8, -1);
+    g.rep_adapted.assign((size_t)g.n_rep * 8, -1);
+    g.rep_stab.assign(g.n_rep, 1);
+    std::vector<int> fixed_mask(g.n_rep, 0);
+    for (int r = 0; r < g.n_rep; ++r) {
+        const int node = g.rep_node[r];
+        const int co[3] = {node % nx, (node / nx) % ny, node / (nx * ny)};
+        int mask = 0;
+        for (int a = 0; a < 3; ++a)
+            if (2 * co[a] == dims[a] - 1) mask |= 1 << a;
+        fixed_mask[r] = mask;
+        g.rep_stab[r] = 1 << __builtin_popcount(mask);
+        for (int gg = 0; gg < 8; ++gg) {
+            int c2[3];
+            for (int a = 0; a < 3; ++a) c2[a] = (gg >> a & 1) ? dims[a] - 1 - co[a] : co[a];
+            g.rep_gamma[(size_t)r * 8 + gg] = g.node_gamma[(c2[2] * ny + c2[1]) * nx + c2[0]];
+        }
+    }
+    int cnt[8] = {0};
+    for (int p = 0; p < 8; ++p)
+        for (int r = 0; r < g.n_rep; ++r)
+            if (!(p & fixed_mask[r])) ++cnt[p];
+    int acc = 0;
+    for (int p = 0; p < 8; ++p) { g.m[p] = cnt[p]; g.off[p] = acc; acc += cnt[p]; }
+    if (acc != g.n_gamma) { err = "internal: parity blocks do not cover Gamma"; return ABC_ERR_ARG; }
+    g.adapted_rep.assign(g.n_gamma, -1);
+    for (int p = 0; p < 8; ++p) {
+        int loc = 0;
+        for (int r = 0; r < g.n_rep; ++r) {
+            if (p & fixed_mask[r]) continue;
+            const int q = g.off[p] + loc++;
+            g.rep_adapted[(size_t)r * 8 + p] = q;
+            g.adapted_rep[q] = r;
+        }
+    }
+    return ABC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Free lattice Green's function (App. D) by a one-dimensional integral
+// ---------------------------------------------------------------------------
+//
+// G = (H_0 - i s)^{-1} = i int_0^inf exp(-i (H_0 - i s) t) dt for s > 0, and
+// exp(-i H_0 t) factorises over the axes: with H_0 = sum_a (1 - cos xi_a)/h^2 in
+// Fourier space, the Jacobi-Anger expansion gives the 1D kernel
+// exp(-i t/h^2) i^|n| J_|n|(t/h^2) at lattice offset n.  With x = t/h^2:
+//   G(a,b,c) = i h^2 i^(a+b+c) int_0^inf exp(-s h^2 x - 3 i x) J_a(x) J_b(x) J_c(x) dx.
+// The integrand oscillates with frequencies 0, 2, 4, 6 and decays like
+// exp(-s h^2 x) x^(-3/2); it is integrated with 16-point Gauss-Legendre panels of
+// unit width up to s h^2 x = 40.
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int k = 1; k <= n; ++k) {
+                const double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+            }
+            const double dp = n * (z * p0 - p1) / (z * z - 1.0);
+            const double dz = p0 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) {
+                x[i] = z;
+                w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+                break;
+            }
+            x[i] = z;
+            w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        }
+    }
+}
+
+// J_0..J_nmax at x by Miller's backward recurrence J_{k-1} = (2k/x) J_k - J_{k+1},
+// normalised with J_0 + 2 sum_{k>=1} J_{2k} = 1.
+static void bessel_j_all(double x, int nmax, double* out) {
+    if (x == 0.0) {
+        out[0] = 1.0;
+        for (int n = 1; n <= nmax; ++n) out[n] = 0.0;
+        return;
+    }
+    const double top = std::max((double)nmax, x);
+    int m = (int)(top + 40.0 + 4.0 * std::sqrt(top));
+    m += m & 1;
+    double jp1 = 0.0, j = 1e-30, norm = 0.0;
+    for (int n = 0; n <= nmax; ++n) out[n] = 0.0;
+    for (int k = m; k >= 1; --k) {
+        // j holds J_k (unnormalised), jp1 holds J_{k+1}
+        if (k <= nmax) out[k] = j;
+        if ((k & 1) == 0) norm += 2.0 * j;
+        const double jm1 = (2.0 * k / x) * j - jp1;
+        jp1 = j;
+        j = jm1;
+        if (std::fabs(j) > 1e250) {
+            const double sc = 1e-250;
+            j *= sc; jp1 *= sc; norm *= sc;
+            for (int n = std::max(k - 1, 0); n <= nmax; ++n) out[n] *= sc;
+        }
+    }
+    out[0] = j;
+    norm += j;
+    const double inv = 1.0 / norm;
+    for (int n = 0; n <= nmax; ++n) out[n] *= inv;
+}
+
+void free_green_table(double h, double s, int dx, int dy, int dz, std::vector<cd>& table) {
+    const int M = std::max(dx, std::max(dy, dz));
+    const double sh2 = s * h * h;
+    const double xmax = 40.0 / sh2;
+    const int npan = (int)std::ceil(xmax);
+    const int NG = 16;
+    std::vector<double> gx, gw;
+    gauss_legendre(NG, gx, gw);
+    const int Q = npan * NG;
+    std::vector<double> xq(Q);
+    std::vector<cd> wq(Q);
+    for (int pn = 0; pn < npan; ++pn)
+        for (int i = 0; i < NG; ++i) {
+            const double x = pn + 0.5 * (gx[i] + 1.0);
+            xq[pn * NG + i] = x;
+            wq[pn * NG + i] = 0.5 * gw[i] * std::exp(-sh2 * x) * cd(std::cos(3.0 * x), -std::sin(3.0 * x));
+        }
+    // Bessel table J[n][q]
+    std::vector<double> J((size_t)M * Q);
+#pragma omp parallel
+    {
+        std::vector<double> tmp(M);
+#pragma omp for schedule(static)
+        for (int q = 0; q < Q; ++q) {
+            bessel_j_all(xq[q], M - 1, tmp.data());
+            for (int n = 0; n < M; ++n) J[(size_t)n * Q + q] = tmp[n];
+        }
+    }
+    // sorted triples a <= b <= c < M
+    std::vector<cd> tri((size_t)M * M * M, cd(0.0, 0.0));
+#pragma omp parallel
+    {
+        std::vector<cd> P(Q);
+#pragma omp for schedule(dynamic)
+        for (int ab = 0; ab < M * M; ++ab) {
+            const int a = ab / M, b = ab % M;
+            if (b < a) continue;
+            const double* Ja = &J[(size_t)a * Q];
+            const double* Jb = &J[(size_t)b * Q];
+            for (int q = 0; q < Q; ++q) P[q] = wq[q] * (Ja[q] * Jb[q]);
+            for (int c = b; c < M; ++c) {
+                const double* Jc = &J[(size_t)c * Q];
+                double sr = 0.0, si = 0.0;
+                for (int q = 0; q < Q; ++q) {
+                    sr += P[q].real() * Jc[q];
+                    si += P[q].imag() * Jc[q];
+                }
+                static const cd ipow[4] = {cd(1, 0), cd(0, 1), cd(-1, 0), cd(0, -1)};
+                tri[((size_t)a * M + b) * M + c] = cd(0.0, h * h) * ipow[(a + b + c) & 3] * cd(sr, si);
+            }
+        }
+    }
+    table.assign((size_t)dx * dy * dz, cd(0.0, 0.0));
+    for (int c = 0; c < dz; ++c)
+        for (int b = 0; b < dy; ++b)
+            for (int a = 0; a < dx; ++a) {
+                int t[3] = {a, b, c};
+                std::sort(t, t + 3);
+                table[((size_t)c * dy + b) * dx + a] = tri[((size_t)t[0] * M + t[1]) * M + t[2]];
+            }
+}
+
+// ---------------------------------------------------------------------------
+// DtN blocks by eq:eval
+// ---------------------------------------------------------------------------
+//
+// With the 3-point stencil H_{Gamma,Sigma} has the single weight -1/(2h^2) between a
+// boundary node and each of its exterior neighbours, so eq:eval's two matrices are
+//   X = I - H_{Gamma,Sigma} G_{Sigma,Gamma}:  X[g,g'] = d_gg' + 1/(2h^2) sum_{s in nb(g)} G(s - g')
+//   Y = H_{Gamma,Sigma} G_{Sigma,Sigma} H_{Sigma,Gamma}:
+//                                   Y[g,g'] = 1/(4h^4) sum_{s in nb(g), s' in nb(g')} G(s - s')
+// and K = -X^{-1} Y.  Both commute with the reflections, so each parity block is
+//   X_p[r,r'] = (|H_r||H_r'|)^{-1/2} sum_g chi_p(g) X[r, g r']   (same for Y),
+// and K_p = -X_p^{-1} Y_p (order 0), K_p^{-1} = -Y_p^{-1} X_p (order 1).
+
+namespace {
+struct Nb {
+    int n;
+    int c[3][3];
+};
+
+Nb exterior_neighbours(int i, int j, int k, int nx, int ny, int nz) {
+    Nb r;
+    r.n = 0;
+    const int co[3] = {i, j, k}, dims[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) {
+        if (co[a] == 0 || co[a] == dims[a] - 1) {
+            int t[3] = {i, j, k};
+            t[a] = co[a] == 0 ? -1 : dims[a];
+            std::memcpy(r.c[r.n++], t, sizeof(t));
+        }
+    }
+    return r;
+}
+}  // namespace
+
+int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::string& err) {
+    if (!(s > 0.0)) { err = "interpolation point must be positive"; return ABC_ERR_ARG; }
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int tx = nx + 2, ty = ny + 2, tz = nz + 2;
+    std::vector<cd> G;
+    free_green_table(g.h, s, tx, ty, tz, G);
+    auto Gt = [&](int dx, int dy, int dz) -> cd {
+        return G[((size_t)std::abs(dz) * ty + std::abs(dy)) * tx + std::abs(dx)];
+    };
+    const double ih2 = 1.0 / (2.0 * g.h * g.h), ih4 = 1.0 / (4.0 * std::pow(g.h, 4));
+    const int R = g.n_rep;
+    std::vector<Nb> nb(R);
+    std::vector<std::array<int, 3>> rc(R);
+    for (int r = 0; r < R; ++r) {
+        const int node = g.rep_node[r];
+        rc[r] = {node % nx, (node / nx) % ny, node / (nx * ny)};
+        nb[r] = exterior_neighbours(rc[r][0], rc[r][1], rc[r][2], nx, ny, nz);
+    }
+    const int dims[3] = {nx, ny, nz};
+    std::vector<cd> X[8], Y[8];
+    for (int p = 0; p < 8; ++p) {
+        X[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
+        Y[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int ri = 0; ri < R; ++ri) {
+        const int* ci = rc[ri].data();
+        const Nb& ni = nb[ri];
+        for (int rj = 0; rj < R; ++rj) {
+            cd xv[8], yv[8];
+            for (int gg = 0; gg < 8; ++gg) {
+                int y[3];
+                for (int a = 0; a < 3; ++a) y[a] = (gg >> a & 1) ? dims[a] - 1 - rc[rj][a] : rc[rj][a];
+                cd xs = (y[0] == ci[0] && y[1] == ci[1] && y[2] == ci[2]) ? cd(1.0, 0.0) : cd(0.0, 0.0);
+                for (int u = 0; u < ni.n; ++u)
+                    xs += ih2 * Gt(ni.c[u][0] - y[0], ni.c[u][1] - y[1], ni.c[u][2] - y[2]);
+                const Nb ny_ = exterior_neighbours(y[0], y[1], y[2], nx, ny, nz);
+                cd ys(0.0, 0.0);
+                for (int u = 0; u < ni.n; ++u)
+                    for (int v = 0; v < ny_.n; ++v)
+                        ys += Gt(ni.c[u][0] - ny_.c[v][0], ni.c[u][1] - ny_.c[v][1], ni.c[u][2] - ny_.c[v][2]);
+                xv[gg] = xs;
+                yv[gg] = ih4 * ys;
+            }
+            const double sc = 1.0 / std::sqrt((double)g.rep_stab[ri] * g.rep_stab[rj]);
+            for (int p = 0; p < 8; ++p) {
+                const int qi = g.rep_adapted[(size_t)ri * 8 + p], qj = g.rep_adapted[(size_t)rj * 8 + p];
+                if (qi < 0 || qj < 0) continue;
+                cd xs(0.0, 0.0), ys(0.0, 0.0);
+                for (int gg = 0; gg < 8; ++gg) {
+                    const double chi = (__builtin_popcount(p & gg) & 1) ? -1.0 : 1.0;
+                    xs += chi * xv[gg];
+                    ys += chi * yv[gg];
+                }
+                const size_t a = qi - g.off[p], b = qj - g.off[p];
+                X[p][b * g.m[p] + a] = sc * xs;    // column-major
+                Y[p][b * g.m[p] + a] = sc * ys;
+            }
+        }
+    }
+    out = Blocks();
+    out.order = order;
+    out.s = s;
+    for (int p = 0; p < 8; ++p) {
+        const int m = g.m[p];
+        if (m == 0) continue;
+        std::vector<int> piv(m);
+        std::vector<cd>& F = order == 0 ? X[p] : Y[p];     // factorised
+        std::vector<cd>& Z = order == 0 ? Y[p] : X[p];     // right-hand sides -> result
+        const int info = zgetrf(m, F.data(), m, piv.data());
+        if (info) {
+            char buf[128];
+            std::snprintf(buf, sizeof(buf), "eq:eval block %d singular at pivot %d", p, info);
+            err = buf;
+            return ABC_ERR_SINGULAR;
+        }
+        zgetrs(m, m, F.data(), m, piv.data(), Z.data(), m);
+        // result = -Z (column-major) -> symmetrised row-major
+        std::vector<cd>& M = out.mat[p];
+        M.assign((size_t)m * m, cd(0.0, 0.0));
+        for (int a = 0; a < m; ++a)
+            for (int b = 0; b < m; ++b)
+                M[(size_t)a * m + b] = -0.5 * (Z[(size_t)b * m + a] + Z[(size_t)a * m + b]);
+        std::vector<cd>().swap(F);
+        std::vector<cd>().swap(Z);
+    }
+    return ABC_OK;
+}
+
+// Dense natural-order matrices from the parity blocks: with U[g r, (r,p)] =
+// chi_p(g) sqrt(|H_r|/8) (orthogonal), S_nat = U S_adapted U^T.
+int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::string& err) {
+    const int n = g.n_gamma;
+    const double h4 = std::pow(g.h, 4);
+    std::fill(out, out + (size_t)n * n, cd(0.0, 0.0));
+    if (which == ABC_MAT_A || which == ABC_MAT_Q) {
+        if (b.order != 1) { err = "A and Q exist for order 1 only"; return ABC_ERR_ARG; }
+        for (int i = 0; i < n; ++i)
+            out[(size_t)i * n + i] = which == ABC_MAT_A ? cd(0.0, -g.gamma_c[i] / (4.0 * h4))
+                                                        : cd(4.0 * h4 / g.gamma_c[i], 0.0);
+        return ABC_OK;
+    }
+    if (which == ABC_MAT_M && b.order != 0) { err = "M exists for order 0 only"; return ABC_ERR_ARG; }
+    if (which == ABC_MAT_B && b.order != 1) { err = "B exists for order 1 only"; return ABC_ERR_ARG; }
+    if (which != ABC_MAT_K && which != ABC_MAT_M && which != ABC_MAT_B) { err = "unknown matrix"; return ABC_ERR_ARG; }
+    // blocks to expand: M_p (order 0) / K_p = S_p^{-1} (order 1, K) / S_p (order 1, B)
+    std::vector<cd> blk[8];
+    for (int p = 0; p < 8; ++p) {
+        const int m = g.m[p];
+        blk[p] = b.mat[p];
+        if (m && b.order == 1 && which == ABC_MAT_K) {
+            std::vector<cd> F(b.mat[p]), Z((size_t)m * m, cd(0.0, 0.0));
+            std::vector<int> piv(m);
+            for (int i = 0; i < m; ++i) Z[(size_t)i * m + i] = 1.0;
+            if (zgetrf(m, F.data(), m, piv.data())) { err = "S block singular"; return ABC_ERR_SINGULAR; }
+            zgetrs(m, m, F.data(), m, piv.data(), Z.data(), m);  // S symmetric: row/col order irrelevant
+            blk[p] = Z;
+        }
+    }
+    const int R = g.n_rep;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int ri = 0; ri < R; ++ri) {
+        for (int rj = 0; rj < R; ++rj) {
+            const double w = std::sqrt((double)g.rep_stab[ri] * g.rep_stab[rj]) / 8.0;
+            for (int gi = 0; gi < 8; ++gi) {
+                const int yi = g.rep_gamma[(size_t)ri * 8 + gi];
+                for (int gj = 0; gj < 8; ++gj) {
+                    const int yj = g.rep_gamma[(size_t)rj * 8 + gj];
+                    cd acc(0.0, 0.0);
+                    for (int p = 0; p < 8; ++p) {
+                        const int qi = g.rep_adapted[(size_t)ri * 8 + p], qj = g.rep_adapted[(size_t)rj * 8 + p];
+                        if (qi < 0 || qj < 0) continue;
+                        const double chi = (__builtin_popcount(p & (gi ^ gj)) & 1) ? -1.0 : 1.0;
+                        acc += chi * blk[p][(size_t)(qi - g.off[p]) * g.m[p] + (qj - g.off[p])];
+                    }
+                    out[(size_t)yi * n + yj] = w * acc;   // duplicates (stabilised reps) agree
+                }
+            }
+        }
+    }
+    if (which == ABC_MAT_B) {
+        // B = s1 I - A S, A = diag(-i c / (4h^4))
+        for (int i = 0; i < n; ++i) {
+            const cd a(0.0, -g.gamma_c[i] / (4.0 * h4));
+            for (int j = 0; j < n; ++j) out[(size_t)i * n + j] *= -a;
+            out[(size_t)i * n + i] += b.s;
+        }
+    }
+    return ABC_OK;
+}
+
+}  // namespace abc
