@@ -163,6 +163,10 @@ int abc_profile_read(abc_ctx* ctx, int kernel, double* ms, long long* launches);
  * 3 complex values per point and orbital plus V per point. */
 int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, double* bytes);
 
+/* Number of kernels this context has launched since set-up (eager launches plus
+ * the kernels of every replayed graph). */
+int abc_launch_count(const abc_ctx* ctx, long long* launches);
+
 void abc_destroy(abc_ctx* ctx);
 const char* abc_status_string(int status);
 const char* abc_last_error(void);

@@ -68,6 +68,7 @@ def load():
         "abc_profile_enable": [_P, ctypes.c_int],
         "abc_profile_read": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
         "abc_kernel_bytes": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+        "abc_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -185,6 +186,12 @@ def abc_kernel_bytes(ctx, kernel: int, n_orb: int) -> float:
     return b.value
 
 
+def abc_launch_count(ctx) -> int:
+    n = ctypes.c_longlong()
+    _check(load().abc_launch_count(ctx, ctypes.byref(n)))
+    return n.value
+
+
 def abc_destroy(ctx):
     if ctx:
         load().abc_destroy(ctx)
@@ -252,10 +259,20 @@ class Context:
         return diag
 
     def run_host(self, psi, aux, V, dt, nsteps, meanfield=None, diag_every=0):
-        """Host (numpy) buffers; copies in, runs, copies back into psi / aux."""
-        b = psi.shape[0]
+        """Host buffers (numpy arrays or CPU torch tensors, e.g. pinned); copies in,
+        runs, copies back into psi / aux."""
+        def host(x):
+            if x is None:
+                return None
+            if isinstance(x, np.ndarray):
+                return x
+            if x.is_cuda or not x.is_contiguous():
+                raise ValueError("run_host needs contiguous host tensors")
+            return x.numpy()
+        psi_h, aux_h, V_h = host(psi), host(aux), host(V)
+        b = psi_h.shape[0]
         diag = np.zeros((nsteps // diag_every, b, 3)) if diag_every else None
-        abc_run_host(self.ctx, psi, aux, V, b, dt, nsteps, meanfield, diag_every, diag)
+        abc_run_host(self.ctx, psi_h, aux_h, V_h, b, dt, nsteps, meanfield, diag_every, diag)
         return diag
 
     def diagnostics(self, psi, aux, V, meanfield=None, stream=None):
@@ -282,6 +299,9 @@ class Context:
 
     def kernel_bytes(self, kernel, n_orb):
         return abc_kernel_bytes(self.ctx, kernel, n_orb)
+
+    def launches(self):
+        return abc_launch_count(self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

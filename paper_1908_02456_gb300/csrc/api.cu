@@ -75,6 +75,9 @@ struct abc_ctx {
     // graph cache
     cudaGraphExec_t gexec = nullptr;
     struct Key { const void *psi, *aux, *V; int n_orb; double dt; int mf; double a, b, alpha; cudaStream_t s; } key{};
+    // launch accounting
+    long long launches = 0;
+    long long graph_kernels = 0;
     // profiling
     bool profiling = false;
     ProfileSlot prof[2];
@@ -259,6 +262,7 @@ void step_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, doubl
             c->Veff.as<T>());
         Vuse = c->Veff.as<T>();
     }
+    c->launches += 16 + (mf ? 1 : 0);
     const double cs[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
     const void* in_p = psi;
     const void* in_f = aux;
@@ -282,6 +286,7 @@ void diag_impl(abc_ctx* c, const void* psi, const void* aux, const void* V, int 
                                                                      (T)mf->a, (T)mf->b, (T)mf->alpha, c->Veff.as<T>());
         Vuse = c->Veff.as<T>();
     }
+    c->launches += 1 + (mf ? 1 : 0) + (c->params.order == 1 && aux ? 1 : 0);
     cudaMemsetAsync(out_dev, 0, sizeof(double) * 3 * n_orb, s);
     dim3 gp((unsigned)std::min<long long>(nblk(c->nvox, 256), 1024), n_orb);
     dev::diag_phi<T><<<gp, 256, 0, s>>>(g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)psi, Vuse, out_dev);
@@ -401,7 +406,10 @@ int run_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double 
             if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
             cudaGraph_t graph;
             CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            const long long before = c->launches;
             one_step(s);
+            c->graph_kernels = c->launches - before;
+            c->launches = before;
             cudaError_t le = cudaGetLastError();
             cudaError_t ce = cudaStreamEndCapture(s, &graph);
             if (le != cudaSuccess || ce != cudaSuccess)
@@ -413,8 +421,12 @@ int run_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double 
         }
     }
     for (long long n = 1; n <= nsteps; ++n) {
-        if (use_graph) CUDA_TRY(cudaGraphLaunch(c->gexec, s));
-        else one_step(s);
+        if (use_graph) {
+            CUDA_TRY(cudaGraphLaunch(c->gexec, s));
+            c->launches += c->graph_kernels;
+        } else {
+            one_step(s);
+        }
         if (diag_every > 0 && n % diag_every == 0) one_diag(n / diag_every - 1, s);
     }
     st = last_launch_status();
@@ -528,6 +540,12 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
     } else {
         return fail(ABC_ERR_ARG, "unknown kernel");
     }
+    return ABC_OK;
+}
+
+extern "C" int abc_launch_count(const abc_ctx* ctx, long long* launches) {
+    if (!ctx || !launches) return fail(ABC_ERR_ARG, "null argument");
+    *launches = ctx->launches;
     return ABC_OK;
 }
 

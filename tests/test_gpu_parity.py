@@ -81,7 +81,7 @@ def test_free_packet_16cube_order0_fp64(torch_cuda):
     p, _, d = gpu_run(torch_cuda, dims, w.h, 0, w.s, "fp64", psi0.reshape(1, -1), V, w.dt, w.steps, diag_every=10)
     assert rel(p, ref_p) < TOL["fp64"]
     assert rel(d, ref_d) < TOL["fp64"]
-    assert d[-1, 0, 0] < 0.9 * d[0, 0, 0]       # the packet is being absorbed
+    assert d[-1, 0, 0] < 0.95 * d[0, 0, 0]      # the packet is being absorbed
 
 
 @pytest.mark.parametrize("prec", ["fp64", "c64"])
