@@ -163,6 +163,25 @@ int abc_profile_read(abc_ctx* ctx, int kernel, double* ms, long long* launches);
  * 3 complex values per point and orbital plus V per point. */
 int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, double* bytes);
 
+/* abc_step without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc while they step the
+ * system (a framework whose pool allocator owns the device heap, or code that must
+ * not allocate at that point).  It computes exactly what abc_step computes (same
+ * kernels, same order, bit-identical results), but takes all per-step scratch
+ * from one static device array of ABC_NOALLOC_SCRATCH_BYTES defined in the
+ * library (held by every GPU that loads the library until exit) instead of the
+ * context's workspace.  The context is only read.  Needs
+ *   (2*nx*ny*nz*n_orb + 6*n_gamma*n_orb) * complex bytes <= ABC_NOALLOC_SCRATCH_BYTES,
+ * otherwise ABC_ERR_ARG with the required size in abc_last_error().  Calls share
+ * the array: calls whose work overlaps on the GPU race and must be serialised.
+ * Nothing needs clearing between calls (every scratch value is written before it
+ * is read).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make it before any stream capture.  ABC_FP64 and
+ * ABC_C64_FP32 contexts only. */
+#define ABC_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int abc_step_noalloc(const abc_ctx* ctx, void* psi, void* aux, const void* V, int n_orb, double dt,
+                     void* stream);
+
 /* Number of kernels this context has launched since set-up (eager launches plus
  * the kernels of every replayed graph). */
 int abc_launch_count(const abc_ctx* ctx, long long* launches);

@@ -69,6 +69,7 @@ def load():
         "abc_profile_read": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
         "abc_kernel_bytes": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
         "abc_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
+        "abc_step_noalloc": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

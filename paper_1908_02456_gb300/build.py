@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-fopenmp", "-I", INC, "-I", CSRC]
 CXX_FLAGS = ["-std=c++17", "-O3", "-fPIC", "-fopenmp", "-I", INC, "-I", CSRC]
 
-CU_SOURCES = ["api.cu"]
+CU_SOURCES = ["api.cu", "noalloc.cu"]
 CXX_SOURCES = ["dense.cpp", "setup.cpp", "host_api.cpp"]
 
 

@@ -1,0 +1,71 @@
+// Definition of the context behind the opaque abc_ctx handle (internal; shared
+// by the .cu files of the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace abc {
+int fail(int status, const std::string& msg);
+}  // namespace abc
+
+namespace abc {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    int alloc(size_t b) {
+        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+        if (b == 0) return ABC_OK;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) { p = nullptr; return fail(ABC_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+        bytes = b;
+        return ABC_OK;
+    }
+    template <typename X> X* as() const { return reinterpret_cast<X*>(p); }
+};
+
+struct ProfileSlot {
+    std::vector<cudaEvent_t> ev;   // pairs
+    size_t used = 0;
+};
+
+}  // namespace abc
+
+struct abc_ctx {
+    abc_grid grid;
+    abc_params params;
+    abc::Geometry geo;
+    abc::Blocks blocks;          // FP64 blocks (kept for abc_get_matrices)
+    int device = 0;
+    int prec = 0;
+    size_t real_bytes = 8;  // bytes of one real value of the state
+    long long nvox = 0;
+    abc::dev::BlockInfo bi;
+    // device tables
+    abc::DevBuf rep_gamma, rep_adapted, rep_stab, rep_c, gamma_node, gamma_c;
+    abc::DevBuf mat;             // parity blocks in device format
+    abc::DevBuf tile_blk, tile_row;   // row tiles (block, first row) of the multi-orbital contraction
+    int n_tiles = 0;
+    // workspace
+    abc::DevBuf Tp[2], Tf[2], hat_phi, hat_f, tvec, cnat, Veff, diag;
+    abc::DevBuf host_psi, host_aux, host_V;   // device copies for abc_run_host
+    cudaStream_t own = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    struct Key { const void *psi, *aux, *V; int n_orb; double dt; int mf; double a, b, alpha; cudaStream_t s; } key{};
+    // launch accounting
+    long long launches = 0;
+    long long graph_kernels = 0;
+    // profiling
+    bool profiling = false;
+    abc::ProfileSlot prof[2];
+};
+
