@@ -433,11 +433,133 @@ extern "C" int abc_diagnostics(abc_ctx* ctx, const void* psi, const void* aux, c
     return ABC_OK;
 }
 
+namespace {
+
+// One adjoint stage: anew = cdt L^H a, acc += anew (both parts).
+template <typename T>
+void adj_stage(abc_ctx* c, int n_orb, T cdt, const void* a_phi, const void* a_f, void* acc_phi, void* acc_f,
+               void* anew_phi, void* anew_f, const T* V, cudaStream_t s) {
+    typedef typename dev::C2<T>::t Vc;
+    const Geometry& g = c->geo;
+    const long long nb = (long long)g.n_rep * n_orb;
+    const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
+    if (c->params.order == 1) {
+        dev::bnd_forward_adj<T><<<nblk(nb, 128), 128, 0, s>>>(
+            g.n_rep, n_orb, c->nvox, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
+            c->rep_c.as<int>(), a_coef, c->gamma_node.as<int>(), (const Vc*)a_phi, (const Vc*)a_f,
+            c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->cnat.as<Vc>());
+        contraction<T>(c, c->cnat.p, c->tvec.p, n_orb, 1, s);
+        dev::bnd_back_adj<T><<<nblk(nb, 128), 128, 0, s>>>(
+            g.n_rep, n_orb, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(), (T)c->blocks.s,
+            c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->tvec.as<Vc>(), (Vc*)acc_f, (Vc*)anew_f, cdt);
+    } else {
+        dev::bnd_forward<T><<<nblk(nb, 128), 128, 0, s>>>(
+            g.n_rep, n_orb, c->nvox, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
+            c->gamma_node.as<int>(), (const Vc*)a_phi, nullptr, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>());
+        contraction<T>(c, c->hat_phi.p, c->tvec.p, n_orb, 1, s);
+        dev::bnd_back<T><<<nblk(nb, 128), 128, 0, s>>>(
+            0, g.n_rep, n_orb, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
+            c->rep_c.as<int>(), (T)c->blocks.s, a_coef, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->tvec.as<Vc>(),
+            nullptr, c->cnat.as<Vc>(), (T)0);
+    }
+    dev::stencil_adj<T><<<nblk(c->nvox * n_orb, 256), 256, 0, s>>>(
+        c->params.order, g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), a_coef, (const Vc*)a_phi, V,
+        c->params.order == 1 ? (const Vc*)a_f : c->cnat.as<Vc>(), (Vc*)acc_phi, (Vc*)anew_phi, cdt);
+    c->launches += 4;
+}
+
+// Discrete adjoint of the Horner step.  With a the adjoint of a stage's output and w
+// its input, a stage out = y + c dt L(w) sends c dt L^H a to w's adjoint and a to y's,
+// and contributes c dt 2 Im(conj(a_phi) w_phi) to dJ/dV (dL/dV = -i on the phi part).
+template <typename T>
+int adjoint_impl(abc_ctx* c, const void* psi0, const void* V, int n_orb, double dt, long long nsteps, int K,
+                 double* J_out, void* dJdV, cudaStream_t s) {
+    typedef typename dev::C2<T>::t Vc;
+    const size_t cb = sizeof(Vc);
+    const bool o1 = c->params.order == 1;
+    const size_t np = (size_t)c->nvox * n_orb, na = o1 ? (size_t)c->geo.n_gamma * n_orb : 0;
+    const size_t sb = (np + na) * cb;
+    const long long nck = nsteps / K;
+    const long long segmax = std::min<long long>(K, std::max<long long>(nsteps, 1));
+    DevBuf ck, seg, work, grad;
+    int st;
+    if ((st = ck.alloc((size_t)(nck + 1) * sb))) return st;
+    if ((st = seg.alloc((size_t)segmax * sb))) return st;
+    if ((st = work.alloc(7 * sb))) return st;
+    if ((st = grad.alloc((size_t)c->nvox * sizeof(double)))) return st;
+    auto S = [&](char* base, long long i) { return base + (size_t)i * sb; };
+    auto PH = [&](char* b) { return (void*)b; };
+    auto AF = [&](char* b) { return o1 ? (void*)(b + np * cb) : (void*)nullptr; };
+    char* W = work.as<char>();
+    char *Y = S(W, 0), *W4 = S(W, 1), *W3 = S(W, 2), *W2 = S(W, 3), *A = S(W, 4), *An = S(W, 5), *Acc = S(W, 6);
+    const T* Vt = (const T*)V;
+    // forward sweep, checkpoints every K steps
+    CUDA_TRY(cudaMemcpyAsync(PH(Y), psi0, np * cb, cudaMemcpyDeviceToDevice, s));
+    if (o1) CUDA_TRY(cudaMemsetAsync(AF(Y), 0, na * cb, s));
+    CUDA_TRY(cudaMemcpyAsync(S(ck.as<char>(), 0), Y, sb, cudaMemcpyDeviceToDevice, s));
+    for (long long n = 1; n <= nsteps; ++n) {
+        step_impl<T>(c, PH(Y), AF(Y), V, n_orb, dt, nullptr, s);
+        if (n % K == 0) CUDA_TRY(cudaMemcpyAsync(S(ck.as<char>(), n / K), Y, sb, cudaMemcpyDeviceToDevice, s));
+    }
+    // J and its adjoint
+    diag_impl<T>(c, PH(Y), AF(Y), V, n_orb, nullptr, c->diag.as<double>(), s);
+    std::vector<double> dg(3 * n_orb);
+    CUDA_TRY(cudaMemcpyAsync(dg.data(), c->diag.p, sizeof(double) * 3 * n_orb, cudaMemcpyDeviceToHost, s));
+    const double h3 = c->geo.h * c->geo.h * c->geo.h;
+    dev::scale_into<T><<<nblk((long long)np, 256), 256, 0, s>>>((long long)np, (const Vc*)PH(Y), (T)(-h3), (Vc*)PH(A));
+    if (o1) CUDA_TRY(cudaMemsetAsync(AF(A), 0, na * cb, s));
+    CUDA_TRY(cudaMemsetAsync(grad.p, 0, (size_t)c->nvox * sizeof(double), s));
+    const double cs[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+    for (long long sg = (nsteps - 1) / K; nsteps > 0 && sg >= 0; --sg) {
+        const long long start = sg * K, end = std::min<long long>(start + K, nsteps);
+        char* SB = seg.as<char>();
+        CUDA_TRY(cudaMemcpyAsync(S(SB, 0), S(ck.as<char>(), sg), sb, cudaMemcpyDeviceToDevice, s));
+        for (long long k = 1; k < end - start; ++k) {
+            CUDA_TRY(cudaMemcpyAsync(S(SB, k), S(SB, k - 1), sb, cudaMemcpyDeviceToDevice, s));
+            step_impl<T>(c, PH(S(SB, k)), AF(S(SB, k)), V, n_orb, dt, nullptr, s);
+        }
+        for (long long n = end - 1; n >= start; --n) {
+            char* y = S(SB, n - start);
+            stage<T>(c, n_orb, (T)(cs[0] * dt), PH(y), AF(y), PH(y), AF(y), PH(W4), AF(W4), Vt, s);
+            stage<T>(c, n_orb, (T)(cs[1] * dt), PH(W4), AF(W4), PH(y), AF(y), PH(W3), AF(W3), Vt, s);
+            stage<T>(c, n_orb, (T)(cs[2] * dt), PH(W3), AF(W3), PH(y), AF(y), PH(W2), AF(W2), Vt, s);
+            c->launches += 12;
+            CUDA_TRY(cudaMemcpyAsync(Acc, A, sb, cudaMemcpyDeviceToDevice, s));
+            char* ws[4] = {y, W4, W3, W2};
+            for (int stg = 3; stg >= 0; --stg) {
+                dev::grad_accum<T><<<nblk(c->nvox, 256), 256, 0, s>>>(c->nvox, n_orb, (const Vc*)PH(A),
+                                                                      (const Vc*)PH(ws[stg]), cs[stg] * dt,
+                                                                      grad.as<double>());
+                adj_stage<T>(c, n_orb, (T)(cs[stg] * dt), PH(A), AF(A), PH(Acc), AF(Acc), PH(An), AF(An), Vt, s);
+                c->launches += 1;
+                std::swap(A, An);
+            }
+            std::swap(A, Acc);
+        }
+    }
+    dev::to_real<T><<<nblk(c->nvox, 256), 256, 0, s>>>(c->nvox, grad.as<double>(), (T*)dJdV);
+    if ((st = last_launch_status())) return st;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    double J = 0;
+    for (int j = 0; j < n_orb; ++j) J += 1.0 - h3 * dg[3 * j];
+    *J_out = J;
+    return ABC_OK;
+}
+
+}  // namespace
+
 extern "C" int abc_adjoint_run(abc_ctx* ctx, const void* psi0, const void* V, int n_orb, double dt, long long nsteps,
                                int ckpt_every, double* J_out, void* dJdV, void* stream) {
-    (void)ctx; (void)psi0; (void)V; (void)n_orb; (void)dt; (void)nsteps; (void)ckpt_every; (void)J_out;
-    (void)dJdV; (void)stream;
-    return fail(ABC_ERR_UNSUPPORTED, "adjoint not built yet");
+    if (!ctx) return fail(ABC_ERR_ARG, "null context");
+    if (!psi0 || !V) return fail(ABC_ERR_ARG, "null psi0 or V");
+    if (n_orb < 1 || n_orb > ctx->params.max_orbitals) return fail(ABC_ERR_ARG, "n_orb outside [1, max_orbitals]");
+    if (!(dt > 0.0)) return fail(ABC_ERR_ARG, "dt must be positive");
+    if (!J_out || !dJdV) return fail(ABC_ERR_ARG, "null J_out or dJdV");
+    if (nsteps < 0) return fail(ABC_ERR_ARG, "nsteps must be >= 0");
+    if (ckpt_every < 1) return fail(ABC_ERR_ARG, "ckpt_every must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->prec == ABC_FP64) return adjoint_impl<double>(ctx, psi0, V, n_orb, dt, nsteps, ckpt_every, J_out, dJdV, s);
+    return adjoint_impl<float>(ctx, psi0, V, n_orb, dt, nsteps, ckpt_every, J_out, dJdV, s);
 }
 
 extern "C" int abc_get_matrices(const abc_ctx* ctx, int which, void* host_dst, size_t bytes) {

@@ -394,3 +394,169 @@ __global__ void diag_aux(int n_gamma, int n_orb, const int* __restrict__ gamma_c
 
 }  // namespace dev
 }  // namespace abc
+
+namespace abc {
+namespace dev {
+
+// ==========================================================================
+// Adjoint (reverse sweep through the Horner stages)
+// ==========================================================================
+// The adjoint operator of eq:dynamics0 / eq:dynamics1 (H real symmetric):
+//   order 0: L^H a = i H a_phi + i E^T M^H E a_phi
+//   order 1: L^H (a_phi, a_f) = (i H a_phi + E^T A^H a_f,  i E a_phi + B^H a_f)
+// with A^H = +i diag(c)/(4h^4) and B^H = s1 I - conj(S) A^H (S = K(s1)^{-1} symmetric).
+
+// Natural -> adapted for the adjoint: like bnd_forward, and additionally
+// u = A^H f_hat (per representative: +i a_coef c_r).
+template <typename T>
+__global__ void bnd_forward_adj(int n_rep, int n_orb, long long nvox, const int* __restrict__ rep_gamma,
+                                const int* __restrict__ rep_adapted, const int* __restrict__ rep_stab,
+                                const int* __restrict__ rep_c, T a_coef, const int* __restrict__ gamma_node,
+                                const typename C2<T>::t* __restrict__ a_phi, const typename C2<T>::t* __restrict__ a_f,
+                                typename C2<T>::t* __restrict__ hat_phi, typename C2<T>::t* __restrict__ hat_f,
+                                typename C2<T>::t* __restrict__ u) {
+    typedef typename C2<T>::t V;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_rep * n_orb) return;
+    const int j = (int)(idx % n_orb);
+    const int r = (int)(idx / n_orb);
+    const T sc = (T)rsqrt(8.0 * rep_stab[r]);
+    const T ac = a_coef * (T)rep_c[r];
+    V xp[8], xf[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        const int gi = rep_gamma[r * 8 + g];
+        xp[g] = a_phi[(long long)j * nvox + gamma_node[gi]];
+        xf[g] = a_f[(long long)gi * n_orb + j];
+    }
+    wht8(xp);
+    wht8(xf);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const int q = rep_adapted[r * 8 + p];
+        if (q < 0) continue;
+        const long long e = (long long)q * n_orb + j;
+        const T fr = sc * xf[p].x, fi = sc * xf[p].y;
+        hat_phi[e] = mk<T>(sc * xp[p].x, sc * xp[p].y);
+        hat_f[e] = mk<T>(fr, fi);
+        u[e] = mk<T>(-ac * fi, ac * fr);          // (+i ac) * f_hat
+    }
+}
+
+// Adapted -> natural for the order-1 adjoint f part:
+//   g_hat = s1 a_f_hat - t + i a_phi_hat,  t = conj(S) u,
+//   anew_f = cdt * U g_hat,  acc_f += anew_f.
+template <typename T>
+__global__ void bnd_back_adj(int n_rep, int n_orb, const int* __restrict__ rep_gamma,
+                             const int* __restrict__ rep_adapted, const int* __restrict__ rep_stab, T s1,
+                             const typename C2<T>::t* __restrict__ hat_phi, const typename C2<T>::t* __restrict__ hat_f,
+                             const typename C2<T>::t* __restrict__ t, typename C2<T>::t* acc_f,
+                             typename C2<T>::t* __restrict__ anew_f, T cdt) {
+    typedef typename C2<T>::t V;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n_rep * n_orb) return;
+    const int j = (int)(idx % n_orb);
+    const int r = (int)(idx / n_orb);
+    V x[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const int q = rep_adapted[r * 8 + p];
+        if (q < 0) { x[p] = mk<T>(0, 0); continue; }
+        const long long e = (long long)q * n_orb + j;
+        const V fv = hat_f[e], tv = t[e], pv = hat_phi[e];
+        x[p] = mk<T>(s1 * fv.x - tv.x - pv.y, s1 * fv.y - tv.y + pv.x);
+    }
+    wht8(x);
+    const T sc = (T)sqrt(rep_stab[r] / 8.0);
+    V av[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) av[g] = acc_f[(long long)rep_gamma[r * 8 + g] * n_orb + j];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        const long long e = (long long)rep_gamma[r * 8 + g] * n_orb + j;
+        const T nr = cdt * sc * x[g].x, ni = cdt * sc * x[g].y;
+        anew_f[e] = mk<T>(nr, ni);
+        acc_f[e] = mk<T>(av[g].x + nr, av[g].y + ni);
+    }
+}
+
+// anew_phi = cdt * (i H a_phi + bt),  acc_phi += anew_phi, with the boundary term
+//   order 1: bt = A^H a_f = (+i c_gamma a_coef) a_f[gamma]
+//   order 0: bt = i cnat[gamma]   (cnat = E^T conj(M) E a_phi)
+template <typename T>
+__global__ void stencil_adj(int order, int nx, int ny, int nz, int n_orb, T inv_h2, T a_coef,
+                            const typename C2<T>::t* __restrict__ a, const T* __restrict__ V,
+                            const typename C2<T>::t* __restrict__ bsrc, typename C2<T>::t* acc,
+                            typename C2<T>::t* __restrict__ anew, T cdt) {
+    typedef typename C2<T>::t Vc;
+    const long long nvox = (long long)nx * ny * nz;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nvox * n_orb) return;
+    const int orb = (int)(idx / nvox);
+    const long long n = idx - (long long)orb * nvox;
+    const int i = (int)(n % nx);
+    const int jy = (int)((n / nx) % ny);
+    const int k = (int)(n / ((long long)nx * ny));
+    const Vc* wo = a + (long long)orb * nvox;
+    const Vc c = wo[n];
+    T sr = 0, si = 0;
+    if (i > 0) { const Vc v = wo[n - 1]; sr += v.x; si += v.y; }
+    if (i < nx - 1) { const Vc v = wo[n + 1]; sr += v.x; si += v.y; }
+    if (jy > 0) { const Vc v = wo[n - nx]; sr += v.x; si += v.y; }
+    if (jy < ny - 1) { const Vc v = wo[n + nx]; sr += v.x; si += v.y; }
+    if (k > 0) { const Vc v = wo[n - (long long)nx * ny]; sr += v.x; si += v.y; }
+    if (k < nz - 1) { const Vc v = wo[n + (long long)nx * ny]; sr += v.x; si += v.y; }
+    const T diag = (T)3 * inv_h2 + V[n];
+    const T hr = diag * c.x - (T)0.5 * inv_h2 * sr;
+    const T hi = diag * c.y - (T)0.5 * inv_h2 * si;
+    // i H a = (-hi, hr)
+    T lr = -hi, li = hr;
+    const int cnt = (i == 0) + (i == nx - 1) + (jy == 0) + (jy == ny - 1) + (k == 0) + (k == nz - 1);
+    if (cnt) {
+        const Vc b = bsrc[(long long)gamma_index(i, jy, k, nx, ny, nz) * n_orb + orb];
+        if (order == 1) {
+            const T ac = a_coef * (T)cnt;
+            lr += -ac * b.y;
+            li += ac * b.x;
+        } else {
+            lr += -b.y;
+            li += b.x;
+        }
+    }
+    const Vc av = acc[idx];
+    const T nr = cdt * lr, ni = cdt * li;
+    anew[idx] = mk<T>(nr, ni);
+    acc[idx] = mk<T>(av.x + nr, av.y + ni);
+}
+
+// grad[x] += coef * sum_j 2 Im(conj(a_j[x]) w_j[x])   (FP64 accumulation, one thread per node)
+template <typename T>
+__global__ void grad_accum(long long nvox, int n_orb, const typename C2<T>::t* __restrict__ a,
+                           const typename C2<T>::t* __restrict__ w, double coef, double* __restrict__ grad) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nvox) return;
+    double s = 0;
+    for (int j = 0; j < n_orb; ++j) {
+        const typename C2<T>::t av = a[(long long)j * nvox + n], wv = w[(long long)j * nvox + n];
+        s += (double)av.x * wv.y - (double)av.y * wv.x;
+    }
+    grad[n] += 2.0 * coef * s;
+}
+
+// adjoint of J = sum_j (1 - h^3 |phi_j|^2):  a_phi = -h^3 phi
+template <typename T>
+__global__ void scale_into(long long n, const typename C2<T>::t* __restrict__ x, T s, typename C2<T>::t* __restrict__ y) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const typename C2<T>::t v = x[i];
+    y[i] = mk<T>(s * v.x, s * v.y);
+}
+
+template <typename T>
+__global__ void to_real(long long n, const double* __restrict__ x, T* __restrict__ y) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (T)x[i];
+}
+
+}  // namespace dev
+}  // namespace abc
