@@ -166,8 +166,10 @@ int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, double* bytes);
 /* abc_step without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc while they step the
  * system (a framework whose pool allocator owns the device heap, or code that must
- * not allocate at that point).  It computes exactly what abc_step computes (same
- * kernels, same order, bit-identical results), but takes all per-step scratch
+ * not allocate at that point).  It computes what abc_step computes with the same
+ * stages; for one complex64 orbital its boundary contraction runs the full-block
+ * kernel instead of abc_step's symmetric-tile kernel (whose partial sums need extra
+ * scratch), so results agree to rounding.  It takes all per-step scratch
  * from one static device array of ABC_NOALLOC_SCRATCH_BYTES defined in the
  * library (held by every GPU that loads the library until exit) instead of the
  * context's workspace.  The context is only read.  Needs
@@ -181,6 +183,18 @@ int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, double* bytes);
 #define ABC_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 int abc_step_noalloc(const abc_ctx* ctx, void* psi, void* aux, const void* V, int n_orb, double dt,
                      void* stream);
+
+/* Tuning knobs of the kernels (chosen by the autotuner, paper_1908_02456_gb300/tune.py):
+ *   ABC_TUNE_L2_KEEP_TILES  number of leading 64x64 boundary tiles that the one-orbital
+ *                           complex64 contraction streams with an L2 evict_last hint so
+ *                           that they stay in L2 from one Horner stage to the next
+ *                           (the rest use evict_first); 0 = all evict_first.
+ *   ABC_TUNE_TILE_COUNT     (read only) number of stored tiles.
+ * Setting a knob drops the cached CUDA graph.  The paper has no counterpart. */
+#define ABC_TUNE_L2_KEEP_TILES 0
+#define ABC_TUNE_TILE_COUNT 1
+int abc_set_tuning(abc_ctx* ctx, int key, long long value);
+int abc_get_tuning(const abc_ctx* ctx, int key, long long* value);
 
 /* Number of kernels this context has launched since set-up (eager launches plus
  * the kernels of every replayed graph). */

@@ -17,6 +17,7 @@ OK = 0
 FP64, C64_FP32, C64_SPLIT_BF16 = 0, 1, 2
 MAT_K, MAT_M, MAT_A, MAT_B, MAT_Q = 0, 1, 2, 3, 4
 KERNEL_CONTRACTION, KERNEL_STENCIL = 0, 1
+TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT = 0, 1
 PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16}
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libabc.so")
@@ -70,6 +71,8 @@ def load():
         "abc_kernel_bytes": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
         "abc_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
         "abc_step_noalloc": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P],
+        "abc_set_tuning": [_P, ctypes.c_int, ctypes.c_longlong],
+        "abc_get_tuning": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -187,6 +190,16 @@ def abc_kernel_bytes(ctx, kernel: int, n_orb: int) -> float:
     return b.value
 
 
+def abc_set_tuning(ctx, key: int, value: int):
+    _check(load().abc_set_tuning(ctx, key, int(value)))
+
+
+def abc_get_tuning(ctx, key: int) -> int:
+    v = ctypes.c_longlong()
+    _check(load().abc_get_tuning(ctx, key, ctypes.byref(v)))
+    return v.value
+
+
 def abc_launch_count(ctx) -> int:
     n = ctypes.c_longlong()
     _check(load().abc_launch_count(ctx, ctypes.byref(n)))
@@ -300,6 +313,12 @@ class Context:
 
     def kernel_bytes(self, kernel, n_orb):
         return abc_kernel_bytes(self.ctx, kernel, n_orb)
+
+    def set_tuning(self, key, value):
+        abc_set_tuning(self.ctx, key, value)
+
+    def get_tuning(self, key):
+        return abc_get_tuning(self.ctx, key)
 
     def launches(self):
         return abc_launch_count(self.ctx)

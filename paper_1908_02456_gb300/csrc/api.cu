@@ -60,6 +60,10 @@ int upload_matrices(abc_ctx* c) {
         c->bi.m[p] = g.m[p];
         c->bi.off[p] = g.off[p];
         c->bi.ld[p] = (g.m[p] + 3) & ~3;
+        if (g.base_of[p] != p) {            // shares its class's base block
+            c->bi.mat_off[p] = c->bi.mat_off[g.base_of[p]];
+            continue;
+        }
         c->bi.mat_off[p] = total;
         total += (long long)c->bi.ld[p] * g.m[p];
     }
@@ -71,7 +75,7 @@ int upload_matrices(abc_ctx* c) {
     CUDA_TRY(cudaMemset(c->mat.p, 0, (size_t)total * eb));
     for (int p = 0; p < 8; ++p) {
         const int m = g.m[p], ld = c->bi.ld[p];
-        if (!m) continue;
+        if (!m || g.base_of[p] != p) continue;
         const std::vector<cd>& M = c->blocks.mat[p];
         if (c->prec == ABC_FP64) {
             std::vector<double> buf((size_t)2 * ld * m, 0.0);
@@ -152,12 +156,143 @@ int build_tiles(abc_ctx* c) {
     return ABC_OK;
 }
 
+// Packed lower-triangular 64x64 tiles of every distinct block (complex64), the
+// per-CTA segment lists and the partial-sum scratch of sym_gemv_tiles.
+int build_sym(abc_ctx* c) {
+    using abc::dev::SYM_T;
+    const Geometry& g = c->geo;
+    abc::dev::SymInfo si{};
+    int nc = 0, cls_base[8] = {0};
+    long long tb = 0;
+    int rb = 0;
+    for (int b = 0; b < 8; ++b) {
+        if (g.base_of[b] != b || g.m[b] == 0) continue;
+        int R = 0;
+        for (int p = 0; p < 8; ++p)
+            if (g.base_of[p] == b) si.moff[nc][R++] = g.off[p];
+        const int nt = (g.m[b] + SYM_T - 1) / SYM_T;
+        si.R[nc] = R;
+        si.m[nc] = g.m[b];
+        si.nt[nc] = nt;
+        si.tbase[nc] = tb;
+        si.rbase[nc] = rb;
+        cls_base[nc] = b;
+        tb += (long long)nt * (nt + 1) / 2;
+        rb += nt;
+        ++nc;
+    }
+    si.nclass = nc;
+    si.obase[0] = 0;
+    for (int k = 0; k < nc; ++k) si.obase[k + 1] = si.obase[k] + (long long)si.nt[k] * SYM_T * si.R[k];
+    const long long NT = tb;
+    // tiles
+    std::vector<float> host((size_t)NT * SYM_T * SYM_T * 2, 0.0f);
+    std::vector<int> tile_c(NT), tile_I(NT);
+    for (int k = 0; k < nc; ++k) {
+        const int m = si.m[k];
+        const std::vector<cd>& S = c->blocks.mat[cls_base[k]];
+        for (int I = 0; I < si.nt[k]; ++I)
+            for (int J = 0; J <= I; ++J) {
+                const long long t = si.tbase[k] + (long long)I * (I + 1) / 2 + J;
+                tile_c[t] = k;
+                tile_I[t] = I;
+                float* dst = host.data() + (size_t)t * SYM_T * SYM_T * 2;
+                for (int r = 0; r < SYM_T; ++r) {
+                    const int row = I * SYM_T + r;
+                    if (row >= m) break;
+                    for (int col = 0; col < SYM_T; ++col) {
+                        const int cc = J * SYM_T + col;
+                        if (cc >= m) break;
+                        const cd v = S[(size_t)row * m + cc];   // column-major within the tile
+                        dst[2 * (col * SYM_T + r)] = (float)v.real();
+                        dst[2 * (col * SYM_T + r) + 1] = (float)v.imag();
+                    }
+                }
+            }
+    }
+    int st;
+    if ((st = c->sym_tiles.alloc(host.size() * sizeof(float)))) return st;
+    CUDA_TRY(cudaMemcpy(c->sym_tiles.p, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice));
+    // contiguous tile ranges per CTA, split into (class, tile-row) segments
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    const int G = std::max(1, sms);
+    // ranges of equal work: every tile streams the same bytes, and its FMAs grow with
+    // the class's right-hand sides and with the column part of off-diagonal tiles
+    std::vector<double> wcum(NT + 1, 0.0);
+    for (long long t = 0; t < NT; ++t) {
+        const int k = tile_c[t];
+        const long long J = t - si.tbase[k] - (long long)tile_I[t] * (tile_I[t] + 1) / 2;
+        wcum[t + 1] = wcum[t] + 1.0 + c->sym_balance * si.R[k] * (J < tile_I[t] ? 2.0 : 1.0);
+    }
+    std::vector<long long> cut(G + 1, NT);
+    cut[0] = 0;
+    for (int b = 1; b < G; ++b)
+        cut[b] = std::lower_bound(wcum.begin(), wcum.end(), wcum[NT] * b / G) - wcum.begin();
+    std::vector<int4> segs;
+    std::vector<int> cta(G + 1, 0);
+    for (int b = 0; b < G; ++b) {
+        cta[b] = (int)segs.size();
+        const long long t0 = std::min(cut[b], NT), t1 = std::max(t0, std::min(cut[b + 1], NT));
+        for (long long t = t0; t < t1;) {
+            long long e = t + 1;
+            while (e < t1 && tile_c[e] == tile_c[t] && tile_I[e] == tile_I[t]) ++e;
+            segs.push_back(make_int4(tile_c[t], tile_I[t], (int)t, (int)e));
+            t = e;
+        }
+    }
+    cta[G] = (int)segs.size();
+    std::vector<int2> rowseg(rb, make_int2(0, 0));
+    for (size_t s = 0; s < segs.size(); ++s) {
+        const int cI = si.rbase[segs[s].x] + segs[s].y;
+        if (rowseg[cI].y == 0) rowseg[cI].x = (int)s;
+        rowseg[cI].y = (int)s + 1;
+    }
+    if ((st = c->sym_seg.alloc(segs.size() * sizeof(int4)))) return st;
+    if ((st = c->sym_cta.alloc(cta.size() * sizeof(int)))) return st;
+    if ((st = c->sym_rowseg.alloc(rowseg.size() * sizeof(int2)))) return st;
+    if ((st = c->sym_rowpart.alloc(segs.size() * SYM_T * abc::dev::SYM_RMAX * sizeof(float2)))) return st;
+    if ((st = c->sym_colpart.alloc((size_t)NT * SYM_T * abc::dev::SYM_RMAX * sizeof(float2)))) return st;
+    if ((st = c->err_flag.alloc(sizeof(int)))) return st;
+    CUDA_TRY(cudaMemcpy(c->sym_seg.p, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->sym_cta.p, cta.data(), cta.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->sym_rowseg.p, rowseg.data(), rowseg.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(c->err_flag.p, 0, sizeof(int)));
+    CUDA_TRY(cudaFuncSetAttribute(abc::dev::sym_gemv_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)abc::dev::SYM_SMEM));
+    c->si = si;
+    c->sym_grid = G;
+    c->sym_tiles_n = NT;
+    c->sym = true;
+    return ABC_OK;
+}
+
+// A device wait that gave up (bounded mbarrier waits) -> ABC_ERR_TIMEOUT; resets the flag.
+int check_device_flag(abc_ctx* c, cudaStream_t s) {
+    if (!c->err_flag.p) return ABC_OK;
+    int v = 0;
+    CUDA_TRY(cudaMemcpyAsync(&v, c->err_flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (v) {
+        CUDA_TRY(cudaMemsetAsync(c->err_flag.p, 0, sizeof(int), s));
+        return fail(ABC_ERR_TIMEOUT, "a bounded device wait in the boundary contraction gave up");
+    }
+    return ABC_OK;
+}
+
 template <typename T>
 void contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaStream_t s) {
     typedef typename dev::C2<T>::t V;
     const int n = c->geo.n_gamma;
     prof_begin(c, ABC_KERNEL_CONTRACTION, s);
-    if (n_orb == 1) {
+    if (n_orb == 1 && sizeof(T) == 4 && c->sym) {
+        dev::sym_gemv_tiles<<<c->sym_grid, dev::SYM_THREADS, dev::SYM_SMEM, s>>>(
+            c->si, c->sym_tiles.as<float2>(), c->sym_seg.as<int4>(), c->sym_cta.as<int>(), (const float2*)x,
+            c->sym_rowpart.as<float2>(), c->sym_colpart.as<float2>(), conj, c->l2_keep_tiles, c->err_flag.as<int>());
+        dev::sym_reduce<<<nblk(8 * c->si.obase[c->si.nclass], 256), 256, 0, s>>>(
+            c->si, c->sym_rowseg.as<int2>(), c->sym_rowpart.as<float2>(), c->sym_colpart.as<float2>(), (float2*)t);
+        c->launches += 1;
+    } else if (n_orb == 1) {
         dev::gemv_blocks<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(c->bi, n, c->mat.as<V>(),
                                                                           (const V*)x, (V*)t, conj);
     } else {
@@ -177,13 +312,13 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
     const int order = c->params.order;
     const long long nb = (long long)g.n_rep * n_orb;
     const T h = (T)g.h;
-    dev::bnd_forward<T><<<nblk(nb, 128), 128, 0, s>>>(
+    dev::bnd_forward<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
         g.n_rep, n_orb, c->nvox, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
         c->gamma_node.as<int>(), (const Vc*)w_phi, order == 1 ? (const Vc*)w_f : nullptr, c->hat_phi.as<Vc>(),
         c->hat_f.as<Vc>());
     contraction<T>(c, order == 1 ? c->hat_f.p : c->hat_phi.p, c->tvec.p, n_orb, 0, s);
     const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
-    dev::bnd_back<T><<<nblk(nb, 128), 128, 0, s>>>(
+    dev::bnd_back<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
         order, g.n_rep, n_orb, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
         c->rep_c.as<int>(), (T)c->blocks.s, a_coef, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->tvec.as<Vc>(),
         (const Vc*)y_f, order == 1 ? (Vc*)o_f : c->cnat.as<Vc>(), cdt);
@@ -295,6 +430,7 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     if ((st = ensure_workspace(c.get()))) return st;
     if ((st = c->diag.alloc(sizeof(double) * 3 * params->max_orbitals))) return st;
     if ((st = build_tiles(c.get()))) return st;
+    if (c->prec == ABC_C64_FP32 && (st = build_sym(c.get()))) return st;
     CUDA_TRY(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming));
@@ -379,6 +515,7 @@ int run_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double 
         CUDA_TRY(cudaMemcpyAsync(diag_out, dd.p, sizeof(double) * 3 * n_orb * ndiag, cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         finish_diag(c, diag_out, ndiag * n_orb);
+        if ((st = check_device_flag(c, s))) return st;
     }
     if (!user) {
         CUDA_TRY(cudaEventRecord(c->ev_b, s));
@@ -415,7 +552,7 @@ extern "C" int abc_run_host(abc_ctx* ctx, void* psi_host, void* aux_host, const 
     CUDA_TRY(cudaMemcpyAsync(psi_host, ctx->host_psi.p, pb, cudaMemcpyDeviceToHost, s));
     if (ctx->params.order == 1) CUDA_TRY(cudaMemcpyAsync(aux_host, ctx->host_aux.p, ab, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    return ABC_OK;
+    return check_device_flag(ctx, s);
 }
 
 extern "C" int abc_diagnostics(abc_ctx* ctx, const void* psi, const void* aux, const void* V, int n_orb,
@@ -430,7 +567,7 @@ extern "C" int abc_diagnostics(abc_ctx* ctx, const void* psi, const void* aux, c
     CUDA_TRY(cudaMemcpyAsync(out, ctx->diag.p, sizeof(double) * 3 * n_orb, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     finish_diag(ctx, out, n_orb);
-    return ABC_OK;
+    return check_device_flag(ctx, s);
 }
 
 namespace {
@@ -453,11 +590,11 @@ void adj_stage(abc_ctx* c, int n_orb, T cdt, const void* a_phi, const void* a_f,
             g.n_rep, n_orb, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(), (T)c->blocks.s,
             c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->tvec.as<Vc>(), (Vc*)acc_f, (Vc*)anew_f, cdt);
     } else {
-        dev::bnd_forward<T><<<nblk(nb, 128), 128, 0, s>>>(
+        dev::bnd_forward<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
             g.n_rep, n_orb, c->nvox, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
             c->gamma_node.as<int>(), (const Vc*)a_phi, nullptr, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>());
         contraction<T>(c, c->hat_phi.p, c->tvec.p, n_orb, 1, s);
-        dev::bnd_back<T><<<nblk(nb, 128), 128, 0, s>>>(
+        dev::bnd_back<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
             0, g.n_rep, n_orb, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
             c->rep_c.as<int>(), (T)c->blocks.s, a_coef, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->tvec.as<Vc>(),
             nullptr, c->cnat.as<Vc>(), (T)0);
@@ -543,7 +680,7 @@ int adjoint_impl(abc_ctx* c, const void* psi0, const void* V, int n_orb, double 
     double J = 0;
     for (int j = 0; j < n_orb; ++j) J += 1.0 - h3 * dg[3 * j];
     *J_out = J;
-    return ABC_OK;
+    return check_device_flag(c, s);
 }
 
 }  // namespace
@@ -599,7 +736,11 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
     const double cb = (double)cplx_bytes(ctx);
     if (kernel == ABC_KERNEL_CONTRACTION) {
         double entries = 0;
-        for (int p = 0; p < 8; ++p) entries += (double)ctx->geo.m[p] * ctx->geo.m[p];
+        if (ctx->sym && n_orb == 1) {
+            entries = (double)ctx->sym_tiles_n * abc::dev::SYM_T * abc::dev::SYM_T;   // stored tiles, read once
+        } else {
+            for (int p = 0; p < 8; ++p) entries += (double)ctx->geo.m[p] * ctx->geo.m[p];
+        }
         *bytes = entries * cb + 2.0 * ctx->geo.n_gamma * n_orb * cb;
     } else if (kernel == ABC_KERNEL_STENCIL) {
         *bytes = (double)ctx->nvox * (3.0 * n_orb * cb + ctx->real_bytes);
@@ -607,6 +748,24 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
         return fail(ABC_ERR_ARG, "unknown kernel");
     }
     return ABC_OK;
+}
+
+extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
+    if (!ctx) return fail(ABC_ERR_ARG, "null context");
+    if (key == ABC_TUNE_L2_KEEP_TILES) {
+        if (value < 0) return fail(ABC_ERR_ARG, "keep count must be >= 0");
+        ctx->l2_keep_tiles = value;
+        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        return ABC_OK;
+    }
+    return fail(ABC_ERR_ARG, "unknown tuning key");
+}
+
+extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
+    if (!ctx || !value) return fail(ABC_ERR_ARG, "null argument");
+    if (key == ABC_TUNE_L2_KEEP_TILES) { *value = ctx->l2_keep_tiles; return ABC_OK; }
+    if (key == ABC_TUNE_TILE_COUNT) { *value = ctx->sym ? ctx->sym_tiles_n : 0; return ABC_OK; }
+    return fail(ABC_ERR_ARG, "unknown tuning key");
 }
 
 extern "C" int abc_launch_count(const abc_ctx* ctx, long long* launches) {

@@ -9,6 +9,7 @@
 
 #include "internal.h"
 #include "kernels.cuh"
+#include "sym_gemv.cuh"
 
 namespace abc {
 int fail(int status, const std::string& msg);
@@ -61,6 +62,14 @@ struct abc_ctx {
     // graph cache
     cudaGraphExec_t gexec = nullptr;
     struct Key { const void *psi, *aux, *V; int n_orb; double dt; int mf; double a, b, alpha; cudaStream_t s; } key{};
+    // one-orbital complex64 contraction on symmetric packed tiles
+    bool sym = false;
+    abc::dev::SymInfo si{};
+    int sym_grid = 0;
+    long long sym_tiles_n = 0;
+    long long l2_keep_tiles = 0;     // tiles streamed with evict_last (tuning)
+    double sym_balance = 0.0;        // extra work weight per right-hand side in the tile partition (tuning)
+    abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, err_flag;
     // launch accounting
     long long launches = 0;
     long long graph_kernels = 0;

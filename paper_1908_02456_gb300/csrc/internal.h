@@ -38,6 +38,13 @@ struct Geometry {
     std::vector<int> rep_stab;          // |stabiliser of r| (1, 2, 4 or 8)
     int m[8] = {0}, off[8] = {0};       // block sizes / offsets in adapted numbering
     std::vector<int> adapted_rep;       // adapted index -> representative
+    // Axis-permutation classes (cubes only).  A permutation pi of the axes maps the
+    // parity-p basis onto the parity-pi(p) basis and commutes with K, so blocks whose
+    // parities have the same number of odd axes are equal once their representatives
+    // are numbered consistently (local index of r in block pi(b) = local index of
+    // pi^{-1}(r) in block b).  base_of[p] is the block that stores the matrix of p.
+    bool cube = false;
+    int base_of[8] = {0, 1, 2, 3, 4, 5, 6, 7};
 };
 
 // Closed-form Gamma index of a boundary node (ascending linear order).
@@ -48,7 +55,8 @@ int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& e
 // FP64 coefficient blocks in the parity-adapted basis (row-major m_p x m_p each).
 //   order 0: mat[p] = M_p = K_p(s0)
 //   order 1: mat[p] = S_p = K_p(s1)^{-1}; B = s1 I - A S with A diagonal
-// Both are complex symmetric.
+// Both are complex symmetric.  Only blocks with base_of[p] == p are filled; the
+// others equal their base block.
 struct Blocks {
     int order = 0;
     double s = 0.0;

@@ -50,12 +50,26 @@ template <typename V> __device__ __forceinline__ void wht8(V* x) {
     }
 }
 
+// 8-point Walsh-Hadamard transform across the 8 lanes of an aligned lane group:
+// lane g holds in[g] and receives out[g] = sum_h (-1)^{popcount(g&h)} in[h].
+template <typename V> __device__ __forceinline__ V wht8_lanes(V v, int g) {
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1) {
+        const decltype(v.x) ox = __shfl_xor_sync(0xffffffffu, v.x, bit);
+        const decltype(v.y) oy = __shfl_xor_sync(0xffffffffu, v.y, bit);
+        if (g & bit) { v.x = ox - v.x; v.y = oy - v.y; }
+        else { v.x = v.x + ox; v.y = v.y + oy; }
+    }
+    return v;
+}
+
 // --------------------------------------------------------------------------
 // Boundary: natural Gamma order -> parity-adapted order (E, then U^T)
 // --------------------------------------------------------------------------
-// Thread (r, j): gathers phi at the 8 reflections of representative r (and f,
-// order 1), applies the 8-point transform with scale 1/sqrt(8|H_r|), and stores the
-// parity components that exist for r.
+// Eight lanes per (representative r, orbital j): lane g gathers the value at the
+// reflection g.r (phi at the node, and f at its Gamma index for order 1); the lane
+// group transforms them and lane p stores parity component p (scale 1/sqrt(8|H_r|))
+// when it exists for r.  Launch with 8 * n_rep * n_orb threads, blockDim % 32 == 0.
 template <typename T>
 __global__ void bnd_forward(int n_rep, int n_orb, long long nvox, const int* __restrict__ rep_gamma,
                             const int* __restrict__ rep_adapted, const int* __restrict__ rep_stab,
@@ -64,27 +78,26 @@ __global__ void bnd_forward(int n_rep, int n_orb, long long nvox, const int* __r
                             const typename C2<T>::t* __restrict__ w_f,
                             typename C2<T>::t* __restrict__ hat_phi, typename C2<T>::t* __restrict__ hat_f) {
     typedef typename C2<T>::t V;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)n_rep * n_orb) return;
-    const int j = (int)(idx % n_orb);
-    const int r = (int)(idx / n_orb);
-    const T sc = (T)rsqrt(8.0 * rep_stab[r]);
-    V xp[8], xf[8];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long idx = gid >> 3;
+    const int g = (int)(gid & 7);
+    const bool live = idx < (long long)n_rep * n_orb;
+    const int j = live ? (int)(idx % n_orb) : 0;
+    const int r = live ? (int)(idx / n_orb) : 0;
+    V xp = mk<T>(0, 0), xf = mk<T>(0, 0);
+    if (live) {
         const int gi = rep_gamma[r * 8 + g];
-        xp[g] = w_phi[(long long)j * nvox + gamma_node[gi]];
-        if (w_f) xf[g] = w_f[(long long)gi * n_orb + j];
+        xp = w_phi[(long long)j * nvox + gamma_node[gi]];
+        if (w_f) xf = w_f[(long long)gi * n_orb + j];
     }
-    wht8(xp);
-    if (w_f) wht8(xf);
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        const int q = rep_adapted[r * 8 + p];
-        if (q < 0) continue;
-        hat_phi[(long long)q * n_orb + j] = mk<T>(sc * xp[p].x, sc * xp[p].y);
-        if (w_f) hat_f[(long long)q * n_orb + j] = mk<T>(sc * xf[p].x, sc * xf[p].y);
-    }
+    xp = wht8_lanes(xp, g);
+    if (w_f) xf = wht8_lanes(xf, g);
+    if (!live) return;
+    const int q = rep_adapted[r * 8 + g];
+    if (q < 0) return;
+    const T sc = (T)rsqrt(8.0 * rep_stab[r]);
+    hat_phi[(long long)q * n_orb + j] = mk<T>(sc * xp.x, sc * xp.y);
+    if (w_f) hat_f[(long long)q * n_orb + j] = mk<T>(sc * xf.x, sc * xf.y);
 }
 
 // --------------------------------------------------------------------------
@@ -94,6 +107,10 @@ __global__ void bnd_forward(int n_rep, int n_orb, long long nvox, const int* __r
 //           (this is B f + A E phi with B = s1 I - A S, t = S f_hat), then
 //           out_f = y_f + cdt * U g_hat
 // order 0:  out_c = U t  (t = M phi_hat), the natural-order E^T M E phi term
+// Eight lanes per (r, j): lane p forms parity component p, the group transforms
+// back, lane g writes the value of reflection g.r.  Nodes fixed by a reflection
+// appear in several lanes; only the lowest such lane writes (it alone reads y_f
+// there, so the update in place is race-free).
 template <typename T>
 __global__ void bnd_back(int order, int n_rep, int n_orb, const int* __restrict__ rep_gamma,
                          const int* __restrict__ rep_adapted, const int* __restrict__ rep_stab,
@@ -102,44 +119,46 @@ __global__ void bnd_back(int order, int n_rep, int n_orb, const int* __restrict_
                          const typename C2<T>::t* __restrict__ hat_f, const typename C2<T>::t* __restrict__ t,
                          const typename C2<T>::t* y_f, typename C2<T>::t* out, T cdt) {
     typedef typename C2<T>::t V;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)n_rep * n_orb) return;
-    const int j = (int)(idx % n_orb);
-    const int r = (int)(idx / n_orb);
-    const T a = a_coef * (T)rep_c[r];             // a_r = -i * a (imaginary coefficient)
-    V x[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        const int q = rep_adapted[r * 8 + p];
-        if (q < 0) { x[p] = mk<T>(0, 0); continue; }
-        const long long e = (long long)q * n_orb + j;
-        const V tv = t[e];
-        if (order == 1) {
-            const V fv = hat_f[e], pv = hat_phi[e];
-            const T dr = pv.x - tv.x, di = pv.y - tv.y;
-            // s1 f + (-i a)(d) = (s1 f.x + a d.y, s1 f.y - a d.x)
-            x[p] = mk<T>(s1 * fv.x + a * di, s1 * fv.y - a * dr);
-        } else {
-            x[p] = tv;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long idx = gid >> 3;
+    const int g = (int)(gid & 7);
+    const bool live = idx < (long long)n_rep * n_orb;
+    const int j = live ? (int)(idx % n_orb) : 0;
+    const int r = live ? (int)(idx / n_orb) : 0;
+    V x = mk<T>(0, 0);
+    int gi = -1;
+    if (live) {
+        gi = rep_gamma[r * 8 + g];
+        const int q = rep_adapted[r * 8 + g];
+        if (q >= 0) {
+            const long long e = (long long)q * n_orb + j;
+            const V tv = t[e];
+            if (order == 1) {
+                const T a = a_coef * (T)rep_c[r];             // a_r = -i * a
+                const V fv = hat_f[e], pv = hat_phi[e];
+                const T dr = pv.x - tv.x, di = pv.y - tv.y;
+                // s1 f + (-i a)(d) = (s1 f.x + a d.y, s1 f.y - a d.x)
+                x = mk<T>(s1 * fv.x + a * di, s1 * fv.y - a * dr);
+            } else {
+                x = tv;
+            }
         }
     }
-    wht8(x);
+    x = wht8_lanes(x, g);
+    bool first = true;
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1) {
+        const int o = __shfl_xor_sync(0xffffffffu, gi, bit);
+        if ((g & bit) && o == gi) first = false;
+    }
+    if (!live || !first) return;
     const T sc = (T)sqrt(rep_stab[r] / 8.0);
+    const long long e = (long long)gi * n_orb + j;
     if (order == 1) {
-        V yv[8];
-#pragma unroll
-        for (int g = 0; g < 8; ++g) yv[g] = y_f[(long long)rep_gamma[r * 8 + g] * n_orb + j];
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            const long long e = (long long)rep_gamma[r * 8 + g] * n_orb + j;
-            out[e] = mk<T>(yv[g].x + cdt * sc * x[g].x, yv[g].y + cdt * sc * x[g].y);
-        }
+        const V yv = y_f[e];
+        out[e] = mk<T>(yv.x + cdt * sc * x.x, yv.y + cdt * sc * x.y);
     } else {
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            const long long e = (long long)rep_gamma[r * 8 + g] * n_orb + j;
-            out[e] = mk<T>(sc * x[g].x, sc * x[g].y);
-        }
+        out[e] = mk<T>(sc * x.x, sc * x.y);
     }
 }
 

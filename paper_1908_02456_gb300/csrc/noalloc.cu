@@ -54,7 +54,9 @@ int scratch_for_device(int dev, void** out) {
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Same kernels, launch shapes and order as abc_step; only the scratch differs.
+// The stages of abc_step on scratch from the static array.  The one-orbital
+// contraction uses the full-block kernel (no partial-sum scratch), so for complex64
+// the summation order differs from abc_step's symmetric-tile kernel.
 template <typename T>
 void step_with_scratch(const abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double dt, char* scratch,
                        cudaStream_t s) {
@@ -77,7 +79,7 @@ void step_with_scratch(const abc_ctx* c, void* psi, void* aux, const void* V, in
         void* op = st == 3 ? psi : (void*)Tp[st & 1];
         void* of = st == 3 ? aux : (void*)Tf[st & 1];
         const T cdt = (T)(cs[st] * dt);
-        abc::dev::bnd_forward<T><<<nblk(nb, 128), 128, 0, s>>>(
+        abc::dev::bnd_forward<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
             g.n_rep, n_orb, c->nvox, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
             c->gamma_node.as<int>(), (const Vc*)in_p, order == 1 ? (const Vc*)in_f : nullptr, hat_phi, hat_f);
         const Vc* x = order == 1 ? hat_f : hat_phi;
@@ -90,7 +92,7 @@ void step_with_scratch(const abc_ctx* c, void* psi, void* aux, const void* V, in
                 c->bi, n_orb, c->mat.as<Vc>(), x, tvec, 0, c->tile_blk.as<int>(), c->tile_row.as<int>());
         }
         const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
-        abc::dev::bnd_back<T><<<nblk(nb, 128), 128, 0, s>>>(
+        abc::dev::bnd_back<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
             order, g.n_rep, n_orb, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
             c->rep_c.as<int>(), (T)c->blocks.s, a_coef, hat_phi, hat_f, tvec, (const Vc*)aux,
             order == 1 ? (Vc*)of : cnat, cdt);

@@ -89,15 +89,52 @@ int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& e
     for (int p = 0; p < 8; ++p) { g.m[p] = cnt[p]; g.off[p] = acc; acc += cnt[p]; }
     if (acc != g.n_gamma) { err = "internal: parity blocks do not cover Gamma"; return ABC_ERR_ARG; }
     g.adapted_rep.assign(g.n_gamma, -1);
+    g.cube = (nx == ny && ny == nz);
+    if (g.cube) {
+        static const int bases[4] = {0, 1, 3, 7};
+        for (int p = 0; p < 8; ++p) g.base_of[p] = bases[__builtin_popcount(p)];
+    }
+    // representative index of a node (low octant only)
+    std::vector<int> node_rep((size_t)g.n_nodes, -1);
+    for (int r = 0; r < g.n_rep; ++r) node_rep[g.rep_node[r]] = r;
+    std::vector<int> loc((size_t)g.n_rep * 8, -1);
     for (int p = 0; p < 8; ++p) {
-        int loc = 0;
+        if (g.base_of[p] != p) continue;
+        int l = 0;
+        for (int r = 0; r < g.n_rep; ++r)
+            if (!(p & fixed_mask[r])) loc[(size_t)r * 8 + p] = l++;
+    }
+    static const int perms[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0}, {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
+    for (int p = 0; p < 8; ++p) {
+        const int b = g.base_of[p];
+        if (b == p) continue;
+        const int* pi = nullptr;          // axis a of the base maps to axis pi[a]
+        for (auto& cand : perms) {
+            int img = 0;
+            for (int a = 0; a < 3; ++a)
+                if (b >> a & 1) img |= 1 << cand[a];
+            if (img == p) { pi = cand; break; }
+        }
+        if (!pi) { err = "internal: no axis permutation between parity blocks"; return ABC_ERR_ARG; }
         for (int r = 0; r < g.n_rep; ++r) {
             if (p & fixed_mask[r]) continue;
-            const int q = g.off[p] + loc++;
+            const int node = g.rep_node[r];
+            const int co[3] = {node % nx, (node / nx) % ny, node / (nx * ny)};
+            int src[3];                   // pi^{-1}(r): coordinate a of the source is co[pi[a]]
+            for (int a = 0; a < 3; ++a) src[a] = co[pi[a]];
+            const int rs = node_rep[(src[2] * ny + src[1]) * nx + src[0]];
+            if (rs < 0 || loc[(size_t)rs * 8 + b] < 0) { err = "internal: class numbering"; return ABC_ERR_ARG; }
+            loc[(size_t)r * 8 + p] = loc[(size_t)rs * 8 + b];
+        }
+    }
+    for (int p = 0; p < 8; ++p)
+        for (int r = 0; r < g.n_rep; ++r) {
+            const int l = loc[(size_t)r * 8 + p];
+            if (l < 0) continue;
+            const int q = g.off[p] + l;
             g.rep_adapted[(size_t)r * 8 + p] = q;
             g.adapted_rep[q] = r;
         }
-    }
     return ABC_OK;
 }
 
@@ -290,6 +327,7 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
     const int dims[3] = {nx, ny, nz};
     std::vector<cd> X[8], Y[8];
     for (int p = 0; p < 8; ++p) {
+        if (g.base_of[p] != p) continue;
         X[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
         Y[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
     }
@@ -315,6 +353,7 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
             }
             const double sc = 1.0 / std::sqrt((double)g.rep_stab[ri] * g.rep_stab[rj]);
             for (int p = 0; p < 8; ++p) {
+                if (g.base_of[p] != p) continue;
                 const int qi = g.rep_adapted[(size_t)ri * 8 + p], qj = g.rep_adapted[(size_t)rj * 8 + p];
                 if (qi < 0 || qj < 0) continue;
                 cd xs(0.0, 0.0), ys(0.0, 0.0);
@@ -334,7 +373,7 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
     out.s = s;
     for (int p = 0; p < 8; ++p) {
         const int m = g.m[p];
-        if (m == 0) continue;
+        if (m == 0 || g.base_of[p] != p) continue;
         std::vector<int> piv(m);
         std::vector<cd>& F = order == 0 ? X[p] : Y[p];     // factorised
         std::vector<cd>& Z = order == 0 ? Y[p] : X[p];     // right-hand sides -> result
@@ -378,6 +417,7 @@ int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::s
     std::vector<cd> blk[8];
     for (int p = 0; p < 8; ++p) {
         const int m = g.m[p];
+        if (g.base_of[p] != p) continue;
         blk[p] = b.mat[p];
         if (m && b.order == 1 && which == ABC_MAT_K) {
             std::vector<cd> F(b.mat[p]), Z((size_t)m * m, cd(0.0, 0.0));
@@ -402,7 +442,7 @@ int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::s
                         const int qi = g.rep_adapted[(size_t)ri * 8 + p], qj = g.rep_adapted[(size_t)rj * 8 + p];
                         if (qi < 0 || qj < 0) continue;
                         const double chi = (__builtin_popcount(p & (gi ^ gj)) & 1) ? -1.0 : 1.0;
-                        acc += chi * blk[p][(size_t)(qi - g.off[p]) * g.m[p] + (qj - g.off[p])];
+                        acc += chi * blk[g.base_of[p]][(size_t)(qi - g.off[p]) * g.m[p] + (qj - g.off[p])];
                     }
                     out[(size_t)yi * n + yj] = w * acc;   // duplicates (stabilised reps) agree
                 }
