@@ -34,6 +34,7 @@ import numpy as np  # noqa: E402
 
 METRIC = "orbital*gridpoint*steps/s"
 WORKLOAD_NUMBER = 2
+L2_FLUSH_BYTES = 256 << 20          # written before every timed step (L2 is 129 MB)
 
 
 def parse():
@@ -44,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU form")
+    ap.add_argument("--workload", type=int, default=WORKLOAD_NUMBER,
+                    help="1-5; the default (2) is the benchmark line, the others print a line of their own")
     return ap.parse_args()
 
 
@@ -177,8 +180,8 @@ def reference_arm(args, w):
 
 
 def config_dict(w, matrix_mb=None):
-    l2 = "inputs larger than L2 (129 MB): the packed boundary tiles read every stage"
-    l2 += f" are {matrix_mb:.0f} MB" if matrix_mb else ""
+    l2 = f"L2 flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write; L2 is 129 MB)"
+    l2 += f"; packed boundary tiles {matrix_mb:.0f} MB" if matrix_mb else ""
     return {"workload": w.name, "grid": list(w.shape), "h": w.h, "n_orb": w.n_orb, "order": w.order,
             "s1": w.s, "dt": w.dt, "potential": "0.5*0.09*r^2 + 8 seeded Gaussian bumps",
             "precision": "complex64 state, FP32 boundary contraction, FP64 reductions", "l2": l2}
@@ -187,12 +190,84 @@ def config_dict(w, matrix_mb=None):
 # ----------------------------------------------------------------------
 # native arm
 # ----------------------------------------------------------------------
+def other_workload(args, w):
+    """One line for a workload other than the benchmark one: K time steps (mean-field
+    workloads: the potential is rebuilt from the density every step) or, for the
+    adjoint workload, one forward + reverse sweep of K steps; the oracle is not timed."""
+    import torch
+    from paper_1908_02456_gb300 import abc
+    from paper_1908_02456_gb300 import build as nbuild
+    nbuild.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    psi0, V = inputs_for(w)
+    ctx = abc.Context(w.shape, w.h, w.order, w.s, precision=w.precision, max_orbitals=w.n_orb)
+    psi = torch.from_numpy(psi0).to(dev, ctx.complex_dtype)
+    aux = ctx.new_aux(w.n_orb) if w.order == 1 else None
+    Vt = torch.from_numpy(V).to(dev, ctx.real_dtype)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    units = float(w.n_orb) * np.prod(w.shape) * args.steps
+    if w.number == 4:
+        ctx.adjoint(psi, Vt, w.dt, max(args.warmup, 1), ckpt_every=50)
+        flush.fill_(0.0)
+        torch.cuda.synchronize()
+        launches0 = ctx.launches()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record(stream)
+            J, g = ctx.adjoint(psi, Vt, w.dt, args.steps, ckpt_every=50)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        what = "forward sweep + checkpointed reverse sweep (abc_adjoint_run), L2 flushed before the call"
+    else:
+        ctx.run(psi, aux, Vt, w.dt, max(args.warmup, 1), meanfield=w.meanfield)
+        flush.fill_(0.0)
+        torch.cuda.synchronize()
+        launches0 = ctx.launches()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record(stream)
+            ctx.run(psi, aux, Vt, w.dt, args.steps, meanfield=w.meanfield)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        what = "graph-replayed steps; state and boundary blocks exceed L2"
+    sec = e0.elapsed_time(e1) * 1e-3
+    launches = ctx.launches() - launches0
+    # contraction timing over a short profiled run
+    nprof = min(args.steps, 50)
+    ctx.profile(True)
+    if w.number == 4:
+        ctx.run(psi, aux, Vt, w.dt, nprof)
+    else:
+        ctx.run(psi, aux, Vt, w.dt, nprof, meanfield=w.meanfield)
+    ms_c, n_c = ctx.profile_read(abc.KERNEL_CONTRACTION)
+    ctx.profile(False)
+    bytes_c = ctx.kernel_bytes(abc.KERNEL_CONTRACTION, w.n_orb)
+    line = {"metric": METRIC, "value": units / sec, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "c64",
+            "data": "synthetic", "config": {"workload": w.name, "grid": list(w.shape), "h": w.h, "n_orb": w.n_orb,
+                                           "order": w.order, "s": w.s, "dt": w.dt, "meanfield": w.meanfield,
+                                           "precision": w.precision, "what": what},
+            "contraction": {"avg_launch_us": round(ms_c / n_c * 1e3, 2), "bytes_per_launch": bytes_c,
+                            "achieved_gbs": round(bytes_c / (ms_c / n_c * 1e-3) / 1e9, 1)},
+            "clocks": clk.summary(), "gpu_launches": launches}
+    print(json.dumps(line))
+    ctx.close()
+
+
+def inputs_for(w):
+    from paper_1908_02456_gb300 import inputs
+    return inputs.make_inputs(w)
+
+
 def main():
     args = parse()
     from paper_1908_02456_gb300 import inputs
-    w = inputs.WORKLOADS[WORKLOAD_NUMBER]
+    w = inputs.WORKLOADS[args.workload]
     if args.impl == "reference":
         return reference_arm(args, w)
+    if args.workload != WORKLOAD_NUMBER:
+        return other_workload(args, w)
 
     import torch
     import torch.distributed as dist
@@ -215,27 +290,46 @@ def main():
     # warm-up (also captures the CUDA graph)
     ctx.run(psi, aux, Vt, w.dt, max(args.warmup, 1))
     torch.cuda.synchronize()
+    # L2 is flushed before every timed step by writing a buffer twice its size (the
+    # boundary tiles alone fit in L2); each step is timed by its own event pair on
+    # the launching stream and the flush stays outside the pairs
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = ctx.launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         barrier()
         torch.cuda.synchronize()
-        e0.record(stream)
-        ctx.run(psi, aux, Vt, w.dt, args.steps)
-        e1.record(stream)
+        for i in range(args.steps):
+            flush.fill_(float(i & 7))
+            ev[i][0].record(stream)
+            ctx.run(psi, aux, Vt, w.dt, 1)
+            ev[i][1].record(stream)
         torch.cuda.synchronize()
         barrier()
-    sec = e0.elapsed_time(e1) * 1e-3
+    sec = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
     gpu_launches = ctx.launches() - launches0
     units = float(w.n_orb) * np.prod(w.shape) * args.steps
     tot_units, max_sec = aggregate(units, sec)
     value = tot_units / max_sec
 
-    # dominant kernel: live CUDA-event timing of every contraction launch over a pass
-    # of the same steps on the launching stream (eager launches, no graph)
+    # steady state for context: the same steps as one graph-replayed run, no flush
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.run(psi, aux, Vt, w.dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    warm_sec = e0.elapsed_time(e1) * 1e-3
+    steady = {"value": units / warm_sec, "ms_per_step": warm_sec / args.steps * 1e3,
+              "note": "one run of the same number of steps, L2 not flushed between steps"}
+
+    # dominant kernel: live CUDA-event timing of every contraction launch over the
+    # same flushed steps on the launching stream (eager launches, no graph)
     nprof = min(args.steps, 500)
     ctx.profile(True)
-    ctx.run(psi, aux, Vt, w.dt, nprof)
+    for i in range(nprof):
+        flush.fill_(float(i & 7))
+        ctx.run(psi, aux, Vt, w.dt, 1)
     ms_c, n_c = ctx.profile_read(abc.KERNEL_CONTRACTION)
     ms_s, n_s = ctx.profile_read(abc.KERNEL_STENCIL)
     ctx.profile(False)
@@ -267,15 +361,18 @@ def main():
     psi_h = torch.from_numpy(psi0.astype(np.complex64)).pin_memory()
     aux_h = torch.zeros((ctx.n_gamma, w.n_orb), dtype=torch.complex64).pin_memory()
     V_h = torch.from_numpy(V.astype(np.float32)).pin_memory()
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctx.run_host(psi_h, aux_h, V_h, w.dt, args.steps)
     e2e_sec = time.perf_counter() - t0
+    del flush
     tot_e2e, max_e2e = aggregate(units, e2e_sec)
     h2d = psi_h.numel() * 8 + aux_h.numel() * 8 + V_h.numel() * 4
     d2h = psi_h.numel() * 8 + aux_h.numel() * 8
     e2e = {"value": tot_e2e / max_e2e, "unit": METRIC, "h2d_bytes_per_step": h2d / args.steps,
            "d2h_bytes_per_step": d2h / args.steps,
-           "call": "abc_run_host: copy psi, f, V in; run the steps; copy psi, f out"}
+           "call": "abc_run_host: copy psi, f, V in; run the steps; copy psi, f out (L2 flushed before the call)"}
 
     # plain FP64 GPU form on the same inputs
     fp64 = None
@@ -311,7 +408,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": max_sec / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
                 "config": config_dict(w, bytes_c / 1e6), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clk.summary(), "gpu_launches": gpu_launches, "fp64_form": fp64,
+                "clocks": clk.summary(), "gpu_launches": gpu_launches, "fp64_form": fp64, "steady_state": steady,
                 "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(line))
     ctx.close()

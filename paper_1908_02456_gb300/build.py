@@ -24,7 +24,7 @@ NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-fop
 CXX_FLAGS = ["-std=c++17", "-O3", "-fPIC", "-fopenmp", "-I", INC, "-I", CSRC]
 
 CU_SOURCES = ["api.cu", "noalloc.cu"]
-CXX_SOURCES = ["dense.cpp", "setup.cpp", "host_api.cpp"]
+CXX_SOURCES = ["dense.cpp", "setup.cpp", "symmetry.cpp", "host_api.cpp"]
 
 
 def _nvcc() -> str:

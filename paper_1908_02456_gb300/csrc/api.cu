@@ -33,50 +33,70 @@ inline size_t cplx_bytes(const abc_ctx* c) { return 2 * c->real_bytes; }
 
 int upload_tables(abc_ctx* c) {
     const Geometry& g = c->geo;
-    std::vector<int> rc(g.n_rep);
-    for (int r = 0; r < g.n_rep; ++r) rc[r] = g.gamma_c[g.node_gamma[g.rep_node[r]]];
     struct { DevBuf* b; const int* src; size_t n; } t[] = {
-        {&c->rep_gamma, g.rep_gamma.data(), g.rep_gamma.size()},
-        {&c->rep_adapted, g.rep_adapted.data(), g.rep_adapted.size()},
-        {&c->rep_stab, g.rep_stab.data(), g.rep_stab.size()},
-        {&c->rep_c, rc.data(), rc.size()},
-        {&c->gamma_node, g.gamma_node.data(), g.gamma_node.size()},
         {&c->gamma_c, g.gamma_c.data(), g.gamma_c.size()},
+        {&c->cell_out, g.cell_out.data(), g.cell_out.size()},
+        {&c->cell_type, g.cell_type.data(), g.cell_type.size()},
+        {&c->cell_c, g.cell_c.data(), g.cell_c.size()},
+        {&c->cell_gi, g.cell_gi.data(), g.cell_gi.size()},
+        {&c->cell_node, g.cell_node.data(), g.cell_node.size()},
+        {&c->cell_wr, g.cell_wr.data(), g.cell_wr.size()},
+        {&c->adapted_cls, g.adapted_cls.data(), g.adapted_cls.size()},
     };
     for (auto& e : t) {
         int st = e.b->alloc(e.n * sizeof(int));
         if (st) return st;
         CUDA_TRY(cudaMemcpy(e.b->p, e.src, e.n * sizeof(int), cudaMemcpyHostToDevice));
     }
+    int st;
+    for (auto pr : {std::make_pair(&c->cell_coef_f, &g.coef_f), std::make_pair(&c->cell_coef_bt, &g.coef_bt)}) {
+        const std::vector<double>& v = *pr.second;
+        if (c->prec == ABC_FP64) {
+            if ((st = pr.first->alloc(v.size() * sizeof(double)))) return st;
+            CUDA_TRY(cudaMemcpy(pr.first->p, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> f(v.begin(), v.end());
+            if ((st = pr.first->alloc(f.size() * sizeof(float)))) return st;
+            CUDA_TRY(cudaMemcpy(pr.first->p, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
+    }
     return ABC_OK;
 }
 
-// Parity blocks in the device format: row-major, rows padded to a multiple of 4
-// complex elements so that every row starts on a 32-byte boundary.
+// Class blocks in the device format: row-major, rows padded to a multiple of 4
+// complex elements so that every row starts on a 32-byte boundary.  One BlockInfo
+// entry per (class, right-hand side), in ascending adapted offset.
 int upload_matrices(abc_ctx* c) {
     const Geometry& g = c->geo;
     long long total = 0;
-    for (int p = 0; p < 8; ++p) {
-        c->bi.m[p] = g.m[p];
-        c->bi.off[p] = g.off[p];
-        c->bi.ld[p] = (g.m[p] + 3) & ~3;
-        if (g.base_of[p] != p) {            // shares its class's base block
-            c->bi.mat_off[p] = c->bi.mat_off[g.base_of[p]];
-            continue;
-        }
-        c->bi.mat_off[p] = total;
-        total += (long long)c->bi.ld[p] * g.m[p];
+    std::vector<long long> moff(g.cls.size());
+    std::vector<int> lds(g.cls.size());
+    for (size_t k = 0; k < g.cls.size(); ++k) {
+        lds[k] = (g.cls[k].m + 3) & ~3;
+        moff[k] = total;
+        total += (long long)lds[k] * g.cls[k].m;
     }
-    if (c->prec == ABC_C64_SPLIT_BF16)
-        return fail(ABC_ERR_UNSUPPORTED, "split-bf16 contraction not built yet");
+    struct E { int off, m, ld; long long mo; };
+    std::vector<E> es;
+    for (size_t k = 0; k < g.cls.size(); ++k)
+        for (int e = 0; e < g.cls[k].R; ++e) es.push_back({g.cls[k].moff[e], g.cls[k].m, lds[k], moff[k]});
+    std::sort(es.begin(), es.end(), [](const E& a, const E& b) { return a.off < b.off; });
+    if ((int)es.size() > dev::MAX_ENTRIES) return fail(ABC_ERR_ARG, "internal: too many block entries");
+    c->bi = BlockInfo{};
+    c->bi.n = (int)es.size();
+    for (size_t i = 0; i < es.size(); ++i) {
+        c->bi.m[i] = es[i].m;
+        c->bi.off[i] = es[i].off;
+        c->bi.ld[i] = es[i].ld;
+        c->bi.mat_off[i] = es[i].mo;
+    }
     const size_t eb = cplx_bytes(c);
     int st = c->mat.alloc((size_t)total * eb);
     if (st) return st;
     CUDA_TRY(cudaMemset(c->mat.p, 0, (size_t)total * eb));
-    for (int p = 0; p < 8; ++p) {
-        const int m = g.m[p], ld = c->bi.ld[p];
-        if (!m || g.base_of[p] != p) continue;
-        const std::vector<cd>& M = c->blocks.mat[p];
+    for (size_t k = 0; k < g.cls.size(); ++k) {
+        const int m = g.cls[k].m, ld = lds[k];
+        const std::vector<cd>& M = c->blocks.mat[k];
         if (c->prec == ABC_FP64) {
             std::vector<double> buf((size_t)2 * ld * m, 0.0);
             for (int a = 0; a < m; ++a)
@@ -84,8 +104,7 @@ int upload_matrices(abc_ctx* c) {
                     buf[2 * ((size_t)a * ld + b)] = M[(size_t)a * m + b].real();
                     buf[2 * ((size_t)a * ld + b) + 1] = M[(size_t)a * m + b].imag();
                 }
-            CUDA_TRY(cudaMemcpy(c->mat.as<char>() + c->bi.mat_off[p] * eb, buf.data(), buf.size() * 8,
-                                cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(c->mat.as<char>() + moff[k] * eb, buf.data(), buf.size() * 8, cudaMemcpyHostToDevice));
         } else {
             std::vector<float> buf((size_t)2 * ld * m, 0.0f);
             for (int a = 0; a < m; ++a)
@@ -93,8 +112,7 @@ int upload_matrices(abc_ctx* c) {
                     buf[2 * ((size_t)a * ld + b)] = (float)M[(size_t)a * m + b].real();
                     buf[2 * ((size_t)a * ld + b) + 1] = (float)M[(size_t)a * m + b].imag();
                 }
-            CUDA_TRY(cudaMemcpy(c->mat.as<char>() + c->bi.mat_off[p] * eb, buf.data(), buf.size() * 4,
-                                cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(c->mat.as<char>() + moff[k] * eb, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice));
         }
     }
     return ABC_OK;
@@ -145,7 +163,7 @@ void prof_end(abc_ctx* c, int k, cudaStream_t s) {
 namespace {
 int build_tiles(abc_ctx* c) {
     std::vector<int> tb, tr;
-    for (int p = 0; p < 8; ++p)
+    for (int p = 0; p < c->bi.n; ++p)
         for (int r0 = 0; r0 < c->bi.m[p]; r0 += 32) { tb.push_back(p); tr.push_back(r0); }
     c->n_tiles = (int)tb.size();
     int st;
@@ -162,35 +180,30 @@ int build_sym(abc_ctx* c) {
     using abc::dev::SYM_T;
     const Geometry& g = c->geo;
     abc::dev::SymInfo si{};
-    int nc = 0, cls_base[8] = {0};
+    int nc = 0;
     long long tb = 0;
     int rb = 0;
-    for (int b = 0; b < 8; ++b) {
-        if (g.base_of[b] != b || g.m[b] == 0) continue;
-        int R = 0;
-        for (int p = 0; p < 8; ++p)
-            if (g.base_of[p] == b) si.moff[nc][R++] = g.off[p];
-        const int nt = (g.m[b] + SYM_T - 1) / SYM_T;
-        si.R[nc] = R;
-        si.m[nc] = g.m[b];
+    if ((int)g.cls.size() > abc::dev::SYM_CMAX) return fail(ABC_ERR_ARG, "internal: too many classes");
+    for (const auto& k : g.cls) {
+        const int nt = (k.m + SYM_T - 1) / SYM_T;
+        for (int e = 0; e < k.R; ++e) si.moff[nc][e] = k.moff[e];
+        si.R[nc] = k.R;
+        si.m[nc] = k.m;
         si.nt[nc] = nt;
         si.tbase[nc] = tb;
         si.rbase[nc] = rb;
-        cls_base[nc] = b;
         tb += (long long)nt * (nt + 1) / 2;
         rb += nt;
         ++nc;
     }
     si.nclass = nc;
-    si.obase[0] = 0;
-    for (int k = 0; k < nc; ++k) si.obase[k + 1] = si.obase[k] + (long long)si.nt[k] * SYM_T * si.R[k];
     const long long NT = tb;
     // tiles
     std::vector<float> host((size_t)NT * SYM_T * SYM_T * 2, 0.0f);
     std::vector<int> tile_c(NT), tile_I(NT);
     for (int k = 0; k < nc; ++k) {
         const int m = si.m[k];
-        const std::vector<cd>& S = c->blocks.mat[cls_base[k]];
+        const std::vector<cd>& S = c->blocks.mat[k];
         for (int I = 0; I < si.nt[k]; ++I)
             for (int J = 0; J <= I; ++J) {
                 const long long t = si.tbase[k] + (long long)I * (I + 1) / 2 + J;
@@ -203,9 +216,10 @@ int build_sym(abc_ctx* c) {
                     for (int col = 0; col < SYM_T; ++col) {
                         const int cc = J * SYM_T + col;
                         if (cc >= m) break;
-                        const cd v = S[(size_t)row * m + cc];   // column-major within the tile
-                        dst[2 * (col * SYM_T + r)] = (float)v.real();
-                        dst[2 * (col * SYM_T + r) + 1] = (float)v.imag();
+                        const cd v = S[(size_t)row * m + cc];
+                        const int q = abc::dev::sym_pack_index(r, col);
+                        dst[2 * q] = (float)v.real();
+                        dst[2 * q + 1] = (float)v.imag();
                     }
                 }
             }
@@ -263,6 +277,18 @@ int build_sym(abc_ctx* c) {
     c->si = si;
     c->sym_grid = G;
     c->sym_tiles_n = NT;
+    c->l2_keep_tiles = 0;
+    abc::dev::SymGather& sg = c->sym_gather;
+    sg.adapted_cls = c->adapted_cls.as<int>();
+    sg.rowseg = c->sym_rowseg.as<int2>();
+    sg.rowpart = c->sym_rowpart.as<float2>();
+    sg.colpart = c->sym_colpart.as<float2>();
+    for (int k = 0; k < nc; ++k) {
+        for (int e = 0; e < 3; ++e) sg.moff[k][e] = si.moff[k][e];
+        sg.tbase[k] = si.tbase[k];
+        sg.rbase[k] = si.rbase[k];
+        sg.nt[k] = si.nt[k];
+    }
     c->sym = true;
     return ABC_OK;
 }
@@ -280,18 +306,20 @@ int check_device_flag(abc_ctx* c, cudaStream_t s) {
     return ABC_OK;
 }
 
+// The boundary contraction t = S x (conj: conj(S) x).  Returns true when it ran on
+// the symmetric tiles, whose result stays as partial sums that the back transform
+// gathers (c->sym_gather); otherwise t holds the result.
 template <typename T>
-void contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaStream_t s) {
+bool contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaStream_t s) {
     typedef typename dev::C2<T>::t V;
     const int n = c->geo.n_gamma;
+    bool gathered = false;
     prof_begin(c, ABC_KERNEL_CONTRACTION, s);
     if (n_orb == 1 && sizeof(T) == 4 && c->sym) {
         dev::sym_gemv_tiles<<<c->sym_grid, dev::SYM_THREADS, dev::SYM_SMEM, s>>>(
             c->si, c->sym_tiles.as<float2>(), c->sym_seg.as<int4>(), c->sym_cta.as<int>(), (const float2*)x,
             c->sym_rowpart.as<float2>(), c->sym_colpart.as<float2>(), conj, c->l2_keep_tiles, c->err_flag.as<int>());
-        dev::sym_reduce<<<nblk(8 * c->si.obase[c->si.nclass], 256), 256, 0, s>>>(
-            c->si, c->sym_rowseg.as<int2>(), c->sym_rowpart.as<float2>(), c->sym_colpart.as<float2>(), (float2*)t);
-        c->launches += 1;
+        gathered = true;
     } else if (n_orb == 1) {
         dev::gemv_blocks<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(c->bi, n, c->mat.as<V>(),
                                                                           (const V*)x, (V*)t, conj);
@@ -301,33 +329,66 @@ void contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
                                                                   (V*)t, conj, c->tile_blk.as<int>(), c->tile_row.as<int>());
     }
     prof_end(c, ABC_KERNEL_CONTRACTION, s);
+    return gathered;
 }
 
-// One Horner stage: out = y + cdt * L(w).
+// Back transform of a stage, reading t directly or gathering it.
+template <typename T, int MODE>
+void back(abc_ctx* c, bool gathered, int n_orb, T s1, T a_coef, const void* y_f, void* out, void* acc, T cdt,
+          cudaStream_t s) {
+    typedef typename dev::C2<T>::t Vc;
+    const dev::CellTab<T> ct = cell_tab<T>(c);
+    const unsigned nbk = cell_blocks(c, n_orb);
+    if constexpr (sizeof(T) == 4) {
+        if (gathered) {
+            dev::bnd_back<T, MODE, true><<<nbk, 128, 0, s>>>(ct, n_orb, s1, a_coef, c->hat_phi.as<Vc>(),
+                                                             c->hat_f.as<Vc>(), nullptr, c->sym_gather,
+                                                             (const Vc*)y_f, (Vc*)out, (Vc*)acc, cdt);
+            return;
+        }
+    }
+    dev::bnd_back<T, MODE, false><<<nbk, 128, 0, s>>>(ct, n_orb, s1, a_coef, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(),
+                                                      c->tvec.as<Vc>(), c->sym_gather, (const Vc*)y_f, (Vc*)out,
+                                                      (Vc*)acc, cdt);
+}
+
+// One Horner stage: out = y + cdt * L(w).  For order 1 the interior part (stencil,
+// which needs only w) and the boundary chain (which writes only the f part) are
+// independent: the stencil runs on the side stream, forked from and joined back
+// to s (inside a captured graph they become parallel branches).
 template <typename T>
 void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, const void* y_phi, const void* y_f,
            void* o_phi, void* o_f, const T* V, cudaStream_t s) {
     typedef typename dev::C2<T>::t Vc;
     const Geometry& g = c->geo;
     const int order = c->params.order;
-    const long long nb = (long long)g.n_rep * n_orb;
-    const T h = (T)g.h;
-    dev::bnd_forward<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
-        g.n_rep, n_orb, c->nvox, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
-        c->gamma_node.as<int>(), (const Vc*)w_phi, order == 1 ? (const Vc*)w_f : nullptr, c->hat_phi.as<Vc>(),
-        c->hat_f.as<Vc>());
-    contraction<T>(c, order == 1 ? c->hat_f.p : c->hat_phi.p, c->tvec.p, n_orb, 0, s);
+    const dev::CellTab<T> ct = cell_tab<T>(c);
+    const unsigned nbk = cell_blocks(c, n_orb);
+    auto stencil = [&](cudaStream_t ss) {
+        prof_begin(c, ABC_KERNEL_STENCIL, ss);
+        dev::stencil_stage<T><<<nblk(c->nvox * n_orb, 256), 256, 0, ss>>>(
+            g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)w_phi, (const Vc*)y_phi, V,
+            order == 1 ? (const Vc*)w_f : c->cnat.as<Vc>(), (Vc*)o_phi, cdt);
+        prof_end(c, ABC_KERNEL_STENCIL, ss);
+    };
+    if (order == 1) {
+        cudaEventRecord(c->ev_fork, s);
+        cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+        stencil(c->side);
+    }
+    dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
+                                               order == 1 ? (const Vc*)w_f : nullptr, c->hat_phi.as<Vc>(),
+                                               c->hat_f.as<Vc>(), nullptr, (T)0);
+    const bool gathered = contraction<T>(c, order == 1 ? c->hat_f.p : c->hat_phi.p, c->tvec.p, n_orb, 0, s);
     const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
-    dev::bnd_back<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
-        order, g.n_rep, n_orb, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
-        c->rep_c.as<int>(), (T)c->blocks.s, a_coef, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->tvec.as<Vc>(),
-        (const Vc*)y_f, order == 1 ? (Vc*)o_f : c->cnat.as<Vc>(), cdt);
-    prof_begin(c, ABC_KERNEL_STENCIL, s);
-    dev::stencil_stage<T><<<nblk(c->nvox * n_orb, 256), 256, 0, s>>>(
-        g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)w_phi, (const Vc*)y_phi, V,
-        order == 1 ? (const Vc*)w_f : c->cnat.as<Vc>(), (Vc*)o_phi, cdt);
-    prof_end(c, ABC_KERNEL_STENCIL, s);
-    (void)h;
+    if (order == 1) {
+        back<T, 0>(c, gathered, n_orb, (T)c->blocks.s, a_coef, y_f, o_f, nullptr, cdt, s);
+        cudaEventRecord(c->ev_join, c->side);
+        cudaStreamWaitEvent(s, c->ev_join, 0);
+    } else {
+        back<T, 1>(c, gathered, n_orb, (T)0, (T)0, nullptr, c->cnat.p, nullptr, (T)0, s);
+        stencil(s);
+    }
 }
 
 // One time step (4 Horner stages) in place on (psi, aux).
@@ -434,6 +495,9 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     CUDA_TRY(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming));
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     *out = c.release();
     return ABC_OK;
 }
@@ -478,7 +542,7 @@ int run_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double 
         if (c->prec == ABC_FP64) diag_impl<double>(c, psi, aux, V, n_orb, mf, o, ss);
         else diag_impl<float>(c, psi, aux, V, n_orb, mf, o, ss);
     };
-    const bool use_graph = !c->profiling && nsteps > 1;
+    const bool use_graph = !c->profiling && nsteps >= 1;
     if (use_graph) {
         abc_ctx::Key k{psi, aux, V, n_orb, dt, mf != nullptr, mf ? mf->a : 0, mf ? mf->b : 0, mf ? mf->alpha : 0, s};
         const bool same = c->gexec && !std::memcmp(&k, &c->key, sizeof(k));
@@ -578,26 +642,19 @@ void adj_stage(abc_ctx* c, int n_orb, T cdt, const void* a_phi, const void* a_f,
                void* anew_phi, void* anew_f, const T* V, cudaStream_t s) {
     typedef typename dev::C2<T>::t Vc;
     const Geometry& g = c->geo;
-    const long long nb = (long long)g.n_rep * n_orb;
     const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
+    const dev::CellTab<T> ct = cell_tab<T>(c);
+    const unsigned nbk = cell_blocks(c, n_orb);
     if (c->params.order == 1) {
-        dev::bnd_forward_adj<T><<<nblk(nb, 128), 128, 0, s>>>(
-            g.n_rep, n_orb, c->nvox, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
-            c->rep_c.as<int>(), a_coef, c->gamma_node.as<int>(), (const Vc*)a_phi, (const Vc*)a_f,
-            c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->cnat.as<Vc>());
-        contraction<T>(c, c->cnat.p, c->tvec.p, n_orb, 1, s);
-        dev::bnd_back_adj<T><<<nblk(nb, 128), 128, 0, s>>>(
-            g.n_rep, n_orb, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(), (T)c->blocks.s,
-            c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->tvec.as<Vc>(), (Vc*)acc_f, (Vc*)anew_f, cdt);
+        dev::bnd_forward<T, 1><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)a_phi, (const Vc*)a_f,
+                                                   c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->cnat.as<Vc>(), a_coef);
+        const bool gathered = contraction<T>(c, c->cnat.p, c->tvec.p, n_orb, 1, s);
+        back<T, 2>(c, gathered, n_orb, (T)c->blocks.s, a_coef, nullptr, anew_f, acc_f, cdt, s);
     } else {
-        dev::bnd_forward<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
-            g.n_rep, n_orb, c->nvox, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
-            c->gamma_node.as<int>(), (const Vc*)a_phi, nullptr, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>());
-        contraction<T>(c, c->hat_phi.p, c->tvec.p, n_orb, 1, s);
-        dev::bnd_back<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
-            0, g.n_rep, n_orb, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
-            c->rep_c.as<int>(), (T)c->blocks.s, a_coef, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->tvec.as<Vc>(),
-            nullptr, c->cnat.as<Vc>(), (T)0);
+        dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)a_phi, nullptr, c->hat_phi.as<Vc>(),
+                                                   c->hat_f.as<Vc>(), nullptr, (T)0);
+        const bool gathered = contraction<T>(c, c->hat_phi.p, c->tvec.p, n_orb, 1, s);
+        back<T, 1>(c, gathered, n_orb, (T)0, (T)0, nullptr, c->cnat.p, nullptr, (T)0, s);
     }
     dev::stencil_adj<T><<<nblk(c->nvox * n_orb, 256), 256, 0, s>>>(
         c->params.order, g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), a_coef, (const Vc*)a_phi, V,
@@ -739,7 +796,7 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
         if (ctx->sym && n_orb == 1) {
             entries = (double)ctx->sym_tiles_n * abc::dev::SYM_T * abc::dev::SYM_T;   // stored tiles, read once
         } else {
-            for (int p = 0; p < 8; ++p) entries += (double)ctx->geo.m[p] * ctx->geo.m[p];
+            for (int p = 0; p < ctx->bi.n; ++p) entries += (double)ctx->bi.m[p] * ctx->bi.m[p];
         }
         *bytes = entries * cb + 2.0 * ctx->geo.n_gamma * n_orb * cb;
     } else if (kernel == ABC_KERNEL_STENCIL) {
@@ -782,5 +839,8 @@ extern "C" void abc_destroy(abc_ctx* ctx) {
     if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
     if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
     if (ctx->own) cudaStreamDestroy(ctx->own);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     delete ctx;
 }

@@ -50,8 +50,10 @@ struct abc_ctx {
     long long nvox = 0;
     abc::dev::BlockInfo bi;
     // device tables
-    abc::DevBuf rep_gamma, rep_adapted, rep_stab, rep_c, gamma_node, gamma_c;
-    abc::DevBuf mat;             // parity blocks in device format
+    abc::DevBuf gamma_c;
+    abc::DevBuf cell_out, cell_type, cell_coef_f, cell_coef_bt, cell_c, cell_gi, cell_node, cell_wr,
+        adapted_cls;                                          // boundary transform tables
+    abc::DevBuf mat;             // irreducible-class blocks in device format
     abc::DevBuf tile_blk, tile_row;   // row tiles (block, first row) of the multi-orbital contraction
     int n_tiles = 0;
     // workspace
@@ -59,6 +61,9 @@ struct abc_ctx {
     abc::DevBuf host_psi, host_aux, host_V;   // device copies for abc_run_host
     cudaStream_t own = nullptr;
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    // order 1: the stencil of a stage runs on `side`, concurrently with the boundary chain
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // graph cache
     cudaGraphExec_t gexec = nullptr;
     struct Key { const void *psi, *aux, *V; int n_orb; double dt; int mf; double a, b, alpha; cudaStream_t s; } key{};
@@ -68,8 +73,9 @@ struct abc_ctx {
     int sym_grid = 0;
     long long sym_tiles_n = 0;
     long long l2_keep_tiles = 0;     // tiles streamed with evict_last (tuning)
-    double sym_balance = 0.0;        // extra work weight per right-hand side in the tile partition (tuning)
+    double sym_balance = 1.0;        // work weight per right-hand side in the tile partition
     abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, err_flag;
+    abc::dev::SymGather sym_gather{};   // partial-sum view for the back transform
     // launch accounting
     long long launches = 0;
     long long graph_kernels = 0;
@@ -78,3 +84,24 @@ struct abc_ctx {
     abc::ProfileSlot prof[2];
 };
 
+namespace abc {
+// Kernel view of the context's boundary transform tables.
+template <typename T>
+inline dev::CellTab<T> cell_tab(const abc_ctx* c) {
+    dev::CellTab<T> t;
+    t.n_cells = c->geo.n_cells;
+    t.out = c->cell_out.as<int>();
+    t.type = c->cell_type.as<int>();
+    t.coef_f = c->cell_coef_f.as<T>();
+    t.coef_bt = c->cell_coef_bt.as<T>();
+    t.cell_c = c->cell_c.as<int>();
+    t.gi = c->cell_gi.as<int>();
+    t.node = c->cell_node.as<int>();
+    t.wr = c->cell_wr.as<int>();
+    return t;
+}
+// Blocks (of 128 threads) of the boundary transforms for n_orb orbitals.
+inline unsigned cell_blocks(const abc_ctx* c, int n_orb) {
+    return (unsigned)(((long long)c->geo.n_cells * n_orb + 1) / 2);
+}
+}  // namespace abc

@@ -45,23 +45,71 @@ struct Geometry {
     // pi^{-1}(r) in block b).  base_of[p] is the block that stores the matrix of p.
     bool cube = false;
     int base_of[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+    int perm_of[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // index in kAxisPerms with pi(base_of[p]) = p
+
+    // Irreducible blocks.  Inside stored block b the axis permutations that fix b
+    // (all six for b = 0 and 7, one transposition for the others, none on a
+    // non-cube) permute the representatives and commute with K, so in a real
+    // orthogonal basis adapted to their irreducible representations rho the block
+    // splits again (Schur's lemma): one m x m matrix per (b, rho), the same for
+    // every component of rho.  A class applies it to R = (parities of b's class) x
+    // dim(rho) right-hand sides stored at adapted offsets moff[0..R-1] (index
+    // member * dim + component).  Columns of the basis change W_b: for component a
+    // and copy c, up to 6 (local index in block b, weight) pairs at
+    // [(a * m + c) * 6 + i]; unused pairs have local index -1.
+    struct IrrepClass {
+        int base = 0, irrep = 0, dim = 1, m = 0, R = 0;
+        int moff[3] = {0, 0, 0};
+        std::vector<int> col_l;
+        std::vector<double> col_w;
+    };
+    std::vector<IrrepClass> cls;
+    // Cells: orbits of representatives under all axis permutations (cubes) or single
+    // representatives.  The device transforms run cell by cell: parity components
+    // of the cell's representatives (slots) in, adapted values out.
+    int n_cells = 0;
+    std::vector<int> cell_rep;      // [n_cells][8] representative per slot, -1 unused
+    std::vector<int> cell_out;      // [n_cells][8 outputs][8 parities] adapted index or -1
+    std::vector<int> cell_type;     // [n_cells][8 parities] coefficient matrix id
+    std::vector<double> coef;       // [types][8 outputs][8 slots]: output = sum coef * slot value
+    std::vector<int> cell_c;        // exterior-neighbour count of the cell's nodes (1..3)
+    // Flattened tables of the device transforms, thread t = 8 slot + g of a cell:
+    std::vector<int> cell_gi;       // [n_cells][64] Gamma index of reflection g of the slot, -1 unused
+    std::vector<int> cell_node;     // [n_cells][64] its linear node index, -1 unused
+    std::vector<int> cell_wr;       // [n_cells][64] Gamma index if lane g is the lowest lane of the
+                                    //   slot reaching that node (the one that writes it), else -1
+    // coefficient matrices with the parity-basis scale of each slot folded in:
+    std::vector<double> coef_f;     // [types][8 o][8 s] = coef[o][s] / sqrt(8 |H_s|)   (forward)
+    std::vector<double> coef_bt;    // [types][8 s][8 o] = coef[o][s] * sqrt(|H_s| / 8)  (back, transposed)
+    std::vector<int> adapted_cls;   // [n_gamma] class | (right-hand side << 8) of each adapted index
 };
+
+// Axis permutations: (pi . x)[kAxisPerms[pi][a]] = x[a]; the same map moves parity bit a
+// to bit kAxisPerms[pi][a].  Entry 0 is the identity.
+extern const int kAxisPerms[6][3];
+
+// Irreducible blocks and cells of a geometry whose parity blocks are built.
+int build_irreps(Geometry& g, std::string& err);
 
 // Closed-form Gamma index of a boundary node (ascending linear order).
 int gamma_index_closed(int i, int j, int k, int nx, int ny, int nz);
 
 int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& err);
 
-// FP64 coefficient blocks in the parity-adapted basis (row-major m_p x m_p each).
-//   order 0: mat[p] = M_p = K_p(s0)
-//   order 1: mat[p] = S_p = K_p(s1)^{-1}; B = s1 I - A S with A diagonal
-// Both are complex symmetric.  Only blocks with base_of[p] == p are filled; the
-// others equal their base block.
+// FP64 coefficient blocks in the symmetry-adapted basis, one per irreducible class
+// (row-major m x m each):
+//   order 0: mat[k] = M_k = K_k(s0)
+//   order 1: mat[k] = S_k = K_k(s1)^{-1}; B = s1 I - A S with A diagonal
+// Both are complex symmetric.
 struct Blocks {
     int order = 0;
     double s = 0.0;
-    std::vector<cd> mat[8];
+    std::vector<std::vector<cd>> mat;
 };
+
+// Dense block-b matrix (row-major m_b x m_b, parity-adapted numbering) from the
+// irreducible blocks whose base is b: sum over classes and components of W blk W^T.
+void expand_base_block(const Geometry& g, int b, const std::vector<std::vector<cd>>& blk, std::vector<cd>& out);
 
 int compute_blocks(const Geometry& g, int order, double s, Blocks& b, std::string& err);
 

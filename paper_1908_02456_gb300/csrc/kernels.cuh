@@ -17,12 +17,49 @@ template <typename T> __device__ __forceinline__ typename C2<T>::t mk(T re, T im
     typename C2<T>::t v; v.x = re; v.y = im; return v;
 }
 
-// Block structure of the parity-adapted boundary matrices (kernel parameter).
+// Block structure of the symmetry-adapted boundary matrices (kernel parameter).
+// Entry e is one right-hand side of one irreducible class: the class's matrix
+// (m x m at mat_off, row stride ld) maps adapted indices [off, off + m) to the same
+// range.  Entries of one class share mat_off.
+constexpr int MAX_ENTRIES = 24;
 struct BlockInfo {
-    int m[8];               // block sizes
-    int off[8];             // first adapted index of each block
-    int ld[8];              // row stride (complex elements) of each block
-    long long mat_off[8];   // first element of each block in the matrix buffer
+    int n;                            // number of entries
+    int m[MAX_ENTRIES];               // block sizes
+    int off[MAX_ENTRIES];             // first adapted index of each entry (ascending)
+    int ld[MAX_ENTRIES];              // row stride (complex elements) of the matrix
+    long long mat_off[MAX_ENTRIES];   // first element of the matrix in the buffer
+};
+
+// Cell tables of the boundary transforms (kernel parameter).  A cell is a set of
+// representatives closed under the axis permutations (one representative on a
+// non-cube); its slots hold the representatives, and for every parity p its
+// adapted outputs are out[o] = sum_s coef[o][s] * (parity-p component of slot s).
+// Thread t = 8 s + g of a cell's group reads entry t of the node tables.
+template <typename T>
+struct CellTab {
+    int n_cells;
+    const int* out;        // [n_cells][8 o][8 p] adapted index or -1
+    const int* type;       // [n_cells][8 p] coefficient matrix id
+    const T* coef_f;       // [types][8 o][8 s] forward coefficients, slot scale folded in
+    const T* coef_bt;      // [types][8 s][8 o] back coefficients (transposed), slot scale folded in
+    const int* cell_c;     // [n_cells] exterior-neighbour count
+    const int* gi;         // [n_cells][64] Gamma index of reflection g of slot s, -1 unused
+    const int* node;       // [n_cells][64] its linear node index
+    const int* wr;         // [n_cells][64] Gamma index written by lane g of slot s, -1 if none
+};
+
+// Partial sums of the tiled one-orbital contraction, gathered by the back transform:
+// t[j] = sum of the row parts of the segments of (class c, tile row I) + the column
+// parts of the tiles (c, K, I), K > I (fixed order).
+struct SymGather {
+    const int* adapted_cls;      // [n_gamma] class | (right-hand side << 8)
+    const int2* rowseg;          // [(class, tile row)] segment range
+    const float2* rowpart;       // [segment][64][3]
+    const float2* colpart;       // [tile][64][3]
+    int moff[16][3];
+    long long tbase[16];
+    int rbase[16];
+    int nt[16];
 };
 
 // Gamma index of a boundary node (ascending linear order, x fastest).
@@ -34,20 +71,6 @@ __device__ __forceinline__ int gamma_index(int i, int j, int k, int nx, int ny, 
     if (j == 0) return base + i;
     if (j == ny - 1) return base + nx + 2 * (ny - 2) + i;
     return base + nx + 2 * (j - 1) + (i == 0 ? 0 : 1);
-}
-
-// In-place 8-point Walsh-Hadamard transform: out[p] = sum_g (-1)^{popcount(p&g)} in[g].
-template <typename V> __device__ __forceinline__ void wht8(V* x) {
-#pragma unroll
-    for (int bit = 1; bit < 8; bit <<= 1) {
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            if (g & bit) continue;
-            const V a = x[g], b = x[g | bit];
-            x[g].x = a.x + b.x; x[g].y = a.y + b.y;
-            x[g | bit].x = a.x - b.x; x[g | bit].y = a.y - b.y;
-        }
-    }
 }
 
 // 8-point Walsh-Hadamard transform across the 8 lanes of an aligned lane group:
@@ -64,101 +87,188 @@ template <typename V> __device__ __forceinline__ V wht8_lanes(V v, int g) {
 }
 
 // --------------------------------------------------------------------------
-// Boundary: natural Gamma order -> parity-adapted order (E, then U^T)
+// Boundary: natural Gamma order <-> symmetry-adapted order
 // --------------------------------------------------------------------------
-// Eight lanes per (representative r, orbital j): lane g gathers the value at the
-// reflection g.r (phi at the node, and f at its Gamma index for order 1); the lane
-// group transforms them and lane p stores parity component p (scale 1/sqrt(8|H_r|))
-// when it exists for r.  Launch with 8 * n_rep * n_orb threads, blockDim % 32 == 0.
-template <typename T>
-__global__ void bnd_forward(int n_rep, int n_orb, long long nvox, const int* __restrict__ rep_gamma,
-                            const int* __restrict__ rep_adapted, const int* __restrict__ rep_stab,
-                            const int* __restrict__ gamma_node,
-                            const typename C2<T>::t* __restrict__ w_phi,
-                            const typename C2<T>::t* __restrict__ w_f,
-                            typename C2<T>::t* __restrict__ hat_phi, typename C2<T>::t* __restrict__ hat_f) {
+// Launch with 128 threads per block: two groups of 64 threads, one group per (cell,
+// orbital j), orbital fastest.  In a group thread t = 8 s + g; every table load of a
+// thread is issued before its first data load.
+//
+// Forward: thread (s, g) gathers the value at the reflection g of slot s's
+// representative; the 8-lane group of the slot transforms them (Walsh-Hadamard),
+// which leaves parity component g in lane g (unscaled); after the exchange through
+// shared memory thread (o, p) = (s, g) forms adapted output o of parity p with the
+// scaled coefficients.
+//   MODE 0: hat_phi (and hat_f when w_f is given)
+//   MODE 1: hat_phi, hat_f and u = (+i a_coef c) hat_f  (order-1 adjoint, A^H f)
+template <typename T, int MODE>
+__global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, long long nvox,
+                                                   const typename C2<T>::t* __restrict__ w_phi,
+                                                   const typename C2<T>::t* __restrict__ w_f,
+                                                   typename C2<T>::t* __restrict__ hat_phi,
+                                                   typename C2<T>::t* __restrict__ hat_f,
+                                                   typename C2<T>::t* __restrict__ u, T a_coef) {
     typedef typename C2<T>::t V;
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long idx = gid >> 3;
-    const int g = (int)(gid & 7);
-    const bool live = idx < (long long)n_rep * n_orb;
-    const int j = live ? (int)(idx % n_orb) : 0;
-    const int r = live ? (int)(idx / n_orb) : 0;
+    __shared__ V sp[2][8][8], sf[2][8][8];     // [group][slot][parity]
+    const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const long long gidx = (long long)blockIdx.x * 2 + grp;
+    const bool live = gidx < (long long)ct.n_cells * n_orb;
+    const int j = live ? (int)(gidx % n_orb) : 0;
+    const int cell = live ? (int)(gidx / n_orb) : 0;
+    const int s = t >> 3, g = t & 7;
+    const int gi = live ? ct.gi[cell * 64 + t] : -1;
+    const int node = live ? ct.node[cell * 64 + t] : 0;
+    const int jj = live ? ct.out[cell * 64 + t] : -1;          // output o = s of parity p = g
+    const int ty = live ? ct.type[cell * 8 + g] : 0;
     V xp = mk<T>(0, 0), xf = mk<T>(0, 0);
-    if (live) {
-        const int gi = rep_gamma[r * 8 + g];
-        xp = w_phi[(long long)j * nvox + gamma_node[gi]];
+    if (gi >= 0) {
+        xp = w_phi[(long long)j * nvox + node];
         if (w_f) xf = w_f[(long long)gi * n_orb + j];
     }
+    T cf[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cf[q] = jj >= 0 ? ct.coef_f[(long long)ty * 64 + s * 8 + q] : (T)0;
+    const T c_cell = (MODE == 1 && live) ? (T)ct.cell_c[cell] : (T)0;
     xp = wht8_lanes(xp, g);
     if (w_f) xf = wht8_lanes(xf, g);
-    if (!live) return;
-    const int q = rep_adapted[r * 8 + g];
-    if (q < 0) return;
-    const T sc = (T)rsqrt(8.0 * rep_stab[r]);
-    hat_phi[(long long)q * n_orb + j] = mk<T>(sc * xp.x, sc * xp.y);
-    if (w_f) hat_f[(long long)q * n_orb + j] = mk<T>(sc * xf.x, sc * xf.y);
+    sp[grp][s][g] = xp;
+    sf[grp][s][g] = xf;
+    __syncthreads();
+    if (jj < 0) return;
+    V ap = mk<T>(0, 0), af = mk<T>(0, 0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        ap.x += cf[q] * sp[grp][q][g].x; ap.y += cf[q] * sp[grp][q][g].y;
+        af.x += cf[q] * sf[grp][q][g].x; af.y += cf[q] * sf[grp][q][g].y;
+    }
+    const long long e = (long long)jj * n_orb + j;
+    hat_phi[e] = ap;
+    if (w_f) hat_f[e] = af;
+    if (MODE == 1) {
+        const T ac = a_coef * c_cell;
+        u[e] = mk<T>(-ac * af.y, ac * af.x);
+    }
 }
 
-// --------------------------------------------------------------------------
-// Boundary: parity-adapted -> natural order, with the order-0 / order-1 epilogue
-// --------------------------------------------------------------------------
-// order 1:  g_hat = s1 f_hat + a_r (phi_hat - t),  a_r = -i c_r / (4 h^4)
-//           (this is B f + A E phi with B = s1 I - A S, t = S f_hat), then
-//           out_f = y_f + cdt * U g_hat
-// order 0:  out_c = U t  (t = M phi_hat), the natural-order E^T M E phi term
-// Eight lanes per (r, j): lane p forms parity component p, the group transforms
-// back, lane g writes the value of reflection g.r.  Nodes fixed by a reflection
-// appear in several lanes; only the lowest such lane writes (it alone reads y_f
-// there, so the update in place is race-free).
-template <typename T>
-__global__ void bnd_back(int order, int n_rep, int n_orb, const int* __restrict__ rep_gamma,
-                         const int* __restrict__ rep_adapted, const int* __restrict__ rep_stab,
-                         const int* __restrict__ rep_c, T s1, T a_coef,
-                         const typename C2<T>::t* __restrict__ hat_phi,
-                         const typename C2<T>::t* __restrict__ hat_f, const typename C2<T>::t* __restrict__ t,
-                         const typename C2<T>::t* y_f, typename C2<T>::t* out, T cdt) {
-    typedef typename C2<T>::t V;
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long idx = gid >> 3;
-    const int g = (int)(gid & 7);
-    const bool live = idx < (long long)n_rep * n_orb;
-    const int j = live ? (int)(idx % n_orb) : 0;
-    const int r = live ? (int)(idx / n_orb) : 0;
-    V x = mk<T>(0, 0);
-    int gi = -1;
-    if (live) {
-        gi = rep_gamma[r * 8 + g];
-        const int q = rep_adapted[r * 8 + g];
-        if (q >= 0) {
-            const long long e = (long long)q * n_orb + j;
-            const V tv = t[e];
-            if (order == 1) {
-                const T a = a_coef * (T)rep_c[r];             // a_r = -i * a
-                const V fv = hat_f[e], pv = hat_phi[e];
-                const T dr = pv.x - tv.x, di = pv.y - tv.y;
-                // s1 f + (-i a)(d) = (s1 f.x + a d.y, s1 f.y - a d.x)
-                x = mk<T>(s1 * fv.x + a * di, s1 * fv.y - a * dr);
-            } else {
-                x = tv;
-            }
+// t[jj] from the partial sums of the tiled contraction (see SymGather).  The column
+// parts are read eight at a time into independent accumulators, so their loads are
+// in flight together; the sums are combined in a fixed order.
+__device__ __forceinline__ float2 sym_gather(const SymGather& sg, int jj) {
+    const int ck = sg.adapted_cls[jj];
+    const int c = ck & 255, k = ck >> 8;
+    const int row = jj - sg.moff[c][k], I = row >> 6, r = row & 63;
+    const int nt = sg.nt[c];
+    const int2 rs = sg.rowseg[sg.rbase[c] + I];
+    float2 acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int q = rs.x; q < rs.y; ++q) {
+        const float2 v = sg.rowpart[((size_t)q * 64 + r) * 3 + k];
+        acc[0].x += v.x;
+        acc[0].y += v.y;
+    }
+    // tile (K, I) = tbase + K (K + 1) / 2 + I for K = I + 1 .. nt - 1
+    const long long base = sg.tbase[c] + I;
+    for (int K0 = I + 1; K0 < nt; K0 += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int K = K0 + q;
+            v[q] = K < nt ? sg.colpart[((size_t)(base + (long long)K * (K + 1) / 2) * 64 + r) * 3 + k]
+                          : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            acc[q].x += v[q].x;
+            acc[q].y += v[q].y;
         }
     }
-    x = wht8_lanes(x, g);
-    bool first = true;
 #pragma unroll
-    for (int bit = 1; bit < 8; bit <<= 1) {
-        const int o = __shfl_xor_sync(0xffffffffu, gi, bit);
-        if ((g & bit) && o == gi) first = false;
+    for (int q = 1; q < 8; ++q) {
+        acc[0].x += acc[q].x;
+        acc[0].y += acc[q].y;
     }
-    if (!live || !first) return;
-    const T sc = (T)sqrt(rep_stab[r] / 8.0);
-    const long long e = (long long)gi * n_orb + j;
-    if (order == 1) {
-        const V yv = y_f[e];
-        out[e] = mk<T>(yv.x + cdt * sc * x.x, yv.y + cdt * sc * x.y);
+    return acc[0];
+}
+
+// Back: thread (o, p) = (s, g) forms the adapted value x of output o of parity p:
+//   MODE 0 (order-1 step):    x = s1 f_hat + (-i a)(phi_hat - t),  a = a_coef c
+//                             (B f + A E phi with B = s1 I - A S, t = S f_hat)
+//   MODE 1 (order 0):         x = t  (t = M phi_hat, or conj(M) phi_hat)
+//   MODE 2 (order-1 adjoint): x = s1 f_hat - t + i phi_hat  (t = conj(S) u)
+// with t read from t_in, or gathered from the contraction's partial sums (GATHER);
+// then thread (s, p) undoes the mixing with the scaled transposed coefficients, the
+// slot's 8-lane group transforms back and lane g holds the value v at the
+// reflection g of the slot's representative.  At that node's Gamma index e, the
+// lane that owns the node (table wr) writes:
+//   MODE 0: out[e] = y_f[e] + cdt v      MODE 1: out[e] = v
+//   MODE 2: out[e] = cdt v, acc[e] += cdt v
+// (only the owner reads y_f / acc there, so the update in place is race-free).
+template <typename T, int MODE, bool GATHER>
+__global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, T a_coef,
+                                                const typename C2<T>::t* __restrict__ hat_phi,
+                                                const typename C2<T>::t* __restrict__ hat_f,
+                                                const typename C2<T>::t* __restrict__ t_in, SymGather sg,
+                                                const typename C2<T>::t* y_f, typename C2<T>::t* out,
+                                                typename C2<T>::t* acc, T cdt) {
+    typedef typename C2<T>::t V;
+    __shared__ V sx[2][8][8];                  // [group][output][parity]
+    const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const long long gidx = (long long)blockIdx.x * 2 + grp;
+    const bool live = gidx < (long long)ct.n_cells * n_orb;
+    const int j = live ? (int)(gidx % n_orb) : 0;
+    const int cell = live ? (int)(gidx / n_orb) : 0;
+    const int s = t >> 3, g = t & 7;
+    const int jj = live ? ct.out[cell * 64 + t] : -1;          // output o = s of parity p = g
+    const int ty = live ? ct.type[cell * 8 + g] : 0;
+    const int wr = live ? ct.wr[cell * 64 + t] : -1;
+    const T c_cell = (MODE == 0 && live) ? (T)ct.cell_c[cell] : (T)0;
+    T cf[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) cf[o] = live ? ct.coef_bt[(long long)ty * 64 + s * 8 + o] : (T)0;
+    V yv = mk<T>(0, 0);
+    const long long ew = (long long)(wr >= 0 ? wr : 0) * n_orb + j;
+    if (wr >= 0 && MODE == 0) yv = y_f[ew];
+    if (wr >= 0 && MODE == 2) yv = acc[ew];
+    V x = mk<T>(0, 0);
+    if (jj >= 0) {
+        const long long e = (long long)jj * n_orb + j;
+        V tv;
+        if constexpr (GATHER) {
+            const float2 q = sym_gather(sg, jj);
+            tv = mk<T>((T)q.x, (T)q.y);
+        } else {
+            tv = t_in[e];
+        }
+        if (MODE == 0) {
+            const T a = a_coef * c_cell;
+            const V fv = hat_f[e], pv = hat_phi[e];
+            const T dr = pv.x - tv.x, di = pv.y - tv.y;
+            x = mk<T>(s1 * fv.x + a * di, s1 * fv.y - a * dr);
+        } else if (MODE == 1) {
+            x = tv;
+        } else {
+            const V fv = hat_f[e], pv = hat_phi[e];
+            x = mk<T>(s1 * fv.x - tv.x - pv.y, s1 * fv.y - tv.y + pv.x);
+        }
+    }
+    sx[grp][s][g] = x;
+    __syncthreads();
+    V v = mk<T>(0, 0);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        v.x += cf[o] * sx[grp][o][g].x;
+        v.y += cf[o] * sx[grp][o][g].y;
+    }
+    v = wht8_lanes(v, g);
+    if (wr < 0) return;
+    if (MODE == 0) {
+        out[ew] = mk<T>(yv.x + cdt * v.x, yv.y + cdt * v.y);
+    } else if (MODE == 1) {
+        out[ew] = v;
     } else {
-        out[e] = mk<T>(sc * x.x, sc * x.y);
+        const T nr = cdt * v.x, ni = cdt * v.y;
+        out[ew] = mk<T>(nr, ni);
+        acc[ew] = mk<T>(yv.x + nr, yv.y + ni);
     }
 }
 
@@ -179,8 +289,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __device__ __forceinline__ int find_block(const BlockInfo& bi, int q) {
     int p = 0;
-#pragma unroll
-    for (int k = 1; k < 8; ++k)
+    for (int k = 1; k < bi.n; ++k)
         if (q >= bi.off[k]) p = k;
     return p;
 }
@@ -424,80 +533,6 @@ namespace dev {
 //   order 0: L^H a = i H a_phi + i E^T M^H E a_phi
 //   order 1: L^H (a_phi, a_f) = (i H a_phi + E^T A^H a_f,  i E a_phi + B^H a_f)
 // with A^H = +i diag(c)/(4h^4) and B^H = s1 I - conj(S) A^H (S = K(s1)^{-1} symmetric).
-
-// Natural -> adapted for the adjoint: like bnd_forward, and additionally
-// u = A^H f_hat (per representative: +i a_coef c_r).
-template <typename T>
-__global__ void bnd_forward_adj(int n_rep, int n_orb, long long nvox, const int* __restrict__ rep_gamma,
-                                const int* __restrict__ rep_adapted, const int* __restrict__ rep_stab,
-                                const int* __restrict__ rep_c, T a_coef, const int* __restrict__ gamma_node,
-                                const typename C2<T>::t* __restrict__ a_phi, const typename C2<T>::t* __restrict__ a_f,
-                                typename C2<T>::t* __restrict__ hat_phi, typename C2<T>::t* __restrict__ hat_f,
-                                typename C2<T>::t* __restrict__ u) {
-    typedef typename C2<T>::t V;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)n_rep * n_orb) return;
-    const int j = (int)(idx % n_orb);
-    const int r = (int)(idx / n_orb);
-    const T sc = (T)rsqrt(8.0 * rep_stab[r]);
-    const T ac = a_coef * (T)rep_c[r];
-    V xp[8], xf[8];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-        const int gi = rep_gamma[r * 8 + g];
-        xp[g] = a_phi[(long long)j * nvox + gamma_node[gi]];
-        xf[g] = a_f[(long long)gi * n_orb + j];
-    }
-    wht8(xp);
-    wht8(xf);
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        const int q = rep_adapted[r * 8 + p];
-        if (q < 0) continue;
-        const long long e = (long long)q * n_orb + j;
-        const T fr = sc * xf[p].x, fi = sc * xf[p].y;
-        hat_phi[e] = mk<T>(sc * xp[p].x, sc * xp[p].y);
-        hat_f[e] = mk<T>(fr, fi);
-        u[e] = mk<T>(-ac * fi, ac * fr);          // (+i ac) * f_hat
-    }
-}
-
-// Adapted -> natural for the order-1 adjoint f part:
-//   g_hat = s1 a_f_hat - t + i a_phi_hat,  t = conj(S) u,
-//   anew_f = cdt * U g_hat,  acc_f += anew_f.
-template <typename T>
-__global__ void bnd_back_adj(int n_rep, int n_orb, const int* __restrict__ rep_gamma,
-                             const int* __restrict__ rep_adapted, const int* __restrict__ rep_stab, T s1,
-                             const typename C2<T>::t* __restrict__ hat_phi, const typename C2<T>::t* __restrict__ hat_f,
-                             const typename C2<T>::t* __restrict__ t, typename C2<T>::t* acc_f,
-                             typename C2<T>::t* __restrict__ anew_f, T cdt) {
-    typedef typename C2<T>::t V;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)n_rep * n_orb) return;
-    const int j = (int)(idx % n_orb);
-    const int r = (int)(idx / n_orb);
-    V x[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        const int q = rep_adapted[r * 8 + p];
-        if (q < 0) { x[p] = mk<T>(0, 0); continue; }
-        const long long e = (long long)q * n_orb + j;
-        const V fv = hat_f[e], tv = t[e], pv = hat_phi[e];
-        x[p] = mk<T>(s1 * fv.x - tv.x - pv.y, s1 * fv.y - tv.y + pv.x);
-    }
-    wht8(x);
-    const T sc = (T)sqrt(rep_stab[r] / 8.0);
-    V av[8];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) av[g] = acc_f[(long long)rep_gamma[r * 8 + g] * n_orb + j];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-        const long long e = (long long)rep_gamma[r * 8 + g] * n_orb + j;
-        const T nr = cdt * sc * x[g].x, ni = cdt * sc * x[g].y;
-        anew_f[e] = mk<T>(nr, ni);
-        acc_f[e] = mk<T>(av[g].x + nr, av[g].y + ni);
-    }
-}
 
 // anew_phi = cdt * (i H a_phi + bt),  acc_phi += anew_phi, with the boundary term
 //   order 1: bt = A^H a_f = (+i c_gamma a_coef) a_f[gamma]

@@ -71,7 +71,8 @@ void step_with_scratch(const abc_ctx* c, void* psi, void* aux, const void* V, in
     Vc* tvec = hat_f + aux_n;
     Vc* cnat = tvec + aux_n;
     const int order = c->params.order;
-    const long long nb = (long long)g.n_rep * n_orb;
+    const abc::dev::CellTab<T> ct = abc::cell_tab<T>(c);
+    const unsigned nbk = abc::cell_blocks(c, n_orb);
     const double cs[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
     const void* in_p = psi;
     const void* in_f = aux;
@@ -79,9 +80,9 @@ void step_with_scratch(const abc_ctx* c, void* psi, void* aux, const void* V, in
         void* op = st == 3 ? psi : (void*)Tp[st & 1];
         void* of = st == 3 ? aux : (void*)Tf[st & 1];
         const T cdt = (T)(cs[st] * dt);
-        abc::dev::bnd_forward<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
-            g.n_rep, n_orb, c->nvox, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
-            c->gamma_node.as<int>(), (const Vc*)in_p, order == 1 ? (const Vc*)in_f : nullptr, hat_phi, hat_f);
+        abc::dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)in_p,
+                                                        order == 1 ? (const Vc*)in_f : nullptr, hat_phi, hat_f,
+                                                        nullptr, (T)0);
         const Vc* x = order == 1 ? hat_f : hat_phi;
         if (n_orb == 1) {
             abc::dev::gemv_blocks<T><<<nblk((long long)g.n_gamma * 32, 256), 256, 0, s>>>(c->bi, g.n_gamma,
@@ -92,10 +93,12 @@ void step_with_scratch(const abc_ctx* c, void* psi, void* aux, const void* V, in
                 c->bi, n_orb, c->mat.as<Vc>(), x, tvec, 0, c->tile_blk.as<int>(), c->tile_row.as<int>());
         }
         const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
-        abc::dev::bnd_back<T><<<nblk(8 * nb, 128), 128, 0, s>>>(
-            order, g.n_rep, n_orb, c->rep_gamma.as<int>(), c->rep_adapted.as<int>(), c->rep_stab.as<int>(),
-            c->rep_c.as<int>(), (T)c->blocks.s, a_coef, hat_phi, hat_f, tvec, (const Vc*)aux,
-            order == 1 ? (Vc*)of : cnat, cdt);
+        if (order == 1)
+            abc::dev::bnd_back<T, 0, false><<<nbk, 128, 0, s>>>(ct, n_orb, (T)c->blocks.s, a_coef, hat_phi, hat_f, tvec,
+                                                                c->sym_gather, (const Vc*)aux, (Vc*)of, nullptr, cdt);
+        else
+            abc::dev::bnd_back<T, 1, false><<<nbk, 128, 0, s>>>(ct, n_orb, (T)0, (T)0, hat_phi, hat_f, tvec,
+                                                                c->sym_gather, nullptr, cnat, nullptr, (T)0);
         abc::dev::stencil_stage<T><<<nblk(c->nvox * n_orb, 256), 256, 0, s>>>(
             g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)in_p, (const Vc*)psi, (const T*)V,
             order == 1 ? (const Vc*)in_f : cnat, (Vc*)op, cdt);

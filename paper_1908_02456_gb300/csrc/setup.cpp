@@ -28,6 +28,8 @@ int gamma_index_closed(int i, int j, int k, int nx, int ny, int nz) {
     return base + nx + 2 * (j - 1) + (i == 0 ? 0 : 1);
 }
 
+const int kAxisPerms[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0}, {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
+
 int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& err) {
     if (nx < 3 || ny < 3 || nz < 3) { err = "each axis needs at least 3 interior nodes"; return ABC_ERR_ARG; }
     if (!(h > 0.0)) { err = "grid spacing must be positive"; return ABC_ERR_ARG; }
@@ -104,16 +106,16 @@ int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& e
         for (int r = 0; r < g.n_rep; ++r)
             if (!(p & fixed_mask[r])) loc[(size_t)r * 8 + p] = l++;
     }
-    static const int perms[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0}, {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
     for (int p = 0; p < 8; ++p) {
         const int b = g.base_of[p];
         if (b == p) continue;
         const int* pi = nullptr;          // axis a of the base maps to axis pi[a]
-        for (auto& cand : perms) {
+        for (int k = 0; k < 6; ++k) {
+            const int* cand = kAxisPerms[k];
             int img = 0;
             for (int a = 0; a < 3; ++a)
                 if (b >> a & 1) img |= 1 << cand[a];
-            if (img == p) { pi = cand; break; }
+            if (img == p) { pi = cand; g.perm_of[p] = k; break; }
         }
         if (!pi) { err = "internal: no axis permutation between parity blocks"; return ABC_ERR_ARG; }
         for (int r = 0; r < g.n_rep; ++r) {
@@ -135,7 +137,7 @@ int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& e
             g.rep_adapted[(size_t)r * 8 + p] = q;
             g.adapted_rep[q] = r;
         }
-    return ABC_OK;
+    return build_irreps(g, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,28 +373,53 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
     out = Blocks();
     out.order = order;
     out.s = s;
-    for (int p = 0; p < 8; ++p) {
-        const int m = g.m[p];
-        if (m == 0 || g.base_of[p] != p) continue;
+    out.mat.resize(g.cls.size());
+    for (size_t ki = 0; ki < g.cls.size(); ++ki) {
+        const auto& k = g.cls[ki];
+        const int m = k.m, mb = g.m[k.base];
+        // restrict X_b, Y_b to the class: Xk = W0^T X_b W0 (component 0 columns)
+        std::vector<cd> Xk((size_t)m * m, cd(0.0, 0.0)), Yk((size_t)m * m, cd(0.0, 0.0));
+        const std::vector<cd>& Xb = X[k.base];
+        const std::vector<cd>& Yb = Y[k.base];
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int c2 = 0; c2 < m; ++c2) {
+            const int* lj = &k.col_l[(size_t)c2 * 6];
+            const double* wj = &k.col_w[(size_t)c2 * 6];
+            for (int c = 0; c < m; ++c) {
+                const int* li = &k.col_l[(size_t)c * 6];
+                const double* wi = &k.col_w[(size_t)c * 6];
+                cd xs(0.0, 0.0), ys(0.0, 0.0);
+                for (int j = 0; j < 6; ++j) {
+                    if (lj[j] < 0) continue;
+                    for (int i = 0; i < 6; ++i) {
+                        if (li[i] < 0) continue;
+                        const double w = wi[i] * wj[j];
+                        const size_t e = (size_t)lj[j] * mb + li[i];     // column-major (row li, col lj)
+                        xs += w * Xb[e];
+                        ys += w * Yb[e];
+                    }
+                }
+                Xk[(size_t)c2 * m + c] = xs;
+                Yk[(size_t)c2 * m + c] = ys;
+            }
+        }
         std::vector<int> piv(m);
-        std::vector<cd>& F = order == 0 ? X[p] : Y[p];     // factorised
-        std::vector<cd>& Z = order == 0 ? Y[p] : X[p];     // right-hand sides -> result
+        std::vector<cd>& F = order == 0 ? Xk : Yk;     // factorised
+        std::vector<cd>& Z = order == 0 ? Yk : Xk;     // right-hand sides -> result
         const int info = zgetrf(m, F.data(), m, piv.data());
         if (info) {
-            char buf[128];
-            std::snprintf(buf, sizeof(buf), "eq:eval block %d singular at pivot %d", p, info);
+            char buf[160];
+            std::snprintf(buf, sizeof(buf), "eq:eval block (parity %d, irrep %d) singular at pivot %d", k.base,
+                          k.irrep, info);
             err = buf;
             return ABC_ERR_SINGULAR;
         }
         zgetrs(m, m, F.data(), m, piv.data(), Z.data(), m);
         // result = -Z (column-major) -> symmetrised row-major
-        std::vector<cd>& M = out.mat[p];
+        std::vector<cd>& M = out.mat[ki];
         M.assign((size_t)m * m, cd(0.0, 0.0));
         for (int a = 0; a < m; ++a)
-            for (int b = 0; b < m; ++b)
-                M[(size_t)a * m + b] = -0.5 * (Z[(size_t)b * m + a] + Z[(size_t)a * m + b]);
-        std::vector<cd>().swap(F);
-        std::vector<cd>().swap(Z);
+            for (int c = 0; c < m; ++c) M[(size_t)a * m + c] = -0.5 * (Z[(size_t)c * m + a] + Z[(size_t)a * m + c]);
     }
     return ABC_OK;
 }
@@ -413,21 +440,22 @@ int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::s
     if (which == ABC_MAT_M && b.order != 0) { err = "M exists for order 0 only"; return ABC_ERR_ARG; }
     if (which == ABC_MAT_B && b.order != 1) { err = "B exists for order 1 only"; return ABC_ERR_ARG; }
     if (which != ABC_MAT_K && which != ABC_MAT_M && which != ABC_MAT_B) { err = "unknown matrix"; return ABC_ERR_ARG; }
-    // blocks to expand: M_p (order 0) / K_p = S_p^{-1} (order 1, K) / S_p (order 1, B)
-    std::vector<cd> blk[8];
-    for (int p = 0; p < 8; ++p) {
-        const int m = g.m[p];
-        if (g.base_of[p] != p) continue;
-        blk[p] = b.mat[p];
-        if (m && b.order == 1 && which == ABC_MAT_K) {
-            std::vector<cd> F(b.mat[p]), Z((size_t)m * m, cd(0.0, 0.0));
+    // class blocks to expand: M_k (order 0) / K_k = S_k^{-1} (order 1, K) / S_k (order 1, B)
+    std::vector<std::vector<cd>> cb(b.mat);
+    if (b.order == 1 && which == ABC_MAT_K) {
+        for (size_t ki = 0; ki < g.cls.size(); ++ki) {
+            const int m = g.cls[ki].m;
+            std::vector<cd> F(b.mat[ki]), Z((size_t)m * m, cd(0.0, 0.0));
             std::vector<int> piv(m);
             for (int i = 0; i < m; ++i) Z[(size_t)i * m + i] = 1.0;
             if (zgetrf(m, F.data(), m, piv.data())) { err = "S block singular"; return ABC_ERR_SINGULAR; }
             zgetrs(m, m, F.data(), m, piv.data(), Z.data(), m);  // S symmetric: row/col order irrelevant
-            blk[p] = Z;
+            cb[ki] = Z;
         }
     }
+    std::vector<cd> blk[8];
+    for (int p = 0; p < 8; ++p)
+        if (g.base_of[p] == p && g.m[p]) expand_base_block(g, p, cb, blk[p]);
     const int R = g.n_rep;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int ri = 0; ri < R; ++ri) {

@@ -54,7 +54,8 @@ def test_rejects_bad_arguments(lib):
 
 
 @pytest.mark.parametrize("dims,h,s", [((5, 4, 6), 0.5, 1.0), ((6, 6, 6), 0.4, 0.5), ((7, 5, 9), 0.5, 2.0),
-                                      ((8, 8, 8), 0.5, 1.0)])
+                                      ((8, 8, 8), 0.5, 1.0), ((7, 7, 7), 0.45, 1.0), ((5, 5, 5), 0.5, 3.0),
+                                      ((9, 9, 9), 0.4, 0.7)])
 def test_host_setup_matches_oracle(lib, dims, h, s):
     box = Box(dims, h)
     M = abc.abc_host_matrices(dims, h, 0, s, abc.MAT_M)
