@@ -58,8 +58,13 @@ extern "C" {
 /* arithmetic of the path */
 #define ABC_FP64 0             /* complex128 state, complex128 boundary matrices   */
 #define ABC_C64_FP32 1         /* complex64 state, complex64 matrices, FP32 FMA     */
-#define ABC_C64_SPLIT_BF16 2   /* complex64 state, matrices as bf16 hi + bf16 lo,
-                                  tensor-core contraction with FP32 accumulation    */
+#define ABC_C64_SPLIT_BF16 2   /* reserved (bf16 hi + lo tensor-core form); not
+                                  built: abc_setup returns ABC_ERR_UNSUPPORTED      */
+#define ABC_C64_3XTF32 3       /* complex64 state; for n_orb >= 2 the boundary
+                                  contraction runs on the tensor cores (tcgen05,
+                                  kind::tf32) with the matrices split as TF32 hi +
+                                  lo and three products per term (FP32-level error),
+                                  FP32 accumulation; n_orb = 1 as ABC_C64_FP32      */
 
 /* matrices for abc_get_matrices / abc_host_matrices (dense, natural Gamma order) */
 #define ABC_MAT_K 0            /* K(s) at the context's interpolation point        */
@@ -69,7 +74,8 @@ extern "C" {
 #define ABC_MAT_Q 4            /* order 1: Q = (H_{Gamma,II} H_{II,Gamma})^{-1}     */
 
 typedef struct {
-    int nx, ny, nz;   /* interior nodes per axis, each >= 3                        */
+    int nx, ny, nz;   /* interior nodes per axis, each >= 3, nz <= 65535,
+                         nx * ny * nz < 2^31                                       */
     int radius;       /* stencil radius per axis; this build supports 1 only       */
     double h;         /* grid spacing > 0                                          */
 } abc_grid;
@@ -78,8 +84,9 @@ typedef struct {
     int order;        /* 0 or 1 (rational order m of eq:24)                         */
     double s0;        /* order 0 interpolation point, > 0 (Thm 3.1)                 */
     double s1;        /* order 1 interpolation point, > 0 (Thm 3.2)                 */
-    int precision;    /* ABC_FP64 | ABC_C64_FP32 | ABC_C64_SPLIT_BF16               */
-    int max_orbitals; /* largest n_orb later passed to step/run (sizes workspace)   */
+    int precision;    /* ABC_FP64 | ABC_C64_FP32 | ABC_C64_3XTF32                   */
+    int max_orbitals; /* largest n_orb later passed to step/run (sizes workspace),
+                         1 .. 65535                                                 */
 } abc_params;
 
 typedef struct {
@@ -157,6 +164,10 @@ int abc_host_matrices(const abc_grid* grid, const abc_params* params, int which,
 #define ABC_KERNEL_STENCIL 1       /* fused stencil + potential + Horner stage       */
 int abc_profile_enable(abc_ctx* ctx, int enable);
 int abc_profile_read(abc_ctx* ctx, int kernel, double* ms, long long* launches);
+/* Per-launch durations (milliseconds, launch order) of the same record: writes
+ * min(max_out, launches) values to the host array ms_out and the launch count to
+ * *launches.  The paper has no counterpart (measurement support). */
+int abc_profile_durations(abc_ctx* ctx, int kernel, float* ms_out, long long max_out, long long* launches);
 
 /* Algorithmic bytes of one launch of a kernel for n_orb orbitals (the roofline
  * numerator): boundary matrix bytes + vectors for the contraction; for the stencil

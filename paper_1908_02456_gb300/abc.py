@@ -14,11 +14,11 @@ from typing import Optional, Sequence
 import numpy as np
 
 OK = 0
-FP64, C64_FP32, C64_SPLIT_BF16 = 0, 1, 2
+FP64, C64_FP32, C64_SPLIT_BF16, C64_3XTF32 = 0, 1, 2, 3
 MAT_K, MAT_M, MAT_A, MAT_B, MAT_Q = 0, 1, 2, 3, 4
 KERNEL_CONTRACTION, KERNEL_STENCIL = 0, 1
 TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT = 0, 1
-PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16}
+PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16, "tf32x3": C64_3XTF32}
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libabc.so")
 
@@ -68,6 +68,7 @@ def load():
         "abc_host_matrices": [G, Pm, ctypes.c_int, _P, ctypes.c_size_t],
         "abc_profile_enable": [_P, ctypes.c_int],
         "abc_profile_read": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
+        "abc_profile_durations": [_P, ctypes.c_int, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)],
         "abc_kernel_bytes": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
         "abc_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
         "abc_step_noalloc": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P],
@@ -182,6 +183,13 @@ def abc_profile_read(ctx, kernel: int):
     ms, n = ctypes.c_double(), ctypes.c_longlong()
     _check(load().abc_profile_read(ctx, kernel, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def abc_profile_durations(ctx, kernel: int, max_out: int = 1 << 16) -> np.ndarray:
+    out = np.zeros(max_out, np.float32)
+    n = ctypes.c_longlong()
+    _check(load().abc_profile_durations(ctx, kernel, out.ctypes.data_as(_P), max_out, ctypes.byref(n)))
+    return out[:min(n.value, max_out)].copy()
 
 
 def abc_kernel_bytes(ctx, kernel: int, n_orb: int) -> float:
@@ -310,6 +318,9 @@ class Context:
 
     def profile_read(self, kernel=KERNEL_CONTRACTION):
         return abc_profile_read(self.ctx, kernel)
+
+    def profile_durations(self, kernel=KERNEL_CONTRACTION):
+        return abc_profile_durations(self.ctx, kernel)
 
     def kernel_bytes(self, kernel, n_orb):
         return abc_kernel_bytes(self.ctx, kernel, n_orb)

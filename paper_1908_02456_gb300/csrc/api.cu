@@ -41,7 +41,6 @@ int upload_tables(abc_ctx* c) {
         {&c->cell_gi, g.cell_gi.data(), g.cell_gi.size()},
         {&c->cell_node, g.cell_node.data(), g.cell_node.size()},
         {&c->cell_wr, g.cell_wr.data(), g.cell_wr.size()},
-        {&c->adapted_cls, g.adapted_cls.data(), g.adapted_cls.size()},
     };
     for (auto& e : t) {
         int st = e.b->alloc(e.n * sizeof(int));
@@ -278,18 +277,144 @@ int build_sym(abc_ctx* c) {
     c->sym_grid = G;
     c->sym_tiles_n = NT;
     c->l2_keep_tiles = 0;
+    // gather descriptors of the back transform, indexed like the cell output table
+    std::vector<int4> gdesc((size_t)g.n_cells * 64, make_int4(0, 0, 0, 0));
+    std::vector<int> cls_of(g.n_gamma, -1), rhs_of(g.n_gamma, -1);
+    for (size_t k = 0; k < g.cls.size(); ++k)
+        for (int e = 0; e < g.cls[k].R; ++e)
+            for (int q = 0; q < g.cls[k].m; ++q) {
+                cls_of[g.cls[k].moff[e] + q] = (int)k;
+                rhs_of[g.cls[k].moff[e] + q] = e;
+            }
+    for (size_t i = 0; i < gdesc.size(); ++i) {
+        const int jj = g.cell_out[i];
+        if (jj < 0) continue;
+        const int k = cls_of[jj], e = rhs_of[jj];
+        const int row = jj - si.moff[k][e], I = row / SYM_T, r = row % SYM_T;
+        const int2 rs = rowseg[si.rbase[k] + I];
+        const long long t1 = si.tbase[k] + (long long)(I + 1) * (I + 2) / 2 + I;
+        const int nk = si.nt[k] - 1 - I;
+        gdesc[i] = make_int4((int)(((long long)rs.x * SYM_T + r) * 3 + e), rs.y - rs.x,
+                             nk > 0 ? (int)((t1 * SYM_T + r) * 3 + e) : 0, nk | ((I + 2) << 16));
+    }
+    if ((st = c->sym_gdesc.alloc(gdesc.size() * sizeof(int4)))) return st;
+    CUDA_TRY(cudaMemcpy(c->sym_gdesc.p, gdesc.data(), gdesc.size() * sizeof(int4), cudaMemcpyHostToDevice));
     abc::dev::SymGather& sg = c->sym_gather;
-    sg.adapted_cls = c->adapted_cls.as<int>();
-    sg.rowseg = c->sym_rowseg.as<int2>();
+    sg.desc = c->sym_gdesc.as<int4>();
     sg.rowpart = c->sym_rowpart.as<float2>();
     sg.colpart = c->sym_colpart.as<float2>();
-    for (int k = 0; k < nc; ++k) {
-        for (int e = 0; e < 3; ++e) sg.moff[k][e] = si.moff[k][e];
-        sg.tbase[k] = si.tbase[k];
-        sg.rbase[k] = si.rbase[k];
-        sg.nt[k] = si.nt[k];
-    }
     c->sym = true;
+    return ABC_OK;
+}
+
+// TF32 with round-to-nearest, ties away from zero (the device's cvt.rna.tf32.f32).
+float tf32_rna(float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+// Tensor-core form of the many-orbital contraction: every class block split into
+// TF32 hi / lo planes of its real and imaginary parts, packed per (128-row tile,
+// 16-deep K block) in the shared-memory image of gemm_tc, and the output tiles for
+// every orbital count 1..max_orbitals (largest classes first).
+int build_tc(abc_ctx* c) {
+    using namespace abc::dev;
+    const Geometry& g = c->geo;
+    if ((int)g.cls.size() > SYM_CMAX) return fail(ABC_ERR_ARG, "internal: too many classes");
+    TcInfo info{};
+    long long chunks = 0;
+    for (size_t k = 0; k < g.cls.size(); ++k) {
+        info.m[k] = g.cls[k].m;
+        info.R[k] = g.cls[k].R;
+        for (int e = 0; e < 3; ++e) info.moff[k][e] = g.cls[k].moff[e];
+        info.nkb[k] = (g.cls[k].m + TC_KB - 1) / TC_KB;
+        info.abase[k] = chunks;
+        chunks += (long long)((g.cls[k].m + TC_M - 1) / TC_M) * info.nkb[k];
+    }
+    const size_t per = TC_A_BYTES / 4;
+    std::vector<float> pack((size_t)chunks * per, 0.0f);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long ch = 0; ch < chunks; ++ch) {
+        int k = 0;
+        while (k + 1 < (int)g.cls.size() && ch >= info.abase[k + 1]) ++k;
+        const int m = info.m[k], nkb = info.nkb[k];
+        const long long loc = ch - info.abase[k];
+        const int mt = (int)(loc / nkb), kb = (int)(loc % nkb);
+        const std::vector<cd>& S = c->blocks.mat[k];
+        float* dst = pack.data() + (size_t)ch * per;
+        for (int r = 0; r < TC_M; ++r) {
+            const int row = mt * TC_M + r;
+            if (row >= m) break;
+            for (int q = 0; q < TC_KB; ++q) {
+                const int col = kb * TC_KB + q;
+                if (col >= m) break;
+                const cd v = S[(size_t)row * m + col];
+                const float re = (float)v.real(), im = (float)v.imag();
+                const float rh = tf32_rna(re), ih = tf32_rna(im);
+                const size_t o = tc_core_offset(r, q) / 4;
+                dst[0 * (TC_A_PLANE / 4) + o] = rh;
+                dst[1 * (TC_A_PLANE / 4) + o] = tf32_rna(re - rh);
+                dst[2 * (TC_A_PLANE / 4) + o] = ih;
+                dst[3 * (TC_A_PLANE / 4) + o] = tf32_rna(im - ih);
+            }
+        }
+    }
+    int st;
+    if ((st = c->tc_apack.alloc(pack.size() * sizeof(float)))) return st;
+    CUDA_TRY(cudaMemcpy(c->tc_apack.p, pack.data(), pack.size() * sizeof(float), cudaMemcpyHostToDevice));
+    std::vector<int> order(g.cls.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return g.cls[a].m > g.cls[b].m; });
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    std::vector<TcTile> tiles;
+    std::vector<TcCols> cranges;
+    const int B = c->params.max_orbitals;
+    c->tc_b.assign(B + 1, abc_ctx::TcPlan{});
+    long long max_chunks = 0, max_part = 0;
+    for (int b = 1; b <= B; ++b) {
+        abc_ctx::TcPlan& pl = c->tc_b[b];
+        pl.tile_off = (int)tiles.size();
+        pl.cols_off = (int)cranges.size();
+        int chunks = 0, maxnkb = 1;
+        for (int k : order) {
+            const int cols = g.cls[k].R * b;
+            const int nch = (cols + TC_NMAX - 1) / TC_NMAX;
+            const int w = ((cols + nch - 1) / nch + 15) / 16 * 16;
+            maxnkb = std::max(maxnkb, info.nkb[k]);
+            for (int col0 = 0; col0 < cols; col0 += w) {
+                const int n = std::min(w, (cols - col0 + 15) / 16 * 16);
+                cranges.push_back(TcCols{k, col0, n, chunks});
+                for (int mt = 0; mt * TC_M < g.cls[k].m; ++mt) tiles.push_back(TcTile{k, mt * TC_M, col0, n, chunks});
+                chunks += info.nkb[k];
+            }
+        }
+        pl.tile_cnt = (int)tiles.size() - pl.tile_off;
+        pl.cols_cnt = (int)cranges.size() - pl.cols_off;
+        pl.max_nkb = maxnkb;
+        // enough CTAs for about three per SM; partial sums of the splits are added later
+        pl.nsplit = std::max(1, std::min(TC_MAX_SPLIT, (3 * sms + pl.tile_cnt - 1) / pl.tile_cnt));
+        max_chunks = std::max<long long>(max_chunks, chunks);
+        if (pl.nsplit > 1) max_part = std::max<long long>(max_part, (long long)pl.nsplit * g.n_gamma * b);
+    }
+    if ((st = c->tc_tiles.alloc(tiles.size() * sizeof(TcTile)))) return st;
+    CUDA_TRY(cudaMemcpy(c->tc_tiles.p, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice));
+    if ((st = c->tc_cols.alloc(cranges.size() * sizeof(TcCols)))) return st;
+    CUDA_TRY(cudaMemcpy(c->tc_cols.p, cranges.data(), cranges.size() * sizeof(TcCols), cudaMemcpyHostToDevice));
+    if ((st = c->tc_bpack.alloc((size_t)max_chunks * TC_B_BYTES))) return st;
+    if (max_part && (st = c->tc_part.alloc((size_t)max_part * sizeof(float2)))) return st;
+    if (!c->err_flag.p) {
+        if ((st = c->err_flag.alloc(sizeof(int)))) return st;
+        CUDA_TRY(cudaMemset(c->err_flag.p, 0, sizeof(int)));
+    }
+    CUDA_TRY(cudaFuncSetAttribute(gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    c->tc_sms = sms;
+    c->tci = info;
+    c->tc = true;
     return ABC_OK;
 }
 
@@ -306,50 +431,71 @@ int check_device_flag(abc_ctx* c, cudaStream_t s) {
     return ABC_OK;
 }
 
-// The boundary contraction t = S x (conj: conj(S) x).  Returns true when it ran on
-// the symmetric tiles, whose result stays as partial sums that the back transform
-// gathers (c->sym_gather); otherwise t holds the result.
+// Where a contraction left its result: partial sums for the back transform to
+// gather (packed tiles), or nsplit arrays t + s * stride to add (split-K tensor
+// cores), or plain t (nsplit = 1).
+struct TRes {
+    bool gathered = false;
+    const void* t = nullptr;
+    int nsplit = 1;
+    long long stride = 0;
+};
+
+// The boundary contraction t = S x (conj: conj(S) x).
 template <typename T>
-bool contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaStream_t s) {
+TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaStream_t s) {
     typedef typename dev::C2<T>::t V;
     const int n = c->geo.n_gamma;
-    bool gathered = false;
+    TRes res;
+    res.t = t;
     prof_begin(c, ABC_KERNEL_CONTRACTION, s);
     if (n_orb == 1 && sizeof(T) == 4 && c->sym) {
         dev::sym_gemv_tiles<<<c->sym_grid, dev::SYM_THREADS, dev::SYM_SMEM, s>>>(
             c->si, c->sym_tiles.as<float2>(), c->sym_seg.as<int4>(), c->sym_cta.as<int>(), (const float2*)x,
             c->sym_rowpart.as<float2>(), c->sym_colpart.as<float2>(), conj, c->l2_keep_tiles, c->err_flag.as<int>());
-        gathered = true;
+        res.gathered = true;
     } else if (n_orb == 1) {
         dev::gemv_blocks<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(c->bi, n, c->mat.as<V>(),
                                                                           (const V*)x, (V*)t, conj);
+    } else if (sizeof(T) == 4 && c->tc) {
+        const abc_ctx::TcPlan& pl = c->tc_b[n_orb];
+        dev::pack_x_tc<<<dim3((unsigned)pl.cols_cnt, (unsigned)pl.max_nkb), 128, 0, s>>>(
+            c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off, n_orb, n, (const float2*)x, c->tc_bpack.as<float>());
+        float2* out = pl.nsplit > 1 ? c->tc_part.as<float2>() : (float2*)t;
+        dev::gemm_tc<<<dim3((unsigned)pl.tile_cnt, (unsigned)pl.nsplit), dev::TC_THREADS, dev::TC_SMEM, s>>>(
+            c->tci, c->tc_tiles.as<dev::TcTile>() + pl.tile_off, c->tc_apack.as<float>(), c->tc_bpack.as<float>(),
+            n_orb, n, pl.nsplit, (long long)n * n_orb, out, conj, c->err_flag.as<int>());
+        c->launches += 1;
+        res.t = out;
+        res.nsplit = pl.nsplit;
+        res.stride = (long long)n * n_orb;
     } else {
         dim3 grid(c->n_tiles, (n_orb + 31) / 32);
-        dev::gemm_blocks_simt<T, 32, 32, 16><<<grid, 256, 0, s>>>(c->bi, n_orb, c->mat.as<V>(), (const V*)x,
+        dev::gemm_blocks_simt<T, 32, 32, 16><<<grid, 256, 0, s>>>(c->bi, n_orb, c->geo.n_gamma, c->mat.as<V>(), (const V*)x,
                                                                   (V*)t, conj, c->tile_blk.as<int>(), c->tile_row.as<int>());
     }
     prof_end(c, ABC_KERNEL_CONTRACTION, s);
-    return gathered;
+    return res;
 }
 
-// Back transform of a stage, reading t directly or gathering it.
+// Back transform of a stage, reading t directly, adding split partials, or gathering it.
 template <typename T, int MODE>
-void back(abc_ctx* c, bool gathered, int n_orb, T s1, T a_coef, const void* y_f, void* out, void* acc, T cdt,
+void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f, void* out, void* acc, T cdt,
           cudaStream_t s) {
     typedef typename dev::C2<T>::t Vc;
     const dev::CellTab<T> ct = cell_tab<T>(c);
     const unsigned nbk = cell_blocks(c, n_orb);
     if constexpr (sizeof(T) == 4) {
-        if (gathered) {
+        if (tr.gathered) {
             dev::bnd_back<T, MODE, true><<<nbk, 128, 0, s>>>(ct, n_orb, s1, a_coef, c->hat_phi.as<Vc>(),
-                                                             c->hat_f.as<Vc>(), nullptr, c->sym_gather,
+                                                             c->hat_f.as<Vc>(), nullptr, 1, 0, c->sym_gather,
                                                              (const Vc*)y_f, (Vc*)out, (Vc*)acc, cdt);
             return;
         }
     }
     dev::bnd_back<T, MODE, false><<<nbk, 128, 0, s>>>(ct, n_orb, s1, a_coef, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(),
-                                                      c->tvec.as<Vc>(), c->sym_gather, (const Vc*)y_f, (Vc*)out,
-                                                      (Vc*)acc, cdt);
+                                                      (const Vc*)tr.t, tr.nsplit, tr.stride, c->sym_gather,
+                                                      (const Vc*)y_f, (Vc*)out, (Vc*)acc, cdt);
 }
 
 // One Horner stage: out = y + cdt * L(w).  For order 1 the interior part (stencil,
@@ -366,7 +512,7 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
     const unsigned nbk = cell_blocks(c, n_orb);
     auto stencil = [&](cudaStream_t ss) {
         prof_begin(c, ABC_KERNEL_STENCIL, ss);
-        dev::stencil_stage<T><<<nblk(c->nvox * n_orb, 256), 256, 0, ss>>>(
+        dev::stencil_stage<T><<<stencil_grid(c, n_orb), 256, 0, ss>>>(
             g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)w_phi, (const Vc*)y_phi, V,
             order == 1 ? (const Vc*)w_f : c->cnat.as<Vc>(), (Vc*)o_phi, cdt);
         prof_end(c, ABC_KERNEL_STENCIL, ss);
@@ -379,7 +525,7 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
     dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
                                                order == 1 ? (const Vc*)w_f : nullptr, c->hat_phi.as<Vc>(),
                                                c->hat_f.as<Vc>(), nullptr, (T)0);
-    const bool gathered = contraction<T>(c, order == 1 ? c->hat_f.p : c->hat_phi.p, c->tvec.p, n_orb, 0, s);
+    const TRes gathered = contraction<T>(c, order == 1 ? c->hat_f.p : c->hat_phi.p, c->tvec.p, n_orb, 0, s);
     const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
     if (order == 1) {
         back<T, 0>(c, gathered, n_orb, (T)c->blocks.s, a_coef, y_f, o_f, nullptr, cdt, s);
@@ -491,7 +637,8 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     if ((st = ensure_workspace(c.get()))) return st;
     if ((st = c->diag.alloc(sizeof(double) * 3 * params->max_orbitals))) return st;
     if ((st = build_tiles(c.get()))) return st;
-    if (c->prec == ABC_C64_FP32 && (st = build_sym(c.get()))) return st;
+    if ((c->prec == ABC_C64_FP32 || c->prec == ABC_C64_3XTF32) && (st = build_sym(c.get()))) return st;
+    if (c->prec == ABC_C64_3XTF32 && (st = build_tc(c.get()))) return st;
     CUDA_TRY(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming));
@@ -648,15 +795,15 @@ void adj_stage(abc_ctx* c, int n_orb, T cdt, const void* a_phi, const void* a_f,
     if (c->params.order == 1) {
         dev::bnd_forward<T, 1><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)a_phi, (const Vc*)a_f,
                                                    c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->cnat.as<Vc>(), a_coef);
-        const bool gathered = contraction<T>(c, c->cnat.p, c->tvec.p, n_orb, 1, s);
+        const TRes gathered = contraction<T>(c, c->cnat.p, c->tvec.p, n_orb, 1, s);
         back<T, 2>(c, gathered, n_orb, (T)c->blocks.s, a_coef, nullptr, anew_f, acc_f, cdt, s);
     } else {
         dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)a_phi, nullptr, c->hat_phi.as<Vc>(),
                                                    c->hat_f.as<Vc>(), nullptr, (T)0);
-        const bool gathered = contraction<T>(c, c->hat_phi.p, c->tvec.p, n_orb, 1, s);
+        const TRes gathered = contraction<T>(c, c->hat_phi.p, c->tvec.p, n_orb, 1, s);
         back<T, 1>(c, gathered, n_orb, (T)0, (T)0, nullptr, c->cnat.p, nullptr, (T)0, s);
     }
-    dev::stencil_adj<T><<<nblk(c->nvox * n_orb, 256), 256, 0, s>>>(
+    dev::stencil_adj<T><<<stencil_grid(c, n_orb), 256, 0, s>>>(
         c->params.order, g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), a_coef, (const Vc*)a_phi, V,
         c->params.order == 1 ? (const Vc*)a_f : c->cnat.as<Vc>(), (Vc*)acc_phi, (Vc*)anew_phi, cdt);
     c->launches += 4;
@@ -785,6 +932,20 @@ extern "C" int abc_profile_read(abc_ctx* ctx, int kernel, double* ms, long long*
     }
     *ms = tot;
     *launches = (long long)(ps.used / 2);
+    return ABC_OK;
+}
+
+extern "C" int abc_profile_durations(abc_ctx* ctx, int kernel, float* ms_out, long long max_out,
+                                     long long* launches) {
+    if (!ctx || !launches || kernel < 0 || kernel > 1 || max_out < 0 || (max_out > 0 && !ms_out))
+        return fail(ABC_ERR_ARG, "bad argument");
+    ProfileSlot& ps = ctx->prof[kernel];
+    const long long n = (long long)(ps.used / 2);
+    for (long long i = 0; i < n && i < max_out; ++i) {
+        CUDA_TRY(cudaEventSynchronize(ps.ev[2 * i + 1]));
+        CUDA_TRY(cudaEventElapsedTime(&ms_out[i], ps.ev[2 * i], ps.ev[2 * i + 1]));
+    }
+    *launches = n;
     return ABC_OK;
 }
 

@@ -10,6 +10,7 @@
 #include "internal.h"
 #include "kernels.cuh"
 #include "sym_gemv.cuh"
+#include "gemm_tc.cuh"
 
 namespace abc {
 int fail(int status, const std::string& msg);
@@ -51,8 +52,8 @@ struct abc_ctx {
     abc::dev::BlockInfo bi;
     // device tables
     abc::DevBuf gamma_c;
-    abc::DevBuf cell_out, cell_type, cell_coef_f, cell_coef_bt, cell_c, cell_gi, cell_node, cell_wr,
-        adapted_cls;                                          // boundary transform tables
+    abc::DevBuf cell_out, cell_type, cell_coef_f, cell_coef_bt, cell_c, cell_gi, cell_node, cell_wr;
+                                                              // boundary transform tables
     abc::DevBuf mat;             // irreducible-class blocks in device format
     abc::DevBuf tile_blk, tile_row;   // row tiles (block, first row) of the multi-orbital contraction
     int n_tiles = 0;
@@ -74,8 +75,15 @@ struct abc_ctx {
     long long sym_tiles_n = 0;
     long long l2_keep_tiles = 0;     // tiles streamed with evict_last (tuning)
     double sym_balance = 1.0;        // work weight per right-hand side in the tile partition
-    abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, err_flag;
+    abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
     abc::dev::SymGather sym_gather{};   // partial-sum view for the back transform
+    // many-orbital complex64 contraction on the tensor cores (ABC_C64_3XTF32)
+    bool tc = false;
+    abc::dev::TcInfo tci{};
+    abc::DevBuf tc_apack, tc_tiles, tc_cols, tc_bpack, tc_part;
+    struct TcPlan { int tile_off = 0, tile_cnt = 0, cols_off = 0, cols_cnt = 0, max_nkb = 1, nsplit = 1; };
+    std::vector<TcPlan> tc_b;                    // launch plan of each orbital count b (index b)
+    int tc_sms = 0;
     // launch accounting
     long long launches = 0;
     long long graph_kernels = 0;
@@ -90,6 +98,7 @@ template <typename T>
 inline dev::CellTab<T> cell_tab(const abc_ctx* c) {
     dev::CellTab<T> t;
     t.n_cells = c->geo.n_cells;
+    t.ng = c->geo.n_gamma;
     t.out = c->cell_out.as<int>();
     t.type = c->cell_type.as<int>();
     t.coef_f = c->cell_coef_f.as<T>();
@@ -103,5 +112,12 @@ inline dev::CellTab<T> cell_tab(const abc_ctx* c) {
 // Blocks (of 128 threads) of the boundary transforms for n_orb orbitals.
 inline unsigned cell_blocks(const abc_ctx* c, int n_orb) {
     return (unsigned)(((long long)c->geo.n_cells * n_orb + 1) / 2);
+}
+}  // namespace abc
+
+namespace abc {
+// Grid of the stencil kernels (256 threads per block): x over a z-plane, y = z, z = orbital.
+inline dim3 stencil_grid(const abc_ctx* c, int n_orb) {
+    return dim3((unsigned)((c->geo.nx * c->geo.ny + 255) / 256), (unsigned)c->geo.nz, (unsigned)n_orb);
 }
 }  // namespace abc

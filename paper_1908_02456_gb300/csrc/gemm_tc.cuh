@@ -1,0 +1,287 @@
+// Boundary DtN contraction for many orbitals on the 5th-generation tensor cores
+// (tcgen05, sm_103a), complex64 in / out with FP32-level accuracy.
+//
+// Per irreducible class the contraction is T = S X: S the class's m x m complex
+// block, X the m x (R b) matrix of its R right-hand sides for b orbitals (adapted
+// vectors are orbital-major, so every column of X is contiguous in K).  With
+// S = Sr + i Si and X = Xr + i Xi the kernel accumulates four real products in
+// TMEM, P1 = Sr Xr, P2 = Si Xi, P3 = Si Xr, P4 = Sr Xi, and forms
+//   T = (P1 - P2) + i (P3 + P4)        (conj(S): (P1 + P2) + i (P4 - P3))
+// in the epilogue.  Each real product is 3xTF32: with a = a_hi + a_lo (a_hi the
+// operand rounded to TF32, a_lo the remainder as TF32), a b ~ a_hi b_hi + a_hi b_lo +
+// a_lo b_hi, so 12 MMAs (kind::tf32, M = 128, K = 8) per 8-deep K step.
+//
+// Operand layout in shared memory: K-major, no swizzle, canonical 8-row x 16-byte
+// core matrices (row stride 16 B inside a core matrix, LBO = 128 B between core
+// matrices along K, SBO = 512 B between 8-row groups, 16-deep K blocks).  The host
+// pre-splits and pre-packs S in exactly that image (4 planes Sr_hi, Sr_lo, Si_hi,
+// Si_lo of 128 x 16 FP32 = 32 KB per (class, 128-row tile, K block)); pack_x_tc does
+// the same for X once per contraction (4 planes of N x 16 per (column range, K
+// block)).  gemm_tc computes one 128 x N output tile (N <= 128, a multiple of 16)
+// over one split of the K blocks: one thread streams both chunks of each K block
+// into a 3-stage ring with 1D bulk copies (mbarrier completion), one thread issues
+// the MMAs and frees each slot with tcgen05.commit, and the four accumulators take
+// 4N TMEM columns.  Split-K partials go to separate buffers that the back transform
+// adds in a fixed order.  Every mbarrier wait is bounded: on a timeout the kernel
+// raises the error flag, still waits (bounded) for its own copies and MMAs, frees
+// its TMEM and returns.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sym_gemv.cuh"
+
+namespace abc {
+namespace dev {
+
+constexpr int TC_M = 128;
+constexpr int TC_KB = 16;                          // K elements per pipeline stage
+constexpr int TC_NMAX = 128;
+constexpr int TC_STAGES = 3;
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_A_PLANE = TC_M * TC_KB * 4;  // 8 KB
+constexpr uint32_t TC_A_BYTES = 4 * TC_A_PLANE;    // 32 KB per (tile, K block)
+constexpr uint32_t TC_B_PLANE = TC_NMAX * TC_KB * 4;
+constexpr uint32_t TC_B_BYTES = 4 * TC_B_PLANE;    // 32 KB at N = 128
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + 1024;
+constexpr int TC_MAX_SPLIT = 8;
+constexpr long long TC_WAIT_LIMIT = 1ll << 24;
+
+// Byte offset of element (row r, k) inside a K-major no-swizzle plane of 16-deep
+// K blocks (core matrix (r / 8, k / 4), row r % 8, element k % 4).
+__host__ __device__ inline uint32_t tc_core_offset(int r, int k) {
+    return (uint32_t)((r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+// Output tile: class, first row, first column of the class's R*b columns, width, and
+// the first of its packed X chunks (one per K block).
+struct TcTile {
+    int cls, row0, col0, n, bchunk0;
+};
+// One column range of a class, packed by pack_x_tc into nkb chunks from bchunk0.
+struct TcCols {
+    int cls, col0, n, bchunk0;
+};
+
+struct TcInfo {
+    int m[SYM_CMAX];
+    int R[SYM_CMAX];
+    int moff[SYM_CMAX][3];
+    int nkb[SYM_CMAX];                 // K blocks of the class
+    long long abase[SYM_CMAX];         // first A chunk (32 KB units) of the class
+};
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;   // LBO: next core matrix along K
+    d |= (uint64_t)((512u >> 4) & 0x3FFF) << 32;   // SBO: next 8-row group
+    d |= (uint64_t)1 << 46;                        // descriptor version for tcgen05
+    return d;                                      // base offset 0, no swizzle
+}
+
+// kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t tc_idesc(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t tf32_hi(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// X -> packed TF32 planes (Xr_hi, Xr_lo, Xi_hi, Xi_lo) of every K block of a column
+// range, in the shared-memory image the GEMM copies with one bulk copy per K block.
+// Grid (column ranges, largest nkb), 128 threads; x orbital-major (o * ng + j).
+static __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCols* __restrict__ cols, int n_orb,
+                                                        int ng, const float2* __restrict__ x,
+                                                        float* __restrict__ bpack) {
+    const TcCols cr = cols[blockIdx.x];
+    const int c = cr.cls, kb = blockIdx.y;
+    if (kb >= info.nkb[c]) return;
+    const int m = info.m[c], N = cr.n;
+    unsigned char* B = reinterpret_cast<unsigned char*>(bpack + (size_t)(cr.bchunk0 + kb) * (TC_B_BYTES / 4));
+    for (int it = threadIdx.x; it < N * 4; it += blockDim.x) {
+        const int cc = (it & 7) | ((it >> 5) << 3), q = (it >> 3) & 3;
+        const int col = cr.col0 + cc;
+        const int k = col / n_orb, o = col - k * n_orb;
+        float re[4], im[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int row = kb * TC_KB + 4 * q + e;
+            float2 v = make_float2(0.f, 0.f);
+            if (k < info.R[c] && row < m) v = __ldg(x + (size_t)o * ng + info.moff[c][k] + row);
+            re[e] = v.x;
+            im[e] = v.y;
+        }
+        uint4 rh, rl, ih, il;
+        uint32_t* prh = &rh.x; uint32_t* prl = &rl.x; uint32_t* pih = &ih.x; uint32_t* pil = &il.x;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            prh[e] = tf32_hi(re[e]);
+            prl[e] = tf32_hi(re[e] - __uint_as_float(prh[e]));
+            pih[e] = tf32_hi(im[e]);
+            pil[e] = tf32_hi(im[e] - __uint_as_float(pih[e]));
+        }
+        // planes of a chunk are N * 64 bytes apart (only the tile's N rows are stored)
+        const uint32_t off = tc_core_offset(cc, 4 * q), pl = (uint32_t)N * 64;
+        *reinterpret_cast<uint4*>(B + 0 * pl + off) = rh;
+        *reinterpret_cast<uint4*>(B + 1 * pl + off) = rl;
+        *reinterpret_cast<uint4*>(B + 2 * pl + off) = ih;
+        *reinterpret_cast<uint4*>(B + 3 * pl + off) = il;
+    }
+}
+
+// One 128 x N output tile over the K blocks of split blockIdx.y (of nsplit); writes
+// the split's partial product to out + split * split_stride (x, out orbital-major).
+// Thread 0 streams the A and X chunks into the ring, thread 32 issues the MMAs, and
+// all four warps run the epilogue.
+static __global__ void __launch_bounds__(TC_THREADS, 1)
+gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const float* __restrict__ apack,
+        const float* __restrict__ bpack, int n_orb, int ng, int nsplit, long long split_stride,
+        float2* __restrict__ out, int conj, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char* sA = tc_smem;                                       // [stage][4 planes]
+    unsigned char* sB = tc_smem + (size_t)TC_STAGES * TC_A_BYTES;      // [stage][4 planes]
+    uint64_t* full = reinterpret_cast<uint64_t*>(tc_smem + (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES));
+    uint64_t* empty = full + TC_STAGES;
+    uint64_t* fin = empty + TC_STAGES;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(fin + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const TcTile tile = tiles[blockIdx.x];
+    const int c = tile.cls, N = tile.n, m = info.m[c], nkb = info.nkb[c];
+    const int split = blockIdx.y;
+    const int kb0 = (int)((long long)nkb * split / nsplit), kb1 = (int)((long long)nkb * (split + 1) / nsplit);
+    const int nk = kb1 - kb0;
+    const int ncols = 4 * N <= 32 ? 32 : (4 * N <= 64 ? 64 : (4 * N <= 128 ? 128 : (4 * N <= 256 ? 256 : 512)));
+    const uint32_t b_bytes = (uint32_t)N * 256;
+    if (tid == 0) {
+        for (int i = 0; i < TC_STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(fin, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+    const uint32_t idesc = tc_idesc(N);
+    const float* achunk = apack + (size_t)(info.abase[c] + (long long)(tile.row0 / TC_M) * nkb) * (TC_A_BYTES / 4);
+    const float* bchunk = bpack + (size_t)tile.bchunk0 * (TC_B_BYTES / 4);
+    bool ok = true;
+    if (tid == 0) {
+        // producer
+        for (int i = 0; i < nk; ++i) {
+            const int kb = kb0 + i, st = i % TC_STAGES;
+            if (i >= TC_STAGES) ok &= mbar_wait_bounded(&empty[st], (uint32_t)((i / TC_STAGES - 1) & 1));
+            mbar_expect_tx(&full[st], TC_A_BYTES + b_bytes);
+            bulk_g2s(sA + (size_t)st * TC_A_BYTES, achunk + (size_t)kb * (TC_A_BYTES / 4), TC_A_BYTES, &full[st]);
+            bulk_g2s(sB + (size_t)st * TC_B_BYTES, bchunk + (size_t)kb * (TC_B_BYTES / 4), b_bytes, &full[st]);
+        }
+    } else if (tid == 32) {
+        // MMA issuer: four accumulators P1 = Sr Xr, P2 = Si Xi, P3 = Si Xr, P4 = Sr Xi (3xTF32 each)
+        const uint32_t pb = (uint32_t)N * 64;                         // X plane stride in the chunk
+        for (int i = 0; i < nk; ++i) {
+            const int st = i % TC_STAGES;
+            ok &= mbar_wait_bounded(&full[st], (uint32_t)((i / TC_STAGES) & 1));
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA + (size_t)st * TC_A_BYTES), b0 = smem_u32(sB + (size_t)st * TC_B_BYTES);
+#pragma unroll
+            for (int ks = 0; ks < TC_KB / 8; ++ks) {
+                const uint32_t ko = ks * 256;          // two core matrices along K per MMA
+                const uint64_t srh = tc_desc(a0 + 0 * TC_A_PLANE + ko), srl = tc_desc(a0 + 1 * TC_A_PLANE + ko);
+                const uint64_t sih = tc_desc(a0 + 2 * TC_A_PLANE + ko), sil = tc_desc(a0 + 3 * TC_A_PLANE + ko);
+                const uint64_t xrh = tc_desc(b0 + 0 * pb + ko), xrl = tc_desc(b0 + 1 * pb + ko);
+                const uint64_t xih = tc_desc(b0 + 2 * pb + ko), xil = tc_desc(b0 + 3 * pb + ko);
+                const uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
+                const uint32_t d1 = tmem, d2 = tmem + N, d3 = tmem + 2 * N, d4 = tmem + 3 * N;
+                tc_mma(d1, srh, xrh, idesc, acc0); tc_mma(d1, srh, xrl, idesc, 1u); tc_mma(d1, srl, xrh, idesc, 1u);
+                tc_mma(d2, sih, xih, idesc, acc0); tc_mma(d2, sih, xil, idesc, 1u); tc_mma(d2, sil, xih, idesc, 1u);
+                tc_mma(d3, sih, xrh, idesc, acc0); tc_mma(d3, sih, xrl, idesc, 1u); tc_mma(d3, sil, xrh, idesc, 1u);
+                tc_mma(d4, srh, xih, idesc, acc0); tc_mma(d4, srh, xil, idesc, 1u); tc_mma(d4, srl, xih, idesc, 1u);
+            }
+            tc_commit(&empty[st]);                    // the slot is free once these MMAs are done
+        }
+        tc_commit(fin);
+    }
+    if (nk > 0) ok &= mbar_wait_bounded(fin, 0);
+    __syncwarp();                                      // the producer / issuer lanes rejoin their warps
+    tc_fence_after();
+    // epilogue: warp w reads TMEM lanes 32w .. 32w + 31 (rows of the tile)
+    const int row = tile.row0 + warp * 32 + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const float cs = conj ? -1.f : 1.f;
+    float2* dst = out + (size_t)split * split_stride;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+        float p1[16], p2[16], p3[16], p4[16];
+        tc_ld16(lane_addr + c0, p1);
+        tc_ld16(lane_addr + N + c0, p2);
+        tc_ld16(lane_addr + 2 * N + c0, p3);
+        tc_ld16(lane_addr + 3 * N + c0, p4);
+        tc_wait_ld();
+        if (row < m) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int col = tile.col0 + c0 + i;
+                const int k = col / n_orb, o = col - k * n_orb;
+                if (c0 + i < N && k < info.R[c]) {
+                    const float2 v = nk > 0 ? make_float2(p1[i] - cs * p2[i], cs * p3[i] + p4[i]) : make_float2(0.f, 0.f);
+                    dst[(size_t)o * ng + info.moff[c][k] + row] = v;
+                }
+            }
+        }
+    }
+    // the producer's copies have all landed unless a wait gave up; wait (bounded) for the last ones
+    if (tid == 0)
+        for (int i = nk > TC_STAGES ? nk - TC_STAGES : 0; i < nk; ++i)
+            ok &= mbar_wait_bounded(&full[i % TC_STAGES], (uint32_t)((i / TC_STAGES) & 1));
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+    if (!ok) atomicExch(err, 1);
+}
+
+}  // namespace dev
+}  // namespace abc

@@ -38,9 +38,12 @@ int check_params(const abc_grid* grid, const abc_params* params) {
     if (params->order != 0 && params->order != 1) return fail(ABC_ERR_ARG, "order must be 0 or 1");
     const double s = params->order == 0 ? params->s0 : params->s1;
     if (!(s > 0.0)) return fail(ABC_ERR_ARG, "interpolation point must be > 0");
-    if (params->precision < ABC_FP64 || params->precision > ABC_C64_SPLIT_BF16)
+    if (params->precision < ABC_FP64 || params->precision > ABC_C64_3XTF32)
         return fail(ABC_ERR_ARG, "unknown precision");
-    if (params->max_orbitals < 1) return fail(ABC_ERR_ARG, "max_orbitals must be >= 1");
+    if (params->precision == ABC_C64_SPLIT_BF16)
+        return fail(ABC_ERR_UNSUPPORTED, "the split-bf16 form is not built (use ABC_C64_3XTF32)");
+    if (params->max_orbitals < 1 || params->max_orbitals > 65535)
+        return fail(ABC_ERR_ARG, "max_orbitals must be in [1, 65535]");
     return ABC_OK;
 }
 }  // namespace abc

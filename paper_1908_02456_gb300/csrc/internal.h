@@ -81,7 +81,6 @@ struct Geometry {
     // coefficient matrices with the parity-basis scale of each slot folded in:
     std::vector<double> coef_f;     // [types][8 o][8 s] = coef[o][s] / sqrt(8 |H_s|)   (forward)
     std::vector<double> coef_bt;    // [types][8 s][8 o] = coef[o][s] * sqrt(|H_s| / 8)  (back, transposed)
-    std::vector<int> adapted_cls;   // [n_gamma] class | (right-hand side << 8) of each adapted index
 };
 
 // Axis permutations: (pi . x)[kAxisPerms[pi][a]] = x[a]; the same map moves parity bit a

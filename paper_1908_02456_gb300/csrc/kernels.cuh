@@ -38,6 +38,7 @@ struct BlockInfo {
 template <typename T>
 struct CellTab {
     int n_cells;
+    int ng;                // adapted vectors are orbital-major: element (j, orbital) at orbital * ng + j
     const int* out;        // [n_cells][8 o][8 p] adapted index or -1
     const int* type;       // [n_cells][8 p] coefficient matrix id
     const T* coef_f;       // [types][8 o][8 s] forward coefficients, slot scale folded in
@@ -50,16 +51,15 @@ struct CellTab {
 
 // Partial sums of the tiled one-orbital contraction, gathered by the back transform:
 // t[j] = sum of the row parts of the segments of (class c, tile row I) + the column
-// parts of the tiles (c, K, I), K > I (fixed order).
+// parts of the tiles (c, K, I), K > I (fixed order).  desc is indexed like the cell
+// output table (cell * 64 + 8 o + p): x = first row-part element, y = number of row
+// segments (consecutive, 192 elements apart), z = column-part element of K = I + 1,
+// w = (number of K) | ((I + 2) << 16); the column-part element of K + 1 is that of K
+// plus (K + 1) * 192.
 struct SymGather {
-    const int* adapted_cls;      // [n_gamma] class | (right-hand side << 8)
-    const int2* rowseg;          // [(class, tile row)] segment range
+    const int4* desc;
     const float2* rowpart;       // [segment][64][3]
     const float2* colpart;       // [tile][64][3]
-    int moff[16][3];
-    long long tbase[16];
-    int rbase[16];
-    int nt[16];
 };
 
 // Gamma index of a boundary node (ascending linear order, x fastest).
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, lon
         ap.x += cf[q] * sp[grp][q][g].x; ap.y += cf[q] * sp[grp][q][g].y;
         af.x += cf[q] * sf[grp][q][g].x; af.y += cf[q] * sf[grp][q][g].y;
     }
-    const long long e = (long long)jj * n_orb + j;
+    const long long e = (long long)j * ct.ng + jj;
     hat_phi[e] = ap;
     if (w_f) hat_f[e] = af;
     if (MODE == 1) {
@@ -149,32 +149,27 @@ __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, lon
     }
 }
 
-// t[jj] from the partial sums of the tiled contraction (see SymGather).  The column
+// t from the partial sums of the tiled contraction (see SymGather).  The column
 // parts are read eight at a time into independent accumulators, so their loads are
 // in flight together; the sums are combined in a fixed order.
-__device__ __forceinline__ float2 sym_gather(const SymGather& sg, int jj) {
-    const int ck = sg.adapted_cls[jj];
-    const int c = ck & 255, k = ck >> 8;
-    const int row = jj - sg.moff[c][k], I = row >> 6, r = row & 63;
-    const int nt = sg.nt[c];
-    const int2 rs = sg.rowseg[sg.rbase[c] + I];
+__device__ __forceinline__ float2 sym_gather(const SymGather& sg, int4 d) {
     float2 acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
-    for (int q = rs.x; q < rs.y; ++q) {
-        const float2 v = sg.rowpart[((size_t)q * 64 + r) * 3 + k];
+    for (int q = 0; q < d.y; ++q) {
+        const float2 v = sg.rowpart[d.x + q * 192];
         acc[0].x += v.x;
         acc[0].y += v.y;
     }
-    // tile (K, I) = tbase + K (K + 1) / 2 + I for K = I + 1 .. nt - 1
-    const long long base = sg.tbase[c] + I;
-    for (int K0 = I + 1; K0 < nt; K0 += 8) {
+    const int nk = d.w & 0xffff;
+    int e = d.z, step = d.w >> 16;
+    for (int i0 = 0; i0 < nk; i0 += 8) {
         float2 v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int K = K0 + q;
-            v[q] = K < nt ? sg.colpart[((size_t)(base + (long long)K * (K + 1) / 2) * 64 + r) * 3 + k]
-                          : make_float2(0.f, 0.f);
+            v[q] = i0 + q < nk ? sg.colpart[e] : make_float2(0.f, 0.f);
+            e += step * 192;
+            ++step;
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -195,7 +190,8 @@ __device__ __forceinline__ float2 sym_gather(const SymGather& sg, int jj) {
 //                             (B f + A E phi with B = s1 I - A S, t = S f_hat)
 //   MODE 1 (order 0):         x = t  (t = M phi_hat, or conj(M) phi_hat)
 //   MODE 2 (order-1 adjoint): x = s1 f_hat - t + i phi_hat  (t = conj(S) u)
-// with t read from t_in, or gathered from the contraction's partial sums (GATHER);
+// with t read from t_in (the sum of its nsplit arrays split_stride apart), or
+// gathered from the tiled contraction's partial sums (GATHER);
 // then thread (s, p) undoes the mixing with the scaled transposed coefficients, the
 // slot's 8-lane group transforms back and lane g holds the value v at the
 // reflection g of the slot's representative.  At that node's Gamma index e, the
@@ -207,7 +203,8 @@ template <typename T, int MODE, bool GATHER>
 __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, T a_coef,
                                                 const typename C2<T>::t* __restrict__ hat_phi,
                                                 const typename C2<T>::t* __restrict__ hat_f,
-                                                const typename C2<T>::t* __restrict__ t_in, SymGather sg,
+                                                const typename C2<T>::t* __restrict__ t_in, int nsplit,
+                                                long long split_stride, SymGather sg,
                                                 const typename C2<T>::t* y_f, typename C2<T>::t* out,
                                                 typename C2<T>::t* acc, T cdt) {
     typedef typename C2<T>::t V;
@@ -221,6 +218,8 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
     const int jj = live ? ct.out[cell * 64 + t] : -1;          // output o = s of parity p = g
     const int ty = live ? ct.type[cell * 8 + g] : 0;
     const int wr = live ? ct.wr[cell * 64 + t] : -1;
+    int4 gd = make_int4(0, 0, 0, 0);
+    if constexpr (GATHER) gd = live ? sg.desc[cell * 64 + t] : gd;
     const T c_cell = (MODE == 0 && live) ? (T)ct.cell_c[cell] : (T)0;
     T cf[8];
 #pragma unroll
@@ -231,13 +230,18 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
     if (wr >= 0 && MODE == 2) yv = acc[ew];
     V x = mk<T>(0, 0);
     if (jj >= 0) {
-        const long long e = (long long)jj * n_orb + j;
+        const long long e = (long long)j * ct.ng + jj;
         V tv;
         if constexpr (GATHER) {
-            const float2 q = sym_gather(sg, jj);
+            const float2 q = sym_gather(sg, gd);
             tv = mk<T>((T)q.x, (T)q.y);
         } else {
             tv = t_in[e];
+            for (int q = 1; q < nsplit; ++q) {
+                const V u = t_in[(long long)q * split_stride + e];
+                tv.x += u.x;
+                tv.y += u.y;
+            }
         }
         if (MODE == 0) {
             const T a = a_coef * c_cell;
@@ -341,11 +345,11 @@ __global__ void gemv_blocks(BlockInfo bi, int n_rows, const typename C2<T>::t* _
 }
 
 // --------------------------------------------------------------------------
-// Boundary contraction, many orbitals: T_p = S_p X_p (X_p: m_p x n_orb, orbital
-// fastest).  CUDA-core reference form (shared-memory tiles).
+// Boundary contraction, many orbitals: T_p = S_p X_p (X_p: m_p x n_orb; adapted
+// vectors orbital-major with stride ng).  CUDA-core form (shared-memory tiles).
 // --------------------------------------------------------------------------
 template <typename T, int BM, int BN, int BK>
-__global__ void gemm_blocks_simt(BlockInfo bi, int n_orb, const typename C2<T>::t* __restrict__ mat,
+__global__ void gemm_blocks_simt(BlockInfo bi, int n_orb, int ng, const typename C2<T>::t* __restrict__ mat,
                                  const typename C2<T>::t* __restrict__ X, typename C2<T>::t* __restrict__ Y,
                                  int conj, const int* __restrict__ tile_block, const int* __restrict__ tile_row) {
     typedef typename C2<T>::t V;
@@ -356,7 +360,7 @@ __global__ void gemm_blocks_simt(BlockInfo bi, int n_orb, const typename C2<T>::
     const int col0 = blockIdx.y * BN;
     const int m = bi.m[p];
     const V* S = mat + bi.mat_off[p];
-    const V* Xp = X + (long long)bi.off[p] * n_orb;
+    const V* Xp = X + bi.off[p];                          // column gc at Xp[gc * ng]
     const int tx = threadIdx.x % BN, ty = threadIdx.x / BN;   // BN columns, (nthr/BN) row groups
     constexpr int NT = 256;
     constexpr int RPT = BM / (NT / BN);                       // rows per thread
@@ -377,7 +381,7 @@ __global__ void gemm_blocks_simt(BlockInfo bi, int n_orb, const typename C2<T>::
             const int kk = e / BN, cc = e % BN;
             const int gk = k0 + kk, gc = col0 + cc;
             V v = mk<T>(0, 0);
-            if (gk < m && gc < n_orb) v = Xp[(long long)gk * n_orb + gc];
+            if (gk < m && gc < n_orb) v = Xp[(long long)gc * ng + gk];
             Bs[kk][cc] = v;
         }
         __syncthreads();
@@ -398,7 +402,7 @@ __global__ void gemm_blocks_simt(BlockInfo bi, int n_orb, const typename C2<T>::
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
         const int gr = row0 + ty * RPT + i;
-        if (gr < m) Y[(long long)(bi.off[p] + gr) * n_orb + gc] = mk<T>(accr[i], acci[i]);
+        if (gr < m) Y[(long long)gc * ng + bi.off[p] + gr] = mk<T>(accr[i], acci[i]);
     }
 }
 
@@ -406,6 +410,7 @@ __global__ void gemm_blocks_simt(BlockInfo bi, int n_orb, const typename C2<T>::
 // Fused stencil + potential + boundary term + Horner stage
 //   out = y + cdt * (-i) [ H_{I,I} w + E^T b ],  H = -1/2 Delta_h + V
 // b = w_f (order 1) or M E w (order 0), natural Gamma order [n_gamma][n_orb].
+// Grid (ceil(nx ny / blockDim), nz, n_orb): one thread per node of a z-plane.
 // --------------------------------------------------------------------------
 template <typename T>
 __global__ void stencil_stage(int nx, int ny, int nz, int n_orb, T inv_h2, const typename C2<T>::t* __restrict__ w,
@@ -413,13 +418,11 @@ __global__ void stencil_stage(int nx, int ny, int nz, int n_orb, T inv_h2, const
                               const typename C2<T>::t* __restrict__ bterm, typename C2<T>::t* out, T cdt) {
     typedef typename C2<T>::t Vc;
     const long long nvox = (long long)nx * ny * nz;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nvox * n_orb) return;
-    const int orb = (int)(idx / nvox);
-    const long long n = idx - (long long)orb * nvox;
-    const int i = (int)(n % nx);
-    const int jy = (int)((n / nx) % ny);
-    const int k = (int)(n / ((long long)nx * ny));
+    const int tp = blockIdx.x * blockDim.x + threadIdx.x;          // node in the z-plane
+    if (tp >= nx * ny) return;
+    const int i = tp % nx, jy = tp / nx, k = blockIdx.y, orb = blockIdx.z;
+    const long long n = (long long)k * nx * ny + tp;
+    const long long idx = (long long)orb * nvox + n;
     const Vc* wo = w + (long long)orb * nvox;
     const Vc c = wo[n];
     T sr = 0, si = 0;
@@ -544,13 +547,11 @@ __global__ void stencil_adj(int order, int nx, int ny, int nz, int n_orb, T inv_
                             typename C2<T>::t* __restrict__ anew, T cdt) {
     typedef typename C2<T>::t Vc;
     const long long nvox = (long long)nx * ny * nz;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nvox * n_orb) return;
-    const int orb = (int)(idx / nvox);
-    const long long n = idx - (long long)orb * nvox;
-    const int i = (int)(n % nx);
-    const int jy = (int)((n / nx) % ny);
-    const int k = (int)(n / ((long long)nx * ny));
+    const int tp = blockIdx.x * blockDim.x + threadIdx.x;          // node in the z-plane
+    if (tp >= nx * ny) return;
+    const int i = tp % nx, jy = tp / nx, k = blockIdx.y, orb = blockIdx.z;
+    const long long n = (long long)k * nx * ny + tp;
+    const long long idx = (long long)orb * nvox + n;
     const Vc* wo = a + (long long)orb * nvox;
     const Vc c = wo[n];
     T sr = 0, si = 0;

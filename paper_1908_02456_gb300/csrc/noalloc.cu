@@ -90,16 +90,17 @@ void step_with_scratch(const abc_ctx* c, void* psi, void* aux, const void* V, in
         } else {
             dim3 grid(c->n_tiles, (n_orb + 31) / 32);
             abc::dev::gemm_blocks_simt<T, 32, 32, 16><<<grid, 256, 0, s>>>(
-                c->bi, n_orb, c->mat.as<Vc>(), x, tvec, 0, c->tile_blk.as<int>(), c->tile_row.as<int>());
+                c->bi, n_orb, g.n_gamma, c->mat.as<Vc>(), x, tvec, 0, c->tile_blk.as<int>(), c->tile_row.as<int>());
         }
         const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
         if (order == 1)
             abc::dev::bnd_back<T, 0, false><<<nbk, 128, 0, s>>>(ct, n_orb, (T)c->blocks.s, a_coef, hat_phi, hat_f, tvec,
-                                                                c->sym_gather, (const Vc*)aux, (Vc*)of, nullptr, cdt);
+                                                                1, 0, c->sym_gather, (const Vc*)aux, (Vc*)of, nullptr,
+                                                                cdt);
         else
-            abc::dev::bnd_back<T, 1, false><<<nbk, 128, 0, s>>>(ct, n_orb, (T)0, (T)0, hat_phi, hat_f, tvec,
+            abc::dev::bnd_back<T, 1, false><<<nbk, 128, 0, s>>>(ct, n_orb, (T)0, (T)0, hat_phi, hat_f, tvec, 1, 0,
                                                                 c->sym_gather, nullptr, cnat, nullptr, (T)0);
-        abc::dev::stencil_stage<T><<<nblk(c->nvox * n_orb, 256), 256, 0, s>>>(
+        abc::dev::stencil_stage<T><<<abc::stencil_grid(c, n_orb), 256, 0, s>>>(
             g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)in_p, (const Vc*)psi, (const T*)V,
             order == 1 ? (const Vc*)in_f : cnat, (Vc*)op, cdt);
         in_p = op;

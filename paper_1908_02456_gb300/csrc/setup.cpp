@@ -36,7 +36,7 @@ int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& e
     g = Geometry();
     g.nx = nx; g.ny = ny; g.nz = nz; g.h = h;
     g.n_nodes = (long long)nx * ny * nz;
-    if (g.n_nodes > (1LL << 31) - 1) { err = "grid too large"; return ABC_ERR_ARG; }
+    if (g.n_nodes > (1LL << 31) - 1 || nz > 65535) { err = "grid too large"; return ABC_ERR_ARG; }
     g.node_gamma.assign((size_t)g.n_nodes, -1);
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)

@@ -139,17 +139,27 @@ __device__ __forceinline__ bool sym_segment(const SymInfo& si, int4 sg, int s, i
     }
     bool ok = true;
     const long long tb = si.tbase[c] + (long long)I * (I + 1) / 2;
+    // x_J of this thread's two columns; the next tile's are fetched while this one is used
+    float2 xn[2][R];
+    auto fetch_xj = [&](int J) {
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int col = J * SYM_T + 2 * cp + cc;
+#pragma unroll
+            for (int k = 0; k < R; ++k) xn[cc][k] = col < m ? __ldg(x + si.moff[c][k] + col) : make_float2(0.f, 0.f);
+        }
+    };
+    fetch_xj((int)(sg.z - tb));
     for (int t = sg.z; t < sg.w; ++t, ++u) {
         const int J = (int)(t - tb);
         const bool offdiag = J < I;
         const int slot = u % SYM_STAGES;
         float2 xj[2][R];
 #pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            const int col = J * SYM_T + 2 * cp + cc;
+        for (int cc = 0; cc < 2; ++cc)
 #pragma unroll
-            for (int k = 0; k < R; ++k) xj[cc][k] = col < m ? __ldg(x + si.moff[c][k] + col) : make_float2(0.f, 0.f);
-        }
+            for (int k = 0; k < R; ++k) xj[cc][k] = xn[cc][k];
+        if (t + 1 < sg.w) fetch_xj(J + 1);
         ok &= mbar_wait_bounded(&full[slot], (uint32_t)((u / SYM_STAGES) & 1));
         const float4* T4 = reinterpret_cast<const float4*>(ring + (size_t)slot * SYM_T * SYM_T);
         float2 cacc[2][R];

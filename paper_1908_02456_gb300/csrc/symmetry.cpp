@@ -304,10 +304,6 @@ int build_irreps(Geometry& g, std::string& err) {
                 g.cell_wr[e] = first ? gi : -1;
             }
         }
-    g.adapted_cls.assign(g.n_gamma, -1);
-    for (size_t ki = 0; ki < g.cls.size(); ++ki)
-        for (int e = 0; e < g.cls[ki].R; ++e)
-            for (int c = 0; c < g.cls[ki].m; ++c) g.adapted_cls[g.cls[ki].moff[e] + c] = (int)ki | (e << 8);
     return ABC_OK;
 }
 

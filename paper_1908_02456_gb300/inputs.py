@@ -40,7 +40,7 @@ class Workload:
     steps: int
     potential: str              # "zero" | "harmonic_bumps" | "smooth_random" | "none"
     meanfield: Optional[Tuple[float, float, float]] = None   # (a, b, alpha)
-    precision: str = "c64"      # "fp64" | "c64" | "bf16x3"
+    precision: str = "c64"      # "fp64" | "c64" | "tf32x3"
 
     @property
     def seed(self) -> int:
@@ -57,11 +57,11 @@ WORKLOADS = {
     2: Workload(2, "harmonic-64cube-order1-single", 64, 0.4, 1, 1, 1.0, 0.005, 2000,
                 "harmonic_bumps", precision="c64"),
     3: Workload(3, "meanfield-64cube-32orb-order1", 64, 0.4, 32, 1, 1.0, 0.005, 1000,
-                "none", meanfield=(-1.0, 0.8, 1.0 / 6.0), precision="bf16x3"),
+                "none", meanfield=(-1.0, 0.8, 1.0 / 6.0), precision="tf32x3"),
     4: Workload(4, "adjoint-48cube-order1", 48, 0.4, 1, 1, 1.0, 0.005, 1000,
                 "smooth_random", precision="c64"),
     5: Workload(5, "meanfield-96cube-128orb-order1", 96, 0.35, 128, 1, 1.0, 0.004, 500,
-                "none", meanfield=(-1.0, 0.8, 1.0 / 6.0), precision="bf16x3"),
+                "none", meanfield=(-1.0, 0.8, 1.0 / 6.0), precision="tf32x3"),
 }
 
 

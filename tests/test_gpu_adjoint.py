@@ -66,6 +66,25 @@ def test_adjoint_complex64_vs_fp64(env):
     assert rel(g32, g64) < 1e-4
 
 
+@pytest.mark.parametrize("order", [0, 1])
+def test_adjoint_tensor_core_vs_fp64(env, order):
+    """Three orbitals through the tensor-core contraction (its conjugated form runs in
+    the reverse sweep) against the FP64 gradient, next to the FP32 CUDA-core form."""
+    torch, abc = env
+    dims, h, dt, steps = (12, 12, 12), 0.4, 0.005, 60
+    rng = np.random.default_rng(5 + order)
+    V = inputs.smooth_random(dims, h, rng).reshape(-1)
+    psi = np.concatenate([inputs.gaussian_packet(dims, h, (0.4 * j - 0.4, 0, 0.2), (2.0, 1.0 - j, 0.5), 1.2)[None]
+                          for j in range(3)]).reshape(3, -1)
+    J64, g64 = _gpu_adjoint(torch, abc, dims, h, order, 1.0, "fp64", psi, V, dt, steps, 20)
+    Jtc, gtc = _gpu_adjoint(torch, abc, dims, h, order, 1.0, "tf32x3", psi, V, dt, steps, 20)
+    Jc, gc = _gpu_adjoint(torch, abc, dims, h, order, 1.0, "c64", psi, V, dt, steps, 20)
+    assert abs(Jtc - J64) < 1e-5 * max(abs(J64), 1e-3)
+    # the tensor-core path is as accurate as the FP32 CUDA-core path on the same case
+    e_tc, e_c = rel(gtc, g64), rel(gc, g64)
+    assert e_tc < max(2.0 * e_c, 1e-5) and e_tc < 1e-3, (e_tc, e_c)
+
+
 def _absorbed(torch, ctx, psi0, V, dt, steps):
     p = psi0.clone()
     aux = ctx.new_aux(p.shape[0]) if ctx.order == 1 else None

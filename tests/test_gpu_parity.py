@@ -13,7 +13,7 @@ from paper_1908_02456_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "c64": 1e-5}
+TOL = {"fp64": 1e-10, "c64": 1e-5, "tf32x3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -100,7 +100,7 @@ def test_harmonic_order1_reduced(torch_cuda, prec):
     assert rel(d, ref_d) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "c64"])
+@pytest.mark.parametrize("prec", ["fp64", "c64", "tf32x3"])
 def test_meanfield_batched_reduced(torch_cuda, prec):
     """Batched orbitals with the density-dependent potential V = a rho + b rho^(1+alpha)
     (a = -1, b = 0.8, alpha = 1/6), first-order ABC; 5 orbitals (a ragged tail of the
@@ -167,3 +167,37 @@ def test_full_size_lyapunov_c64(torch_cuda):
     W = d[:, 0, 1]
     assert np.all(np.diff(W) <= 1e-6 * W[:-1])
     assert abs(d[0, 0, 0] - 1.0) < 1e-3
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("dims,b", [((22, 22, 22), 48), ((13, 11, 12), 7)])
+def test_tensor_core_contraction_many_tiles(torch_cuda, order, dims, b):
+    """The tensor-core (3xTF32) many-orbital contraction against the FP64 oracle, one
+    step from an unstructured state: on the 22^3 cube the classes span several
+    128-row tiles and 16-deep K blocks, and 3 x 48 columns split into two N tiles
+    (80 + 64); the non-cube has eight R = 1 classes and a 16-column tile holding 7
+    orbitals."""
+    h, dt = 0.45, 0.005
+    rng = np.random.default_rng(77 + order + b)
+    psi0 = inputs.random_state(dims, b, rng).reshape(b, -1)
+    V = rng.uniform(-0.5, 0.5, size=dims[::-1])
+    sy = oracle_system(dims, h, order, 1.0, V)
+    f0 = (rng.normal(size=(b, len(sy.G))) + 1j * rng.normal(size=(b, len(sy.G)))) if order == 1 else None
+    ref_p, ref_f = sy.step(psi0, f0, dt)
+    p, f, _ = gpu_run(torch_cuda, dims, h, order, 1.0, "tf32x3", psi0, V, dt, 1, aux0=f0)
+    assert rel(p, ref_p) < 1e-6
+    if order == 1:
+        assert rel(f, ref_f) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["c64", "tf32x3"])
+def test_one_orbital_complex64_uses_packed_tiles(torch_cuda, prec):
+    """One complex64 orbital runs the packed symmetric-tile contraction, not the
+    full-block fallback: the context holds tiles and the algorithmic bytes of a launch
+    are the tiles' (64 x 64 complex64 each) plus the two boundary vectors."""
+    from paper_1908_02456_gb300 import abc
+    ctx = abc.Context((16, 16, 16), 0.5, 1, 1.0, precision=prec, max_orbitals=2)
+    tiles = ctx.get_tuning(abc.TUNE_TILE_COUNT)
+    assert tiles > 0
+    assert ctx.kernel_bytes(abc.KERNEL_CONTRACTION, 1) == tiles * 64 * 64 * 8 + 2 * ctx.n_gamma * 8
+    ctx.close()
