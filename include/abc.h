@@ -13,6 +13,10 @@
  *   order 1 (eq:dynamics1):  phi' = -i H phi - i E^T f,
  *                            f'   = B f + A E phi,
  *                            A = -i H_{Gamma,II} H_{II,Gamma}, B = s1 I - A K(s1)^{-1}
+ *   order 2 (eq:dynamics2):  phi' = -i H phi - i E^T f,  f' = g,
+ *                            g' = B1 g + B0 f + A1 E phi' + A0 E phi,
+ *                            R_22(s) = (s^2 I - s B1 - B0)^{-1}(s A1 + A0) fitted to
+ *                            K at four points (Sec. 3.3)
  * with K(s) the DtN map of eq:17, evaluated by eq:eval (App. A).  One time step
  * applies sum_{k=0..4} (dt L)^k / k! (eq:21, signs read as the Taylor series of
  * exp(dt L)) in Horner form.
@@ -24,8 +28,9 @@
  * - psi: device array [n_orb][nz][ny][nx] of complex values, interleaved (re, im):
  *   complex128 when precision == ABC_FP64, complex64 otherwise.
  * - aux: device array [n_gamma][n_orb] (orbital fastest) of the same complex type,
- *   holding f_Gamma (order 1 only; pass NULL for order 0).  Gamma nodes are
- *   numbered by ascending linear index.  Start it at zero (f_Gamma(0) = 0, Sec. 2).
+ *   holding f_Gamma (order 1; pass NULL for order 0), or [2][n_gamma][n_orb] holding
+ *   f_Gamma then g = df_Gamma/dt (order 2).  Gamma nodes are numbered by ascending
+ *   linear index.  Start it with abc_aux_init (order 1: zero, f_Gamma(0) = 0, Sec. 2).
  * - V: device array [nz][ny][nx] of real values (double for ABC_FP64, float
  *   otherwise): the external potential.
  * - The caller owns psi, aux and V.  The context owns the boundary matrices and
@@ -72,6 +77,10 @@ extern "C" {
 #define ABC_MAT_A 2            /* order 1: A                                        */
 #define ABC_MAT_B 3            /* order 1: B                                        */
 #define ABC_MAT_Q 4            /* order 1: Q = (H_{Gamma,II} H_{II,Gamma})^{-1}     */
+#define ABC_MAT_B1 5           /* order 2: B1 of R_22 (Sec. 3.3, eq:dynamics2)      */
+#define ABC_MAT_B0 6           /* order 2: B0                                       */
+#define ABC_MAT_A1 7           /* order 2: A1                                       */
+#define ABC_MAT_A0 8           /* order 2: A0                                       */
 
 typedef struct {
     int nx, ny, nz;   /* interior nodes per axis, each >= 3, nz <= 65535,
@@ -81,12 +90,14 @@ typedef struct {
 } abc_grid;
 
 typedef struct {
-    int order;        /* 0 or 1 (rational order m of eq:24)                         */
+    int order;        /* 0, 1 or 2 (rational order m of eq:24)                      */
     double s0;        /* order 0 interpolation point, > 0 (Thm 3.1)                 */
     double s1;        /* order 1 interpolation point, > 0 (Thm 3.2)                 */
     int precision;    /* ABC_FP64 | ABC_C64_FP32 | ABC_C64_3XTF32                   */
     int max_orbitals; /* largest n_orb later passed to step/run (sizes workspace),
                          1 .. 65535                                                 */
+    double s2[4];     /* order 2 interpolation points, > 0 and distinct (Sec. 3.3:
+                         R_22(s) = (s^2 I - s B1 - B0)^{-1}(s A1 + A0) = K(s) there) */
 } abc_params;
 
 typedef struct {
@@ -128,6 +139,14 @@ int abc_run(abc_ctx* ctx, void* psi, void* aux, const void* V, int n_orb, double
 int abc_run_host(abc_ctx* ctx, void* psi_host, void* aux_host, const void* V_host, int n_orb,
                  double dt, long long nsteps, const abc_meanfield* mf, int diag_every,
                  double* diag_out);
+
+/* Consistent auxiliary state at t = 0 for the wave function psi (device, [n_orb]
+ * orbitals): order 1 aux = 0 (f(0) = 0 since phi_II(0) = 0, Sec. 2); order 2 aux =
+ * [f | g] with f = 0 and g = A1 E psi (the value for which the Laplace transform of
+ * eq:dynamics2 gives f = R_22(s) E phi); order 0 holds no auxiliary state (no-op).
+ * aux: device [n_gamma][n_orb] complex (order 1) or [2][n_gamma][n_orb] (order 2:
+ * f then g), overwritten.  Asynchronous on the stream. */
+int abc_aux_init(abc_ctx* ctx, const void* psi, void* aux, int n_orb, void* stream);
 
 /* Per-orbital diagnostics of the current state into host out[n_orb][3]:
  * norm_j = h^3 |phi_j|^2; W_j = norm_j + h^3 f_j^* Q f_j (eq:lyapunov1; = norm_j
@@ -201,9 +220,14 @@ int abc_step_noalloc(const abc_ctx* ctx, void* psi, void* aux, const void* V, in
  *                           that they stay in L2 from one Horner stage to the next
  *                           (the rest use evict_first); 0 = all evict_first.
  *   ABC_TUNE_TILE_COUNT     (read only) number of stored tiles.
+ *   ABC_TUNE_PDL            1: launch the tiled contraction and the back transform
+ *                           that gathers its partial sums with a programmatic
+ *                           dependency on the preceding kernel (early start of
+ *                           their independent work); 0 (default): ordinary launches.
  * Setting a knob drops the cached CUDA graph.  The paper has no counterpart. */
 #define ABC_TUNE_L2_KEEP_TILES 0
 #define ABC_TUNE_TILE_COUNT 1
+#define ABC_TUNE_PDL 2
 int abc_set_tuning(abc_ctx* ctx, int key, long long value);
 int abc_get_tuning(const abc_ctx* ctx, int key, long long* value);
 

@@ -4,11 +4,14 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
 State y = (phi, f): phi holds b orbitals on the interior nodes (shape (b, n_I)),
 f the auxiliary boundary variable f_Gamma of the first-order ABC (shape (b, n_Gamma),
-f(0) = 0 because phi_II(0) = 0, Sec. 2).  The linear operator L of y' = L y is
+f(0) = 0 because phi_II(0) = 0, Sec. 2).  For the second-order ABC f holds [f | g]
+with g = df/dt (shape (b, 2 n_Gamma)).  The linear operator L of y' = L y is
 
   no ABC  : L phi = -i H_{I,I} phi                            (zero Dirichlet)
   order 0 : L phi = -i H_{I,I} phi - i E^T M E phi            (eq:dynamics0)
   order 1 : L (phi, f) = (-i H_{I,I} phi - i E^T f,  B f + A E phi)   (eq:dynamics1)
+  order 2 : L (phi, f, g) = (phidot, g, B1 g + B0 f + A1 E phidot + A0 E phi),
+            phidot = -i H_{I,I} phi - i E^T f                 (eq:dynamics2)
 
 with H_{I,I} = kinetic + diag(V).  One time step applies the degree-4 Taylor
 polynomial of exp(dt L) (eq:21, read as sum_{k=0..4} (dt L)^k / k!; the printed
@@ -72,10 +75,20 @@ class System:
             A, B = self.coeffs["A"], self.coeffs["B"]
             dphi = dphi - 1j * self.ET(f, phi.shape[1])
             df = (B @ f.T).T + (A @ self.E(phi).T).T
+        elif self.order == 2:
+            co = self.coeffs
+            ng = len(self.G)
+            fa, ga = f[:, :ng], f[:, ng:]
+            dphi = dphi - 1j * self.ET(fa, phi.shape[1])
+            dg = (co["B1"] @ ga.T).T + (co["B0"] @ fa.T).T + (co["A1"] @ self.E(dphi).T).T \
+                + (co["A0"] @ self.E(phi).T).T
+            df = np.concatenate([ga, dg], axis=1)
         return dphi, df
 
     def LH(self, phi, f, V):
-        """Adjoint operator L^H (for the reverse sweep)."""
+        """Adjoint operator L^H (for the reverse sweep; orders 0 and 1)."""
+        if self.order == 2:
+            raise NotImplementedError("the reverse sweep covers orders 0 and 1")
         dphi = 1j * self.H(phi, V)
         df = None
         if self.order == 0:
@@ -88,8 +101,22 @@ class System:
         return dphi, df
 
     # ---- time stepping ------------------------------------------------
+    def initial_aux(self, phi):
+        """Auxiliary data at t = 0.  Order 1: f(0) = 0 (phi_II(0) = 0, Sec. 2).  Order 2:
+        f(0) = 0 and g(0) = A1 E phi(0), the value for which the Laplace transform of
+        eq:dynamics2 gives f_hat = R_22(s) E phi_hat (the A1 E phidot term carries phi(0);
+        the exact exterior solution likewise has df/dt(0) = -i H_{Gamma,II} H_{II,Gamma} phi(0))."""
+        aux = self.zero_aux(phi.shape[0])
+        if self.order == 2:
+            aux[:, len(self.G):] = (self.coeffs["A1"] @ self.E(phi).T).T
+        return aux
+
     def zero_aux(self, b):
-        return np.zeros((b, len(self.G)), dtype=np.complex128) if self.order == 1 else None
+        if self.order == 1:
+            return np.zeros((b, len(self.G)), dtype=np.complex128)
+        if self.order == 2:
+            return np.zeros((b, 2 * len(self.G)), dtype=np.complex128)
+        return None
 
     def taylor(self, op, phi, f, V, dt):
         """sum_{k=0..4} (dt op)^k / k! applied to (phi, f), term by term."""
@@ -111,7 +138,8 @@ class System:
         """Per orbital: [norm, W, interior energy] (all with the h^d weight).
 
         norm = h^d |phi_j|^2; W = norm + h^d f_j^* Q f_j (eq:lyapunov1; = norm for
-        order 0 / no ABC, eq:lyapunov0); energy = h^d Re <phi_j, H_{I,I}[V] phi_j> with V
+        order 0 / no ABC, eq:lyapunov0, and for order 2, which has no proven
+        Lyapunov functional); energy = h^d Re <phi_j, H_{I,I}[V] phi_j> with V
         the potential of the current state."""
         V = self.potential(phi)
         norm = self.w * np.sum(np.abs(phi) ** 2, axis=1)
@@ -124,7 +152,7 @@ class System:
 
     def run(self, phi0, dt, nsteps, f0=None, diag_every=0):
         phi = np.asarray(phi0, dtype=np.complex128).reshape(phi0.shape[0], -1)
-        f = self.zero_aux(phi.shape[0]) if f0 is None else np.asarray(f0, dtype=np.complex128)
+        f = self.initial_aux(phi) if f0 is None else np.asarray(f0, dtype=np.complex128)
         diags = []
         for n in range(1, nsteps + 1):
             phi, f = self.step(phi, f, dt)

@@ -16,8 +16,9 @@ import numpy as np
 OK = 0
 FP64, C64_FP32, C64_SPLIT_BF16, C64_3XTF32 = 0, 1, 2, 3
 MAT_K, MAT_M, MAT_A, MAT_B, MAT_Q = 0, 1, 2, 3, 4
+MAT_B1, MAT_B0, MAT_A1, MAT_A0 = 5, 6, 7, 8
 KERNEL_CONTRACTION, KERNEL_STENCIL = 0, 1
-TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT = 0, 1
+TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT, TUNE_PDL = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16, "tf32x3": C64_3XTF32}
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libabc.so")
@@ -36,7 +37,7 @@ class abc_grid(ctypes.Structure):
 
 class abc_params(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("s0", ctypes.c_double), ("s1", ctypes.c_double),
-                ("precision", ctypes.c_int), ("max_orbitals", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("max_orbitals", ctypes.c_int), ("s2", ctypes.c_double * 4)]
 
 
 class abc_meanfield(ctypes.Structure):
@@ -73,6 +74,7 @@ def load():
         "abc_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
         "abc_step_noalloc": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P],
         "abc_set_tuning": [_P, ctypes.c_int, ctypes.c_longlong],
+        "abc_aux_init": [_P, _P, _P, ctypes.c_int, _P],
         "abc_get_tuning": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
     }
     for name, args in sig.items():
@@ -100,9 +102,15 @@ def _grid(shape: Sequence[int], h: float) -> abc_grid:
     return abc_grid(nx, ny, nz, 1, float(h))
 
 
-def _params(order: int, s: float, precision, max_orbitals: int) -> abc_params:
+def _params(order: int, s, precision, max_orbitals: int) -> abc_params:
+    """s: the interpolation point (orders 0, 1) or the four points (order 2)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    return abc_params(int(order), float(s), float(s), prec, int(max_orbitals))
+    if int(order) == 2:
+        pts = [float(v) for v in s]
+        if len(pts) != 4:
+            raise ValueError("order 2 needs four interpolation points")
+        return abc_params(2, pts[0], pts[0], prec, int(max_orbitals), (ctypes.c_double * 4)(*pts))
+    return abc_params(int(order), float(s), float(s), prec, int(max_orbitals), (ctypes.c_double * 4)(0, 0, 0, 0))
 
 
 def _mf(meanfield) -> Optional[ctypes.POINTER(abc_meanfield)]:
@@ -227,7 +235,8 @@ class Context:
 
     def __init__(self, shape, h, order, s, precision="c64", max_orbitals=1):
         self.shape = tuple(int(v) for v in shape)
-        self.h, self.order, self.s = float(h), int(order), float(s)
+        self.h, self.order = float(h), int(order)
+        self.s = tuple(float(v) for v in s) if self.order == 2 else float(s)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.max_orbitals = int(max_orbitals)
         self.ctx = abc_setup(_grid(self.shape, h), _params(order, s, self.precision, max_orbitals))
@@ -251,10 +260,11 @@ class Context:
         if psi.dim() != 4 or tuple(psi.shape[1:]) != (nz, ny, nx):
             raise ValueError(f"psi must have shape [b, {nz}, {ny}, {nx}]")
         b = psi.shape[0]
-        if self.order == 1:
+        if self.order >= 1:
+            shp = self.aux_shape(b)
             if aux is None or not aux.is_cuda or aux.dtype != self.complex_dtype or not aux.is_contiguous() \
-                    or tuple(aux.shape) != (self.n_gamma, b):
-                raise ValueError(f"aux must be a contiguous CUDA {self.complex_dtype} tensor [{self.n_gamma}, {b}]")
+                    or tuple(aux.shape) != shp:
+                raise ValueError(f"aux must be a contiguous CUDA {self.complex_dtype} tensor {list(shp)}")
         if not V.is_cuda or V.dtype != self.real_dtype or not V.is_contiguous() or tuple(V.shape) != (nz, ny, nx):
             raise ValueError(f"V must be a contiguous CUDA {self.real_dtype} tensor [{nz}, {ny}, {nx}]")
         return b
@@ -264,9 +274,22 @@ class Context:
         import torch
         return (stream or torch.cuda.current_stream()).cuda_stream
 
+    def aux_shape(self, b):
+        """[n_gamma, b] (order 1: f) or [2, n_gamma, b] (order 2: f then g = df/dt)."""
+        return (2, self.n_gamma, b) if self.order == 2 else (self.n_gamma, b)
+
     def new_aux(self, b):
+        """Zero auxiliary state (order 1 starts there; order 2 needs init_aux)."""
         import torch
-        return torch.zeros((self.n_gamma, b), dtype=self.complex_dtype, device="cuda")
+        return torch.zeros(self.aux_shape(b), dtype=self.complex_dtype, device="cuda")
+
+    def init_aux(self, psi, stream=None):
+        """Consistent auxiliary state at t = 0 for psi (abc_aux_init); None for order 0."""
+        if self.order == 0:
+            return None
+        aux = self.new_aux(psi.shape[0])
+        _check(load().abc_aux_init(self.ctx, psi.data_ptr(), aux.data_ptr(), psi.shape[0], self._stream(stream)))
+        return aux
 
     def step(self, psi, aux, V, dt, stream=None):
         b = self._check_tensors(psi, aux, V)

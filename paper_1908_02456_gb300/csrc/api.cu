@@ -9,6 +9,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "ctx.h"
@@ -30,6 +31,25 @@ using abc::dev::BlockInfo;
 namespace {
 
 inline size_t cplx_bytes(const abc_ctx* c) { return 2 * c->real_bytes; }
+
+// Launch with a programmatic dependency on the preceding kernel of the stream: the
+// kernel may start early and calls griddepcontrol.wait before it reads that kernel's
+// results (inside a captured graph this becomes a programmatic edge).
+// With pdl == false it is an ordinary launch.
+template <typename... K, typename... A>
+void launch_pdl(bool pdl, void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 int upload_tables(abc_ctx* c) {
     const Geometry& g = c->geo;
@@ -67,26 +87,31 @@ int upload_tables(abc_ctx* c) {
 // entry per (class, right-hand side), in ascending adapted offset.
 int upload_matrices(abc_ctx* c) {
     const Geometry& g = c->geo;
+    const bool o2 = c->params.order == 2;
+    const int nseg = o2 ? 4 : 1;
     long long total = 0;
     std::vector<long long> moff(g.cls.size());
-    std::vector<int> lds(g.cls.size());
+    std::vector<int> lds(g.cls.size()), segw(g.cls.size());
     for (size_t k = 0; k < g.cls.size(); ++k) {
-        lds[k] = (g.cls[k].m + 3) & ~3;
+        segw[k] = (g.cls[k].m + 3) & ~3;
+        lds[k] = nseg * segw[k];
         moff[k] = total;
         total += (long long)lds[k] * g.cls[k].m;
     }
-    struct E { int off, m, ld; long long mo; };
+    struct E { int off, m, ld, sw; long long mo; };
     std::vector<E> es;
     for (size_t k = 0; k < g.cls.size(); ++k)
-        for (int e = 0; e < g.cls[k].R; ++e) es.push_back({g.cls[k].moff[e], g.cls[k].m, lds[k], moff[k]});
+        for (int e = 0; e < g.cls[k].R; ++e) es.push_back({g.cls[k].moff[e], g.cls[k].m, lds[k], segw[k], moff[k]});
     std::sort(es.begin(), es.end(), [](const E& a, const E& b) { return a.off < b.off; });
     if ((int)es.size() > dev::MAX_ENTRIES) return fail(ABC_ERR_ARG, "internal: too many block entries");
     c->bi = BlockInfo{};
     c->bi.n = (int)es.size();
+    c->bi.nseg = nseg;
     for (size_t i = 0; i < es.size(); ++i) {
         c->bi.m[i] = es[i].m;
         c->bi.off[i] = es[i].off;
         c->bi.ld[i] = es[i].ld;
+        c->bi.segw[i] = es[i].sw;
         c->bi.mat_off[i] = es[i].mo;
     }
     const size_t eb = cplx_bytes(c);
@@ -95,23 +120,32 @@ int upload_matrices(abc_ctx* c) {
     CUDA_TRY(cudaMemset(c->mat.p, 0, (size_t)total * eb));
     for (size_t k = 0; k < g.cls.size(); ++k) {
         const int m = g.cls[k].m, ld = lds[k];
-        const std::vector<cd>& M = c->blocks.mat[k];
-        if (c->prec == ABC_FP64) {
-            std::vector<double> buf((size_t)2 * ld * m, 0.0);
-            for (int a = 0; a < m; ++a)
+        // row a, segment q: order 2 [B1 | B0 - i A1 | -i A1 | A0] (the g equation with
+        // E phidot = -i E H w - i f substituted); otherwise the single class block
+        auto entry = [&](int q, int a, int b) -> cd {
+            if (!o2) return c->blocks.mat[k][(size_t)a * m + b];
+            const size_t e = (size_t)a * m + b;
+            const cd mi(0.0, -1.0);
+            switch (q) {
+                case 0: return c->blocks.mat2[0][k][e];
+                case 1: return c->blocks.mat2[1][k][e] + mi * c->blocks.mat2[2][k][e];
+                case 2: return mi * c->blocks.mat2[2][k][e];
+                default: return c->blocks.mat2[3][k][e];
+            }
+        };
+        std::vector<double> buf((size_t)2 * ld * m, 0.0);
+        for (int a = 0; a < m; ++a)
+            for (int q = 0; q < nseg; ++q)
                 for (int b = 0; b < m; ++b) {
-                    buf[2 * ((size_t)a * ld + b)] = M[(size_t)a * m + b].real();
-                    buf[2 * ((size_t)a * ld + b) + 1] = M[(size_t)a * m + b].imag();
+                    const cd v = entry(q, a, b);
+                    buf[2 * ((size_t)a * ld + q * segw[k] + b)] = v.real();
+                    buf[2 * ((size_t)a * ld + q * segw[k] + b) + 1] = v.imag();
                 }
+        if (c->prec == ABC_FP64) {
             CUDA_TRY(cudaMemcpy(c->mat.as<char>() + moff[k] * eb, buf.data(), buf.size() * 8, cudaMemcpyHostToDevice));
         } else {
-            std::vector<float> buf((size_t)2 * ld * m, 0.0f);
-            for (int a = 0; a < m; ++a)
-                for (int b = 0; b < m; ++b) {
-                    buf[2 * ((size_t)a * ld + b)] = (float)M[(size_t)a * m + b].real();
-                    buf[2 * ((size_t)a * ld + b) + 1] = (float)M[(size_t)a * m + b].imag();
-                }
-            CUDA_TRY(cudaMemcpy(c->mat.as<char>() + moff[k] * eb, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice));
+            std::vector<float> fb(buf.begin(), buf.end());
+            CUDA_TRY(cudaMemcpy(c->mat.as<char>() + moff[k] * eb, fb.data(), fb.size() * 4, cudaMemcpyHostToDevice));
         }
     }
     return ABC_OK;
@@ -121,18 +155,23 @@ int ensure_workspace(abc_ctx* c) {
     const size_t cb = cplx_bytes(c);
     const size_t b = (size_t)c->params.max_orbitals;
     const size_t phi_b = (size_t)c->nvox * b * cb, aux_b = (size_t)c->geo.n_gamma * b * cb;
+    const size_t state_aux_b = aux_b * (c->params.order == 2 ? 2 : 1);     // order 2: [f | g]
     int st;
     for (int i = 0; i < 2; ++i) {
         if ((st = c->Tp[i].alloc(phi_b))) return st;
-        if ((st = c->Tf[i].alloc(aux_b))) return st;
+        if ((st = c->Tf[i].alloc(state_aux_b))) return st;
     }
     if ((st = c->hat_phi.alloc(aux_b))) return st;
     if ((st = c->hat_f.alloc(aux_b))) return st;
+    if (c->params.order == 2) {
+        if ((st = c->hat_h.alloc(aux_b))) return st;
+        if ((st = c->hat_g.alloc(aux_b))) return st;
+    }
     if ((st = c->tvec.alloc(aux_b))) return st;
     if ((st = c->cnat.alloc(aux_b))) return st;
     if ((st = c->Veff.alloc((size_t)c->nvox * c->real_bytes))) return st;
-    CUDA_TRY(cudaMemset(c->Tf[0].p, 0, aux_b));
-    CUDA_TRY(cudaMemset(c->Tf[1].p, 0, aux_b));
+    CUDA_TRY(cudaMemset(c->Tf[0].p, 0, state_aux_b));
+    CUDA_TRY(cudaMemset(c->Tf[1].p, 0, state_aux_b));
     return ABC_OK;
 }
 
@@ -264,7 +303,9 @@ int build_sym(abc_ctx* c) {
     if ((st = c->sym_seg.alloc(segs.size() * sizeof(int4)))) return st;
     if ((st = c->sym_cta.alloc(cta.size() * sizeof(int)))) return st;
     if ((st = c->sym_rowseg.alloc(rowseg.size() * sizeof(int2)))) return st;
-    if ((st = c->sym_rowpart.alloc(segs.size() * SYM_T * abc::dev::SYM_RMAX * sizeof(float2)))) return st;
+    if ((st = c->sym_rowpart.alloc(segs.size() * SYM_T * abc::dev::SYM_RMAX * abc::dev::SYM_CONSUMERS *
+                                   sizeof(float2))))
+        return st;
     if ((st = c->sym_colpart.alloc((size_t)NT * SYM_T * abc::dev::SYM_RMAX * sizeof(float2)))) return st;
     if ((st = c->err_flag.alloc(sizeof(int)))) return st;
     CUDA_TRY(cudaMemcpy(c->sym_seg.p, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice));
@@ -294,7 +335,7 @@ int build_sym(abc_ctx* c) {
         const int2 rs = rowseg[si.rbase[k] + I];
         const long long t1 = si.tbase[k] + (long long)(I + 1) * (I + 2) / 2 + I;
         const int nk = si.nt[k] - 1 - I;
-        gdesc[i] = make_int4((int)(((long long)rs.x * SYM_T + r) * 3 + e), rs.y - rs.x,
+        gdesc[i] = make_int4((int)((((long long)rs.x * SYM_T + r) * 3 + e) * abc::dev::SYM_CONSUMERS), rs.y - rs.x,
                              nk > 0 ? (int)((t1 * SYM_T + r) * 3 + e) : 0, nk | ((I + 2) << 16));
     }
     if ((st = c->sym_gdesc.alloc(gdesc.size() * sizeof(int4)))) return st;
@@ -443,20 +484,25 @@ struct TRes {
 
 // The boundary contraction t = S x (conj: conj(S) x).
 template <typename T>
-TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaStream_t s) {
+TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaStream_t s,
+                 const void* const* x4 = nullptr) {
     typedef typename dev::C2<T>::t V;
+    dev::XSeg<V> xs{{(const V*)x, nullptr, nullptr, nullptr}};
+    if (x4)
+        for (int q = 0; q < 4; ++q) xs.p[q] = (const V*)x4[q];
     const int n = c->geo.n_gamma;
     TRes res;
     res.t = t;
     prof_begin(c, ABC_KERNEL_CONTRACTION, s);
     if (n_orb == 1 && sizeof(T) == 4 && c->sym) {
-        dev::sym_gemv_tiles<<<c->sym_grid, dev::SYM_THREADS, dev::SYM_SMEM, s>>>(
-            c->si, c->sym_tiles.as<float2>(), c->sym_seg.as<int4>(), c->sym_cta.as<int>(), (const float2*)x,
-            c->sym_rowpart.as<float2>(), c->sym_colpart.as<float2>(), conj, c->l2_keep_tiles, c->err_flag.as<int>());
+        launch_pdl(c->pdl, dev::sym_gemv_tiles, dim3(c->sym_grid), dim3(dev::SYM_THREADS), dev::SYM_SMEM, s, c->si,
+                   c->sym_tiles.as<const float2>(), c->sym_seg.as<const int4>(), c->sym_cta.as<const int>(),
+                   (const float2*)x, c->sym_rowpart.as<float2>(), c->sym_colpart.as<float2>(), conj,
+                   (long long)c->l2_keep_tiles, c->err_flag.as<int>());
         res.gathered = true;
     } else if (n_orb == 1) {
-        dev::gemv_blocks<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(c->bi, n, c->mat.as<V>(),
-                                                                          (const V*)x, (V*)t, conj);
+        dev::gemv_blocks<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(c->bi, n, c->mat.as<V>(), xs, (V*)t,
+                                                                          conj);
     } else if (sizeof(T) == 4 && c->tc) {
         const abc_ctx::TcPlan& pl = c->tc_b[n_orb];
         dev::pack_x_tc<<<dim3((unsigned)pl.cols_cnt, (unsigned)pl.max_nkb), 128, 0, s>>>(
@@ -471,7 +517,7 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
         res.stride = (long long)n * n_orb;
     } else {
         dim3 grid(c->n_tiles, (n_orb + 31) / 32);
-        dev::gemm_blocks_simt<T, 32, 32, 16><<<grid, 256, 0, s>>>(c->bi, n_orb, c->geo.n_gamma, c->mat.as<V>(), (const V*)x,
+        dev::gemm_blocks_simt<T, 32, 32, 16><<<grid, 256, 0, s>>>(c->bi, n_orb, c->geo.n_gamma, c->mat.as<V>(), xs,
                                                                   (V*)t, conj, c->tile_blk.as<int>(), c->tile_row.as<int>());
     }
     prof_end(c, ABC_KERNEL_CONTRACTION, s);
@@ -487,9 +533,9 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
     const unsigned nbk = cell_blocks(c, n_orb);
     if constexpr (sizeof(T) == 4) {
         if (tr.gathered) {
-            dev::bnd_back<T, MODE, true><<<nbk, 128, 0, s>>>(ct, n_orb, s1, a_coef, c->hat_phi.as<Vc>(),
-                                                             c->hat_f.as<Vc>(), nullptr, 1, 0, c->sym_gather,
-                                                             (const Vc*)y_f, (Vc*)out, (Vc*)acc, cdt);
+            launch_pdl(c->pdl, dev::bnd_back<T, MODE, true>, dim3(nbk), dim3(128), 0, s, ct, n_orb, s1, a_coef,
+                       c->hat_phi.as<const Vc>(), c->hat_f.as<const Vc>(), (const Vc*)nullptr, 1, 0LL,
+                       c->sym_gather, (const Vc*)y_f, (Vc*)out, (Vc*)acc, cdt);
             return;
         }
     }
@@ -514,19 +560,32 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
         prof_begin(c, ABC_KERNEL_STENCIL, ss);
         dev::stencil_stage<T><<<stencil_grid(c, n_orb), 256, 0, ss>>>(
             g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)w_phi, (const Vc*)y_phi, V,
-            order == 1 ? (const Vc*)w_f : c->cnat.as<Vc>(), (Vc*)o_phi, cdt);
+            order >= 1 ? (const Vc*)w_f : c->cnat.as<Vc>(), (Vc*)o_phi, cdt);
         prof_end(c, ABC_KERNEL_STENCIL, ss);
     };
-    if (order == 1) {
+    if (order >= 1) {
         cudaEventRecord(c->ev_fork, s);
         cudaStreamWaitEvent(c->side, c->ev_fork, 0);
         stencil(c->side);
     }
+    const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
+    if (order == 2) {
+        // g' = B1 g + (B0 - i A1) f - i A1 E H w + A0 E w  (eq:dynamics2 with E phidot substituted)
+        const dev::Ord2Fwd<T> o2{(const Vc*)w_f + (long long)g.n_gamma * n_orb, V, c->hat_h.as<Vc>(),
+                                 c->hat_g.as<Vc>(), g.nx, g.ny, g.nz, (T)(1.0 / (g.h * g.h))};
+        dev::bnd_forward<T, 2><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi, (const Vc*)w_f,
+                                                   c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), nullptr, (T)0, o2);
+        const void* x4[4] = {c->hat_g.p, c->hat_f.p, c->hat_h.p, c->hat_phi.p};
+        const TRes tr = contraction<T>(c, nullptr, c->tvec.p, n_orb, 0, s, x4);
+        back<T, 3>(c, tr, n_orb, (T)0, (T)0, y_f, o_f, const_cast<void*>(w_f), cdt, s);
+        cudaEventRecord(c->ev_join, c->side);
+        cudaStreamWaitEvent(s, c->ev_join, 0);
+        return;
+    }
     dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
                                                order == 1 ? (const Vc*)w_f : nullptr, c->hat_phi.as<Vc>(),
-                                               c->hat_f.as<Vc>(), nullptr, (T)0);
+                                               c->hat_f.as<Vc>(), nullptr, (T)0, dev::Ord2Fwd<T>{});
     const TRes gathered = contraction<T>(c, order == 1 ? c->hat_f.p : c->hat_phi.p, c->tvec.p, n_orb, 0, s);
-    const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
     if (order == 1) {
         back<T, 0>(c, gathered, n_orb, (T)c->blocks.s, a_coef, y_f, o_f, nullptr, cdt, s);
         cudaEventRecord(c->ev_join, c->side);
@@ -598,7 +657,7 @@ void finish_diag(const abc_ctx* c, double* v, long long rows) {
 int check_run_args(abc_ctx* c, const void* psi, const void* aux, const void* V, int n_orb, double dt) {
     if (!c) return fail(ABC_ERR_ARG, "null context");
     if (!psi || !V) return fail(ABC_ERR_ARG, "null psi or V");
-    if (c->params.order == 1 && !aux) return fail(ABC_ERR_ARG, "order 1 needs the auxiliary buffer");
+    if (c->params.order >= 1 && !aux) return fail(ABC_ERR_ARG, "orders 1 and 2 need the auxiliary buffer");
     if (n_orb < 1 || n_orb > c->params.max_orbitals) return fail(ABC_ERR_ARG, "n_orb outside [1, max_orbitals]");
     if (!(dt > 0.0)) return fail(ABC_ERR_ARG, "dt must be positive");
     return ABC_OK;
@@ -629,7 +688,9 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     st = build_geometry(grid->nx, grid->ny, grid->nz, grid->h, c->geo, err);
     if (st) return fail(st, err);
     c->nvox = c->geo.n_nodes;
-    st = compute_blocks(c->geo, params->order, params->order == 0 ? params->s0 : params->s1, c->blocks, err);
+    st = params->order == 2 ? compute_blocks2(c->geo, params->s2, c->blocks, err)
+                            : compute_blocks(c->geo, params->order, params->order == 0 ? params->s0 : params->s1,
+                                             c->blocks, err);
     if (st) return fail(st, err);
     CUDA_TRY(cudaGetDevice(&c->device));
     if ((st = upload_tables(c.get()))) return st;
@@ -637,8 +698,15 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     if ((st = ensure_workspace(c.get()))) return st;
     if ((st = c->diag.alloc(sizeof(double) * 3 * params->max_orbitals))) return st;
     if ((st = build_tiles(c.get()))) return st;
-    if ((c->prec == ABC_C64_FP32 || c->prec == ABC_C64_3XTF32) && (st = build_sym(c.get()))) return st;
-    if (c->prec == ABC_C64_3XTF32 && (st = build_tc(c.get()))) return st;
+    // the packed symmetric tiles and the tensor-core image hold one m x m block per class
+    // (orders 0, 1); the order-2 rows [B1 | B0 - i A1 | -i A1 | A0] use the full-block kernels
+    const bool one_seg = params->order < 2;
+    if (one_seg && (c->prec == ABC_C64_FP32 || c->prec == ABC_C64_3XTF32) && (st = build_sym(c.get()))) return st;
+    if (one_seg && c->prec == ABC_C64_3XTF32 && (st = build_tc(c.get()))) return st;
+    if (!c->err_flag.p) {
+        if ((st = c->err_flag.alloc(sizeof(int)))) return st;
+        CUDA_TRY(cudaMemset(c->err_flag.p, 0, sizeof(int)));
+    }
     CUDA_TRY(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming));
@@ -743,25 +811,61 @@ extern "C" int abc_run(abc_ctx* ctx, void* psi, void* aux, const void* V, int n_
     return run_impl(ctx, psi, aux, V, n_orb, dt, nsteps, mf, diag_every, diag_out, (cudaStream_t)stream);
 }
 
+namespace {
+template <typename T>
+int aux_init_impl(abc_ctx* c, const void* psi, void* aux, int n_orb, cudaStream_t s) {
+    typedef typename dev::C2<T>::t Vc;
+    const size_t ab = (size_t)c->geo.n_gamma * n_orb * sizeof(Vc);
+    CUDA_TRY(cudaMemsetAsync(aux, 0, ab * (c->params.order == 2 ? 2 : 1), s));
+    if (c->params.order != 2) return ABC_OK;
+    // g(0) = A1 E psi: the contraction row [B1 | B0 - i A1 | -i A1 | A0] applied to
+    // (0, 0, E psi, 0) gives -i A1 E psi; then g = i * that
+    const dev::CellTab<T> ct = cell_tab<T>(c);
+    const unsigned nbk = cell_blocks(c, n_orb);
+    const size_t hb = (size_t)c->geo.n_gamma * n_orb * sizeof(Vc);
+    CUDA_TRY(cudaMemsetAsync(c->hat_g.p, 0, hb, s));
+    dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)psi, nullptr, c->hat_h.as<Vc>(),
+                                               c->hat_f.as<Vc>(), nullptr, (T)0, dev::Ord2Fwd<T>{});
+    const void* x4[4] = {c->hat_g.p, c->hat_g.p, c->hat_h.p, c->hat_g.p};
+    const TRes tr = contraction<T>(c, nullptr, c->tvec.p, n_orb, 0, s, x4);
+    back<T, 1>(c, tr, n_orb, (T)0, (T)0, nullptr, c->cnat.p, nullptr, (T)0, s);
+    const long long n = (long long)c->geo.n_gamma * n_orb;
+    dev::mul_i_into<T><<<nblk(n, 256), 256, 0, s>>>(n, c->cnat.as<Vc>(), (Vc*)aux + n);
+    c->launches += 4;
+    return last_launch_status();
+}
+}  // namespace
+
+extern "C" int abc_aux_init(abc_ctx* ctx, const void* psi, void* aux, int n_orb, void* stream) {
+    if (!ctx || !psi) return fail(ABC_ERR_ARG, "null context or psi");
+    if (n_orb < 1 || n_orb > ctx->params.max_orbitals) return fail(ABC_ERR_ARG, "n_orb outside [1, max_orbitals]");
+    if (ctx->params.order == 0) return ABC_OK;
+    if (!aux) return fail(ABC_ERR_ARG, "null aux");
+    cudaStream_t s = (cudaStream_t)stream;
+    return ctx->prec == ABC_FP64 ? aux_init_impl<double>(ctx, psi, aux, n_orb, s)
+                                 : aux_init_impl<float>(ctx, psi, aux, n_orb, s);
+}
+
 extern "C" int abc_run_host(abc_ctx* ctx, void* psi_host, void* aux_host, const void* V_host, int n_orb, double dt,
                             long long nsteps, const abc_meanfield* mf, int diag_every, double* diag_out) {
     int st = check_run_args(ctx, psi_host, aux_host, V_host, n_orb, dt);
     if (st) return st;
     const size_t cb = cplx_bytes(ctx);
-    const size_t pb = (size_t)ctx->nvox * n_orb * cb, ab = (size_t)ctx->geo.n_gamma * n_orb * cb,
+    const size_t pb = (size_t)ctx->nvox * n_orb * cb,
+                 ab = (size_t)ctx->geo.n_gamma * n_orb * cb * (ctx->params.order == 2 ? 2 : 1),
                  vb = (size_t)ctx->nvox * ctx->real_bytes;
     if (ctx->host_psi.bytes < pb && (st = ctx->host_psi.alloc(pb))) return st;
     if (ctx->host_aux.bytes < ab && (st = ctx->host_aux.alloc(ab))) return st;
     if (ctx->host_V.bytes < vb && (st = ctx->host_V.alloc(vb))) return st;
     cudaStream_t s = ctx->own;
     CUDA_TRY(cudaMemcpyAsync(ctx->host_psi.p, psi_host, pb, cudaMemcpyHostToDevice, s));
-    if (ctx->params.order == 1) CUDA_TRY(cudaMemcpyAsync(ctx->host_aux.p, aux_host, ab, cudaMemcpyHostToDevice, s));
+    if (ctx->params.order >= 1) CUDA_TRY(cudaMemcpyAsync(ctx->host_aux.p, aux_host, ab, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(ctx->host_V.p, V_host, vb, cudaMemcpyHostToDevice, s));
-    st = run_impl(ctx, ctx->host_psi.p, ctx->params.order == 1 ? ctx->host_aux.p : nullptr, ctx->host_V.p, n_orb, dt,
+    st = run_impl(ctx, ctx->host_psi.p, ctx->params.order >= 1 ? ctx->host_aux.p : nullptr, ctx->host_V.p, n_orb, dt,
                   nsteps, mf, diag_every, diag_out, s);
     if (st) return st;
     CUDA_TRY(cudaMemcpyAsync(psi_host, ctx->host_psi.p, pb, cudaMemcpyDeviceToHost, s));
-    if (ctx->params.order == 1) CUDA_TRY(cudaMemcpyAsync(aux_host, ctx->host_aux.p, ab, cudaMemcpyDeviceToHost, s));
+    if (ctx->params.order >= 1) CUDA_TRY(cudaMemcpyAsync(aux_host, ctx->host_aux.p, ab, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return check_device_flag(ctx, s);
 }
@@ -794,12 +898,13 @@ void adj_stage(abc_ctx* c, int n_orb, T cdt, const void* a_phi, const void* a_f,
     const unsigned nbk = cell_blocks(c, n_orb);
     if (c->params.order == 1) {
         dev::bnd_forward<T, 1><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)a_phi, (const Vc*)a_f,
-                                                   c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->cnat.as<Vc>(), a_coef);
+                                                   c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), c->cnat.as<Vc>(), a_coef,
+                                                   dev::Ord2Fwd<T>{});
         const TRes gathered = contraction<T>(c, c->cnat.p, c->tvec.p, n_orb, 1, s);
         back<T, 2>(c, gathered, n_orb, (T)c->blocks.s, a_coef, nullptr, anew_f, acc_f, cdt, s);
     } else {
         dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)a_phi, nullptr, c->hat_phi.as<Vc>(),
-                                                   c->hat_f.as<Vc>(), nullptr, (T)0);
+                                                   c->hat_f.as<Vc>(), nullptr, (T)0, dev::Ord2Fwd<T>{});
         const TRes gathered = contraction<T>(c, c->hat_phi.p, c->tvec.p, n_orb, 1, s);
         back<T, 1>(c, gathered, n_orb, (T)0, (T)0, nullptr, c->cnat.p, nullptr, (T)0, s);
     }
@@ -898,6 +1003,7 @@ extern "C" int abc_adjoint_run(abc_ctx* ctx, const void* psi0, const void* V, in
     if (!J_out || !dJdV) return fail(ABC_ERR_ARG, "null J_out or dJdV");
     if (nsteps < 0) return fail(ABC_ERR_ARG, "nsteps must be >= 0");
     if (ckpt_every < 1) return fail(ABC_ERR_ARG, "ckpt_every must be >= 1");
+    if (ctx->params.order == 2) return fail(ABC_ERR_UNSUPPORTED, "the adjoint covers orders 0 and 1");
     cudaStream_t s = (cudaStream_t)stream;
     if (ctx->prec == ABC_FP64) return adjoint_impl<double>(ctx, psi0, V, n_orb, dt, nsteps, ckpt_every, J_out, dJdV, s);
     return adjoint_impl<float>(ctx, psi0, V, n_orb, dt, nsteps, ckpt_every, J_out, dJdV, s);
@@ -957,7 +1063,7 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
         if (ctx->sym && n_orb == 1) {
             entries = (double)ctx->sym_tiles_n * abc::dev::SYM_T * abc::dev::SYM_T;   // stored tiles, read once
         } else {
-            for (int p = 0; p < ctx->bi.n; ++p) entries += (double)ctx->bi.m[p] * ctx->bi.m[p];
+            for (int p = 0; p < ctx->bi.n; ++p) entries += (double)ctx->bi.nseg * ctx->bi.m[p] * ctx->bi.m[p];
         }
         *bytes = entries * cb + 2.0 * ctx->geo.n_gamma * n_orb * cb;
     } else if (kernel == ABC_KERNEL_STENCIL) {
@@ -976,6 +1082,11 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
         return ABC_OK;
     }
+    if (key == ABC_TUNE_PDL) {
+        ctx->pdl = value != 0;
+        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        return ABC_OK;
+    }
     return fail(ABC_ERR_ARG, "unknown tuning key");
 }
 
@@ -983,6 +1094,7 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (!ctx || !value) return fail(ABC_ERR_ARG, "null argument");
     if (key == ABC_TUNE_L2_KEEP_TILES) { *value = ctx->l2_keep_tiles; return ABC_OK; }
     if (key == ABC_TUNE_TILE_COUNT) { *value = ctx->sym ? ctx->sym_tiles_n : 0; return ABC_OK; }
+    if (key == ABC_TUNE_PDL) { *value = ctx->pdl ? 1 : 0; return ABC_OK; }
     return fail(ABC_ERR_ARG, "unknown tuning key");
 }
 

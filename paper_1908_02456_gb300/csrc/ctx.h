@@ -58,7 +58,7 @@ struct abc_ctx {
     abc::DevBuf tile_blk, tile_row;   // row tiles (block, first row) of the multi-orbital contraction
     int n_tiles = 0;
     // workspace
-    abc::DevBuf Tp[2], Tf[2], hat_phi, hat_f, tvec, cnat, Veff, diag;
+    abc::DevBuf Tp[2], Tf[2], hat_phi, hat_f, hat_h, hat_g, tvec, cnat, Veff, diag;
     abc::DevBuf host_psi, host_aux, host_V;   // device copies for abc_run_host
     cudaStream_t own = nullptr;
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
@@ -74,6 +74,7 @@ struct abc_ctx {
     int sym_grid = 0;
     long long sym_tiles_n = 0;
     long long l2_keep_tiles = 0;     // tiles streamed with evict_last (tuning)
+    bool pdl = false;                // programmatic dependent launch of the contraction and gather (tuning)
     double sym_balance = 1.0;        // work weight per right-hand side in the tile partition
     abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
     abc::dev::SymGather sym_gather{};   // partial-sum view for the back transform
@@ -99,6 +100,7 @@ inline dev::CellTab<T> cell_tab(const abc_ctx* c) {
     dev::CellTab<T> t;
     t.n_cells = c->geo.n_cells;
     t.ng = c->geo.n_gamma;
+    t.n_gamma = c->geo.n_gamma;
     t.out = c->cell_out.as<int>();
     t.type = c->cell_type.as<int>();
     t.coef_f = c->cell_coef_f.as<T>();

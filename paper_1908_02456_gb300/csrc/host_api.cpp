@@ -35,9 +35,17 @@ namespace abc {
 int check_params(const abc_grid* grid, const abc_params* params) {
     if (!grid || !params) return fail(ABC_ERR_ARG, "null grid or params");
     if (grid->radius != 1) return fail(ABC_ERR_UNSUPPORTED, "only the 3-point stencil (radius 1) is built");
-    if (params->order != 0 && params->order != 1) return fail(ABC_ERR_ARG, "order must be 0 or 1");
-    const double s = params->order == 0 ? params->s0 : params->s1;
-    if (!(s > 0.0)) return fail(ABC_ERR_ARG, "interpolation point must be > 0");
+    if (params->order < 0 || params->order > 2) return fail(ABC_ERR_ARG, "order must be 0, 1 or 2");
+    if (params->order == 2) {
+        for (int j = 0; j < 4; ++j) {
+            if (!(params->s2[j] > 0.0)) return fail(ABC_ERR_ARG, "interpolation point must be > 0");
+            for (int i = 0; i < j; ++i)
+                if (params->s2[i] == params->s2[j]) return fail(ABC_ERR_ARG, "order-2 points must be distinct");
+        }
+    } else {
+        const double s = params->order == 0 ? params->s0 : params->s1;
+        if (!(s > 0.0)) return fail(ABC_ERR_ARG, "interpolation point must be > 0");
+    }
     if (params->precision < ABC_FP64 || params->precision > ABC_C64_3XTF32)
         return fail(ABC_ERR_ARG, "unknown precision");
     if (params->precision == ABC_C64_SPLIT_BF16)
@@ -59,7 +67,8 @@ extern "C" int abc_host_matrices(const abc_grid* grid, const abc_params* params,
     if (st) return fail(st, err);
     if (bytes < (size_t)16 * g.n_gamma * g.n_gamma) return fail(ABC_ERR_ARG, "destination too small");
     Blocks b;
-    st = compute_blocks(g, params->order, params->order == 0 ? params->s0 : params->s1, b, err);
+    st = params->order == 2 ? compute_blocks2(g, params->s2, b, err)
+                            : compute_blocks(g, params->order, params->order == 0 ? params->s0 : params->s1, b, err);
     if (st) return fail(st, err);
     st = dense_natural(g, b, which, reinterpret_cast<cd*>(host_dst), err);
     if (st) return fail(st, err);

@@ -104,7 +104,15 @@ struct Blocks {
     int order = 0;
     double s = 0.0;
     std::vector<std::vector<cd>> mat;
+    // order 2: per class the four coefficient blocks B1, B0, A1, A0 (row-major m x m,
+    // general complex), and the interpolation points
+    std::vector<std::vector<cd>> mat2[4];
+    double s2[4] = {0, 0, 0, 0};
 };
+
+// Order-2 coefficients (Sec. 3.3): per class, K_k(s_j) at the four points by the
+// order-0 route, then [B1 B0 A1 A0] from s_j^2 K_j = s_j B1 K_j + B0 K_j + s_j A1 + A0.
+int compute_blocks2(const Geometry& g, const double s[4], Blocks& b, std::string& err);
 
 // Dense block-b matrix (row-major m_b x m_b, parity-adapted numbering) from the
 // irreducible blocks whose base is b: sum over classes and components of W blk W^T.

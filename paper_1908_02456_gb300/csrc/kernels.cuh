@@ -9,6 +9,12 @@
 namespace abc {
 namespace dev {
 
+// Programmatic dependent launch: wait until the preceding kernel of the stream has
+// completed and its writes are visible (a no-op without a programmatic dependency),
+// and allow the next kernel to be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename T> struct C2;
 template <> struct C2<float> { typedef float2 t; };
 template <> struct C2<double> { typedef double2 t; };
@@ -24,10 +30,19 @@ template <typename T> __device__ __forceinline__ typename C2<T>::t mk(T re, T im
 constexpr int MAX_ENTRIES = 24;
 struct BlockInfo {
     int n;                            // number of entries
+    int nseg;                         // input segments per row: 1, or 4 for order 2 ([B1 | B0 - iA1 | -iA1 | A0])
     int m[MAX_ENTRIES];               // block sizes
     int off[MAX_ENTRIES];             // first adapted index of each entry (ascending)
     int ld[MAX_ENTRIES];              // row stride (complex elements) of the matrix
+    int segw[MAX_ENTRIES];            // stride of the segments inside a row (multiple of 4)
     long long mat_off[MAX_ENTRIES];   // first element of the matrix in the buffer
+};
+
+// Input vectors of the contraction: segment q of a row multiplies x.p[q] (adapted,
+// orbital-major); only p[0] is used when nseg = 1.
+template <typename V>
+struct XSeg {
+    const V* p[4];
 };
 
 // Cell tables of the boundary transforms (kernel parameter).  A cell is a set of
@@ -39,6 +54,7 @@ template <typename T>
 struct CellTab {
     int n_cells;
     int ng;                // adapted vectors are orbital-major: element (j, orbital) at orbital * ng + j
+    int n_gamma;           // natural boundary vectors: [n_gamma][n_orb]
     const int* out;        // [n_cells][8 o][8 p] adapted index or -1
     const int* type;       // [n_cells][8 p] coefficient matrix id
     const T* coef_f;       // [types][8 o][8 s] forward coefficients, slot scale folded in
@@ -52,13 +68,14 @@ struct CellTab {
 // Partial sums of the tiled one-orbital contraction, gathered by the back transform:
 // t[j] = sum of the row parts of the segments of (class c, tile row I) + the column
 // parts of the tiles (c, K, I), K > I (fixed order).  desc is indexed like the cell
-// output table (cell * 64 + 8 o + p): x = first row-part element, y = number of row
-// segments (consecutive, 192 elements apart), z = column-part element of K = I + 1,
+// output table (cell * 64 + 8 o + p): x = first row-part element (8 consecutive
+// values, one per consumer warp), y = number of row segments (consecutive, 1536
+// elements apart), z = column-part element of K = I + 1,
 // w = (number of K) | ((I + 2) << 16); the column-part element of K + 1 is that of K
 // plus (K + 1) * 192.
 struct SymGather {
     const int4* desc;
-    const float2* rowpart;       // [segment][64][3]
+    const float2* rowpart;       // [segment][64][3][8 warps]
     const float2* colpart;       // [tile][64][3]
 };
 
@@ -100,15 +117,29 @@ template <typename V> __device__ __forceinline__ V wht8_lanes(V v, int g) {
 // scaled coefficients.
 //   MODE 0: hat_phi (and hat_f when w_f is given)
 //   MODE 1: hat_phi, hat_f and u = (+i a_coef c) hat_f  (order-1 adjoint, A^H f)
+//   MODE 2: order 2: hat_phi, hat_f, and (in o2) the transforms of H_{I,I} w_phi at the
+//           boundary nodes (hat_h) and of the g part of the auxiliary state (hat_g)
+// Order-2 data (MODE 2 only).
+template <typename T>
+struct Ord2Fwd {
+    const typename C2<T>::t* w_g;   // g part of the stage input, natural [n_gamma][n_orb]
+    const T* V;                      // potential [nz][ny][nx]
+    typename C2<T>::t* hat_h;
+    typename C2<T>::t* hat_g;
+    int nx, ny, nz;
+    T inv_h2;
+};
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, long long nvox,
                                                    const typename C2<T>::t* __restrict__ w_phi,
                                                    const typename C2<T>::t* __restrict__ w_f,
                                                    typename C2<T>::t* __restrict__ hat_phi,
                                                    typename C2<T>::t* __restrict__ hat_f,
-                                                   typename C2<T>::t* __restrict__ u, T a_coef) {
+                                                   typename C2<T>::t* __restrict__ u, T a_coef, Ord2Fwd<T> o2) {
     typedef typename C2<T>::t V;
     __shared__ V sp[2][8][8], sf[2][8][8];     // [group][slot][parity]
+    __shared__ V sh[MODE == 2 ? 2 : 1][8][8], sg2[MODE == 2 ? 2 : 1][8][8];
     const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
     const long long gidx = (long long)blockIdx.x * 2 + grp;
     const bool live = gidx < (long long)ct.n_cells * n_orb;
@@ -119,10 +150,26 @@ __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, lon
     const int node = live ? ct.node[cell * 64 + t] : 0;
     const int jj = live ? ct.out[cell * 64 + t] : -1;          // output o = s of parity p = g
     const int ty = live ? ct.type[cell * 8 + g] : 0;
-    V xp = mk<T>(0, 0), xf = mk<T>(0, 0);
+    V xp = mk<T>(0, 0), xf = mk<T>(0, 0), xh = mk<T>(0, 0), xg = mk<T>(0, 0);
     if (gi >= 0) {
-        xp = w_phi[(long long)j * nvox + node];
+        const V* wo = w_phi + (long long)j * nvox;
+        xp = wo[node];
         if (w_f) xf = w_f[(long long)gi * n_orb + j];
+        if constexpr (MODE == 2) {
+            // (H_{I,I} w)(node) with the neighbours outside the box omitted
+            const int nx = o2.nx, ny = o2.ny, nxy = nx * ny;
+            const int i = node % nx, jy = (node / nx) % ny, k = node / nxy;
+            T sr = 0, si = 0;
+            if (i > 0) { sr += wo[node - 1].x; si += wo[node - 1].y; }
+            if (i < nx - 1) { sr += wo[node + 1].x; si += wo[node + 1].y; }
+            if (jy > 0) { sr += wo[node - nx].x; si += wo[node - nx].y; }
+            if (jy < ny - 1) { sr += wo[node + nx].x; si += wo[node + nx].y; }
+            if (k > 0) { sr += wo[node - nxy].x; si += wo[node - nxy].y; }
+            if (k < o2.nz - 1) { sr += wo[node + nxy].x; si += wo[node + nxy].y; }
+            const T d = (T)3 * o2.inv_h2 + o2.V[node];
+            xh = mk<T>(d * xp.x - (T)0.5 * o2.inv_h2 * sr, d * xp.y - (T)0.5 * o2.inv_h2 * si);
+            xg = o2.w_g[(long long)gi * n_orb + j];
+        }
     }
     T cf[8];
 #pragma unroll
@@ -130,19 +177,33 @@ __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, lon
     const T c_cell = (MODE == 1 && live) ? (T)ct.cell_c[cell] : (T)0;
     xp = wht8_lanes(xp, g);
     if (w_f) xf = wht8_lanes(xf, g);
+    if constexpr (MODE == 2) {
+        xh = wht8_lanes(xh, g);
+        xg = wht8_lanes(xg, g);
+        sh[grp][s][g] = xh;
+        sg2[grp][s][g] = xg;
+    }
     sp[grp][s][g] = xp;
     sf[grp][s][g] = xf;
     __syncthreads();
     if (jj < 0) return;
-    V ap = mk<T>(0, 0), af = mk<T>(0, 0);
+    V ap = mk<T>(0, 0), af = mk<T>(0, 0), ah = mk<T>(0, 0), ag = mk<T>(0, 0);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         ap.x += cf[q] * sp[grp][q][g].x; ap.y += cf[q] * sp[grp][q][g].y;
         af.x += cf[q] * sf[grp][q][g].x; af.y += cf[q] * sf[grp][q][g].y;
+        if constexpr (MODE == 2) {
+            ah.x += cf[q] * sh[grp][q][g].x; ah.y += cf[q] * sh[grp][q][g].y;
+            ag.x += cf[q] * sg2[grp][q][g].x; ag.y += cf[q] * sg2[grp][q][g].y;
+        }
     }
     const long long e = (long long)j * ct.ng + jj;
     hat_phi[e] = ap;
     if (w_f) hat_f[e] = af;
+    if constexpr (MODE == 2) {
+        o2.hat_h[e] = ah;
+        o2.hat_g[e] = ag;
+    }
     if (MODE == 1) {
         const T ac = a_coef * c_cell;
         u[e] = mk<T>(-ac * af.y, ac * af.x);
@@ -157,9 +218,15 @@ __device__ __forceinline__ float2 sym_gather(const SymGather& sg, int4 d) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
     for (int q = 0; q < d.y; ++q) {
-        const float2 v = sg.rowpart[d.x + q * 192];
-        acc[0].x += v.x;
-        acc[0].y += v.y;
+        const float4* rp = reinterpret_cast<const float4*>(sg.rowpart + d.x + (size_t)q * 1536);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {                  // the 8 warps' partials of the segment
+            const float4 v = rp[w];
+            acc[2 * w].x += v.x;
+            acc[2 * w].y += v.y;
+            acc[2 * w + 1].x += v.z;
+            acc[2 * w + 1].y += v.w;
+        }
     }
     const int nk = d.w & 0xffff;
     int e = d.z, step = d.w >> 16;
@@ -190,6 +257,9 @@ __device__ __forceinline__ float2 sym_gather(const SymGather& sg, int4 d) {
 //                             (B f + A E phi with B = s1 I - A S, t = S f_hat)
 //   MODE 1 (order 0):         x = t  (t = M phi_hat, or conj(M) phi_hat)
 //   MODE 2 (order-1 adjoint): x = s1 f_hat - t + i phi_hat  (t = conj(S) u)
+//   MODE 3 (order-2 step):    x = t  (t = B1 g + (B0 - i A1) f - i A1 E H w + A0 E phi, the
+//                             derivative of g); y_f / out / acc are then the step-start,
+//                             stage-output and stage-input auxiliary states [f | g]
 // with t read from t_in (the sum of its nsplit arrays split_stride apart), or
 // gathered from the tiled contraction's partial sums (GATHER);
 // then thread (s, p) undoes the mixing with the scaled transposed coefficients, the
@@ -198,6 +268,7 @@ __device__ __forceinline__ float2 sym_gather(const SymGather& sg, int4 d) {
 // lane that owns the node (table wr) writes:
 //   MODE 0: out[e] = y_f[e] + cdt v      MODE 1: out[e] = v
 //   MODE 2: out[e] = cdt v, acc[e] += cdt v
+//   MODE 3: out_f[e] = y_f[e] + cdt w_g[e], out_g[e] = y_g[e] + cdt v  (f' = g, g' = v)
 // (only the owner reads y_f / acc there, so the update in place is race-free).
 template <typename T, int MODE, bool GATHER>
 __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, T a_coef,
@@ -224,10 +295,17 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
     T cf[8];
 #pragma unroll
     for (int o = 0; o < 8; ++o) cf[o] = live ? ct.coef_bt[(long long)ty * 64 + s * 8 + o] : (T)0;
-    V yv = mk<T>(0, 0);
+    pdl_wait();                                // the tables above do not depend on the preceding kernel
+    V yv = mk<T>(0, 0), yg = mk<T>(0, 0), wg = mk<T>(0, 0);
     const long long ew = (long long)(wr >= 0 ? wr : 0) * n_orb + j;
+    const long long gofs = (long long)ct.n_gamma * n_orb;      // g part of an order-2 auxiliary state
     if (wr >= 0 && MODE == 0) yv = y_f[ew];
     if (wr >= 0 && MODE == 2) yv = acc[ew];
+    if (wr >= 0 && MODE == 3) {
+        yv = y_f[ew];
+        yg = y_f[gofs + ew];
+        wg = acc[gofs + ew];
+    }
     V x = mk<T>(0, 0);
     if (jj >= 0) {
         const long long e = (long long)j * ct.ng + jj;
@@ -248,7 +326,7 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
             const V fv = hat_f[e], pv = hat_phi[e];
             const T dr = pv.x - tv.x, di = pv.y - tv.y;
             x = mk<T>(s1 * fv.x + a * di, s1 * fv.y - a * dr);
-        } else if (MODE == 1) {
+        } else if (MODE == 1 || MODE == 3) {
             x = tv;
         } else {
             const V fv = hat_f[e], pv = hat_phi[e];
@@ -269,10 +347,13 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
         out[ew] = mk<T>(yv.x + cdt * v.x, yv.y + cdt * v.y);
     } else if (MODE == 1) {
         out[ew] = v;
-    } else {
+    } else if (MODE == 2) {
         const T nr = cdt * v.x, ni = cdt * v.y;
         out[ew] = mk<T>(nr, ni);
         acc[ew] = mk<T>(yv.x + nr, yv.y + ni);
+    } else {
+        out[ew] = mk<T>(yv.x + cdt * wg.x, yv.y + cdt * wg.y);
+        out[gofs + ew] = mk<T>(yg.x + cdt * v.x, yg.y + cdt * v.y);
     }
 }
 
@@ -300,43 +381,45 @@ __device__ __forceinline__ int find_block(const BlockInfo& bi, int q) {
 
 template <typename T>
 __global__ void gemv_blocks(BlockInfo bi, int n_rows, const typename C2<T>::t* __restrict__ mat,
-                            const typename C2<T>::t* __restrict__ x, typename C2<T>::t* __restrict__ y, int conj) {
+                            XSeg<typename C2<T>::t> xs, typename C2<T>::t* __restrict__ y, int conj) {
     const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= n_rows) return;
     const int p = find_block(bi, warp);
     const int a = warp - bi.off[p];
     const int m = bi.m[p];
-    const typename C2<T>::t* row = mat + bi.mat_off[p] + (long long)a * bi.ld[p];
-    const typename C2<T>::t* xv = x + bi.off[p];
     T sr = 0, si = 0;
     const T cs = conj ? (T)-1 : (T)1;     // conj: y = conj(S conj(x)) = conj(S) x
-    if constexpr (sizeof(T) == 4) {
-        // two complex per lane per load (row start 16-byte aligned: ld, mat_off even)
-        const float4* row4 = reinterpret_cast<const float4*>(row);
-        const int m2 = m >> 1;
-        int c = lane;
+    for (int q = 0; q < bi.nseg; ++q) {
+        const typename C2<T>::t* row = mat + bi.mat_off[p] + (long long)a * bi.ld[p] + (long long)q * bi.segw[p];
+        const typename C2<T>::t* xv = xs.p[q] + bi.off[p];
+        if constexpr (sizeof(T) == 4) {
+            // two complex per lane per load (segment start 16-byte aligned: ld, segw, mat_off multiples of 4)
+            const float4* row4 = reinterpret_cast<const float4*>(row);
+            const int m2 = m >> 1;
+            int c = lane;
 #pragma unroll 4
-        for (; c < m2; c += 32) {
-            const float4 sv = __ldcs(row4 + c);
-            const typename C2<T>::t x0 = xv[2 * c], x1 = xv[2 * c + 1];
-            const T sy0 = cs * sv.y, sy1 = cs * sv.w;
-            sr += sv.x * x0.x - sy0 * x0.y + sv.z * x1.x - sy1 * x1.y;
-            si += sv.x * x0.y + sy0 * x0.x + sv.z * x1.y + sy1 * x1.x;
-        }
-        if ((m & 1) && lane == 0) {
-            const typename C2<T>::t sv = row[m - 1], xx = xv[m - 1];
-            const T sy = cs * sv.y;
-            sr += sv.x * xx.x - sy * xx.y;
-            si += sv.x * xx.y + sy * xx.x;
-        }
-    } else {
+            for (; c < m2; c += 32) {
+                const float4 sv = __ldcs(row4 + c);
+                const typename C2<T>::t x0 = xv[2 * c], x1 = xv[2 * c + 1];
+                const T sy0 = cs * sv.y, sy1 = cs * sv.w;
+                sr += sv.x * x0.x - sy0 * x0.y + sv.z * x1.x - sy1 * x1.y;
+                si += sv.x * x0.y + sy0 * x0.x + sv.z * x1.y + sy1 * x1.x;
+            }
+            if ((m & 1) && lane == 0) {
+                const typename C2<T>::t sv = row[m - 1], xx = xv[m - 1];
+                const T sy = cs * sv.y;
+                sr += sv.x * xx.x - sy * xx.y;
+                si += sv.x * xx.y + sy * xx.x;
+            }
+        } else {
 #pragma unroll 4
-        for (int c = lane; c < m; c += 32) {
-            const typename C2<T>::t sv = row[c], xx = xv[c];
-            const T sy = cs * sv.y;
-            sr += sv.x * xx.x - sy * xx.y;
-            si += sv.x * xx.y + sy * xx.x;
+            for (int c = lane; c < m; c += 32) {
+                const typename C2<T>::t sv = row[c], xx = xv[c];
+                const T sy = cs * sv.y;
+                sr += sv.x * xx.x - sy * xx.y;
+                si += sv.x * xx.y + sy * xx.x;
+            }
         }
     }
     sr = warp_sum(sr);
@@ -350,7 +433,7 @@ __global__ void gemv_blocks(BlockInfo bi, int n_rows, const typename C2<T>::t* _
 // --------------------------------------------------------------------------
 template <typename T, int BM, int BN, int BK>
 __global__ void gemm_blocks_simt(BlockInfo bi, int n_orb, int ng, const typename C2<T>::t* __restrict__ mat,
-                                 const typename C2<T>::t* __restrict__ X, typename C2<T>::t* __restrict__ Y,
+                                 XSeg<typename C2<T>::t> xs, typename C2<T>::t* __restrict__ Y,
                                  int conj, const int* __restrict__ tile_block, const int* __restrict__ tile_row) {
     typedef typename C2<T>::t V;
     __shared__ V As[BK][BM + 1];
@@ -359,8 +442,7 @@ __global__ void gemm_blocks_simt(BlockInfo bi, int n_orb, int ng, const typename
     const int row0 = tile_row[blockIdx.x];          // local row in block p
     const int col0 = blockIdx.y * BN;
     const int m = bi.m[p];
-    const V* S = mat + bi.mat_off[p];
-    const V* Xp = X + bi.off[p];                          // column gc at Xp[gc * ng]
+    const V* S0 = mat + bi.mat_off[p];
     const int tx = threadIdx.x % BN, ty = threadIdx.x / BN;   // BN columns, (nthr/BN) row groups
     constexpr int NT = 256;
     constexpr int RPT = BM / (NT / BN);                       // rows per thread
@@ -368,7 +450,10 @@ __global__ void gemm_blocks_simt(BlockInfo bi, int n_orb, int ng, const typename
 #pragma unroll
     for (int i = 0; i < RPT; ++i) accr[i] = acci[i] = 0;
     const T cs = conj ? (T)-1 : (T)1;
+    for (int q = 0; q < bi.nseg; ++q)
     for (int k0 = 0; k0 < m; k0 += BK) {
+        const V* S = S0 + (long long)q * bi.segw[p];
+        const V* Xp = xs.p[q] + bi.off[p];                // column gc at Xp[gc * ng]
         for (int e = threadIdx.x; e < BM * BK; e += NT) {
             const int rr = e / BK, kk = e % BK;
             const int gr = row0 + rr, gk = k0 + kk;
@@ -596,6 +681,15 @@ __global__ void grad_accum(long long nvox, int n_orb, const typename C2<T>::t* _
         s += (double)av.x * wv.y - (double)av.y * wv.x;
     }
     grad[n] += 2.0 * coef * s;
+}
+
+// y = i x
+template <typename T>
+__global__ void mul_i_into(long long n, const typename C2<T>::t* __restrict__ x, typename C2<T>::t* __restrict__ y) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const typename C2<T>::t v = x[i];
+    y[i] = mk<T>(-v.y, v.x);
 }
 
 // adjoint of J = sum_j (1 - h^3 |phi_j|^2):  a_phi = -h^3 phi

@@ -82,15 +82,16 @@ void step_with_scratch(const abc_ctx* c, void* psi, void* aux, const void* V, in
         const T cdt = (T)(cs[st] * dt);
         abc::dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)in_p,
                                                         order == 1 ? (const Vc*)in_f : nullptr, hat_phi, hat_f,
-                                                        nullptr, (T)0);
+                                                        nullptr, (T)0, abc::dev::Ord2Fwd<T>{});
         const Vc* x = order == 1 ? hat_f : hat_phi;
         if (n_orb == 1) {
-            abc::dev::gemv_blocks<T><<<nblk((long long)g.n_gamma * 32, 256), 256, 0, s>>>(c->bi, g.n_gamma,
-                                                                                         c->mat.as<Vc>(), x, tvec, 0);
+            abc::dev::gemv_blocks<T><<<nblk((long long)g.n_gamma * 32, 256), 256, 0, s>>>(
+                c->bi, g.n_gamma, c->mat.as<Vc>(), abc::dev::XSeg<Vc>{{x, nullptr, nullptr, nullptr}}, tvec, 0);
         } else {
             dim3 grid(c->n_tiles, (n_orb + 31) / 32);
             abc::dev::gemm_blocks_simt<T, 32, 32, 16><<<grid, 256, 0, s>>>(
-                c->bi, n_orb, g.n_gamma, c->mat.as<Vc>(), x, tvec, 0, c->tile_blk.as<int>(), c->tile_row.as<int>());
+                c->bi, n_orb, g.n_gamma, c->mat.as<Vc>(), abc::dev::XSeg<Vc>{{x, nullptr, nullptr, nullptr}}, tvec, 0,
+                c->tile_blk.as<int>(), c->tile_row.as<int>());
         }
         const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
         if (order == 1)
@@ -117,6 +118,7 @@ extern "C" int abc_step_noalloc(const abc_ctx* ctx, void* psi, void* aux, const 
     if (ctx->params.order == 1 && !aux) return abc::fail(ABC_ERR_ARG, "order 1 needs the auxiliary buffer");
     if (n_orb < 1 || n_orb > ctx->params.max_orbitals) return abc::fail(ABC_ERR_ARG, "n_orb outside [1, max_orbitals]");
     if (!(dt > 0.0)) return abc::fail(ABC_ERR_ARG, "dt must be positive");
+    if (ctx->params.order == 2) return abc::fail(ABC_ERR_UNSUPPORTED, "abc_step_noalloc covers orders 0 and 1");
     if (ctx->prec != ABC_FP64 && ctx->prec != ABC_C64_FP32)
         return abc::fail(ABC_ERR_UNSUPPORTED, "abc_step_noalloc covers the ABC_FP64 and ABC_C64_FP32 forms");
     const size_t cb = 2 * ctx->real_bytes;

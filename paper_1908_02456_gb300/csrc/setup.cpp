@@ -424,38 +424,11 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
     return ABC_OK;
 }
 
-// Dense natural-order matrices from the parity blocks: with U[g r, (r,p)] =
-// chi_p(g) sqrt(|H_r|/8) (orthogonal), S_nat = U S_adapted U^T.
-int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::string& err) {
+// Natural-order dense matrix (row-major n_gamma^2) from the blocks of the base
+// parities in the parity-adapted numbering: with U[g r, (r,p)] = chi_p(g) sqrt(|H_r|/8)
+// (orthogonal), X_nat = U X_adapted U^T.
+static int natural_from_blocks(const Geometry& g, const std::vector<cd>* blk, cd* out) {
     const int n = g.n_gamma;
-    const double h4 = std::pow(g.h, 4);
-    std::fill(out, out + (size_t)n * n, cd(0.0, 0.0));
-    if (which == ABC_MAT_A || which == ABC_MAT_Q) {
-        if (b.order != 1) { err = "A and Q exist for order 1 only"; return ABC_ERR_ARG; }
-        for (int i = 0; i < n; ++i)
-            out[(size_t)i * n + i] = which == ABC_MAT_A ? cd(0.0, -g.gamma_c[i] / (4.0 * h4))
-                                                        : cd(4.0 * h4 / g.gamma_c[i], 0.0);
-        return ABC_OK;
-    }
-    if (which == ABC_MAT_M && b.order != 0) { err = "M exists for order 0 only"; return ABC_ERR_ARG; }
-    if (which == ABC_MAT_B && b.order != 1) { err = "B exists for order 1 only"; return ABC_ERR_ARG; }
-    if (which != ABC_MAT_K && which != ABC_MAT_M && which != ABC_MAT_B) { err = "unknown matrix"; return ABC_ERR_ARG; }
-    // class blocks to expand: M_k (order 0) / K_k = S_k^{-1} (order 1, K) / S_k (order 1, B)
-    std::vector<std::vector<cd>> cb(b.mat);
-    if (b.order == 1 && which == ABC_MAT_K) {
-        for (size_t ki = 0; ki < g.cls.size(); ++ki) {
-            const int m = g.cls[ki].m;
-            std::vector<cd> F(b.mat[ki]), Z((size_t)m * m, cd(0.0, 0.0));
-            std::vector<int> piv(m);
-            for (int i = 0; i < m; ++i) Z[(size_t)i * m + i] = 1.0;
-            if (zgetrf(m, F.data(), m, piv.data())) { err = "S block singular"; return ABC_ERR_SINGULAR; }
-            zgetrs(m, m, F.data(), m, piv.data(), Z.data(), m);  // S symmetric: row/col order irrelevant
-            cb[ki] = Z;
-        }
-    }
-    std::vector<cd> blk[8];
-    for (int p = 0; p < 8; ++p)
-        if (g.base_of[p] == p && g.m[p]) expand_base_block(g, p, cb, blk[p]);
     const int R = g.n_rep;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int ri = 0; ri < R; ++ri) {
@@ -477,6 +450,102 @@ int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::s
             }
         }
     }
+    return ABC_OK;
+}
+
+int compute_blocks2(const Geometry& g, const double s[4], Blocks& out, std::string& err) {
+    Blocks Kj[4];
+    for (int j = 0; j < 4; ++j) {
+        const int st = compute_blocks(g, 0, s[j], Kj[j], err);
+        if (st) return st;
+    }
+    out = Blocks();
+    out.order = 2;
+    out.s = s[0];
+    for (int j = 0; j < 4; ++j) out.s2[j] = s[j];
+    const size_t nc = g.cls.size();
+    for (int q = 0; q < 4; ++q) out.mat2[q].resize(nc);
+    for (size_t k = 0; k < nc; ++k) {
+        const int m = g.cls[k].m, n4 = 4 * m;
+        // M (4m x 4m) row-major: block column j = (s_j K_j; K_j; s_j I; I); Y (m x 4m)
+        // row-major: block j = s_j^2 K_j.  X M = Y  <=>  M^T X^T = Y^T, and a row-major
+        // array read column-major is the transpose, so the column-major solver is
+        // applied to M's row-major buffer with Y's row-major buffer as right-hand sides.
+        std::vector<cd> M((size_t)n4 * n4, cd(0.0, 0.0)), Y((size_t)m * n4, cd(0.0, 0.0));
+        for (int j = 0; j < 4; ++j) {
+            const std::vector<cd>& K = Kj[j].mat[k];
+            for (int r = 0; r < m; ++r)
+                for (int c = 0; c < m; ++c) {
+                    const cd v = K[(size_t)r * m + c];
+                    M[(size_t)r * n4 + j * m + c] = s[j] * v;
+                    M[(size_t)(m + r) * n4 + j * m + c] = v;
+                    Y[(size_t)r * n4 + j * m + c] = s[j] * s[j] * v;
+                }
+            for (int r = 0; r < m; ++r) {
+                M[(size_t)(2 * m + r) * n4 + j * m + r] = s[j];
+                M[(size_t)(3 * m + r) * n4 + j * m + r] = 1.0;
+            }
+        }
+        std::vector<int> piv(n4);
+        const int info = zgetrf(n4, M.data(), n4, piv.data());
+        if (info) {
+            char buf[128];
+            std::snprintf(buf, sizeof(buf), "order-2 interpolation system of class %zu singular at pivot %d", k, info);
+            err = buf;
+            return ABC_ERR_SINGULAR;
+        }
+        zgetrs(n4, m, M.data(), n4, piv.data(), Y.data(), n4);     // Y now holds X row-major (m x 4m)
+        for (int q = 0; q < 4; ++q) {
+            std::vector<cd>& D = out.mat2[q][k];
+            D.assign((size_t)m * m, cd(0.0, 0.0));
+            for (int r = 0; r < m; ++r)
+                for (int c = 0; c < m; ++c) D[(size_t)r * m + c] = Y[(size_t)r * n4 + q * m + c];
+        }
+    }
+    return ABC_OK;
+}
+
+// Dense natural-order matrices from the parity blocks: with U[g r, (r,p)] =
+// chi_p(g) sqrt(|H_r|/8) (orthogonal), S_nat = U S_adapted U^T.
+int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::string& err) {
+    const int n = g.n_gamma;
+    const double h4 = std::pow(g.h, 4);
+    std::fill(out, out + (size_t)n * n, cd(0.0, 0.0));
+    if (which == ABC_MAT_A || which == ABC_MAT_Q) {
+        if (b.order != 1) { err = "A and Q exist for order 1 only"; return ABC_ERR_ARG; }
+        for (int i = 0; i < n; ++i)
+            out[(size_t)i * n + i] = which == ABC_MAT_A ? cd(0.0, -g.gamma_c[i] / (4.0 * h4))
+                                                        : cd(4.0 * h4 / g.gamma_c[i], 0.0);
+        return ABC_OK;
+    }
+    if (which >= ABC_MAT_B1 && which <= ABC_MAT_A0) {
+        if (b.order != 2) { err = "B1, B0, A1, A0 exist for order 2 only"; return ABC_ERR_ARG; }
+        std::vector<cd> blk[8];
+        for (int p = 0; p < 8; ++p)
+            if (g.base_of[p] == p && g.m[p]) expand_base_block(g, p, b.mat2[which - ABC_MAT_B1], blk[p]);
+        return natural_from_blocks(g, blk, out);
+    }
+    if (b.order == 2) { err = "order 2 holds B1, B0, A1, A0 (ABC_MAT_B1 .. ABC_MAT_A0)"; return ABC_ERR_ARG; }
+    if (which == ABC_MAT_M && b.order != 0) { err = "M exists for order 0 only"; return ABC_ERR_ARG; }
+    if (which == ABC_MAT_B && b.order != 1) { err = "B exists for order 1 only"; return ABC_ERR_ARG; }
+    if (which != ABC_MAT_K && which != ABC_MAT_M && which != ABC_MAT_B) { err = "unknown matrix"; return ABC_ERR_ARG; }
+    // class blocks to expand: M_k (order 0) / K_k = S_k^{-1} (order 1, K) / S_k (order 1, B)
+    std::vector<std::vector<cd>> cb(b.mat);
+    if (b.order == 1 && which == ABC_MAT_K) {
+        for (size_t ki = 0; ki < g.cls.size(); ++ki) {
+            const int m = g.cls[ki].m;
+            std::vector<cd> F(b.mat[ki]), Z((size_t)m * m, cd(0.0, 0.0));
+            std::vector<int> piv(m);
+            for (int i = 0; i < m; ++i) Z[(size_t)i * m + i] = 1.0;
+            if (zgetrf(m, F.data(), m, piv.data())) { err = "S block singular"; return ABC_ERR_SINGULAR; }
+            zgetrs(m, m, F.data(), m, piv.data(), Z.data(), m);  // S symmetric: row/col order irrelevant
+            cb[ki] = Z;
+        }
+    }
+    std::vector<cd> blk[8];
+    for (int p = 0; p < 8; ++p)
+        if (g.base_of[p] == p && g.m[p]) expand_base_block(g, p, cb, blk[p]);
+    natural_from_blocks(g, blk, out);
     if (which == ABC_MAT_B) {
         // B = s1 I - A S, A = diag(-i c / (4h^4))
         for (int i = 0; i < n; ++i) {

@@ -6,14 +6,17 @@
 //     t_I += S_IJ x_J          (row part)
 //     t_J += S_IJ^T x_I        (column part, J < I)
 // for every right-hand side x of the class.  One producer warp streams the tiles
-// with 1D bulk copies (cp.async.bulk) into a shared-memory ring ("full" mbarriers).
+// with 1D bulk copies (cp.async.bulk) into a shared-memory ring ("full" mbarriers);
+// its lanes also stage, next to each tile, the slices x_J (the tile's columns) and x_I
+// (its rows) of every right-hand side, so the consumers never wait on global loads.
 // Eight consumer warps run decoupled: consumer thread (warp w, lane l) owns the
 // column pair cp = 4w + l/8 and the eight rows 8(l%8) .. 8(l%8)+7 of every tile.  The
 // host packs each tile in exactly that order (sym_pack_index), so chunk i of all
 // 256 consumer threads is one contiguous 4 KB run and every 16-byte shared load is
 // conflict-free.  A warp releases a slot through its "empty" mbarrier once the
 // values are in registers, sums the column part over its 8 row groups by shuffles,
-// and keeps the row part in registers until its (class, tile-row) segment ends.
+// and keeps the row part in registers until its (class, tile-row) segment ends, when
+// each warp stores its own partial.
 // Every wait is bounded: a wait that gives up raises an error flag, and all warps
 // still follow the same control flow to the end, so no barrier can hang.  Partial
 // sums go to global scratch; the back transform of the stage gathers them in a
@@ -22,6 +25,8 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "kernels.cuh"
 
 namespace abc {
 namespace dev {
@@ -32,8 +37,11 @@ constexpr int SYM_THREADS = (SYM_CONSUMERS + 1) * 32;
 constexpr int SYM_STAGES = 6;
 constexpr int SYM_RMAX = 3;
 constexpr uint32_t SYM_TILE_BYTES = SYM_T * SYM_T * 8;
-constexpr size_t SYM_FLUSH_BYTES = (size_t)SYM_CONSUMERS * SYM_T * SYM_RMAX * 8;
-constexpr size_t SYM_SMEM = SYM_STAGES * (size_t)SYM_TILE_BYTES + SYM_FLUSH_BYTES + 2 * SYM_STAGES * 8;
+constexpr size_t SYM_XS_FLOAT2 = 2 * SYM_RMAX * SYM_T;   // per ring slot: x_J and x_I of the tile
+constexpr size_t SYM_XS_BYTES = (size_t)SYM_STAGES * SYM_XS_FLOAT2 * 8;
+constexpr int SYM_SEG_CACHE = 64;                // segments of a CTA kept in shared memory
+constexpr size_t SYM_SMEM =
+    SYM_STAGES * (size_t)SYM_TILE_BYTES + SYM_XS_BYTES + 2 * SYM_STAGES * 8 + SYM_SEG_CACHE * 16;
 constexpr long long SYM_WAIT_LIMIT = 1ll << 24;  // try_wait polls before giving up
 
 // Complex offset of tile element (row, col) in the packed tile: chunk row % 8 of
@@ -64,7 +72,19 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(SYM_CONSUMERS * 32) : "memory"); }
+// Adds bytes to the barrier's expected transaction count without arriving.
+__device__ __forceinline__ void mbar_add_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 8-byte asynchronous copy global -> shared; src_bytes = 0 fills the destination with zeros.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+// One arrival on the barrier once this thread's earlier cp.async copies have landed.
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
@@ -122,45 +142,41 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // (0..255): tiles sg.z .. sg.w-1 of the ring, u counts the CTA's tiles so far.
 template <int R>
 __device__ __forceinline__ bool sym_segment(const SymInfo& si, int4 sg, int s, int& u, const float2* ring,
-                                            uint64_t* full, uint64_t* empty, const float2* __restrict__ x,
+                                            const float2* xs, uint64_t* full, uint64_t* empty,
                                             float2* __restrict__ rowpart, float2* __restrict__ colpart,
-                                            float2* flush, float cs, int tid) {
-    const int c = sg.x, I = sg.y, m = si.m[c];
+                                            float cs, int tid) {
+    const int I = sg.y;
     const int warp = tid >> 5, lane = tid & 31, rg = lane & 7, cp = warp * 4 + (lane >> 3);
     float2 xi[8][R], racc[8][R];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int row = I * SYM_T + rg * 8 + i;
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            xi[i][k] = row < m ? __ldg(x + si.moff[c][k] + row) : make_float2(0.f, 0.f);
-            racc[i][k] = make_float2(0.f, 0.f);
-        }
-    }
+        for (int k = 0; k < R; ++k) xi[i][k] = racc[i][k] = make_float2(0.f, 0.f);
     bool ok = true;
-    const long long tb = si.tbase[c] + (long long)I * (I + 1) / 2;
-    // x_J of this thread's two columns; the next tile's are fetched while this one is used
-    float2 xn[2][R];
-    auto fetch_xj = [&](int J) {
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            const int col = J * SYM_T + 2 * cp + cc;
-#pragma unroll
-            for (int k = 0; k < R; ++k) xn[cc][k] = col < m ? __ldg(x + si.moff[c][k] + col) : make_float2(0.f, 0.f);
-        }
-    };
-    fetch_xj((int)(sg.z - tb));
+    const long long tb = si.tbase[sg.x] + (long long)I * (I + 1) / 2;
     for (int t = sg.z; t < sg.w; ++t, ++u) {
         const int J = (int)(t - tb);
         const bool offdiag = J < I;
         const int slot = u % SYM_STAGES;
+        ok &= mbar_wait_bounded(&full[slot], (uint32_t)((u / SYM_STAGES) & 1));
+        const float2* xsl = xs + (size_t)slot * SYM_XS_FLOAT2;      // [0][k][64] x_J, [1][k][64] x_I
+        if (t == sg.z) {
+#pragma unroll
+            for (int k = 0; k < R; ++k)
+#pragma unroll
+                for (int i = 0; i < 8; i += 2) {
+                    const float4 v = *reinterpret_cast<const float4*>(xsl + (SYM_RMAX + k) * SYM_T + rg * 8 + i);
+                    xi[i][k] = make_float2(v.x, v.y);
+                    xi[i + 1][k] = make_float2(v.z, v.w);
+                }
+        }
         float2 xj[2][R];
 #pragma unroll
-        for (int cc = 0; cc < 2; ++cc)
-#pragma unroll
-            for (int k = 0; k < R; ++k) xj[cc][k] = xn[cc][k];
-        if (t + 1 < sg.w) fetch_xj(J + 1);
-        ok &= mbar_wait_bounded(&full[slot], (uint32_t)((u / SYM_STAGES) & 1));
+        for (int k = 0; k < R; ++k) {
+            const float4 v = *reinterpret_cast<const float4*>(xsl + k * SYM_T + 2 * cp);
+            xj[0][k] = make_float2(v.x, v.y);
+            xj[1][k] = make_float2(v.z, v.w);
+        }
         const float4* T4 = reinterpret_cast<const float4*>(ring + (size_t)slot * SYM_T * SYM_T);
         float2 cacc[2][R];
 #pragma unroll
@@ -207,7 +223,9 @@ __device__ __forceinline__ bool sym_segment(const SymInfo& si, int4 sg, int s, i
                         colpart[((size_t)t * SYM_T + 2 * cp + cc) * SYM_RMAX + k] = cacc[cc][k];
         }
     }
-    // row part of the segment: over the warp's 4 column pairs, then over the 8 warps
+    // row part of the segment: summed over the warp's 4 column pairs; each warp stores
+    // its own partial (the back transform adds the 8 warps' values in a fixed order),
+    // so segment ends need no block-wide barrier
 #pragma unroll
     for (int o = 8; o < 32; o <<= 1)
 #pragma unroll
@@ -221,64 +239,94 @@ __device__ __forceinline__ bool sym_segment(const SymInfo& si, int4 sg, int s, i
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int k = 0; k < R; ++k) flush[((size_t)warp * SYM_T + rg * 8 + i) * SYM_RMAX + k] = racc[i][k];
-    consumer_sync();
-    if (tid < SYM_T * R) {
-        const int row = tid % SYM_T, k = tid / SYM_T;
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int w = 0; w < SYM_CONSUMERS; ++w) {
-            const float2 v = flush[((size_t)w * SYM_T + row) * SYM_RMAX + k];
-            acc.x += v.x;
-            acc.y += v.y;
-        }
-        rowpart[((size_t)s * SYM_T + row) * SYM_RMAX + k] = acc;
-    }
-    consumer_sync();
+            for (int k = 0; k < R; ++k)
+                rowpart[(((size_t)s * SYM_T + rg * 8 + i) * SYM_RMAX + k) * SYM_CONSUMERS + warp] = racc[i][k];
     return ok;
 }
 
 // seg[s] = (class, tile row I, first tile, end tile); cta_seg[b]..cta_seg[b+1] are
-// the segments of CTA b (contiguous tiles).  rowpart[s][64][3], colpart[t][64][3].
+// the segments of CTA b (contiguous tiles).  rowpart[s][64][3][8 warps], colpart[t][64][3].
 static __global__ void __launch_bounds__(SYM_THREADS, 1)
 sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restrict__ seg,
                const int* __restrict__ cta_seg, const float2* __restrict__ x, float2* __restrict__ rowpart,
                float2* __restrict__ colpart, int conj, long long keep, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     float2* ring = reinterpret_cast<float2*>(smem);
-    float2* flush = reinterpret_cast<float2*>(smem + SYM_STAGES * (size_t)SYM_TILE_BYTES);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + SYM_STAGES * (size_t)SYM_TILE_BYTES + SYM_FLUSH_BYTES);
+    float2* xs = reinterpret_cast<float2*>(smem + SYM_STAGES * (size_t)SYM_TILE_BYTES);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + SYM_STAGES * (size_t)SYM_TILE_BYTES + SYM_XS_BYTES);
     uint64_t* empty = full + SYM_STAGES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int s_begin = cta_seg[blockIdx.x], s_end = cta_seg[blockIdx.x + 1];
     if (s_begin >= s_end) return;
     const long long t_first = seg[s_begin].z;
     const int ntl = (int)(seg[s_end - 1].w - t_first);
+    // this CTA's segments, read once (segment boundaries then cost no global load)
+    int4* segc = reinterpret_cast<int4*>(empty + SYM_STAGES);
+    const bool cached = s_end - s_begin <= SYM_SEG_CACHE;
+    if (cached)
+        for (int i = tid; i < s_end - s_begin; i += blockDim.x) segc[i] = seg[s_begin + i];
     if (tid == 0) {
         for (int i = 0; i < SYM_STAGES; ++i) {
-            mbar_init(&full[i], 1);
+            mbar_init(&full[i], 32);                 // the producer warp's lanes (one with the tile bytes)
             mbar_init(&empty[i], SYM_CONSUMERS);
         }
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_trigger();
 
     if (warp == SYM_CONSUMERS) {
         // ---------------- producer warp ----------------
-        if (lane == 0) {
-            bool ok = true;
-            for (int u = 0; u < ntl; ++u) {
-                const int slot = u % SYM_STAGES;
-                if (u >= SYM_STAGES) ok &= mbar_wait_bounded(&empty[slot], (uint32_t)((u / SYM_STAGES - 1) & 1));
-                fence_proxy_async();
-                mbar_expect_tx(&full[slot], SYM_TILE_BYTES);
-                tile_copy(ring + (size_t)slot * SYM_T * SYM_T, tiles, t_first + u, &full[slot], keep);
+        // per tile: lane 0 announces the tile's bytes and starts its bulk copy; every lane
+        // copies its share of x_J (the tile's columns) and x_I (its rows) of each
+        // right-hand side into the slot with cp.async (zeros past the class size) and
+        // arrives on the slot's "full" barrier once its copies have landed (32 arrivals)
+        bool ok = true;
+        int cur = s_begin;
+        int4 sg = cached ? segc[0] : seg[cur];
+        // the tiles do not depend on the preceding kernel: start the first copies before
+        // waiting for it (the vector slices below do depend on it)
+        const int early = ntl < SYM_STAGES ? ntl : SYM_STAGES;
+        if (lane == 0)
+            for (int u = 0; u < early; ++u) {
+                mbar_add_tx(&full[u], SYM_TILE_BYTES);
+                tile_copy(ring + (size_t)u * SYM_T * SYM_T, tiles, t_first + u, &full[u], keep);
             }
-            // the last copies land before the CTA can release its shared memory
+        pdl_wait();
+        for (int u = 0; u < ntl; ++u) {
+            const int slot = u % SYM_STAGES;
+            const long long t = t_first + u;
+            while (t >= sg.w && cur + 1 < s_end) {
+                ++cur;
+                sg = cached ? segc[cur - s_begin] : seg[cur];
+            }
+            if (u >= SYM_STAGES) ok &= mbar_wait_bounded(&empty[slot], (uint32_t)((u / SYM_STAGES - 1) & 1));
+            const int c = sg.x, I = sg.y, R = si.R[c], m = si.m[c];
+            const int J = (int)(t - si.tbase[c] - (long long)I * (I + 1) / 2);
+            if (lane == 0 && u >= early) {
+                mbar_add_tx(&full[slot], SYM_TILE_BYTES);
+                tile_copy(ring + (size_t)slot * SYM_T * SYM_T, tiles, t, &full[slot], keep);
+            }
+            float2* xsl = xs + (size_t)slot * SYM_XS_FLOAT2;
+#pragma unroll
+            for (int half = 0; half < 2; ++half)
+#pragma unroll
+                for (int k = 0; k < SYM_RMAX; ++k) {
+                    if (k >= R) break;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int q = lane + 32 * h, idx = (half ? I : J) * SYM_T + q;
+                        cp_async8(xsl + (half * SYM_RMAX + k) * SYM_T + q, x + si.moff[c][k] + (idx < m ? idx : 0),
+                                  idx < m ? 8u : 0u);
+                    }
+                }
+            cp_async_arrive(&full[slot]);
+        }
+        // the last copies land before the CTA can release its shared memory
+        if (lane == 0)
             for (int u = ntl > SYM_STAGES ? ntl - SYM_STAGES : 0; u < ntl; ++u)
                 ok &= mbar_wait_bounded(&full[u % SYM_STAGES], (uint32_t)((u / SYM_STAGES) & 1));
-            if (!ok) atomicExch(err, 1);
-        }
+        if (!ok) atomicExch(err, 1);
         return;
     }
 
@@ -287,11 +335,11 @@ sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restr
     bool ok = true;
     int u = 0;
     for (int s = s_begin; s < s_end; ++s) {
-        const int4 sg = seg[s];
+        const int4 sg = cached ? segc[s - s_begin] : seg[s];
         switch (si.R[sg.x]) {
-            case 1: ok &= sym_segment<1>(si, sg, s, u, ring, full, empty, x, rowpart, colpart, flush, cs, tid); break;
-            case 2: ok &= sym_segment<2>(si, sg, s, u, ring, full, empty, x, rowpart, colpart, flush, cs, tid); break;
-            default: ok &= sym_segment<3>(si, sg, s, u, ring, full, empty, x, rowpart, colpart, flush, cs, tid); break;
+            case 1: ok &= sym_segment<1>(si, sg, s, u, ring, xs, full, empty, rowpart, colpart, cs, tid); break;
+            case 2: ok &= sym_segment<2>(si, sg, s, u, ring, xs, full, empty, rowpart, colpart, cs, tid); break;
+            default: ok &= sym_segment<3>(si, sg, s, u, ring, xs, full, empty, rowpart, colpart, cs, tid); break;
         }
     }
     if (!ok && lane == 0) atomicExch(err, 1);

@@ -10,7 +10,7 @@ import re
 import numpy as np
 import pytest
 
-from oracle.coefficients import order0, order1
+from oracle.coefficients import order0, order1, order2
 from oracle.lattice import Box
 from paper_1908_02456_gb300 import abc
 from paper_1908_02456_gb300 import build as nb
@@ -65,3 +65,15 @@ def test_host_setup_matches_oracle(lib, dims, h, s):
     for which, ref in [(abc.MAT_B, co["B"]), (abc.MAT_A, co["A"]), (abc.MAT_Q, co["Q"]), (abc.MAT_K, Mo)]:
         X = abc.abc_host_matrices(dims, h, 1, s, which)
         assert np.abs(X - ref).max() < 1e-11 * np.abs(ref).max(), which
+
+
+@pytest.mark.parametrize("dims,h,pts", [((5, 4, 6), 0.5, (1.0, 2.0, 3.0, 10.0)), ((6, 6, 6), 0.45, (0.7, 1.5, 3.0, 8.0)),
+                                        ((7, 7, 7), 0.5, (1.0, 2.0, 4.0, 8.0))])
+def test_order2_host_setup_matches_oracle(lib, dims, h, pts):
+    """The four order-2 coefficient matrices (Sec. 3.3): the library fits each
+    irreducible class block separately, the oracle fits the dense matrices at once."""
+    co = order2(Box(dims, h), pts)
+    for which, key in [(abc.MAT_B1, "B1"), (abc.MAT_B0, "B0"), (abc.MAT_A1, "A1"), (abc.MAT_A0, "A0")]:
+        X = abc.abc_host_matrices(dims, h, 2, pts, which)
+        ref = co[key]
+        assert np.abs(X - ref).max() < 1e-9 * np.abs(ref).max(), key

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import scipy.fft as sfft
 
-from oracle.coefficients import order0, order1
+from oracle.coefficients import order0, order1, order2
 from oracle.lattice import Box
 from oracle.propagate import System
 from paper_1908_02456_gb300 import inputs
@@ -137,7 +137,8 @@ def test_dirichlet_norm_conservation():
 def test_reflection_against_large_box():
     """The same packet on a large zero-Dirichlet box, restricted to the small box, is the
     reflection-free reference (Sec. 4.3's test design).  The ABCs cut the error of the
-    Dirichlet box, order 1 more than order 0 (Sec. 4.1, Sec. 4.2)."""
+    Dirichlet box, order 1 more than order 0 (Sec. 4.1, Sec. 4.2), and the second-order
+    ABC at the paper's points s = 1, 2, 3, 10 (Sec. 4.2) more than order 1."""
     N, h, Nb, T, dt = 10, 0.5, 42, 1.6, 0.01
     k = (2.5, 0.0, 0.0)
     small = Box((N,) * 3, h)
@@ -151,13 +152,15 @@ def test_reflection_against_large_box():
     o = (Nb - N) // 2
     ref = ref.reshape(Nb, Nb, Nb)[o:o + N, o:o + N, o:o + N].reshape(1, -1)
     errs = {}
-    for name, co in (("dirichlet", None), ("order0", order0(small, 1.0)), ("order1", order1(small, 1.0))):
+    for name, co in (("dirichlet", None), ("order0", order0(small, 1.0)), ("order1", order1(small, 1.0)),
+                     ("order2", order2(small, (1.0, 2.0, 3.0, 10.0)))):
         phi, _, _ = System(small, coeffs=co).run(p_s, dt, n)
         errs[name] = np.linalg.norm(phi - ref) / np.linalg.norm(p_s)
-    # measured 0.63 / 0.47 / 0.23 at kh = 1.25 (a coarse, strongly dispersive case)
+    # measured 0.63 / 0.47 / 0.23 / 0.025 at kh = 1.25 (a coarse, strongly dispersive case)
     assert errs["order0"] < 0.85 * errs["dirichlet"]
     assert errs["order1"] < 0.5 * errs["dirichlet"]
     assert errs["order1"] < errs["order0"]
+    assert errs["order2"] < 0.3 * errs["order1"]
 
 
 def test_meanfield_keeps_orbitals_orthonormal():
