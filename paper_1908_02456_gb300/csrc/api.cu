@@ -265,35 +265,51 @@ int build_sym(abc_ctx* c) {
     int st;
     if ((st = c->sym_tiles.alloc(host.size() * sizeof(float)))) return st;
     CUDA_TRY(cudaMemcpy(c->sym_tiles.p, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice));
-    // contiguous tile ranges per CTA, split into (class, tile-row) segments
+    // Work units: tile rows of a class (row I has I + 1 tiles), split into pieces of at
+    // most SYM_PIECE tiles.  Each piece is one segment: its row part stays in registers
+    // and is stored once at its end, which costs about as much as two tiles.  The
+    // pieces are bin-packed over the CTAs longest first (LPT); a CTA takes any set of
+    // segments.  Segments are numbered by (class, row, first tile), so the segments of
+    // one row are consecutive (the back transform's gather relies on it).
     int sms = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     const int G = std::max(1, sms);
-    // ranges of equal work: every tile streams the same bytes, and its FMAs grow with
-    // the class's right-hand sides and with the column part of off-diagonal tiles
-    std::vector<double> wcum(NT + 1, 0.0);
-    for (long long t = 0; t < NT; ++t) {
-        const int k = tile_c[t];
-        const long long J = t - si.tbase[k] - (long long)tile_I[t] * (tile_I[t] + 1) / 2;
-        wcum[t + 1] = wcum[t] + 1.0 + c->sym_balance * si.R[k] * (J < tile_I[t] ? 2.0 : 1.0);
-    }
-    std::vector<long long> cut(G + 1, NT);
-    cut[0] = 0;
-    for (int b = 1; b < G; ++b)
-        cut[b] = std::lower_bound(wcum.begin(), wcum.end(), wcum[NT] * b / G) - wcum.begin();
-    std::vector<int4> segs;
-    std::vector<int> cta(G + 1, 0);
-    for (int b = 0; b < G; ++b) {
-        cta[b] = (int)segs.size();
-        const long long t0 = std::min(cut[b], NT), t1 = std::max(t0, std::min(cut[b + 1], NT));
-        for (long long t = t0; t < t1;) {
-            long long e = t + 1;
-            while (e < t1 && tile_c[e] == tile_c[t] && tile_I[e] == tile_I[t]) ++e;
-            segs.push_back(make_int4(tile_c[t], tile_I[t], (int)t, (int)e));
-            t = e;
+    struct Piece { int c, I, t0, t1; double cost; };
+    std::vector<Piece> pieces;
+    constexpr int SYM_PIECE = 12;
+    const double seg_cost = 1.5 * c->sym_balance, tile_base = 0.3;
+    for (int k = 0; k < nc; ++k)
+        for (int I = 0; I < si.nt[k]; ++I) {
+            const int len = I + 1, np = (len + SYM_PIECE - 1) / SYM_PIECE;
+            const int t0 = (int)(si.tbase[k] + (long long)I * (I + 1) / 2);
+            for (int q = 0; q < np; ++q) {
+                const int a = t0 + q * len / np, b = t0 + (q + 1) * len / np;
+                pieces.push_back({k, I, a, b, (b - a) * (tile_base + 0.2 * si.R[k]) + seg_cost});
+            }
         }
+    std::vector<int> order(pieces.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pieces[a].cost > pieces[b].cost; });
+    std::vector<double> load(G, 0.0);
+    std::vector<int> owner(pieces.size(), 0);
+    for (int i : order) {
+        const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        owner[i] = b;
+        load[b] += pieces[i].cost;
     }
-    cta[G] = (int)segs.size();
+    // pieces are generated in (class, row, first tile) order already: their index is the segment id
+    std::vector<int4> segs(pieces.size());
+    for (size_t i = 0; i < pieces.size(); ++i)
+        segs[i] = make_int4(pieces[i].c, pieces[i].I, pieces[i].t0, pieces[i].t1);
+    std::vector<int> cta(G + 1, 0), cta_list;
+    for (int b = 0; b < G; ++b) {
+        cta[b] = (int)cta_list.size();
+        for (size_t i = 0; i < pieces.size(); ++i)
+            if (owner[i] == b) cta_list.push_back((int)i);
+        if ((int)cta_list.size() - cta[b] > abc::dev::SYM_SEG_CACHE)
+            return fail(ABC_ERR_ARG, "internal: too many segments for one CTA of the tiled contraction");
+    }
+    cta[G] = (int)cta_list.size();
     std::vector<int2> rowseg(rb, make_int2(0, 0));
     for (size_t s = 0; s < segs.size(); ++s) {
         const int cI = si.rbase[segs[s].x] + segs[s].y;
@@ -302,6 +318,8 @@ int build_sym(abc_ctx* c) {
     }
     if ((st = c->sym_seg.alloc(segs.size() * sizeof(int4)))) return st;
     if ((st = c->sym_cta.alloc(cta.size() * sizeof(int)))) return st;
+    if ((st = c->sym_cta_list.alloc(cta_list.size() * sizeof(int)))) return st;
+    CUDA_TRY(cudaMemcpy(c->sym_cta_list.p, cta_list.data(), cta_list.size() * sizeof(int), cudaMemcpyHostToDevice));
     if ((st = c->sym_rowseg.alloc(rowseg.size() * sizeof(int2)))) return st;
     if ((st = c->sym_rowpart.alloc(segs.size() * SYM_T * abc::dev::SYM_RMAX * abc::dev::SYM_CONSUMERS *
                                    sizeof(float2))))
@@ -497,6 +515,7 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
     if (n_orb == 1 && sizeof(T) == 4 && c->sym) {
         launch_pdl(c->pdl, dev::sym_gemv_tiles, dim3(c->sym_grid), dim3(dev::SYM_THREADS), dev::SYM_SMEM, s, c->si,
                    c->sym_tiles.as<const float2>(), c->sym_seg.as<const int4>(), c->sym_cta.as<const int>(),
+                   c->sym_cta_list.as<const int>(),
                    (const float2*)x, c->sym_rowpart.as<float2>(), c->sym_colpart.as<float2>(), conj,
                    (long long)c->l2_keep_tiles, c->err_flag.as<int>());
         res.gathered = true;

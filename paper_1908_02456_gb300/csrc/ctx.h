@@ -76,7 +76,7 @@ struct abc_ctx {
     long long l2_keep_tiles = 0;     // tiles streamed with evict_last (tuning)
     bool pdl = false;                // programmatic dependent launch of the contraction and gather (tuning)
     double sym_balance = 1.0;        // work weight per right-hand side in the tile partition
-    abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
+    abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_cta_list, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
     abc::dev::SymGather sym_gather{};   // partial-sum view for the back transform
     // many-orbital complex64 contraction on the tensor cores (ABC_C64_3XTF32)
     bool tc = false;

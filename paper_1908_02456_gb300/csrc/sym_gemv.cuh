@@ -41,7 +41,7 @@ constexpr size_t SYM_XS_FLOAT2 = 2 * SYM_RMAX * SYM_T;   // per ring slot: x_J a
 constexpr size_t SYM_XS_BYTES = (size_t)SYM_STAGES * SYM_XS_FLOAT2 * 8;
 constexpr int SYM_SEG_CACHE = 64;                // segments of a CTA kept in shared memory
 constexpr size_t SYM_SMEM =
-    SYM_STAGES * (size_t)SYM_TILE_BYTES + SYM_XS_BYTES + 2 * SYM_STAGES * 8 + SYM_SEG_CACHE * 16;
+    SYM_STAGES * (size_t)SYM_TILE_BYTES + SYM_XS_BYTES + 2 * SYM_STAGES * 8 + SYM_SEG_CACHE * 20;
 constexpr long long SYM_WAIT_LIMIT = 1ll << 24;  // try_wait polls before giving up
 
 // Complex offset of tile element (row, col) in the packed tile: chunk row % 8 of
@@ -244,27 +244,30 @@ __device__ __forceinline__ bool sym_segment(const SymInfo& si, int4 sg, int s, i
     return ok;
 }
 
-// seg[s] = (class, tile row I, first tile, end tile); cta_seg[b]..cta_seg[b+1] are
-// the segments of CTA b (contiguous tiles).  rowpart[s][64][3][8 warps], colpart[t][64][3].
+// seg[s] = (class, tile row I, first tile, end tile), numbered by (class, row, first
+// tile); CTA b works on the segments cta_list[cta_seg[b]] .. cta_list[cta_seg[b+1]-1]
+// (at most SYM_SEG_CACHE, tiles of different segments need not be contiguous).
+// rowpart[s][64][3][8 warps], colpart[t][64][3].
 static __global__ void __launch_bounds__(SYM_THREADS, 1)
 sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restrict__ seg,
-               const int* __restrict__ cta_seg, const float2* __restrict__ x, float2* __restrict__ rowpart,
-               float2* __restrict__ colpart, int conj, long long keep, int* __restrict__ err) {
+               const int* __restrict__ cta_seg, const int* __restrict__ cta_list, const float2* __restrict__ x,
+               float2* __restrict__ rowpart, float2* __restrict__ colpart, int conj, long long keep,
+               int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     float2* ring = reinterpret_cast<float2*>(smem);
     float2* xs = reinterpret_cast<float2*>(smem + SYM_STAGES * (size_t)SYM_TILE_BYTES);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + SYM_STAGES * (size_t)SYM_TILE_BYTES + SYM_XS_BYTES);
     uint64_t* empty = full + SYM_STAGES;
+    int4* segc = reinterpret_cast<int4*>(empty + SYM_STAGES);       // this CTA's segments
+    int* sidc = reinterpret_cast<int*>(segc + SYM_SEG_CACHE);       // and their ids
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int s_begin = cta_seg[blockIdx.x], s_end = cta_seg[blockIdx.x + 1];
-    if (s_begin >= s_end) return;
-    const long long t_first = seg[s_begin].z;
-    const int ntl = (int)(seg[s_end - 1].w - t_first);
-    // this CTA's segments, read once (segment boundaries then cost no global load)
-    int4* segc = reinterpret_cast<int4*>(empty + SYM_STAGES);
-    const bool cached = s_end - s_begin <= SYM_SEG_CACHE;
-    if (cached)
-        for (int i = tid; i < s_end - s_begin; i += blockDim.x) segc[i] = seg[s_begin + i];
+    const int l_begin = cta_seg[blockIdx.x], nseg = cta_seg[blockIdx.x + 1] - l_begin;
+    if (nseg <= 0 || nseg > SYM_SEG_CACHE) return;               // the host guarantees <= SYM_SEG_CACHE
+    for (int i = tid; i < nseg; i += blockDim.x) {
+        const int id = cta_list[l_begin + i];
+        sidc[i] = id;
+        segc[i] = seg[id];
+    }
     if (tid == 0) {
         for (int i = 0; i < SYM_STAGES; ++i) {
             mbar_init(&full[i], 32);                 // the producer warp's lanes (one with the tile bytes)
@@ -274,6 +277,8 @@ sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restr
     }
     __syncthreads();
     pdl_trigger();
+    int ntl = 0;                                     // tiles of this CTA
+    for (int i = 0; i < nseg; ++i) ntl += segc[i].w - segc[i].z;
 
     if (warp == SYM_CONSUMERS) {
         // ---------------- producer warp ----------------
@@ -282,23 +287,28 @@ sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restr
         // right-hand side into the slot with cp.async (zeros past the class size) and
         // arrives on the slot's "full" barrier once its copies have landed (32 arrivals)
         bool ok = true;
-        int cur = s_begin;
-        int4 sg = cached ? segc[0] : seg[cur];
         // the tiles do not depend on the preceding kernel: start the first copies before
         // waiting for it (the vector slices below do depend on it)
         const int early = ntl < SYM_STAGES ? ntl : SYM_STAGES;
-        if (lane == 0)
+        if (lane == 0) {
+            int i = 0;
+            long long t = segc[0].z;
             for (int u = 0; u < early; ++u) {
+                while (t >= segc[i].w) t = segc[++i].z;
                 mbar_add_tx(&full[u], SYM_TILE_BYTES);
-                tile_copy(ring + (size_t)u * SYM_T * SYM_T, tiles, t_first + u, &full[u], keep);
+                tile_copy(ring + (size_t)u * SYM_T * SYM_T, tiles, t, &full[u], keep);
+                ++t;
             }
+        }
         pdl_wait();
-        for (int u = 0; u < ntl; ++u) {
+        int i = 0;
+        int4 sg = segc[0];
+        long long t = sg.z;
+        for (int u = 0; u < ntl; ++u, ++t) {
             const int slot = u % SYM_STAGES;
-            const long long t = t_first + u;
-            while (t >= sg.w && cur + 1 < s_end) {
-                ++cur;
-                sg = cached ? segc[cur - s_begin] : seg[cur];
+            while (t >= sg.w) {
+                sg = segc[++i];
+                t = sg.z;
             }
             if (u >= SYM_STAGES) ok &= mbar_wait_bounded(&empty[slot], (uint32_t)((u / SYM_STAGES - 1) & 1));
             const int c = sg.x, I = sg.y, R = si.R[c], m = si.m[c];
@@ -334,8 +344,9 @@ sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restr
     const float cs = conj ? -1.f : 1.f;
     bool ok = true;
     int u = 0;
-    for (int s = s_begin; s < s_end; ++s) {
-        const int4 sg = cached ? segc[s - s_begin] : seg[s];
+    for (int i = 0; i < nseg; ++i) {
+        const int4 sg = segc[i];
+        const int s = sidc[i];
         switch (si.R[sg.x]) {
             case 1: ok &= sym_segment<1>(si, sg, s, u, ring, xs, full, empty, rowpart, colpart, cs, tid); break;
             case 2: ok &= sym_segment<2>(si, sg, s, u, ring, xs, full, empty, rowpart, colpart, cs, tid); break;
