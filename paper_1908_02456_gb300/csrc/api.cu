@@ -353,8 +353,8 @@ int build_sym(abc_ctx* c) {
         const int2 rs = rowseg[si.rbase[k] + I];
         const long long t1 = si.tbase[k] + (long long)(I + 1) * (I + 2) / 2 + I;
         const int nk = si.nt[k] - 1 - I;
-        gdesc[i] = make_int4((int)((((long long)rs.x * SYM_T + r) * 3 + e) * abc::dev::SYM_CONSUMERS), rs.y - rs.x,
-                             nk > 0 ? (int)((t1 * SYM_T + r) * 3 + e) : 0, nk | ((I + 2) << 16));
+        gdesc[i] = make_int4((int)((((long long)rs.x * abc::dev::SYM_CONSUMERS) * 3 + e) * SYM_T + r), rs.y - rs.x,
+                             nk > 0 ? (int)((t1 * 3 + e) * SYM_T + r) : 0, nk | ((I + 2) << 16));
     }
     if ((st = c->sym_gdesc.alloc(gdesc.size() * sizeof(int4)))) return st;
     CUDA_TRY(cudaMemcpy(c->sym_gdesc.p, gdesc.data(), gdesc.size() * sizeof(int4), cudaMemcpyHostToDevice));

@@ -68,15 +68,15 @@ struct CellTab {
 // Partial sums of the tiled one-orbital contraction, gathered by the back transform:
 // t[j] = sum of the row parts of the segments of (class c, tile row I) + the column
 // parts of the tiles (c, K, I), K > I (fixed order).  desc is indexed like the cell
-// output table (cell * 64 + 8 o + p): x = first row-part element (8 consecutive
-// values, one per consumer warp), y = number of row segments (consecutive, 1536
-// elements apart), z = column-part element of K = I + 1,
+// output table (cell * 64 + 8 o + p): x = row-part element of the first segment and
+// warp 0 (the 8 consumer warps' partials are 192 elements apart), y = number of row
+// segments (consecutive, 1536 elements apart), z = column-part element of K = I + 1,
 // w = (number of K) | ((I + 2) << 16); the column-part element of K + 1 is that of K
 // plus (K + 1) * 192.
 struct SymGather {
     const int4* desc;
-    const float2* rowpart;       // [segment][64][3][8 warps]
-    const float2* colpart;       // [tile][64][3]
+    const float2* rowpart;       // [segment][8 warps][3][64]
+    const float2* colpart;       // [tile][3][64]
 };
 
 // Gamma index of a boundary node (ascending linear order, x fastest).
@@ -218,14 +218,12 @@ __device__ __forceinline__ float2 sym_gather(const SymGather& sg, int4 d) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
     for (int q = 0; q < d.y; ++q) {
-        const float4* rp = reinterpret_cast<const float4*>(sg.rowpart + d.x + (size_t)q * 1536);
+        const float2* rp = sg.rowpart + d.x + (size_t)q * 1536;
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {                  // the 8 warps' partials of the segment
-            const float4 v = rp[w];
-            acc[2 * w].x += v.x;
-            acc[2 * w].y += v.y;
-            acc[2 * w + 1].x += v.z;
-            acc[2 * w + 1].y += v.w;
+        for (int w = 0; w < 8; ++w) {                  // the 8 warps' partials of the segment
+            const float2 v = rp[w * 192];
+            acc[w].x += v.x;
+            acc[w].y += v.y;
         }
     }
     const int nk = d.w & 0xffff;

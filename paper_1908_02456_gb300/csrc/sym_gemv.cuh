@@ -140,13 +140,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 // One (class c, tile row I) segment of R right-hand sides for consumer thread tid
 // (0..255): tiles sg.z .. sg.w-1 of the ring, u counts the CTA's tiles so far.
-template <int R>
+// CONJ applies conj(S) instead of S.
+//
+// Both partial sums are reduced by halving exchanges (a reduce-scatter over lanes):
+// at each level a lane keeps half of its values, sends the other half to its partner
+// and adds what the partner sent for the kept half, so every level moves half as
+// much as the one before and the reduced values end up spread over the lanes, in
+// the order the stores want them.
+template <int R, bool CONJ>
 __device__ __forceinline__ bool sym_segment(const SymInfo& si, int4 sg, int s, int& u, const float2* ring,
                                             const float2* xs, uint64_t* full, uint64_t* empty,
-                                            float2* __restrict__ rowpart, float2* __restrict__ colpart,
-                                            float cs, int tid) {
+                                            float2* __restrict__ rowpart, float* __restrict__ colpart, int tid) {
     const int I = sg.y;
     const int warp = tid >> 5, lane = tid & 31, rg = lane & 7, cp = warp * 4 + (lane >> 3);
+    const bool b0 = lane & 1, b1 = lane & 2, b2 = lane & 4, b3 = lane & 8, b4 = lane & 16;
     float2 xi[8][R], racc[8][R];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -184,7 +191,7 @@ __device__ __forceinline__ bool sym_segment(const SymInfo& si, int4 sg, int s, i
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const float4 e = T4[i * 256 + tid];            // (8 rg + i, 2 cp) and (8 rg + i, 2 cp + 1)
-            const float a0r = e.x, a0i = cs * e.y, a1r = e.z, a1i = cs * e.w;
+            const float a0r = e.x, a0i = CONJ ? -e.y : e.y, a1r = e.z, a1i = CONJ ? -e.w : e.w;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 float2 r = racc[i][k];
@@ -205,54 +212,67 @@ __device__ __forceinline__ bool sym_segment(const SymInfo& si, int4 sg, int s, i
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);          // the slot's data is in registers
         if (offdiag) {
-            // column part: sum over the 8 row groups (lanes differing in the low 3 bits)
-#pragma unroll
-            for (int o = 1; o < 8; o <<= 1)
-#pragma unroll
-                for (int cc = 0; cc < 2; ++cc)
-#pragma unroll
-                    for (int k = 0; k < R; ++k) {
-                        cacc[cc][k].x += __shfl_xor_sync(0xffffffffu, cacc[cc][k].x, o);
-                        cacc[cc][k].y += __shfl_xor_sync(0xffffffffu, cacc[cc][k].y, o);
-                    }
-            if (rg == 0)
-#pragma unroll
-                for (int cc = 0; cc < 2; ++cc)
-#pragma unroll
-                    for (int k = 0; k < R; ++k)
-                        colpart[((size_t)t * SYM_T + 2 * cp + cc) * SYM_RMAX + k] = cacc[cc][k];
-        }
-    }
-    // row part of the segment: summed over the warp's 4 column pairs; each warp stores
-    // its own partial (the back transform adds the 8 warps' values in a fixed order),
-    // so segment ends need no block-wide barrier
-#pragma unroll
-    for (int o = 8; o < 32; o <<= 1)
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
+            // column part: sum over the 8 row groups (lane bits 0-2).  Bit 2 picks the
+            // column of the pair, bit 1 the real or imaginary part; bit 0 adds the last pair.
+            float w[R];
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                racc[i][k].x += __shfl_xor_sync(0xffffffffu, racc[i][k].x, o);
-                racc[i][k].y += __shfl_xor_sync(0xffffffffu, racc[i][k].y, o);
+                const float2 snd = b2 ? cacc[0][k] : cacc[1][k], kp = b2 ? cacc[1][k] : cacc[0][k];
+                float2 v;
+                v.x = kp.x + __shfl_xor_sync(0xffffffffu, snd.x, 4);
+                v.y = kp.y + __shfl_xor_sync(0xffffffffu, snd.y, 4);
+                w[k] = (b1 ? v.y : v.x) + __shfl_xor_sync(0xffffffffu, b1 ? v.x : v.y, 2);
+                w[k] += __shfl_xor_sync(0xffffffffu, w[k], 1);
             }
-    if (lane < 8)
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
+            // colpart[t][k][64 columns] complex: the warp's 8 columns are 64 contiguous bytes per k
+            float* dst = colpart + (((size_t)t * SYM_RMAX) * SYM_T + 2 * cp + (b2 ? 1 : 0)) * 2 + (b1 ? 1 : 0);
 #pragma unroll
             for (int k = 0; k < R; ++k)
-                rowpart[(((size_t)s * SYM_T + rg * 8 + i) * SYM_RMAX + k) * SYM_CONSUMERS + warp] = racc[i][k];
+                if (R == 1 ? !b0 : ((k & 1) != 0) == b0) dst[k * SYM_T * 2] = w[k];
+        }
+    }
+    // row part of the segment, summed over the warp's 4 column pairs (lane bits 3, 4):
+    // bit 4 keeps rows 0-3 or 4-7 of the lane's eight, bit 3 a pair of those, so lane
+    // (rg, q = lane / 8) ends with rows 8 rg + 2 q and 8 rg + 2 q + 1.  Each warp stores
+    // its own partial (the back transform adds the 8 warps' values in a fixed order),
+    // so segment ends need no block-wide barrier.
+    float2 r4[4][R];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const float2 snd = b4 ? racc[j][k] : racc[j + 4][k], kp = b4 ? racc[j + 4][k] : racc[j][k];
+            r4[j][k].x = kp.x + __shfl_xor_sync(0xffffffffu, snd.x, 16);
+            r4[j][k].y = kp.y + __shfl_xor_sync(0xffffffffu, snd.y, 16);
+        }
+    // rowpart[s][warp][k][64 rows] complex: one contiguous 512-byte store per k
+    float4* dst = reinterpret_cast<float4*>(rowpart + (((size_t)s * SYM_CONSUMERS + warp) * SYM_RMAX) * SYM_T) +
+                  (rg * 8 + 2 * (lane >> 3)) / 2;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        float2 r2[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float2 snd = b3 ? r4[j][k] : r4[j + 2][k], kp = b3 ? r4[j + 2][k] : r4[j][k];
+            r2[j].x = kp.x + __shfl_xor_sync(0xffffffffu, snd.x, 8);
+            r2[j].y = kp.y + __shfl_xor_sync(0xffffffffu, snd.y, 8);
+        }
+        dst[k * SYM_T / 2] = make_float4(r2[0].x, r2[0].y, r2[1].x, r2[1].y);
+    }
     return ok;
 }
 
 // seg[s] = (class, tile row I, first tile, end tile), numbered by (class, row, first
 // tile); CTA b works on the segments cta_list[cta_seg[b]] .. cta_list[cta_seg[b+1]-1]
 // (at most SYM_SEG_CACHE, tiles of different segments need not be contiguous).
-// rowpart[s][64][3][8 warps], colpart[t][64][3].
+// rowpart[s][8 warps][3][64] and colpart[t][3][64] (complex, right-hand side k of R
+// at index k; slots k >= R are not written).
 static __global__ void __launch_bounds__(SYM_THREADS, 1)
 sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restrict__ seg,
                const int* __restrict__ cta_seg, const int* __restrict__ cta_list, const float2* __restrict__ x,
                float2* __restrict__ rowpart, float2* __restrict__ colpart, int conj, long long keep,
                int* __restrict__ err) {
+    float* colf = reinterpret_cast<float*>(colpart);
     extern __shared__ __align__(128) unsigned char smem[];
     float2* ring = reinterpret_cast<float2*>(smem);
     float2* xs = reinterpret_cast<float2*>(smem + SYM_STAGES * (size_t)SYM_TILE_BYTES);
@@ -341,16 +361,20 @@ sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restr
     }
 
     // ---------------- consumer warps ----------------
-    const float cs = conj ? -1.f : 1.f;
     bool ok = true;
     int u = 0;
     for (int i = 0; i < nseg; ++i) {
         const int4 sg = segc[i];
         const int s = sidc[i];
-        switch (si.R[sg.x]) {
-            case 1: ok &= sym_segment<1>(si, sg, s, u, ring, xs, full, empty, rowpart, colpart, cs, tid); break;
-            case 2: ok &= sym_segment<2>(si, sg, s, u, ring, xs, full, empty, rowpart, colpart, cs, tid); break;
-            default: ok &= sym_segment<3>(si, sg, s, u, ring, xs, full, empty, rowpart, colpart, cs, tid); break;
+        const int R = si.R[sg.x];
+        if (conj) {
+            if (R == 1) ok &= sym_segment<1, true>(si, sg, s, u, ring, xs, full, empty, rowpart, colf, tid);
+            else if (R == 2) ok &= sym_segment<2, true>(si, sg, s, u, ring, xs, full, empty, rowpart, colf, tid);
+            else ok &= sym_segment<3, true>(si, sg, s, u, ring, xs, full, empty, rowpart, colf, tid);
+        } else {
+            if (R == 1) ok &= sym_segment<1, false>(si, sg, s, u, ring, xs, full, empty, rowpart, colf, tid);
+            else if (R == 2) ok &= sym_segment<2, false>(si, sg, s, u, ring, xs, full, empty, rowpart, colf, tid);
+            else ok &= sym_segment<3, false>(si, sg, s, u, ring, xs, full, empty, rowpart, colf, tid);
         }
     }
     if (!ok && lane == 0) atomicExch(err, 1);
