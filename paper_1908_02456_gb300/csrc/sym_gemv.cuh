@@ -9,14 +9,14 @@
 // with 1D bulk copies (cp.async.bulk) into a shared-memory ring ("full" mbarriers);
 // its lanes also stage, next to each tile, the slices x_J (the tile's columns) and x_I
 // (its rows) of every right-hand side, so the consumers never wait on global loads.
-// Eight consumer warps run decoupled: consumer thread (warp w, lane l) owns the
-// column pair cp = 4w + l/8 and the eight rows 8(l%8) .. 8(l%8)+7 of every tile.  The
-// host packs each tile in exactly that order (sym_pack_index), so chunk i of all
-// 256 consumer threads is one contiguous 4 KB run and every 16-byte shared load is
-// conflict-free.  A warp releases a slot through its "empty" mbarrier once the
-// values are in registers, sums the column part over its 8 row groups by shuffles,
-// and keeps the row part in registers until its (class, tile-row) segment ends, when
-// each warp stores its own partial.
+// Eight consumer warps in two groups of four take alternate tiles; within a group,
+// thread (warp wq, lane l) owns the column pairs cp = 4 wq + l/8 and cp + 16 and the
+// eight rows 8(l%8) .. 8(l%8)+7 of the tile.  The host packs each tile in exactly that
+// order (sym_pack_index), so chunk i of one column-pair half is one contiguous 2 KB
+// run and every 16-byte shared load is conflict-free.  A warp releases a slot through
+// its group's "empty" mbarrier once the values are in registers, sums the column part
+// over its 8 row groups by shuffles, and keeps the row part in registers until its
+// (class, tile-row) segment ends, when each warp stores its own partial.
 // Every wait is bounded: a wait that gives up raises an error flag, and all warps
 // still follow the same control flow to the end, so no barrier can hang.  Partial
 // sums go to global scratch; the back transform of the stage gathers them in a
@@ -138,9 +138,65 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
+// 16-byte shared-memory load.
+__device__ __forceinline__ float4 lds128(const void* p) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(smem_u32(p)));
+    return v;
+}
+
+// The FMAs of one column pair of a tile for thread (tq, cp): row part into racc,
+// column part (OFFDIAG) into cacc.
+template <int R, bool CONJ, bool OFFDIAG>
+__device__ __forceinline__ void sym_pair_fma(const float4* T4, const float2* xsl, int tq, int cp,
+                                             const float2 (&xi)[8][R], float2 (&racc)[8][R],
+                                             float2 (&cacc)[2][R]) {
+    float2 xj[2][R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float4 v = lds128(xsl + k * SYM_T + 2 * cp);
+        xj[0][k] = make_float2(v.x, v.y);
+        xj[1][k] = make_float2(v.z, v.w);
+        cacc[0][k] = cacc[1][k] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 e = lds128(T4 + i * 256 + tq);     // (8 rg + i, 2 cp) and (8 rg + i, 2 cp + 1)
+        const float a0r = e.x, a0i = CONJ ? -e.y : e.y, a1r = e.z, a1i = CONJ ? -e.w : e.w;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            float2 r = racc[i][k];
+            r.x = fmaf(a0r, xj[0][k].x, r.x); r.x = fmaf(-a0i, xj[0][k].y, r.x);
+            r.y = fmaf(a0r, xj[0][k].y, r.y); r.y = fmaf(a0i, xj[0][k].x, r.y);
+            r.x = fmaf(a1r, xj[1][k].x, r.x); r.x = fmaf(-a1i, xj[1][k].y, r.x);
+            r.y = fmaf(a1r, xj[1][k].y, r.y); r.y = fmaf(a1i, xj[1][k].x, r.y);
+            racc[i][k] = r;
+            if (OFFDIAG) {
+                const float2 v = xi[i][k];
+                float2 c0 = cacc[0][k], c1 = cacc[1][k];
+                c0.x = fmaf(a0r, v.x, c0.x); c0.x = fmaf(-a0i, v.y, c0.x);
+                c0.y = fmaf(a0r, v.y, c0.y); c0.y = fmaf(a0i, v.x, c0.y);
+                c1.x = fmaf(a1r, v.x, c1.x); c1.x = fmaf(-a1i, v.y, c1.x);
+                c1.y = fmaf(a1r, v.y, c1.y); c1.y = fmaf(a1i, v.x, c1.y);
+                cacc[0][k] = c0;
+                cacc[1][k] = c1;
+            }
+        }
+    }
+}
+
 // One (class c, tile row I) segment of R right-hand sides for consumer thread tid
 // (0..255): tiles sg.z .. sg.w-1 of the ring, u counts the CTA's tiles so far.
 // CONJ applies conj(S) instead of S.
+//
+// The consumers form two groups of four warps (group = warp / 4, one warp of each
+// group per scheduler); group g takes the CTA's tiles u with u % 2 == g, so the two
+// warps that share a scheduler are at different points of different tiles and one
+// hides the other's latency.  Thread (group warp wq, lane) of a group owns the
+// column pairs cp = 4 wq + lane / 8 and cp + 16 and the eight rows 8 rg .. 8 rg + 7
+// (rg = lane % 8) of its tiles.
 //
 // Both partial sums are reduced by halving exchanges (a reduce-scatter over lanes):
 // at each level a lane keeps half of its values, sends the other half to its partner
@@ -152,7 +208,8 @@ __device__ __forceinline__ bool sym_segment(const SymInfo& si, int4 sg, int s, i
                                             const float2* xs, uint64_t* full, uint64_t* empty,
                                             float2* __restrict__ rowpart, float* __restrict__ colpart, int tid) {
     const int I = sg.y;
-    const int warp = tid >> 5, lane = tid & 31, rg = lane & 7, cp = warp * 4 + (lane >> 3);
+    const int warp = tid >> 5, lane = tid & 31, rg = lane & 7, grp = warp >> 2, wq = warp & 3;
+    const int cp = wq * 4 + (lane >> 3), tq = wq * 32 + lane;      // tq: the pair's thread in the packing
     const bool b0 = lane & 1, b1 = lane & 2, b2 = lane & 4, b3 = lane & 8, b4 = lane & 16;
     float2 xi[8][R], racc[8][R];
 #pragma unroll
@@ -161,77 +218,59 @@ __device__ __forceinline__ bool sym_segment(const SymInfo& si, int4 sg, int s, i
         for (int k = 0; k < R; ++k) xi[i][k] = racc[i][k] = make_float2(0.f, 0.f);
     bool ok = true;
     const long long tb = si.tbase[sg.x] + (long long)I * (I + 1) / 2;
-    for (int t = sg.z; t < sg.w; ++t, ++u) {
+    const int skip = (grp + u) & 1;                  // this group's first tile of the segment
+    bool first = true;
+    for (int t = sg.z + skip, uu = u + skip; t < sg.w; t += 2, uu += 2) {
         const int J = (int)(t - tb);
         const bool offdiag = J < I;
-        const int slot = u % SYM_STAGES;
-        ok &= mbar_wait_bounded(&full[slot], (uint32_t)((u / SYM_STAGES) & 1));
+        const int slot = uu % SYM_STAGES;
+        ok &= mbar_wait_bounded(&full[slot], (uint32_t)((uu / SYM_STAGES) & 1));
         const float2* xsl = xs + (size_t)slot * SYM_XS_FLOAT2;      // [0][k][64] x_J, [1][k][64] x_I
-        if (t == sg.z) {
+        if (first) {
+            first = false;
 #pragma unroll
             for (int k = 0; k < R; ++k)
 #pragma unroll
                 for (int i = 0; i < 8; i += 2) {
-                    const float4 v = *reinterpret_cast<const float4*>(xsl + (SYM_RMAX + k) * SYM_T + rg * 8 + i);
+                    const float4 v = lds128(xsl + (SYM_RMAX + k) * SYM_T + rg * 8 + i);
                     xi[i][k] = make_float2(v.x, v.y);
                     xi[i + 1][k] = make_float2(v.z, v.w);
                 }
         }
-        float2 xj[2][R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const float4 v = *reinterpret_cast<const float4*>(xsl + k * SYM_T + 2 * cp);
-            xj[0][k] = make_float2(v.x, v.y);
-            xj[1][k] = make_float2(v.z, v.w);
-        }
         const float4* T4 = reinterpret_cast<const float4*>(ring + (size_t)slot * SYM_T * SYM_T);
-        float2 cacc[2][R];
+        // the two column pairs in turn (a rolled loop keeps the hot code small); one
+        // straight-line body per tile kind, so loads and FMAs schedule freely
+#pragma unroll 1
+        for (int p = 0; p < 2; ++p) {
+            const int cpp = cp + 16 * p;
+            float2 cacc[2][R];                       // [column of the pair][k]
+            if (offdiag) sym_pair_fma<R, CONJ, true>(T4, xsl, tq + 128 * p, cpp, xi, racc, cacc);
+            else sym_pair_fma<R, CONJ, false>(T4, xsl, tq + 128 * p, cpp, xi, racc, cacc);
+            if (offdiag) {
+                // column part: sum over the 8 row groups (lane bits 0-2).  Bit 2 picks the
+                // column of the pair, bit 1 the real or imaginary part; bit 0 adds the last pair.
+                float w[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) cacc[0][k] = cacc[1][k] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float4 e = T4[i * 256 + tid];            // (8 rg + i, 2 cp) and (8 rg + i, 2 cp + 1)
-            const float a0r = e.x, a0i = CONJ ? -e.y : e.y, a1r = e.z, a1i = CONJ ? -e.w : e.w;
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                float2 r = racc[i][k];
-                r.x = fmaf(a0r, xj[0][k].x, r.x); r.x = fmaf(-a0i, xj[0][k].y, r.x);
-                r.y = fmaf(a0r, xj[0][k].y, r.y); r.y = fmaf(a0i, xj[0][k].x, r.y);
-                r.x = fmaf(a1r, xj[1][k].x, r.x); r.x = fmaf(-a1i, xj[1][k].y, r.x);
-                r.y = fmaf(a1r, xj[1][k].y, r.y); r.y = fmaf(a1i, xj[1][k].x, r.y);
-                racc[i][k] = r;
-                if (offdiag) {
-                    const float2 v = xi[i][k];
-                    cacc[0][k].x = fmaf(a0r, v.x, cacc[0][k].x); cacc[0][k].x = fmaf(-a0i, v.y, cacc[0][k].x);
-                    cacc[0][k].y = fmaf(a0r, v.y, cacc[0][k].y); cacc[0][k].y = fmaf(a0i, v.x, cacc[0][k].y);
-                    cacc[1][k].x = fmaf(a1r, v.x, cacc[1][k].x); cacc[1][k].x = fmaf(-a1i, v.y, cacc[1][k].x);
-                    cacc[1][k].y = fmaf(a1r, v.y, cacc[1][k].y); cacc[1][k].y = fmaf(a1i, v.x, cacc[1][k].y);
+                for (int k = 0; k < R; ++k) {
+                    const float2 snd = b2 ? cacc[0][k] : cacc[1][k], kp = b2 ? cacc[1][k] : cacc[0][k];
+                    float2 v;
+                    v.x = kp.x + __shfl_xor_sync(0xffffffffu, snd.x, 4);
+                    v.y = kp.y + __shfl_xor_sync(0xffffffffu, snd.y, 4);
+                    w[k] = (b1 ? v.y : v.x) + __shfl_xor_sync(0xffffffffu, b1 ? v.x : v.y, 2);
+                    w[k] += __shfl_xor_sync(0xffffffffu, w[k], 1);
                 }
+                // colpart[t][k][64 columns] complex: the warp's 8 columns are 64 contiguous bytes per k
+                float* dst = colpart + (((size_t)t * SYM_RMAX) * SYM_T + 2 * cpp + (b2 ? 1 : 0)) * 2 + (b1 ? 1 : 0);
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+                    if (R == 1 ? !b0 : ((k & 1) != 0) == b0) dst[k * SYM_T * 2] = w[k];
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);          // the slot's data is in registers
-        if (offdiag) {
-            // column part: sum over the 8 row groups (lane bits 0-2).  Bit 2 picks the
-            // column of the pair, bit 1 the real or imaginary part; bit 0 adds the last pair.
-            float w[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                const float2 snd = b2 ? cacc[0][k] : cacc[1][k], kp = b2 ? cacc[1][k] : cacc[0][k];
-                float2 v;
-                v.x = kp.x + __shfl_xor_sync(0xffffffffu, snd.x, 4);
-                v.y = kp.y + __shfl_xor_sync(0xffffffffu, snd.y, 4);
-                w[k] = (b1 ? v.y : v.x) + __shfl_xor_sync(0xffffffffu, b1 ? v.x : v.y, 2);
-                w[k] += __shfl_xor_sync(0xffffffffu, w[k], 1);
-            }
-            // colpart[t][k][64 columns] complex: the warp's 8 columns are 64 contiguous bytes per k
-            float* dst = colpart + (((size_t)t * SYM_RMAX) * SYM_T + 2 * cp + (b2 ? 1 : 0)) * 2 + (b1 ? 1 : 0);
-#pragma unroll
-            for (int k = 0; k < R; ++k)
-                if (R == 1 ? !b0 : ((k & 1) != 0) == b0) dst[k * SYM_T * 2] = w[k];
-        }
     }
-    // row part of the segment, summed over the warp's 4 column pairs (lane bits 3, 4):
+    u += sg.w - sg.z;
+    // row part of the segment, summed over the warp's lanes that share rows (lane bits 3, 4):
     // bit 4 keeps rows 0-3 or 4-7 of the lane's eight, bit 3 a pair of those, so lane
     // (rg, q = lane / 8) ends with rows 8 rg + 2 q and 8 rg + 2 q + 1.  Each warp stores
     // its own partial (the back transform adds the 8 warps' values in a fixed order),
@@ -291,7 +330,7 @@ sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restr
     if (tid == 0) {
         for (int i = 0; i < SYM_STAGES; ++i) {
             mbar_init(&full[i], 32);                 // the producer warp's lanes (one with the tile bytes)
-            mbar_init(&empty[i], SYM_CONSUMERS);
+            mbar_init(&empty[i], SYM_CONSUMERS / 2);     // the group that consumes the slot
         }
         fence_mbar_init();
     }
