@@ -563,10 +563,13 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
                                                       (const Vc*)y_f, (Vc*)out, (Vc*)acc, cdt);
 }
 
-// One Horner stage: out = y + cdt * L(w).  For order 1 the interior part (stencil,
+// One Horner stage: out = y + cdt * L(w).  For order >= 1 the interior part (stencil,
 // which needs only w) and the boundary chain (which writes only the f part) are
 // independent: the stencil runs on the side stream, forked from and joined back
-// to s (inside a captured graph they become parallel branches).
+// to s (inside a captured graph they become parallel branches).  The fork follows
+// the contraction: its CTAs each need a whole SM (shared memory), so stencil blocks
+// resident at its launch would hold back its start; forked after it, the stencil
+// overlaps the back transform instead.
 template <typename T>
 void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, const void* y_phi, const void* y_f,
            void* o_phi, void* o_f, const T* V, cudaStream_t s) {
@@ -582,11 +585,11 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             order >= 1 ? (const Vc*)w_f : c->cnat.as<Vc>(), (Vc*)o_phi, cdt);
         prof_end(c, ABC_KERNEL_STENCIL, ss);
     };
-    if (order >= 1) {
+    auto fork_stencil = [&]() {
         cudaEventRecord(c->ev_fork, s);
         cudaStreamWaitEvent(c->side, c->ev_fork, 0);
         stencil(c->side);
-    }
+    };
     const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
     if (order == 2) {
         // g' = B1 g + (B0 - i A1) f - i A1 E H w + A0 E w  (eq:dynamics2 with E phidot substituted)
@@ -596,6 +599,7 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
                                                    c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), nullptr, (T)0, o2);
         const void* x4[4] = {c->hat_g.p, c->hat_f.p, c->hat_h.p, c->hat_phi.p};
         const TRes tr = contraction<T>(c, nullptr, c->tvec.p, n_orb, 0, s, x4);
+        fork_stencil();
         back<T, 3>(c, tr, n_orb, (T)0, (T)0, y_f, o_f, const_cast<void*>(w_f), cdt, s);
         cudaEventRecord(c->ev_join, c->side);
         cudaStreamWaitEvent(s, c->ev_join, 0);
@@ -606,6 +610,7 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
                                                c->hat_f.as<Vc>(), nullptr, (T)0, dev::Ord2Fwd<T>{});
     const TRes gathered = contraction<T>(c, order == 1 ? c->hat_f.p : c->hat_phi.p, c->tvec.p, n_orb, 0, s);
     if (order == 1) {
+        fork_stencil();
         back<T, 0>(c, gathered, n_orb, (T)c->blocks.s, a_coef, y_f, o_f, nullptr, cdt, s);
         cudaEventRecord(c->ev_join, c->side);
         cudaStreamWaitEvent(s, c->ev_join, 0);
