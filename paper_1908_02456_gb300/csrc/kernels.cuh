@@ -210,25 +210,56 @@ __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, lon
     }
 }
 
-// t from the partial sums of the tiled contraction (see SymGather).  The column
-// parts are read eight at a time into independent accumulators, so their loads are
-// in flight together; the sums are combined in a fixed order.
+// t from the partial sums of the tiled contraction (see SymGather).  The loads of the
+// first two row segments and the first 24 column parts are all issued before any
+// of them is used (one memory round trip for the common case); the sums are then
+// formed in a fixed order: eight accumulators (the row part of warp w into
+// accumulator w, column part K into accumulator (K - I - 1) % 8), added at the end.
 __device__ __forceinline__ float2 sym_gather(const SymGather& sg, int4 d) {
+    constexpr int RS = 2, CB = 3;                  // row segments and column batches of 8 hoisted
+    const int nk = d.w & 0xffff;
+    float2 rv[RS][8], cv[CB][8];
+#pragma unroll
+    for (int q = 0; q < RS; ++q)
+#pragma unroll
+        for (int w = 0; w < 8; ++w)
+            rv[q][w] = q < d.y ? sg.rowpart[d.x + (size_t)q * 1536 + w * 192] : make_float2(0.f, 0.f);
+    int e = d.z, step = d.w >> 16;
+#pragma unroll
+    for (int b = 0; b < CB; ++b)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            cv[b][q] = b * 8 + q < nk ? sg.colpart[e] : make_float2(0.f, 0.f);
+            e += step * 192;
+            ++step;
+        }
     float2 acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
-    for (int q = 0; q < d.y; ++q) {
-        const float2* rp = sg.rowpart + d.x + (size_t)q * 1536;
+#pragma unroll
+    for (int q = 0; q < RS; ++q)
 #pragma unroll
         for (int w = 0; w < 8; ++w) {                  // the 8 warps' partials of the segment
+            acc[w].x += rv[q][w].x;
+            acc[w].y += rv[q][w].y;
+        }
+    for (int q = RS; q < d.y; ++q) {
+        const float2* rp = sg.rowpart + d.x + (size_t)q * 1536;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
             const float2 v = rp[w * 192];
             acc[w].x += v.x;
             acc[w].y += v.y;
         }
     }
-    const int nk = d.w & 0xffff;
-    int e = d.z, step = d.w >> 16;
-    for (int i0 = 0; i0 < nk; i0 += 8) {
+#pragma unroll
+    for (int b = 0; b < CB; ++b)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            acc[q].x += cv[b][q].x;
+            acc[q].y += cv[b][q].y;
+        }
+    for (int i0 = CB * 8; i0 < nk; i0 += 8) {
         float2 v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -307,6 +338,12 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
     V x = mk<T>(0, 0);
     if (jj >= 0) {
         const long long e = (long long)j * ct.ng + jj;
+        // the adapted inputs are loaded before t, so their loads overlap the gather's
+        V fv = mk<T>(0, 0), pv = mk<T>(0, 0);
+        if (MODE == 0 || MODE == 2) {
+            fv = hat_f[e];
+            pv = hat_phi[e];
+        }
         V tv;
         if constexpr (GATHER) {
             const float2 q = sym_gather(sg, gd);
@@ -321,13 +358,11 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
         }
         if (MODE == 0) {
             const T a = a_coef * c_cell;
-            const V fv = hat_f[e], pv = hat_phi[e];
             const T dr = pv.x - tv.x, di = pv.y - tv.y;
             x = mk<T>(s1 * fv.x + a * di, s1 * fv.y - a * dr);
         } else if (MODE == 1 || MODE == 3) {
             x = tv;
         } else {
-            const V fv = hat_f[e], pv = hat_phi[e];
             x = mk<T>(s1 * fv.x - tv.x - pv.y, s1 * fv.y - tv.y + pv.x);
         }
     }
