@@ -71,12 +71,30 @@ extern "C" {
                                   lo and three products per term (FP32-level error),
                                   FP32 accumulation; n_orb = 1 as ABC_C64_FP32      */
 
+/* how the order-1 coefficients of R_11(s) = (sI - B)^{-1} A are fitted to K(s) */
+#define ABC_FIT1_LIMIT 0       /* Thm 3.2: R_11(s1) = K(s1) and the s -> infinity
+                                  limit, A = -i H_{Gamma,II} H_{II,Gamma} (diagonal
+                                  for radius 1), B = s1 I - A K(s1)^{-1}             */
+#define ABC_FIT1_TWO_POINT 1   /* R_11(s1) = K(s1), R_11(s1b) = K(s1b), both finite
+                                  (the variant Sec. 3.2 reports as still stable):
+                                  B = (s1 K1 - s1b K2)(K1 - K2)^{-1},
+                                  A = (s1 I - B) K1; B and A dense per class         */
+#define ABC_FIT1_HERMITE 2     /* value and derivative at s1 (eq:39, App. C):
+                                  (s1 I - B)^{-1} A = K(s1), (s1 I - B)^{-2} A =
+                                  -K'(s1); B = s1 I + K1 K1'^{-1},
+                                  A = -K1 K1'^{-1} K1                                */
+
 /* matrices for abc_get_matrices / abc_host_matrices (dense, natural Gamma order) */
-#define ABC_MAT_K 0            /* K(s) at the context's interpolation point        */
+#define ABC_MAT_K 0            /* K(s) at the context's interpolation point (orders
+                                  0 and 1 with the limit fit)                       */
 #define ABC_MAT_M 1            /* order 0: M = K(s0)                                */
 #define ABC_MAT_A 2            /* order 1: A                                        */
 #define ABC_MAT_B 3            /* order 1: B                                        */
-#define ABC_MAT_Q 4            /* order 1: Q = (H_{Gamma,II} H_{II,Gamma})^{-1}     */
+#define ABC_MAT_Q 4            /* order 1: Q = (H_{Gamma,II} H_{II,Gamma})^{-1}
+                                  (the Lyapunov weight of Thm 3.2; with the
+                                  two-point and Hermite fits it is the weight of
+                                  the diagnostic W only, not a proven Lyapunov
+                                  functional)                                       */
 #define ABC_MAT_B1 5           /* order 2: B1 of R_22 (Sec. 3.3, eq:dynamics2)      */
 #define ABC_MAT_B0 6           /* order 2: B0                                       */
 #define ABC_MAT_A1 7           /* order 2: A1                                       */
@@ -98,6 +116,12 @@ typedef struct {
                          1 .. 65535                                                 */
     double s2[4];     /* order 2 interpolation points, > 0 and distinct (Sec. 3.3:
                          R_22(s) = (s^2 I - s B1 - B0)^{-1}(s A1 + A0) = K(s) there) */
+    int fit1;         /* order 1: ABC_FIT1_LIMIT (0, default), ABC_FIT1_TWO_POINT or
+                         ABC_FIT1_HERMITE; must be 0 for orders 0 and 2.  The fitted
+                         forms run on the dense class blocks [B | A] (no packed
+                         symmetric tiles, no tensor-core image); the adjoint and
+                         abc_step_noalloc cover the limit fit only                    */
+    double s1b;       /* ABC_FIT1_TWO_POINT: the second point, > 0 and != s1        */
 } abc_params;
 
 typedef struct {

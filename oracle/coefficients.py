@@ -11,6 +11,13 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
     Q = (H_{Gamma,II} H_{II,Gamma})^{-1} (the Lyapunov weight of eq:lyapunov1).
   H_{Gamma,II} H_{II,Gamma} = H_{Gamma,Sigma} H_{Sigma,Gamma} because H_{Gamma,II} is
   non-zero only on Sigma.
+* Order 1, other fits of the same R_11(s) = (sI - B)^{-1} A (both B and A dense):
+    two finite points (Sec. 3.2's closing remark: still stable with s2 finite):
+      R_11(s1) = K(s1), R_11(s2) = K(s2), i.e. (s_j I - B) K_j = A for j = 1, 2;
+    value and derivative at s1 (App. C, eq:39):
+      (s1 I - B)^{-1} A = K(s1),  (s1 I - B)^{-2} A = -K'(s1).
+  Both are solved here as the linear systems they are.  Q stays the Thm 3.2 weight
+  (H_{Gamma,II} H_{II,Gamma})^{-1}, used for the diagnostic W only.
 * Order 2 (Sec. 3.3, eq:dynamics2): R_22(s) = (s^2 I - s B1 - B0)^{-1} (s A1 + A0),
   fitted by interpolation at four points s_j (R_22(s_j) = K(s_j)); each condition
   s_j^2 K_j = s_j B1 K_j + B0 K_j + s_j A1 + A0 is linear in [B1, B0, A1, A0].
@@ -19,7 +26,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .dtn import dtn_eval
+from .dtn import dtn_eval, dtn_eval_deriv
 from .lattice import Box
 
 
@@ -36,6 +43,45 @@ def order1(box: Box, s1: float, K1=None) -> dict:
     B = s1 * np.eye(len(Hgg)) - A @ np.linalg.inv(K1)
     Q = np.linalg.inv(Hgg)
     return {"order": 1, "s": s1, "A": A, "B": B, "Q": Q, "K1": K1}
+
+
+def order1_two_point(box: Box, s1: float, s2: float, K1=None, K2=None) -> dict:
+    """B and A from (s1 I - B) K1 = A and (s2 I - B) K2 = A: subtracting gives
+    B (K1 - K2) = s1 K1 - s2 K2; then A = (s1 I - B) K1."""
+    if not (s1 > 0 and s2 > 0) or s1 == s2:
+        raise ValueError("two distinct positive interpolation points are needed")
+    K1 = dtn_eval(box, s1) if K1 is None else K1
+    K2 = dtn_eval(box, s2) if K2 is None else K2
+    n = K1.shape[0]
+    # B D = C  <=>  D^T B^T = C^T
+    B = np.linalg.solve((K1 - K2).T, (s1 * K1 - s2 * K2).T).T
+    A = (s1 * np.eye(n) - B) @ K1
+    _, HGS = box.sigma()
+    Q = np.linalg.inv(HGS @ HGS.T)
+    return {"order": 1, "fit": "two_point", "s": s1, "s2": s2, "A": A, "B": B, "Q": Q, "K1": K1, "K2": K2}
+
+
+def order1_hermite(box: Box, s1: float, K1=None, dK1=None) -> dict:
+    """eq:39: with X = (s1 I - B)^{-1}, X A = K1 and X (X A) = -K1' give X K1 = -K1', so
+    X = -K1' K1^{-1}; then B = s1 I - X^{-1} and A = X^{-1} K1."""
+    if not s1 > 0:
+        raise ValueError("the interpolation point must be positive")
+    K1 = dtn_eval(box, s1) if K1 is None else K1
+    dK1 = dtn_eval_deriv(box, s1) if dK1 is None else dK1
+    n = K1.shape[0]
+    X = -dK1 @ np.linalg.inv(K1)
+    Xi = np.linalg.inv(X)
+    B = s1 * np.eye(n) - Xi
+    A = Xi @ K1
+    _, HGS = box.sigma()
+    Q = np.linalg.inv(HGS @ HGS.T)
+    return {"order": 1, "fit": "hermite", "s": s1, "A": A, "B": B, "Q": Q, "K1": K1, "dK1": dK1}
+
+
+def rational11(co: dict, s: float) -> np.ndarray:
+    """R_11(s) = (sI - B)^{-1} A."""
+    n = co["B"].shape[0]
+    return np.linalg.solve(s * np.eye(n) - co["B"], co["A"])
 
 
 def order2(box: Box, points=(1.0, 2.0, 3.0, 10.0), Ks=None) -> dict:

@@ -16,6 +16,8 @@ Two independent routes to the same matrix:
   App. D sampled on P points); the periodic Green's function is the sum of the free one
   over all images, so P is chosen so that the images are below 1e-17.
 
+``dtn_eval_deriv`` gives K'(s) (the Hermite fit, eq:39) by differentiating eq:eval.
+
 Plus the 1D closed form: with R = 1 each end of a 1D box sees a half-line, and
 f_Gamma = H_{Gamma,II} phi_II = -(1/2h^2) u phi_Gamma, where u is the root with |u| < 1
 of u + 1/u = 2 - 2 i s h^2 (the exterior equation (H - i s) phi = 0 solved by phi_j ~ u^j).
@@ -50,7 +52,9 @@ def dtn_1d_closed(h: float, s: float) -> complex:
 class FreeGreen:
     """G(Delta) = [(H_0 - i s)^{-1}](Delta) on the infinite lattice, V = 0."""
 
-    def __init__(self, d: int, h: float, R: int, s: float, max_offset: int, P: int | None = None):
+    def __init__(self, d: int, h: float, R: int, s: float, max_offset: int, P: int | None = None,
+                 deriv: bool = False):
+        """deriv: the table of dG/ds = i G^2 instead of G (symbol i / (sigma - i s)^2)."""
         self.d, self.h, self.R, self.s = d, h, R, s
         if P is None:
             rate = -math.log(abs(decay_root_1d(s, h)))
@@ -67,7 +71,10 @@ class FreeGreen:
             shp[k] = P
             symbol = symbol + sym1.reshape(shp)
         symbol = symbol - 1j * s
-        self.table = np.fft.ifftn(1.0 / symbol)   # periodic Green's function
+        if deriv:
+            self.table = np.fft.ifftn(1j / symbol ** 2)
+        else:
+            self.table = np.fft.ifftn(1.0 / symbol)   # periodic Green's function
 
     def __call__(self, delta: np.ndarray) -> np.ndarray:
         delta = np.asarray(delta) % self.P
@@ -87,6 +94,27 @@ def dtn_eval(box: Box, s: float, P: int | None = None) -> np.ndarray:
     X = np.eye(len(G_idx)) - HGS @ G_SG
     Y = HGS @ G_SS @ HSG
     return -np.linalg.solve(X, Y)
+
+
+def dtn_eval_deriv(box: Box, s: float, P: int | None = None) -> np.ndarray:
+    """K'(s) = dK/ds by differentiating eq:eval: with X = I - H_{Gamma,Sigma} G_{Sigma,Gamma}
+    and Y = H_{Gamma,Sigma} G_{Sigma,Sigma} H_{Sigma,Gamma}, X K = -Y gives
+    K' = -X^{-1} (Y' + X' K), and G' = dG/ds = i G^2 (G = (H_0 - i s)^{-1})."""
+    G_idx = box.gamma()
+    Cg = box.coords()[G_idx]
+    Sg, HGS = box.sigma()
+    HSG = HGS.T
+    span = max(box.dims) + 2 * box.R
+    g = FreeGreen(box.d, box.h, box.R, s, span, P)
+    gd = FreeGreen(box.d, box.h, box.R, s, span, g.P, deriv=True)
+    dSG = Sg[:, None, :] - Cg[None, :, :]
+    dSS = Sg[:, None, :] - Sg[None, :, :]
+    X = np.eye(len(G_idx)) - HGS @ g(dSG)
+    Y = HGS @ g(dSS) @ HSG
+    K = -np.linalg.solve(X, Y)
+    Xd = -(HGS @ gd(dSG))
+    Yd = HGS @ gd(dSS) @ HSG
+    return -np.linalg.solve(X, Yd + Xd @ K)
 
 
 def dtn_bruteforce(box: Box, s: float, L: int) -> np.ndarray:

@@ -20,6 +20,8 @@ MAT_B1, MAT_B0, MAT_A1, MAT_A0 = 5, 6, 7, 8
 KERNEL_CONTRACTION, KERNEL_STENCIL = 0, 1
 TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT, TUNE_PDL = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16, "tf32x3": C64_3XTF32}
+FIT1_LIMIT, FIT1_TWO_POINT, FIT1_HERMITE = 0, 1, 2
+FITS1 = {"limit": FIT1_LIMIT, "two_point": FIT1_TWO_POINT, "hermite": FIT1_HERMITE}
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libabc.so")
 
@@ -37,7 +39,8 @@ class abc_grid(ctypes.Structure):
 
 class abc_params(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("s0", ctypes.c_double), ("s1", ctypes.c_double),
-                ("precision", ctypes.c_int), ("max_orbitals", ctypes.c_int), ("s2", ctypes.c_double * 4)]
+                ("precision", ctypes.c_int), ("max_orbitals", ctypes.c_int), ("s2", ctypes.c_double * 4),
+                ("fit1", ctypes.c_int), ("s1b", ctypes.c_double)]
 
 
 class abc_meanfield(ctypes.Structure):
@@ -102,15 +105,19 @@ def _grid(shape: Sequence[int], h: float) -> abc_grid:
     return abc_grid(nx, ny, nz, 1, float(h))
 
 
-def _params(order: int, s, precision, max_orbitals: int) -> abc_params:
-    """s: the interpolation point (orders 0, 1) or the four points (order 2)."""
+def _params(order: int, s, precision, max_orbitals: int, fit1="limit", s1b: float = 0.0) -> abc_params:
+    """s: the interpolation point (orders 0, 1) or the four points (order 2); fit1 (order 1):
+    "limit" (Thm 3.2), "two_point" (with the second point s1b) or "hermite" (eq:39)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    fit = FITS1[fit1] if isinstance(fit1, str) else int(fit1)
     if int(order) == 2:
         pts = [float(v) for v in s]
         if len(pts) != 4:
             raise ValueError("order 2 needs four interpolation points")
-        return abc_params(2, pts[0], pts[0], prec, int(max_orbitals), (ctypes.c_double * 4)(*pts))
-    return abc_params(int(order), float(s), float(s), prec, int(max_orbitals), (ctypes.c_double * 4)(0, 0, 0, 0))
+        return abc_params(2, pts[0], pts[0], prec, int(max_orbitals), (ctypes.c_double * 4)(*pts), fit,
+                          float(s1b))
+    return abc_params(int(order), float(s), float(s), prec, int(max_orbitals), (ctypes.c_double * 4)(0, 0, 0, 0),
+                      fit, float(s1b))
 
 
 def _mf(meanfield) -> Optional[ctypes.POINTER(abc_meanfield)]:
@@ -173,12 +180,12 @@ def abc_get_matrices(ctx, which: int, n_gamma: int) -> np.ndarray:
     return out
 
 
-def abc_host_matrices(shape, h, order, s, which) -> np.ndarray:
+def abc_host_matrices(shape, h, order, s, which, fit1="limit", s1b: float = 0.0) -> np.ndarray:
     """FP64 setup on the host only (no CUDA): dense ABC_MAT_* in natural Gamma order."""
     nx, ny, nz = shape
     n = nx * ny * nz - (nx - 2) * (ny - 2) * (nz - 2)
     out = np.zeros((n, n), np.complex128)
-    g, p = _grid(shape, h), _params(order, s, FP64, 1)
+    g, p = _grid(shape, h), _params(order, s, FP64, 1, fit1, s1b)
     _check(load().abc_host_matrices(ctypes.byref(g), ctypes.byref(p), which, out.ctypes.data_as(_P), out.nbytes))
     return out
 
@@ -233,13 +240,16 @@ def abc_destroy(ctx):
 class Context:
     """Owns one abc_ctx.  psi: [b, nz, ny, nx] complex CUDA tensor; aux: [n_gamma, b]."""
 
-    def __init__(self, shape, h, order, s, precision="c64", max_orbitals=1):
+    def __init__(self, shape, h, order, s, precision="c64", max_orbitals=1, fit1="limit", s1b=0.0):
         self.shape = tuple(int(v) for v in shape)
         self.h, self.order = float(h), int(order)
         self.s = tuple(float(v) for v in s) if self.order == 2 else float(s)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.max_orbitals = int(max_orbitals)
-        self.ctx = abc_setup(_grid(self.shape, h), _params(order, s, self.precision, max_orbitals))
+        self.fit1 = FITS1[fit1] if isinstance(fit1, str) else int(fit1)
+        self.s1b = float(s1b)
+        self.ctx = abc_setup(_grid(self.shape, h),
+                             _params(order, s, self.precision, max_orbitals, self.fit1, self.s1b))
         self.n_gamma = abc_boundary_size(self.ctx)
 
     # dtypes of the path

@@ -88,7 +88,8 @@ int upload_tables(abc_ctx* c) {
 int upload_matrices(abc_ctx* c) {
     const Geometry& g = c->geo;
     const bool o2 = c->params.order == 2;
-    const int nseg = o2 ? 4 : 1;
+    const bool f1 = c->params.order == 1 && c->params.fit1 != ABC_FIT1_LIMIT;
+    const int nseg = o2 ? 4 : f1 ? 2 : 1;
     long long total = 0;
     std::vector<long long> moff(g.cls.size());
     std::vector<int> lds(g.cls.size()), segw(g.cls.size());
@@ -121,8 +122,10 @@ int upload_matrices(abc_ctx* c) {
     for (size_t k = 0; k < g.cls.size(); ++k) {
         const int m = g.cls[k].m, ld = lds[k];
         // row a, segment q: order 2 [B1 | B0 - i A1 | -i A1 | A0] (the g equation with
-        // E phidot = -i E H w - i f substituted); otherwise the single class block
+        // E phidot = -i E H w - i f substituted); fitted order 1 [B | A]; otherwise the
+        // single class block
         auto entry = [&](int q, int a, int b) -> cd {
+            if (f1) return c->blocks.mat2[q][k][(size_t)a * m + b];
             if (!o2) return c->blocks.mat[k][(size_t)a * m + b];
             const size_t e = (size_t)a * m + b;
             const cd mi(0.0, -1.0);
@@ -608,6 +611,16 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
     dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
                                                order == 1 ? (const Vc*)w_f : nullptr, c->hat_phi.as<Vc>(),
                                                c->hat_f.as<Vc>(), nullptr, (T)0, dev::Ord2Fwd<T>{});
+    if (order == 1 && c->params.fit1 != ABC_FIT1_LIMIT) {
+        // fitted B and A: t = B f_hat + A phi_hat on the rows [B | A], f' = t
+        const void* x2[4] = {c->hat_f.p, c->hat_phi.p, nullptr, nullptr};
+        const TRes tr = contraction<T>(c, nullptr, c->tvec.p, n_orb, 0, s, x2);
+        fork_stencil();
+        back<T, 4>(c, tr, n_orb, (T)0, (T)0, y_f, o_f, nullptr, cdt, s);
+        cudaEventRecord(c->ev_join, c->side);
+        cudaStreamWaitEvent(s, c->ev_join, 0);
+        return;
+    }
     const TRes gathered = contraction<T>(c, order == 1 ? c->hat_f.p : c->hat_phi.p, c->tvec.p, n_orb, 0, s);
     if (order == 1) {
         fork_stencil();
@@ -712,9 +725,7 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     st = build_geometry(grid->nx, grid->ny, grid->nz, grid->h, c->geo, err);
     if (st) return fail(st, err);
     c->nvox = c->geo.n_nodes;
-    st = params->order == 2 ? compute_blocks2(c->geo, params->s2, c->blocks, err)
-                            : compute_blocks(c->geo, params->order, params->order == 0 ? params->s0 : params->s1,
-                                             c->blocks, err);
+    st = compute_param_blocks(c->geo, *params, c->blocks, err);
     if (st) return fail(st, err);
     CUDA_TRY(cudaGetDevice(&c->device));
     if ((st = upload_tables(c.get()))) return st;
@@ -722,9 +733,11 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     if ((st = ensure_workspace(c.get()))) return st;
     if ((st = c->diag.alloc(sizeof(double) * 3 * params->max_orbitals))) return st;
     if ((st = build_tiles(c.get()))) return st;
-    // the packed symmetric tiles and the tensor-core image hold one m x m block per class
-    // (orders 0, 1); the order-2 rows [B1 | B0 - i A1 | -i A1 | A0] use the full-block kernels
-    const bool one_seg = params->order < 2;
+    // the packed symmetric tiles and the tensor-core image hold one symmetric m x m block
+    // per class (order 0, order 1 with the limit fit); the order-2 rows
+    // [B1 | B0 - i A1 | -i A1 | A0] and the fitted order-1 rows [B | A] use the
+    // full-block kernels
+    const bool one_seg = params->order < 2 && params->fit1 == ABC_FIT1_LIMIT;
     if (one_seg && (c->prec == ABC_C64_FP32 || c->prec == ABC_C64_3XTF32) && (st = build_sym(c.get()))) return st;
     if (one_seg && c->prec == ABC_C64_3XTF32 && (st = build_tc(c.get()))) return st;
     if (!c->err_flag.p) {
@@ -1028,6 +1041,8 @@ extern "C" int abc_adjoint_run(abc_ctx* ctx, const void* psi0, const void* V, in
     if (nsteps < 0) return fail(ABC_ERR_ARG, "nsteps must be >= 0");
     if (ckpt_every < 1) return fail(ABC_ERR_ARG, "ckpt_every must be >= 1");
     if (ctx->params.order == 2) return fail(ABC_ERR_UNSUPPORTED, "the adjoint covers orders 0 and 1");
+    if (ctx->params.fit1 != ABC_FIT1_LIMIT)
+        return fail(ABC_ERR_UNSUPPORTED, "the adjoint covers the limit fit of order 1 (Thm 3.2) only");
     cudaStream_t s = (cudaStream_t)stream;
     if (ctx->prec == ABC_FP64) return adjoint_impl<double>(ctx, psi0, V, n_orb, dt, nsteps, ckpt_every, J_out, dJdV, s);
     return adjoint_impl<float>(ctx, psi0, V, n_orb, dt, nsteps, ckpt_every, J_out, dJdV, s);

@@ -46,6 +46,12 @@ int check_params(const abc_grid* grid, const abc_params* params) {
         const double s = params->order == 0 ? params->s0 : params->s1;
         if (!(s > 0.0)) return fail(ABC_ERR_ARG, "interpolation point must be > 0");
     }
+    if (params->fit1 < ABC_FIT1_LIMIT || params->fit1 > ABC_FIT1_HERMITE)
+        return fail(ABC_ERR_ARG, "fit1 must be ABC_FIT1_LIMIT, ABC_FIT1_TWO_POINT or ABC_FIT1_HERMITE");
+    if (params->fit1 != ABC_FIT1_LIMIT && params->order != 1)
+        return fail(ABC_ERR_ARG, "fit1 applies to order 1 only");
+    if (params->fit1 == ABC_FIT1_TWO_POINT && (!(params->s1b > 0.0) || params->s1b == params->s1))
+        return fail(ABC_ERR_ARG, "the two-point fit needs s1b > 0 and s1b != s1");
     if (params->precision < ABC_FP64 || params->precision > ABC_C64_3XTF32)
         return fail(ABC_ERR_ARG, "unknown precision");
     if (params->precision == ABC_C64_SPLIT_BF16)
@@ -67,8 +73,7 @@ extern "C" int abc_host_matrices(const abc_grid* grid, const abc_params* params,
     if (st) return fail(st, err);
     if (bytes < (size_t)16 * g.n_gamma * g.n_gamma) return fail(ABC_ERR_ARG, "destination too small");
     Blocks b;
-    st = params->order == 2 ? compute_blocks2(g, params->s2, b, err)
-                            : compute_blocks(g, params->order, params->order == 0 ? params->s0 : params->s1, b, err);
+    st = compute_param_blocks(g, *params, b, err);
     if (st) return fail(st, err);
     st = dense_natural(g, b, which, reinterpret_cast<cd*>(host_dst), err);
     if (st) return fail(st, err);

@@ -102,10 +102,12 @@ int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& e
 // Both are complex symmetric.
 struct Blocks {
     int order = 0;
-    double s = 0.0;
+    int fit = 0;          // order 1: ABC_FIT1_*
+    double s = 0.0, s1b = 0.0;
     std::vector<std::vector<cd>> mat;
-    // order 2: per class the four coefficient blocks B1, B0, A1, A0 (row-major m x m,
-    // general complex), and the interpolation points
+    // order 2: per class the four coefficient blocks B1, B0, A1, A0; order 1 with a
+    // two-point or Hermite fit: B, A in mat2[0], mat2[1] (row-major m x m, general
+    // complex); and the interpolation points
     std::vector<std::vector<cd>> mat2[4];
     double s2[4] = {0, 0, 0, 0};
 };
@@ -118,14 +120,24 @@ int compute_blocks2(const Geometry& g, const double s[4], Blocks& b, std::string
 // irreducible blocks whose base is b: sum over classes and components of W blk W^T.
 void expand_base_block(const Geometry& g, int b, const std::vector<std::vector<cd>>& blk, std::vector<cd>& out);
 
-int compute_blocks(const Geometry& g, int order, double s, Blocks& b, std::string& err);
+// Class blocks of K(s) (order 0: M = K(s); order 1: S = K(s)^{-1}).  dK (order 0 only):
+// also the class blocks of K'(s) = dK/ds, row-major.
+int compute_blocks(const Geometry& g, int order, double s, Blocks& b, std::string& err,
+                   std::vector<std::vector<cd>>* dK = nullptr);
+
+// Order-1 coefficients fitted by two finite points or by value and derivative
+// (ABC_FIT1_TWO_POINT / ABC_FIT1_HERMITE): per class B (mat2[0]) and A (mat2[1]).
+int compute_blocks_fit1(const Geometry& g, int fit, double s1, double s1b, Blocks& b, std::string& err);
+
+// The blocks a parameter set asks for (dispatch on order and fit).
+int compute_param_blocks(const Geometry& g, const abc_params& p, Blocks& b, std::string& err);
 
 // Dense natural-order (row-major n_gamma^2) reconstruction of ABC_MAT_* from blocks.
 int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::string& err);
 
 // Free lattice Green's function table G(|dx|,|dy|,|dz|) = [(H_0 - i s)^{-1}](dx,dy,dz)
-// for 0 <= |d| < dims[a]; layout [(c*dy)+b]*dx + a.
-void free_green_table(double h, double s, int dx, int dy, int dz, std::vector<cd>& table);
+// for 0 <= |d| < dims[a]; layout [(c*dy)+b]*dx + a.  deriv: dG/ds instead (= i G^2).
+void free_green_table(double h, double s, int dx, int dy, int dz, std::vector<cd>& table, bool deriv = false);
 
 // Dense complex LU with partial pivoting (column-major), and the solve with many
 // right-hand sides.  Return 0, or k+1 if U(k,k) == 0.

@@ -289,13 +289,15 @@ __device__ __forceinline__ float2 sym_gather(const SymGather& sg, int4 d) {
 //   MODE 3 (order-2 step):    x = t  (t = B1 g + (B0 - i A1) f - i A1 E H w + A0 E phi, the
 //                             derivative of g); y_f / out / acc are then the step-start,
 //                             stage-output and stage-input auxiliary states [f | g]
+//   MODE 4 (order-1 step, two-point or Hermite fit): x = t  (t = B f_hat + A phi_hat,
+//                             both general class blocks)
 // with t read from t_in (the sum of its nsplit arrays split_stride apart), or
 // gathered from the tiled contraction's partial sums (GATHER);
 // then thread (s, p) undoes the mixing with the scaled transposed coefficients, the
 // slot's 8-lane group transforms back and lane g holds the value v at the
 // reflection g of the slot's representative.  At that node's Gamma index e, the
 // lane that owns the node (table wr) writes:
-//   MODE 0: out[e] = y_f[e] + cdt v      MODE 1: out[e] = v
+//   MODE 0, 4: out[e] = y_f[e] + cdt v   MODE 1: out[e] = v
 //   MODE 2: out[e] = cdt v, acc[e] += cdt v
 //   MODE 3: out_f[e] = y_f[e] + cdt w_g[e], out_g[e] = y_g[e] + cdt v  (f' = g, g' = v)
 // (only the owner reads y_f / acc there, so the update in place is race-free).
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
     V yv = mk<T>(0, 0), yg = mk<T>(0, 0), wg = mk<T>(0, 0);
     const long long ew = (long long)(wr >= 0 ? wr : 0) * n_orb + j;
     const long long gofs = (long long)ct.n_gamma * n_orb;      // g part of an order-2 auxiliary state
-    if (wr >= 0 && MODE == 0) yv = y_f[ew];
+    if (wr >= 0 && (MODE == 0 || MODE == 4)) yv = y_f[ew];
     if (wr >= 0 && MODE == 2) yv = acc[ew];
     if (wr >= 0 && MODE == 3) {
         yv = y_f[ew];
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
             const T a = a_coef * c_cell;
             const T dr = pv.x - tv.x, di = pv.y - tv.y;
             x = mk<T>(s1 * fv.x + a * di, s1 * fv.y - a * dr);
-        } else if (MODE == 1 || MODE == 3) {
+        } else if (MODE == 1 || MODE == 3 || MODE == 4) {
             x = tv;
         } else {
             x = mk<T>(s1 * fv.x - tv.x - pv.y, s1 * fv.y - tv.y + pv.x);
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
     }
     v = wht8_lanes(v, g);
     if (wr < 0) return;
-    if (MODE == 0) {
+    if (MODE == 0 || MODE == 4) {
         out[ew] = mk<T>(yv.x + cdt * v.x, yv.y + cdt * v.y);
     } else if (MODE == 1) {
         out[ew] = v;

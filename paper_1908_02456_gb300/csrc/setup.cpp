@@ -212,7 +212,7 @@ static void bessel_j_all(double x, int nmax, double* out) {
     for (int n = 0; n <= nmax; ++n) out[n] *= inv;
 }
 
-void free_green_table(double h, double s, int dx, int dy, int dz, std::vector<cd>& table) {
+void free_green_table(double h, double s, int dx, int dy, int dz, std::vector<cd>& table, bool deriv) {
     const int M = std::max(dx, std::max(dy, dz));
     const double sh2 = s * h * h;
     const double xmax = 40.0 / sh2;
@@ -227,7 +227,9 @@ void free_green_table(double h, double s, int dx, int dy, int dz, std::vector<cd
         for (int i = 0; i < NG; ++i) {
             const double x = pn + 0.5 * (gx[i] + 1.0);
             xq[pn * NG + i] = x;
-            wq[pn * NG + i] = 0.5 * gw[i] * std::exp(-sh2 * x) * cd(std::cos(3.0 * x), -std::sin(3.0 * x));
+            // d/ds of the integrand is -h^2 x times the integrand
+            wq[pn * NG + i] = 0.5 * gw[i] * std::exp(-sh2 * x) * cd(std::cos(3.0 * x), -std::sin(3.0 * x)) *
+                              (deriv ? -h * h * x : 1.0);
         }
     // Bessel table J[n][q]
     std::vector<double> J((size_t)M * Q);
@@ -308,14 +310,22 @@ Nb exterior_neighbours(int i, int j, int k, int nx, int ny, int nz) {
 }
 }  // namespace
 
-int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::string& err) {
+int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::string& err,
+                   std::vector<std::vector<cd>>* dK) {
     if (!(s > 0.0)) { err = "interpolation point must be positive"; return ABC_ERR_ARG; }
+    if (dK && order != 0) { err = "internal: K' is formed on the order-0 route"; return ABC_ERR_ARG; }
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int tx = nx + 2, ty = ny + 2, tz = nz + 2;
-    std::vector<cd> G;
+    // with dK, a second pass over the same loops with G' = dG/ds gives X' and Y'
+    // (X = I + ..., so X' has no identity term)
+    std::vector<cd> G, Gd;
     free_green_table(g.h, s, tx, ty, tz, G);
+    if (dK) free_green_table(g.h, s, tx, ty, tz, Gd, true);
     auto Gt = [&](int dx, int dy, int dz) -> cd {
         return G[((size_t)std::abs(dz) * ty + std::abs(dy)) * tx + std::abs(dx)];
+    };
+    auto Gdt = [&](int dx, int dy, int dz) -> cd {
+        return Gd[((size_t)std::abs(dz) * ty + std::abs(dy)) * tx + std::abs(dx)];
     };
     const double ih2 = 1.0 / (2.0 * g.h * g.h), ih4 = 1.0 / (4.0 * std::pow(g.h, 4));
     const int R = g.n_rep;
@@ -327,46 +337,64 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
         nb[r] = exterior_neighbours(rc[r][0], rc[r][1], rc[r][2], nx, ny, nz);
     }
     const int dims[3] = {nx, ny, nz};
-    std::vector<cd> X[8], Y[8];
+    std::vector<cd> X[8], Y[8], Xd[8], Yd[8];
     for (int p = 0; p < 8; ++p) {
         if (g.base_of[p] != p) continue;
         X[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
         Y[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
+        if (dK) {
+            Xd[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
+            Yd[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
+        }
     }
 #pragma omp parallel for schedule(dynamic, 4)
     for (int ri = 0; ri < R; ++ri) {
         const int* ci = rc[ri].data();
         const Nb& ni = nb[ri];
         for (int rj = 0; rj < R; ++rj) {
-            cd xv[8], yv[8];
+            cd xv[8], yv[8], xdv[8], ydv[8];
             for (int gg = 0; gg < 8; ++gg) {
                 int y[3];
                 for (int a = 0; a < 3; ++a) y[a] = (gg >> a & 1) ? dims[a] - 1 - rc[rj][a] : rc[rj][a];
                 cd xs = (y[0] == ci[0] && y[1] == ci[1] && y[2] == ci[2]) ? cd(1.0, 0.0) : cd(0.0, 0.0);
-                for (int u = 0; u < ni.n; ++u)
+                cd xds(0.0, 0.0);
+                for (int u = 0; u < ni.n; ++u) {
                     xs += ih2 * Gt(ni.c[u][0] - y[0], ni.c[u][1] - y[1], ni.c[u][2] - y[2]);
+                    if (dK) xds += ih2 * Gdt(ni.c[u][0] - y[0], ni.c[u][1] - y[1], ni.c[u][2] - y[2]);
+                }
                 const Nb ny_ = exterior_neighbours(y[0], y[1], y[2], nx, ny, nz);
-                cd ys(0.0, 0.0);
+                cd ys(0.0, 0.0), yds(0.0, 0.0);
                 for (int u = 0; u < ni.n; ++u)
-                    for (int v = 0; v < ny_.n; ++v)
+                    for (int v = 0; v < ny_.n; ++v) {
                         ys += Gt(ni.c[u][0] - ny_.c[v][0], ni.c[u][1] - ny_.c[v][1], ni.c[u][2] - ny_.c[v][2]);
+                        if (dK)
+                            yds += Gdt(ni.c[u][0] - ny_.c[v][0], ni.c[u][1] - ny_.c[v][1], ni.c[u][2] - ny_.c[v][2]);
+                    }
                 xv[gg] = xs;
                 yv[gg] = ih4 * ys;
+                xdv[gg] = xds;
+                ydv[gg] = ih4 * yds;
             }
             const double sc = 1.0 / std::sqrt((double)g.rep_stab[ri] * g.rep_stab[rj]);
             for (int p = 0; p < 8; ++p) {
                 if (g.base_of[p] != p) continue;
                 const int qi = g.rep_adapted[(size_t)ri * 8 + p], qj = g.rep_adapted[(size_t)rj * 8 + p];
                 if (qi < 0 || qj < 0) continue;
-                cd xs(0.0, 0.0), ys(0.0, 0.0);
+                cd xs(0.0, 0.0), ys(0.0, 0.0), xds(0.0, 0.0), yds(0.0, 0.0);
                 for (int gg = 0; gg < 8; ++gg) {
                     const double chi = (__builtin_popcount(p & gg) & 1) ? -1.0 : 1.0;
                     xs += chi * xv[gg];
                     ys += chi * yv[gg];
+                    xds += chi * xdv[gg];
+                    yds += chi * ydv[gg];
                 }
                 const size_t a = qi - g.off[p], b = qj - g.off[p];
                 X[p][b * g.m[p] + a] = sc * xs;    // column-major
                 Y[p][b * g.m[p] + a] = sc * ys;
+                if (dK) {
+                    Xd[p][b * g.m[p] + a] = sc * xds;
+                    Yd[p][b * g.m[p] + a] = sc * yds;
+                }
             }
         }
     }
@@ -374,35 +402,35 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
     out.order = order;
     out.s = s;
     out.mat.resize(g.cls.size());
+    if (dK) dK->assign(g.cls.size(), std::vector<cd>());
     for (size_t ki = 0; ki < g.cls.size(); ++ki) {
         const auto& k = g.cls[ki];
         const int m = k.m, mb = g.m[k.base];
         // restrict X_b, Y_b to the class: Xk = W0^T X_b W0 (component 0 columns)
-        std::vector<cd> Xk((size_t)m * m, cd(0.0, 0.0)), Yk((size_t)m * m, cd(0.0, 0.0));
-        const std::vector<cd>& Xb = X[k.base];
-        const std::vector<cd>& Yb = Y[k.base];
+        auto restrict_ = [&](const std::vector<cd>& Xb, std::vector<cd>& Xk) {
+            Xk.assign((size_t)m * m, cd(0.0, 0.0));
 #pragma omp parallel for schedule(dynamic, 8)
-        for (int c2 = 0; c2 < m; ++c2) {
-            const int* lj = &k.col_l[(size_t)c2 * 6];
-            const double* wj = &k.col_w[(size_t)c2 * 6];
-            for (int c = 0; c < m; ++c) {
-                const int* li = &k.col_l[(size_t)c * 6];
-                const double* wi = &k.col_w[(size_t)c * 6];
-                cd xs(0.0, 0.0), ys(0.0, 0.0);
-                for (int j = 0; j < 6; ++j) {
-                    if (lj[j] < 0) continue;
-                    for (int i = 0; i < 6; ++i) {
-                        if (li[i] < 0) continue;
-                        const double w = wi[i] * wj[j];
-                        const size_t e = (size_t)lj[j] * mb + li[i];     // column-major (row li, col lj)
-                        xs += w * Xb[e];
-                        ys += w * Yb[e];
+            for (int c2 = 0; c2 < m; ++c2) {
+                const int* lj = &k.col_l[(size_t)c2 * 6];
+                const double* wj = &k.col_w[(size_t)c2 * 6];
+                for (int c = 0; c < m; ++c) {
+                    const int* li = &k.col_l[(size_t)c * 6];
+                    const double* wi = &k.col_w[(size_t)c * 6];
+                    cd xs(0.0, 0.0);
+                    for (int j = 0; j < 6; ++j) {
+                        if (lj[j] < 0) continue;
+                        for (int i = 0; i < 6; ++i) {
+                            if (li[i] < 0) continue;
+                            xs += (wi[i] * wj[j]) * Xb[(size_t)lj[j] * mb + li[i]];   // column-major (li, lj)
+                        }
                     }
+                    Xk[(size_t)c2 * m + c] = xs;
                 }
-                Xk[(size_t)c2 * m + c] = xs;
-                Yk[(size_t)c2 * m + c] = ys;
             }
-        }
+        };
+        std::vector<cd> Xk, Yk;
+        restrict_(X[k.base], Xk);
+        restrict_(Y[k.base], Yk);
         std::vector<int> piv(m);
         std::vector<cd>& F = order == 0 ? Xk : Yk;     // factorised
         std::vector<cd>& Z = order == 0 ? Yk : Xk;     // right-hand sides -> result
@@ -420,6 +448,20 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
         M.assign((size_t)m * m, cd(0.0, 0.0));
         for (int a = 0; a < m; ++a)
             for (int c = 0; c < m; ++c) M[(size_t)a * m + c] = -0.5 * (Z[(size_t)c * m + a] + Z[(size_t)a * m + c]);
+        if (dK) {
+            // X K = -Y  =>  X' K + X K' = -Y'  =>  K' = -X^{-1} (Y' + X' K); F holds X's LU.
+            // M is symmetric, so its row-major buffer is also its column-major one.
+            std::vector<cd> Xdk, T;
+            restrict_(Xd[k.base], Xdk);
+            restrict_(Yd[k.base], T);                                 // T = Y'
+            for (cd& v : Xdk) v = -v;
+            zgemm_sub(m, m, m, Xdk.data(), m, M.data(), m, T.data(), m);   // T = Y' + X' K
+            zgetrs(m, m, F.data(), m, piv.data(), T.data(), m);      // X^{-1} (Y' + X' K)
+            std::vector<cd>& D = (*dK)[ki];
+            D.assign((size_t)m * m, cd(0.0, 0.0));
+            for (int a = 0; a < m; ++a)
+                for (int c = 0; c < m; ++c) D[(size_t)a * m + c] = -0.5 * (T[(size_t)c * m + a] + T[(size_t)a * m + c]);
+        }
     }
     return ABC_OK;
 }
@@ -505,12 +547,102 @@ int compute_blocks2(const Geometry& g, const double s[4], Blocks& out, std::stri
     return ABC_OK;
 }
 
+// Order-1 coefficients of R_11(s) = (sI - B)^{-1} A fitted by two finite points or by
+// value and derivative at one point (Sec. 3.2's remark on a finite s2; eq:39).  All
+// K blocks are complex symmetric (row-major = column-major), so a column-major solve
+// X = K^{-1} Y read row-major is X^T.
+//   two points:  (s_j I - B) K_j = A (j = 1, 2)  =>  B (K1 - K2) = s1 K1 - s2 K2,
+//                B^T = (K1 - K2)^{-1} (s1 K1 - s2 K2),  A = s1 K1 - B K1
+//   Hermite:     X K1 = -K1' with X = (s1 I - B)^{-1}  =>  B = s1 I + K1 K1'^{-1},
+//                A = X^{-1} K1 = -K1 K1'^{-1} K1;  with W = K1'^{-1} K1:
+//                K1 K1'^{-1} = W^T, A = -K1 W
+int compute_blocks_fit1(const Geometry& g, int fit, double s1, double s1b, Blocks& out, std::string& err) {
+    if (fit != ABC_FIT1_TWO_POINT && fit != ABC_FIT1_HERMITE) { err = "unknown order-1 fit"; return ABC_ERR_ARG; }
+    Blocks K1, K2;
+    std::vector<std::vector<cd>> dK;
+    int st = compute_blocks(g, 0, s1, K1, err, fit == ABC_FIT1_HERMITE ? &dK : nullptr);
+    if (st) return st;
+    if (fit == ABC_FIT1_TWO_POINT && (st = compute_blocks(g, 0, s1b, K2, err))) return st;
+    out = Blocks();
+    out.order = 1;
+    out.fit = fit;
+    out.s = s1;
+    out.s1b = fit == ABC_FIT1_TWO_POINT ? s1b : 0.0;
+    const size_t nc = g.cls.size();
+    out.mat2[0].resize(nc);
+    out.mat2[1].resize(nc);
+    for (size_t k = 0; k < nc; ++k) {
+        const int m = g.cls[k].m;
+        const size_t mm = (size_t)m * m;
+        const std::vector<cd>& Ka = K1.mat[k];
+        std::vector<cd> F(mm), Z(mm);
+        if (fit == ABC_FIT1_TWO_POINT) {
+            const std::vector<cd>& Kb = K2.mat[k];
+            for (size_t e = 0; e < mm; ++e) {
+                F[e] = Ka[e] - Kb[e];
+                Z[e] = s1 * Ka[e] - s1b * Kb[e];
+            }
+        } else {
+            F = dK[k];
+            Z = Ka;
+        }
+        std::vector<int> piv(m);
+        const int info = zgetrf(m, F.data(), m, piv.data());
+        if (info) {
+            char buf[160];
+            std::snprintf(buf, sizeof(buf), "order-1 %s fit of class %zu singular at pivot %d",
+                          fit == ABC_FIT1_TWO_POINT ? "two-point" : "Hermite", k, info);
+            err = buf;
+            return ABC_ERR_SINGULAR;
+        }
+        zgetrs(m, m, F.data(), m, piv.data(), Z.data(), m);      // column-major solution
+        std::vector<cd>& B = out.mat2[0][k];
+        std::vector<cd>& A = out.mat2[1][k];
+        B.assign(mm, cd(0.0, 0.0));
+        A.assign(mm, cd(0.0, 0.0));
+        // P = -Ka Z (column-major): two-point Z = B^T, so B Ka = (Ka Z)^T; Hermite Z = W,
+        // A = -Ka W = P
+        std::vector<cd> P(mm, cd(0.0, 0.0));
+        zgemm_sub(m, m, m, Ka.data(), m, Z.data(), m, P.data(), m);
+        if (fit == ABC_FIT1_TWO_POINT) {
+            for (size_t e = 0; e < mm; ++e) {
+                B[e] = Z[e];                        // row-major B = column-major Z buffer
+                A[e] = s1 * Ka[e] + P[e];           // s1 K1 - B K1; (B K1) row-major = -P buffer
+            }
+        } else {
+            for (int a = 0; a < m; ++a)
+                for (int c = 0; c < m; ++c) {
+                    // B = s1 I + W^T (row-major = the column-major W buffer); A symmetric
+                    B[(size_t)a * m + c] = Z[(size_t)a * m + c] + (a == c ? cd(s1, 0.0) : cd(0.0, 0.0));
+                    A[(size_t)a * m + c] = 0.5 * (P[(size_t)a * m + c] + P[(size_t)c * m + a]);
+                }
+        }
+    }
+    return ABC_OK;
+}
+
+int compute_param_blocks(const Geometry& g, const abc_params& p, Blocks& b, std::string& err) {
+    if (p.order == 2) return compute_blocks2(g, p.s2, b, err);
+    if (p.order == 1 && p.fit1 != ABC_FIT1_LIMIT) return compute_blocks_fit1(g, p.fit1, p.s1, p.s1b, b, err);
+    return compute_blocks(g, p.order, p.order == 0 ? p.s0 : p.s1, b, err);
+}
+
 // Dense natural-order matrices from the parity blocks: with U[g r, (r,p)] =
 // chi_p(g) sqrt(|H_r|/8) (orthogonal), S_nat = U S_adapted U^T.
 int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::string& err) {
     const int n = g.n_gamma;
     const double h4 = std::pow(g.h, 4);
     std::fill(out, out + (size_t)n * n, cd(0.0, 0.0));
+    if (b.order == 1 && b.fit != ABC_FIT1_LIMIT && (which == ABC_MAT_A || which == ABC_MAT_B)) {
+        std::vector<cd> blk[8];
+        for (int p = 0; p < 8; ++p)
+            if (g.base_of[p] == p && g.m[p]) expand_base_block(g, p, b.mat2[which == ABC_MAT_B ? 0 : 1], blk[p]);
+        return natural_from_blocks(g, blk, out);
+    }
+    if (b.order == 1 && b.fit != ABC_FIT1_LIMIT && which == ABC_MAT_K) {
+        err = "the two-point and Hermite fits keep B and A only (take K from an order-0 context)";
+        return ABC_ERR_ARG;
+    }
     if (which == ABC_MAT_A || which == ABC_MAT_Q) {
         if (b.order != 1) { err = "A and Q exist for order 1 only"; return ABC_ERR_ARG; }
         for (int i = 0; i < n; ++i)

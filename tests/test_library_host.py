@@ -10,7 +10,7 @@ import re
 import numpy as np
 import pytest
 
-from oracle.coefficients import order0, order1, order2
+from oracle.coefficients import order0, order1, order1_hermite, order1_two_point, order2
 from oracle.lattice import Box
 from paper_1908_02456_gb300 import abc
 from paper_1908_02456_gb300 import build as nb
@@ -77,3 +77,36 @@ def test_order2_host_setup_matches_oracle(lib, dims, h, pts):
         X = abc.abc_host_matrices(dims, h, 2, pts, which)
         ref = co[key]
         assert np.abs(X - ref).max() < 1e-9 * np.abs(ref).max(), key
+
+
+@pytest.mark.parametrize("dims,h,fit,s1,s1b", [((5, 4, 6), 0.5, "two_point", 1.0, 2.0),
+                                               ((7, 5, 9), 0.5, "two_point", 0.6, 3.0),
+                                               ((6, 6, 6), 0.45, "hermite", 1.0, 0.0),
+                                               ((7, 5, 9), 0.5, "hermite", 2.0, 0.0)])
+def test_fit1_host_setup_matches_oracle(lib, dims, h, fit, s1, s1b):
+    """The two-point and Hermite first-order fits: the library forms B and A per
+    irreducible class block (K' from the differentiated Green's-function integral), the
+    oracle from the dense matrices (K' from the differentiated FFT Green's function)."""
+    box = Box(dims, h)
+    co = order1_two_point(box, s1, s1b) if fit == "two_point" else order1_hermite(box, s1)
+    for which, key in [(abc.MAT_B, "B"), (abc.MAT_A, "A")]:
+        X = abc.abc_host_matrices(dims, h, 1, s1, which, fit1=fit, s1b=s1b)
+        ref = co[key]
+        assert np.abs(X - ref).max() < 1e-9 * np.abs(ref).max(), key
+    Q = abc.abc_host_matrices(dims, h, 1, s1, abc.MAT_Q, fit1=fit, s1b=s1b)
+    assert np.abs(Q - co["Q"]).max() < 1e-12 * np.abs(co["Q"]).max()
+
+
+def test_fit1_rejects_bad_parameters(lib):
+    dims, h = (5, 5, 5), 0.5
+    with pytest.raises(abc.AbcError) as e:                      # the fits belong to order 1
+        abc.abc_host_matrices(dims, h, 0, 1.0, abc.MAT_M, fit1="hermite")
+    assert e.value.status == 1
+    with pytest.raises(abc.AbcError):                           # two distinct points
+        abc.abc_host_matrices(dims, h, 1, 1.0, abc.MAT_B, fit1="two_point", s1b=1.0)
+    with pytest.raises(abc.AbcError):
+        abc.abc_host_matrices(dims, h, 1, 1.0, abc.MAT_B, fit1="two_point", s1b=-2.0)
+    with pytest.raises(abc.AbcError):                           # unknown fit
+        abc.abc_host_matrices(dims, h, 1, 1.0, abc.MAT_B, fit1=7)
+    with pytest.raises(abc.AbcError):                           # K is not kept by the fits
+        abc.abc_host_matrices(dims, h, 1, 1.0, abc.MAT_K, fit1="hermite")
