@@ -200,9 +200,10 @@ def other_workload(args, w):
     nbuild.build()
     dev = torch.device("cuda", torch.cuda.current_device())
     psi0, V = inputs_for(w)
-    ctx = abc.Context(w.shape, w.h, w.order, w.s, precision=w.precision, max_orbitals=w.n_orb)
+    ctx = abc.Context(w.shape, w.h, w.order, w.interp, precision=w.precision, max_orbitals=w.n_orb,
+                      fit1=w.fit1, s1b=w.s1b)
     psi = torch.from_numpy(psi0).to(dev, ctx.complex_dtype)
-    aux = ctx.new_aux(w.n_orb) if w.order == 1 else None
+    aux = ctx.new_aux(w.n_orb) if w.order == 1 else ctx.init_aux(psi) if w.order == 2 else None
     Vt = torch.from_numpy(V).to(dev, ctx.real_dtype)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -246,7 +247,8 @@ def other_workload(args, w):
             "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "c64",
             "data": "synthetic", "config": {"workload": w.name, "grid": list(w.shape), "h": w.h, "n_orb": w.n_orb,
-                                           "order": w.order, "s": w.s, "dt": w.dt, "meanfield": w.meanfield,
+                                           "order": w.order, "s": w.interp, "fit1": w.fit1, "s1b": w.s1b,
+                                           "dt": w.dt, "meanfield": w.meanfield,
                                            "precision": w.precision, "what": what},
             "contraction": {"avg_launch_us": round(ms_c / n_c * 1e3, 2), "bytes_per_launch": bytes_c,
                             "achieved_gbs": round(bytes_c / (ms_c / n_c * 1e-3) / 1e9, 1)},

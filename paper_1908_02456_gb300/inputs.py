@@ -41,6 +41,14 @@ class Workload:
     potential: str              # "zero" | "harmonic_bumps" | "smooth_random" | "none"
     meanfield: Optional[Tuple[float, float, float]] = None   # (a, b, alpha)
     precision: str = "c64"      # "fp64" | "c64" | "tf32x3"
+    points: Tuple[float, ...] = ()   # order 2: the four interpolation points
+    fit1: str = "limit"         # order 1: "limit" | "two_point" | "hermite"
+    s1b: float = 0.0            # order 1, two-point fit: the second point
+
+    @property
+    def interp(self):
+        """The interpolation argument of the context: s, or the four order-2 points."""
+        return self.points if self.order == 2 else self.s
 
     @property
     def seed(self) -> int:
@@ -62,6 +70,13 @@ WORKLOADS = {
                 "smooth_random", precision="c64"),
     5: Workload(5, "meanfield-96cube-128orb-order1", 96, 0.35, 128, 1, 1.0, 0.004, 500,
                 "none", meanfield=(-1.0, 0.8, 1.0 / 6.0), precision="tf32x3"),
+    # the next-row variants on the benchmark grid and potential
+    6: Workload(6, "harmonic-64cube-order2-single", 64, 0.4, 1, 2, 1.0, 0.005, 500,
+                "harmonic_bumps", precision="c64", points=(1.0, 2.0, 3.0, 10.0)),
+    7: Workload(7, "harmonic-64cube-order1-twopoint-single", 64, 0.4, 1, 1, 1.0, 0.005, 500,
+                "harmonic_bumps", precision="c64", fit1="two_point", s1b=2.0),
+    8: Workload(8, "harmonic-64cube-order1-hermite-single", 64, 0.4, 1, 1, 1.0, 0.005, 500,
+                "harmonic_bumps", precision="c64", fit1="hermite"),
 }
 
 
