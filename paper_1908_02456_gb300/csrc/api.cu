@@ -115,6 +115,19 @@ int upload_matrices(abc_ctx* c) {
         c->bi.segw[i] = es[i].sw;
         c->bi.mat_off[i] = es[i].mo;
     }
+    if ((int)g.cls.size() > dev::MAX_CLASSES) return fail(ABC_ERR_ARG, "internal: too many classes");
+    c->ci = dev::ClassInfo{};
+    c->ci.n = (int)g.cls.size();
+    c->ci.rowbase[0] = 0;
+    for (size_t k = 0; k < g.cls.size(); ++k) {
+        c->ci.R[k] = g.cls[k].R;
+        c->ci.m[k] = g.cls[k].m;
+        for (int e = 0; e < 3; ++e) c->ci.moff[k][e] = e < g.cls[k].R ? g.cls[k].moff[e] : 0;
+        c->ci.ld[k] = lds[k];
+        c->ci.segw[k] = segw[k];
+        c->ci.mat_off[k] = moff[k];
+        c->ci.rowbase[k + 1] = c->ci.rowbase[k] + (g.cls[k].m + dev::GEMV_RB - 1) / dev::GEMV_RB;
+    }
     const size_t eb = cplx_bytes(c);
     int st = c->mat.alloc((size_t)total * eb);
     if (st) return st;
@@ -523,8 +536,8 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
                    (long long)c->l2_keep_tiles, c->err_flag.as<int>());
         res.gathered = true;
     } else if (n_orb == 1) {
-        dev::gemv_blocks<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(c->bi, n, c->mat.as<V>(), xs, (V*)t,
-                                                                          conj);
+        dev::gemv_classes<T><<<c->ci.rowbase[c->ci.n], 32 * dev::GEMV_WARPS, 0, s>>>(c->ci, c->mat.as<V>(), xs,
+                                                                                  (V*)t, conj);
     } else if (sizeof(T) == 4 && c->tc) {
         const abc_ctx::TcPlan& pl = c->tc_b[n_orb];
         dev::pack_x_tc<<<dim3((unsigned)pl.cols_cnt, (unsigned)pl.max_nkb), 128, 0, s>>>(
@@ -1101,6 +1114,9 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
         double entries = 0;
         if (ctx->sym && n_orb == 1) {
             entries = (double)ctx->sym_tiles_n * abc::dev::SYM_T * abc::dev::SYM_T;   // stored tiles, read once
+        } else if (n_orb == 1) {
+            for (int k = 0; k < ctx->ci.n; ++k)                                        // class blocks, read once
+                entries += (double)ctx->bi.nseg * ctx->ci.m[k] * ctx->ci.m[k];
         } else {
             for (int p = 0; p < ctx->bi.n; ++p) entries += (double)ctx->bi.nseg * ctx->bi.m[p] * ctx->bi.m[p];
         }

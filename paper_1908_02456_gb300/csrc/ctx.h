@@ -50,6 +50,7 @@ struct abc_ctx {
     size_t real_bytes = 8;  // bytes of one real value of the state
     long long nvox = 0;
     abc::dev::BlockInfo bi;
+    abc::dev::ClassInfo ci;           // the same blocks by class (one-orbital contraction)
     // device tables
     abc::DevBuf gamma_c;
     abc::DevBuf cell_out, cell_type, cell_coef_f, cell_coef_bt, cell_c, cell_gi, cell_node, cell_wr;

@@ -38,6 +38,21 @@ struct BlockInfo {
     long long mat_off[MAX_ENTRIES];   // first element of the matrix in the buffer
 };
 
+// The same blocks by irreducible class: class c owns the thread blocks rowbase[c] ..
+// rowbase[c+1]-1 (GEMV_RB block rows each) and applies its block to its R right-hand
+// sides, which start at adapted offsets moff[c][k].
+constexpr int MAX_CLASSES = 16;
+struct ClassInfo {
+    int n;                            // classes
+    int R[MAX_CLASSES];
+    int m[MAX_CLASSES];
+    int moff[MAX_CLASSES][3];
+    int ld[MAX_CLASSES];
+    int segw[MAX_CLASSES];
+    long long mat_off[MAX_CLASSES];
+    int rowbase[MAX_CLASSES + 1];     // first block of each class (ceil(m / GEMV_RB) blocks per class)
+};
+
 // Input vectors of the contraction: segment q of a row multiplies x.p[q] (adapted,
 // orbital-major); only p[0] is used when nseg = 1.
 template <typename V>
@@ -412,6 +427,123 @@ __device__ __forceinline__ int find_block(const BlockInfo& bi, int q) {
     for (int k = 1; k < bi.n; ++k)
         if (q >= bi.off[k]) p = k;
     return p;
+}
+
+// One orbital, one block of GEMV_WARPS warps per GEMV_RB consecutive block rows of a
+// class: each row is streamed once and applied to all R right-hand sides of the class
+// (the matrix bytes are read once per launch, where gemv_blocks reads a class block
+// once per right-hand side); each loaded slice of x serves GEMV_RB rows; the warps
+// split the columns (more loads in flight) and their partial sums are added through
+// shared memory in a fixed order.
+constexpr int GEMV_RB = 4, GEMV_WARPS = 4;
+template <typename T, int R>
+__device__ __forceinline__ void gemv_class_rows(const ClassInfo& ci, int c, int a0, const typename C2<T>::t* mat,
+                                                const XSeg<typename C2<T>::t>& xs, typename C2<T>::t* y, T cs,
+                                                typename C2<T>::t (*red)[GEMV_RB][3]) {
+    typedef typename C2<T>::t V;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int m = ci.m[c];
+    const int nr = m - a0 < GEMV_RB ? m - a0 : GEMV_RB;    // rows of this block (the last may be short)
+    T sr[GEMV_RB][R], si[GEMV_RB][R];
+#pragma unroll
+    for (int r = 0; r < GEMV_RB; ++r)
+#pragma unroll
+        for (int k = 0; k < R; ++k) sr[r][k] = si[r][k] = 0;
+    for (int q = 0; q < 4; ++q) {
+        if (!xs.p[q]) break;
+        const V* row0 = mat + ci.mat_off[c] + (long long)a0 * ci.ld[c] + (long long)q * ci.segw[c];
+        if constexpr (sizeof(T) == 4) {
+            const int m2 = m >> 1;
+#pragma unroll 2
+            for (int cc = threadIdx.x; cc < m2; cc += 32 * GEMV_WARPS) {
+                float4 sv[GEMV_RB];
+#pragma unroll
+                for (int r = 0; r < GEMV_RB; ++r)
+                    sv[r] = r < nr ? __ldcs(reinterpret_cast<const float4*>(row0 + (long long)r * ci.ld[c]) + cc)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const V* xv = xs.p[q] + ci.moff[c][k];
+                    const V x0 = xv[2 * cc], x1 = xv[2 * cc + 1];
+#pragma unroll
+                    for (int r = 0; r < GEMV_RB; ++r) {
+                        const T sy0 = cs * sv[r].y, sy1 = cs * sv[r].w;
+                        sr[r][k] += sv[r].x * x0.x - sy0 * x0.y + sv[r].z * x1.x - sy1 * x1.y;
+                        si[r][k] += sv[r].x * x0.y + sy0 * x0.x + sv[r].z * x1.y + sy1 * x1.x;
+                    }
+                }
+            }
+            if ((m & 1) && threadIdx.x == 0) {
+#pragma unroll
+                for (int r = 0; r < GEMV_RB; ++r) {
+                    if (r >= nr) break;
+                    const V sv = row0[(long long)r * ci.ld[c] + m - 1];
+                    const T sy = cs * sv.y;
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        const V xx = xs.p[q][ci.moff[c][k] + m - 1];
+                        sr[r][k] += sv.x * xx.x - sy * xx.y;
+                        si[r][k] += sv.x * xx.y + sy * xx.x;
+                    }
+                }
+            }
+        } else {
+#pragma unroll 2
+            for (int cc = threadIdx.x; cc < m; cc += 32 * GEMV_WARPS) {
+                V sv[GEMV_RB];
+#pragma unroll
+                for (int r = 0; r < GEMV_RB; ++r) sv[r] = r < nr ? __ldcs(row0 + (long long)r * ci.ld[c] + cc) : mk<T>(0, 0);
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const V xx = xs.p[q][ci.moff[c][k] + cc];
+#pragma unroll
+                    for (int r = 0; r < GEMV_RB; ++r) {
+                        const T sy = cs * sv[r].y;
+                        sr[r][k] += sv[r].x * xx.x - sy * xx.y;
+                        si[r][k] += sv[r].x * xx.y + sy * xx.x;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < GEMV_RB; ++r)
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const T re = warp_sum(sr[r][k]), im = warp_sum(si[r][k]);
+            if (lane == 0) red[w][r][k] = mk<T>(re, im);
+        }
+    __syncthreads();
+    if (threadIdx.x < GEMV_RB * R) {
+        const int r = threadIdx.x / R, k = threadIdx.x % R;
+        if (r < nr) {
+            V acc = red[0][r][k];
+#pragma unroll
+            for (int u = 1; u < GEMV_WARPS; ++u) {
+                acc.x += red[u][r][k].x;
+                acc.y += red[u][r][k].y;
+            }
+            y[ci.moff[c][k] + a0 + r] = acc;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * GEMV_WARPS) gemv_classes(ClassInfo ci, const typename C2<T>::t* __restrict__ mat,
+                                                                XSeg<typename C2<T>::t> xs,
+                                                                typename C2<T>::t* __restrict__ y, int conj) {
+    __shared__ typename C2<T>::t red[GEMV_WARPS][GEMV_RB][3];
+    const int blk = blockIdx.x;
+    if (blk >= ci.rowbase[ci.n]) return;
+    int c = 0;
+    while (c + 1 < ci.n && blk >= ci.rowbase[c + 1]) ++c;
+    const int a0 = (blk - ci.rowbase[c]) * GEMV_RB;
+    const T cs = conj ? (T)-1 : (T)1;     // conj: y = conj(S) x
+    switch (ci.R[c]) {
+        case 1: gemv_class_rows<T, 1>(ci, c, a0, mat, xs, y, cs, red); break;
+        case 2: gemv_class_rows<T, 2>(ci, c, a0, mat, xs, y, cs, red); break;
+        default: gemv_class_rows<T, 3>(ci, c, a0, mat, xs, y, cs, red); break;
+    }
 }
 
 template <typename T>
