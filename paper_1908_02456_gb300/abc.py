@@ -100,9 +100,9 @@ def _check(st: int):
         raise AbcError(st, f"{lib.abc_status_string(st).decode()}: {lib.abc_last_error().decode()}")
 
 
-def _grid(shape: Sequence[int], h: float) -> abc_grid:
+def _grid(shape: Sequence[int], h: float, radius: int = 1) -> abc_grid:
     nx, ny, nz = (int(v) for v in shape)
-    return abc_grid(nx, ny, nz, 1, float(h))
+    return abc_grid(nx, ny, nz, int(radius), float(h))
 
 
 def _params(order: int, s, precision, max_orbitals: int, fit1="limit", s1b: float = 0.0) -> abc_params:
@@ -180,12 +180,13 @@ def abc_get_matrices(ctx, which: int, n_gamma: int) -> np.ndarray:
     return out
 
 
-def abc_host_matrices(shape, h, order, s, which, fit1="limit", s1b: float = 0.0) -> np.ndarray:
+def abc_host_matrices(shape, h, order, s, which, fit1="limit", s1b: float = 0.0, radius: int = 1) -> np.ndarray:
     """FP64 setup on the host only (no CUDA): dense ABC_MAT_* in natural Gamma order."""
     nx, ny, nz = shape
-    n = nx * ny * nz - (nx - 2) * (ny - 2) * (nz - 2)
+    R = int(radius)
+    n = nx * ny * nz - max(nx - 2 * R, 0) * max(ny - 2 * R, 0) * max(nz - 2 * R, 0)
     out = np.zeros((n, n), np.complex128)
-    g, p = _grid(shape, h), _params(order, s, FP64, 1, fit1, s1b)
+    g, p = _grid(shape, h, radius), _params(order, s, FP64, 1, fit1, s1b)
     _check(load().abc_host_matrices(ctypes.byref(g), ctypes.byref(p), which, out.ctypes.data_as(_P), out.nbytes))
     return out
 
@@ -240,7 +241,7 @@ def abc_destroy(ctx):
 class Context:
     """Owns one abc_ctx.  psi: [b, nz, ny, nx] complex CUDA tensor; aux: [n_gamma, b]."""
 
-    def __init__(self, shape, h, order, s, precision="c64", max_orbitals=1, fit1="limit", s1b=0.0):
+    def __init__(self, shape, h, order, s, precision="c64", max_orbitals=1, fit1="limit", s1b=0.0, radius=1):
         self.shape = tuple(int(v) for v in shape)
         self.h, self.order = float(h), int(order)
         self.s = tuple(float(v) for v in s) if self.order == 2 else float(s)
@@ -248,7 +249,8 @@ class Context:
         self.max_orbitals = int(max_orbitals)
         self.fit1 = FITS1[fit1] if isinstance(fit1, str) else int(fit1)
         self.s1b = float(s1b)
-        self.ctx = abc_setup(_grid(self.shape, h),
+        self.radius = int(radius)
+        self.ctx = abc_setup(_grid(self.shape, h, self.radius),
                              _params(order, s, self.precision, max_orbitals, self.fit1, self.s1b))
         self.n_gamma = abc_boundary_size(self.ctx)
 

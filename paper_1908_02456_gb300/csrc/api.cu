@@ -88,7 +88,7 @@ int upload_tables(abc_ctx* c) {
 int upload_matrices(abc_ctx* c) {
     const Geometry& g = c->geo;
     const bool o2 = c->params.order == 2;
-    const bool f1 = c->params.order == 1 && c->params.fit1 != ABC_FIT1_LIMIT;
+    const bool f1 = c->params.order == 1 && c->blocks.rows1;
     const int nseg = o2 ? 4 : f1 ? 2 : 1;
     long long total = 0;
     std::vector<long long> moff(g.cls.size());
@@ -596,9 +596,15 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
     const unsigned nbk = cell_blocks(c, n_orb);
     auto stencil = [&](cudaStream_t ss) {
         prof_begin(c, ABC_KERNEL_STENCIL, ss);
-        dev::stencil_stage<T><<<stencil_grid(c, n_orb), 256, 0, ss>>>(
-            g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)w_phi, (const Vc*)y_phi, V,
-            order >= 1 ? (const Vc*)w_f : c->cnat.as<Vc>(), (Vc*)o_phi, cdt);
+        const Vc* bt = order >= 1 ? (const Vc*)w_f : c->cnat.as<Vc>();
+        if (g.R == 3)
+            dev::stencil_stage<T, 3><<<stencil_grid(c, n_orb), 256, 0, ss>>>(
+                g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)w_phi, (const Vc*)y_phi, V, bt,
+                (Vc*)o_phi, cdt);
+        else
+            dev::stencil_stage<T, 1><<<stencil_grid(c, n_orb), 256, 0, ss>>>(
+                g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)w_phi, (const Vc*)y_phi, V, bt,
+                (Vc*)o_phi, cdt);
         prof_end(c, ABC_KERNEL_STENCIL, ss);
     };
     auto fork_stencil = [&]() {
@@ -624,8 +630,8 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
     dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
                                                order == 1 ? (const Vc*)w_f : nullptr, c->hat_phi.as<Vc>(),
                                                c->hat_f.as<Vc>(), nullptr, (T)0, dev::Ord2Fwd<T>{});
-    if (order == 1 && c->params.fit1 != ABC_FIT1_LIMIT) {
-        // fitted B and A: t = B f_hat + A phi_hat on the rows [B | A], f' = t
+    if (order == 1 && c->blocks.rows1) {
+        // general B and A: t = B f_hat + A phi_hat on the rows [B | A], f' = t
         const void* x2[4] = {c->hat_f.p, c->hat_phi.p, nullptr, nullptr};
         const TRes tr = contraction<T>(c, nullptr, c->tvec.p, n_orb, 0, s, x2);
         fork_stencil();
@@ -681,11 +687,15 @@ void diag_impl(abc_ctx* c, const void* psi, const void* aux, const void* V, int 
                                                                      (T)mf->a, (T)mf->b, (T)mf->alpha, c->Veff.as<T>());
         Vuse = c->Veff.as<T>();
     }
-    c->launches += 1 + (mf ? 1 : 0) + (c->params.order == 1 && aux ? 1 : 0);
+    // W's auxiliary term f*Qf uses the diagonal Q of radius 1 (Thm 3.2); with R = 3, W = |phi|^2
+    const bool waux = c->params.order == 1 && aux && g.R == 1;
+    c->launches += 1 + (mf ? 1 : 0) + (waux ? 1 : 0);
     cudaMemsetAsync(out_dev, 0, sizeof(double) * 3 * n_orb, s);
     dim3 gp((unsigned)std::min<long long>(nblk(c->nvox, 256), 1024), n_orb);
-    dev::diag_phi<T><<<gp, 256, 0, s>>>(g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)psi, Vuse, out_dev);
-    if (c->params.order == 1 && aux) {
+    const T ih2 = (T)(1.0 / (g.h * g.h));
+    if (g.R == 3) dev::diag_phi<T, 3><<<gp, 256, 0, s>>>(g.nx, g.ny, g.nz, n_orb, ih2, (const Vc*)psi, Vuse, out_dev);
+    else dev::diag_phi<T, 1><<<gp, 256, 0, s>>>(g.nx, g.ny, g.nz, n_orb, ih2, (const Vc*)psi, Vuse, out_dev);
+    if (waux) {
         dim3 ga((unsigned)std::min<long long>(nblk(g.n_gamma, 256), 256), n_orb);
         dev::diag_aux<T><<<ga, 256, 0, s>>>(g.n_gamma, n_orb, c->gamma_c.as<int>(), 4.0 * std::pow(g.h, 4),
                                             (const Vc*)aux, out_dev);
@@ -735,7 +745,7 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     c->prec = params->precision;
     c->real_bytes = c->prec == ABC_FP64 ? 8 : 4;
     std::string err;
-    st = build_geometry(grid->nx, grid->ny, grid->nz, grid->h, c->geo, err);
+    st = build_geometry(grid->nx, grid->ny, grid->nz, grid->h, c->geo, err, grid->radius);
     if (st) return fail(st, err);
     c->nvox = c->geo.n_nodes;
     st = compute_param_blocks(c->geo, *params, c->blocks, err);
@@ -750,7 +760,7 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     // per class (order 0, order 1 with the limit fit); the order-2 rows
     // [B1 | B0 - i A1 | -i A1 | A0] and the fitted order-1 rows [B | A] use the
     // full-block kernels
-    const bool one_seg = params->order < 2 && params->fit1 == ABC_FIT1_LIMIT;
+    const bool one_seg = params->order < 2 && !c->blocks.rows1;
     if (one_seg && (c->prec == ABC_C64_FP32 || c->prec == ABC_C64_3XTF32) && (st = build_sym(c.get()))) return st;
     if (one_seg && c->prec == ABC_C64_3XTF32 && (st = build_tc(c.get()))) return st;
     if (!c->err_flag.p) {
@@ -1056,6 +1066,7 @@ extern "C" int abc_adjoint_run(abc_ctx* ctx, const void* psi0, const void* V, in
     if (ctx->params.order == 2) return fail(ABC_ERR_UNSUPPORTED, "the adjoint covers orders 0 and 1");
     if (ctx->params.fit1 != ABC_FIT1_LIMIT)
         return fail(ABC_ERR_UNSUPPORTED, "the adjoint covers the limit fit of order 1 (Thm 3.2) only");
+    if (ctx->geo.R != 1) return fail(ABC_ERR_UNSUPPORTED, "the adjoint covers the radius-1 stencil only");
     cudaStream_t s = (cudaStream_t)stream;
     if (ctx->prec == ABC_FP64) return adjoint_impl<double>(ctx, psi0, V, n_orb, dt, nsteps, ckpt_every, J_out, dJdV, s);
     return adjoint_impl<float>(ctx, psi0, V, n_orb, dt, nsteps, ckpt_every, J_out, dJdV, s);

@@ -34,7 +34,10 @@ extern "C" const char* abc_last_error(void) { return g_last_error.c_str(); }
 namespace abc {
 int check_params(const abc_grid* grid, const abc_params* params) {
     if (!grid || !params) return fail(ABC_ERR_ARG, "null grid or params");
-    if (grid->radius != 1) return fail(ABC_ERR_UNSUPPORTED, "only the 3-point stencil (radius 1) is built");
+    if (grid->radius != 1 && grid->radius != 3)
+        return fail(ABC_ERR_UNSUPPORTED, "stencil radius 1 (3-point) or 3 (7-point, Sec. 4.2) only");
+    if (grid->radius == 3 && params->order == 2)
+        return fail(ABC_ERR_UNSUPPORTED, "the second-order ABC is built for radius 1 only");
     if (params->order < 0 || params->order > 2) return fail(ABC_ERR_ARG, "order must be 0, 1 or 2");
     if (params->order == 2) {
         for (int j = 0; j < 4; ++j) {
@@ -69,7 +72,7 @@ extern "C" int abc_host_matrices(const abc_grid* grid, const abc_params* params,
     if (!host_dst) return fail(ABC_ERR_ARG, "null destination");
     Geometry g;
     std::string err;
-    st = build_geometry(grid->nx, grid->ny, grid->nz, grid->h, g, err);
+    st = build_geometry(grid->nx, grid->ny, grid->nz, grid->h, g, err, grid->radius);
     if (st) return fail(st, err);
     if (bytes < (size_t)16 * g.n_gamma * g.n_gamma) return fail(ABC_ERR_ARG, "destination too small");
     Blocks b;

@@ -26,11 +26,13 @@ typedef std::complex<double> cd;
 struct Geometry {
     int nx = 0, ny = 0, nz = 0;
     double h = 0.0;
+    int R = 1;                          // stencil radius per axis (1 or 3)
+    double cst[5] = {0, 0, 0, 0, 0};    // second-difference coefficients c_0 .. c_R
     long long n_nodes = 0;
     int n_gamma = 0;
     std::vector<int> gamma_node;        // Gamma index -> linear node index (ascending)
     std::vector<int> node_gamma;        // linear node index -> Gamma index or -1
-    std::vector<int> gamma_c;           // number of exterior neighbours (1..3)
+    std::vector<int> gamma_c;           // number of exterior nodes coupled to the node (1..3 for R = 1)
     int n_rep = 0;
     std::vector<int> rep_node;          // representative -> linear node index
     std::vector<int> rep_gamma;         // [n_rep][8] Gamma index of g.r
@@ -91,9 +93,9 @@ extern const int kAxisPerms[6][3];
 int build_irreps(Geometry& g, std::string& err);
 
 // Closed-form Gamma index of a boundary node (ascending linear order).
-int gamma_index_closed(int i, int j, int k, int nx, int ny, int nz);
+int gamma_index_closed(int i, int j, int k, int nx, int ny, int nz, int R = 1);
 
-int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& err);
+int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& err, int R = 1);
 
 // FP64 coefficient blocks in the symmetry-adapted basis, one per irreducible class
 // (row-major m x m each):
@@ -103,6 +105,9 @@ int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& e
 struct Blocks {
     int order = 0;
     int fit = 0;          // order 1: ABC_FIT1_*
+    bool rows1 = false;   // order 1 held as general class rows [B | A] in mat2[0], mat2[1]
+                          // (the two-point and Hermite fits; every fit when R > 1, where
+                          // A = -i H_{Gamma,II} H_{II,Gamma} is not diagonal)
     double s = 0.0, s1b = 0.0;
     std::vector<std::vector<cd>> mat;
     // order 2: per class the four coefficient blocks B1, B0, A1, A0; order 1 with a
@@ -121,9 +126,10 @@ int compute_blocks2(const Geometry& g, const double s[4], Blocks& b, std::string
 void expand_base_block(const Geometry& g, int b, const std::vector<std::vector<cd>>& blk, std::vector<cd>& out);
 
 // Class blocks of K(s) (order 0: M = K(s); order 1: S = K(s)^{-1}).  dK (order 0 only):
-// also the class blocks of K'(s) = dK/ds, row-major.
+// also the class blocks of K'(s) = dK/ds, row-major.  HH: also the class blocks of
+// H_{Gamma,II} H_{II,Gamma} (real symmetric).
 int compute_blocks(const Geometry& g, int order, double s, Blocks& b, std::string& err,
-                   std::vector<std::vector<cd>>* dK = nullptr);
+                   std::vector<std::vector<cd>>* dK = nullptr, std::vector<std::vector<cd>>* HH = nullptr);
 
 // Order-1 coefficients fitted by two finite points or by value and derivative
 // (ABC_FIT1_TWO_POINT / ABC_FIT1_HERMITE): per class B (mat2[0]) and A (mat2[1]).
@@ -136,8 +142,10 @@ int compute_param_blocks(const Geometry& g, const abc_params& p, Blocks& b, std:
 int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::string& err);
 
 // Free lattice Green's function table G(|dx|,|dy|,|dz|) = [(H_0 - i s)^{-1}](dx,dy,dz)
-// for 0 <= |d| < dims[a]; layout [(c*dy)+b]*dx + a.  deriv: dG/ds instead (= i G^2).
-void free_green_table(double h, double s, int dx, int dy, int dz, std::vector<cd>& table, bool deriv = false);
+// for 0 <= |d| < dims[a] with the geometry's (2R + 1)-point stencil and spacing;
+// layout [(c*dy)+b]*dx + a.  deriv: dG/ds instead (= i G^2).
+void free_green_table(const Geometry& g, double s, int dx, int dy, int dz, std::vector<cd>& table,
+                      bool deriv = false);
 
 // Dense complex LU with partial pivoting (column-major), and the solve with many
 // right-hand sides.  Return 0, or k+1 if U(k,k) == 0.

@@ -94,15 +94,65 @@ struct SymGather {
     const float2* colpart;       // [tile][3][64]
 };
 
-// Gamma index of a boundary node (ascending linear order, x fastest).
+// Gamma index of a boundary node (Gamma = nodes within R of a face, ascending linear
+// order, x fastest): the first and last R planes z are entirely on Gamma; a middle
+// plane contributes its first and last R rows and the first and last R nodes of every
+// other row.
+template <int R = 1>
 __device__ __forceinline__ int gamma_index(int i, int j, int k, int nx, int ny, int nz) {
-    const int plane = 2 * nx + 2 * (ny - 2);
-    if (k == 0) return j * nx + i;
-    if (k == nz - 1) return nx * ny + (nz - 2) * plane + j * nx + i;
-    const int base = nx * ny + (k - 1) * plane;
-    if (j == 0) return base + i;
-    if (j == ny - 1) return base + nx + 2 * (ny - 2) + i;
-    return base + nx + 2 * (j - 1) + (i == 0 ? 0 : 1);
+    const int full = nx * ny, mid_rows = ny - 2 * R;
+    const int plane = 2 * R * nx + mid_rows * 2 * R;
+    if (k < R) return k * full + j * nx + i;
+    if (k >= nz - R) return R * full + (nz - 2 * R) * plane + (k - (nz - R)) * full + j * nx + i;
+    const int base = R * full + (k - R) * plane;
+    if (j < R) return base + j * nx + i;
+    if (j >= ny - R) return base + R * nx + mid_rows * 2 * R + (j - (ny - R)) * nx + i;
+    return base + R * nx + (j - R) * 2 * R + (i < R ? i : R + (i - (nx - R)));
+}
+
+// Second-difference coefficients c_1 .. c_R of the (2R + 1)-point formula (c_0 enters
+// through the diagonal -1/2 * 3 c_0 / h^2): R = 1: (1); R = 3: (3/2, -3/20, 1/90), the
+// "7-point scheme in each direction" of Sec. 4.2.
+template <int R> __device__ __forceinline__ double stencil_c(int m);
+template <> __device__ __forceinline__ double stencil_c<1>(int) { return 1.0; }
+template <> __device__ __forceinline__ double stencil_c<3>(int m) {
+    return m == 1 ? 1.5 : m == 2 ? -0.15 : 1.0 / 90.0;
+}
+template <int R> __device__ __forceinline__ double stencil_c0() { return R == 1 ? -2.0 : -49.0 / 18.0; }
+
+// True when the node lies within R of a face (on Gamma).
+template <int R>
+__device__ __forceinline__ bool on_gamma(int i, int j, int k, int nx, int ny, int nz) {
+    return i < R || i >= nx - R || j < R || j >= ny - R || k < R || k >= nz - R;
+}
+
+// (H_{I,I} w)(node) = -1/(2h^2) [3 c_0 w + sum over axes and 1 <= m <= R of c_m (w(+m) +
+// w(-m))] + V w, the neighbours outside the box omitted (eq:22, eq:32).  Sums in S.
+template <typename S, int R, typename V>
+__device__ __forceinline__ void apply_h(const V* wo, long long n, int i, int j, int k, int nx, int ny, int nz,
+                                        S inv_h2, S vpot, V c, S& hr, S& hi) {
+    const long long sy = nx, sz = (long long)nx * ny;
+    S sr = 0, si = 0;
+#pragma unroll
+    for (int m = 1; m <= R; ++m) {
+        S ar = 0, ai = 0;
+        if (i >= m) { const V v = wo[n - m]; ar += v.x; ai += v.y; }
+        if (i < nx - m) { const V v = wo[n + m]; ar += v.x; ai += v.y; }
+        if (j >= m) { const V v = wo[n - m * sy]; ar += v.x; ai += v.y; }
+        if (j < ny - m) { const V v = wo[n + m * sy]; ar += v.x; ai += v.y; }
+        if (k >= m) { const V v = wo[n - m * sz]; ar += v.x; ai += v.y; }
+        if (k < nz - m) { const V v = wo[n + m * sz]; ar += v.x; ai += v.y; }
+        if (R == 1) {
+            sr = ar;
+            si = ai;
+        } else {
+            sr += (S)stencil_c<R>(m) * ar;
+            si += (S)stencil_c<R>(m) * ai;
+        }
+    }
+    const S diag = (S)(-1.5 * stencil_c0<R>()) * inv_h2 + vpot;
+    hr = diag * c.x - (S)0.5 * inv_h2 * sr;
+    hi = diag * c.y - (S)0.5 * inv_h2 * si;
 }
 
 // 8-point Walsh-Hadamard transform across the 8 lanes of an aligned lane group:
@@ -664,7 +714,7 @@ __global__ void gemm_blocks_simt(BlockInfo bi, int n_orb, int ng, const typename
 // b = w_f (order 1) or M E w (order 0), natural Gamma order [n_gamma][n_orb].
 // Grid (ceil(nx ny / blockDim), nz, n_orb): one thread per node of a z-plane.
 // --------------------------------------------------------------------------
-template <typename T>
+template <typename T, int R = 1>
 __global__ void stencil_stage(int nx, int ny, int nz, int n_orb, T inv_h2, const typename C2<T>::t* __restrict__ w,
                               const typename C2<T>::t* y, const T* __restrict__ V,
                               const typename C2<T>::t* __restrict__ bterm, typename C2<T>::t* out, T cdt) {
@@ -676,19 +726,10 @@ __global__ void stencil_stage(int nx, int ny, int nz, int n_orb, T inv_h2, const
     const long long n = (long long)k * nx * ny + tp;
     const long long idx = (long long)orb * nvox + n;
     const Vc* wo = w + (long long)orb * nvox;
-    const Vc c = wo[n];
-    T sr = 0, si = 0;
-    if (i > 0) { const Vc v = wo[n - 1]; sr += v.x; si += v.y; }
-    if (i < nx - 1) { const Vc v = wo[n + 1]; sr += v.x; si += v.y; }
-    if (jy > 0) { const Vc v = wo[n - nx]; sr += v.x; si += v.y; }
-    if (jy < ny - 1) { const Vc v = wo[n + nx]; sr += v.x; si += v.y; }
-    if (k > 0) { const Vc v = wo[n - (long long)nx * ny]; sr += v.x; si += v.y; }
-    if (k < nz - 1) { const Vc v = wo[n + (long long)nx * ny]; sr += v.x; si += v.y; }
-    const T diag = (T)3 * inv_h2 + V[n];
-    T hr = diag * c.x - (T)0.5 * inv_h2 * sr;
-    T hi = diag * c.y - (T)0.5 * inv_h2 * si;
-    if (i == 0 || i == nx - 1 || jy == 0 || jy == ny - 1 || k == 0 || k == nz - 1) {
-        const Vc b = bterm[(long long)gamma_index(i, jy, k, nx, ny, nz) * n_orb + orb];
+    T hr, hi;
+    apply_h<T, R>(wo, n, i, jy, k, nx, ny, nz, inv_h2, V[n], wo[n], hr, hi);
+    if (on_gamma<R>(i, jy, k, nx, ny, nz)) {
+        const Vc b = bterm[(long long)gamma_index<R>(i, jy, k, nx, ny, nz) * n_orb + orb];
         hr += b.x;
         hi += b.y;
     }
@@ -730,7 +771,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
-template <typename T>
+template <typename T, int R = 1>
 __global__ void diag_phi(int nx, int ny, int nz, int n_orb, T inv_h2, const typename C2<T>::t* __restrict__ phi,
                          const T* __restrict__ V, double* __restrict__ out /* [n_orb][3] */) {
     __shared__ double sh[32];
@@ -741,15 +782,8 @@ __global__ void diag_phi(int nx, int ny, int nz, int n_orb, T inv_h2, const type
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < nvox; n += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(n % nx), jy = (int)((n / nx) % ny), k = (int)(n / ((long long)nx * ny));
         const typename C2<T>::t c = w[n];
-        double sr = 0, si = 0;
-        if (i > 0) { sr += w[n - 1].x; si += w[n - 1].y; }
-        if (i < nx - 1) { sr += w[n + 1].x; si += w[n + 1].y; }
-        if (jy > 0) { sr += w[n - nx].x; si += w[n - nx].y; }
-        if (jy < ny - 1) { sr += w[n + nx].x; si += w[n + nx].y; }
-        if (k > 0) { sr += w[n - (long long)nx * ny].x; si += w[n - (long long)nx * ny].y; }
-        if (k < nz - 1) { sr += w[n + (long long)nx * ny].x; si += w[n + (long long)nx * ny].y; }
-        const double d = 3.0 * (double)inv_h2 + (double)V[n];
-        const double hr = d * c.x - 0.5 * (double)inv_h2 * sr, hi = d * c.y - 0.5 * (double)inv_h2 * si;
+        double hr, hi;
+        apply_h<double, R>(w, n, i, jy, k, nx, ny, nz, (double)inv_h2, (double)V[n], c, hr, hi);
         s_norm += (double)c.x * c.x + (double)c.y * c.y;
         s_en += (double)c.x * hr + (double)c.y * hi;
     }

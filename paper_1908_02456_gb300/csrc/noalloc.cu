@@ -121,6 +121,7 @@ extern "C" int abc_step_noalloc(const abc_ctx* ctx, void* psi, void* aux, const 
     if (ctx->params.order == 2) return abc::fail(ABC_ERR_UNSUPPORTED, "abc_step_noalloc covers orders 0 and 1");
     if (ctx->params.fit1 != ABC_FIT1_LIMIT)
         return abc::fail(ABC_ERR_UNSUPPORTED, "abc_step_noalloc covers the limit fit of order 1 only");
+    if (ctx->geo.R != 1) return abc::fail(ABC_ERR_UNSUPPORTED, "abc_step_noalloc covers the radius-1 stencil only");
     if (ctx->prec != ABC_FP64 && ctx->prec != ABC_C64_FP32)
         return abc::fail(ABC_ERR_UNSUPPORTED, "abc_step_noalloc covers the ABC_FP64 and ABC_C64_FP32 forms");
     const size_t cb = 2 * ctx->real_bytes;

@@ -15,37 +15,55 @@ namespace abc {
 // Index sets
 // ---------------------------------------------------------------------------
 
-// Gamma index of a boundary node when Gamma is numbered by ascending linear index
-// (x fastest).  Face planes z = 0 and z = nz-1 are entirely on Gamma; a middle
-// plane contributes its first and last rows and the two end nodes of every other row.
-int gamma_index_closed(int i, int j, int k, int nx, int ny, int nz) {
-    const int plane = 2 * nx + 2 * (ny - 2);
-    if (k == 0) return j * nx + i;
-    if (k == nz - 1) return nx * ny + (nz - 2) * plane + j * nx + i;
-    const int base = nx * ny + (k - 1) * plane;
-    if (j == 0) return base + i;
-    if (j == ny - 1) return base + nx + 2 * (ny - 2) + i;
-    return base + nx + 2 * (j - 1) + (i == 0 ? 0 : 1);
+// Gamma index of a boundary node when Gamma (the nodes within R of a face) is numbered
+// by ascending linear index (x fastest).  The first and last R planes z are entirely on
+// Gamma; a middle plane contributes its first and last R rows and the first and last
+// R nodes of every other row.
+int gamma_index_closed(int i, int j, int k, int nx, int ny, int nz, int R) {
+    const int full = nx * ny, mid_rows = ny - 2 * R;
+    const int plane = 2 * R * nx + mid_rows * 2 * R;          // a middle plane
+    if (k < R) return k * full + j * nx + i;
+    if (k >= nz - R) return R * full + (nz - 2 * R) * plane + (k - (nz - R)) * full + j * nx + i;
+    const int base = R * full + (k - R) * plane;
+    if (j < R) return base + j * nx + i;
+    if (j >= ny - R) return base + R * nx + mid_rows * 2 * R + (j - (ny - R)) * nx + i;
+    return base + R * nx + (j - R) * 2 * R + (i < R ? i : R + (i - (nx - R)));
 }
 
 const int kAxisPerms[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0}, {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
 
-int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& err) {
-    if (nx < 3 || ny < 3 || nz < 3) { err = "each axis needs at least 3 interior nodes"; return ABC_ERR_ARG; }
+int build_geometry(int nx, int ny, int nz, double h, Geometry& g, std::string& err, int R) {
+    if (R != 1 && R != 3) { err = "stencil radius must be 1 or 3"; return ABC_ERR_ARG; }
+    if (nx < 2 * R + 1 || ny < 2 * R + 1 || nz < 2 * R + 1) {
+        err = R == 1 ? "each axis needs at least 3 interior nodes" : "each axis needs at least 2R + 1 interior nodes";
+        return ABC_ERR_ARG;
+    }
     if (!(h > 0.0)) { err = "grid spacing must be positive"; return ABC_ERR_ARG; }
     g = Geometry();
-    g.nx = nx; g.ny = ny; g.nz = nz; g.h = h;
+    g.nx = nx; g.ny = ny; g.nz = nz; g.h = h; g.R = R;
+    {
+        // second-difference coefficients c_0 .. c_R of the (2R + 1)-point formula
+        static const double c1[2] = {-2.0, 1.0};
+        static const double c3[4] = {-49.0 / 18.0, 1.5, -0.15, 1.0 / 90.0};
+        for (int m = 0; m <= R; ++m) g.cst[m] = R == 1 ? c1[m] : c3[m];
+    }
     g.n_nodes = (long long)nx * ny * nz;
     if (g.n_nodes > (1LL << 31) - 1 || nz > 65535) { err = "grid too large"; return ABC_ERR_ARG; }
     g.node_gamma.assign((size_t)g.n_nodes, -1);
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
-                const int c = (i == 0) + (i == nx - 1) + (j == 0) + (j == ny - 1) + (k == 0) + (k == nz - 1);
+                // c: exterior nodes coupled to the node (one per axis step m <= R that leaves the box)
+                int c = 0;
+                const int co[3] = {i, j, k}, dm[3] = {nx, ny, nz};
+                for (int a = 0; a < 3; ++a) {
+                    if (co[a] < R) c += R - co[a];
+                    if (co[a] > dm[a] - 1 - R) c += co[a] - (dm[a] - 1 - R);
+                }
                 if (!c) continue;
                 const int node = (k * ny + j) * nx + i;
                 const int gi = (int)g.gamma_node.size();
-                if (gamma_index_closed(i, j, k, nx, ny, nz) != gi) {
+                if (gamma_index_closed(i, j, k, nx, ny, nz, R) != gi) {
                     err = "internal: Gamma numbering mismatch";
                     return ABC_ERR_ARG;
                 }
@@ -212,7 +230,113 @@ static void bessel_j_all(double x, int nmax, double* out) {
     for (int n = 0; n <= nmax; ++n) out[n] *= inv;
 }
 
-void free_green_table(double h, double s, int dx, int dy, int dz, std::vector<cd>& table, bool deriv) {
+// In-place radix-2 FFT of length P (a power of two), sign +1: sum_j e^{+2 pi i jk/P} a_j.
+static void fft_pos(std::vector<cd>& a) {
+    const size_t P = a.size();
+    for (size_t i = 1, j = 0; i < P; ++i) {
+        size_t bit = P >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= P; len <<= 1) {
+        const double ang = 2.0 * M_PI / (double)len;
+        const cd wl(std::cos(ang), std::sin(ang));
+        for (size_t i = 0; i < P; i += len) {
+            cd w(1.0, 0.0);
+            for (size_t k = 0; k < len / 2; ++k) {
+                const cd u = a[i + k], v = a[i + k + len / 2] * w;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+                w *= wl;
+            }
+        }
+    }
+}
+
+// Radius R > 1: the same time integral, G(a,b,c) = i h^2 int_0^inf exp(-s h^2 x)
+// g_a(x) g_b(x) g_c(x) dx, with the 1D kernel g_n(x) = (1/2pi) int exp(i n xi - i x theta(xi))
+// d xi, theta = -(c_0 + 2 sum_m c_m cos(m xi)) / 2 (h^2 times the 1D symbol of -1/2 d^2/dx^2),
+// taken at each quadrature node from one length-P FFT of exp(-i x theta(xi_j)).  P
+// exceeds twice the reach of the kernel at the last node (speed max|theta'| times x)
+// plus the largest offset, so the periodic images add nothing.
+static void free_green_table_fft(const Geometry& g, double s, int dx, int dy, int dz, std::vector<cd>& table,
+                                 bool deriv) {
+    const double h = g.h;
+    const int M = std::max(dx, std::max(dy, dz));
+    const double sh2 = s * h * h;
+    const double xmax = 40.0 / sh2;
+    const int npan = (int)std::ceil(xmax);
+    const int NG = 16;
+    std::vector<double> gx, gw;
+    gauss_legendre(NG, gx, gw);
+    const int Q = npan * NG;
+    std::vector<double> xq(Q), wq(Q);
+    for (int pn = 0; pn < npan; ++pn)
+        for (int i = 0; i < NG; ++i) {
+            const double x = pn + 0.5 * (gx[i] + 1.0);
+            xq[pn * NG + i] = x;
+            wq[pn * NG + i] = 0.5 * gw[i] * std::exp(-sh2 * x) * (deriv ? -h * h * x : 1.0);
+        }
+    double vmax = 0.0;
+    for (int j = 0; j <= 4096; ++j) {
+        const double xi = M_PI * j / 4096.0;
+        double d = 0.0;
+        for (int m = 1; m <= g.R; ++m) d += m * g.cst[m] * std::sin(m * xi);
+        vmax = std::max(vmax, std::fabs(d));
+    }
+    size_t P = 64;
+    while ((double)P < 2.0 * (M + vmax * (npan + 1)) + 64.0) P <<= 1;
+    std::vector<double> theta(P);
+    for (size_t j = 0; j < P; ++j) {
+        const double xi = 2.0 * M_PI * (double)j / (double)P;
+        double t = g.cst[0];
+        for (int m = 1; m <= g.R; ++m) t += 2.0 * g.cst[m] * std::cos(m * xi);
+        theta[j] = -0.5 * t;
+    }
+    std::vector<cd> F((size_t)M * Q);                 // F[n][q] = g_n(x_q)
+#pragma omp parallel
+    {
+        std::vector<cd> a(P);
+#pragma omp for schedule(static)
+        for (int q = 0; q < Q; ++q) {
+            for (size_t j = 0; j < P; ++j) a[j] = std::polar(1.0 / (double)P, -xq[q] * theta[j]);
+            fft_pos(a);
+            for (int n = 0; n < M; ++n) F[(size_t)n * Q + q] = a[n];
+        }
+    }
+    std::vector<cd> tri((size_t)M * M * M, cd(0.0, 0.0));
+#pragma omp parallel
+    {
+        std::vector<cd> Pq(Q);
+#pragma omp for schedule(dynamic)
+        for (int ab = 0; ab < M * M; ++ab) {
+            const int a = ab / M, b = ab % M;
+            if (b < a) continue;
+            const cd* Fa = &F[(size_t)a * Q];
+            const cd* Fb = &F[(size_t)b * Q];
+            for (int q = 0; q < Q; ++q) Pq[q] = wq[q] * (Fa[q] * Fb[q]);
+            for (int c = b; c < M; ++c) {
+                const cd* Fc = &F[(size_t)c * Q];
+                cd acc(0.0, 0.0);
+                for (int q = 0; q < Q; ++q) acc += Pq[q] * Fc[q];
+                tri[((size_t)a * M + b) * M + c] = cd(0.0, h * h) * acc;
+            }
+        }
+    }
+    table.assign((size_t)dx * dy * dz, cd(0.0, 0.0));
+    for (int c = 0; c < dz; ++c)
+        for (int b = 0; b < dy; ++b)
+            for (int a = 0; a < dx; ++a) {
+                int t[3] = {a, b, c};
+                std::sort(t, t + 3);
+                table[((size_t)c * dy + b) * dx + a] = tri[((size_t)t[0] * M + t[1]) * M + t[2]];
+            }
+}
+
+void free_green_table(const Geometry& g, double s, int dx, int dy, int dz, std::vector<cd>& table, bool deriv) {
+    if (g.R != 1) return free_green_table_fft(g, s, dx, dy, dz, table, deriv);
+    const double h = g.h;
     const int M = std::max(dx, std::max(dy, dz));
     const double sh2 = s * h * h;
     const double xmax = 40.0 / sh2;
@@ -290,37 +414,45 @@ void free_green_table(double h, double s, int dx, int dy, int dz, std::vector<cd
 // and K_p = -X_p^{-1} Y_p (order 0), K_p^{-1} = -Y_p^{-1} X_p (order 1).
 
 namespace {
+// Exterior nodes coupled to interior node (i, j, k) by the (2R + 1)-point stencil:
+// n of them, with coordinates c[u] and -H_{node,c[u]} = w[u] / (2 h^2) (w = c_m for an
+// axis step m; 1 for every neighbour when R = 1).
 struct Nb {
     int n;
-    int c[3][3];
+    int c[9][3];
+    double w[9];
 };
 
-Nb exterior_neighbours(int i, int j, int k, int nx, int ny, int nz) {
+Nb exterior_neighbours(const Geometry& g, int i, int j, int k) {
     Nb r;
     r.n = 0;
-    const int co[3] = {i, j, k}, dims[3] = {nx, ny, nz};
-    for (int a = 0; a < 3; ++a) {
-        if (co[a] == 0 || co[a] == dims[a] - 1) {
-            int t[3] = {i, j, k};
-            t[a] = co[a] == 0 ? -1 : dims[a];
-            std::memcpy(r.c[r.n++], t, sizeof(t));
-        }
-    }
+    const int co[3] = {i, j, k}, dims[3] = {g.nx, g.ny, g.nz};
+    for (int a = 0; a < 3; ++a)
+        for (int m = 1; m <= g.R; ++m)
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const int t_a = co[a] + sg * m;
+                if (t_a >= 0 && t_a < dims[a]) continue;
+                int t[3] = {i, j, k};
+                t[a] = t_a;
+                std::memcpy(r.c[r.n], t, sizeof(t));
+                r.w[r.n++] = g.cst[m];
+            }
     return r;
 }
 }  // namespace
 
 int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::string& err,
-                   std::vector<std::vector<cd>>* dK) {
+                   std::vector<std::vector<cd>>* dK, std::vector<std::vector<cd>>* HH) {
     if (!(s > 0.0)) { err = "interpolation point must be positive"; return ABC_ERR_ARG; }
     if (dK && order != 0) { err = "internal: K' is formed on the order-0 route"; return ABC_ERR_ARG; }
+    const bool wantHH = HH != nullptr;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const int tx = nx + 2, ty = ny + 2, tz = nz + 2;
+    const int tx = nx + 2 * g.R, ty = ny + 2 * g.R, tz = nz + 2 * g.R;
     // with dK, a second pass over the same loops with G' = dG/ds gives X' and Y'
     // (X = I + ..., so X' has no identity term)
     std::vector<cd> G, Gd;
-    free_green_table(g.h, s, tx, ty, tz, G);
-    if (dK) free_green_table(g.h, s, tx, ty, tz, Gd, true);
+    free_green_table(g, s, tx, ty, tz, G);
+    if (dK) free_green_table(g, s, tx, ty, tz, Gd, true);
     auto Gt = [&](int dx, int dy, int dz) -> cd {
         return G[((size_t)std::abs(dz) * ty + std::abs(dy)) * tx + std::abs(dx)];
     };
@@ -334,14 +466,15 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
     for (int r = 0; r < R; ++r) {
         const int node = g.rep_node[r];
         rc[r] = {node % nx, (node / nx) % ny, node / (nx * ny)};
-        nb[r] = exterior_neighbours(rc[r][0], rc[r][1], rc[r][2], nx, ny, nz);
+        nb[r] = exterior_neighbours(g, rc[r][0], rc[r][1], rc[r][2]);
     }
     const int dims[3] = {nx, ny, nz};
-    std::vector<cd> X[8], Y[8], Xd[8], Yd[8];
+    std::vector<cd> X[8], Y[8], Xd[8], Yd[8], ZZ[8];
     for (int p = 0; p < 8; ++p) {
         if (g.base_of[p] != p) continue;
         X[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
         Y[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
+        if (wantHH) ZZ[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
         if (dK) {
             Xd[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
             Yd[p].assign((size_t)g.m[p] * g.m[p], cd(0.0, 0.0));
@@ -352,24 +485,28 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
         const int* ci = rc[ri].data();
         const Nb& ni = nb[ri];
         for (int rj = 0; rj < R; ++rj) {
-            cd xv[8], yv[8], xdv[8], ydv[8];
+            cd xv[8], yv[8], xdv[8], ydv[8], zv[8];
             for (int gg = 0; gg < 8; ++gg) {
                 int y[3];
                 for (int a = 0; a < 3; ++a) y[a] = (gg >> a & 1) ? dims[a] - 1 - rc[rj][a] : rc[rj][a];
                 cd xs = (y[0] == ci[0] && y[1] == ci[1] && y[2] == ci[2]) ? cd(1.0, 0.0) : cd(0.0, 0.0);
                 cd xds(0.0, 0.0);
                 for (int u = 0; u < ni.n; ++u) {
-                    xs += ih2 * Gt(ni.c[u][0] - y[0], ni.c[u][1] - y[1], ni.c[u][2] - y[2]);
-                    if (dK) xds += ih2 * Gdt(ni.c[u][0] - y[0], ni.c[u][1] - y[1], ni.c[u][2] - y[2]);
+                    xs += (ih2 * ni.w[u]) * Gt(ni.c[u][0] - y[0], ni.c[u][1] - y[1], ni.c[u][2] - y[2]);
+                    if (dK) xds += (ih2 * ni.w[u]) * Gdt(ni.c[u][0] - y[0], ni.c[u][1] - y[1], ni.c[u][2] - y[2]);
                 }
-                const Nb ny_ = exterior_neighbours(y[0], y[1], y[2], nx, ny, nz);
-                cd ys(0.0, 0.0), yds(0.0, 0.0);
+                const Nb ny_ = exterior_neighbours(g, y[0], y[1], y[2]);
+                cd ys(0.0, 0.0), yds(0.0, 0.0), zs(0.0, 0.0);
                 for (int u = 0; u < ni.n; ++u)
                     for (int v = 0; v < ny_.n; ++v) {
-                        ys += Gt(ni.c[u][0] - ny_.c[v][0], ni.c[u][1] - ny_.c[v][1], ni.c[u][2] - ny_.c[v][2]);
-                        if (dK)
-                            yds += Gdt(ni.c[u][0] - ny_.c[v][0], ni.c[u][1] - ny_.c[v][1], ni.c[u][2] - ny_.c[v][2]);
+                        const double wuv = ni.w[u] * ny_.w[v];
+                        const int d0 = ni.c[u][0] - ny_.c[v][0], d1 = ni.c[u][1] - ny_.c[v][1],
+                                  d2 = ni.c[u][2] - ny_.c[v][2];
+                        ys += wuv * Gt(d0, d1, d2);
+                        if (dK) yds += wuv * Gdt(d0, d1, d2);
+                        if (wantHH && d0 == 0 && d1 == 0 && d2 == 0) zs += wuv;   // shared exterior node
                     }
+                zv[gg] = ih4 * zs;
                 xv[gg] = xs;
                 yv[gg] = ih4 * ys;
                 xdv[gg] = xds;
@@ -380,17 +517,19 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
                 if (g.base_of[p] != p) continue;
                 const int qi = g.rep_adapted[(size_t)ri * 8 + p], qj = g.rep_adapted[(size_t)rj * 8 + p];
                 if (qi < 0 || qj < 0) continue;
-                cd xs(0.0, 0.0), ys(0.0, 0.0), xds(0.0, 0.0), yds(0.0, 0.0);
+                cd xs(0.0, 0.0), ys(0.0, 0.0), xds(0.0, 0.0), yds(0.0, 0.0), zs(0.0, 0.0);
                 for (int gg = 0; gg < 8; ++gg) {
                     const double chi = (__builtin_popcount(p & gg) & 1) ? -1.0 : 1.0;
                     xs += chi * xv[gg];
                     ys += chi * yv[gg];
                     xds += chi * xdv[gg];
                     yds += chi * ydv[gg];
+                    zs += chi * zv[gg];
                 }
                 const size_t a = qi - g.off[p], b = qj - g.off[p];
                 X[p][b * g.m[p] + a] = sc * xs;    // column-major
                 Y[p][b * g.m[p] + a] = sc * ys;
+                if (wantHH) ZZ[p][b * g.m[p] + a] = sc * zs;
                 if (dK) {
                     Xd[p][b * g.m[p] + a] = sc * xds;
                     Yd[p][b * g.m[p] + a] = sc * yds;
@@ -403,6 +542,7 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
     out.s = s;
     out.mat.resize(g.cls.size());
     if (dK) dK->assign(g.cls.size(), std::vector<cd>());
+    if (wantHH) HH->assign(g.cls.size(), std::vector<cd>());
     for (size_t ki = 0; ki < g.cls.size(); ++ki) {
         const auto& k = g.cls[ki];
         const int m = k.m, mb = g.m[k.base];
@@ -431,6 +571,7 @@ int compute_blocks(const Geometry& g, int order, double s, Blocks& out, std::str
         std::vector<cd> Xk, Yk;
         restrict_(X[k.base], Xk);
         restrict_(Y[k.base], Yk);
+        if (wantHH) restrict_(ZZ[k.base], (*HH)[ki]);     // symmetric: row-major = column-major
         std::vector<int> piv(m);
         std::vector<cd>& F = order == 0 ? Xk : Yk;     // factorised
         std::vector<cd>& Z = order == 0 ? Yk : Xk;     // right-hand sides -> result
@@ -566,6 +707,7 @@ int compute_blocks_fit1(const Geometry& g, int fit, double s1, double s1b, Block
     out = Blocks();
     out.order = 1;
     out.fit = fit;
+    out.rows1 = true;
     out.s = s1;
     out.s1b = fit == ABC_FIT1_TWO_POINT ? s1b : 0.0;
     const size_t nc = g.cls.size();
@@ -621,9 +763,44 @@ int compute_blocks_fit1(const Geometry& g, int fit, double s1, double s1b, Block
     return ABC_OK;
 }
 
+// Thm 3.2's fit as general rows (R > 1): A = -i H_{Gamma,II} H_{II,Gamma} per class and
+// B = s1 I - A S with S = K(s1)^{-1} (the order-1 route's blocks).
+static int compute_blocks_limit_rows(const Geometry& g, double s1, Blocks& out, std::string& err) {
+    std::vector<std::vector<cd>> HH;
+    Blocks Sb;
+    int st = compute_blocks(g, 1, s1, Sb, err, nullptr, &HH);
+    if (st) return st;
+    out = Blocks();
+    out.order = 1;
+    out.fit = ABC_FIT1_LIMIT;
+    out.rows1 = true;
+    out.s = s1;
+    const size_t nc = g.cls.size();
+    out.mat2[0].resize(nc);
+    out.mat2[1].resize(nc);
+    for (size_t k = 0; k < nc; ++k) {
+        const int m = g.cls[k].m;
+        const size_t mm = (size_t)m * m;
+        std::vector<cd>& A = out.mat2[1][k];
+        A.assign(mm, cd(0.0, 0.0));
+        for (size_t e = 0; e < mm; ++e) A[e] = cd(0.0, -1.0) * HH[k][e];
+        // B = s1 I - A S.  A and S are symmetric, so their row-major buffers read
+        // column-major are A and S again, and zgemm_sub leaves P = -S A (column-major)
+        // = -(A S)^T; the column-major buffer of a transpose is the row-major buffer of
+        // the matrix, so P's buffer is -(A S) row-major.
+        std::vector<cd> P(mm, cd(0.0, 0.0));
+        zgemm_sub(m, m, m, Sb.mat[k].data(), m, A.data(), m, P.data(), m);
+        std::vector<cd>& B = out.mat2[0][k];
+        B = P;
+        for (int a = 0; a < m; ++a) B[(size_t)a * m + a] += s1;
+    }
+    return ABC_OK;
+}
+
 int compute_param_blocks(const Geometry& g, const abc_params& p, Blocks& b, std::string& err) {
     if (p.order == 2) return compute_blocks2(g, p.s2, b, err);
     if (p.order == 1 && p.fit1 != ABC_FIT1_LIMIT) return compute_blocks_fit1(g, p.fit1, p.s1, p.s1b, b, err);
+    if (p.order == 1 && g.R > 1) return compute_blocks_limit_rows(g, p.s1, b, err);
     return compute_blocks(g, p.order, p.order == 0 ? p.s0 : p.s1, b, err);
 }
 
@@ -633,14 +810,18 @@ int dense_natural(const Geometry& g, const Blocks& b, int which, cd* out, std::s
     const int n = g.n_gamma;
     const double h4 = std::pow(g.h, 4);
     std::fill(out, out + (size_t)n * n, cd(0.0, 0.0));
-    if (b.order == 1 && b.fit != ABC_FIT1_LIMIT && (which == ABC_MAT_A || which == ABC_MAT_B)) {
+    if (b.order == 1 && b.rows1 && (which == ABC_MAT_A || which == ABC_MAT_B)) {
         std::vector<cd> blk[8];
         for (int p = 0; p < 8; ++p)
             if (g.base_of[p] == p && g.m[p]) expand_base_block(g, p, b.mat2[which == ABC_MAT_B ? 0 : 1], blk[p]);
         return natural_from_blocks(g, blk, out);
     }
-    if (b.order == 1 && b.fit != ABC_FIT1_LIMIT && which == ABC_MAT_K) {
-        err = "the two-point and Hermite fits keep B and A only (take K from an order-0 context)";
+    if (b.order == 1 && b.rows1 && which == ABC_MAT_K) {
+        err = "this order-1 form keeps B and A only (take K from an order-0 context)";
+        return ABC_ERR_ARG;
+    }
+    if (which == ABC_MAT_Q && g.R > 1) {
+        err = "Q is kept for radius 1 only (diagonal there)";
         return ABC_ERR_ARG;
     }
     if (which == ABC_MAT_A || which == ABC_MAT_Q) {

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from oracle.coefficients import order0, order1, order1_hermite, order1_two_point, order2
+from oracle.dtn import dtn_eval
 from oracle.lattice import Box
 from paper_1908_02456_gb300 import abc
 from paper_1908_02456_gb300 import build as nb
@@ -44,9 +45,15 @@ def test_rejects_bad_arguments(lib):
                     (abc.abc_params(1, 1.0, 1.0, 9, 1), 1),      # precision
                     (abc.abc_params(1, 1.0, 1.0, 1, 0), 1)]:     # max_orbitals
         assert lib.abc_setup(ctypes.byref(g), ctypes.byref(p), ctypes.byref(ctx)) == code
-    g3 = abc.abc_grid(8, 8, 8, 3, 0.5)
+    g2r = abc.abc_grid(8, 8, 8, 2, 0.5)                         # radius 2 is not built
     p = abc.abc_params(1, 1.0, 1.0, 1, 1)
-    assert lib.abc_setup(ctypes.byref(g3), ctypes.byref(p), ctypes.byref(ctx)) == 7
+    assert lib.abc_setup(ctypes.byref(g2r), ctypes.byref(p), ctypes.byref(ctx)) == 7
+    g3 = abc.abc_grid(8, 8, 8, 3, 0.5)                          # radius 3 with order 2 neither
+    p2 = abc.abc_params(2, 1.0, 1.0, 1, 1, (ctypes.c_double * 4)(1.0, 2.0, 3.0, 10.0))
+    assert lib.abc_setup(ctypes.byref(g3), ctypes.byref(p2), ctypes.byref(ctx)) == 7
+    g3s = abc.abc_grid(6, 8, 8, 3, 0.5)                         # radius 3 needs 2R + 1 nodes per axis
+    out1 = np.zeros(1, np.complex128)
+    assert lib.abc_host_matrices(ctypes.byref(g3s), ctypes.byref(p), 0, out1.ctypes.data_as(ctypes.c_void_p), 16) == 1
     g2 = abc.abc_grid(2, 8, 8, 1, 0.5)
     out = np.zeros(4, np.complex128)
     assert lib.abc_host_matrices(ctypes.byref(g2), ctypes.byref(p), 0, out.ctypes.data_as(ctypes.c_void_p), 64) == 1
@@ -110,3 +117,33 @@ def test_fit1_rejects_bad_parameters(lib):
         abc.abc_host_matrices(dims, h, 1, 1.0, abc.MAT_B, fit1=7)
     with pytest.raises(abc.AbcError):                           # K is not kept by the fits
         abc.abc_host_matrices(dims, h, 1, 1.0, abc.MAT_K, fit1="hermite")
+
+
+@pytest.mark.parametrize("dims,h,s", [((7, 7, 7), 0.5, 1.0), ((8, 7, 9), 0.5, 2.0), ((9, 9, 9), 0.4, 1.0)])
+def test_radius3_host_setup_matches_oracle(lib, dims, h, s):
+    """Radius 3 (Sec. 4.2's 7-point scheme per axis): K(s) by the library's time
+    integral over FFT'd 1D kernels vs the oracle's 3D FFT Green's function; order 1 (Thm
+    3.2) with A = -i H_{Gamma,II} H_{II,Gamma} block-sparse.  K and H H have condition
+    numbers near 1e8 here, so B is compared through the interpolation condition it
+    solves, (s1 I - B)^{-1} A = K(s1), and elementwise only to cond * eps."""
+    box = Box(dims, h, 3)
+    K = dtn_eval(box, s)
+    M = abc.abc_host_matrices(dims, h, 0, s, abc.MAT_M, radius=3)
+    assert np.abs(M - K).max() < 1e-11 * np.abs(K).max()
+    co = order1(box, s, K1=K)
+    A = abc.abc_host_matrices(dims, h, 1, s, abc.MAT_A, radius=3)
+    B = abc.abc_host_matrices(dims, h, 1, s, abc.MAT_B, radius=3)
+    assert np.abs(A - co["A"]).max() < 1e-12 * np.abs(co["A"]).max()
+    assert np.abs(B - co["B"]).max() < 1e-6 * np.abs(co["B"]).max()
+    R11 = np.linalg.solve(s * np.eye(len(B)) - B, A)
+    assert np.abs(R11 - K).max() < 1e-9 * np.abs(K).max()
+    with pytest.raises(abc.AbcError):                  # Q is kept for radius 1 only
+        abc.abc_host_matrices(dims, h, 1, s, abc.MAT_Q, radius=3)
+
+
+def test_radius3_two_point_host_matches_oracle(lib):
+    dims, h = (7, 8, 7), 0.5
+    co = order1_two_point(Box(dims, h, 3), 1.0, 2.0)
+    for which, key in [(abc.MAT_B, "B"), (abc.MAT_A, "A")]:
+        X = abc.abc_host_matrices(dims, h, 1, 1.0, which, fit1="two_point", s1b=2.0, radius=3)
+        assert np.abs(X - co[key]).max() < 1e-6 * np.abs(co[key]).max(), key

@@ -85,3 +85,13 @@ def test_green_continuum_limit():
         errs.append(abs(lat - cont) / abs(cont))
     assert max(errs) < 1e-2
     assert errs[2] < errs[0]
+
+
+@pytest.mark.parametrize("dims,h,s,L,tol", [((7, 8), 1.0, 1.0, 16, 1e-12), ((7, 7, 7), 1.0, 4.0, 8, 1e-11)])
+def test_eval_matches_bruteforce_radius3(dims, h, s, L, tol):
+    """The same two routes with the 7-point-per-axis stencil of Sec. 4.2 (R = 3): a
+    three-node-deep Gamma and exterior couplings c_1 .. c_3 across it."""
+    box = Box(dims, h, 3)
+    Ke = dtn_eval(box, s)
+    Kb = dtn_bruteforce(box, s, L)
+    assert np.abs(Ke - Kb).max() < tol * np.abs(Ke).max()
