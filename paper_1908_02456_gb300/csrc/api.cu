@@ -616,7 +616,7 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
     if (order == 2) {
         // g' = B1 g + (B0 - i A1) f - i A1 E H w + A0 E w  (eq:dynamics2 with E phidot substituted)
         const dev::Ord2Fwd<T> o2{(const Vc*)w_f + (long long)g.n_gamma * n_orb, V, c->hat_h.as<Vc>(),
-                                 c->hat_g.as<Vc>(), g.nx, g.ny, g.nz, (T)(1.0 / (g.h * g.h))};
+                                 c->hat_g.as<Vc>(), g.nx, g.ny, g.nz, (T)(1.0 / (g.h * g.h)), g.R};
         dev::bnd_forward<T, 2><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi, (const Vc*)w_f,
                                                    c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), nullptr, (T)0, o2);
         const void* x4[4] = {c->hat_g.p, c->hat_f.p, c->hat_h.p, c->hat_phi.p};

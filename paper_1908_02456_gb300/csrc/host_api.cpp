@@ -36,8 +36,6 @@ int check_params(const abc_grid* grid, const abc_params* params) {
     if (!grid || !params) return fail(ABC_ERR_ARG, "null grid or params");
     if (grid->radius != 1 && grid->radius != 3)
         return fail(ABC_ERR_UNSUPPORTED, "stencil radius 1 (3-point) or 3 (7-point, Sec. 4.2) only");
-    if (grid->radius == 3 && params->order == 2)
-        return fail(ABC_ERR_UNSUPPORTED, "the second-order ABC is built for radius 1 only");
     if (params->order < 0 || params->order > 2) return fail(ABC_ERR_ARG, "order must be 0, 1 or 2");
     if (params->order == 2) {
         for (int j = 0; j < 4; ++j) {
@@ -57,6 +55,11 @@ int check_params(const abc_grid* grid, const abc_params* params) {
         return fail(ABC_ERR_ARG, "the two-point fit needs s1b > 0 and s1b != s1");
     if (params->precision < ABC_FP64 || params->precision > ABC_C64_3XTF32)
         return fail(ABC_ERR_ARG, "unknown precision");
+    // With radius 3 the order-2 interpolation system is nearly singular (K(s) has
+    // condition numbers near 1e8): B1 and B0 come out with entries near 1e7 whose
+    // products cancel down to eigenvalues of order 1e2, which FP32 cannot resolve.
+    if (grid->radius == 3 && params->order == 2 && params->precision != ABC_FP64)
+        return fail(ABC_ERR_UNSUPPORTED, "the second-order ABC with radius 3 needs ABC_FP64");
     if (params->precision == ABC_C64_SPLIT_BF16)
         return fail(ABC_ERR_UNSUPPORTED, "the split-bf16 form is not built (use ABC_C64_3XTF32)");
     if (params->max_orbitals < 1 || params->max_orbitals > 65535)

@@ -193,6 +193,7 @@ struct Ord2Fwd {
     typename C2<T>::t* hat_g;
     int nx, ny, nz;
     T inv_h2;
+    int R;                           // stencil radius (1 or 3)
 };
 
 template <typename T, int MODE>
@@ -224,15 +225,10 @@ __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, lon
             // (H_{I,I} w)(node) with the neighbours outside the box omitted
             const int nx = o2.nx, ny = o2.ny, nxy = nx * ny;
             const int i = node % nx, jy = (node / nx) % ny, k = node / nxy;
-            T sr = 0, si = 0;
-            if (i > 0) { sr += wo[node - 1].x; si += wo[node - 1].y; }
-            if (i < nx - 1) { sr += wo[node + 1].x; si += wo[node + 1].y; }
-            if (jy > 0) { sr += wo[node - nx].x; si += wo[node - nx].y; }
-            if (jy < ny - 1) { sr += wo[node + nx].x; si += wo[node + nx].y; }
-            if (k > 0) { sr += wo[node - nxy].x; si += wo[node - nxy].y; }
-            if (k < o2.nz - 1) { sr += wo[node + nxy].x; si += wo[node + nxy].y; }
-            const T d = (T)3 * o2.inv_h2 + o2.V[node];
-            xh = mk<T>(d * xp.x - (T)0.5 * o2.inv_h2 * sr, d * xp.y - (T)0.5 * o2.inv_h2 * si);
+            T hr, hi;
+            if (o2.R == 3) apply_h<T, 3>(wo, node, i, jy, k, nx, ny, o2.nz, o2.inv_h2, o2.V[node], xp, hr, hi);
+            else apply_h<T, 1>(wo, node, i, jy, k, nx, ny, o2.nz, o2.inv_h2, o2.V[node], xp, hr, hi);
+            xh = mk<T>(hr, hi);
             xg = o2.w_g[(long long)gi * n_orb + j];
         }
     }

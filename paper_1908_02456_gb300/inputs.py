@@ -44,6 +44,7 @@ class Workload:
     points: Tuple[float, ...] = ()   # order 2: the four interpolation points
     fit1: str = "limit"         # order 1: "limit" | "two_point" | "hermite"
     s1b: float = 0.0            # order 1, two-point fit: the second point
+    radius: int = 1             # stencil radius per axis (1, or 3: Sec. 4.2's 7-point scheme)
 
     @property
     def interp(self):
@@ -77,6 +78,11 @@ WORKLOADS = {
                 "harmonic_bumps", precision="c64", fit1="two_point", s1b=2.0),
     8: Workload(8, "harmonic-64cube-order1-hermite-single", 64, 0.4, 1, 1, 1.0, 0.005, 500,
                 "harmonic_bumps", precision="c64", fit1="hermite"),
+    # Sec. 4.2's 3D experiment: box [-1.5, 1.5]^3 at h = 0.1 (31^3, 7-point scheme per axis,
+    # n_Gamma = 14166), free packet exp(-|x|^2 + 5 i x1) (eq:15 at t = 0), dt = 0.001,
+    # first order fitted at s = 1, 2
+    9: Workload(9, "paper-free-31cube-r3-order1-twopoint", 31, 0.1, 1, 1, 1.0, 0.001, 600,
+                "zero", precision="c64", fit1="two_point", s1b=2.0, radius=3),
 }
 
 
@@ -176,7 +182,10 @@ def make_inputs(w: Workload, n: Optional[int] = None, n_orb: Optional[int] = Non
         V = smooth_random(shape, w.h, rng)
     else:
         raise ValueError(w.potential)
-    if w.number == 1:
+    if w.number == 9:
+        # the paper's packet: eq:15 at t = 0 with k0 = 5 (sigma^2 = 1/2, centre 0)
+        psi = gaussian_packet(shape, w.h, (0.0, 0.0, 0.0), (5.0, 0.0, 0.0), 1.0)[None]
+    elif w.number == 1:
         theta = rng.uniform(0.0, 2.0 * math.pi)
         # centre offset 2 at the 16^3, h=0.5 box (half-width 3.75), scaled with the box
         xc = (-2.0 * half / 3.75, 0.0, 0.0)

@@ -7,7 +7,7 @@ axes, one and three orbitals, element by element."""
 import numpy as np
 import pytest
 
-from oracle.coefficients import order0, order1, order1_two_point
+from oracle.coefficients import order0, order1, order1_two_point, order2
 from oracle.lattice import Box
 from oracle.propagate import System
 from paper_1908_02456_gb300 import inputs
@@ -72,7 +72,37 @@ def test_radius3_run_matches_oracle(torch_cuda, dims, b, prec, order, fit):
     ctx.close()
 
 
-def test_radius3_refuses_adjoint_noalloc_and_order2(torch_cuda):
+@pytest.mark.parametrize("prec", ["fp64"])
+def test_radius3_order2_matches_oracle(torch_cuda, prec):
+    """The second-order ABC (s = 1, 2, 3, 10 as in Sec. 4.2) with the radius-3 stencil, in
+    FP64 (the library refuses complex64 here: the interpolation system is nearly
+    singular and B1, B0 carry entries near 1e7 that cancel to eigenvalues near 1e2).  Two
+    FP64 setups agree only to cond * eps: the library's and the oracle's coefficient sets
+    differ elementwise by ~1e-3 while both interpolate K to ~1e-8 at the four points, so
+    phi is compared at 1e-7 and the auxiliary state [f | g] they drive at 1e-5."""
+    torch = torch_cuda
+    from paper_1908_02456_gb300 import abc
+    dims, h, dt, steps, b = (9, 8, 9), 0.5, 0.005, 40, 2
+    pts = (1.0, 2.0, 3.0, 10.0)
+    rng = np.random.default_rng(95)
+    V = inputs.smooth_random(dims, h, rng)
+    psi0 = np.concatenate([inputs.gaussian_packet(dims, h, (0.2 * j, 0.1, -0.1), (2.0, -0.5 * j, 1.0), 1.0)[None]
+                           for j in range(b)])
+    box = Box(dims, h, 3)
+    sy = System(box, V_ext=V.reshape(-1), coeffs=order2(box, pts))
+    ctx = abc.Context(dims, h, 2, pts, precision=prec, max_orbitals=b, radius=3)
+    psi = torch.from_numpy(psi0).to("cuda", ctx.complex_dtype).contiguous()
+    Vt = torch.from_numpy(V).to("cuda", ctx.real_dtype).contiguous()
+    aux = ctx.init_aux(psi)
+    ref_p, ref_a, _ = sy.run(psi0.reshape(b, -1), dt, steps, f0=sy.initial_aux(psi0.reshape(b, -1)))
+    ctx.run(psi, aux, Vt, dt, steps)
+    torch.cuda.synchronize()
+    assert rel(psi.cpu().numpy().reshape(b, -1), ref_p) < 1e-7
+    a = aux.cpu().numpy().astype(np.complex128)
+    assert rel(a.transpose(2, 0, 1).reshape(b, -1), ref_a) < 1e-5
+
+
+def test_radius3_refuses_adjoint_and_noalloc(torch_cuda):
     import ctypes
     torch = torch_cuda
     from paper_1908_02456_gb300 import abc
@@ -88,5 +118,49 @@ def test_radius3_refuses_adjoint_noalloc_and_order2(torch_cuda):
     assert lib.abc_step_noalloc(ctx.ctx, p.data_ptr(), aux.data_ptr(), V.data_ptr(), 1, 0.01, None) == 7
     ctx.close()
     with pytest.raises(abc.AbcError) as e:
-        abc.Context((8, 8, 8), 0.5, 2, (1.0, 2.0, 3.0, 10.0), precision="fp64", radius=3)
+        abc.Context((8, 8, 8), 0.5, 2, (1.0, 2.0, 3.0, 10.0), precision="c64", radius=3)
     assert e.value.status == 7
+
+
+def test_paper_3d_experiment_replay(torch_cuda):
+    """Sec. 4.2's experiment: box [-1.5, 1.5]^3 at h = 0.1 (31^3, 7 points per axis,
+    n_Gamma = 14166), the free packet of eq:15 with k0 = 5, dt = 0.001, 600 steps.  The
+    paper reports for the number of electrons in the box that about 20 % is reflected
+    with the first-order ABC fitted at s = 1, 2; read here as the norm left in the box
+    minus the closed form's norm in the box at t = 0.6.  Before the packet reaches the
+    faces (t = 0.1) the run follows eq:15 up to the discretisation and the first
+    absorption (< 7 %).  The zeroth order (s0 = 1) reflects more.  (The second order at
+    s = 1, 2, 3, 10 is not replayed: with this stencil and spacing its four-point fit is
+    nearly singular and the fitted dynamics diverge, in the oracle as in the library.)"""
+    torch = torch_cuda
+    from oracle.exact import free_packet
+    from paper_1908_02456_gb300 import abc
+    w1 = inputs.WORKLOADS[9]
+    dims, h, dt = w1.shape, w1.h, w1.dt
+    psi0, V = inputs.make_inputs(w1)
+    ax = (np.arange(dims[0]) - 0.5 * (dims[0] - 1)) * h
+    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+    ex0 = free_packet([X, Y, Z], 0.0, (0, 0, 0), (5.0, 0, 0), 0.5)
+    scale = psi0[0][0, 0, 0] / ex0[0, 0, 0]             # the inputs are h^3-normalised
+    res = {}
+    for name, order, kw in [("order0", 0, {}), ("order1", 1, dict(fit1="two_point", s1b=2.0))]:
+        ctx = abc.Context(dims, h, order, 1.0, precision="c64", radius=3, **kw)
+        assert ctx.n_gamma == 14166
+        psi = torch.from_numpy(psi0).to("cuda", ctx.complex_dtype).contiguous()
+        Vt = torch.from_numpy(V).to("cuda", ctx.real_dtype).contiguous()
+        aux = ctx.new_aux(1) if order == 1 else None
+        d1 = ctx.run(psi, aux, Vt, dt, 100, diag_every=100)
+        p1 = psi.cpu().numpy()[0].astype(np.complex128)
+        d = ctx.run(psi, aux, Vt, dt, 500, diag_every=100)
+        torch.cuda.synchronize()
+        norms = np.concatenate([d1[:, 0, 0], d[:, 0, 0]])
+        ex1 = scale * free_packet([X, Y, Z], 0.1, (0, 0, 0), (5.0, 0, 0), 0.5)
+        res[name] = (norms, float(np.linalg.norm(p1 - ex1) / np.linalg.norm(ex1)))
+        ctx.close()
+    ex6 = scale * free_packet([X, Y, Z], 0.6, (0, 0, 0), (5.0, 0, 0), 0.5)
+    n_exact = float(np.sum(np.abs(ex6) ** 2) * h ** 3)
+    refl = {k: v[0][-1] - n_exact for k, v in res.items()}
+    assert res["order1"][1] < 0.07, res["order1"][1]
+    assert np.all(np.diff(res["order1"][0][:4]) < 0), res["order1"][0]
+    assert 0.1 < refl["order1"] < 0.3, refl
+    assert refl["order0"] > refl["order1"], refl

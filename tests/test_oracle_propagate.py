@@ -8,6 +8,7 @@ import pytest
 import scipy.fft as sfft
 
 from oracle.coefficients import order0, order1, order2
+from oracle.exact import free_packet
 from oracle.lattice import Box
 from oracle.propagate import System
 from paper_1908_02456_gb300 import inputs
@@ -44,13 +45,7 @@ def test_dirichlet_dst_exact():
 
 
 def closed_form_packet(X, t, center, k, sigma2):
-    """Free packet psi0 = exp(-|x-c|^2/(2 sigma^2) + i k.(x-c)) evolved by i psi_t = -Delta psi/2."""
-    d = len(X)
-    a = sigma2 + 1j * t
-    r2 = sum((X[i] - center[i] - k[i] * t) ** 2 for i in range(d))
-    kx = sum(k[i] * (X[i] - center[i]) for i in range(d))
-    k2 = sum(ki * ki for ki in k)
-    return (sigma2 / a) ** (d / 2) * np.exp(-r2 / (2 * a) + 1j * kx - 0.5j * k2 * t)
+    return free_packet(X, t, center, k, sigma2)
 
 
 def test_closed_form_is_papers_eq15():
