@@ -103,7 +103,12 @@ extern "C" {
 typedef struct {
     int nx, ny, nz;   /* interior nodes per axis, each >= 3, nz <= 65535,
                          nx * ny * nz < 2^31                                       */
-    int radius;       /* stencil radius per axis; this build supports 1 only       */
+    int radius;       /* stencil radius per axis: 1 (the 3-point formula) or 3 (the
+                         7-point formula of Sec. 4.2, c = -49/18, 3/2, -3/20, 1/90;
+                         Gamma is then the nodes within 3 of a face, each axis needs
+                         >= 7 nodes, A is block-sparse and order 1 runs on dense class
+                         rows, order 2 needs ABC_FP64, the adjoint and
+                         abc_step_noalloc refuse it, and W is |phi|^2)              */
     double h;         /* grid spacing > 0                                          */
 } abc_grid;
 
@@ -140,7 +145,7 @@ typedef struct abc_ctx abc_ctx;
  * sizes/order/precision, ABC_ERR_SINGULAR, ABC_ERR_ALLOC, ABC_ERR_CUDA. */
 int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx** out);
 
-/* n_gamma = |Gamma| = nx*ny*nz - (nx-2)(ny-2)(nz-2) (eq:25, radius 1). */
+/* n_gamma = |Gamma| = nx*ny*nz - (nx-2R)(ny-2R)(nz-2R) (eq:25, radius R). */
 int abc_boundary_size(const abc_ctx* ctx, long long* n_gamma);
 
 /* One time step of the augmented system in place on (psi, aux), static potential
