@@ -179,6 +179,10 @@ int ensure_workspace(abc_ctx* c) {
     }
     if ((st = c->hat_phi.alloc(aux_b))) return st;
     if ((st = c->hat_f.alloc(aux_b))) return st;
+    if (c->params.order == 1) {
+        if ((st = c->hat2_phi.alloc(aux_b))) return st;
+        if ((st = c->hat2_f.alloc(aux_b))) return st;
+    }
     if (c->params.order == 2) {
         if ((st = c->hat_h.alloc(aux_b))) return st;
         if ((st = c->hat_g.alloc(aux_b))) return st;
@@ -560,23 +564,40 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
 }
 
 // Back transform of a stage, reading t directly, adding split partials, or gathering it.
+// hat_phi / hat_f: the stage's adapted inputs (nullptr: the context's first set).  With
+// fn.hat_phi set (order 1), the kernel also forms the next stage's adapted inputs.
 template <typename T, int MODE>
 void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f, void* out, void* acc, T cdt,
-          cudaStream_t s) {
+          cudaStream_t s, const void* hat_phi = nullptr, const void* hat_f = nullptr,
+          dev::FwdNext<T> fn = dev::FwdNext<T>{}) {
     typedef typename dev::C2<T>::t Vc;
     const dev::CellTab<T> ct = cell_tab<T>(c);
     const unsigned nbk = cell_blocks(c, n_orb);
+    const Vc* hp = (const Vc*)(hat_phi ? hat_phi : c->hat_phi.p);
+    const Vc* hf = (const Vc*)(hat_f ? hat_f : c->hat_f.p);
+    constexpr bool can_fuse = MODE == 0 || MODE == 4;
+    const bool fuse = can_fuse && fn.hat_phi != nullptr;
     if constexpr (sizeof(T) == 4) {
         if (tr.gathered) {
-            launch_pdl(c->pdl, dev::bnd_back<T, MODE, true>, dim3(nbk), dim3(128), 0, s, ct, n_orb, s1, a_coef,
-                       c->hat_phi.as<const Vc>(), c->hat_f.as<const Vc>(), (const Vc*)nullptr, 1, 0LL,
-                       c->sym_gather, (const Vc*)y_f, (Vc*)out, (Vc*)acc, cdt);
+            if (fuse)
+                launch_pdl(c->pdl, dev::bnd_back<T, MODE, true, can_fuse>, dim3(nbk), dim3(128), 0, s, ct, n_orb, s1,
+                           a_coef, hp, hf, (const Vc*)nullptr, 1, 0LL, c->sym_gather, (const Vc*)y_f, (Vc*)out,
+                           (Vc*)acc, cdt, fn);
+            else
+                launch_pdl(c->pdl, dev::bnd_back<T, MODE, true>, dim3(nbk), dim3(128), 0, s, ct, n_orb, s1, a_coef,
+                           hp, hf, (const Vc*)nullptr, 1, 0LL, c->sym_gather, (const Vc*)y_f, (Vc*)out, (Vc*)acc,
+                           cdt, fn);
             return;
         }
     }
-    dev::bnd_back<T, MODE, false><<<nbk, 128, 0, s>>>(ct, n_orb, s1, a_coef, c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(),
-                                                      (const Vc*)tr.t, tr.nsplit, tr.stride, c->sym_gather,
-                                                      (const Vc*)y_f, (Vc*)out, (Vc*)acc, cdt);
+    if (fuse)
+        dev::bnd_back<T, MODE, false, can_fuse><<<nbk, 128, 0, s>>>(ct, n_orb, s1, a_coef, hp, hf, (const Vc*)tr.t,
+                                                                    tr.nsplit, tr.stride, c->sym_gather,
+                                                                    (const Vc*)y_f, (Vc*)out, (Vc*)acc, cdt, fn);
+    else
+        dev::bnd_back<T, MODE, false><<<nbk, 128, 0, s>>>(ct, n_orb, s1, a_coef, hp, hf, (const Vc*)tr.t, tr.nsplit,
+                                                          tr.stride, c->sym_gather, (const Vc*)y_f, (Vc*)out,
+                                                          (Vc*)acc, cdt, fn);
 }
 
 // One Horner stage: out = y + cdt * L(w).  For order >= 1 the interior part (stencil,
@@ -588,7 +609,7 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
 // overlaps the back transform instead.
 template <typename T>
 void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, const void* y_phi, const void* y_f,
-           void* o_phi, void* o_f, const T* V, cudaStream_t s) {
+           void* o_phi, void* o_f, const T* V, cudaStream_t s, int st = -1) {
     typedef typename dev::C2<T>::t Vc;
     const Geometry& g = c->geo;
     const int order = c->params.order;
@@ -607,13 +628,26 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
                 (Vc*)o_phi, cdt);
         prof_end(c, ABC_KERNEL_STENCIL, ss);
     };
+    // where the stencil of an order >= 1 stage runs (ABC_TUNE_STENCIL): 0 forked after the
+    // contraction, 1 forked at the stage start, 2 on the main stream after the back transform
+    const int smode = c->stencil_mode;
     auto fork_stencil = [&]() {
         cudaEventRecord(c->ev_fork, s);
         cudaStreamWaitEvent(c->side, c->ev_fork, 0);
         stencil(c->side);
     };
+    auto stencil_at = [&](int point) {       // point 0: after the contraction, 1: stage start, 2: stage end
+        if (point == 2 && smode == 2) stencil(s);
+        if (point < 2 && point == smode) fork_stencil();
+    };
+    auto join = [&]() {
+        if (smode == 2) return;
+        cudaEventRecord(c->ev_join, c->side);
+        cudaStreamWaitEvent(s, c->ev_join, 0);
+    };
     const T a_coef = (T)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
     if (order == 2) {
+        stencil_at(1);
         // g' = B1 g + (B0 - i A1) f - i A1 E H w + A0 E w  (eq:dynamics2 with E phidot substituted)
         const dev::Ord2Fwd<T> o2{(const Vc*)w_f + (long long)g.n_gamma * n_orb, V, c->hat_h.as<Vc>(),
                                  c->hat_g.as<Vc>(), g.nx, g.ny, g.nz, (T)(1.0 / (g.h * g.h)), g.R};
@@ -621,31 +655,47 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
                                                    c->hat_phi.as<Vc>(), c->hat_f.as<Vc>(), nullptr, (T)0, o2);
         const void* x4[4] = {c->hat_g.p, c->hat_f.p, c->hat_h.p, c->hat_phi.p};
         const TRes tr = contraction<T>(c, nullptr, c->tvec.p, n_orb, 0, s, x4);
-        fork_stencil();
+        stencil_at(0);
         back<T, 3>(c, tr, n_orb, (T)0, (T)0, y_f, o_f, const_cast<void*>(w_f), cdt, s);
-        cudaEventRecord(c->ev_join, c->side);
-        cudaStreamWaitEvent(s, c->ev_join, 0);
+        stencil_at(2);
+        join();
         return;
     }
-    dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
-                                               order == 1 ? (const Vc*)w_f : nullptr, c->hat_phi.as<Vc>(),
-                                               c->hat_f.as<Vc>(), nullptr, (T)0, dev::Ord2Fwd<T>{});
+    // Order 1 inside a step (st = stage 0..3): the back transform of stages 0-2 also forms
+    // the next stage's adapted inputs (two alternating sets), so stages 1-3 skip the
+    // forward transform.
+    const bool chain = st >= 0 && order == 1 && c->chain;
+    if (order >= 1) stencil_at(1);
+    void* hp = chain && (st & 1) ? c->hat2_phi.p : c->hat_phi.p;
+    void* hf = chain && (st & 1) ? c->hat2_f.p : c->hat_f.p;
+    dev::FwdNext<T> fn{};
+    if (chain && st < 3)
+        fn = dev::FwdNext<T>{(const Vc*)w_phi, (const Vc*)y_phi, V, (const Vc*)w_f,
+                             (Vc*)((st & 1) ? c->hat_phi.p : c->hat2_phi.p), (Vc*)((st & 1) ? c->hat_f.p : c->hat2_f.p),
+                             g.nx, g.ny, g.nz, g.R, (T)(1.0 / (g.h * g.h)), c->nvox};
+    if (!(chain && st > 0)) {
+        dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
+                                                   order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf, nullptr,
+                                                   (T)0, dev::Ord2Fwd<T>{});
+    } else {
+        c->launches -= 1;                    // the forward kernel counted by step_impl did not run
+    }
     if (order == 1 && c->blocks.rows1) {
         // general B and A: t = B f_hat + A phi_hat on the rows [B | A], f' = t
-        const void* x2[4] = {c->hat_f.p, c->hat_phi.p, nullptr, nullptr};
+        const void* x2[4] = {hf, hp, nullptr, nullptr};
         const TRes tr = contraction<T>(c, nullptr, c->tvec.p, n_orb, 0, s, x2);
-        fork_stencil();
-        back<T, 4>(c, tr, n_orb, (T)0, (T)0, y_f, o_f, nullptr, cdt, s);
-        cudaEventRecord(c->ev_join, c->side);
-        cudaStreamWaitEvent(s, c->ev_join, 0);
+        stencil_at(0);
+        back<T, 4>(c, tr, n_orb, (T)0, (T)0, y_f, o_f, nullptr, cdt, s, hp, hf, fn);
+        stencil_at(2);
+        join();
         return;
     }
-    const TRes gathered = contraction<T>(c, order == 1 ? c->hat_f.p : c->hat_phi.p, c->tvec.p, n_orb, 0, s);
+    const TRes gathered = contraction<T>(c, order == 1 ? hf : hp, c->tvec.p, n_orb, 0, s);
     if (order == 1) {
-        fork_stencil();
-        back<T, 0>(c, gathered, n_orb, (T)c->blocks.s, a_coef, y_f, o_f, nullptr, cdt, s);
-        cudaEventRecord(c->ev_join, c->side);
-        cudaStreamWaitEvent(s, c->ev_join, 0);
+        stencil_at(0);
+        back<T, 0>(c, gathered, n_orb, (T)c->blocks.s, a_coef, y_f, o_f, nullptr, cdt, s, hp, hf, fn);
+        stencil_at(2);
+        join();
     } else {
         back<T, 1>(c, gathered, n_orb, (T)0, (T)0, nullptr, c->cnat.p, nullptr, (T)0, s);
         stencil(s);
@@ -670,7 +720,7 @@ void step_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, doubl
     for (int st = 0; st < 4; ++st) {
         void* op = st == 3 ? psi : c->Tp[st & 1].p;
         void* of = st == 3 ? aux : c->Tf[st & 1].p;
-        stage<T>(c, n_orb, (T)(cs[st] * dt), in_p, in_f, psi, aux, op, of, Vuse, s);
+        stage<T>(c, n_orb, (T)(cs[st] * dt), in_p, in_f, psi, aux, op, of, Vuse, s, st);
         in_p = op;
         in_f = of;
     }
@@ -1153,6 +1203,17 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
         return ABC_OK;
     }
+    if (key == ABC_TUNE_CHAIN) {
+        ctx->chain = value != 0;
+        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        return ABC_OK;
+    }
+    if (key == ABC_TUNE_STENCIL) {
+        if (value < 0 || value > 2) return fail(ABC_ERR_ARG, "stencil placement must be 0, 1 or 2");
+        ctx->stencil_mode = (int)value;
+        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        return ABC_OK;
+    }
     return fail(ABC_ERR_ARG, "unknown tuning key");
 }
 
@@ -1161,6 +1222,8 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_L2_KEEP_TILES) { *value = ctx->l2_keep_tiles; return ABC_OK; }
     if (key == ABC_TUNE_TILE_COUNT) { *value = ctx->sym ? ctx->sym_tiles_n : 0; return ABC_OK; }
     if (key == ABC_TUNE_PDL) { *value = ctx->pdl ? 1 : 0; return ABC_OK; }
+    if (key == ABC_TUNE_CHAIN) { *value = ctx->chain ? 1 : 0; return ABC_OK; }
+    if (key == ABC_TUNE_STENCIL) { *value = ctx->stencil_mode; return ABC_OK; }
     return fail(ABC_ERR_ARG, "unknown tuning key");
 }
 

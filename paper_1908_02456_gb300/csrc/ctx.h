@@ -59,7 +59,7 @@ struct abc_ctx {
     abc::DevBuf tile_blk, tile_row;   // row tiles (block, first row) of the multi-orbital contraction
     int n_tiles = 0;
     // workspace
-    abc::DevBuf Tp[2], Tf[2], hat_phi, hat_f, hat_h, hat_g, tvec, cnat, Veff, diag;
+    abc::DevBuf Tp[2], Tf[2], hat_phi, hat_f, hat2_phi, hat2_f, hat_h, hat_g, tvec, cnat, Veff, diag;
     abc::DevBuf host_psi, host_aux, host_V;   // device copies for abc_run_host
     cudaStream_t own = nullptr;
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
@@ -76,6 +76,8 @@ struct abc_ctx {
     long long sym_tiles_n = 0;
     long long l2_keep_tiles = 0;     // tiles streamed with evict_last (tuning)
     bool pdl = false;                // programmatic dependent launch of the contraction and gather (tuning)
+    bool chain = true;               // order-1 back transforms form the next stage's adapted inputs (tuning)
+    int stencil_mode = 0;            // where the stencil runs in a stage (tuning, ABC_TUNE_STENCIL)
     double sym_balance = 1.0;        // work weight per right-hand side in the tile partition
     abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_cta_list, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
     abc::dev::SymGather sym_gather{};   // partial-sum view for the back transform

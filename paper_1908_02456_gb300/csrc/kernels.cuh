@@ -342,6 +342,23 @@ __device__ __forceinline__ float2 sym_gather(const SymGather& sg, int4 d) {
     return acc[0];
 }
 
+// The next stage's adapted inputs, formed by the back transform of an order-1 stage
+// (FUSE): at each node of the cell the lane has the stage outputs f' = y_f + cdt v and
+// phi' = y_phi + cdt (-i)(H w + w_f) (the interior stencil's formula at that node), and
+// applies bnd_forward's transform to them, so the next stage needs no forward kernel.
+template <typename T>
+struct FwdNext {
+    const typename C2<T>::t* w_phi;  // stage input phi [n_orb][nvox]
+    const typename C2<T>::t* y_phi;  // step-start phi
+    const T* V;                      // potential
+    const typename C2<T>::t* w_f;    // stage input f, natural [n_gamma][n_orb]
+    typename C2<T>::t* hat_phi;      // next stage's adapted phi
+    typename C2<T>::t* hat_f;        // next stage's adapted f
+    int nx, ny, nz, R;
+    T inv_h2;
+    long long nvox;
+};
+
 // Back: thread (o, p) = (s, g) forms the adapted value x of output o of parity p:
 //   MODE 0 (order-1 step):    x = s1 f_hat + (-i a)(phi_hat - t),  a = a_coef c
 //                             (B f + A E phi with B = s1 I - A S, t = S f_hat)
@@ -362,16 +379,18 @@ __device__ __forceinline__ float2 sym_gather(const SymGather& sg, int4 d) {
 //   MODE 2: out[e] = cdt v, acc[e] += cdt v
 //   MODE 3: out_f[e] = y_f[e] + cdt w_g[e], out_g[e] = y_g[e] + cdt v  (f' = g, g' = v)
 // (only the owner reads y_f / acc there, so the update in place is race-free).
-template <typename T, int MODE, bool GATHER>
+template <typename T, int MODE, bool GATHER, bool FUSE = false>
 __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, T a_coef,
                                                 const typename C2<T>::t* __restrict__ hat_phi,
                                                 const typename C2<T>::t* __restrict__ hat_f,
                                                 const typename C2<T>::t* __restrict__ t_in, int nsplit,
                                                 long long split_stride, SymGather sg,
                                                 const typename C2<T>::t* y_f, typename C2<T>::t* out,
-                                                typename C2<T>::t* acc, T cdt) {
+                                                typename C2<T>::t* acc, T cdt, FwdNext<T> fn) {
+    static_assert(!FUSE || MODE == 0 || MODE == 4, "the fused forward follows an order-1 step");
     typedef typename C2<T>::t V;
     __shared__ V sx[2][8][8];                  // [group][output][parity]
+    __shared__ V sp[FUSE ? 2 : 1][8][8], sf[FUSE ? 2 : 1][8][8];
     const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
     const long long gidx = (long long)blockIdx.x * 2 + grp;
     const bool live = gidx < (long long)ct.n_cells * n_orb;
@@ -384,10 +403,35 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
     int4 gd = make_int4(0, 0, 0, 0);
     if constexpr (GATHER) gd = live ? sg.desc[cell * 64 + t] : gd;
     const T c_cell = (MODE == 0 && live) ? (T)ct.cell_c[cell] : (T)0;
-    T cf[8];
+    T cf[8], cff[8];
 #pragma unroll
     for (int o = 0; o < 8; ++o) cf[o] = live ? ct.coef_bt[(long long)ty * 64 + s * 8 + o] : (T)0;
+    int fgi = -1, fnode = 0;
+    if constexpr (FUSE) {
+        fgi = live ? ct.gi[cell * 64 + t] : -1;
+        fnode = live ? ct.node[cell * 64 + t] : 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cff[q] = jj >= 0 ? ct.coef_f[(long long)ty * 64 + s * 8 + q] : (T)0;
+    }
     pdl_wait();                                // the tables above do not depend on the preceding kernel
+    // FUSE: phi' at this lane's node (the interior stencil's formula) and y_f there; the
+    // loads run while the partial sums are gathered below
+    V fy = mk<T>(0, 0), pn = mk<T>(0, 0);
+    if constexpr (FUSE) {
+        if (fgi >= 0) {
+            fy = y_f[(long long)fgi * n_orb + j];
+            const V* wo = fn.w_phi + (long long)j * fn.nvox;
+            const int fi = fnode % fn.nx, fj = (fnode / fn.nx) % fn.ny, fk = fnode / (fn.nx * fn.ny);
+            T hr, hi;
+            if (fn.R == 3) apply_h<T, 3>(wo, fnode, fi, fj, fk, fn.nx, fn.ny, fn.nz, fn.inv_h2, fn.V[fnode], wo[fnode], hr, hi);
+            else apply_h<T, 1>(wo, fnode, fi, fj, fk, fn.nx, fn.ny, fn.nz, fn.inv_h2, fn.V[fnode], wo[fnode], hr, hi);
+            const V b = fn.w_f[(long long)fgi * n_orb + j];
+            hr += b.x;
+            hi += b.y;
+            const V yp = fn.y_phi[(long long)j * fn.nvox + fnode];
+            pn = mk<T>(yp.x + cdt * hi, yp.y - cdt * hr);
+        }
+    }
     V yv = mk<T>(0, 0), yg = mk<T>(0, 0), wg = mk<T>(0, 0);
     const long long ew = (long long)(wr >= 0 ? wr : 0) * n_orb + j;
     const long long gofs = (long long)ct.n_gamma * n_orb;      // g part of an order-2 auxiliary state
@@ -438,18 +482,43 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
         v.y += cf[o] * sx[grp][o][g].y;
     }
     v = wht8_lanes(v, g);
-    if (wr < 0) return;
-    if (MODE == 0 || MODE == 4) {
-        out[ew] = mk<T>(yv.x + cdt * v.x, yv.y + cdt * v.y);
-    } else if (MODE == 1) {
-        out[ew] = v;
-    } else if (MODE == 2) {
-        const T nr = cdt * v.x, ni = cdt * v.y;
-        out[ew] = mk<T>(nr, ni);
-        acc[ew] = mk<T>(yv.x + nr, yv.y + ni);
-    } else {
-        out[ew] = mk<T>(yv.x + cdt * wg.x, yv.y + cdt * wg.y);
-        out[gofs + ew] = mk<T>(yg.x + cdt * v.x, yg.y + cdt * v.y);
+    if (wr >= 0) {
+        if (MODE == 0 || MODE == 4) {
+            out[ew] = mk<T>(yv.x + cdt * v.x, yv.y + cdt * v.y);
+        } else if (MODE == 1) {
+            out[ew] = v;
+        } else if (MODE == 2) {
+            const T nr = cdt * v.x, ni = cdt * v.y;
+            out[ew] = mk<T>(nr, ni);
+            acc[ew] = mk<T>(yv.x + nr, yv.y + ni);
+        } else {
+            out[ew] = mk<T>(yv.x + cdt * wg.x, yv.y + cdt * wg.y);
+            out[gofs + ew] = mk<T>(yg.x + cdt * v.x, yg.y + cdt * v.y);
+        }
+    }
+    if constexpr (FUSE) {
+        // bnd_forward<T, 0> on (phi', f') at the cell's nodes
+        V xp = mk<T>(0, 0), xf = mk<T>(0, 0);
+        if (fgi >= 0) {
+            xp = pn;
+            xf = mk<T>(fy.x + cdt * v.x, fy.y + cdt * v.y);
+        }
+        xp = wht8_lanes(xp, g);
+        xf = wht8_lanes(xf, g);
+        sp[grp][s][g] = xp;
+        sf[grp][s][g] = xf;
+        __syncthreads();
+        if (jj >= 0) {
+            V ap = mk<T>(0, 0), af = mk<T>(0, 0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                ap.x += cff[q] * sp[grp][q][g].x; ap.y += cff[q] * sp[grp][q][g].y;
+                af.x += cff[q] * sf[grp][q][g].x; af.y += cff[q] * sf[grp][q][g].y;
+            }
+            const long long e = (long long)j * ct.ng + jj;
+            fn.hat_phi[e] = ap;
+            fn.hat_f[e] = af;
+        }
     }
 }
 

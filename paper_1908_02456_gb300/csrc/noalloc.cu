@@ -97,10 +97,11 @@ void step_with_scratch(const abc_ctx* c, void* psi, void* aux, const void* V, in
         if (order == 1)
             abc::dev::bnd_back<T, 0, false><<<nbk, 128, 0, s>>>(ct, n_orb, (T)c->blocks.s, a_coef, hat_phi, hat_f, tvec,
                                                                 1, 0, c->sym_gather, (const Vc*)aux, (Vc*)of, nullptr,
-                                                                cdt);
+                                                                cdt, abc::dev::FwdNext<T>{});
         else
             abc::dev::bnd_back<T, 1, false><<<nbk, 128, 0, s>>>(ct, n_orb, (T)0, (T)0, hat_phi, hat_f, tvec, 1, 0,
-                                                                c->sym_gather, nullptr, cnat, nullptr, (T)0);
+                                                                c->sym_gather, nullptr, cnat, nullptr, (T)0,
+                                                                abc::dev::FwdNext<T>{});
         abc::dev::stencil_stage<T><<<abc::stencil_grid(c, n_orb), 256, 0, s>>>(
             g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)in_p, (const Vc*)psi, (const T*)V,
             order == 1 ? (const Vc*)in_f : cnat, (Vc*)op, cdt);
