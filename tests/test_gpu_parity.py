@@ -201,3 +201,30 @@ def test_one_orbital_complex64_uses_packed_tiles(torch_cuda, prec):
     assert tiles > 0
     assert ctx.kernel_bytes(abc.KERNEL_CONTRACTION, 1) == tiles * 64 * 64 * 8 + 2 * ctx.n_gamma * 8
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,b", [("c64", 1), ("fp64", 1), ("c64", 3), ("tf32x3", 3)])
+def test_chained_forward_matches_separate_forward(torch_cuda, prec, b):
+    """ABC_TUNE_CHAIN (the back transform forms the next stage's adapted inputs) gives the
+    same steps as separate forward transforms, to rounding."""
+    torch = torch_cuda
+    from paper_1908_02456_gb300 import abc
+    dims, h, dt = (10, 9, 11), 0.5, 0.01
+    rng = np.random.default_rng(70 + b)
+    V = inputs.smooth_random(dims, h, rng)
+    psi0 = np.concatenate([inputs.gaussian_packet(dims, h, (0.2 * j, 0.0, -0.2), (2.0, 1.0 - j, 0.5), 1.0)[None]
+                           for j in range(b)])
+    outs = []
+    for chain in (0, 1):
+        ctx = abc.Context(dims, h, 1, 1.0, precision=prec, max_orbitals=b)
+        ctx.set_tuning(abc.TUNE_CHAIN, chain)
+        psi = torch.from_numpy(psi0).to("cuda", ctx.complex_dtype).contiguous()
+        Vt = torch.from_numpy(V).to("cuda", ctx.real_dtype).contiguous()
+        aux = ctx.new_aux(b)
+        ctx.run(psi, aux, Vt, dt, 30)
+        torch.cuda.synchronize()
+        outs.append((psi.cpu().numpy().astype(np.complex128), aux.cpu().numpy().astype(np.complex128)))
+        ctx.close()
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    for a, c in zip(outs[0], outs[1]):
+        assert np.linalg.norm(a - c) <= tol * np.linalg.norm(a)
