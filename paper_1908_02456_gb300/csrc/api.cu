@@ -82,6 +82,9 @@ int upload_tables(abc_ctx* c) {
     return ABC_OK;
 }
 
+static_assert(abc::dev::SYM_CONSUMERS == abc::dev::SYM_GATHER_WARPS,
+              "the back transform gathers one row partial per consumer warp of the contraction");
+
 // Class blocks in the device format: row-major, rows padded to a multiple of 4
 // complex elements so that every row starts on a 32-byte boundary.  One BlockInfo
 // entry per (class, right-hand side), in ascending adapted offset.

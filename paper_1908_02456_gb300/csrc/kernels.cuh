@@ -84,13 +84,18 @@ struct CellTab {
 // t[j] = sum of the row parts of the segments of (class c, tile row I) + the column
 // parts of the tiles (c, K, I), K > I (fixed order).  desc is indexed like the cell
 // output table (cell * 64 + 8 o + p): x = row-part element of the first segment and
-// warp 0 (the 8 consumer warps' partials are 192 elements apart), y = number of row
-// segments (consecutive, 1536 elements apart), z = column-part element of K = I + 1,
+// warp 0 (the SYM_GATHER_WARPS warps' partials are 192 elements apart), y = number of row
+// segments (consecutive, 192 * SYM_GATHER_WARPS elements apart), z = column-part element
+// of K = I + 1,
 // w = (number of K) | ((I + 2) << 16); the column-part element of K + 1 is that of K
 // plus (K + 1) * 192.
+// Row partials per segment of the tiled contraction: one per consumer warp (equal to
+// its SYM_CONSUMERS, checked where both are visible).
+constexpr int SYM_GATHER_WARPS = 8;
+
 struct SymGather {
     const int4* desc;
-    const float2* rowpart;       // [segment][8 warps][3][64]
+    const float2* rowpart;       // [segment][SYM_GATHER_WARPS warps][3][64]
     const float2* colpart;       // [tile][3][64]
 };
 
@@ -275,16 +280,17 @@ __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, lon
 // first two row segments and the first 24 column parts are all issued before any
 // of them is used (one memory round trip for the common case); the sums are then
 // formed in a fixed order: eight accumulators (the row part of warp w into
-// accumulator w, column part K into accumulator (K - I - 1) % 8), added at the end.
+// accumulator w % 8, column part K into accumulator (K - I - 1) % 8), added at the end.
 __device__ __forceinline__ float2 sym_gather(const SymGather& sg, int4 d) {
-    constexpr int RS = 2, CB = 3;                  // row segments and column batches of 8 hoisted
+    constexpr int RS = 2, CB = 3, NW = SYM_GATHER_WARPS;   // row segments and column batches hoisted
+    constexpr int SEG = 192 * NW;
     const int nk = d.w & 0xffff;
-    float2 rv[RS][8], cv[CB][8];
+    float2 rv[RS][NW], cv[CB][8];
 #pragma unroll
     for (int q = 0; q < RS; ++q)
 #pragma unroll
-        for (int w = 0; w < 8; ++w)
-            rv[q][w] = q < d.y ? sg.rowpart[d.x + (size_t)q * 1536 + w * 192] : make_float2(0.f, 0.f);
+        for (int w = 0; w < NW; ++w)
+            rv[q][w] = q < d.y ? sg.rowpart[d.x + (size_t)q * SEG + w * 192] : make_float2(0.f, 0.f);
     int e = d.z, step = d.w >> 16;
 #pragma unroll
     for (int b = 0; b < CB; ++b)
@@ -300,17 +306,17 @@ __device__ __forceinline__ float2 sym_gather(const SymGather& sg, int4 d) {
 #pragma unroll
     for (int q = 0; q < RS; ++q)
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {                  // the 8 warps' partials of the segment
-            acc[w].x += rv[q][w].x;
-            acc[w].y += rv[q][w].y;
+        for (int w = 0; w < NW; ++w) {                 // the warps' partials of the segment
+            acc[w & 7].x += rv[q][w].x;
+            acc[w & 7].y += rv[q][w].y;
         }
     for (int q = RS; q < d.y; ++q) {
-        const float2* rp = sg.rowpart + d.x + (size_t)q * 1536;
+        const float2* rp = sg.rowpart + d.x + (size_t)q * SEG;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
+        for (int w = 0; w < NW; ++w) {
             const float2 v = rp[w * 192];
-            acc[w].x += v.x;
-            acc[w].y += v.y;
+            acc[w & 7].x += v.x;
+            acc[w & 7].y += v.y;
         }
     }
 #pragma unroll
