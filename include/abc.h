@@ -243,6 +243,13 @@ int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, double* bytes);
 int abc_step_noalloc(const abc_ctx* ctx, void* psi, void* aux, const void* V, int n_orb, double dt,
                      void* stream);
 
+/* Fault-free check of the bounded-wait error path: one block waits on a barrier that
+ * nothing completes, gives up after `polls` (1 .. 2^24) polls and raises the context's
+ * device error flag, exactly as a bounded wait of the contraction does; the call then
+ * returns ABC_ERR_TIMEOUT (and clears the flag), synchronising `stream`.  The context
+ * stays usable.  Nothing traps, faults or spins without a bound. */
+int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
+
 /* Tuning knobs of the kernels (chosen by the autotuner, paper_1908_02456_gb300/tune.py):
  *   ABC_TUNE_L2_KEEP_TILES  number of leading 64x64 boundary tiles that the one-orbital
  *                           complex64 contraction streams with an L2 evict_last hint so

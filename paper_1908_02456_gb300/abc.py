@@ -69,6 +69,7 @@ def load():
         "abc_diagnostics": [_P, _P, _P, _P, ctypes.c_int, MF, _P, _P],
         "abc_adjoint_run": [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_int, _P, _P, _P],
         "abc_get_matrices": [_P, ctypes.c_int, _P, ctypes.c_size_t],
+        "abc_wait_selftest": [_P, ctypes.c_longlong, _P],
         "abc_host_matrices": [G, Pm, ctypes.c_int, _P, ctypes.c_size_t],
         "abc_profile_enable": [_P, ctypes.c_int],
         "abc_profile_read": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
@@ -172,6 +173,11 @@ def abc_adjoint_run(ctx, psi0_ptr, V_ptr, n_orb, dt, nsteps, ckpt_every, dJdV_pt
     _check(load().abc_adjoint_run(ctx, psi0_ptr, V_ptr, n_orb, dt, nsteps, ckpt_every, ctypes.byref(J), dJdV_ptr,
                                   stream or None))
     return J.value
+
+
+def abc_wait_selftest(ctx, polls: int, stream=None) -> int:
+    """Status of the bounded-wait self-test (ABC_ERR_TIMEOUT = 5 when the path works)."""
+    return int(load().abc_wait_selftest(ctx, int(polls), stream))
 
 
 def abc_get_matrices(ctx, which: int, n_gamma: int) -> np.ndarray:

@@ -500,6 +500,21 @@ int build_tc(abc_ctx* c) {
     return ABC_OK;
 }
 
+// Waits on a barrier that nothing completes, at most `polls` polls, then raises the
+// error flag the way the contraction's bounded waits do (the fault-free check of that
+// path; nothing traps or spins without a bound).
+__global__ void wait_selftest_kernel(long long polls, int* err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        dev::mbar_init(&bar, 1);                // one arrival expected, none ever made
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    bool done = false;
+    for (long long i = 0; i < polls && !done; ++i) done = dev::mbar_try_wait(&bar, 0);
+    if (!done && threadIdx.x == 0) atomicExch(err, 1);
+}
+
 // A device wait that gave up (bounded mbarrier waits) -> ABC_ERR_TIMEOUT; resets the flag.
 int check_device_flag(abc_ctx* c, cudaStream_t s) {
     if (!c->err_flag.p) return ABC_OK;
@@ -1248,4 +1263,15 @@ extern "C" void abc_destroy(abc_ctx* ctx) {
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     delete ctx;
+}
+
+extern "C" int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream) {
+    if (!ctx) return fail(ABC_ERR_ARG, "null context");
+    if (polls < 1 || polls > (1LL << 24)) return fail(ABC_ERR_ARG, "polls must be in [1, 2^24]");
+    if (!ctx->err_flag.p) return fail(ABC_ERR_ARG, "context has no device error flag");
+    cudaStream_t s = (cudaStream_t)stream;
+    wait_selftest_kernel<<<1, 32, 0, s>>>(polls, ctx->err_flag.as<int>());
+    int st = last_launch_status();
+    if (st) return st;
+    return check_device_flag(ctx, s);
 }

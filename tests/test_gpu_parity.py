@@ -228,3 +228,24 @@ def test_chained_forward_matches_separate_forward(torch_cuda, prec, b):
     tol = 1e-13 if prec == "fp64" else 1e-6
     for a, c in zip(outs[0], outs[1]):
         assert np.linalg.norm(a - c) <= tol * np.linalg.norm(a)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(torch_cuda):
+    """Failure detection without a fault: a device wait on a barrier that nothing
+    completes gives up after a bounded number of polls, the host reads ABC_ERR_TIMEOUT
+    from the context's flag, and the context keeps working afterwards."""
+    torch = torch_cuda
+    from paper_1908_02456_gb300 import abc
+    dims, h = (8, 8, 8), 0.5
+    ctx = abc.Context(dims, h, 1, 1.0, precision="c64")
+    assert abc.abc_wait_selftest(ctx.ctx, 1000) == 5
+    assert b"bounded device wait" in abc.load().abc_last_error()
+    psi = torch.from_numpy(inputs.gaussian_packet(dims, h, (0, 0, 0), (2.0, 0, 0), 1.0)[None]).to(
+        "cuda", torch.complex64).contiguous()
+    aux = ctx.new_aux(1)
+    V = torch.zeros(dims, dtype=torch.float32, device="cuda")
+    ctx.run(psi, aux, V, 0.01, 10)                      # raises on a nonzero status
+    torch.cuda.synchronize()
+    assert torch.isfinite(torch.view_as_real(psi)).all()
+    assert abc.abc_wait_selftest(ctx.ctx, 1000) == 5    # and the check works again
+    ctx.close()
