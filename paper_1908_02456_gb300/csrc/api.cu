@@ -289,37 +289,116 @@ int build_sym(abc_ctx* c) {
     if ((st = c->sym_tiles.alloc(host.size() * sizeof(float)))) return st;
     CUDA_TRY(cudaMemcpy(c->sym_tiles.p, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice));
     // Work units: tile rows of a class (row I has I + 1 tiles), split into pieces of at
-    // most SYM_PIECE tiles.  Each piece is one segment: its row part stays in registers
-    // and is stored once at its end, which costs about as much as two tiles.  The
-    // pieces are bin-packed over the CTAs longest first (LPT); a CTA takes any set of
-    // segments.  Segments are numbered by (class, row, first tile), so the segments of
-    // one row are consecutive (the back transform's gather relies on it).
+    // most `cap` tiles.  Each piece is one segment: its row part stays in registers and
+    // is stored once at its end.  The pieces are bin-packed over the CTAs longest first
+    // (LPT); a CTA takes any set of segments.  Costs are a model fitted to per-CTA
+    // timings of this kernel on GB300 (us): 1.0 per segment, and per tile 0.36 / 0.59 /
+    // 0.87 off the diagonal and 0.0 / 0.29 / 0.41 on it for R = 1 / 2 / 3 right-hand
+    // sides.  The cap with the smallest predicted makespan is kept.  Segments are
+    // numbered by (class, row, first tile), so the segments of one row are consecutive
+    // (the back transform's gather relies on it).
     int sms = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     const int G = std::max(1, sms);
     struct Piece { int c, I, t0, t1; double cost; };
-    std::vector<Piece> pieces;
-    constexpr int SYM_PIECE = 12;
-    const double seg_cost = 1.5 * c->sym_balance, tile_base = 0.3;
-    for (int k = 0; k < nc; ++k)
-        for (int I = 0; I < si.nt[k]; ++I) {
-            const int len = I + 1, np = (len + SYM_PIECE - 1) / SYM_PIECE;
-            const int t0 = (int)(si.tbase[k] + (long long)I * (I + 1) / 2);
-            for (int q = 0; q < np; ++q) {
-                const int a = t0 + q * len / np, b = t0 + (q + 1) * len / np;
-                pieces.push_back({k, I, a, b, (b - a) * (tile_base + 0.2 * si.R[k]) + seg_cost});
+    static const double tile_off[4] = {0.0, 0.36, 0.59, 0.87}, tile_diag[4] = {0.0, 0.0, 0.29, 0.41};
+    const double seg_cost = 1.0;
+    auto make_pieces = [&](int cap, std::vector<Piece>& out) {
+        out.clear();
+        for (int k = 0; k < nc; ++k)
+            for (int I = 0; I < si.nt[k]; ++I) {
+                const int len = I + 1, np = (len + cap - 1) / cap;
+                const int t0 = (int)(si.tbase[k] + (long long)I * (I + 1) / 2);
+                for (int q = 0; q < np; ++q) {
+                    const int a = t0 + q * len / np, b = t0 + (q + 1) * len / np;
+                    const bool has_diag = q == np - 1;          // the row's last tile is its diagonal one
+                    const int R = si.R[k];
+                    const double cost = seg_cost + (b - a - (has_diag ? 1 : 0)) * tile_off[R] +
+                                        (has_diag ? tile_diag[R] : 0.0);
+                    out.push_back({k, I, a, b, cost});
+                }
             }
+    };
+    auto lpt = [&](const std::vector<Piece>& ps, std::vector<int>& owner) {
+        std::vector<int> order(ps.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ps[a].cost > ps[b].cost; });
+        std::vector<double> load(G, 0.0);
+        std::vector<int> cnt(G, 0);
+        owner.assign(ps.size(), 0);
+        for (int i : order) {
+            // least loaded CTA that still has room in its segment cache
+            int best = -1;
+            for (int g2 = 0; g2 < G; ++g2)
+                if (cnt[g2] < abc::dev::SYM_SEG_CACHE && (best < 0 || load[g2] < load[best])) best = g2;
+            if (best < 0) return 1e300;
+            owner[i] = best;
+            load[best] += ps[i].cost;
+            ++cnt[best];
         }
-    std::vector<int> order(pieces.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pieces[a].cost > pieces[b].cost; });
-    std::vector<double> load(G, 0.0);
-    std::vector<int> owner(pieces.size(), 0);
-    for (int i : order) {
-        const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        owner[i] = b;
-        load[b] += pieces[i].cost;
+        return *std::max_element(load.begin(), load.end());
+    };
+    // Alternative: contiguous runs of tiles in (class, row, tile) order, cut where the
+    // running cost (tiles plus one segment cost at every row start and at every cut)
+    // reaches the next multiple of the total / G; a CTA's run is split at row ends
+    // into its segments.
+    auto contiguous = [&](std::vector<Piece>& out, std::vector<int>& own) {
+        struct T1 { int k, I, t; double c; };
+        std::vector<T1> tl;
+        double total = 0.0;
+        for (int k = 0; k < nc; ++k)
+            for (int I = 0; I < si.nt[k]; ++I) {
+                const int t0 = (int)(si.tbase[k] + (long long)I * (I + 1) / 2);
+                for (int J = 0; J <= I; ++J) {
+                    const double ct = (J < I ? tile_off[si.R[k]] : tile_diag[si.R[k]]) + (J == 0 ? seg_cost : 0.0);
+                    tl.push_back({k, I, t0 + J, ct});
+                    total += ct;
+                }
+            }
+        const double target = (total + seg_cost * G) / G;
+        out.clear();
+        own.clear();
+        std::vector<double> load(G, 0.0);
+        int b = 0;
+        size_t i = 0;
+        while (i < tl.size()) {
+            // one segment: tiles of the same row, within CTA b
+            const size_t i0 = i;
+            double c = (tl[i].t == (int)(si.tbase[tl[i].k] + (long long)tl[i].I * (tl[i].I + 1) / 2)) ? 0.0 : seg_cost;
+            while (i < tl.size() && tl[i].k == tl[i0].k && tl[i].I == tl[i0].I) {
+                if (b < G - 1 && load[b] + c + 0.5 * tl[i].c > target && i > i0) break;
+                c += tl[i].c;
+                ++i;
+            }
+            if (i == i0) {                                // the CTA is full before this segment starts
+                ++b;
+                continue;
+            }
+            out.push_back({tl[i0].k, tl[i0].I, tl[i0].t, tl[i - 1].t + 1, c});
+            own.push_back(b);
+            load[b] += c;
+            if (i < tl.size() && b < G - 1 && load[b] + 0.5 * tl[i].c > target) ++b;
+        }
+        for (int g2 = 0; g2 < G; ++g2) {
+            int n = 0;
+            for (int o : own) n += o == g2;
+            if (n > abc::dev::SYM_SEG_CACHE) return 1e300;
+        }
+        return *std::max_element(load.begin(), load.end());
+    };
+    std::vector<Piece> pieces, trial;
+    std::vector<int> owner, trial_owner;
+    double best_span = contiguous(pieces, owner);
+    for (int cap : {4, 6, 8, 12, 16}) {
+        make_pieces(cap, trial);
+        const double span = lpt(trial, trial_owner);
+        if (span < best_span - 1e-9) {
+            best_span = span;
+            pieces = trial;
+            owner = trial_owner;
+        }
     }
+    if (best_span >= 1e300) return fail(ABC_ERR_ARG, "internal: too many segments for the tiled contraction");
     // pieces are generated in (class, row, first tile) order already: their index is the segment id
     std::vector<int4> segs(pieces.size());
     for (size_t i = 0; i < pieces.size(); ++i)
