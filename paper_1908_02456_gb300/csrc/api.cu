@@ -403,33 +403,34 @@ int build_sym(abc_ctx* c) {
     std::vector<int4> segs(pieces.size());
     for (size_t i = 0; i < pieces.size(); ++i)
         segs[i] = make_int4(pieces[i].c, pieces[i].I, pieces[i].t0, pieces[i].t1);
-    std::vector<int> cta(G + 1, 0), cta_list;
-    for (int b = 0; b < G; ++b) {
-        cta[b] = (int)cta_list.size();
-        for (size_t i = 0; i < pieces.size(); ++i)
-            if (owner[i] == b) cta_list.push_back((int)i);
-        if ((int)cta_list.size() - cta[b] > abc::dev::SYM_SEG_CACHE)
-            return fail(ABC_ERR_ARG, "internal: too many segments for one CTA of the tiled contraction");
+    // per-CTA work lists at a fixed stride: (16 s + class, I, first tile, end tile)
+    const int CAP = abc::dev::SYM_SEG_CACHE;
+    static_assert(abc::dev::SYM_SEG_CACHE <= abc::dev::SYM_THREADS, "one record per thread");
+    static_assert(abc::dev::SYM_CMAX <= 16, "class index packed in 4 bits");
+    std::vector<int4> rec((size_t)G * CAP, make_int4(0, 0, 0, 0));
+    std::vector<int> cta_cnt(G, 0);
+    for (size_t i = 0; i < pieces.size(); ++i) {
+        const int b = owner[i];
+        if (cta_cnt[b] >= CAP) return fail(ABC_ERR_ARG, "internal: too many segments for one CTA of the tiled contraction");
+        if (i >= (size_t)1 << 27) return fail(ABC_ERR_ARG, "internal: too many segments for the tiled contraction");
+        rec[(size_t)b * CAP + cta_cnt[b]++] = make_int4(((int)i << 4) | segs[i].x, segs[i].y, segs[i].z, segs[i].w);
     }
-    cta[G] = (int)cta_list.size();
     std::vector<int2> rowseg(rb, make_int2(0, 0));
     for (size_t s = 0; s < segs.size(); ++s) {
         const int cI = si.rbase[segs[s].x] + segs[s].y;
         if (rowseg[cI].y == 0) rowseg[cI].x = (int)s;
         rowseg[cI].y = (int)s + 1;
     }
-    if ((st = c->sym_seg.alloc(segs.size() * sizeof(int4)))) return st;
-    if ((st = c->sym_cta.alloc(cta.size() * sizeof(int)))) return st;
-    if ((st = c->sym_cta_list.alloc(cta_list.size() * sizeof(int)))) return st;
-    CUDA_TRY(cudaMemcpy(c->sym_cta_list.p, cta_list.data(), cta_list.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if ((st = c->sym_seg.alloc(rec.size() * sizeof(int4)))) return st;
+    if ((st = c->sym_cta.alloc(cta_cnt.size() * sizeof(int)))) return st;
     if ((st = c->sym_rowseg.alloc(rowseg.size() * sizeof(int2)))) return st;
     if ((st = c->sym_rowpart.alloc(segs.size() * SYM_T * abc::dev::SYM_RMAX * abc::dev::SYM_CONSUMERS *
                                    sizeof(float2))))
         return st;
     if ((st = c->sym_colpart.alloc((size_t)NT * SYM_T * abc::dev::SYM_RMAX * sizeof(float2)))) return st;
     if ((st = c->err_flag.alloc(sizeof(int)))) return st;
-    CUDA_TRY(cudaMemcpy(c->sym_seg.p, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(c->sym_cta.p, cta.data(), cta.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->sym_seg.p, rec.data(), rec.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->sym_cta.p, cta_cnt.data(), cta_cnt.size() * sizeof(int), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(c->sym_rowseg.p, rowseg.data(), rowseg.size() * sizeof(int2), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemset(c->err_flag.p, 0, sizeof(int)));
     CUDA_TRY(cudaFuncSetAttribute(abc::dev::sym_gemv_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -632,7 +633,6 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
     if (n_orb == 1 && sizeof(T) == 4 && c->sym) {
         launch_pdl(c->pdl, dev::sym_gemv_tiles, dim3(c->sym_grid), dim3(dev::SYM_THREADS), dev::SYM_SMEM, s, c->si,
                    c->sym_tiles.as<const float2>(), c->sym_seg.as<const int4>(), c->sym_cta.as<const int>(),
-                   c->sym_cta_list.as<const int>(),
                    (const float2*)x, c->sym_rowpart.as<float2>(), c->sym_colpart.as<float2>(), conj,
                    (long long)c->l2_keep_tiles, c->err_flag.as<int>());
         res.gathered = true;

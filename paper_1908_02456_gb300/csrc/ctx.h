@@ -78,7 +78,7 @@ struct abc_ctx {
     bool pdl = false;                // programmatic dependent launch of the contraction and gather (tuning)
     bool chain = false;              // order-1 back transforms form the next stage's adapted inputs (tuning)
     int stencil_mode = 0;            // where the stencil runs in a stage (tuning, ABC_TUNE_STENCIL)
-    abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_cta_list, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
+    abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
     abc::dev::SymGather sym_gather{};   // partial-sum view for the back transform
     // many-orbital complex64 contraction on the tensor cores (ABC_C64_3XTF32)
     bool tc = false;

@@ -301,16 +301,16 @@ __device__ __forceinline__ bool sym_segment(const SymInfo& si, int4 sg, int s, i
     return ok;
 }
 
-// seg[s] = (class, tile row I, first tile, end tile), numbered by (class, row, first
-// tile); CTA b works on the segments cta_list[cta_seg[b]] .. cta_list[cta_seg[b+1]-1]
-// (at most SYM_SEG_CACHE, tiles of different segments need not be contiguous).
-// rowpart[s][8 warps][3][64] and colpart[t][3][64] (complex, right-hand side k of R
-// at index k; slots k >= R are not written).
+// Segment s = (class c, tile row I, first tile, end tile), numbered by (class, row,
+// first tile).  CTA b works on cta_cnt[b] <= SYM_SEG_CACHE segments, stored in order at
+// rec[b * SYM_SEG_CACHE + i] as (16 s + c, I, first tile, end tile), so the CTA reads its
+// whole work list with one round of independent loads (tiles of different segments need
+// not be contiguous).  rowpart[s][8 warps][3][64] and colpart[t][3][64] (complex,
+// right-hand side k of R at index k; slots k >= R are not written).
 static __global__ void __launch_bounds__(SYM_THREADS, 1)
-sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restrict__ seg,
-               const int* __restrict__ cta_seg, const int* __restrict__ cta_list, const float2* __restrict__ x,
-               float2* __restrict__ rowpart, float2* __restrict__ colpart, int conj, long long keep,
-               int* __restrict__ err) {
+sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restrict__ rec,
+               const int* __restrict__ cta_cnt, const float2* __restrict__ x, float2* __restrict__ rowpart,
+               float2* __restrict__ colpart, int conj, long long keep, int* __restrict__ err) {
     float* colf = reinterpret_cast<float*>(colpart);
     extern __shared__ __align__(128) unsigned char smem[];
     float2* ring = reinterpret_cast<float2*>(smem);
@@ -320,12 +320,12 @@ sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restr
     int4* segc = reinterpret_cast<int4*>(empty + SYM_STAGES);       // this CTA's segments
     int* sidc = reinterpret_cast<int*>(segc + SYM_SEG_CACHE);       // and their ids
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int l_begin = cta_seg[blockIdx.x], nseg = cta_seg[blockIdx.x + 1] - l_begin;
+    const int nseg = cta_cnt[blockIdx.x];
+    const int4 r = tid < SYM_SEG_CACHE ? rec[(size_t)blockIdx.x * SYM_SEG_CACHE + tid] : make_int4(0, 0, 0, 0);
     if (nseg <= 0 || nseg > SYM_SEG_CACHE) return;               // the host guarantees <= SYM_SEG_CACHE
-    for (int i = tid; i < nseg; i += blockDim.x) {
-        const int id = cta_list[l_begin + i];
-        sidc[i] = id;
-        segc[i] = seg[id];
+    if (tid < nseg) {
+        sidc[tid] = r.x >> 4;
+        segc[tid] = make_int4(r.x & 15, r.y, r.z, r.w);
     }
     if (tid == 0) {
         for (int i = 0; i < SYM_STAGES; ++i) {
