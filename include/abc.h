@@ -256,10 +256,12 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           that they stay in L2 from one Horner stage to the next
  *                           (the rest use evict_first); 0 = all evict_first.
  *   ABC_TUNE_TILE_COUNT     (read only) number of stored tiles.
- *   ABC_TUNE_PDL            1: launch the tiled contraction and the back transform
- *                           that gathers its partial sums with a programmatic
- *                           dependency on the preceding kernel (early start of
- *                           their independent work); 0 (default): ordinary launches.
+ *   ABC_TUNE_PDL            1 (default): launch the one-orbital tiled contraction
+ *                           as a programmatic dependent of the forward transform
+ *                           before it, so its CTAs start and copy their first
+ *                           boundary tiles while the forward transform runs (they
+ *                           wait for it before reading its output); 0: ordinary
+ *                           launch.
  *   ABC_TUNE_CHAIN          1: in an order-1 step the back transforms of stages 1-3
  *                           also form the next stage's symmetry-adapted inputs (the
  *                           stencil's formula at the boundary nodes plus the forward

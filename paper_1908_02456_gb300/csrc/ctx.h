@@ -75,7 +75,7 @@ struct abc_ctx {
     int sym_grid = 0;
     long long sym_tiles_n = 0;
     long long l2_keep_tiles = 0;     // tiles streamed with evict_last (tuning)
-    bool pdl = false;                // programmatic dependent launch of the contraction and gather (tuning)
+    bool pdl = true;                 // the contraction is a programmatic dependent of the forward transform (tuning)
     bool chain = false;              // order-1 back transforms form the next stage's adapted inputs (tuning)
     int stencil_mode = 0;            // where the stencil runs in a stage (tuning, ABC_TUNE_STENCIL)
     abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;

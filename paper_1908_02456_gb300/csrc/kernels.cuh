@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, lon
                                                    typename C2<T>::t* __restrict__ hat_f,
                                                    typename C2<T>::t* __restrict__ u, T a_coef, Ord2Fwd<T> o2) {
     typedef typename C2<T>::t V;
+    pdl_trigger();                             // the contraction's tile copies need nothing from here
     __shared__ V sp[2][8][8], sf[2][8][8];     // [group][slot][parity]
     __shared__ V sh[MODE == 2 ? 2 : 1][8][8], sg2[MODE == 2 ? 2 : 1][8][8];
     const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
@@ -419,7 +420,6 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
 #pragma unroll
         for (int q = 0; q < 8; ++q) cff[q] = jj >= 0 ? ct.coef_f[(long long)ty * 64 + s * 8 + q] : (T)0;
     }
-    pdl_wait();                                // the tables above do not depend on the preceding kernel
     // FUSE: phi' at this lane's node (the interior stencil's formula) and y_f there; the
     // loads run while the partial sums are gathered below
     V fy = mk<T>(0, 0), pn = mk<T>(0, 0);

@@ -335,7 +335,6 @@ sym_gemv_tiles(SymInfo si, const float2* __restrict__ tiles, const int4* __restr
         fence_mbar_init();
     }
     __syncthreads();
-    pdl_trigger();
     int ntl = 0;                                     // tiles of this CTA
     for (int i = 0; i < nseg; ++i) ntl += segc[i].w - segc[i].z;
 
