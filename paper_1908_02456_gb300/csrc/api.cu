@@ -435,11 +435,11 @@ int build_sym(abc_ctx* c) {
     CUDA_TRY(cudaMemset(c->err_flag.p, 0, sizeof(int)));
     CUDA_TRY(cudaFuncSetAttribute(abc::dev::sym_gemv_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)abc::dev::SYM_SMEM));
-    // the forward transform that precedes the contraction runs with the largest shared-memory
-    // carveout, so the contraction's CTAs (launched as its programmatic dependents) fit on
-    // an SM beside its blocks
-    CUDA_TRY(cudaFuncSetAttribute(abc::dev::bnd_forward<float, 0>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  (int)cudaSharedmemCarveoutMaxShared));
+    // the forward transform that precedes the one-orbital contraction runs with the largest
+    // shared-memory carveout, so the contraction's CTAs (launched as its programmatic
+    // dependents) fit on an SM beside its blocks
+    CUDA_TRY(cudaFuncSetAttribute(abc::dev::bnd_forward<float, 0, true>,
+                                  cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared));
     c->si = si;
     c->sym_grid = G;
     c->sym_tiles_n = NT;
@@ -778,9 +778,16 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
                              (Vc*)((st & 1) ? c->hat_phi.p : c->hat2_phi.p), (Vc*)((st & 1) ? c->hat_f.p : c->hat2_f.p),
                              g.nx, g.ny, g.nz, g.R, (T)(1.0 / (g.h * g.h)), c->nvox};
     if (!(chain && st > 0)) {
-        dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
-                                                   order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf, nullptr,
-                                                   (T)0, dev::Ord2Fwd<T>{});
+        // ahead of the one-orbital tiled contraction, the variant that lets it start early
+        const bool early = n_orb == 1 && sizeof(T) == 4 && c->sym && !(order == 1 && c->blocks.rows1);
+        if (early)
+            dev::bnd_forward<T, 0, true><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
+                                                             order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,
+                                                             nullptr, (T)0, dev::Ord2Fwd<T>{});
+        else
+            dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
+                                                       order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,
+                                                       nullptr, (T)0, dev::Ord2Fwd<T>{});
     } else {
         c->launches -= 1;                    // the forward kernel counted by step_impl did not run
     }

@@ -201,7 +201,9 @@ struct Ord2Fwd {
     int R;                           // stencil radius (1 or 3)
 };
 
-template <typename T, int MODE>
+// EARLY: the kernel lets its programmatic dependent (the one-orbital tiled contraction)
+// launch as soon as it starts.
+template <typename T, int MODE, bool EARLY = false>
 __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, long long nvox,
                                                    const typename C2<T>::t* __restrict__ w_phi,
                                                    const typename C2<T>::t* __restrict__ w_f,
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, lon
                                                    typename C2<T>::t* __restrict__ hat_f,
                                                    typename C2<T>::t* __restrict__ u, T a_coef, Ord2Fwd<T> o2) {
     typedef typename C2<T>::t V;
-    pdl_trigger();                             // the contraction's tile copies need nothing from here
+    if constexpr (EARLY) pdl_trigger();        // the contraction's tile copies need nothing from here
     __shared__ V sp[2][8][8], sf[2][8][8];     // [group][slot][parity]
     __shared__ V sh[MODE == 2 ? 2 : 1][8][8], sg2[MODE == 2 ? 2 : 1][8][8];
     const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
