@@ -540,6 +540,8 @@ int build_tc(abc_ctx* c) {
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     std::vector<TcTile> tiles;
     std::vector<TcCols> cranges;
+    std::vector<TcItem> items;
+    std::vector<int> item_off;
     const int B = c->params.max_orbitals;
     c->tc_b.assign(B + 1, abc_ctx::TcPlan{});
     long long max_chunks = 0, max_part = 0;
@@ -565,6 +567,41 @@ int build_tc(abc_ctx* c) {
         pl.max_nkb = maxnkb;
         // enough CTAs for about three per SM; partial sums of the splits are added later
         pl.nsplit = std::max(1, std::min(TC_MAX_SPLIT, (3 * sms + pl.tile_cnt - 1) / pl.tile_cnt));
+        // persistent form: items (tile, split) in (class, row tile, split, column range)
+        // order, so the items that share an A chunk run at about the same time, each given
+        // to the CTA with the least work so far (cost: its K blocks plus two for the
+        // fill and the epilogue)
+        {
+            std::vector<TcItem> its;
+            for (int ti = pl.tile_off; ti < pl.tile_off + pl.tile_cnt; ++ti)
+                for (int sp = 0; sp < pl.nsplit; ++sp) its.push_back(TcItem{ti, sp});
+            std::stable_sort(its.begin(), its.end(), [&](const TcItem& a, const TcItem& b2) {
+                const TcTile &x = tiles[a.tile], &y = tiles[b2.tile];
+                if (x.cls != y.cls) return x.cls < y.cls;
+                if (x.row0 != y.row0) return x.row0 < y.row0;
+                if (a.split != b2.split) return a.split < b2.split;
+                return x.col0 < y.col0;
+            });
+            const int G = std::min<int>(sms, (int)its.size());
+            std::vector<std::vector<TcItem>> per(G);
+            std::vector<long long> load(G, 0);
+            for (const TcItem& w : its) {
+                const int nkb = info.nkb[tiles[w.tile].cls];
+                const int nk = (int)((long long)nkb * (w.split + 1) / pl.nsplit - (long long)nkb * w.split / pl.nsplit);
+                int best = 0;
+                for (int g2 = 1; g2 < G; ++g2)
+                    if (load[g2] < load[best]) best = g2;
+                per[best].push_back(w);
+                load[best] += nk + 2;
+            }
+            pl.grid = G;
+            pl.off_base = (int)item_off.size();
+            for (int g2 = 0; g2 < G; ++g2) {
+                item_off.push_back((int)items.size());
+                for (const TcItem& w : per[g2]) items.push_back(w);
+            }
+            item_off.push_back((int)items.size());
+        }
         max_chunks = std::max<long long>(max_chunks, chunks);
         if (pl.nsplit > 1) max_part = std::max<long long>(max_part, (long long)pl.nsplit * g.n_gamma * b);
     }
@@ -572,6 +609,10 @@ int build_tc(abc_ctx* c) {
     CUDA_TRY(cudaMemcpy(c->tc_tiles.p, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice));
     if ((st = c->tc_cols.alloc(cranges.size() * sizeof(TcCols)))) return st;
     CUDA_TRY(cudaMemcpy(c->tc_cols.p, cranges.data(), cranges.size() * sizeof(TcCols), cudaMemcpyHostToDevice));
+    if ((st = c->tc_items.alloc(items.size() * sizeof(TcItem)))) return st;
+    CUDA_TRY(cudaMemcpy(c->tc_items.p, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice));
+    if ((st = c->tc_item_off.alloc(item_off.size() * sizeof(int)))) return st;
+    CUDA_TRY(cudaMemcpy(c->tc_item_off.p, item_off.data(), item_off.size() * sizeof(int), cudaMemcpyHostToDevice));
     if ((st = c->tc_bpack.alloc((size_t)max_chunks * TC_B_BYTES))) return st;
     if (max_part && (st = c->tc_part.alloc((size_t)max_part * sizeof(float2)))) return st;
     if (!c->err_flag.p) {
@@ -579,6 +620,7 @@ int build_tc(abc_ctx* c) {
         CUDA_TRY(cudaMemset(c->err_flag.p, 0, sizeof(int)));
     }
     CUDA_TRY(cudaFuncSetAttribute(gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    CUDA_TRY(cudaFuncSetAttribute(gemm_tc_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCP_SMEM));
     c->tc_sms = sms;
     c->tci = info;
     c->tc = true;
@@ -651,9 +693,16 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
         dev::pack_x_tc<<<dim3((unsigned)pl.cols_cnt, (unsigned)pl.max_nkb), 128, 0, s>>>(
             c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off, n_orb, n, (const float2*)x, c->tc_bpack.as<float>());
         float2* out = pl.nsplit > 1 ? c->tc_part.as<float2>() : (float2*)t;
-        dev::gemm_tc<<<dim3((unsigned)pl.tile_cnt, (unsigned)pl.nsplit), dev::TC_THREADS, dev::TC_SMEM, s>>>(
-            c->tci, c->tc_tiles.as<dev::TcTile>() + pl.tile_off, c->tc_apack.as<float>(), c->tc_bpack.as<float>(),
-            n_orb, n, pl.nsplit, (long long)n * n_orb, out, conj, c->err_flag.as<int>());
+        if (c->tc_persist)
+            dev::gemm_tc_persist<<<(unsigned)pl.grid, dev::TCP_THREADS, dev::TCP_SMEM, s>>>(
+                c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(),
+                c->tc_item_off.as<int>() + pl.off_base, c->tc_apack.as<float>(), c->tc_bpack.as<float>(), n_orb, n,
+                pl.nsplit, (long long)n * n_orb, out, conj, c->err_flag.as<int>());
+        else
+            dev::gemm_tc<<<dim3((unsigned)pl.tile_cnt, (unsigned)pl.nsplit), dev::TC_THREADS, dev::TC_SMEM, s>>>(
+                c->tci, c->tc_tiles.as<dev::TcTile>() + pl.tile_off, c->tc_apack.as<float>(),
+                c->tc_bpack.as<float>(), n_orb, n, pl.nsplit, (long long)n * n_orb, out, conj,
+                c->err_flag.as<int>());
         c->launches += 1;
         res.t = out;
         res.nsplit = pl.nsplit;
@@ -1319,6 +1368,11 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
         return ABC_OK;
     }
+    if (key == ABC_TUNE_TC_PERSIST) {
+        ctx->tc_persist = value != 0;
+        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        return ABC_OK;
+    }
     if (key == ABC_TUNE_STENCIL) {
         if (value < 0 || value > 2) return fail(ABC_ERR_ARG, "stencil placement must be 0, 1 or 2");
         ctx->stencil_mode = (int)value;
@@ -1335,6 +1389,7 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_PDL) { *value = ctx->pdl ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_CHAIN) { *value = ctx->chain ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL) { *value = ctx->stencil_mode; return ABC_OK; }
+    if (key == ABC_TUNE_TC_PERSIST) { *value = ctx->tc_persist ? 1 : 0; return ABC_OK; }
     return fail(ABC_ERR_ARG, "unknown tuning key");
 }
 

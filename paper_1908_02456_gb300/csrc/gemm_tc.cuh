@@ -283,5 +283,184 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const float* __restrict__
     if (!ok) atomicExch(err, 1);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent form.  One CTA per SM works through its own list of (output tile, K
+// split) items (item_off[b] .. item_off[b + 1] of items[], balanced by the host);
+// warp 0 streams the A and X chunks of all its items through one ring, warp 1 issues
+// the MMAs, and warps 2-5 run the epilogue.  Each item accumulates its real and
+// imaginary parts directly,
+//     Re T = Sr Xr - Si Xi,   Im T = Si Xr + Sr Xi     (conj(S): + Si Xi, - Si Xr)
+// the minus sign taken by the instruction descriptor's negate-A bit, into one of two
+// TMEM buffers (2 x 128 columns each), so the epilogue of an item drains one buffer
+// while the MMAs of the next fill the other.
+constexpr int TCP_THREADS = 192;
+constexpr size_t TCP_SMEM = (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + 1024;
+
+struct TcItem {
+    int tile, split;
+};
+
+static __global__ void __launch_bounds__(TCP_THREADS, 1)
+gemm_tc_persist(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict__ items,
+                const int* __restrict__ item_off, const float* __restrict__ apack, const float* __restrict__ bpack,
+                int n_orb, int ng, int nsplit, long long split_stride, float2* __restrict__ out, int conj,
+                int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char* sA = tc_smem;                                       // [stage][4 planes]
+    unsigned char* sB = tc_smem + (size_t)TC_STAGES * TC_A_BYTES;      // [stage][4 planes]
+    uint64_t* full = reinterpret_cast<uint64_t*>(tc_smem + (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES));
+    uint64_t* empty = full + TC_STAGES;
+    uint64_t* tfull = empty + TC_STAGES;                               // [2] accumulators ready
+    uint64_t* tempty = tfull + 2;                                      // [2] accumulators drained
+    uint64_t* fin = tempty + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(fin + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = item_off[blockIdx.x], i1 = item_off[blockIdx.x + 1];
+    if (tid == 0) {
+        for (int i = 0; i < TC_STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], 4);                  // the four epilogue warps
+        }
+        mbar_init(fin, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+    bool ok = true;
+    long long issued = 0;                              // producer: K blocks copied
+    if (tid == 0) {
+        // ---------------- producer ----------------
+        for (int it = i0; it < i1 && ok; ++it) {
+            const TcItem w = items[it];
+            const TcTile tile = tiles[w.tile];
+            const int c = tile.cls, nkb = info.nkb[c], N = tile.n;
+            const int kb0 = (int)((long long)nkb * w.split / nsplit), kb1 = (int)((long long)nkb * (w.split + 1) / nsplit);
+            const float* achunk =
+                apack + (size_t)(info.abase[c] + (long long)(tile.row0 / TC_M) * nkb) * (TC_A_BYTES / 4);
+            const float* bchunk = bpack + (size_t)tile.bchunk0 * (TC_B_BYTES / 4);
+            const uint32_t b_bytes = (uint32_t)N * 256;
+            for (int kb = kb0; kb < kb1 && ok; ++kb, ++issued) {
+                const int st = (int)(issued % TC_STAGES);
+                if (issued >= TC_STAGES) ok &= mbar_wait_bounded(&empty[st], (uint32_t)((issued / TC_STAGES - 1) & 1));
+                mbar_expect_tx(&full[st], TC_A_BYTES + b_bytes);
+                bulk_g2s(sA + (size_t)st * TC_A_BYTES, achunk + (size_t)kb * (TC_A_BYTES / 4), TC_A_BYTES, &full[st]);
+                bulk_g2s(sB + (size_t)st * TC_B_BYTES, bchunk + (size_t)kb * (TC_B_BYTES / 4), b_bytes, &full[st]);
+            }
+        }
+    } else if (tid == 32) {
+        // ---------------- MMA issuer ----------------
+        long long g = 0;                               // K blocks consumed
+        int q = 0;                                     // items with K blocks
+        for (int it = i0; it < i1 && ok; ++it) {
+            const TcItem w = items[it];
+            const TcTile tile = tiles[w.tile];
+            const int c = tile.cls, nkb = info.nkb[c], N = tile.n;
+            const int kb0 = (int)((long long)nkb * w.split / nsplit), kb1 = (int)((long long)nkb * (w.split + 1) / nsplit);
+            if (kb1 <= kb0) continue;
+            const int buf = q & 1;
+            if (q >= 2) ok &= mbar_wait_bounded(&tempty[buf], (uint32_t)((q / 2 - 1) & 1));
+            tc_fence_after();
+            const uint32_t idesc = tc_idesc(N), idesc_neg = idesc | (1u << 13);   // negate A
+            const uint32_t d_re = tmem + buf * 256, d_im = d_re + 128;
+            const uint32_t pb = (uint32_t)N * 64;                         // X plane stride in the chunk
+            // Re: Sr Xr -+ Si Xi; Im: +- Si Xr + Sr Xi (conj: the second sign)
+            const uint32_t id_sixi = conj ? idesc : idesc_neg, id_sixr = conj ? idesc_neg : idesc;
+            for (int kb = kb0; kb < kb1 && ok; ++kb, ++g) {
+                const int st = (int)(g % TC_STAGES);
+                ok &= mbar_wait_bounded(&full[st], (uint32_t)((g / TC_STAGES) & 1));
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sA + (size_t)st * TC_A_BYTES), b0 = smem_u32(sB + (size_t)st * TC_B_BYTES);
+#pragma unroll
+                for (int ks = 0; ks < TC_KB / 8; ++ks) {
+                    const uint32_t ko = ks * 256;
+                    const uint64_t srh = tc_desc(a0 + 0 * TC_A_PLANE + ko), srl = tc_desc(a0 + 1 * TC_A_PLANE + ko);
+                    const uint64_t sih = tc_desc(a0 + 2 * TC_A_PLANE + ko), sil = tc_desc(a0 + 3 * TC_A_PLANE + ko);
+                    const uint64_t xrh = tc_desc(b0 + 0 * pb + ko), xrl = tc_desc(b0 + 1 * pb + ko);
+                    const uint64_t xih = tc_desc(b0 + 2 * pb + ko), xil = tc_desc(b0 + 3 * pb + ko);
+                    const uint32_t acc0 = (kb > kb0 || ks > 0) ? 1u : 0u;
+                    tc_mma(d_re, srh, xrh, idesc, acc0); tc_mma(d_re, srh, xrl, idesc, 1u); tc_mma(d_re, srl, xrh, idesc, 1u);
+                    tc_mma(d_re, sih, xih, id_sixi, 1u); tc_mma(d_re, sih, xil, id_sixi, 1u); tc_mma(d_re, sil, xih, id_sixi, 1u);
+                    tc_mma(d_im, sih, xrh, id_sixr, acc0); tc_mma(d_im, sih, xrl, id_sixr, 1u); tc_mma(d_im, sil, xrh, id_sixr, 1u);
+                    tc_mma(d_im, srh, xih, idesc, 1u); tc_mma(d_im, srh, xil, idesc, 1u); tc_mma(d_im, srl, xih, idesc, 1u);
+                }
+                tc_commit(&empty[st]);                // the slot is free once these MMAs are done
+            }
+            tc_commit(&tfull[buf]);                   // the item's accumulators are complete
+            ++q;
+        }
+        tc_commit(fin);
+        ok &= mbar_wait_bounded(fin, 0);              // every MMA done before the TMEM is freed
+    } else if (warp >= 2) {
+        // ---------------- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 ----------------
+        const int quad = warp & 3;
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+        int q = 0;
+        for (int it = i0; it < i1 && ok; ++it) {
+            const TcItem w = items[it];
+            const TcTile tile = tiles[w.tile];
+            const int c = tile.cls, nkb = info.nkb[c], N = tile.n, m = info.m[c];
+            const int kb0 = (int)((long long)nkb * w.split / nsplit), kb1 = (int)((long long)nkb * (w.split + 1) / nsplit);
+            const bool any = kb1 > kb0;
+            const int buf = q & 1;
+            if (any) {
+                ok &= mbar_wait_bounded(&tfull[buf], (uint32_t)((q / 2) & 1));
+                ok = __all_sync(0xffffffffu, ok);      // the warp stays converged for tcgen05.ld
+                if (!ok) break;
+                tc_fence_after();
+            }
+            const int row = tile.row0 + quad * 32 + lane;
+            float2* dst = out + (size_t)w.split * split_stride;
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float pr[16], pi[16];
+                if (any) {
+                    tc_ld16(lane_base + buf * 256 + c0, pr);
+                    tc_ld16(lane_base + buf * 256 + 128 + c0, pi);
+                    tc_wait_ld();
+                }
+                if (row < m) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int col = tile.col0 + c0 + i;
+                        const int k = col / n_orb, o = col - k * n_orb;
+                        if (c0 + i < N && k < info.R[c])
+                            dst[(size_t)o * ng + info.moff[c][k] + row] =
+                                any ? make_float2(pr[i], pi[i]) : make_float2(0.f, 0.f);
+                    }
+                }
+            }
+            if (any) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+                ++q;
+            }
+        }
+    }
+    // the producer's last copies land before the CTA frees its shared memory (they have,
+    // unless a wait gave up)
+    if (tid == 0)
+        for (long long g = issued > TC_STAGES ? issued - TC_STAGES : 0; g < issued; ++g)
+            ok &= mbar_wait_bounded(&full[g % TC_STAGES], (uint32_t)((g / TC_STAGES) & 1));
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+    if (!ok) atomicExch(err, 1);
+}
+
 }  // namespace dev
 }  // namespace abc
