@@ -272,10 +272,6 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           0 (default) on a second stream forked after the boundary
  *                           contraction, 1 forked at the stage start, 2 on the main
  *                           stream after the back transform.
- *   ABC_TUNE_TC_PERSIST     1 (default): the many-orbital tensor-core contraction
- *                           runs as one persistent CTA per SM over a balanced list
- *                           of (output tile, K split) items, its epilogue
- *                           overlapping the next item's MMAs; 0: one CTA per item.
  * Setting a knob drops the cached CUDA graph.  The paper has no counterpart.
  */
 #define ABC_TUNE_L2_KEEP_TILES 0
@@ -283,7 +279,6 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
 #define ABC_TUNE_PDL 2
 #define ABC_TUNE_CHAIN 3
 #define ABC_TUNE_STENCIL 4
-#define ABC_TUNE_TC_PERSIST 5
 int abc_set_tuning(abc_ctx* ctx, int key, long long value);
 int abc_get_tuning(const abc_ctx* ctx, int key, long long* value);
 

@@ -18,7 +18,7 @@ FP64, C64_FP32, C64_SPLIT_BF16, C64_3XTF32 = 0, 1, 2, 3
 MAT_K, MAT_M, MAT_A, MAT_B, MAT_Q = 0, 1, 2, 3, 4
 MAT_B1, MAT_B0, MAT_A1, MAT_A0 = 5, 6, 7, 8
 KERNEL_CONTRACTION, KERNEL_STENCIL = 0, 1
-TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT, TUNE_PDL, TUNE_CHAIN, TUNE_STENCIL, TUNE_TC_PERSIST = 0, 1, 2, 3, 4, 5
+TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT, TUNE_PDL, TUNE_CHAIN, TUNE_STENCIL = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16, "tf32x3": C64_3XTF32}
 FIT1_LIMIT, FIT1_TWO_POINT, FIT1_HERMITE = 0, 1, 2
 FITS1 = {"limit": FIT1_LIMIT, "two_point": FIT1_TWO_POINT, "hermite": FIT1_HERMITE}

@@ -620,7 +620,6 @@ int build_tc(abc_ctx* c) {
         CUDA_TRY(cudaMemset(c->err_flag.p, 0, sizeof(int)));
     }
     CUDA_TRY(cudaFuncSetAttribute(gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-    CUDA_TRY(cudaFuncSetAttribute(gemm_tc_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCP_SMEM));
     c->tc_sms = sms;
     c->tci = info;
     c->tc = true;
@@ -691,18 +690,13 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
     } else if (sizeof(T) == 4 && c->tc) {
         const abc_ctx::TcPlan& pl = c->tc_b[n_orb];
         dev::pack_x_tc<<<dim3((unsigned)pl.cols_cnt, (unsigned)pl.max_nkb), 128, 0, s>>>(
-            c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off, n_orb, n, (const float2*)x, c->tc_bpack.as<float>());
+            c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off, n_orb, n, (const float2*)x, conj,
+            c->tc_bpack.as<float>());
         float2* out = pl.nsplit > 1 ? c->tc_part.as<float2>() : (float2*)t;
-        if (c->tc_persist)
-            dev::gemm_tc_persist<<<(unsigned)pl.grid, dev::TCP_THREADS, dev::TCP_SMEM, s>>>(
-                c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(),
-                c->tc_item_off.as<int>() + pl.off_base, c->tc_apack.as<float>(), c->tc_bpack.as<float>(), n_orb, n,
-                pl.nsplit, (long long)n * n_orb, out, conj, c->err_flag.as<int>());
-        else
-            dev::gemm_tc<<<dim3((unsigned)pl.tile_cnt, (unsigned)pl.nsplit), dev::TC_THREADS, dev::TC_SMEM, s>>>(
-                c->tci, c->tc_tiles.as<dev::TcTile>() + pl.tile_off, c->tc_apack.as<float>(),
-                c->tc_bpack.as<float>(), n_orb, n, pl.nsplit, (long long)n * n_orb, out, conj,
-                c->err_flag.as<int>());
+        dev::gemm_tc<<<(unsigned)pl.grid, dev::TC_THREADS, dev::TC_SMEM, s>>>(
+            c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
+            c->tc_apack.as<float>(), c->tc_bpack.as<float>(), n_orb, n, pl.nsplit, (long long)n * n_orb, out, conj,
+            c->err_flag.as<int>());
         c->launches += 1;
         res.t = out;
         res.nsplit = pl.nsplit;
@@ -1368,11 +1362,6 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
         return ABC_OK;
     }
-    if (key == ABC_TUNE_TC_PERSIST) {
-        ctx->tc_persist = value != 0;
-        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
-        return ABC_OK;
-    }
     if (key == ABC_TUNE_STENCIL) {
         if (value < 0 || value > 2) return fail(ABC_ERR_ARG, "stencil placement must be 0, 1 or 2");
         ctx->stencil_mode = (int)value;
@@ -1389,7 +1378,6 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_PDL) { *value = ctx->pdl ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_CHAIN) { *value = ctx->chain ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL) { *value = ctx->stencil_mode; return ABC_OK; }
-    if (key == ABC_TUNE_TC_PERSIST) { *value = ctx->tc_persist ? 1 : 0; return ABC_OK; }
     return fail(ABC_ERR_ARG, "unknown tuning key");
 }
 

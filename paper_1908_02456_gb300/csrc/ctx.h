@@ -86,10 +86,9 @@ struct abc_ctx {
     abc::DevBuf tc_apack, tc_tiles, tc_cols, tc_bpack, tc_part;
     struct TcPlan {
         int tile_off = 0, tile_cnt = 0, cols_off = 0, cols_cnt = 0, max_nkb = 1, nsplit = 1;
-        int grid = 0, off_base = 0;     // persistent form: CTAs and their item offsets in tc_item_off
+        int grid = 0, off_base = 0;     // CTAs of the persistent GEMM and their item offsets in tc_item_off
     };
     abc::DevBuf tc_items, tc_item_off;
-    bool tc_persist = true;             // persistent tensor-core contraction (tuning)
     std::vector<TcPlan> tc_b;                    // launch plan of each orbital count b (index b)
     int tc_sms = 0;
     // launch accounting

@@ -4,27 +4,31 @@
 // Per irreducible class the contraction is T = S X: S the class's m x m complex
 // block, X the m x (R b) matrix of its R right-hand sides for b orbitals (adapted
 // vectors are orbital-major, so every column of X is contiguous in K).  With
-// S = Sr + i Si and X = Xr + i Xi the kernel accumulates four real products in
-// TMEM, P1 = Sr Xr, P2 = Si Xi, P3 = Si Xr, P4 = Sr Xi, and forms
-//   T = (P1 - P2) + i (P3 + P4)        (conj(S): (P1 + P2) + i (P4 - P3))
-// in the epilogue.  Each real product is 3xTF32: with a = a_hi + a_lo (a_hi the
-// operand rounded to TF32, a_lo the remainder as TF32), a b ~ a_hi b_hi + a_hi b_lo +
-// a_lo b_hi, so 12 MMAs (kind::tf32, M = 128, K = 8) per 8-deep K step.
+// S = Sr + i Si and X = Xr + i Xi, one accumulator of 2N columns holds
+// [Re T | Im T] for an output tile of N columns:
+//     [Re T | Im T] = Sr [Xr | Xi] + Si [-Xi | Xr]        (conj(S): + Si [Xi | -Xr])
+// so a K step is two real products of width 2N, each 3xTF32: with a = a_hi + a_lo
+// (a_hi the operand rounded to TF32, a_lo the remainder as TF32),
+// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, i.e. 6 MMAs (kind::tf32, M = 128, N = 2N, K = 8).
 //
 // Operand layout in shared memory: K-major, no swizzle, canonical 8-row x 16-byte
 // core matrices (row stride 16 B inside a core matrix, LBO = 128 B between core
 // matrices along K, SBO = 512 B between 8-row groups, 16-deep K blocks).  The host
 // pre-splits and pre-packs S in exactly that image (4 planes Sr_hi, Sr_lo, Si_hi,
-// Si_lo of 128 x 16 FP32 = 32 KB per (class, 128-row tile, K block)); pack_x_tc does
-// the same for X once per contraction (4 planes of N x 16 per (column range, K
-// block)).  gemm_tc computes one 128 x N output tile (N <= 128, a multiple of 16)
-// over one split of the K blocks: one thread streams both chunks of each K block
-// into a 3-stage ring with 1D bulk copies (mbarrier completion), one thread issues
-// the MMAs and frees each slot with tcgen05.commit, and the four accumulators take
-// 4N TMEM columns.  Split-K partials go to separate buffers that the back transform
-// adds in a fixed order.  Every mbarrier wait is bounded: on a timeout the kernel
-// raises the error flag, still waits (bounded) for its own copies and MMAs, frees
-// its TMEM and returns.
+// Si_lo of 128 x 16 FP32 = 32 KB per (class, 128-row tile, K block)); pack_x_tc packs
+// X once per contraction as 6 planes of N rows x 16 per (column range, K block):
+// (-Xi, Xr, Xi) for S and (Xr, Xi, -Xr) for conj(S), hi parts then lo parts, so both
+// width-2N operands of a product are windows of two adjacent planes.
+//
+// gemm_tc is persistent: one CTA per SM works through its own list of (output tile,
+// K split) items, balanced by the host.  Warp 0 streams the A and X chunks of all its
+// items through one 3-stage ring with 1D bulk copies (mbarrier completion), warp 1
+// issues the MMAs and frees each slot with tcgen05.commit, and warps 2-5 run the
+// epilogue; the accumulators of consecutive items alternate between two TMEM buffers,
+// so the epilogue of one item overlaps the MMAs of the next.  Split-K partials go to
+// separate buffers that the back transform adds in a fixed order.  Every mbarrier wait
+// is bounded: on a timeout the kernel raises the error flag, stops issuing, waits
+// (bounded) for its own copies and MMAs, frees its TMEM and returns.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -37,13 +41,14 @@ namespace dev {
 
 constexpr int TC_M = 128;
 constexpr int TC_KB = 16;                          // K elements per pipeline stage
-constexpr int TC_NMAX = 128;
+constexpr int TC_NMAX = 96;                        // output columns per tile (accumulator 2 TC_NMAX)
 constexpr int TC_STAGES = 3;
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 192;                    // producer, MMA issuer, four epilogue warps
 constexpr uint32_t TC_A_PLANE = TC_M * TC_KB * 4;  // 8 KB
 constexpr uint32_t TC_A_BYTES = 4 * TC_A_PLANE;    // 32 KB per (tile, K block)
+constexpr int TC_B_PLANES = 6;
 constexpr uint32_t TC_B_PLANE = TC_NMAX * TC_KB * 4;
-constexpr uint32_t TC_B_BYTES = 4 * TC_B_PLANE;    // 32 KB at N = 128
+constexpr uint32_t TC_B_BYTES = TC_B_PLANES * TC_B_PLANE;   // 36 KB at N = 96
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + 1024;
 constexpr int TC_MAX_SPLIT = 8;
 constexpr long long TC_WAIT_LIMIT = 1ll << 24;
@@ -121,11 +126,17 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// X -> packed TF32 planes (Xr_hi, Xr_lo, Xi_hi, Xi_lo) of every K block of a column
-// range, in the shared-memory image the GEMM copies with one bulk copy per K block.
-// Grid (column ranges, largest nkb), 128 threads; x orbital-major (o * ng + j).
+// One unit of a CTA's work list: an output tile over one K split.
+struct TcItem {
+    int tile, split;
+};
+
+// X -> packed TF32 planes of every K block of a column range, in the shared-memory
+// image the GEMM copies with one bulk copy per K block: hi planes (-Xi, Xr, Xi), then
+// lo planes in the same order (conj: (Xr, Xi, -Xr)).  Grid (column ranges, largest
+// nkb), 128 threads; x orbital-major (o * ng + j).
 static __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCols* __restrict__ cols, int n_orb,
-                                                        int ng, const float2* __restrict__ x,
+                                                        int ng, const float2* __restrict__ x, int conj,
                                                         float* __restrict__ bpack) {
     const TcCols cr = cols[blockIdx.x];
     const int c = cr.cls, kb = blockIdx.y;
@@ -145,169 +156,39 @@ static __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCol
             re[e] = v.x;
             im[e] = v.y;
         }
-        uint4 rh, rl, ih, il;
-        uint32_t* prh = &rh.x; uint32_t* prl = &rl.x; uint32_t* pih = &ih.x; uint32_t* pil = &il.x;
+        // planes 0-2 (hi) and 3-5 (lo) of this 16-byte row
+        uint4 pl[6];
+        uint32_t* w[6] = {&pl[0].x, &pl[1].x, &pl[2].x, &pl[3].x, &pl[4].x, &pl[5].x};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            prh[e] = tf32_hi(re[e]);
-            prl[e] = tf32_hi(re[e] - __uint_as_float(prh[e]));
-            pih[e] = tf32_hi(im[e]);
-            pil[e] = tf32_hi(im[e] - __uint_as_float(pih[e]));
+            const uint32_t rh = tf32_hi(re[e]), ih = tf32_hi(im[e]);
+            const uint32_t rl = tf32_hi(re[e] - __uint_as_float(rh)), il = tf32_hi(im[e] - __uint_as_float(ih));
+            const uint32_t sgn = 0x80000000u;
+            if (conj) {
+                w[0][e] = rh; w[1][e] = ih; w[2][e] = rh ^ sgn;
+                w[3][e] = rl; w[4][e] = il; w[5][e] = rl ^ sgn;
+            } else {
+                w[0][e] = ih ^ sgn; w[1][e] = rh; w[2][e] = ih;
+                w[3][e] = il ^ sgn; w[4][e] = rl; w[5][e] = il;
+            }
         }
         // planes of a chunk are N * 64 bytes apart (only the tile's N rows are stored)
-        const uint32_t off = tc_core_offset(cc, 4 * q), pl = (uint32_t)N * 64;
-        *reinterpret_cast<uint4*>(B + 0 * pl + off) = rh;
-        *reinterpret_cast<uint4*>(B + 1 * pl + off) = rl;
-        *reinterpret_cast<uint4*>(B + 2 * pl + off) = ih;
-        *reinterpret_cast<uint4*>(B + 3 * pl + off) = il;
+        const uint32_t off = tc_core_offset(cc, 4 * q), pb = (uint32_t)N * 64;
+#pragma unroll
+        for (int p = 0; p < 6; ++p) *reinterpret_cast<uint4*>(B + p * pb + off) = pl[p];
     }
 }
 
-// One 128 x N output tile over the K blocks of split blockIdx.y (of nsplit); writes
-// the split's partial product to out + split * split_stride (x, out orbital-major).
-// Thread 0 streams the A and X chunks into the ring, thread 32 issues the MMAs, and
-// all four warps run the epilogue.
+// One CTA per SM over the items item_off[blockIdx.x] .. item_off[blockIdx.x + 1] of
+// items[]; out + split * split_stride receives each item's (split's) partial product
+// (x, out orbital-major).
 static __global__ void __launch_bounds__(TC_THREADS, 1)
-gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const float* __restrict__ apack,
-        const float* __restrict__ bpack, int n_orb, int ng, int nsplit, long long split_stride,
-        float2* __restrict__ out, int conj, int* __restrict__ err) {
+gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict__ items,
+        const int* __restrict__ item_off, const float* __restrict__ apack, const float* __restrict__ bpack, int n_orb,
+        int ng, int nsplit, long long split_stride, float2* __restrict__ out, int conj, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char* sA = tc_smem;                                       // [stage][4 planes]
-    unsigned char* sB = tc_smem + (size_t)TC_STAGES * TC_A_BYTES;      // [stage][4 planes]
-    uint64_t* full = reinterpret_cast<uint64_t*>(tc_smem + (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES));
-    uint64_t* empty = full + TC_STAGES;
-    uint64_t* fin = empty + TC_STAGES;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(fin + 1);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const TcTile tile = tiles[blockIdx.x];
-    const int c = tile.cls, N = tile.n, m = info.m[c], nkb = info.nkb[c];
-    const int split = blockIdx.y;
-    const int kb0 = (int)((long long)nkb * split / nsplit), kb1 = (int)((long long)nkb * (split + 1) / nsplit);
-    const int nk = kb1 - kb0;
-    const int ncols = 4 * N <= 32 ? 32 : (4 * N <= 64 ? 64 : (4 * N <= 128 ? 128 : (4 * N <= 256 ? 256 : 512)));
-    const uint32_t b_bytes = (uint32_t)N * 256;
-    if (tid == 0) {
-        for (int i = 0; i < TC_STAGES; ++i) {
-            mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
-        }
-        mbar_init(fin, 1);
-        fence_mbar_init();
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(ncols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_holder;
-    const uint32_t idesc = tc_idesc(N);
-    const float* achunk = apack + (size_t)(info.abase[c] + (long long)(tile.row0 / TC_M) * nkb) * (TC_A_BYTES / 4);
-    const float* bchunk = bpack + (size_t)tile.bchunk0 * (TC_B_BYTES / 4);
-    bool ok = true;
-    if (tid == 0) {
-        // producer
-        for (int i = 0; i < nk; ++i) {
-            const int kb = kb0 + i, st = i % TC_STAGES;
-            if (i >= TC_STAGES) ok &= mbar_wait_bounded(&empty[st], (uint32_t)((i / TC_STAGES - 1) & 1));
-            mbar_expect_tx(&full[st], TC_A_BYTES + b_bytes);
-            bulk_g2s(sA + (size_t)st * TC_A_BYTES, achunk + (size_t)kb * (TC_A_BYTES / 4), TC_A_BYTES, &full[st]);
-            bulk_g2s(sB + (size_t)st * TC_B_BYTES, bchunk + (size_t)kb * (TC_B_BYTES / 4), b_bytes, &full[st]);
-        }
-    } else if (tid == 32) {
-        // MMA issuer: four accumulators P1 = Sr Xr, P2 = Si Xi, P3 = Si Xr, P4 = Sr Xi (3xTF32 each)
-        const uint32_t pb = (uint32_t)N * 64;                         // X plane stride in the chunk
-        for (int i = 0; i < nk; ++i) {
-            const int st = i % TC_STAGES;
-            ok &= mbar_wait_bounded(&full[st], (uint32_t)((i / TC_STAGES) & 1));
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(sA + (size_t)st * TC_A_BYTES), b0 = smem_u32(sB + (size_t)st * TC_B_BYTES);
-#pragma unroll
-            for (int ks = 0; ks < TC_KB / 8; ++ks) {
-                const uint32_t ko = ks * 256;          // two core matrices along K per MMA
-                const uint64_t srh = tc_desc(a0 + 0 * TC_A_PLANE + ko), srl = tc_desc(a0 + 1 * TC_A_PLANE + ko);
-                const uint64_t sih = tc_desc(a0 + 2 * TC_A_PLANE + ko), sil = tc_desc(a0 + 3 * TC_A_PLANE + ko);
-                const uint64_t xrh = tc_desc(b0 + 0 * pb + ko), xrl = tc_desc(b0 + 1 * pb + ko);
-                const uint64_t xih = tc_desc(b0 + 2 * pb + ko), xil = tc_desc(b0 + 3 * pb + ko);
-                const uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
-                const uint32_t d1 = tmem, d2 = tmem + N, d3 = tmem + 2 * N, d4 = tmem + 3 * N;
-                tc_mma(d1, srh, xrh, idesc, acc0); tc_mma(d1, srh, xrl, idesc, 1u); tc_mma(d1, srl, xrh, idesc, 1u);
-                tc_mma(d2, sih, xih, idesc, acc0); tc_mma(d2, sih, xil, idesc, 1u); tc_mma(d2, sil, xih, idesc, 1u);
-                tc_mma(d3, sih, xrh, idesc, acc0); tc_mma(d3, sih, xrl, idesc, 1u); tc_mma(d3, sil, xrh, idesc, 1u);
-                tc_mma(d4, srh, xih, idesc, acc0); tc_mma(d4, srh, xil, idesc, 1u); tc_mma(d4, srl, xih, idesc, 1u);
-            }
-            tc_commit(&empty[st]);                    // the slot is free once these MMAs are done
-        }
-        tc_commit(fin);
-    }
-    if (nk > 0) ok &= mbar_wait_bounded(fin, 0);
-    __syncwarp();                                      // the producer / issuer lanes rejoin their warps
-    tc_fence_after();
-    // epilogue: warp w reads TMEM lanes 32w .. 32w + 31 (rows of the tile)
-    const int row = tile.row0 + warp * 32 + lane;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    const float cs = conj ? -1.f : 1.f;
-    float2* dst = out + (size_t)split * split_stride;
-    for (int c0 = 0; c0 < N; c0 += 16) {
-        float p1[16], p2[16], p3[16], p4[16];
-        tc_ld16(lane_addr + c0, p1);
-        tc_ld16(lane_addr + N + c0, p2);
-        tc_ld16(lane_addr + 2 * N + c0, p3);
-        tc_ld16(lane_addr + 3 * N + c0, p4);
-        tc_wait_ld();
-        if (row < m) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int col = tile.col0 + c0 + i;
-                const int k = col / n_orb, o = col - k * n_orb;
-                if (c0 + i < N && k < info.R[c]) {
-                    const float2 v = nk > 0 ? make_float2(p1[i] - cs * p2[i], cs * p3[i] + p4[i]) : make_float2(0.f, 0.f);
-                    dst[(size_t)o * ng + info.moff[c][k] + row] = v;
-                }
-            }
-        }
-    }
-    // the producer's copies have all landed unless a wait gave up; wait (bounded) for the last ones
-    if (tid == 0)
-        for (int i = nk > TC_STAGES ? nk - TC_STAGES : 0; i < nk; ++i)
-            ok &= mbar_wait_bounded(&full[i % TC_STAGES], (uint32_t)((i / TC_STAGES) & 1));
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
-    }
-    if (!ok) atomicExch(err, 1);
-}
-
-// ---------------------------------------------------------------------------
-// Persistent form.  One CTA per SM works through its own list of (output tile, K
-// split) items (item_off[b] .. item_off[b + 1] of items[], balanced by the host);
-// warp 0 streams the A and X chunks of all its items through one ring, warp 1 issues
-// the MMAs, and warps 2-5 run the epilogue.  Each item accumulates its real and
-// imaginary parts directly,
-//     Re T = Sr Xr - Si Xi,   Im T = Si Xr + Sr Xi     (conj(S): + Si Xi, - Si Xr)
-// the minus sign taken by the instruction descriptor's negate-A bit, into one of two
-// TMEM buffers (2 x 128 columns each), so the epilogue of an item drains one buffer
-// while the MMAs of the next fill the other.
-constexpr int TCP_THREADS = 192;
-constexpr size_t TCP_SMEM = (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + 1024;
-
-struct TcItem {
-    int tile, split;
-};
-
-static __global__ void __launch_bounds__(TCP_THREADS, 1)
-gemm_tc_persist(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict__ items,
-                const int* __restrict__ item_off, const float* __restrict__ apack, const float* __restrict__ bpack,
-                int n_orb, int ng, int nsplit, long long split_stride, float2* __restrict__ out, int conj,
-                int* __restrict__ err) {
-    extern __shared__ __align__(1024) unsigned char tc_smem[];
-    unsigned char* sA = tc_smem;                                       // [stage][4 planes]
-    unsigned char* sB = tc_smem + (size_t)TC_STAGES * TC_A_BYTES;      // [stage][4 planes]
+    unsigned char* sB = tc_smem + (size_t)TC_STAGES * TC_A_BYTES;      // [stage][6 planes]
     uint64_t* full = reinterpret_cast<uint64_t*>(tc_smem + (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES));
     uint64_t* empty = full + TC_STAGES;
     uint64_t* tfull = empty + TC_STAGES;                               // [2] accumulators ready
@@ -350,7 +231,7 @@ gemm_tc_persist(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __r
             const float* achunk =
                 apack + (size_t)(info.abase[c] + (long long)(tile.row0 / TC_M) * nkb) * (TC_A_BYTES / 4);
             const float* bchunk = bpack + (size_t)tile.bchunk0 * (TC_B_BYTES / 4);
-            const uint32_t b_bytes = (uint32_t)N * 256;
+            const uint32_t b_bytes = (uint32_t)N * 64 * TC_B_PLANES;
             for (int kb = kb0; kb < kb1 && ok; ++kb, ++issued) {
                 const int st = (int)(issued % TC_STAGES);
                 if (issued >= TC_STAGES) ok &= mbar_wait_bounded(&empty[st], (uint32_t)((issued / TC_STAGES - 1) & 1));
@@ -372,11 +253,11 @@ gemm_tc_persist(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __r
             const int buf = q & 1;
             if (q >= 2) ok &= mbar_wait_bounded(&tempty[buf], (uint32_t)((q / 2 - 1) & 1));
             tc_fence_after();
-            const uint32_t idesc = tc_idesc(N), idesc_neg = idesc | (1u << 13);   // negate A
-            const uint32_t d_re = tmem + buf * 256, d_im = d_re + 128;
+            const uint32_t idesc = tc_idesc(2 * N);
+            const uint32_t d = tmem + buf * 256;                          // [Re | Im], 2N columns
             const uint32_t pb = (uint32_t)N * 64;                         // X plane stride in the chunk
-            // Re: Sr Xr -+ Si Xi; Im: +- Si Xr + Sr Xi (conj: the second sign)
-            const uint32_t id_sixi = conj ? idesc : idesc_neg, id_sixr = conj ? idesc_neg : idesc;
+            // windows of two planes: [Xr | Xi] and [-Xi | Xr] (conj: [Xr | Xi] and [Xi | -Xr])
+            const uint32_t wr = conj ? 0u : pb, wi = conj ? pb : 0u, lo = 3 * pb;
             for (int kb = kb0; kb < kb1 && ok; ++kb, ++g) {
                 const int st = (int)(g % TC_STAGES);
                 ok &= mbar_wait_bounded(&full[st], (uint32_t)((g / TC_STAGES) & 1));
@@ -384,16 +265,14 @@ gemm_tc_persist(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __r
                 const uint32_t a0 = smem_u32(sA + (size_t)st * TC_A_BYTES), b0 = smem_u32(sB + (size_t)st * TC_B_BYTES);
 #pragma unroll
                 for (int ks = 0; ks < TC_KB / 8; ++ks) {
-                    const uint32_t ko = ks * 256;
+                    const uint32_t ko = ks * 256;      // two core matrices along K per MMA
                     const uint64_t srh = tc_desc(a0 + 0 * TC_A_PLANE + ko), srl = tc_desc(a0 + 1 * TC_A_PLANE + ko);
                     const uint64_t sih = tc_desc(a0 + 2 * TC_A_PLANE + ko), sil = tc_desc(a0 + 3 * TC_A_PLANE + ko);
-                    const uint64_t xrh = tc_desc(b0 + 0 * pb + ko), xrl = tc_desc(b0 + 1 * pb + ko);
-                    const uint64_t xih = tc_desc(b0 + 2 * pb + ko), xil = tc_desc(b0 + 3 * pb + ko);
+                    const uint64_t brh = tc_desc(b0 + wr + ko), brl = tc_desc(b0 + lo + wr + ko);
+                    const uint64_t bih = tc_desc(b0 + wi + ko), bil = tc_desc(b0 + lo + wi + ko);
                     const uint32_t acc0 = (kb > kb0 || ks > 0) ? 1u : 0u;
-                    tc_mma(d_re, srh, xrh, idesc, acc0); tc_mma(d_re, srh, xrl, idesc, 1u); tc_mma(d_re, srl, xrh, idesc, 1u);
-                    tc_mma(d_re, sih, xih, id_sixi, 1u); tc_mma(d_re, sih, xil, id_sixi, 1u); tc_mma(d_re, sil, xih, id_sixi, 1u);
-                    tc_mma(d_im, sih, xrh, id_sixr, acc0); tc_mma(d_im, sih, xrl, id_sixr, 1u); tc_mma(d_im, sil, xrh, id_sixr, 1u);
-                    tc_mma(d_im, srh, xih, idesc, 1u); tc_mma(d_im, srh, xil, idesc, 1u); tc_mma(d_im, srl, xih, idesc, 1u);
+                    tc_mma(d, srh, brh, idesc, acc0); tc_mma(d, srh, brl, idesc, 1u); tc_mma(d, srl, brh, idesc, 1u);
+                    tc_mma(d, sih, bih, idesc, 1u); tc_mma(d, sih, bil, idesc, 1u); tc_mma(d, sil, bih, idesc, 1u);
                 }
                 tc_commit(&empty[st]);                // the slot is free once these MMAs are done
             }
@@ -426,7 +305,7 @@ gemm_tc_persist(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __r
                 float pr[16], pi[16];
                 if (any) {
                     tc_ld16(lane_base + buf * 256 + c0, pr);
-                    tc_ld16(lane_base + buf * 256 + 128 + c0, pi);
+                    tc_ld16(lane_base + buf * 256 + N + c0, pi);
                     tc_wait_ld();
                 }
                 if (row < m) {

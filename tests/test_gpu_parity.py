@@ -190,35 +190,6 @@ def test_tensor_core_contraction_many_tiles(torch_cuda, order, dims, b):
         assert rel(f, ref_f) < 1e-6
 
 
-@pytest.mark.parametrize("dims,b,order", [((22, 22, 22), 48, 1), ((10, 9, 11), 5, 1), ((12, 12, 12), 20, 0)])
-def test_persistent_tensor_core_matches_per_item_launch(torch_cuda, dims, b, order):
-    """ABC_TUNE_TC_PERSIST: the persistent tensor-core contraction (items balanced over
-    one CTA per SM, two accumulator buffers, real and imaginary parts accumulated
-    directly) gives the same steps as one CTA per item, to rounding; 22^3 x 48 puts
-    several items on each CTA."""
-    torch = torch_cuda
-    from paper_1908_02456_gb300 import abc
-    h, dt = 0.5, 0.01
-    rng = np.random.default_rng(90 + b)
-    V = inputs.smooth_random(dims, h, rng)
-    psi0 = inputs.random_state(dims, b, rng).reshape((b,) + tuple(dims[::-1]))
-    outs = []
-    for persist in (0, 1):
-        ctx = abc.Context(dims, h, order, 1.0, precision="tf32x3", max_orbitals=b)
-        ctx.set_tuning(abc.TUNE_TC_PERSIST, persist)
-        assert ctx.get_tuning(abc.TUNE_TC_PERSIST) == persist
-        psi = torch.from_numpy(psi0).to("cuda", ctx.complex_dtype).contiguous()
-        Vt = torch.from_numpy(V).to("cuda", ctx.real_dtype).contiguous()
-        aux = ctx.new_aux(b) if order == 1 else None
-        ctx.run(psi, aux, Vt, dt, 20)
-        torch.cuda.synchronize()
-        outs.append([psi.cpu().numpy().astype(np.complex128)] +
-                    ([aux.cpu().numpy().astype(np.complex128)] if order == 1 else []))
-        ctx.close()
-    for a, c in zip(outs[0], outs[1]):
-        assert np.linalg.norm(a - c) <= 1e-6 * np.linalg.norm(a)
-
-
 @pytest.mark.parametrize("prec", ["c64", "tf32x3"])
 def test_one_orbital_complex64_uses_packed_tiles(torch_cuda, prec):
     """One complex64 orbital runs the packed symmetric-tile contraction, not the
