@@ -565,17 +565,27 @@ int build_tc(abc_ctx* c) {
         pl.tile_cnt = (int)tiles.size() - pl.tile_off;
         pl.cols_cnt = (int)cranges.size() - pl.cols_off;
         pl.max_nkb = maxnkb;
-        // enough CTAs for about three per SM; partial sums of the splits are added later
-        pl.nsplit = std::max(1, std::min(TC_MAX_SPLIT, (3 * sms + pl.tile_cnt - 1) / pl.tile_cnt));
-        // persistent form: items (tile, split) in (class, row tile, split, column range)
-        // order, so the items that share an A chunk run at about the same time, each given
-        // to the CTA with the least work so far (cost: its K blocks plus two for the
-        // fill and the epilogue)
+        // about two items per SM; partial sums of the splits are added by the back transform
+        pl.nsplit = std::max(1, std::min(TC_MAX_SPLIT, (2 * sms + pl.tile_cnt - 1) / pl.tile_cnt));
+        // persistent GEMM: items (tile, split) longest first, each given to the CTA with the
+        // least work so far; cost = bytes streamed for the item (its K blocks of A and X,
+        // plus two K blocks' worth for the fill and the epilogue).  Items of equal cost
+        // stay in (class, row tile, split, column range) order, so the items that share an
+        // A chunk go to different CTAs at about the same time.
         {
             std::vector<TcItem> its;
+            std::vector<double> cost;
             for (int ti = pl.tile_off; ti < pl.tile_off + pl.tile_cnt; ++ti)
                 for (int sp = 0; sp < pl.nsplit; ++sp) its.push_back(TcItem{ti, sp});
+            auto item_cost = [&](const TcItem& w) {
+                const TcTile& x = tiles[w.tile];
+                const int nkb = info.nkb[x.cls];
+                const int nk = (int)((long long)nkb * (w.split + 1) / pl.nsplit - (long long)nkb * w.split / pl.nsplit);
+                return (nk + 2.0) * (TC_A_BYTES + (double)x.n * 64 * TC_B_PLANES);
+            };
             std::stable_sort(its.begin(), its.end(), [&](const TcItem& a, const TcItem& b2) {
+                const double ca = item_cost(a), cb = item_cost(b2);
+                if (ca != cb) return ca > cb;
                 const TcTile &x = tiles[a.tile], &y = tiles[b2.tile];
                 if (x.cls != y.cls) return x.cls < y.cls;
                 if (x.row0 != y.row0) return x.row0 < y.row0;
@@ -584,15 +594,13 @@ int build_tc(abc_ctx* c) {
             });
             const int G = std::min<int>(sms, (int)its.size());
             std::vector<std::vector<TcItem>> per(G);
-            std::vector<long long> load(G, 0);
+            std::vector<double> load(G, 0.0);
             for (const TcItem& w : its) {
-                const int nkb = info.nkb[tiles[w.tile].cls];
-                const int nk = (int)((long long)nkb * (w.split + 1) / pl.nsplit - (long long)nkb * w.split / pl.nsplit);
                 int best = 0;
                 for (int g2 = 1; g2 < G; ++g2)
                     if (load[g2] < load[best]) best = g2;
                 per[best].push_back(w);
-                load[best] += nk + 2;
+                load[best] += item_cost(w);
             }
             pl.grid = G;
             pl.off_base = (int)item_off.size();
