@@ -835,6 +835,9 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             dev::bnd_forward<T, 0, true><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
                                                              order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,
                                                              nullptr, (T)0, dev::Ord2Fwd<T>{});
+        else if (n_orb % dev::FO == 0)
+            dev::bnd_forward_multi<T><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
+                ct, n_orb, c->nvox, (const Vc*)w_phi, order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf);
         else
             dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
                                                        order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,

@@ -279,6 +279,60 @@ __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, lon
     }
 }
 
+// bnd_forward MODE 0 for many orbitals: a group of 64 threads transforms one cell for
+// FO consecutive orbitals (n_orb a multiple of FO), so the cell's tables and
+// coefficients are read once per FO orbitals and each thread has FO independent value
+// loads in flight.  Same arithmetic, order and outputs as bnd_forward<T, 0>.
+constexpr int FO = 4;
+template <typename T>
+__global__ void __launch_bounds__(128) bnd_forward_multi(CellTab<T> ct, int n_orb, long long nvox,
+                                                         const typename C2<T>::t* __restrict__ w_phi,
+                                                         const typename C2<T>::t* __restrict__ w_f,
+                                                         typename C2<T>::t* __restrict__ hat_phi,
+                                                         typename C2<T>::t* __restrict__ hat_f) {
+    typedef typename C2<T>::t V;
+    __shared__ V sp[2][FO][8][8], sf[2][FO][8][8];     // [group][orbital][slot][parity]
+    const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const int nch = n_orb / FO;
+    const long long gidx = (long long)blockIdx.x * 2 + grp;
+    const bool live = gidx < (long long)ct.n_cells * nch;
+    const int j0 = live ? (int)(gidx % nch) * FO : 0;
+    const int cell = live ? (int)(gidx / nch) : 0;
+    const int s = t >> 3, g = t & 7;
+    const int gi = live ? ct.gi[cell * 64 + t] : -1;
+    const int node = live ? ct.node[cell * 64 + t] : 0;
+    const int jj = live ? ct.out[cell * 64 + t] : -1;          // output o = s of parity p = g
+    const int ty = live ? ct.type[cell * 8 + g] : 0;
+    V xp[FO], xf[FO];
+#pragma unroll
+    for (int o = 0; o < FO; ++o) {
+        xp[o] = gi >= 0 ? w_phi[(long long)(j0 + o) * nvox + node] : mk<T>(0, 0);
+        xf[o] = (gi >= 0 && w_f) ? w_f[(long long)gi * n_orb + j0 + o] : mk<T>(0, 0);
+    }
+    T cf[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cf[q] = jj >= 0 ? ct.coef_f[(long long)ty * 64 + s * 8 + q] : (T)0;
+#pragma unroll
+    for (int o = 0; o < FO; ++o) {
+        sp[grp][o][s][g] = wht8_lanes(xp[o], g);
+        if (w_f) sf[grp][o][s][g] = wht8_lanes(xf[o], g);
+    }
+    __syncthreads();
+    if (jj < 0) return;
+#pragma unroll
+    for (int o = 0; o < FO; ++o) {
+        V ap = mk<T>(0, 0), af = mk<T>(0, 0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            ap.x += cf[q] * sp[grp][o][q][g].x; ap.y += cf[q] * sp[grp][o][q][g].y;
+            if (w_f) { af.x += cf[q] * sf[grp][o][q][g].x; af.y += cf[q] * sf[grp][o][q][g].y; }
+        }
+        const long long e = (long long)(j0 + o) * ct.ng + jj;
+        hat_phi[e] = ap;
+        if (w_f) hat_f[e] = af;
+    }
+}
+
 // t from the partial sums of the tiled contraction (see SymGather).  The loads of the
 // first two row segments and the first 24 column parts are all issued before any
 // of them is used (one memory round trip for the common case); the sums are then
