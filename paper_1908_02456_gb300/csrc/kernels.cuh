@@ -683,13 +683,43 @@ __device__ __forceinline__ void gemv_class_rows(const ClassInfo& ci, int c, int 
             }
         }
     }
+    // the warp's 2 GEMV_RB R partial sums, reduced by halving exchanges (a reduce-scatter
+    // over the lanes with the xor masks 16, 8, ... of warp_sum, so every total is the same
+    // pairwise tree): after the L = log2(NV) levels lane l holds slot l >> (5 - L), summed
+    // over the lanes that differ in the top L bits; the remaining masks finish it
+    constexpr int NV0 = 2 * GEMV_RB * R;
+    constexpr int NV = NV0 <= 8 ? 8 : NV0 <= 16 ? 16 : 32;
+    constexpr int L = NV == 8 ? 3 : NV == 16 ? 4 : 5;
+    T v[NV];
 #pragma unroll
     for (int r = 0; r < GEMV_RB; ++r)
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            const T re = warp_sum(sr[r][k]), im = warp_sum(si[r][k]);
-            if (lane == 0) red[w][r][k] = mk<T>(re, im);
+            v[2 * (r * R + k)] = sr[r][k];
+            v[2 * (r * R + k) + 1] = si[r][k];
         }
+#pragma unroll
+    for (int i = NV0; i < NV; ++i) v[i] = 0;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const int half = NV >> (l + 1), m = 16 >> l;
+        const bool up = lane & m;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const T keep = up ? v[i + half] : v[i], send = up ? v[i] : v[i + half];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+#pragma unroll
+    for (int m = 16 >> L; m; m >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
+    {
+        const int slot = lane >> (5 - L);
+        if ((lane & ((1 << (5 - L)) - 1)) == 0 && slot < NV0) {
+            const int rk = slot >> 1;
+            T* dst = reinterpret_cast<T*>(&red[w][rk / R][rk % R]);
+            dst[slot & 1] = v[0];
+        }
+    }
     __syncthreads();
     if (threadIdx.x < GEMV_RB * R) {
         const int r = threadIdx.x / R, k = threadIdx.x % R;
