@@ -288,15 +288,16 @@ int build_sym(abc_ctx* c) {
     int st;
     if ((st = c->sym_tiles.alloc(host.size() * sizeof(float)))) return st;
     CUDA_TRY(cudaMemcpy(c->sym_tiles.p, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice));
-    // Work units: tile rows of a class (row I has I + 1 tiles), split into pieces of at
-    // most `cap` tiles.  Each piece is one segment: its row part stays in registers and
-    // is stored once at its end.  The pieces are bin-packed over the CTAs longest first
-    // (LPT); a CTA takes any set of segments.  Costs are a model fitted to per-CTA
-    // timings of this kernel on GB300 (us): 1.0 per segment, and per tile 0.36 / 0.59 /
-    // 0.87 off the diagonal and 0.0 / 0.29 / 0.41 on it for R = 1 / 2 / 3 right-hand
-    // sides.  The cap with the smallest predicted makespan is kept.  Segments are
-    // numbered by (class, row, first tile), so the segments of one row are consecutive
-    // (the back transform's gather relies on it).
+    // Work units: tile rows of a class (row I has I + 1 tiles), split into segments (runs
+    // of tiles of one row); a segment's row part stays in registers and is stored once at
+    // its end.  Costs are a model fitted to per-CTA timings of this kernel on GB300 (us):
+    // 1.0 per segment, and per tile 0.36 / 0.59 / 0.87 off the diagonal and 0.0 / 0.29 /
+    // 0.41 on it for R = 1 / 2 / 3 right-hand sides.  Two kinds of partition are built
+    // and the one with the smallest predicted makespan is kept: contiguous runs of tiles
+    // cut at the per-CTA cost target (`contiguous`), and pieces of at most `cap` tiles
+    // bin-packed over the CTAs longest first (`lpt`, a CTA takes any set of segments).
+    // Segments are numbered by (class, row, first tile), so the segments of one row are
+    // consecutive (the back transform's gather relies on it).
     int sms = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     const int G = std::max(1, sms);
@@ -338,10 +339,10 @@ int build_sym(abc_ctx* c) {
         }
         return *std::max_element(load.begin(), load.end());
     };
-    // Alternative: contiguous runs of tiles in (class, row, tile) order, cut where the
-    // running cost (tiles plus one segment cost at every row start and at every cut)
-    // reaches the next multiple of the total / G; a CTA's run is split at row ends
-    // into its segments.
+    // Contiguous runs of tiles in (class, row, tile) order: a CTA takes tiles while its
+    // cost (tiles plus one segment cost at every row start and at every cut) stays within
+    // half a tile of the target (total + G segment costs) / G; its run is split at row
+    // ends into its segments.
     auto contiguous = [&](std::vector<Piece>& out, std::vector<int>& own) {
         struct T1 { int k, I, t; double c; };
         std::vector<T1> tl;
