@@ -190,6 +190,22 @@ def test_tensor_core_contraction_many_tiles(torch_cuda, order, dims, b):
         assert rel(f, ref_f) < 1e-6
 
 
+def test_tensor_core_several_items_per_cta(torch_cuda):
+    """At 48^3 x 32 orbitals the persistent tensor-core contraction has about two
+    (tile, split) items per SM, so many CTAs work through three, reusing each TMEM
+    accumulator buffer after its epilogue drained it.  Three steps of the 3xTF32 path
+    against the FP64 path on the same inputs (the FP64 path is the one the small-box
+    tests hold to the oracle at 1e-10)."""
+    dims, h, dt, b = (48, 48, 48), 0.4, 0.005, 32
+    rng = np.random.default_rng(404)
+    psi0 = inputs.random_state(dims, b, rng).reshape(b, -1)
+    V = inputs.smooth_random(dims, h, rng)
+    p64, f64, _ = gpu_run(torch_cuda, dims, h, 1, 1.0, "fp64", psi0, V, dt, 3)
+    ptc, ftc, _ = gpu_run(torch_cuda, dims, h, 1, 1.0, "tf32x3", psi0, V, dt, 3)
+    assert rel(ptc, p64) < 1e-6
+    assert rel(ftc, f64) < 1e-5
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("c64", 1e-5), ("tf32x3", 1e-6)])
 @pytest.mark.parametrize("order,dims,b", [(1, (13, 11, 12), 8), (0, (10, 9, 11), 4)])
 def test_multi_orbital_forward_transform(torch_cuda, prec, tol, order, dims, b):
