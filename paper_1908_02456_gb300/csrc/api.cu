@@ -778,7 +778,16 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             dev::stencil_stage<T, 3><<<stencil_grid(c, n_orb), 256, 0, ss>>>(
                 g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)w_phi, (const Vc*)y_phi, V, bt,
                 (Vc*)o_phi, cdt);
-        else if (sizeof(T) == 4 && (g.nx & 1) == 0) {       // complex64, even rows: two nodes per thread
+        else if (sizeof(T) == 4 && (g.nx & 1) == 0 && n_orb == 1) {
+            // one orbital: also two planes per thread (half the blocks beside the back
+            // transform, which runs at the same time)
+            dim3 gp = stencil_grid(c, n_orb);
+            gp.x = (unsigned)(((g.nx / 2) * g.ny + 255) / 256);
+            gp.y = (gp.y + 1) / 2;
+            dev::stencil_stage_x2z2<<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, (float)(1.0 / (g.h * g.h)),
+                                                        (const float2*)w_phi, (const float2*)y_phi, (const float*)V,
+                                                        (const float2*)bt, (float2*)o_phi, (float)cdt);
+        } else if (sizeof(T) == 4 && (g.nx & 1) == 0) {       // complex64, even rows: two nodes per thread
             dim3 gp = stencil_grid(c, n_orb);
             gp.x = (unsigned)(((g.nx / 2) * g.ny + 255) / 256);
             dev::stencil_stage_x2<<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, (float)(1.0 / (g.h * g.h)),

@@ -956,6 +956,76 @@ static __global__ void stencil_stage_x2(int nx, int ny, int nz, int n_orb, float
         make_float4(yv.x + cdt * hi[0], yv.y - cdt * hr[0], yv.z + cdt * hi[1], yv.w - cdt * hr[1]);
 }
 
+// stencil_stage_x2 for two planes per thread as well (grid y = plane pairs): the pair's
+// column at k - 1 .. k + 2 serves both planes.
+static __global__ void stencil_stage_x2z2(int nx, int ny, int nz, int n_orb, float inv_h2,
+                                          const float2* __restrict__ w, const float2* y,
+                                          const float* __restrict__ V, const float2* __restrict__ bterm, float2* out,
+                                          float cdt) {
+    const long long nxy = (long long)nx * ny, nvox = nxy * nz;
+    const int tp2 = blockIdx.x * blockDim.x + threadIdx.x;         // pair in the z-plane
+    if (tp2 >= (nx >> 1) * ny) return;
+    const int jy = tp2 / (nx >> 1), i = 2 * (tp2 - jy * (nx >> 1)), k0 = 2 * blockIdx.y, orb = blockIdx.z;
+    const long long n0 = (long long)k0 * nxy + (long long)jy * nx + i;
+    const float2* wo = w + (long long)orb * nvox;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool two = k0 + 1 < nz;
+    // column k0 - 1 .. k0 + 2 of the pair
+    float4 col[4];
+    col[0] = k0 >= 1 ? *reinterpret_cast<const float4*>(wo + n0 - nxy) : zero;
+    col[1] = *reinterpret_cast<const float4*>(wo + n0);
+    col[2] = two ? *reinterpret_cast<const float4*>(wo + n0 + nxy) : zero;
+    col[3] = k0 + 2 < nz ? *reinterpret_cast<const float4*>(wo + n0 + 2 * nxy) : zero;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (q == 1 && !two) break;
+        const int k = k0 + q;
+        const long long n = n0 + q * nxy;
+        const float4 c = col[q + 1], zm = col[q], zp = col[q + 2];
+        const float2 xm = i >= 1 ? wo[n - 1] : make_float2(0.f, 0.f);
+        const float2 xp = i + 2 < nx ? wo[n + 2] : make_float2(0.f, 0.f);
+        const float4 ym = jy >= 1 ? *reinterpret_cast<const float4*>(wo + n - nx) : zero;
+        const float4 yp = jy + 1 < ny ? *reinterpret_cast<const float4*>(wo + n + nx) : zero;
+        const float2 vv = *reinterpret_cast<const float2*>(V + n);
+        const long long idx = (long long)orb * nvox + n;
+        const float4 yv = *reinterpret_cast<const float4*>(y + idx);
+        float hr[2], hi[2];
+        {
+            float sr = 0.f, si = 0.f;
+            sr += xm.x; si += xm.y;
+            sr += c.z; si += c.w;
+            sr += ym.x; si += ym.y;
+            sr += yp.x; si += yp.y;
+            sr += zm.x; si += zm.y;
+            sr += zp.x; si += zp.y;
+            const float dg = 3.f * inv_h2 + vv.x;
+            hr[0] = dg * c.x - 0.5f * inv_h2 * sr;
+            hi[0] = dg * c.y - 0.5f * inv_h2 * si;
+        }
+        {
+            float sr = 0.f, si = 0.f;
+            sr += c.x; si += c.y;
+            sr += xp.x; si += xp.y;
+            sr += ym.z; si += ym.w;
+            sr += yp.z; si += yp.w;
+            sr += zm.z; si += zm.w;
+            sr += zp.z; si += zp.w;
+            const float dg = 3.f * inv_h2 + vv.y;
+            hr[1] = dg * c.z - 0.5f * inv_h2 * sr;
+            hi[1] = dg * c.w - 0.5f * inv_h2 * si;
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+            if (on_gamma<1>(i + e, jy, k, nx, ny, nz)) {
+                const float2 b = bterm[(long long)gamma_index<1>(i + e, jy, k, nx, ny, nz) * n_orb + orb];
+                hr[e] += b.x;
+                hi[e] += b.y;
+            }
+        *reinterpret_cast<float4*>(out + idx) =
+            make_float4(yv.x + cdt * hi[0], yv.y - cdt * hr[0], yv.z + cdt * hi[1], yv.w - cdt * hr[1]);
+    }
+}
+
 // --------------------------------------------------------------------------
 // Mean field: V = V_ext + a rho + b rho^(1+alpha), rho = sum_j |phi_j|^2
 // --------------------------------------------------------------------------
