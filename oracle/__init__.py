@@ -21,8 +21,9 @@ order, in float64 / complex128:
                      ABC matrices.
 * ``propagate``   -- the reduced dynamics eq:dynamics0 / eq:dynamics1, the
                      degree-4 Taylor propagator (eq:21 with its signs read as
-                     sum_k (dt L)^k / k!), the density-dependent mean field and the
-                     norm / Lyapunov / energy diagnostics.
+                     sum_k (dt L)^k / k!), the density-dependent mean field, its
+                     energy functional (whose rho-derivative is the potential) and
+                     the norm / Lyapunov / energy diagnostics.
 * ``adjoint``     -- reverse-mode gradient of the absorbed probability with
                      respect to the potential, written from the same Taylor form.
 

@@ -19,7 +19,12 @@ signs of its cubic and quartic terms are garbled) term by term.
 
 Mean field (Sec. 4.3, eq:ham_tdhf, in the simplified density-dependent form
 V = V_ext + a rho + b rho^(1+alpha), rho = sum_j |phi_j|^2): V is computed from the
-state at the start of each step and held fixed within the step.
+state at the start of each step and held fixed within the step.  The energy that the
+exact mean-field dynamics conserves (with a closed box) is the functional whose
+derivative with respect to rho is V (Sec. 4.3 reports the energy released):
+
+  E[phi] = h^d sum_j Re <phi_j, H_kin phi_j>
+         + h^d sum_x [ V_ext rho + (a/2) rho^2 + b/(2+alpha) rho^(2+alpha) ].
 """
 from __future__ import annotations
 
@@ -46,11 +51,33 @@ class System:
         return np.sum(np.abs(phi) ** 2, axis=0)
 
     def potential(self, phi):
+        """V = V_ext + a rho + b rho^(1+alpha) (mean field), else V_ext."""
         if self.meanfield is None:
             return self.V_ext
         a, b, alpha = self.meanfield
         rho = self.density(phi)
         return self.V_ext + a * rho + b * np.power(rho, 1.0 + alpha)
+
+    def energy_potential(self, phi):
+        """V_ext + e(rho) with e(rho) = (a/2) rho + b/(2+alpha) rho^(1+alpha), the
+        interaction energy per unit density: h^d sum_x rho e(rho) is the interaction
+        term of E[phi].  Without a mean field this is V_ext."""
+        if self.meanfield is None:
+            return self.V_ext
+        a, b, alpha = self.meanfield
+        rho = self.density(phi)
+        return self.V_ext + 0.5 * a * rho + b / (2.0 + alpha) * np.power(rho, 1.0 + alpha)
+
+    def energy_functional(self, phi):
+        """E[phi] = h^d sum_j Re<phi_j, H_kin phi_j> + h^d sum_x [V_ext rho + (a/2) rho^2
+        + b/(2+alpha) rho^(2+alpha)] (no mean field: the last two terms are absent)."""
+        kin = self.w * np.real(np.sum(phi.conj() * (self.Hk @ phi.T).T))
+        rho = self.density(phi)
+        pot = self.w * np.sum(self.V_ext * rho)
+        if self.meanfield is not None:
+            a, b, alpha = self.meanfield
+            pot += self.w * np.sum(0.5 * a * rho ** 2 + b / (2.0 + alpha) * np.power(rho, 2.0 + alpha))
+        return kin + pot
 
     # ---- operators ----------------------------------------------------
     def H(self, phi, V):
@@ -139,9 +166,11 @@ class System:
 
         norm = h^d |phi_j|^2; W = norm + h^d f_j^* Q f_j (eq:lyapunov1; = norm for
         order 0 / no ABC, eq:lyapunov0, and for order 2, which has no proven
-        Lyapunov functional); energy = h^d Re <phi_j, H_{I,I}[V] phi_j> with V
-        the potential of the current state."""
-        V = self.potential(phi)
+        Lyapunov functional); energy = h^d Re <phi_j, (H_kin + V_ext + e(rho)) phi_j>
+        with e the interaction energy per unit density (``energy_potential``), so
+        that the orbitals' energies sum to E[phi] (``energy_functional``); without a
+        mean field it is h^d Re <phi_j, H_{I,I} phi_j>."""
+        V = self.energy_potential(phi)
         norm = self.w * np.sum(np.abs(phi) ** 2, axis=1)
         W = norm.copy()
         if self.order == 1:

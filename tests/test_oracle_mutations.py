@@ -71,3 +71,66 @@ def test_dropped_boundary_forcing_is_caught(monkeypatch):
     _, _, d = System(box, coeffs=order1(box, 1.0)).run(psi, 0.01, 100, diag_every=1)
     W = np.concatenate([[1.0], d[:, 0, 1]])
     assert not np.all(W[1:] <= W[:-1] * (1 + 1e-12))              # Lyapunov pin fails
+
+
+# ---------------------------------------------------------------------------
+# mean-field potential and energy functional (Sec. 4.3)
+# ---------------------------------------------------------------------------
+from meanfield_pins import energy_drift_ok, energy_scaling_ok, potential_scaling_ok  # noqa: E402
+
+
+class _PowerAlpha(System):
+    def potential(self, phi):                          # rho^alpha for rho^(1+alpha)
+        a, b, al = self.meanfield
+        rho = self.density(phi)
+        return self.V_ext + a * rho + b * np.power(rho, al)
+
+
+class _OneOrbitalDensity(System):
+    def density(self, phi):                            # orbital sum dropped
+        return np.abs(phi[0]) ** 2
+
+
+class _WeightedDensityPotential(System):
+    def potential(self, phi):                          # stray h^3 weight
+        a, b, al = self.meanfield
+        rho = self.w * self.density(phi)
+        return self.V_ext + a * rho + b * np.power(rho, 1.0 + al)
+
+
+class _EnergyFullA(System):
+    def energy_functional(self, phi):                  # a rho^2 for (a/2) rho^2
+        a, b, al = self.meanfield if self.meanfield else (0.0, 0.0, 0.0)
+        rho = self.density(phi)
+        kin = self.w * np.real(np.sum(phi.conj() * (self.Hk @ phi.T).T))
+        return kin + self.w * np.sum(self.V_ext * rho + a * rho ** 2 + b / (2 + al) * rho ** (2 + al))
+
+
+class _EnergyWrongB(System):
+    def energy_functional(self, phi):                  # b/(1+alpha) for b/(2+alpha)
+        a, b, al = self.meanfield if self.meanfield else (0.0, 0.0, 0.0)
+        rho = self.density(phi)
+        kin = self.w * np.real(np.sum(phi.conj() * (self.Hk @ phi.T).T))
+        return kin + self.w * np.sum(self.V_ext * rho + 0.5 * a * rho ** 2 + b / (1 + al) * rho ** (2 + al))
+
+
+class _EnergyPowerOnePlusAlpha(System):
+    def energy_functional(self, phi):                  # rho^(1+alpha) in the energy
+        a, b, al = self.meanfield if self.meanfield else (0.0, 0.0, 0.0)
+        rho = self.density(phi)
+        kin = self.w * np.real(np.sum(phi.conj() * (self.Hk @ phi.T).T))
+        return kin + self.w * np.sum(self.V_ext * rho + 0.5 * a * rho ** 2 + b / (2 + al) * rho ** (1 + al))
+
+
+def test_meanfield_potential_mistakes_are_caught():
+    for bad in (_PowerAlpha, _OneOrbitalDensity, _WeightedDensityPotential):
+        assert not energy_drift_ok(bad), bad.__name__
+    assert not potential_scaling_ok(_PowerAlpha)
+    assert not potential_scaling_ok(_OneOrbitalDensity)
+    assert not potential_scaling_ok(_WeightedDensityPotential)
+
+
+def test_meanfield_energy_mistakes_are_caught():
+    for bad in (_EnergyFullA, _EnergyWrongB, _EnergyPowerOnePlusAlpha):
+        assert not energy_drift_ok(bad), bad.__name__
+    assert not energy_scaling_ok(_EnergyPowerOnePlusAlpha)

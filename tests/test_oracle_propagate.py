@@ -176,3 +176,65 @@ def test_meanfield_keeps_orbitals_orthonormal():
     zero = System(box, meanfield=(0.0, 0.0, 1.0 / 6.0))
     p3, _, _ = zero.run(psi, 0.005, 40)
     assert np.array_equal(p3, p2)
+
+
+# ---------------------------------------------------------------------------
+# mean-field potential and energy functional (Sec. 4.3)
+# ---------------------------------------------------------------------------
+from meanfield_pins import (MF_STRONG, energy_drift, energy_drift_ok, energy_scaling_ok,  # noqa: E402
+                            potential_scaling_ok, small_case)
+
+
+def test_meanfield_energy_conserved_to_first_order():
+    """Zero Dirichlet faces: the exact dynamics conserves E[phi]; the stepper (V held at
+    the step's start density) changes it by O(dt) over a fixed time, so the change halves
+    with dt and its extrapolation to dt -> 0 vanishes."""
+    d1, d2 = energy_drift(System)
+    assert 1.9 < d1 / d2 < 2.1
+    assert abs(2 * d2 - d1) < 0.02 * abs(d1)
+    assert energy_drift_ok(System)
+
+
+def test_meanfield_potential_scaling():
+    assert potential_scaling_ok(System)
+
+
+def test_meanfield_energy_scaling():
+    assert energy_scaling_ok(System)
+
+
+def test_kinetic_energy_of_a_dst_mode():
+    """A product of sines sin(pi k_a (i_a+1)/(N_a+1)) is an eigenvector of the Dirichlet
+    kinetic operator with eigenvalue sum_a (1 - cos(pi k_a/(N_a+1)))/h^2; h^3-normalised,
+    its energy is that eigenvalue (no potential, no mean field)."""
+    dims, h = (7, 6, 9), 0.45
+    box = Box(dims, h)
+    kk = (2, 3, 1)
+    axes = [np.sin(np.pi * k * np.arange(1, N + 1) / (N + 1)) for k, N in zip(kk, dims)]
+    phi = np.einsum("k,j,i->kji", axes[2], axes[1], axes[0]).reshape(1, -1).astype(np.complex128)
+    phi *= np.exp(0.7j) / np.sqrt(h ** 3 * np.sum(np.abs(phi) ** 2))
+    lam = sum((1 - np.cos(np.pi * k / (N + 1))) / h ** 2 for k, N in zip(kk, dims))
+    sy = System(box)
+    assert abs(sy.energy_functional(phi) - lam) < 1e-12 * lam
+    assert abs(sy.diagnostics(phi, None)[0, 2] - lam) < 1e-12 * lam
+
+
+def test_linear_energy_conserved_within_truncation():
+    """Zero Dirichlet, static V >= 0: each DST component's weight changes per step by
+    |P(i theta)|^2 = 1 - theta^6/72 + O(theta^8), so the energy changes per step by at most
+    that factor of the largest theta times the energy."""
+    box, phi0 = _packet_case()
+    V = np.linspace(0.0, 0.5, box.n)
+    sy = System(box, V_ext=V)
+    dt = 0.01
+    _, _, d = sy.run(phi0, dt, 40, diag_every=1)
+    lam = 3 * 2 / box.h ** 2 + 0.5
+    e = np.concatenate([[sy.diagnostics(phi0, None)[0, 2]], d[:, 0, 2]])
+    assert np.all(np.abs(np.diff(e)) <= (dt * lam) ** 6 / 72 * 1.5 * np.abs(e[:-1]) + 1e-15)
+
+
+def test_energy_column_sums_to_functional():
+    box, psi = small_case()
+    sy = System(box, V_ext=np.linspace(-0.2, 0.2, box.n), meanfield=MF_STRONG)
+    assert abs(sy.diagnostics(psi, None)[:, 2].sum() - sy.energy_functional(psi)) < 1e-12 * abs(
+        sy.energy_functional(psi))
