@@ -179,9 +179,14 @@ int abc_aux_init(abc_ctx* ctx, const void* psi, void* aux, int n_orb, void* stre
 
 /* Per-orbital diagnostics of the current state into host out[n_orb][3]:
  * norm_j = h^3 |phi_j|^2; W_j = norm_j + h^3 f_j^* Q f_j (eq:lyapunov1; = norm_j
- * for order 0, eq:lyapunov0); energy_j = h^3 Re <phi_j, H_{I,I}[V] phi_j>.
- * All sums in FP64.  mf as in abc_run (V_ext + mean field of the given state).
- * Synchronises the stream. */
+ * for order 0, eq:lyapunov0); energy_j = h^3 Re <phi_j, H_{I,I}[V] phi_j> for a
+ * static potential.  With a mean field (mf as in abc_run) energy_j =
+ * h^3 Re <phi_j, (H_kin + V_ext + e(rho)) phi_j> with e(rho) = (a/2) rho +
+ * b/(2+alpha) rho^(1+alpha), the interaction energy per unit density, so that
+ * sum_j energy_j = E[phi] = h^3 sum_j Re <phi_j, H_kin phi_j> + h^3 sum_x [V_ext rho
+ * + (a/2) rho^2 + b/(2+alpha) rho^(2+alpha)], the energy the mean-field dynamics
+ * conserves in a closed box (its rho-derivative is the potential; Sec. 4.3 reports
+ * the energy a run releases).  All sums in FP64.  Synchronises the stream. */
 int abc_diagnostics(abc_ctx* ctx, const void* psi, const void* aux, const void* V, int n_orb,
                     const abc_meanfield* mf, double* out, void* stream);
 
@@ -208,8 +213,11 @@ int abc_host_matrices(const abc_grid* grid, const abc_params* params, int which,
  * every launch of the dominant kernel `kernel` (ABC_KERNEL_*) with CUDA events on
  * the launching stream; abc_profile_read returns the summed milliseconds and the
  * launch count since the last enable, after synchronising. */
-#define ABC_KERNEL_CONTRACTION 0   /* boundary DtN contraction (GEMV / GEMM)        */
+#define ABC_KERNEL_CONTRACTION 0   /* boundary DtN contraction (GEMV / GEMM; for the
+                                      tensor-core forms the GEMM alone)              */
 #define ABC_KERNEL_STENCIL 1       /* fused stencil + potential + Horner stage       */
+#define ABC_KERNEL_PACK 2          /* tensor-core forms: packing of the right-hand
+                                      sides into the GEMM's operand image            */
 int abc_profile_enable(abc_ctx* ctx, int enable);
 int abc_profile_read(abc_ctx* ctx, int kernel, double* ms, long long* launches);
 /* Per-launch durations (milliseconds, launch order) of the same record: writes
@@ -218,9 +226,19 @@ int abc_profile_read(abc_ctx* ctx, int kernel, double* ms, long long* launches);
 int abc_profile_durations(abc_ctx* ctx, int kernel, float* ms_out, long long max_out, long long* launches);
 
 /* Algorithmic bytes of one launch of a kernel for n_orb orbitals (the roofline
- * numerator): boundary matrix bytes + vectors for the contraction; for the stencil
- * 3 complex values per point and orbital plus V per point. */
+ * numerator): boundary matrix bytes + vectors for the contraction (for the
+ * tensor-core GEMM: its split operand planes of every class block once, the packed
+ * right-hand sides and the partial outputs); for the stencil 3 complex values per
+ * point and orbital plus V per point. */
 int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, double* bytes);
+
+/* Floating-point operations of one contraction launch for n_orb orbitals (kernel
+ * must be ABC_KERNEL_CONTRACTION): useful = 8 real flops per complex multiply-add of
+ * the class blocks with their right-hand sides, sum_k nseg R_k m_k^2 n_orb of them;
+ * issued = what the arithmetic performs: 3 x useful on the tensor-core split forms
+ * (three products per term), useful otherwise.  The paper has no counterpart
+ * (measurement support). */
+int abc_kernel_flops(const abc_ctx* ctx, int kernel, int n_orb, double* useful, double* issued);
 
 /* abc_step without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc while they step the

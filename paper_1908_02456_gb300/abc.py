@@ -17,7 +17,7 @@ OK = 0
 FP64, C64_FP32, C64_SPLIT_BF16, C64_3XTF32 = 0, 1, 2, 3
 MAT_K, MAT_M, MAT_A, MAT_B, MAT_Q = 0, 1, 2, 3, 4
 MAT_B1, MAT_B0, MAT_A1, MAT_A0 = 5, 6, 7, 8
-KERNEL_CONTRACTION, KERNEL_STENCIL = 0, 1
+KERNEL_CONTRACTION, KERNEL_STENCIL, KERNEL_PACK = 0, 1, 2
 TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT, TUNE_PDL, TUNE_CHAIN, TUNE_STENCIL = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16, "tf32x3": C64_3XTF32}
 FIT1_LIMIT, FIT1_TWO_POINT, FIT1_HERMITE = 0, 1, 2
@@ -75,6 +75,8 @@ def load():
         "abc_profile_read": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
         "abc_profile_durations": [_P, ctypes.c_int, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)],
         "abc_kernel_bytes": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+        "abc_kernel_flops": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double)],
         "abc_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
         "abc_step_noalloc": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P],
         "abc_set_tuning": [_P, ctypes.c_int, ctypes.c_longlong],
@@ -218,6 +220,13 @@ def abc_kernel_bytes(ctx, kernel: int, n_orb: int) -> float:
     b = ctypes.c_double()
     _check(load().abc_kernel_bytes(ctx, kernel, n_orb, ctypes.byref(b)))
     return b.value
+
+
+def abc_kernel_flops(ctx, kernel: int, n_orb: int):
+    """(useful, issued) flops of one contraction launch."""
+    u, i = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().abc_kernel_flops(ctx, kernel, n_orb, ctypes.byref(u), ctypes.byref(i)))
+    return u.value, i.value
 
 
 def abc_set_tuning(ctx, key: int, value: int):
@@ -365,6 +374,9 @@ class Context:
 
     def kernel_bytes(self, kernel, n_orb):
         return abc_kernel_bytes(self.ctx, kernel, n_orb)
+
+    def kernel_flops(self, kernel, n_orb):
+        return abc_kernel_flops(self.ctx, kernel, n_orb)
 
     def set_tuning(self, key, value):
         abc_set_tuning(self.ctx, key, value)

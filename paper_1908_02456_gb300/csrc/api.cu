@@ -684,7 +684,8 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
     const int n = c->geo.n_gamma;
     TRes res;
     res.t = t;
-    prof_begin(c, ABC_KERNEL_CONTRACTION, s);
+    const bool tc_path = n_orb > 1 && sizeof(T) == 4 && c->tc;
+    if (!tc_path) prof_begin(c, ABC_KERNEL_CONTRACTION, s);
     if (n_orb == 1 && sizeof(T) == 4 && c->sym) {
         // early start behind the forward transform, except when the launch is timed by
         // an event pair (profiling), which must bracket the kernel alone
@@ -696,11 +697,15 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
     } else if (n_orb == 1) {
         dev::gemv_classes<T><<<c->ci.rowbase[c->ci.n], 32 * dev::GEMV_WARPS, 0, s>>>(c->ci, c->mat.as<V>(), xs,
                                                                                   (V*)t, conj);
-    } else if (sizeof(T) == 4 && c->tc) {
+    } else if (tc_path) {
         const abc_ctx::TcPlan& pl = c->tc_b[n_orb];
+        // the operand packing has its own timing slot, so the contraction slot times the GEMM alone
+        prof_begin(c, ABC_KERNEL_PACK, s);
         dev::pack_x_tc<<<dim3((unsigned)pl.cols_cnt, (unsigned)pl.max_nkb), 128, 0, s>>>(
             c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off, n_orb, n, (const float2*)x, conj,
             c->tc_bpack.as<float>());
+        prof_end(c, ABC_KERNEL_PACK, s);
+        prof_begin(c, ABC_KERNEL_CONTRACTION, s);
         float2* out = pl.nsplit > 1 ? c->tc_part.as<float2>() : (float2*)t;
         dev::gemm_tc<<<(unsigned)pl.grid, dev::TC_THREADS, dev::TC_SMEM, s>>>(
             c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
@@ -914,8 +919,12 @@ void diag_impl(abc_ctx* c, const void* psi, const void* aux, const void* V, int 
     const Geometry& g = c->geo;
     const T* Vuse = (const T*)V;
     if (mf) {
-        dev::density_potential<T><<<nblk(c->nvox, 256), 256, 0, s>>>(c->nvox, n_orb, (const Vc*)psi, (const T*)V,
-                                                                     (T)mf->a, (T)mf->b, (T)mf->alpha, c->Veff.as<T>());
+        // the energy column weighs each orbital with V_ext + e(rho), e(rho) = (a/2) rho +
+        // b/(2+alpha) rho^(1+alpha): the interaction energy per unit density, so the
+        // orbitals' energies sum to the mean-field functional whose rho-derivative is V
+        dev::density_potential<T><<<nblk(c->nvox, 256), 256, 0, s>>>(
+            c->nvox, n_orb, (const Vc*)psi, (const T*)V, (T)(0.5 * mf->a), (T)(mf->b / (2.0 + mf->alpha)),
+            (T)mf->alpha, c->Veff.as<T>());
         Vuse = c->Veff.as<T>();
     }
     // W's auxiliary term f*Qf uses the diagonal Q of radius 1 (Thm 3.2); with R = 3, W = |phi|^2
@@ -1321,7 +1330,7 @@ extern "C" int abc_profile_enable(abc_ctx* ctx, int enable) {
 }
 
 extern "C" int abc_profile_read(abc_ctx* ctx, int kernel, double* ms, long long* launches) {
-    if (!ctx || !ms || !launches || kernel < 0 || kernel > 1) return fail(ABC_ERR_ARG, "bad argument");
+    if (!ctx || !ms || !launches || kernel < 0 || kernel > 2) return fail(ABC_ERR_ARG, "bad argument");
     ProfileSlot& ps = ctx->prof[kernel];
     double tot = 0;
     for (size_t i = 0; i + 1 < ps.used; i += 2) {
@@ -1337,7 +1346,7 @@ extern "C" int abc_profile_read(abc_ctx* ctx, int kernel, double* ms, long long*
 
 extern "C" int abc_profile_durations(abc_ctx* ctx, int kernel, float* ms_out, long long max_out,
                                      long long* launches) {
-    if (!ctx || !launches || kernel < 0 || kernel > 1 || max_out < 0 || (max_out > 0 && !ms_out))
+    if (!ctx || !launches || kernel < 0 || kernel > 2 || max_out < 0 || (max_out > 0 && !ms_out))
         return fail(ABC_ERR_ARG, "bad argument");
     ProfileSlot& ps = ctx->prof[kernel];
     const long long n = (long long)(ps.used / 2);
@@ -1359,6 +1368,17 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
         } else if (n_orb == 1) {
             for (int k = 0; k < ctx->ci.n; ++k)                                        // class blocks, read once
                 entries += (double)ctx->bi.nseg * ctx->ci.m[k] * ctx->ci.m[k];
+        } else if (ctx->tc && n_orb <= ctx->params.max_orbitals) {
+            // tensor-core GEMM: the split planes of every class block once (4 planes of
+            // 4-byte TF32), the packed right-hand sides (6 planes) and the partial outputs
+            double a = 0, x = 0;
+            for (int k = 0; k < ctx->ci.n; ++k) {
+                a += (double)ctx->tci.m[k] * ctx->tci.m[k];
+                x += (double)ctx->tci.R[k] * ctx->tci.m[k] * n_orb;
+            }
+            const int ns = ctx->tc_b[n_orb].nsplit;
+            *bytes = a * 4 * 4 + x * 6 * 4 + x * ns * 8;
+            return ABC_OK;
         } else {
             for (int p = 0; p < ctx->bi.n; ++p) entries += (double)ctx->bi.nseg * ctx->bi.m[p] * ctx->bi.m[p];
         }
@@ -1368,6 +1388,17 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
     } else {
         return fail(ABC_ERR_ARG, "unknown kernel");
     }
+    return ABC_OK;
+}
+
+extern "C" int abc_kernel_flops(const abc_ctx* ctx, int kernel, int n_orb, double* useful, double* issued) {
+    if (!ctx || !useful || !issued || n_orb < 1) return fail(ABC_ERR_ARG, "bad argument");
+    if (kernel != ABC_KERNEL_CONTRACTION) return fail(ABC_ERR_ARG, "flops are reported for the contraction only");
+    // complex multiply-add = 8 real flops per stored class-block entry and right-hand side
+    double u = 0;
+    for (int k = 0; k < ctx->ci.n; ++k) u += 8.0 * ctx->bi.nseg * ctx->ci.R[k] * (double)ctx->ci.m[k] * ctx->ci.m[k];
+    *useful = u * n_orb;
+    *issued = (ctx->tc && n_orb > 1) ? 3.0 * *useful : *useful;   // three products per split term
     return ABC_OK;
 }
 

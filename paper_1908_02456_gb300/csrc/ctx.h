@@ -96,7 +96,7 @@ struct abc_ctx {
     long long graph_kernels = 0;
     // profiling
     bool profiling = false;
-    abc::ProfileSlot prof[2];
+    abc::ProfileSlot prof[3];
 };
 
 namespace abc {

@@ -118,6 +118,9 @@ def test_meanfield_batched_reduced(torch_cuda, prec):
         assert rel(p, ref_p) < TOL[prec]
         assert rel(f, ref_f) < TOL[prec]
         assert rel(d, ref_d) < TOL[prec]
+        # the orbitals' energies sum to the mean-field functional E[phi] (Sec. 4.3)
+        E_ref = sy.energy_functional(ref_p)
+        assert abs(d[-1, :, 2].sum() - E_ref) < TOL[prec] * abs(E_ref)
 
 
 def test_odd_nonuniform_box_fp64(torch_cuda):
