@@ -297,6 +297,9 @@ def measure(args, w, rank, world, dev, extra_lines=True):
     state_bytes = w.n_orb * np.prod(w.shape) * 8
     big = state_bytes > 2 * L2_BYTES
 
+    # per-shape kernel choices (untimed set-up, on a copy of the state)
+    from paper_1908_02456_gb300 import tune
+    tuned = tune.tune(ctx, psi, aux, Vt, w.dt, meanfield=mf, use_cache=False)
     # warm-up (also captures the CUDA graph)
     ctx.run(psi, aux, Vt, w.dt, max(args.warmup, 1), meanfield=mf)
     torch.cuda.synchronize()
@@ -328,7 +331,8 @@ def measure(args, w, rank, world, dev, extra_lines=True):
     gpu_launches = ctx.launches() - launches0
     tot_units, max_sec = aggregate(units, sec)
     out = {"value": tot_units / max_sec, "ms_per_step": max_sec / steps * 1e3, "steps": steps,
-           "clocks": clk.summary(), "gpu_launches": gpu_launches}
+           "clocks": clk.summary(), "gpu_launches": gpu_launches,
+           "tuning": {"setting": tune.describe(tuned.get("setting", {})), "sweep_ms_per_step": tuned.get("sweep")}}
 
     # dominant kernels: live CUDA-event timing of every launch over eager steps on the
     # launching stream (no graph), the same flush policy as the timed steps
@@ -352,7 +356,10 @@ def measure(args, w, rank, world, dev, extra_lines=True):
     avg_c = ms_c / n_c * 1e-3
     avg_s = ms_s / n_s * 1e-3
     ach_s = bytes_s / avg_s / 1e9
-    stencil = {"bound": "hbm", "kernel": "stencil_stage_x2 (fused stencil + potential + Horner stage)",
+    fused = ctx.get_tuning(abc.TUNE_FUSED) == 1 or (ctx.get_tuning(abc.TUNE_FUSED) == -1 and w.n_orb >= 2)
+    sname = ("stencil_bulk4 (the four Horner stages' interior fused in time)" if fused else
+             "stencil_stage_x2 (fused stencil + potential + Horner stage)")
+    stencil = {"bound": "hbm", "kernel": sname,
                "achieved": round(ach_s, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach_s / hbm, 4),
                "avg_launch_us": round(avg_s * 1e6, 2), "bytes_per_launch": bytes_s, "launches_timed": n_s}
     traffic = traffic_for(w)
@@ -417,6 +424,29 @@ def measure(args, w, rank, world, dev, extra_lines=True):
                   "d2h_bytes_per_step": d2h / steps,
                   "call": "abc_run_host: copy psi, f, V in from pinned host memory; run the steps; copy psi, f out"}
 
+    # the 3xTF32 tensor-core form of the same workload (context for the split-FP16 GEMM)
+    if w.precision == "fp16x3" and not args.no_fp64:
+        ctx_t = abc.Context(w.shape, w.h, w.order, w.s, precision="tf32x3", max_orbitals=w.n_orb)
+        pt = torch.from_numpy(psi0).to(dev, torch.complex64)
+        at = ctx_t.new_aux(w.n_orb)
+        ctx_t.run(pt, at, Vt, w.dt, 2, meanfield=mf)
+        nt = min(steps, 50)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        g0.record(stream)
+        ctx_t.run(pt, at, Vt, w.dt, nt, meanfield=mf)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        st_ = g0.elapsed_time(g1) * 1e-3
+        ctx_t.profile(True)
+        ctx_t.run(pt, at, Vt, w.dt, 2, meanfield=mf)
+        ms_t, n_t = ctx_t.profile_read(abc.KERNEL_CONTRACTION)
+        ctx_t.profile(False)
+        out["tf32x3_form"] = {"value": w.n_orb * np.prod(w.shape) * nt / st_, "ms_per_step": st_ / nt * 1e3,
+                              "gemm_avg_launch_us": round(ms_t / n_t * 1e3, 2),
+                              "gemm_tflops_issued": round(issued / (ms_t / n_t * 1e-3) / 1e12, 1)}
+        ctx_t.close()
+
     # plain FP64 GPU form on the same inputs, and the reduced form's distance from it
     if not args.no_fp64:
         ctx64 = abc.Context(w.shape, w.h, w.order, w.s, precision="fp64", max_orbitals=w.n_orb)
@@ -452,9 +482,9 @@ def traffic_for(w):
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(tr_path):
         return None
-    key = "contraction_c64_64cube" if w.n_orb == 1 else f"gemm_tc_{w.name}"
+    key = "contraction_c64_64cube" if w.n_orb == 1 else f"gemm_tc_{w.name}_{w.precision}"
     tr = json.load(open(tr_path)).get(key)
-    if tr and tr.get("kernel_stamp") == ctx_stamp(tr.get("source", "sym_gemv.cuh")):
+    if tr and tr.get("kernel_stamp") == ctx_stamp(tr.get("kernel_file", "sym_gemv.cuh")):
         return tr["bytes_per_launch"]
     return None
 
@@ -573,6 +603,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
                 "config": config_dict(w), "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"],
                 "clocks": res["clocks"], "gpu_launches": res["gpu_launches"], "fp64_form": res.get("fp64_form"),
+                "tf32x3_form": res.get("tf32x3_form"), "tuning": res.get("tuning"),
                 "single_orbital": single, "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(line))
     if world > 1:

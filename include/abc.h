@@ -70,6 +70,17 @@ extern "C" {
                                   kind::tf32) with the matrices split as TF32 hi +
                                   lo and three products per term (FP32-level error),
                                   FP32 accumulation; n_orb = 1 as ABC_C64_FP32      */
+#define ABC_C64_SPLIT_FP16 4   /* complex64 state; for n_orb >= 2 the boundary
+                                  contraction runs on the tensor cores with FP16
+                                  operands (kind::f16, twice the TF32 rate): every
+                                  class block is scaled by a power of two and every
+                                  right-hand-side column by a power of two found per
+                                  contraction, both split as FP16 hi + lo (the same
+                                  10 + 10 mantissa bits as 3xTF32), three products
+                                  per term, FP32 accumulation, the scales undone in
+                                  the epilogue (exact); n_orb = 1 as ABC_C64_FP32.
+                                  Columns whose largest part is above ~2^78 overflow
+                                  FP16 (a state that large has diverged)            */
 
 /* how the order-1 coefficients of R_11(s) = (sI - B)^{-1} A are fitted to K(s) */
 #define ABC_FIT1_LIMIT 0       /* Thm 3.2: R_11(s1) = K(s1) and the s -> infinity
@@ -116,7 +127,7 @@ typedef struct {
     int order;        /* 0, 1 or 2 (rational order m of eq:24)                      */
     double s0;        /* order 0 interpolation point, > 0 (Thm 3.1)                 */
     double s1;        /* order 1 interpolation point, > 0 (Thm 3.2)                 */
-    int precision;    /* ABC_FP64 | ABC_C64_FP32 | ABC_C64_3XTF32                   */
+    int precision;    /* ABC_FP64 | ABC_C64_FP32 | ABC_C64_3XTF32 | ABC_C64_SPLIT_FP16 */
     int max_orbitals; /* largest n_orb later passed to step/run (sizes workspace),
                          1 .. 65535                                                 */
     double s2[4];     /* order 2 interpolation points, > 0 and distinct (Sec. 3.3:
@@ -158,7 +169,19 @@ int abc_step(abc_ctx* ctx, void* psi, void* aux, const void* V, int n_orb, doubl
  * it.  If diag_every > 0, after every diag_every steps the per-orbital
  * diagnostics [norm, W, energy] (see abc_diagnostics) are stored; diag_out (host,
  * [nsteps/diag_every][n_orb][3] doubles) is filled when the call returns, which
- * then synchronises the stream.  The step loop is replayed as a CUDA graph. */
+ * then synchronises the stream.  The step loop is replayed as a CUDA graph.
+ *
+ * Divergence monitor (with diag_every > 0): Thm 3.1 and Thm 3.2 make W (= |phi|^2
+ * for order 0, |phi|^2 + f^* Q f for order 1) non-increasing, and the degree-4
+ * Taylor step keeps that for stable dt.  On the device, every diagnostic row is
+ * compared with the previous one (with the start state for the first): for order 0
+ * and for the order-1 limit fit at radius 1 W may not grow by more than
+ * diag_every * 1e-12 (FP64) or diag_every * 1e-6 (complex64) relative; for the
+ * forms without a proof (order 2, the other order-1 fits, order 1 at radius 3) W
+ * may not pass twice its start value; a non-finite W always fails.  The run still
+ * completes its nsteps (the host learns of the failure when the call synchronises)
+ * and then returns ABC_ERR_UNSTABLE, naming the first failing step and orbital in
+ * abc_last_error(); diag_out is filled all the same. */
 int abc_run(abc_ctx* ctx, void* psi, void* aux, const void* V, int n_orb, double dt,
             long long nsteps, const abc_meanfield* mf, int diag_every, double* diag_out,
             void* stream);
@@ -176,6 +199,27 @@ int abc_run_host(abc_ctx* ctx, void* psi_host, void* aux_host, const void* V_hos
  * aux: device [n_gamma][n_orb] complex (order 1) or [2][n_gamma][n_orb] (order 2:
  * f then g), overwritten.  Asynchronous on the stream. */
 int abc_aux_init(abc_ctx* ctx, const void* psi, void* aux, int n_orb, void* stream);
+
+/* Checkpoint / resume.  A state blob is a self-describing host buffer: a header
+ * (format version, grid, radius, ABC order and interpolation points, precision,
+ * orbital count, n_gamma, the context's step count and time, payload sizes and a
+ * 64-bit checksum) followed by psi and aux exactly as they are stored on the device
+ * (layouts above).  abc_state_size gives the blob size for n_orb orbitals.
+ * abc_get_state copies psi and aux (device) into host_dst (at least that size),
+ * recording the context's progress; it synchronises the stream.  abc_set_state
+ * checks that the blob was written by a context with the same grid, radius, order,
+ * fit, interpolation points, precision and orbital count and that its checksum
+ * matches (else ABC_ERR_ARG, nothing copied), then copies psi and aux to the given
+ * device buffers and sets the context's progress to the recorded one; it
+ * synchronises the stream.  abc_progress reports the steps and the time the
+ * context has advanced (abc_step, abc_run, abc_run_host; abc_set_state resets
+ * them).  The paper has no counterpart (it defines the state y = (phi, f) that the
+ * blob holds, Sec. 3). */
+int abc_state_size(const abc_ctx* ctx, int n_orb, size_t* bytes);
+int abc_get_state(const abc_ctx* ctx, const void* psi, const void* aux, int n_orb, void* host_dst, size_t bytes,
+                  void* stream);
+int abc_set_state(abc_ctx* ctx, void* psi, void* aux, int n_orb, const void* host_src, size_t bytes, void* stream);
+int abc_progress(const abc_ctx* ctx, long long* steps, double* t);
 
 /* Per-orbital diagnostics of the current state into host out[n_orb][3]:
  * norm_j = h^3 |phi_j|^2; W_j = norm_j + h^3 f_j^* Q f_j (eq:lyapunov1; = norm_j
@@ -229,7 +273,9 @@ int abc_profile_durations(abc_ctx* ctx, int kernel, float* ms_out, long long max
  * numerator): boundary matrix bytes + vectors for the contraction (for the
  * tensor-core GEMM: its split operand planes of every class block once, the packed
  * right-hand sides and the partial outputs); for the stencil 3 complex values per
- * point and orbital plus V per point. */
+ * point and orbital plus V per point, or, when abc_run fuses the stages in time
+ * (ABC_TUNE_FUSED), the fused pass's 2 complex values per point and orbital plus V
+ * plus the band values it stores. */
 int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, double* bytes);
 
 /* Floating-point operations of one contraction launch for n_orb orbitals (kernel
@@ -254,9 +300,10 @@ int abc_kernel_flops(const abc_ctx* ctx, int kernel, int n_orb, double* useful, 
  * otherwise ABC_ERR_ARG with the required size in abc_last_error().  Calls share
  * the array: calls whose work overlaps on the GPU race and must be serialised.
  * Nothing needs clearing between calls (every scratch value is written before it
- * is read).  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make it before any stream capture.  ABC_FP64 and
- * ABC_C64_FP32 contexts only. */
+ * is read).  Every call outside stream capture looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device; a call during capture reuses the
+ * address the last uncaptured call found, so make one call on each device before
+ * any stream capture.  ABC_FP64 and ABC_C64_FP32 contexts only. */
 #define ABC_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 int abc_step_noalloc(const abc_ctx* ctx, void* psi, void* aux, const void* V, int n_orb, double dt,
                      void* stream);
@@ -290,6 +337,21 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           0 (default) on a second stream forked after the boundary
  *                           contraction, 1 forked at the stage start, 2 on the main
  *                           stream after the back transform.
+ *   ABC_TUNE_FUSED          order 1, complex64, radius 1, nx even: abc_run computes the
+ *                           interior stencil of the four Horner stages of a step in one
+ *                           pass (shared-memory rings of planes, the stages' boundary band
+ *                           finished stage by stage after each contraction; same formula,
+ *                           FP32 rounding differences only) and alternates the state
+ *                           between psi and a context-owned buffer (one copy back after an
+ *                           odd step count).  0 (default) off; 1 on; -1 on for n_orb >= 2.
+ *                           abc_step and the adjoint always step stage by stage.
+ *   ABC_TUNE_GEMM_TILE      tensor-core forms, n_orb >= 2: 0 (default) output tiles of up
+ *                           to 96 columns, three ring stages, one CTA per SM; 1: up to 64
+ *                           columns, two stages, two CTAs per SM.  Rebuilds the work lists
+ *                           (synchronises the device).
+ *   ABC_TUNE_GEMM_SPLIT     tensor-core forms: number of K splits of every output tile
+ *                           (1..8), or 0 (default) for about two work items per CTA slot.
+ *                           Rebuilds the work lists (synchronises the device).
  * Setting a knob drops the cached CUDA graph.  The paper has no counterpart.
  */
 #define ABC_TUNE_L2_KEEP_TILES 0
@@ -297,6 +359,9 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
 #define ABC_TUNE_PDL 2
 #define ABC_TUNE_CHAIN 3
 #define ABC_TUNE_STENCIL 4
+#define ABC_TUNE_FUSED 5
+#define ABC_TUNE_GEMM_TILE 6
+#define ABC_TUNE_GEMM_SPLIT 7
 int abc_set_tuning(abc_ctx* ctx, int key, long long value);
 int abc_get_tuning(const abc_ctx* ctx, int key, long long* value);
 

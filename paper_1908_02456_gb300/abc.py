@@ -14,12 +14,14 @@ from typing import Optional, Sequence
 import numpy as np
 
 OK = 0
-FP64, C64_FP32, C64_SPLIT_BF16, C64_3XTF32 = 0, 1, 2, 3
+FP64, C64_FP32, C64_SPLIT_BF16, C64_3XTF32, C64_SPLIT_FP16 = 0, 1, 2, 3, 4
 MAT_K, MAT_M, MAT_A, MAT_B, MAT_Q = 0, 1, 2, 3, 4
 MAT_B1, MAT_B0, MAT_A1, MAT_A0 = 5, 6, 7, 8
 KERNEL_CONTRACTION, KERNEL_STENCIL, KERNEL_PACK = 0, 1, 2
-TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT, TUNE_PDL, TUNE_CHAIN, TUNE_STENCIL = 0, 1, 2, 3, 4
-PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16, "tf32x3": C64_3XTF32}
+TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT, TUNE_PDL, TUNE_CHAIN, TUNE_STENCIL, TUNE_FUSED = 0, 1, 2, 3, 4, 5
+TUNE_GEMM_TILE, TUNE_GEMM_SPLIT = 6, 7
+PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16, "tf32x3": C64_3XTF32,
+              "fp16x3": C64_SPLIT_FP16}
 FIT1_LIMIT, FIT1_TWO_POINT, FIT1_HERMITE = 0, 1, 2
 FITS1 = {"limit": FIT1_LIMIT, "two_point": FIT1_TWO_POINT, "hermite": FIT1_HERMITE}
 
@@ -77,6 +79,10 @@ def load():
         "abc_kernel_bytes": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
         "abc_kernel_flops": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)],
+        "abc_state_size": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+        "abc_get_state": [_P, _P, _P, ctypes.c_int, _P, ctypes.c_size_t, _P],
+        "abc_set_state": [_P, _P, _P, ctypes.c_int, _P, ctypes.c_size_t, _P],
+        "abc_progress": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)],
         "abc_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
         "abc_step_noalloc": [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, _P],
         "abc_set_tuning": [_P, ctypes.c_int, ctypes.c_longlong],
@@ -229,6 +235,30 @@ def abc_kernel_flops(ctx, kernel: int, n_orb: int):
     return u.value, i.value
 
 
+def abc_state_size(ctx, n_orb: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().abc_state_size(ctx, n_orb, ctypes.byref(n)))
+    return n.value
+
+
+def abc_get_state(ctx, psi_ptr, aux_ptr, n_orb, stream: int = 0) -> np.ndarray:
+    """The state blob (uint8 array) of psi / aux on the device."""
+    buf = np.empty(abc_state_size(ctx, n_orb), dtype=np.uint8)
+    _check(load().abc_get_state(ctx, psi_ptr, aux_ptr or None, n_orb, buf.ctypes.data, buf.nbytes, stream or None))
+    return buf
+
+
+def abc_set_state(ctx, psi_ptr, aux_ptr, n_orb, blob: np.ndarray, stream: int = 0):
+    blob = np.ascontiguousarray(blob, dtype=np.uint8)
+    _check(load().abc_set_state(ctx, psi_ptr, aux_ptr or None, n_orb, blob.ctypes.data, blob.nbytes, stream or None))
+
+
+def abc_progress(ctx):
+    n, t = ctypes.c_longlong(0), ctypes.c_double(0)
+    _check(load().abc_progress(ctx, ctypes.byref(n), ctypes.byref(t)))
+    return n.value, t.value
+
+
 def abc_set_tuning(ctx, key: int, value: int):
     _check(load().abc_set_tuning(ctx, key, int(value)))
 
@@ -374,6 +404,21 @@ class Context:
 
     def kernel_bytes(self, kernel, n_orb):
         return abc_kernel_bytes(self.ctx, kernel, n_orb)
+
+    def get_state(self, psi, aux, stream=None) -> np.ndarray:
+        """Checkpoint blob of (psi, aux) and the context's progress."""
+        b = psi.shape[0]
+        return abc_get_state(self.ctx, psi.data_ptr(), aux.data_ptr() if aux is not None else 0, b,
+                             self._stream(stream))
+
+    def set_state(self, psi, aux, blob, stream=None):
+        """Restore (psi, aux) in place from a checkpoint blob (validated by the library)."""
+        b = psi.shape[0]
+        abc_set_state(self.ctx, psi.data_ptr(), aux.data_ptr() if aux is not None else 0, b, blob,
+                      self._stream(stream))
+
+    def progress(self):
+        return abc_progress(self.ctx)
 
     def kernel_flops(self, kernel, n_orb):
         return abc_kernel_flops(self.ctx, kernel, n_orb)

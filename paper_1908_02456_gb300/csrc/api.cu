@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "stencil_fused.cuh"
 
 namespace abc {
 int fail(int status, const std::string& msg);
@@ -485,60 +487,19 @@ float tf32_rna(float v) {
     return r;
 }
 
-// Tensor-core form of the many-orbital contraction: every class block split into
-// TF32 hi / lo planes of its real and imaginary parts, packed per (128-row tile,
-// 16-deep K block) in the shared-memory image of gemm_tc, and the output tiles for
-// every orbital count 1..max_orbitals (largest classes first).
-int build_tc(abc_ctx* c) {
+// Output tiles and work lists of the persistent GEMM for every orbital count
+// 1..max_orbitals (largest classes first), for the context's tile configuration
+// (tc_wide: 96 columns, one CTA per SM; else 64 columns, two CTAs per SM) and split
+// choice (tc_split = 0: about two items per CTA slot; else that many K splits).
+int build_tc_plans(abc_ctx* c) {
     using namespace abc::dev;
     const Geometry& g = c->geo;
-    if ((int)g.cls.size() > SYM_CMAX) return fail(ABC_ERR_ARG, "internal: too many classes");
-    TcInfo info{};
-    long long chunks = 0;
-    for (size_t k = 0; k < g.cls.size(); ++k) {
-        info.m[k] = g.cls[k].m;
-        info.R[k] = g.cls[k].R;
-        for (int e = 0; e < 3; ++e) info.moff[k][e] = g.cls[k].moff[e];
-        info.nkb[k] = (g.cls[k].m + TC_KB - 1) / TC_KB;
-        info.abase[k] = chunks;
-        chunks += (long long)((g.cls[k].m + TC_M - 1) / TC_M) * info.nkb[k];
-    }
-    const size_t per = TC_A_BYTES / 4;
-    std::vector<float> pack((size_t)chunks * per, 0.0f);
-#pragma omp parallel for schedule(dynamic, 4)
-    for (long long ch = 0; ch < chunks; ++ch) {
-        int k = 0;
-        while (k + 1 < (int)g.cls.size() && ch >= info.abase[k + 1]) ++k;
-        const int m = info.m[k], nkb = info.nkb[k];
-        const long long loc = ch - info.abase[k];
-        const int mt = (int)(loc / nkb), kb = (int)(loc % nkb);
-        const std::vector<cd>& S = c->blocks.mat[k];
-        float* dst = pack.data() + (size_t)ch * per;
-        for (int r = 0; r < TC_M; ++r) {
-            const int row = mt * TC_M + r;
-            if (row >= m) break;
-            for (int q = 0; q < TC_KB; ++q) {
-                const int col = kb * TC_KB + q;
-                if (col >= m) break;
-                const cd v = S[(size_t)row * m + col];
-                const float re = (float)v.real(), im = (float)v.imag();
-                const float rh = tf32_rna(re), ih = tf32_rna(im);
-                const size_t o = tc_core_offset(r, q) / 4;
-                dst[0 * (TC_A_PLANE / 4) + o] = rh;
-                dst[1 * (TC_A_PLANE / 4) + o] = tf32_rna(re - rh);
-                dst[2 * (TC_A_PLANE / 4) + o] = ih;
-                dst[3 * (TC_A_PLANE / 4) + o] = tf32_rna(im - ih);
-            }
-        }
-    }
-    int st;
-    if ((st = c->tc_apack.alloc(pack.size() * sizeof(float)))) return st;
-    CUDA_TRY(cudaMemcpy(c->tc_apack.p, pack.data(), pack.size() * sizeof(float), cudaMemcpyHostToDevice));
+    const TcInfo& info = c->tci;
+    const int nmax = c->tc_wide ? TcWide::nmax : TcNarrow::nmax;
+    const int slots = c->tc_sms * (c->tc_wide ? TcWide::cps : TcNarrow::cps);
     std::vector<int> order(g.cls.size());
     for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return g.cls[a].m > g.cls[b].m; });
-    int sms = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     std::vector<TcTile> tiles;
     std::vector<TcCols> cranges;
     std::vector<TcItem> items;
@@ -553,7 +514,7 @@ int build_tc(abc_ctx* c) {
         int chunks = 0, maxnkb = 1;
         for (int k : order) {
             const int cols = g.cls[k].R * b;
-            const int nch = (cols + TC_NMAX - 1) / TC_NMAX;
+            const int nch = (cols + nmax - 1) / nmax;
             const int w = ((cols + nch - 1) / nch + 15) / 16 * 16;
             maxnkb = std::max(maxnkb, info.nkb[k]);
             for (int col0 = 0; col0 < cols; col0 += w) {
@@ -566,8 +527,10 @@ int build_tc(abc_ctx* c) {
         pl.tile_cnt = (int)tiles.size() - pl.tile_off;
         pl.cols_cnt = (int)cranges.size() - pl.cols_off;
         pl.max_nkb = maxnkb;
-        // about two items per SM; partial sums of the splits are added by the back transform
-        pl.nsplit = std::max(1, std::min(TC_MAX_SPLIT, (2 * sms + pl.tile_cnt - 1) / pl.tile_cnt));
+        // about two items per CTA slot unless fixed; partial sums of the splits are added
+        // by the back transform
+        pl.nsplit = c->tc_split > 0 ? std::min(c->tc_split, TC_MAX_SPLIT)
+                                    : std::max(1, std::min(TC_MAX_SPLIT, (2 * slots + pl.tile_cnt - 1) / pl.tile_cnt));
         // persistent GEMM: items (tile, split) longest first, each given to the CTA with the
         // least work so far; cost = bytes streamed for the item (its K blocks of A and X,
         // plus two K blocks' worth for the fill and the epilogue).  Items of equal cost
@@ -575,7 +538,6 @@ int build_tc(abc_ctx* c) {
         // A chunk go to different CTAs at about the same time.
         {
             std::vector<TcItem> its;
-            std::vector<double> cost;
             for (int ti = pl.tile_off; ti < pl.tile_off + pl.tile_cnt; ++ti)
                 for (int sp = 0; sp < pl.nsplit; ++sp) its.push_back(TcItem{ti, sp});
             auto item_cost = [&](const TcItem& w) {
@@ -593,7 +555,7 @@ int build_tc(abc_ctx* c) {
                 if (a.split != b2.split) return a.split < b2.split;
                 return x.col0 < y.col0;
             });
-            const int G = std::min<int>(sms, (int)its.size());
+            const int G = std::min<int>(slots, (int)its.size());
             std::vector<std::vector<TcItem>> per(G);
             std::vector<double> load(G, 0.0);
             for (const TcItem& w : its) {
@@ -614,6 +576,7 @@ int build_tc(abc_ctx* c) {
         max_chunks = std::max<long long>(max_chunks, chunks);
         if (pl.nsplit > 1) max_part = std::max<long long>(max_part, (long long)pl.nsplit * g.n_gamma * b);
     }
+    int st;
     if ((st = c->tc_tiles.alloc(tiles.size() * sizeof(TcTile)))) return st;
     CUDA_TRY(cudaMemcpy(c->tc_tiles.p, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice));
     if ((st = c->tc_cols.alloc(cranges.size() * sizeof(TcCols)))) return st;
@@ -622,15 +585,105 @@ int build_tc(abc_ctx* c) {
     CUDA_TRY(cudaMemcpy(c->tc_items.p, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice));
     if ((st = c->tc_item_off.alloc(item_off.size() * sizeof(int)))) return st;
     CUDA_TRY(cudaMemcpy(c->tc_item_off.p, item_off.data(), item_off.size() * sizeof(int), cudaMemcpyHostToDevice));
-    if ((st = c->tc_bpack.alloc((size_t)max_chunks * TC_B_BYTES))) return st;
-    if (max_part && (st = c->tc_part.alloc((size_t)max_part * sizeof(float2)))) return st;
+    if ((size_t)max_chunks * TC_B_BYTES > c->tc_bpack.bytes && (st = c->tc_bpack.alloc((size_t)max_chunks * TC_B_BYTES)))
+        return st;
+    if ((size_t)max_part * sizeof(float2) > c->tc_part.bytes && (st = c->tc_part.alloc((size_t)max_part * sizeof(float2))))
+        return st;
+    return ABC_OK;
+}
+
+// Tensor-core form of the many-orbital contraction: every class block split into
+// hi / lo planes of its real and imaginary parts (TF32, or FP16 after scaling the
+// block by 2^es), packed per (128-row tile, K block) in the shared-memory image of
+// gemm_tc, and the output tiles for every orbital count 1..max_orbitals (largest
+// classes first).
+int build_tc(abc_ctx* c) {
+    using namespace abc::dev;
+    const Geometry& g = c->geo;
+    if ((int)g.cls.size() > SYM_CMAX) return fail(ABC_ERR_ARG, "internal: too many classes");
+    const bool f16 = c->prec == ABC_C64_SPLIT_FP16;
+    const int KB = f16 ? TcKind<TC_F16>::KB : TcKind<TC_TF32>::KB;
+    TcInfo info{};
+    info.ncls = (int)g.cls.size();
+    long long chunks = 0;
+    int rsum = 0;
+    for (size_t k = 0; k < g.cls.size(); ++k) {
+        info.m[k] = g.cls[k].m;
+        info.R[k] = g.cls[k].R;
+        for (int e = 0; e < 3; ++e) info.moff[k][e] = g.cls[k].moff[e];
+        info.nkb[k] = (g.cls[k].m + KB - 1) / KB;
+        info.abase[k] = chunks;
+        info.rsum[k] = rsum;
+        rsum += g.cls[k].R;
+        chunks += (long long)((g.cls[k].m + TC_M - 1) / TC_M) * info.nkb[k];
+        // FP16: the block's largest real or imaginary part scaled into [2^13, 2^14)
+        double mx = 0;
+        for (const cd& v : c->blocks.mat[k]) mx = std::max(mx, std::max(std::fabs(v.real()), std::fabs(v.imag())));
+        int ex = 0;
+        if (mx > 0) std::frexp(mx, &ex);                 // mx = f 2^ex, f in [0.5, 1)
+        info.es[k] = f16 && mx > 0 ? std::min(60, std::max(-60, TC_TARGET_EXP - ex)) : 0;
+    }
+    const size_t per = TC_A_BYTES / 4;
+    std::vector<float> pack((size_t)chunks * per, 0.0f);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long ch = 0; ch < chunks; ++ch) {
+        int k = 0;
+        while (k + 1 < (int)g.cls.size() && ch >= info.abase[k + 1]) ++k;
+        const int m = info.m[k], nkb = info.nkb[k];
+        const long long loc = ch - info.abase[k];
+        const int mt = (int)(loc / nkb), kb = (int)(loc % nkb);
+        const std::vector<cd>& S = c->blocks.mat[k];
+        float* dst = pack.data() + (size_t)ch * per;
+        __half* dh = reinterpret_cast<__half*>(dst);
+        const double sc = std::ldexp(1.0, info.es[k]);
+        for (int r = 0; r < TC_M; ++r) {
+            const int row = mt * TC_M + r;
+            if (row >= m) break;
+            for (int q = 0; q < KB; ++q) {
+                const int col = kb * KB + q;
+                if (col >= m) break;
+                const cd v = S[(size_t)row * m + col];
+                if (f16) {
+                    const float re = (float)(v.real() * sc), im = (float)(v.imag() * sc);
+                    const __half rh = __float2half_rn(re), ih = __float2half_rn(im);
+                    const size_t o = tc_core_offset_f16(r, q) / 2;
+                    dh[0 * (TC_A_PLANE / 2) + o] = rh;
+                    dh[1 * (TC_A_PLANE / 2) + o] = __float2half_rn(re - __half2float(rh));
+                    dh[2 * (TC_A_PLANE / 2) + o] = ih;
+                    dh[3 * (TC_A_PLANE / 2) + o] = __float2half_rn(im - __half2float(ih));
+                } else {
+                    const float re = (float)v.real(), im = (float)v.imag();
+                    const float rh = tf32_rna(re), ih = tf32_rna(im);
+                    const size_t o = tc_core_offset(r, q) / 4;
+                    dst[0 * (TC_A_PLANE / 4) + o] = rh;
+                    dst[1 * (TC_A_PLANE / 4) + o] = tf32_rna(re - rh);
+                    dst[2 * (TC_A_PLANE / 4) + o] = ih;
+                    dst[3 * (TC_A_PLANE / 4) + o] = tf32_rna(im - ih);
+                }
+            }
+        }
+    }
+    int st;
+    if ((st = c->tc_apack.alloc(pack.size() * sizeof(float)))) return st;
+    CUDA_TRY(cudaMemcpy(c->tc_apack.p, pack.data(), pack.size() * sizeof(float), cudaMemcpyHostToDevice));
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     if (!c->err_flag.p) {
         if ((st = c->err_flag.alloc(sizeof(int)))) return st;
         CUDA_TRY(cudaMemset(c->err_flag.p, 0, sizeof(int)));
     }
-    CUDA_TRY(cudaFuncSetAttribute(gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    CUDA_TRY(cudaFuncSetAttribute(gemm_tc<TC_TF32, TcWide>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcWide::smem));
+    CUDA_TRY(cudaFuncSetAttribute(gemm_tc<TC_F16, TcWide>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcWide::smem));
+    CUDA_TRY(cudaFuncSetAttribute(gemm_tc<TC_TF32, TcNarrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TcNarrow::smem));
+    CUDA_TRY(cudaFuncSetAttribute(gemm_tc<TC_F16, TcNarrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TcNarrow::smem));
+    if (f16 && (st = c->tc_colexp.alloc(sizeof(int) * (size_t)rsum * c->params.max_orbitals))) return st;
+    c->tc_f16 = f16;
+    c->tc_ncols = rsum;
     c->tc_sms = sms;
     c->tci = info;
+    if ((st = build_tc_plans(c))) return st;
     c->tc = true;
     return ABC_OK;
 }
@@ -673,6 +726,23 @@ struct TRes {
     long long stride = 0;
 };
 
+// The persistent tensor-core GEMM in the context's tile configuration.
+template <int KIND>
+void launch_gemm_tc(abc_ctx* c, const abc_ctx::TcPlan& pl, int n_orb, float2* out, int conj, const int* colexp,
+                    cudaStream_t s) {
+    const long long n = c->geo.n_gamma;
+    if (c->tc_wide)
+        dev::gemm_tc<KIND, dev::TcWide><<<(unsigned)pl.grid, dev::TC_THREADS, dev::TcWide::smem, s>>>(
+            c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
+            c->tc_apack.as<float>(), c->tc_bpack.as<float>(), n_orb, (int)n, pl.nsplit, n * n_orb, out, conj,
+            c->err_flag.as<int>(), colexp);
+    else
+        dev::gemm_tc<KIND, dev::TcNarrow><<<(unsigned)pl.grid, dev::TC_THREADS, dev::TcNarrow::smem, s>>>(
+            c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
+            c->tc_apack.as<float>(), c->tc_bpack.as<float>(), n_orb, (int)n, pl.nsplit, n * n_orb, out, conj,
+            c->err_flag.as<int>(), colexp);
+}
+
 // The boundary contraction t = S x (conj: conj(S) x).
 template <typename T>
 TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaStream_t s,
@@ -701,17 +771,29 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
         const abc_ctx::TcPlan& pl = c->tc_b[n_orb];
         // the operand packing has its own timing slot, so the contraction slot times the GEMM alone
         prof_begin(c, ABC_KERNEL_PACK, s);
-        dev::pack_x_tc<<<dim3((unsigned)pl.cols_cnt, (unsigned)pl.max_nkb), 128, 0, s>>>(
-            c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off, n_orb, n, (const float2*)x, conj,
-            c->tc_bpack.as<float>());
-        prof_end(c, ABC_KERNEL_PACK, s);
-        prof_begin(c, ABC_KERNEL_CONTRACTION, s);
+        const dim3 pgrid((unsigned)pl.cols_cnt, (unsigned)pl.max_nkb);
         float2* out = pl.nsplit > 1 ? c->tc_part.as<float2>() : (float2*)t;
-        dev::gemm_tc<<<(unsigned)pl.grid, dev::TC_THREADS, dev::TC_SMEM, s>>>(
-            c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
-            c->tc_apack.as<float>(), c->tc_bpack.as<float>(), n_orb, n, pl.nsplit, (long long)n * n_orb, out, conj,
-            c->err_flag.as<int>());
-        c->launches += 1;
+        const int* colexp = c->tc_colexp.as<int>();
+        if (c->tc_f16) {
+            const int ncols = c->tc_ncols * n_orb;
+            dev::tc_colexp<<<(unsigned)((ncols + 7) / 8), 256, 0, s>>>(c->tci, n_orb, n, (const float2*)x,
+                                                                       c->tc_colexp.as<int>(), ncols);
+            dev::pack_x_tc<dev::TC_F16><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
+                                                               n_orb, n, (const float2*)x, conj,
+                                                               c->tc_bpack.as<float>(), colexp);
+            prof_end(c, ABC_KERNEL_PACK, s);
+            prof_begin(c, ABC_KERNEL_CONTRACTION, s);
+            launch_gemm_tc<dev::TC_F16>(c, pl, n_orb, out, conj, colexp, s);
+            c->launches += 2;
+        } else {
+            dev::pack_x_tc<dev::TC_TF32><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
+                                                                n_orb, n, (const float2*)x, conj,
+                                                                c->tc_bpack.as<float>(), colexp);
+            prof_end(c, ABC_KERNEL_PACK, s);
+            prof_begin(c, ABC_KERNEL_CONTRACTION, s);
+            launch_gemm_tc<dev::TC_TF32>(c, pl, n_orb, out, conj, colexp, s);
+            c->launches += 1;
+        }
         res.t = out;
         res.nsplit = pl.nsplit;
         res.stride = (long long)n * n_orb;
@@ -912,6 +994,113 @@ void step_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, doubl
     }
 }
 
+// ---------------------------------------------------------------------------
+// Order-1 step with the interior stencil fused in time (complex64, radius 1, nx even):
+// stencil_bulk4 computes the four stages' interior in one pass beside the first
+// boundary chain; stencil_band finishes the boundary band stage by stage after each
+// contraction (see stencil_fused.cuh).  The result goes to `out` (not `in`: the bulk
+// pass reads the input with a halo while it writes).
+// ---------------------------------------------------------------------------
+bool fused_ok(const abc_ctx* c, int n_orb) {
+    if (c->prec == ABC_FP64 || c->params.order != 1 || c->geo.R != 1 || (c->geo.nx & 1)) return false;
+    if (c->geo.nx < 8 || c->geo.ny < 8 || c->geo.nz < 8) return false;
+    return c->fused_mode == 1 || (c->fused_mode == -1 && n_orb >= 2);
+}
+
+int ensure_fused_workspace(abc_ctx* c) {
+    if (c->alt.p) return ABC_OK;
+    const size_t phi_b = (size_t)c->nvox * c->params.max_orbitals * cplx_bytes(c);
+    int st;
+    if ((st = c->Tp3.alloc(phi_b))) return st;
+    if ((st = c->alt.alloc(phi_b))) return st;
+    for (int i = 0; i < 8; ++i)
+        if (!c->ev_fz[i]) CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fz[i], cudaEventDisableTiming));
+    CUDA_TRY(cudaFuncSetAttribute(dev::stencil_bulk4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::FB_SMEM));
+    int sms = 0, per_sm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dev::stencil_bulk4, dev::FB_THREADS, dev::FB_SMEM));
+    c->fused_grid = sms * std::max(per_sm, 1);
+    return ABC_OK;
+}
+
+// The boundary part of an order-1 stage: forward transform of (w_phi, w_f), the
+// contraction and the back transform writing o_f = y_f + cdt (B w_f + A E w_phi).
+void boundary_chain_f(abc_ctx* c, int n_orb, float cdt, const void* w_phi, const void* w_f, const void* y_f, void* o_f,
+                      cudaStream_t s) {
+    typedef float2 Vc;
+    const dev::CellTab<float> ct = cell_tab<float>(c);
+    const unsigned nbk = cell_blocks(c, n_orb);
+    const float a_coef = (float)(1.0 / (4.0 * c->geo.h * c->geo.h * c->geo.h * c->geo.h));
+    void* hp = c->hat_phi.p;
+    void* hf = c->hat_f.p;
+    if (n_orb % dev::FO == 0)
+        dev::bnd_forward_multi<float><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
+            ct, n_orb, c->nvox, (const Vc*)w_phi, (const Vc*)w_f, (Vc*)hp, (Vc*)hf);
+    else
+        dev::bnd_forward<float, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi, (const Vc*)w_f, (Vc*)hp,
+                                                       (Vc*)hf, nullptr, 0.f, dev::Ord2Fwd<float>{});
+    if (c->blocks.rows1) {
+        const void* x2[4] = {hf, hp, nullptr, nullptr};
+        const TRes tr = contraction<float>(c, nullptr, c->tvec.p, n_orb, 0, s, x2);
+        back<float, 4>(c, tr, n_orb, 0.f, 0.f, y_f, o_f, nullptr, cdt, s, hp, hf);
+    } else {
+        const TRes tr = contraction<float>(c, hf, c->tvec.p, n_orb, 0, s);
+        back<float, 0>(c, tr, n_orb, (float)c->blocks.s, a_coef, y_f, o_f, nullptr, cdt, s, hp, hf);
+    }
+}
+
+void step_fused(abc_ctx* c, const void* in, void* out, void* aux, const void* V, int n_orb, double dt,
+                const abc_meanfield* mf, cudaStream_t s) {
+    const Geometry& g = c->geo;
+    const float* Vuse = (const float*)V;
+    if (mf) {
+        dev::density_potential<float><<<nblk(c->nvox, 256), 256, 0, s>>>(
+            c->nvox, n_orb, (const float2*)in, (const float*)V, (float)mf->a, (float)mf->b, (float)mf->alpha,
+            c->Veff.as<float>());
+        Vuse = c->Veff.as<float>();
+    }
+    const double cs[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+    const float ih2 = (float)(1.0 / (g.h * g.h));
+    float2* U[4] = {nullptr, c->Tp[0].as<float2>(), c->Tp[1].as<float2>(), c->Tp3.as<float2>()};
+    void* F[4] = {aux, c->Tf[0].p, c->Tf[1].p, c->Tf[0].p};           // f^0 .. f^3
+    cudaStream_t side = c->side;
+    // the bulk pass beside the first boundary chain
+    cudaEventRecord(c->ev_fz[0], s);
+    cudaStreamWaitEvent(side, c->ev_fz[0], 0);
+    dev::FusedBulkArgs ba{};
+    ba.nx = g.nx; ba.ny = g.ny; ba.nz = g.nz; ba.n_orb = n_orb; ba.n_gamma = g.n_gamma; ba.inv_h2 = ih2;
+    for (int q = 0; q < 4; ++q) ba.cdt[q] = (float)(cs[q] * dt);
+    ba.y = (const float2*)in; ba.V = Vuse; ba.f0 = (const float2*)aux; ba.out = (float2*)out;
+    ba.u1 = U[1]; ba.u2 = U[2]; ba.u3 = U[3];
+    prof_begin(c, ABC_KERNEL_STENCIL, side);
+    dev::stencil_bulk4<<<c->fused_grid, dev::FB_THREADS, dev::FB_SMEM, side>>>(ba);
+    prof_end(c, ABC_KERNEL_STENCIL, side);
+    cudaEventRecord(c->ev_fz[1], side);
+    int launches = 1 + (mf ? 1 : 0);
+    // events: ev_fz[1] bulk done; ev_fz[2 + st] band of u^{st+2} done (side);
+    // ev_fz[5 + st] f^{st+1} ready (main), st = 0, 1, 2
+    for (int st = 0; st < 4; ++st) {
+        const void* w_phi = st == 0 ? in : (const void*)U[st];
+        void* o_f = st == 3 ? aux : c->Tf[st & 1].p;
+        if (st > 0) cudaStreamWaitEvent(s, c->ev_fz[st], 0);   // u^st on Gamma (bulk, then bands)
+        boundary_chain_f(c, n_orb, (float)(cs[st] * dt), w_phi, F[st], aux, o_f, s);
+        launches += 3;
+        if (st == 3) break;
+        // the band of u^{st+2} (d <= st) once f^{st+1} is out
+        cudaEventRecord(c->ev_fz[5 + st], s);
+        cudaStreamWaitEvent(side, c->ev_fz[5 + st], 0);
+        const int j = st + 2, dmax = st;
+        const dim3 gb((unsigned)nblk(dev::band_nodes(g.nx, g.ny, g.nz, dmax), 256), (unsigned)n_orb);
+        dev::stencil_band<<<gb, 256, 0, side>>>(g.nx, g.ny, g.nz, n_orb, dmax, ih2, U[j - 1], (const float2*)in, Vuse,
+                                                (const float2*)F[j - 1], j == 4 ? (float2*)out : U[j],
+                                                (float)(cs[j - 1] * dt));
+        cudaEventRecord(c->ev_fz[2 + st], side);
+        launches += 1;
+    }
+    cudaStreamWaitEvent(s, c->ev_fz[4], 0);     // the last band (u^4 on d <= 2)
+    c->launches += launches;
+}
+
 template <typename T>
 void diag_impl(abc_ctx* c, const void* psi, const void* aux, const void* V, int n_orb, const abc_meanfield* mf,
                double* out_dev, cudaStream_t s) {
@@ -1001,8 +1190,9 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     // [B1 | B0 - i A1 | -i A1 | A0] and the fitted order-1 rows [B | A] use the
     // full-block kernels
     const bool one_seg = params->order < 2 && !c->blocks.rows1;
-    if (one_seg && (c->prec == ABC_C64_FP32 || c->prec == ABC_C64_3XTF32) && (st = build_sym(c.get()))) return st;
-    if (one_seg && c->prec == ABC_C64_3XTF32 && (st = build_tc(c.get()))) return st;
+    const bool tc_prec = c->prec == ABC_C64_3XTF32 || c->prec == ABC_C64_SPLIT_FP16;
+    if (one_seg && (c->prec == ABC_C64_FP32 || tc_prec) && (st = build_sym(c.get()))) return st;
+    if (one_seg && tc_prec && (st = build_tc(c.get()))) return st;
     if (!c->err_flag.p) {
         if ((st = c->err_flag.alloc(sizeof(int)))) return st;
         CUDA_TRY(cudaMemset(c->err_flag.p, 0, sizeof(int)));
@@ -1029,6 +1219,8 @@ extern "C" int abc_step(abc_ctx* ctx, void* psi, void* aux, const void* V, int n
     cudaStream_t s = (cudaStream_t)stream;
     if (ctx->prec == ABC_FP64) step_impl<double>(ctx, psi, aux, V, n_orb, dt, nullptr, s);
     else step_impl<float>(ctx, psi, aux, V, n_orb, dt, nullptr, s);
+    ctx->steps_done += 1;
+    ctx->t_done += dt;
     return last_launch_status();
 }
 
@@ -1039,62 +1231,117 @@ int run_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double 
     if (diag_every < 0) return fail(ABC_ERR_ARG, "diag_every must be >= 0");
     if (diag_every > 0 && !diag_out) return fail(ABC_ERR_ARG, "diag_out is NULL");
     const long long ndiag = diag_every > 0 ? nsteps / diag_every : 0;
-    DevBuf dd;
+    if (ndiag >= INT_MAX) return fail(ABC_ERR_ARG, "too many diagnostic rows");
+    // diagnostic rows: row 0 is the start state (the monitor's reference), row n the
+    // state after n * diag_every steps; mon = {first failing row, its orbital}
+    DevBuf dd, mon;
     int st;
-    if (ndiag > 0 && (st = dd.alloc(sizeof(double) * 3 * n_orb * ndiag))) return st;
+    if (ndiag > 0 && (st = dd.alloc(sizeof(double) * 3 * n_orb * (ndiag + 1)))) return st;
+    if (ndiag > 0 && (st = mon.alloc(2 * sizeof(int)))) return st;
     // work on a non-blocking stream ordered after the caller's stream
     cudaStream_t s = user ? user : c->own;
     if (!user) {
         CUDA_TRY(cudaEventRecord(c->ev_a, 0));
         CUDA_TRY(cudaStreamWaitEvent(s, c->ev_a, 0));
     }
-    auto one_step = [&](cudaStream_t ss) {
-        if (c->prec == ABC_FP64) step_impl<double>(c, psi, aux, V, n_orb, dt, mf, ss);
+    const bool fused = fused_ok(c, n_orb);
+    if (fused && (st = ensure_fused_workspace(c))) return st;
+    // fused steps alternate between psi and the context's alternate buffer: step n (from
+    // 1) reads psi and writes alt when n is odd, the reverse when n is even
+    auto one_step = [&](cudaStream_t ss, int parity) {
+        if (fused) {
+            if (parity) step_fused(c, psi, c->alt.p, aux, V, n_orb, dt, mf, ss);
+            else step_fused(c, c->alt.p, psi, aux, V, n_orb, dt, mf, ss);
+        } else if (c->prec == ABC_FP64) step_impl<double>(c, psi, aux, V, n_orb, dt, mf, ss);
         else step_impl<float>(c, psi, aux, V, n_orb, dt, mf, ss);
     };
+    auto state_after = [&](long long n) -> const void* { return fused && (n & 1) ? c->alt.p : psi; };
+    // divergence monitor (Thm 3.1 / Thm 3.2 give W as the quantity that may not grow):
+    // proven for order 0 and for the order-1 limit fit at radius 1 (W^{n+1} <= W^n up to
+    // a per-step slack for rounding), otherwise W may not pass twice its start value
+    const bool proven = c->params.order == 0 ||
+                        (c->params.order == 1 && c->params.fit1 == ABC_FIT1_LIMIT && c->geo.R == 1);
+    const double slack = (c->prec == ABC_FP64 ? 1e-12 : 1e-6) * diag_every;
     auto one_diag = [&](long long row, cudaStream_t ss) {
         double* o = dd.as<double>() + row * 3 * n_orb;
-        if (c->prec == ABC_FP64) diag_impl<double>(c, psi, aux, V, n_orb, mf, o, ss);
-        else diag_impl<float>(c, psi, aux, V, n_orb, mf, o, ss);
+        const void* cur = state_after(row * diag_every);
+        if (c->prec == ABC_FP64) diag_impl<double>(c, cur, aux, V, n_orb, mf, o, ss);
+        else diag_impl<float>(c, cur, aux, V, n_orb, mf, o, ss);
+        if (row > 0) {
+            dev::diag_monitor<<<1, 128, 0, ss>>>(dd.as<double>(), row, n_orb, proven ? 1 : 0, slack, mon.as<int>());
+            c->launches += 1;
+        }
     };
+    if (ndiag > 0) {
+        const int init[2] = {INT_MAX, -1};
+        CUDA_TRY(cudaMemcpyAsync(mon.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+        one_diag(0, s);
+    }
     const bool use_graph = !c->profiling && nsteps >= 1;
     if (use_graph) {
-        abc_ctx::Key k{psi, aux, V, n_orb, dt, mf != nullptr, mf ? mf->a : 0, mf ? mf->b : 0, mf ? mf->alpha : 0, s};
+        abc_ctx::Key k;
+        std::memset(&k, 0, sizeof(k));              // padding included: the key is compared bytewise
+        k.psi = psi; k.aux = aux; k.V = V; k.n_orb = n_orb; k.dt = dt; k.mf = mf != nullptr;
+        k.a = mf ? mf->a : 0; k.b = mf ? mf->b : 0; k.alpha = mf ? mf->alpha : 0; k.s = s; k.fused = fused ? 1 : 0;
         const bool same = c->gexec && !std::memcmp(&k, &c->key, sizeof(k));
         if (!same) {
-            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-            cudaGraph_t graph;
-            CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            const long long before = c->launches;
-            one_step(s);
-            c->graph_kernels = c->launches - before;
-            c->launches = before;
-            cudaError_t le = cudaGetLastError();
-            cudaError_t ce = cudaStreamEndCapture(s, &graph);
-            if (le != cudaSuccess || ce != cudaSuccess)
-                return fail(ABC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ce));
-            cudaError_t ie = cudaGraphInstantiate(&c->gexec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ie != cudaSuccess) { c->gexec = nullptr; return fail(ABC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie)); }
+            for (cudaGraphExec_t* ge : {&c->gexec, &c->gexec_b})
+                if (*ge) { cudaGraphExecDestroy(*ge); *ge = nullptr; }
+            for (int par = 1; par >= (fused ? 0 : 1); --par) {
+                cudaGraph_t graph;
+                CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                const long long before = c->launches;
+                one_step(s, par);
+                c->graph_kernels = c->launches - before;
+                c->launches = before;
+                cudaError_t le = cudaGetLastError();
+                cudaError_t ce = cudaStreamEndCapture(s, &graph);
+                if (le != cudaSuccess || ce != cudaSuccess)
+                    return fail(ABC_ERR_CUDA,
+                                std::string("graph capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ce));
+                cudaGraphExec_t* ge = par ? &c->gexec : &c->gexec_b;
+                cudaError_t ie = cudaGraphInstantiate(ge, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ie != cudaSuccess) {
+                    *ge = nullptr;
+                    return fail(ABC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+                }
+            }
             c->key = k;
         }
     }
     for (long long n = 1; n <= nsteps; ++n) {
+        const int par = (int)(n & 1) | (fused ? 0 : 1);
         if (use_graph) {
-            CUDA_TRY(cudaGraphLaunch(c->gexec, s));
+            CUDA_TRY(cudaGraphLaunch(par ? c->gexec : c->gexec_b, s));
             c->launches += c->graph_kernels;
         } else {
-            one_step(s);
+            one_step(s, par);
         }
-        if (diag_every > 0 && n % diag_every == 0) one_diag(n / diag_every - 1, s);
+        if (diag_every > 0 && n % diag_every == 0) one_diag(n / diag_every, s);
     }
+    if (fused && (nsteps & 1))                   // the result of an odd count is in alt
+        CUDA_TRY(cudaMemcpyAsync(psi, c->alt.p, (size_t)c->nvox * n_orb * cplx_bytes(c), cudaMemcpyDeviceToDevice, s));
     st = last_launch_status();
     if (st) return st;
+    c->steps_done += nsteps;
+    c->t_done += (double)nsteps * dt;
     if (ndiag > 0) {
-        CUDA_TRY(cudaMemcpyAsync(diag_out, dd.p, sizeof(double) * 3 * n_orb * ndiag, cudaMemcpyDeviceToHost, s));
+        int bad[2] = {INT_MAX, -1};
+        CUDA_TRY(cudaMemcpyAsync(diag_out, dd.as<double>() + 3 * n_orb, sizeof(double) * 3 * n_orb * ndiag,
+                                 cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(bad, mon.p, sizeof(bad), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         finish_diag(c, diag_out, ndiag * n_orb);
         if ((st = check_device_flag(c, s))) return st;
+        if (bad[0] != INT_MAX) {
+            const double* d = diag_out + ((long long)(bad[0] - 1) * n_orb + bad[1]) * 3;
+            char msg[256];
+            std::snprintf(msg, sizeof(msg),
+                          "divergence monitor: W of orbital %d %s at step %lld of the run (W = %.6e)", bad[1],
+                          proven ? "grew" : "passed twice its start value", (long long)bad[0] * diag_every, d[1]);
+            return fail(ABC_ERR_UNSTABLE, msg);
+        }
     }
     if (!user) {
         CUDA_TRY(cudaEventRecord(c->ev_b, s));
@@ -1312,6 +1559,123 @@ extern "C" int abc_adjoint_run(abc_ctx* ctx, const void* psi0, const void* V, in
     return adjoint_impl<float>(ctx, psi0, V, n_orb, dt, nsteps, ckpt_every, J_out, dJdV, s);
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint / resume
+// ---------------------------------------------------------------------------
+namespace {
+struct StateHeader {
+    char magic[8];                   // "ABCSTATE"
+    uint32_t version, header_bytes;
+    int32_t nx, ny, nz, radius, order, precision, fit1, n_orb, n_gamma, reserved;
+    double h, s, s1b, s2[4];
+    int64_t steps_done;
+    double t_done;
+    uint64_t psi_bytes, aux_bytes, checksum;
+};
+const char kStateMagic[8] = {'A', 'B', 'C', 'S', 'T', 'A', 'T', 'E'};
+
+uint64_t aux_bytes_of(const abc_ctx* c, int n_orb) {
+    const uint64_t per = c->params.order == 2 ? 2 : c->params.order == 1 ? 1 : 0;
+    return per * (uint64_t)c->geo.n_gamma * n_orb * cplx_bytes(c);
+}
+
+// 64-bit FNV-1a over 8-byte words, then the tail bytes.
+uint64_t payload_hash(const unsigned char* p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+        uint64_t w;
+        std::memcpy(&w, p + i, 8);
+        h = (h ^ w) * 1099511628211ull;
+    }
+    for (; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+    return h;
+}
+
+StateHeader make_header(const abc_ctx* c, int n_orb) {
+    StateHeader hd{};
+    std::memcpy(hd.magic, kStateMagic, 8);
+    hd.version = 1;
+    hd.header_bytes = sizeof(StateHeader);
+    hd.nx = c->grid.nx; hd.ny = c->grid.ny; hd.nz = c->grid.nz; hd.radius = c->geo.R;
+    hd.order = c->params.order; hd.precision = c->prec; hd.fit1 = c->params.fit1;
+    hd.n_orb = n_orb; hd.n_gamma = c->geo.n_gamma;
+    hd.h = c->grid.h; hd.s = c->blocks.s; hd.s1b = c->params.s1b;
+    for (int q = 0; q < 4; ++q) hd.s2[q] = c->params.order == 2 ? c->params.s2[q] : 0.0;
+    hd.psi_bytes = (uint64_t)c->nvox * n_orb * cplx_bytes(c);
+    hd.aux_bytes = aux_bytes_of(c, n_orb);
+    return hd;
+}
+}  // namespace
+
+extern "C" int abc_state_size(const abc_ctx* ctx, int n_orb, size_t* bytes) {
+    if (!ctx || !bytes) return fail(ABC_ERR_ARG, "null argument");
+    if (n_orb < 1 || n_orb > ctx->params.max_orbitals) return fail(ABC_ERR_ARG, "n_orb outside [1, max_orbitals]");
+    const StateHeader hd = make_header(ctx, n_orb);
+    *bytes = sizeof(StateHeader) + hd.psi_bytes + hd.aux_bytes;
+    return ABC_OK;
+}
+
+extern "C" int abc_get_state(const abc_ctx* ctx, const void* psi, const void* aux, int n_orb, void* host_dst,
+                             size_t bytes, void* stream) {
+    size_t need = 0;
+    int st = abc_state_size(ctx, n_orb, &need);
+    if (st) return st;
+    if (!psi || !host_dst) return fail(ABC_ERR_ARG, "null psi or destination");
+    if (ctx->params.order >= 1 && !aux) return fail(ABC_ERR_ARG, "orders 1 and 2 need the auxiliary buffer");
+    if (bytes < need) return fail(ABC_ERR_ARG, "destination smaller than abc_state_size");
+    StateHeader hd = make_header(ctx, n_orb);
+    hd.steps_done = ctx->steps_done;
+    hd.t_done = ctx->t_done;
+    unsigned char* dst = static_cast<unsigned char*>(host_dst);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(dst + sizeof(hd), psi, hd.psi_bytes, cudaMemcpyDeviceToHost, s));
+    if (hd.aux_bytes) CUDA_TRY(cudaMemcpyAsync(dst + sizeof(hd) + hd.psi_bytes, aux, hd.aux_bytes, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    hd.checksum = payload_hash(dst + sizeof(hd), hd.psi_bytes + hd.aux_bytes);
+    std::memcpy(dst, &hd, sizeof(hd));
+    return ABC_OK;
+}
+
+extern "C" int abc_set_state(abc_ctx* ctx, void* psi, void* aux, int n_orb, const void* host_src, size_t bytes,
+                             void* stream) {
+    size_t need = 0;
+    int st = abc_state_size(ctx, n_orb, &need);
+    if (st) return st;
+    if (!psi || !host_src) return fail(ABC_ERR_ARG, "null psi or source");
+    if (ctx->params.order >= 1 && !aux) return fail(ABC_ERR_ARG, "orders 1 and 2 need the auxiliary buffer");
+    if (bytes < sizeof(StateHeader)) return fail(ABC_ERR_ARG, "state blob shorter than its header");
+    StateHeader hd;
+    std::memcpy(&hd, host_src, sizeof(hd));
+    const StateHeader want = make_header(ctx, n_orb);
+    if (std::memcmp(hd.magic, kStateMagic, 8) || hd.version != 1 || hd.header_bytes != sizeof(StateHeader))
+        return fail(ABC_ERR_ARG, "not a state blob of this library version");
+    if (hd.nx != want.nx || hd.ny != want.ny || hd.nz != want.nz || hd.radius != want.radius || hd.h != want.h ||
+        hd.order != want.order || hd.precision != want.precision || hd.fit1 != want.fit1 || hd.s != want.s ||
+        hd.s1b != want.s1b || std::memcmp(hd.s2, want.s2, sizeof(hd.s2)) || hd.n_orb != want.n_orb ||
+        hd.n_gamma != want.n_gamma ||
+        hd.psi_bytes != want.psi_bytes || hd.aux_bytes != want.aux_bytes)
+        return fail(ABC_ERR_ARG, "state blob was written by a context with another grid, ABC, precision or orbital count");
+    if (bytes < need) return fail(ABC_ERR_ARG, "state blob truncated");
+    const unsigned char* src = static_cast<const unsigned char*>(host_src);
+    if (payload_hash(src + sizeof(hd), hd.psi_bytes + hd.aux_bytes) != hd.checksum)
+        return fail(ABC_ERR_ARG, "state blob checksum mismatch (corrupted)");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(psi, src + sizeof(hd), hd.psi_bytes, cudaMemcpyHostToDevice, s));
+    if (hd.aux_bytes) CUDA_TRY(cudaMemcpyAsync(aux, src + sizeof(hd) + hd.psi_bytes, hd.aux_bytes, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    ctx->steps_done = hd.steps_done;
+    ctx->t_done = hd.t_done;
+    return ABC_OK;
+}
+
+extern "C" int abc_progress(const abc_ctx* ctx, long long* steps, double* t) {
+    if (!ctx || !steps || !t) return fail(ABC_ERR_ARG, "null argument");
+    *steps = ctx->steps_done;
+    *t = ctx->t_done;
+    return ABC_OK;
+}
+
 extern "C" int abc_get_matrices(const abc_ctx* ctx, int which, void* host_dst, size_t bytes) {
     if (!ctx || !host_dst) return fail(ABC_ERR_ARG, "null argument");
     const size_t n = ctx->geo.n_gamma;
@@ -1377,14 +1741,23 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
                 x += (double)ctx->tci.R[k] * ctx->tci.m[k] * n_orb;
             }
             const int ns = ctx->tc_b[n_orb].nsplit;
-            *bytes = a * 4 * 4 + x * 6 * 4 + x * ns * 8;
+            const double eb = ctx->tc_f16 ? 2.0 : 4.0;        // bytes per split-plane element
+            *bytes = a * 4 * eb + x * 6 * eb + x * ns * 8;
             return ABC_OK;
         } else {
             for (int p = 0; p < ctx->bi.n; ++p) entries += (double)ctx->bi.nseg * ctx->bi.m[p] * ctx->bi.m[p];
         }
         *bytes = entries * cb + 2.0 * ctx->geo.n_gamma * n_orb * cb;
     } else if (kernel == ABC_KERNEL_STENCIL) {
-        *bytes = (double)ctx->nvox * (3.0 * n_orb * cb + ctx->real_bytes);
+        if (fused_ok(ctx, n_orb))   // the time-fused pass: y in, u^4 out, V, and the band values it stores
+            *bytes = (double)ctx->nvox * (2.0 * n_orb * cb + ctx->real_bytes) +
+                     (double)n_orb * cb *
+                         (dev::band_nodes(ctx->geo.nx, ctx->geo.ny, ctx->geo.nz, 1) +
+                          (dev::band_nodes(ctx->geo.nx, ctx->geo.ny, ctx->geo.nz, 2) - ctx->geo.n_gamma) +
+                          (dev::band_nodes(ctx->geo.nx, ctx->geo.ny, ctx->geo.nz, 3) -
+                           dev::band_nodes(ctx->geo.nx, ctx->geo.ny, ctx->geo.nz, 1)));
+        else
+            *bytes = (double)ctx->nvox * (3.0 * n_orb * cb + ctx->real_bytes);
     } else {
         return fail(ABC_ERR_ARG, "unknown kernel");
     }
@@ -1402,28 +1775,53 @@ extern "C" int abc_kernel_flops(const abc_ctx* ctx, int kernel, int n_orb, doubl
     return ABC_OK;
 }
 
+namespace {
+void drop_graphs(abc_ctx* ctx) {
+    if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+    if (ctx->gexec_b) { cudaGraphExecDestroy(ctx->gexec_b); ctx->gexec_b = nullptr; }
+}
+}  // namespace
+
 extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
     if (!ctx) return fail(ABC_ERR_ARG, "null context");
     if (key == ABC_TUNE_L2_KEEP_TILES) {
         if (value < 0) return fail(ABC_ERR_ARG, "keep count must be >= 0");
         ctx->l2_keep_tiles = value;
-        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        drop_graphs(ctx);
         return ABC_OK;
     }
     if (key == ABC_TUNE_PDL) {
         ctx->pdl = value != 0;
-        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        drop_graphs(ctx);
         return ABC_OK;
     }
     if (key == ABC_TUNE_CHAIN) {
         ctx->chain = value != 0;
-        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        drop_graphs(ctx);
         return ABC_OK;
     }
     if (key == ABC_TUNE_STENCIL) {
         if (value < 0 || value > 2) return fail(ABC_ERR_ARG, "stencil placement must be 0, 1 or 2");
         ctx->stencil_mode = (int)value;
-        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        drop_graphs(ctx);
+        return ABC_OK;
+    }
+    if (key == ABC_TUNE_GEMM_TILE || key == ABC_TUNE_GEMM_SPLIT) {
+        if (key == ABC_TUNE_GEMM_TILE && (value < 0 || value > 1)) return fail(ABC_ERR_ARG, "GEMM tile must be 0 or 1");
+        if (key == ABC_TUNE_GEMM_SPLIT && (value < 0 || value > 8)) return fail(ABC_ERR_ARG, "GEMM split must be 0..8");
+        if (key == ABC_TUNE_GEMM_TILE) ctx->tc_wide = value == 0;
+        else ctx->tc_split = (int)value;
+        drop_graphs(ctx);
+        if (ctx->tc) {
+            CUDA_TRY(cudaDeviceSynchronize());       // the old work lists may be in use
+            return build_tc_plans(ctx);
+        }
+        return ABC_OK;
+    }
+    if (key == ABC_TUNE_FUSED) {
+        if (value < -1 || value > 1) return fail(ABC_ERR_ARG, "fused stencil must be -1 (auto), 0 or 1");
+        ctx->fused_mode = (int)value;
+        drop_graphs(ctx);
         return ABC_OK;
     }
     return fail(ABC_ERR_ARG, "unknown tuning key");
@@ -1436,6 +1834,9 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_PDL) { *value = ctx->pdl ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_CHAIN) { *value = ctx->chain ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL) { *value = ctx->stencil_mode; return ABC_OK; }
+    if (key == ABC_TUNE_FUSED) { *value = ctx->fused_mode; return ABC_OK; }
+    if (key == ABC_TUNE_GEMM_TILE) { *value = ctx->tc_wide ? 0 : 1; return ABC_OK; }
+    if (key == ABC_TUNE_GEMM_SPLIT) { *value = ctx->tc_split; return ABC_OK; }
     return fail(ABC_ERR_ARG, "unknown tuning key");
 }
 
@@ -1448,6 +1849,9 @@ extern "C" int abc_launch_count(const abc_ctx* ctx, long long* launches) {
 extern "C" void abc_destroy(abc_ctx* ctx) {
     if (!ctx) return;
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->gexec_b) cudaGraphExecDestroy(ctx->gexec_b);
+    for (auto e : ctx->ev_fz)
+        if (e) cudaEventDestroy(e);
     for (auto& p : ctx->prof)
         for (auto e : p.ev) cudaEventDestroy(e);
     if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);

@@ -66,9 +66,15 @@ struct abc_ctx {
     // order 1: the stencil of a stage runs on `side`, concurrently with the boundary chain
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    // graph cache
-    cudaGraphExec_t gexec = nullptr;
-    struct Key { const void *psi, *aux, *V; int n_orb; double dt; int mf; double a, b, alpha; cudaStream_t s; } key{};
+    // order-1 steps with the interior stencil fused in time (stencil_fused.cuh): the
+    // third stage buffer, the alternate state buffer of abc_run, events, grid
+    int fused_mode = 0;              // ABC_TUNE_FUSED: 0 off (default), 1 on, -1 on for n_orb >= 2
+    abc::DevBuf Tp3, alt;
+    cudaEvent_t ev_fz[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int fused_grid = 0;
+    // graph cache (gexec_b: the second graph of a fused run, alt -> psi)
+    cudaGraphExec_t gexec = nullptr, gexec_b = nullptr;
+    struct Key { const void *psi, *aux, *V; int n_orb; double dt; int mf; double a, b, alpha; cudaStream_t s; int fused; } key{};
     // one-orbital complex64 contraction on symmetric packed tiles
     bool sym = false;
     abc::dev::SymInfo si{};
@@ -84,6 +90,11 @@ struct abc_ctx {
     bool tc = false;
     abc::dev::TcInfo tci{};
     abc::DevBuf tc_apack, tc_tiles, tc_cols, tc_bpack, tc_part;
+    bool tc_f16 = false;             // ABC_C64_SPLIT_FP16: kind::f16 operands with power-of-two scales
+    bool tc_wide = true;             // GEMM tiles: 96 columns, one CTA per SM (else 64, two per SM)
+    int tc_split = 0;                // GEMM K splits: 0 = about two items per CTA slot
+    int tc_ncols = 0;                // right-hand sides over all classes (column scales per orbital)
+    abc::DevBuf tc_colexp;           // TC_F16: per-column scale exponents of the current contraction
     struct TcPlan {
         int tile_off = 0, tile_cnt = 0, cols_off = 0, cols_cnt = 0, max_nkb = 1, nsplit = 1;
         int grid = 0, off_base = 0;     // CTAs of the persistent GEMM and their item offsets in tc_item_off
@@ -91,6 +102,10 @@ struct abc_ctx {
     abc::DevBuf tc_items, tc_item_off;
     std::vector<TcPlan> tc_b;                    // launch plan of each orbital count b (index b)
     int tc_sms = 0;
+    // progress of the state the context last advanced (steps and time), kept by
+    // abc_step / abc_run and restored by abc_set_state
+    long long steps_done = 0;
+    double t_done = 0.0;
     // launch accounting
     long long launches = 0;
     long long graph_kernels = 0;

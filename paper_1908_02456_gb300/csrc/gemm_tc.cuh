@@ -20,6 +20,15 @@
 // (-Xi, Xr, Xi) for S and (Xr, Xi, -Xr) for conj(S), hi parts then lo parts, so both
 // width-2N operands of a product are windows of two adjacent planes.
 //
+// The split-FP16 form (TC_F16) runs the same products with FP16 hi + lo operands on
+// kind::f16 (twice the TF32 rate): a K block is then 32 elements deep in the same
+// 64-byte rows, so one MMA (K = 16) still spans two core matrices along K.  FP16
+// keeps TF32's 10 mantissa bits but not its exponent range, so each class block is
+// scaled by a power of two 2^es (its largest part near 2^14, on the host) and each
+// right-hand-side column by 2^ec (tc_colexp, per contraction); the epilogue
+// multiplies by 2^-(es + ec).  Power-of-two scales are exact, so the products carry
+// the same rounding as 3xTF32.
+//
 // gemm_tc is persistent: one CTA per SM works through its own list of (output tile,
 // K split) items, balanced by the host.  Warp 0 streams the A and X chunks of all its
 // items through one 3-stage ring with 1D bulk copies (mbarrier completion), warp 1
@@ -34,23 +43,45 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_fp16.h>
+
 #include "sym_gemv.cuh"
 
 namespace abc {
 namespace dev {
 
+constexpr int TC_TF32 = 0;                         // kind::tf32, K block of 16 four-byte elements
+constexpr int TC_F16 = 1;                          // kind::f16, K block of 32 two-byte elements
+template <int KIND>
+struct TcKind {
+    static constexpr int KB = KIND == TC_F16 ? 32 : 16;     // K elements per 64-byte row
+    static constexpr int EB = KIND == TC_F16 ? 2 : 4;       // bytes per element
+};
+
 constexpr int TC_M = 128;
-constexpr int TC_KB = 16;                          // K elements per pipeline stage
-constexpr int TC_NMAX = 96;                        // output columns per tile (accumulator 2 TC_NMAX)
-constexpr int TC_STAGES = 3;
+constexpr int TC_KB = 16;                          // K elements per pipeline stage (TF32)
+constexpr int TC_NMAX = 96;                        // largest output tile width (accumulator 2 TC_NMAX)
 constexpr int TC_THREADS = 192;                    // producer, MMA issuer, four epilogue warps
 constexpr uint32_t TC_A_PLANE = TC_M * TC_KB * 4;  // 8 KB
 constexpr uint32_t TC_A_BYTES = 4 * TC_A_PLANE;    // 32 KB per (tile, K block)
 constexpr int TC_B_PLANES = 6;
 constexpr uint32_t TC_B_PLANE = TC_NMAX * TC_KB * 4;
-constexpr uint32_t TC_B_BYTES = TC_B_PLANES * TC_B_PLANE;   // 36 KB at N = 96
-constexpr size_t TC_SMEM = (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + 1024;
+constexpr uint32_t TC_B_BYTES = TC_B_PLANES * TC_B_PLANE;   // 36 KB: the packed X chunk stride in global memory
 constexpr int TC_MAX_SPLIT = 8;
+
+// Tile configurations of the persistent GEMM (chosen per shape by the autotuner):
+// NMX output columns at most per tile, STG ring stages, CPS resident CTAs per SM.
+// TMEM holds two accumulators of 2 NMX columns (rounded up to a power of two).
+template <int NMX, int STG, int CPS>
+struct TcCfg {
+    static constexpr int nmax = NMX, stages = STG, cps = CPS;
+    static constexpr uint32_t b_stage = (uint32_t)TC_B_PLANES * NMX * 64;
+    static constexpr uint32_t tmem_cols = 4 * NMX > 256 ? 512 : 4 * NMX > 128 ? 256 : 128;
+    static constexpr uint32_t buf_cols = tmem_cols / 2;
+    static constexpr size_t smem = (size_t)STG * (TC_A_BYTES + b_stage) + 256;
+};
+typedef TcCfg<96, 3, 1> TcWide;                    // 96 columns, one CTA per SM
+typedef TcCfg<64, 2, 2> TcNarrow;                  // 64 columns, two CTAs per SM
 constexpr long long TC_WAIT_LIMIT = 1ll << 24;
 
 // Byte offset of element (row r, k) inside a K-major no-swizzle plane of 16-deep
@@ -58,6 +89,19 @@ constexpr long long TC_WAIT_LIMIT = 1ll << 24;
 __host__ __device__ inline uint32_t tc_core_offset(int r, int k) {
     return (uint32_t)((r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
 }
+// The same for two-byte elements in 32-deep K blocks (8 elements per core-matrix row).
+__host__ __device__ inline uint32_t tc_core_offset_f16(int r, int k) {
+    return (uint32_t)((r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// 2^e as a float for |e| <= 126 (exact: exponent bits only).
+__host__ __device__ inline float tc_exp2i(int e) {
+    union { uint32_t u; float f; } v;
+    v.u = (uint32_t)(127 + e) << 23;
+    return v.f;
+}
+constexpr int TC_COLEXP_MAX = 126;                 // |ec| bound of the column scales (float range)
+constexpr int TC_TARGET_EXP = 14;                  // scaled parts below 2^14 (FP16 max 65504)
 
 // Output tile: class, first row, first column of the class's R*b columns, width, and
 // the first of its packed X chunks (one per K block).
@@ -75,6 +119,9 @@ struct TcInfo {
     int moff[SYM_CMAX][3];
     int nkb[SYM_CMAX];                 // K blocks of the class
     long long abase[SYM_CMAX];         // first A chunk (32 KB units) of the class
+    int es[SYM_CMAX];                  // TC_F16: the class block is stored times 2^es
+    int rsum[SYM_CMAX];                // right-hand sides of the classes before this one
+    int ncls;
 };
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
@@ -86,17 +133,27 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
     return d;                                      // base offset 0, no swizzle
 }
 
-// kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = n.
+// D = F32, A = B = TF32 (kind::tf32) or F16 (kind::f16), both K-major, M = 128, N = n.
+template <int KIND>
 __device__ __forceinline__ uint32_t tc_idesc(int n) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+    const uint32_t fmt = KIND == TC_F16 ? 0u : 2u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
 
+template <int KIND>
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
+    if constexpr (KIND == TC_F16)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
 }
 
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
@@ -134,10 +191,13 @@ struct TcItem {
 // X -> packed TF32 planes of every K block of a column range, in the shared-memory
 // image the GEMM copies with one bulk copy per K block: hi planes (-Xi, Xr, Xi), then
 // lo planes in the same order (conj: (Xr, Xi, -Xr)).  Grid (column ranges, largest
-// nkb), 128 threads; x orbital-major (o * ng + j).
-static __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCols* __restrict__ cols, int n_orb,
-                                                        int ng, const float2* __restrict__ x, int conj,
-                                                        float* __restrict__ bpack) {
+// nkb), 128 threads; x orbital-major (o * ng + j).  TC_F16: FP16 hi + lo of the
+// column scaled by 2^colexp[column], 8 elements per 16-byte core-matrix row.
+template <int KIND>
+__global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCols* __restrict__ cols, int n_orb, int ng,
+                                                 const float2* __restrict__ x, int conj, float* __restrict__ bpack,
+                                                 const int* __restrict__ colexp) {
+    constexpr int EPR = 16 / TcKind<KIND>::EB;          // elements per 16-byte row
     const TcCols cr = cols[blockIdx.x];
     const int c = cr.cls, kb = blockIdx.y;
     if (kb >= info.nkb[c]) return;
@@ -147,49 +207,119 @@ static __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCol
         const int cc = (it & 7) | ((it >> 5) << 3), q = (it >> 3) & 3;
         const int col = cr.col0 + cc;
         const int k = col / n_orb, o = col - k * n_orb;
-        float re[4], im[4];
+        float sc = 1.0f;
+        if constexpr (KIND == TC_F16)
+            if (k < info.R[c]) sc = tc_exp2i(colexp[info.rsum[c] * n_orb + col]);
+        float re[EPR], im[EPR];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int row = kb * TC_KB + 4 * q + e;
+        for (int e = 0; e < EPR; ++e) {
+            const int row = kb * TcKind<KIND>::KB + EPR * q + e;
             float2 v = make_float2(0.f, 0.f);
             if (k < info.R[c] && row < m) v = __ldg(x + (size_t)o * ng + info.moff[c][k] + row);
-            re[e] = v.x;
-            im[e] = v.y;
+            re[e] = v.x * sc;
+            im[e] = v.y * sc;
         }
         // planes 0-2 (hi) and 3-5 (lo) of this 16-byte row
-        uint4 pl[6];
-        uint32_t* w[6] = {&pl[0].x, &pl[1].x, &pl[2].x, &pl[3].x, &pl[4].x, &pl[5].x};
+        uint32_t w[6][4];
+        if constexpr (KIND == TC_F16) {
+            const uint32_t sgn = 0x80008000u;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const uint32_t rh = tf32_hi(re[e]), ih = tf32_hi(im[e]);
-            const uint32_t rl = tf32_hi(re[e] - __uint_as_float(rh)), il = tf32_hi(im[e] - __uint_as_float(ih));
+            for (int e2 = 0; e2 < 4; ++e2) {
+                const __half2 rh = __floats2half2_rn(re[2 * e2], re[2 * e2 + 1]);
+                const __half2 ih = __floats2half2_rn(im[2 * e2], im[2 * e2 + 1]);
+                const float2 rhf = __half22float2(rh), ihf = __half22float2(ih);
+                const __half2 rl = __floats2half2_rn(re[2 * e2] - rhf.x, re[2 * e2 + 1] - rhf.y);
+                const __half2 il = __floats2half2_rn(im[2 * e2] - ihf.x, im[2 * e2 + 1] - ihf.y);
+                const uint32_t urh = *reinterpret_cast<const uint32_t*>(&rh), uih = *reinterpret_cast<const uint32_t*>(&ih);
+                const uint32_t url = *reinterpret_cast<const uint32_t*>(&rl), uil = *reinterpret_cast<const uint32_t*>(&il);
+                if (conj) {
+                    w[0][e2] = urh; w[1][e2] = uih; w[2][e2] = urh ^ sgn;
+                    w[3][e2] = url; w[4][e2] = uil; w[5][e2] = url ^ sgn;
+                } else {
+                    w[0][e2] = uih ^ sgn; w[1][e2] = urh; w[2][e2] = uih;
+                    w[3][e2] = uil ^ sgn; w[4][e2] = url; w[5][e2] = uil;
+                }
+            }
+        } else {
             const uint32_t sgn = 0x80000000u;
-            if (conj) {
-                w[0][e] = rh; w[1][e] = ih; w[2][e] = rh ^ sgn;
-                w[3][e] = rl; w[4][e] = il; w[5][e] = rl ^ sgn;
-            } else {
-                w[0][e] = ih ^ sgn; w[1][e] = rh; w[2][e] = ih;
-                w[3][e] = il ^ sgn; w[4][e] = rl; w[5][e] = il;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t rh = tf32_hi(re[e]), ih = tf32_hi(im[e]);
+                const uint32_t rl = tf32_hi(re[e] - __uint_as_float(rh)), il = tf32_hi(im[e] - __uint_as_float(ih));
+                if (conj) {
+                    w[0][e] = rh; w[1][e] = ih; w[2][e] = rh ^ sgn;
+                    w[3][e] = rl; w[4][e] = il; w[5][e] = rl ^ sgn;
+                } else {
+                    w[0][e] = ih ^ sgn; w[1][e] = rh; w[2][e] = ih;
+                    w[3][e] = il ^ sgn; w[4][e] = rl; w[5][e] = il;
+                }
             }
         }
-        // planes of a chunk are N * 64 bytes apart (only the tile's N rows are stored)
-        const uint32_t off = tc_core_offset(cc, 4 * q), pb = (uint32_t)N * 64;
+        // planes of a chunk are N * 64 bytes apart (only the tile's N rows are stored);
+        // the 16-byte row of column cc and row group q sits where element (cc, EPR q) does
+        const uint32_t off = KIND == TC_F16 ? tc_core_offset_f16(cc, EPR * q) : tc_core_offset(cc, EPR * q);
+        const uint32_t pb = (uint32_t)N * 64;
 #pragma unroll
-        for (int p = 0; p < 6; ++p) *reinterpret_cast<uint4*>(B + p * pb + off) = pl[p];
+        for (int p = 0; p < 6; ++p)
+            *reinterpret_cast<uint4*>(B + p * pb + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+    }
+}
+
+// TC_F16 column scales: for every right-hand-side column of every class (index
+// rsum[c] * n_orb + k * n_orb + o) the exponent ec with max |part| * 2^ec in
+// [2^13, 2^14), clamped to +-TC_COLEXP_MAX (0 for an all-zero column; the largest
+// FP32 subnormals reach 2^-23 after the clamp, still an FP16 value).  One warp per
+// column; x orbital-major.
+static __global__ void __launch_bounds__(256) tc_colexp(TcInfo info, int n_orb, int ng, const float2* __restrict__ x,
+                                                 int* __restrict__ colexp, int ncols) {
+    const int gw = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (gw >= ncols) return;
+    int c = 0;
+    while (c + 1 < info.ncls && gw >= info.rsum[c + 1] * n_orb) ++c;
+    const int col = gw - info.rsum[c] * n_orb;
+    const int k = col / n_orb, o = col - k * n_orb;
+    const float2* p = x + (size_t)o * ng + info.moff[c][k];
+    const int m = info.m[c];
+    uint32_t mx = 0;
+    // eight independent loads in flight per lane
+    for (int r0 = 0; r0 < m; r0 += 256) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int r = r0 + u * 32 + lane;
+            v[u] = r < m ? __ldg(p + r) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            mx = max(mx, max(__float_as_uint(v[u].x) & 0x7fffffffu, __float_as_uint(v[u].y) & 0x7fffffffu));
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+    if (lane == 0) {
+        int e = 0;
+        if (mx != 0) {
+            const int E = (int)(mx >> 23) - 127;              // floor(log2(max)) (subnormals: -127)
+            e = min(TC_COLEXP_MAX, max(-TC_COLEXP_MAX, TC_TARGET_EXP - 1 - E));
+        }
+        colexp[gw] = e;
     }
 }
 
 // One CTA per SM over the items item_off[blockIdx.x] .. item_off[blockIdx.x + 1] of
 // items[]; out + split * split_stride receives each item's (split's) partial product
 // (x, out orbital-major).
-static __global__ void __launch_bounds__(TC_THREADS, 1)
+template <int KIND, typename CFG>
+__global__ void __launch_bounds__(TC_THREADS, CFG::cps)
 gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict__ items,
         const int* __restrict__ item_off, const float* __restrict__ apack, const float* __restrict__ bpack, int n_orb,
-        int ng, int nsplit, long long split_stride, float2* __restrict__ out, int conj, int* __restrict__ err) {
+        int ng, int nsplit, long long split_stride, float2* __restrict__ out, int conj, int* __restrict__ err,
+        const int* __restrict__ colexp) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char* sA = tc_smem;                                       // [stage][4 planes]
+    constexpr int TC_STAGES = CFG::stages;
+    constexpr uint32_t SB = CFG::b_stage;                              // smem bytes of one X stage
     unsigned char* sB = tc_smem + (size_t)TC_STAGES * TC_A_BYTES;      // [stage][6 planes]
-    uint64_t* full = reinterpret_cast<uint64_t*>(tc_smem + (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES));
+    uint64_t* full = reinterpret_cast<uint64_t*>(tc_smem + (size_t)TC_STAGES * (TC_A_BYTES + SB));
     uint64_t* empty = full + TC_STAGES;
     uint64_t* tfull = empty + TC_STAGES;                               // [2] accumulators ready
     uint64_t* tempty = tfull + 2;                                      // [2] accumulators drained
@@ -211,7 +341,7 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(512)
+                     "r"(CFG::tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -237,7 +367,7 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
                 if (issued >= TC_STAGES) ok &= mbar_wait_bounded(&empty[st], (uint32_t)((issued / TC_STAGES - 1) & 1));
                 mbar_expect_tx(&full[st], TC_A_BYTES + b_bytes);
                 bulk_g2s(sA + (size_t)st * TC_A_BYTES, achunk + (size_t)kb * (TC_A_BYTES / 4), TC_A_BYTES, &full[st]);
-                bulk_g2s(sB + (size_t)st * TC_B_BYTES, bchunk + (size_t)kb * (TC_B_BYTES / 4), b_bytes, &full[st]);
+                bulk_g2s(sB + (size_t)st * SB, bchunk + (size_t)kb * (TC_B_BYTES / 4), b_bytes, &full[st]);
             }
         }
     } else if (tid == 32) {
@@ -253,8 +383,8 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
             const int buf = q & 1;
             if (q >= 2) ok &= mbar_wait_bounded(&tempty[buf], (uint32_t)((q / 2 - 1) & 1));
             tc_fence_after();
-            const uint32_t idesc = tc_idesc(2 * N);
-            const uint32_t d = tmem + buf * 256;                          // [Re | Im], 2N columns
+            const uint32_t idesc = tc_idesc<KIND>(2 * N);
+            const uint32_t d = tmem + buf * CFG::buf_cols;                // [Re | Im], 2N columns
             const uint32_t pb = (uint32_t)N * 64;                         // X plane stride in the chunk
             // windows of two planes: [Xr | Xi] and [-Xi | Xr] (conj: [Xr | Xi] and [Xi | -Xr])
             const uint32_t wr = conj ? 0u : pb, wi = conj ? pb : 0u, lo = 3 * pb;
@@ -262,7 +392,7 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
                 const int st = (int)(g % TC_STAGES);
                 ok &= mbar_wait_bounded(&full[st], (uint32_t)((g / TC_STAGES) & 1));
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(sA + (size_t)st * TC_A_BYTES), b0 = smem_u32(sB + (size_t)st * TC_B_BYTES);
+                const uint32_t a0 = smem_u32(sA + (size_t)st * TC_A_BYTES), b0 = smem_u32(sB + (size_t)st * SB);
 #pragma unroll
                 for (int ks = 0; ks < TC_KB / 8; ++ks) {
                     const uint32_t ko = ks * 256;      // two core matrices along K per MMA
@@ -271,8 +401,12 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
                     const uint64_t brh = tc_desc(b0 + wr + ko), brl = tc_desc(b0 + lo + wr + ko);
                     const uint64_t bih = tc_desc(b0 + wi + ko), bil = tc_desc(b0 + lo + wi + ko);
                     const uint32_t acc0 = (kb > kb0 || ks > 0) ? 1u : 0u;
-                    tc_mma(d, srh, brh, idesc, acc0); tc_mma(d, srh, brl, idesc, 1u); tc_mma(d, srl, brh, idesc, 1u);
-                    tc_mma(d, sih, bih, idesc, 1u); tc_mma(d, sih, bil, idesc, 1u); tc_mma(d, sil, bih, idesc, 1u);
+                    tc_mma<KIND>(d, srh, brh, idesc, acc0);
+                    tc_mma<KIND>(d, srh, brl, idesc, 1u);
+                    tc_mma<KIND>(d, srl, brh, idesc, 1u);
+                    tc_mma<KIND>(d, sih, bih, idesc, 1u);
+                    tc_mma<KIND>(d, sih, bil, idesc, 1u);
+                    tc_mma<KIND>(d, sil, bih, idesc, 1u);
                 }
                 tc_commit(&empty[st]);                // the slot is free once these MMAs are done
             }
@@ -304,8 +438,8 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
             for (int c0 = 0; c0 < N; c0 += 16) {
                 float pr[16], pi[16];
                 if (any) {
-                    tc_ld16(lane_base + buf * 256 + c0, pr);
-                    tc_ld16(lane_base + buf * 256 + N + c0, pi);
+                    tc_ld16(lane_base + buf * CFG::buf_cols + c0, pr);
+                    tc_ld16(lane_base + buf * CFG::buf_cols + N + c0, pi);
                     tc_wait_ld();
                 }
                 if (row < m) {
@@ -313,9 +447,15 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
                     for (int i = 0; i < 16; ++i) {
                         const int col = tile.col0 + c0 + i;
                         const int k = col / n_orb, o = col - k * n_orb;
-                        if (c0 + i < N && k < info.R[c])
-                            dst[(size_t)o * ng + info.moff[c][k] + row] =
-                                any ? make_float2(pr[i], pi[i]) : make_float2(0.f, 0.f);
+                        if (c0 + i < N && k < info.R[c]) {
+                            float2 v = any ? make_float2(pr[i], pi[i]) : make_float2(0.f, 0.f);
+                            if constexpr (KIND == TC_F16) {      // undo the power-of-two scales, one at a time
+                                const float sc = tc_exp2i(-info.es[c]);
+                                const float sx = tc_exp2i(-colexp[info.rsum[c] * n_orb + col]);
+                                v = make_float2(v.x * sc * sx, v.y * sc * sx);
+                            }
+                            dst[(size_t)o * ng + info.moff[c][k] + row] = v;
+                        }
                     }
                 }
             }
@@ -336,7 +476,8 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CFG::tmem_cols)
+                     : "memory");
     }
     if (!ok) atomicExch(err, 1);
 }

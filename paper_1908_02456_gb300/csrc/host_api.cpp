@@ -53,7 +53,7 @@ int check_params(const abc_grid* grid, const abc_params* params) {
         return fail(ABC_ERR_ARG, "fit1 applies to order 1 only");
     if (params->fit1 == ABC_FIT1_TWO_POINT && (!(params->s1b > 0.0) || params->s1b == params->s1))
         return fail(ABC_ERR_ARG, "the two-point fit needs s1b > 0 and s1b != s1");
-    if (params->precision < ABC_FP64 || params->precision > ABC_C64_3XTF32)
+    if (params->precision < ABC_FP64 || params->precision > ABC_C64_SPLIT_FP16)
         return fail(ABC_ERR_ARG, "unknown precision");
     // With radius 3 the order-2 interpolation system is nearly singular (K(s) has
     // condition numbers near 1e8): B1 and B0 come out with entries near 1e7 whose
@@ -61,7 +61,8 @@ int check_params(const abc_grid* grid, const abc_params* params) {
     if (grid->radius == 3 && params->order == 2 && params->precision != ABC_FP64)
         return fail(ABC_ERR_UNSUPPORTED, "the second-order ABC with radius 3 needs ABC_FP64");
     if (params->precision == ABC_C64_SPLIT_BF16)
-        return fail(ABC_ERR_UNSUPPORTED, "the split-bf16 form is not built (use ABC_C64_3XTF32)");
+        return fail(ABC_ERR_UNSUPPORTED,
+                    "the split-bf16 form is not built (use ABC_C64_SPLIT_FP16 or ABC_C64_3XTF32)");
     if (params->max_orbitals < 1 || params->max_orbitals > 65535)
         return fail(ABC_ERR_ARG, "max_orbitals must be in [1, 65535]");
     return ABC_OK;

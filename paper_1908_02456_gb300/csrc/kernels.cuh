@@ -1098,6 +1098,23 @@ __global__ void diag_aux(int n_gamma, int n_orb, const int* __restrict__ gamma_c
     if (threadIdx.x == 0) atomicAdd(out + orb * 3 + 1, s);
 }
 
+// Divergence monitor over the raw diagnostic rows (sums before the h^3 weight:
+// [norm, f^* Q f, energy] per orbital) of a run: row r is compared with row r - 1
+// (proven forms: W may not grow by more than the slack, Thm 3.1 / Thm 3.2 after
+// the time discretisation) or with row 0 (other forms: W may not exceed twice its
+// start), and any non-finite W fails.  The first failing row goes to *bad
+// (atomicMin; the caller initialises it to a large value), its orbital to bad[1].
+static __global__ void diag_monitor(const double* __restrict__ rows, long long r, int n_orb, int proven, double slack,
+                             int* __restrict__ bad) {
+    for (int j = threadIdx.x; j < n_orb; j += blockDim.x) {
+        const double* cur = rows + r * 3 * n_orb + 3 * j;
+        const double* ref = rows + (proven ? r - 1 : 0) * 3 * n_orb + 3 * j;
+        const double w = cur[0] + cur[1], w0 = ref[0] + ref[1];
+        const bool ok = isfinite(w) && (proven ? w <= w0 * (1.0 + slack) : w <= 2.0 * w0);
+        if (!ok && atomicMin(bad, (int)r) > (int)r) bad[1] = j;
+    }
+}
+
 }  // namespace dev
 }  // namespace abc
 

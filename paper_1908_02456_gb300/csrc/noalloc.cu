@@ -18,10 +18,13 @@
 // nothing needs to be cleared between calls.
 //
 // Host code cannot use the array's name as a device address (on the host the
-// symbol is only a stand-in).  The first call on each device therefore looks the
-// address up with cudaGetSymbolAddress, with that device current, and caches it;
-// make that first call before any stream capture, since the lookup is a runtime
-// call that capture does not allow.
+// symbol is only a stand-in).  Every call made outside stream capture therefore
+// looks the address up with cudaGetSymbolAddress, with the context's device
+// current, so the address always belongs to the device's current primary context
+// (it changes after a cudaDeviceReset).  A call made while its stream is being
+// captured cannot make that runtime call and uses the address the last uncaptured
+// call on the device found; make at least one call on each device before any
+// stream capture.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -38,15 +41,21 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-int scratch_for_device(int dev, void** out) {
+int scratch_for_device(int dev, cudaStream_t s, void** out) {
     if (dev < 0 || dev >= kMaxDevices) return abc::fail(ABC_ERR_ARG, "device ordinal out of range");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return abc::fail(ABC_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p)
             return abc::fail(ABC_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
         g_scratch_ptr[dev] = p;
+    } else if (!g_scratch_ptr[dev]) {
+        return abc::fail(ABC_ERR_ARG, "abc_step_noalloc: first call on this device made during stream capture "
+                                      "(make one call outside capture first)");
     }
     *out = g_scratch_ptr[dev];
     return ABC_OK;
@@ -136,9 +145,9 @@ extern "C" int abc_step_noalloc(const abc_ctx* ctx, void* psi, void* aux, const 
     if (e != cudaSuccess) return abc::fail(ABC_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev != ctx->device) return abc::fail(ABC_ERR_ARG, "the context belongs to another device");
     void* scratch = nullptr;
-    int st = scratch_for_device(dev, &scratch);
-    if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    int st = scratch_for_device(dev, s, &scratch);
+    if (st) return st;
     if (ctx->prec == ABC_FP64) step_with_scratch<double>(ctx, psi, aux, V, n_orb, dt, (char*)scratch, s);
     else step_with_scratch<float>(ctx, psi, aux, V, n_orb, dt, (char*)scratch, s);
     e = cudaGetLastError();

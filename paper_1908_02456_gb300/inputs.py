@@ -66,11 +66,11 @@ WORKLOADS = {
     2: Workload(2, "harmonic-64cube-order1-single", 64, 0.4, 1, 1, 1.0, 0.005, 2000,
                 "harmonic_bumps", precision="c64"),
     3: Workload(3, "meanfield-64cube-32orb-order1", 64, 0.4, 32, 1, 1.0, 0.005, 1000,
-                "none", meanfield=(-1.0, 0.8, 1.0 / 6.0), precision="tf32x3"),
+                "none", meanfield=(-1.0, 0.8, 1.0 / 6.0), precision="fp16x3"),
     4: Workload(4, "adjoint-48cube-order1", 48, 0.4, 1, 1, 1.0, 0.005, 1000,
                 "smooth_random", precision="c64"),
     5: Workload(5, "meanfield-96cube-128orb-order1", 96, 0.35, 128, 1, 1.0, 0.004, 500,
-                "none", meanfield=(-1.0, 0.8, 1.0 / 6.0), precision="tf32x3"),
+                "none", meanfield=(-1.0, 0.8, 1.0 / 6.0), precision="fp16x3"),
     # the next-row variants on the benchmark grid and potential
     6: Workload(6, "harmonic-64cube-order2-single", 64, 0.4, 1, 2, 1.0, 0.005, 500,
                 "harmonic_bumps", precision="c64", points=(1.0, 2.0, 3.0, 10.0)),

@@ -1,13 +1,23 @@
-"""Autotuner for the kernels' launch-time knobs.
+"""Autotuner for the kernels' per-shape launch choices.
 
-The one-orbital complex64 contraction streams the boundary tiles once per Horner
-stage.  When the tiles are about the size of L2, keeping a leading part of them in
-L2 (evict_last) lets the next stage read that part from L2 instead of HBM; how much
-to keep depends on the grid and the device.  ``tune(ctx, ...)`` times short
-``abc_run`` calls for a few candidate values on a copy of the caller's state, sets
-the fastest on the context and caches the choice in a JSON file keyed by the
-problem shape and the device name.  Tuning is set-up work: callers run it before
-any timed region.
+The fastest form of a time step depends on the grid, the orbital count, the
+precision and the device, so the library exposes its choices as tuning knobs
+(``abc_set_tuning``) and this module picks them by timing:
+
+* the tensor-core GEMM's tile configuration (``TUNE_GEMM_TILE``: 96-column tiles with
+  one CTA per SM, or 64-column tiles with two) and its K split count
+  (``TUNE_GEMM_SPLIT``: automatic, or 1, 2, 4 splits per output tile);
+* the interior stencil of an order-1 step: the four Horner stages fused in time
+  (``TUNE_FUSED``) or stage by stage, and for the latter where the stencil runs
+  beside the boundary chain (``TUNE_STENCIL``);
+* for one complex64 orbital, the early start of the tiled contraction behind the
+  forward transform (``TUNE_PDL``).
+
+``tune(ctx, psi, aux, V, dt, ...)`` times short ``abc_run`` calls on a copy of the
+caller's state, one knob group after the other (GEMM first, then the stencil form),
+keeps the fastest setting on the context, and caches the choice in a JSON file keyed
+by the device name and the problem shape.  Tuning is set-up work: callers run it
+before any timed region.  Every setting computes the same step up to FP32 rounding.
 """
 from __future__ import annotations
 
@@ -20,8 +30,9 @@ from . import abc
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tune_cache.json")
 
 
-def _key(ctx: abc.Context, n_orb: int, device_name: str) -> str:
-    return f"{device_name}|{ctx.shape}|h={ctx.h}|order={ctx.order}|prec={ctx.precision}|b={n_orb}"
+def _key(ctx: abc.Context, n_orb: int, device_name: str, meanfield) -> str:
+    return (f"{device_name}|{ctx.shape}|h={ctx.h}|order={ctx.order}|prec={ctx.precision}|fit={ctx.fit1}"
+            f"|b={n_orb}|mf={meanfield is not None}")
 
 
 def _load():
@@ -39,47 +50,83 @@ def _save(d):
     os.replace(tmp, CACHE)
 
 
-def candidates(n_tiles: int):
-    """Candidate evict_last tile counts: none, fractions of the tile set, and all."""
-    fr = [0.0, 0.3, 0.45, 0.55, 0.65, 0.75, 0.85, 1.0]
-    return sorted({int(round(f * n_tiles)) for f in fr})
+def knob_groups(ctx: abc.Context, n_orb: int):
+    """The candidate settings, as groups of {knob: value} dicts searched one group at a time."""
+    groups = []
+    tc = ctx.precision in (abc.C64_3XTF32, abc.C64_SPLIT_FP16) and n_orb >= 2 and ctx.order < 2 \
+        and ctx.fit1 == abc.FIT1_LIMIT
+    if tc:
+        groups.append([{abc.TUNE_GEMM_TILE: t, abc.TUNE_GEMM_SPLIT: sp} for t in (0, 1) for sp in (0, 1, 2, 4)])
+    if ctx.order == 1 and ctx.precision != abc.FP64:
+        nx = ctx.shape[0]
+        stencil = [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: m} for m in (0, 2)]
+        if nx % 2 == 0 and min(ctx.shape) >= 8 and ctx.radius == 1:
+            stencil.append({abc.TUNE_FUSED: 1})
+        groups.append(stencil)
+    if n_orb == 1 and ctx.precision != abc.FP64 and ctx.get_tuning(abc.TUNE_TILE_COUNT) > 0:
+        groups.append([{abc.TUNE_PDL: 1}, {abc.TUNE_PDL: 0}])
+    return groups
 
 
-def tune(ctx: abc.Context, psi, aux, V, dt: float, steps: int = 40, repeats: int = 2,
+def _apply(ctx, setting):
+    for k, v in setting.items():
+        ctx.set_tuning(k, v)
+
+
+def tune(ctx: abc.Context, psi, aux, V, dt: float, meanfield=None, steps: int = 8, repeats: int = 2,
          use_cache: bool = True, device_name: Optional[str] = None) -> dict:
-    """Pick ABC_TUNE_L2_KEEP_TILES for this context; returns {"keep": k, "ms_per_step": t, ...}."""
+    """Pick the knobs for this context and orbital count; returns the chosen setting,
+    its step time and the sweep."""
     import torch
     n_orb = psi.shape[0]
-    n_tiles = ctx.get_tuning(abc.TUNE_TILE_COUNT)
-    if n_tiles == 0 or n_orb != 1:
-        return {"keep": 0, "tuned": False, "reason": "no tiled contraction for this context"}
     name = device_name or torch.cuda.get_device_name()
-    key = _key(ctx, n_orb, name)
-    cache = _load() if use_cache else {}
-    if key in cache:
-        ctx.set_tuning(abc.TUNE_L2_KEEP_TILES, cache[key]["keep"])
-        return dict(cache[key], cached=True)
+    key = _key(ctx, n_orb, name, meanfield)
+    if use_cache:
+        cache = _load()
+        if key in cache:
+            setting = {int(k): v for k, v in cache[key]["setting"].items()}
+            _apply(ctx, setting)
+            return dict(cache[key], cached=True)
     p, a = psi.clone(), (aux.clone() if aux is not None else None)
-    results = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for keep in candidates(n_tiles):
-        ctx.set_tuning(abc.TUNE_L2_KEEP_TILES, keep)
-        ctx.run(p, a, V, dt, 3)                     # capture + warm
+
+    def time_setting(setting):
+        _apply(ctx, setting)
+        ctx.run(p, a, V, dt, 2, meanfield=meanfield)        # capture + warm
         best = float("inf")
         for _ in range(repeats):
             torch.cuda.synchronize()
             e0.record()
-            ctx.run(p, a, V, dt, steps)
+            ctx.run(p, a, V, dt, steps, meanfield=meanfield)
             e1.record()
             torch.cuda.synchronize()
             best = min(best, e0.elapsed_time(e1) / steps)
-        results[keep] = best
-    keep = min(results, key=results.get)
-    ctx.set_tuning(abc.TUNE_L2_KEEP_TILES, keep)
-    out = {"keep": keep, "ms_per_step": results[keep], "tiles": n_tiles,
-           "sweep": {str(k): round(v, 5) for k, v in sorted(results.items())}, "tuned": True}
+        return best
+
+    chosen, sweep = {}, {}
+    for group in knob_groups(ctx, n_orb):
+        times = []
+        for cand in group:
+            setting = dict(chosen, **cand)
+            t = time_setting(setting)
+            sweep[json.dumps({str(k): v for k, v in sorted(setting.items())})] = round(t, 5)
+            times.append((t, cand))
+        best = min(times, key=lambda x: x[0])
+        chosen.update(best[1])
+    _apply(ctx, chosen)
+    ms = time_setting(chosen) if chosen else None
+    out = {"setting": {str(k): v for k, v in sorted(chosen.items())}, "ms_per_step": ms, "sweep": sweep,
+           "tuned": True}
     if use_cache:
         cache = _load()
         cache[key] = out
         _save(cache)
     return dict(out, cached=False)
+
+
+def describe(setting: dict) -> dict:
+    """Readable names of a setting returned by tune()."""
+    names = {abc.TUNE_GEMM_TILE: "gemm_tile(0=96 cols x 1 CTA/SM, 1=64 cols x 2 CTAs/SM)",
+             abc.TUNE_GEMM_SPLIT: "gemm_split(0=auto)", abc.TUNE_FUSED: "fused_stencil",
+             abc.TUNE_STENCIL: "stencil_placement", abc.TUNE_PDL: "pdl"}
+    return {names.get(int(k), str(k)): v for k, v in setting.items()}

@@ -66,8 +66,9 @@ def test_adjoint_complex64_vs_fp64(env):
     assert rel(g32, g64) < 1e-4
 
 
+@pytest.mark.parametrize("tc", ["tf32x3", "fp16x3"])
 @pytest.mark.parametrize("order", [0, 1])
-def test_adjoint_tensor_core_vs_fp64(env, order):
+def test_adjoint_tensor_core_vs_fp64(env, order, tc):
     """Three orbitals through the tensor-core contraction (its conjugated form runs in
     the reverse sweep) against the FP64 gradient, next to the FP32 CUDA-core form."""
     torch, abc = env
@@ -77,7 +78,7 @@ def test_adjoint_tensor_core_vs_fp64(env, order):
     psi = np.concatenate([inputs.gaussian_packet(dims, h, (0.4 * j - 0.4, 0, 0.2), (2.0, 1.0 - j, 0.5), 1.2)[None]
                           for j in range(3)]).reshape(3, -1)
     J64, g64 = _gpu_adjoint(torch, abc, dims, h, order, 1.0, "fp64", psi, V, dt, steps, 20)
-    Jtc, gtc = _gpu_adjoint(torch, abc, dims, h, order, 1.0, "tf32x3", psi, V, dt, steps, 20)
+    Jtc, gtc = _gpu_adjoint(torch, abc, dims, h, order, 1.0, tc, psi, V, dt, steps, 20)
     Jc, gc = _gpu_adjoint(torch, abc, dims, h, order, 1.0, "c64", psi, V, dt, steps, 20)
     assert abs(Jtc - J64) < 1e-5 * max(abs(J64), 1e-3)
     # the tensor-core path is as accurate as the FP32 CUDA-core path on the same case

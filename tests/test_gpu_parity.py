@@ -13,7 +13,7 @@ from paper_1908_02456_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "c64": 1e-5, "tf32x3": 1e-5}
+TOL = {"fp64": 1e-10, "c64": 1e-5, "tf32x3": 1e-5, "fp16x3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -100,7 +100,7 @@ def test_harmonic_order1_reduced(torch_cuda, prec):
     assert rel(d, ref_d) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "c64", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "c64", "tf32x3", "fp16x3"])
 def test_meanfield_batched_reduced(torch_cuda, prec):
     """Batched orbitals with the density-dependent potential V = a rho + b rho^(1+alpha)
     (a = -1, b = 0.8, alpha = 1/6), first-order ABC; 5 orbitals (a ragged tail of the
@@ -172,12 +172,13 @@ def test_full_size_lyapunov_c64(torch_cuda):
     assert abs(d[0, 0, 0] - 1.0) < 1e-3
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
 @pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("dims,b", [((22, 22, 22), 48), ((13, 11, 12), 7)])
-def test_tensor_core_contraction_many_tiles(torch_cuda, order, dims, b):
-    """The tensor-core (3xTF32) many-orbital contraction against the FP64 oracle, one
-    step from an unstructured state: on the 22^3 cube the classes span several
-    128-row tiles and 16-deep K blocks, and 3 x 48 columns split into two N tiles
+def test_tensor_core_contraction_many_tiles(torch_cuda, prec, order, dims, b):
+    """The tensor-core many-orbital contraction (3xTF32 and split FP16) against the
+    FP64 oracle, one step from an unstructured state: on the 22^3 cube the classes
+    span several 128-row tiles and K blocks, and 3 x 48 columns split into two N tiles
     (80 + 64); the non-cube has eight R = 1 classes and a 16-column tile holding 7
     orbitals."""
     h, dt = 0.45, 0.005
@@ -187,13 +188,36 @@ def test_tensor_core_contraction_many_tiles(torch_cuda, order, dims, b):
     sy = oracle_system(dims, h, order, 1.0, V)
     f0 = (rng.normal(size=(b, len(sy.G))) + 1j * rng.normal(size=(b, len(sy.G)))) if order == 1 else None
     ref_p, ref_f = sy.step(psi0, f0, dt)
-    p, f, _ = gpu_run(torch_cuda, dims, h, order, 1.0, "tf32x3", psi0, V, dt, 1, aux0=f0)
+    p, f, _ = gpu_run(torch_cuda, dims, h, order, 1.0, prec, psi0, V, dt, 1, aux0=f0)
     assert rel(p, ref_p) < 1e-6
     if order == 1:
         assert rel(f, ref_f) < 1e-6
 
 
-def test_tensor_core_several_items_per_cta(torch_cuda):
+@pytest.mark.parametrize("scale", [1e-20, 1e-6, 1e12])
+def test_split_fp16_column_scales(torch_cuda, scale):
+    """The split-FP16 contraction scales every right-hand-side column by a power of two
+    found per contraction, so its relative accuracy does not depend on the state's
+    magnitude: the linear step of a state (and aux) multiplied by `scale` equals
+    `scale` times the oracle's step, far outside FP16's own range."""
+    dims, h, dt, b = (14, 14, 14), 0.45, 0.005, 12
+    rng = np.random.default_rng(91)
+    psi0 = inputs.random_state(dims, b, rng).reshape(b, -1)
+    V = rng.uniform(-0.5, 0.5, size=dims[::-1])
+    sy = oracle_system(dims, h, 1, 1.0, V)
+    f0 = rng.normal(size=(b, len(sy.G))) + 1j * rng.normal(size=(b, len(sy.G)))
+    # one orbital's columns far smaller than the rest (a per-column scale, not a global one)
+    psi0[3] *= 1e-9
+    f0[3] *= 1e-9
+    ref_p, ref_f = sy.step(psi0, f0, dt)
+    p, f, _ = gpu_run(torch_cuda, dims, h, 1, 1.0, "fp16x3", psi0 * scale, V, dt, 1, aux0=f0 * scale)
+    assert rel(p / scale, ref_p) < 1e-6
+    assert rel(f / scale, ref_f) < 1e-6
+    assert rel(f[3] / scale, ref_f[3]) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
+def test_tensor_core_several_items_per_cta(torch_cuda, prec):
     """At 48^3 x 32 orbitals the persistent tensor-core contraction has about two
     (tile, split) items per SM, so many CTAs work through three, reusing each TMEM
     accumulator buffer after its epilogue drained it.  Three steps of the 3xTF32 path
@@ -204,12 +228,12 @@ def test_tensor_core_several_items_per_cta(torch_cuda):
     psi0 = inputs.random_state(dims, b, rng).reshape(b, -1)
     V = inputs.smooth_random(dims, h, rng)
     p64, f64, _ = gpu_run(torch_cuda, dims, h, 1, 1.0, "fp64", psi0, V, dt, 3)
-    ptc, ftc, _ = gpu_run(torch_cuda, dims, h, 1, 1.0, "tf32x3", psi0, V, dt, 3)
+    ptc, ftc, _ = gpu_run(torch_cuda, dims, h, 1, 1.0, prec, psi0, V, dt, 3)
     assert rel(ptc, p64) < 1e-6
     assert rel(ftc, f64) < 1e-5
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("c64", 1e-5), ("tf32x3", 1e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("c64", 1e-5), ("tf32x3", 1e-6), ("fp16x3", 1e-6)])
 @pytest.mark.parametrize("order,dims,b", [(1, (13, 11, 12), 8), (0, (10, 9, 11), 4)])
 def test_multi_orbital_forward_transform(torch_cuda, prec, tol, order, dims, b):
     """With the orbital count a multiple of four the forward transform handles four
@@ -228,7 +252,7 @@ def test_multi_orbital_forward_transform(torch_cuda, prec, tol, order, dims, b):
         assert rel(f, ref_f) < tol
 
 
-@pytest.mark.parametrize("prec", ["c64", "tf32x3"])
+@pytest.mark.parametrize("prec", ["c64", "tf32x3", "fp16x3"])
 def test_one_orbital_complex64_uses_packed_tiles(torch_cuda, prec):
     """One complex64 orbital runs the packed symmetric-tile contraction, not the
     full-block fallback: the context holds tiles and the algorithmic bytes of a launch
@@ -241,7 +265,7 @@ def test_one_orbital_complex64_uses_packed_tiles(torch_cuda, prec):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec,b", [("c64", 1), ("fp64", 1), ("c64", 3), ("tf32x3", 3)])
+@pytest.mark.parametrize("prec,b", [("c64", 1), ("fp64", 1), ("c64", 3), ("tf32x3", 3), ("fp16x3", 4)])
 def test_chained_forward_matches_separate_forward(torch_cuda, prec, b):
     """ABC_TUNE_CHAIN (the back transform forms the next stage's adapted inputs) gives the
     same steps as separate forward transforms, to rounding."""

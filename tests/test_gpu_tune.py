@@ -1,0 +1,84 @@
+"""The autotuner and every setting it chooses among (marked gpu).
+
+Each GEMM tile configuration and split count, and each stencil form, computes the
+same step up to FP32 rounding: checked against the FP64 oracle on a box whose
+classes span several 128-row tiles and K blocks, and the tuned setting against the
+default one over a mean-field run."""
+import numpy as np
+import pytest
+
+from oracle.coefficients import order1
+from oracle.lattice import Box
+from oracle.propagate import System
+from paper_1908_02456_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from paper_1908_02456_gb300 import abc, build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return torch, abc
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
+@pytest.mark.parametrize("tile,split", [(0, 0), (0, 1), (0, 4), (1, 0), (1, 2), (1, 8)])
+def test_gemm_settings_against_oracle(env, prec, tile, split):
+    torch, abc = env
+    dims, h, dt, b = (22, 22, 22), 0.45, 0.005, 40
+    rng = np.random.default_rng(808)
+    psi0 = inputs.random_state(dims, b, rng).reshape(b, -1)
+    V = rng.uniform(-0.5, 0.5, size=dims[::-1])
+    box = Box(dims, h)
+    sy = System(box, V_ext=V.reshape(-1), coeffs=order1(box, 1.0))
+    f0 = rng.normal(size=(b, len(sy.G))) + 1j * rng.normal(size=(b, len(sy.G)))
+    ref_p, ref_f = sy.step(psi0, f0, dt)
+    ctx = abc.Context(dims, h, 1, 1.0, precision=prec, max_orbitals=b)
+    ctx.set_tuning(abc.TUNE_GEMM_TILE, tile)
+    ctx.set_tuning(abc.TUNE_GEMM_SPLIT, split)
+    psi = torch.from_numpy(psi0.reshape(b, *dims[::-1])).to("cuda", torch.complex64).contiguous()
+    aux = torch.from_numpy(f0.T.copy()).to("cuda", torch.complex64).contiguous()
+    Vt = torch.from_numpy(V).to("cuda", torch.float32).contiguous()
+    ctx.run(psi, aux, Vt, dt, 1)
+    torch.cuda.synchronize()
+    assert rel(psi.cpu().numpy().reshape(b, -1), ref_p) < 1e-6
+    assert rel(aux.cpu().numpy().T, ref_f) < 1e-6
+    ctx.close()
+
+
+def test_tuned_setting_matches_default(env, tmp_path, monkeypatch):
+    """tune() picks a setting (timed on a copy of the state; the caller's state is not
+    touched), caches it, and the tuned run equals the default run to FP32 rounding."""
+    torch, abc = env
+    from paper_1908_02456_gb300 import tune
+    monkeypatch.setattr(tune, "CACHE", str(tmp_path / "cache.json"))
+    dims, h, dt, b = (24, 24, 24), 0.4, 0.005, 16
+    mf = (-1.0, 0.8, 1.0 / 6.0)
+    psi0 = inputs.orbital_set(dims, h, np.random.default_rng(9), b)
+    outs = []
+    for tuned in (False, True):
+        ctx = abc.Context(dims, h, 1, 1.0, precision="fp16x3", max_orbitals=b)
+        psi = torch.from_numpy(psi0).to("cuda", torch.complex64).contiguous()
+        aux = ctx.new_aux(b)
+        V = torch.zeros(dims, dtype=torch.float32, device="cuda")
+        if tuned:
+            keep = psi.clone()
+            res = tune.tune(ctx, psi, aux, V, dt, meanfield=mf, steps=3, repeats=1)
+            assert res["tuned"] and res["setting"]
+            assert torch.equal(psi, keep)
+            again = tune.tune(ctx, psi, aux, V, dt, meanfield=mf)
+            assert again["cached"] and again["setting"] == res["setting"]
+        ctx.run(psi, aux, V, dt, 21, meanfield=mf)
+        torch.cuda.synchronize()
+        outs.append((psi.cpu().numpy().astype(np.complex128), aux.cpu().numpy().astype(np.complex128)))
+        ctx.close()
+    assert rel(outs[1][0], outs[0][0]) < 2e-6
+    assert rel(outs[1][1], outs[0][1]) < 2e-6

@@ -36,12 +36,15 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+@pytest.mark.parametrize("b", [1, 2])
 @pytest.mark.parametrize("prec,order", [("c64", 1), ("fp64", 1), ("c64", 0), ("fp64", 0)])
-def test_noalloc_step_matches_step(env, prec, order):
+def test_noalloc_step_matches_step(env, prec, order, b):
+    """b = 1 runs the one-orbital full-block kernel of the no-allocation step, b = 2 the
+    many-orbital one; abc_step runs its own kernels for both."""
     torch, abc, lib = env
-    dims, h, dt, b = (14, 12, 10), 0.5, 0.01, 2
+    dims, h, dt = (14, 12, 10), 0.5, 0.01
     ctx = abc.Context(dims, h, order, 1.0, precision=prec, max_orbitals=b)
-    rng = np.random.default_rng(42 + order)
+    rng = np.random.default_rng(42 + order + 10 * b)
     psi0 = inputs.random_state(dims, b, rng)
     V0 = rng.uniform(-1, 1, size=dims[::-1])
     psi_a = torch.from_numpy(psi0).to("cuda", ctx.complex_dtype).contiguous()
