@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU form")
     ap.add_argument("--no-extra", action="store_true", help="skip the single-orbital figures on the default line")
+    ap.add_argument("--reuse-tuning", action="store_true",
+                    help="take the autotuner's cached choice when there is one (profiling runs)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the library's default knobs (profiling runs)")
     ap.add_argument("--workload", type=int, default=WORKLOAD_NUMBER,
                     help="5 (default) or 2 give a full line; 1, 3, 4, 6-9 a line of their own")
     return ap.parse_args()
@@ -299,7 +302,13 @@ def measure(args, w, rank, world, dev, extra_lines=True):
 
     # per-shape kernel choices (untimed set-up, on a copy of the state)
     from paper_1908_02456_gb300 import tune
-    tuned = tune.tune(ctx, psi, aux, Vt, w.dt, meanfield=mf, use_cache=False)
+    if args.no_tune:
+        tuned = {"setting": {}, "sweep": None}
+    elif args.reuse_tuning:
+        tuned = tune.tune(ctx, psi, aux, Vt, w.dt, meanfield=mf, use_cache=True)
+    else:
+        tuned = tune.tune(ctx, psi, aux, Vt, w.dt, meanfield=mf, use_cache=False)
+        tune.tune(ctx, psi, aux, Vt, w.dt, meanfield=mf, use_cache=True, fresh=tuned)
     # warm-up (also captures the CUDA graph)
     ctx.run(psi, aux, Vt, w.dt, max(args.warmup, 1), meanfield=mf)
     torch.cuda.synchronize()

@@ -19,7 +19,7 @@ MAT_K, MAT_M, MAT_A, MAT_B, MAT_Q = 0, 1, 2, 3, 4
 MAT_B1, MAT_B0, MAT_A1, MAT_A0 = 5, 6, 7, 8
 KERNEL_CONTRACTION, KERNEL_STENCIL, KERNEL_PACK = 0, 1, 2
 TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT, TUNE_PDL, TUNE_CHAIN, TUNE_STENCIL, TUNE_FUSED = 0, 1, 2, 3, 4, 5
-TUNE_GEMM_TILE, TUNE_GEMM_SPLIT = 6, 7
+TUNE_GEMM_TILE, TUNE_GEMM_SPLIT, TUNE_STENCIL_BPS, TUNE_STENCIL_KZ, TUNE_BACK_MULTI = 6, 7, 8, 9, 10
 PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16, "tf32x3": C64_3XTF32,
               "fp16x3": C64_SPLIT_FP16}
 FIT1_LIMIT, FIT1_TWO_POINT, FIT1_HERMITE = 0, 1, 2
@@ -435,6 +435,89 @@ class Context:
     def close(self):
         if getattr(self, "ctx", None):
             abc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------
+# the one-dimensional stepper of Sec. 4.1 (include/abc1d.h)
+# ----------------------------------------------------------------------
+class abc1d_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("h", ctypes.c_double), ("order", ctypes.c_int),
+                ("s", ctypes.c_double * 4), ("fit1", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+def _params1d(n, h, order, s, fit1="limit", precision="fp64") -> abc1d_params:
+    pts = [float(v) for v in (s if isinstance(s, (tuple, list)) else (s,))] + [0.0] * 4
+    fit = FITS1[fit1] if isinstance(fit1, str) else int(fit1)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return abc1d_params(int(n), float(h), int(order), (ctypes.c_double * 4)(*pts[:4]), fit, prec)
+
+
+def _sig1d(lib):
+    P1 = ctypes.POINTER(abc1d_params)
+    for name, args in {"abc1d_setup": [P1, ctypes.POINTER(_P)], "abc1d_aux_init": [_P, _P, _P, _P],
+                       "abc1d_run": [_P, _P, _P, ctypes.c_double, ctypes.c_longlong, ctypes.c_int, _P, _P],
+                       "abc1d_host_block": [P1, ctypes.c_int, _P], "abc1d_destroy": [_P]}.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = None if name == "abc1d_destroy" else ctypes.c_int
+
+
+def abc1d_host_block(n, h, order, s, which, fit1="limit") -> np.ndarray:
+    """The left end's 2 x 2 block of matrix `which` (GPU-free set-up)."""
+    lib = load()
+    _sig1d(lib)
+    out = np.zeros(8)
+    p = _params1d(n, h, order, s, fit1)
+    _check(lib.abc1d_host_block(ctypes.byref(p), which, out.ctypes.data))
+    return out.view(np.complex128).reshape(2, 2)
+
+
+class Context1D:
+    """One abc1d_ctx: psi is a CUDA tensor of n complex values, aux of 4 (order 1) or 8
+    (order 2: f then g)."""
+
+    def __init__(self, n, h, order, s, fit1="limit", precision="fp64"):
+        lib = load()
+        _sig1d(lib)
+        self.n, self.h, self.order = int(n), float(h), int(order)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p = _params1d(n, h, order, s, fit1, precision)
+        c = _P()
+        _check(lib.abc1d_setup(ctypes.byref(p), ctypes.byref(c)))
+        self.ctx = c
+
+    @property
+    def complex_dtype(self):
+        import torch
+        return torch.complex128 if self.precision == FP64 else torch.complex64
+
+    def new_aux(self, psi):
+        """The consistent auxiliary state at t = 0 (None for order 0)."""
+        import torch
+        if self.order == 0:
+            return None
+        aux = torch.zeros(4 if self.order == 1 else 8, dtype=self.complex_dtype, device="cuda")
+        _check(load().abc1d_aux_init(self.ctx, psi.data_ptr(), aux.data_ptr(), None))
+        return aux
+
+    def run(self, psi, aux, dt, nsteps, diag_every=0):
+        if psi.dtype != self.complex_dtype or not psi.is_cuda or psi.numel() != self.n or not psi.is_contiguous():
+            raise ValueError(f"psi must be a contiguous CUDA {self.complex_dtype} tensor of {self.n} values")
+        norms = np.zeros(nsteps // diag_every) if diag_every else None
+        _check(load().abc1d_run(self.ctx, psi.data_ptr(), aux.data_ptr() if aux is not None else None, dt, nsteps,
+                                diag_every, norms.ctypes.data if norms is not None else None, None))
+        return norms
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().abc1d_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):

@@ -23,8 +23,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-fopenmp", "-I", INC, "-I", CSRC]
 CXX_FLAGS = ["-std=c++17", "-O3", "-fPIC", "-fopenmp", "-I", INC, "-I", CSRC]
 
-CU_SOURCES = ["api.cu", "noalloc.cu"]
-CXX_SOURCES = ["dense.cpp", "setup.cpp", "symmetry.cpp", "host_api.cpp"]
+CU_SOURCES = ["api.cu", "noalloc.cu", "one_d.cu"]
+CXX_SOURCES = ["dense.cpp", "setup.cpp", "symmetry.cpp", "host_api.cpp", "one_d_setup.cpp"]
 
 
 def _nvcc() -> str:
@@ -36,7 +36,7 @@ def _nvcc() -> str:
 
 def _stamp() -> str:
     h = hashlib.sha256()
-    for name in sorted(os.listdir(CSRC)) + ["../../include/abc.h"]:
+    for name in sorted(os.listdir(CSRC)) + ["../../include/abc.h", "../../include/abc1d.h"]:
         path = os.path.normpath(os.path.join(CSRC, name))
         if os.path.isfile(path):
             h.update(name.encode())

@@ -771,7 +771,7 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
         const abc_ctx::TcPlan& pl = c->tc_b[n_orb];
         // the operand packing has its own timing slot, so the contraction slot times the GEMM alone
         prof_begin(c, ABC_KERNEL_PACK, s);
-        const dim3 pgrid((unsigned)pl.cols_cnt, (unsigned)pl.max_nkb);
+        const dim3 pgrid((unsigned)pl.cols_cnt, (unsigned)((pl.max_nkb + dev::TC_PACK_KB - 1) / dev::TC_PACK_KB));
         float2* out = pl.nsplit > 1 ? c->tc_part.as<float2>() : (float2*)t;
         const int* colexp = c->tc_colexp.as<int>();
         if (c->tc_f16) {
@@ -833,6 +833,11 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
             return;
         }
     }
+    if (MODE == 0 && !fuse && c->back_multi && n_orb % dev::FO == 0) {
+        dev::bnd_back_multi<T><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
+            ct, n_orb, s1, a_coef, hp, hf, (const Vc*)tr.t, tr.nsplit, tr.stride, (const Vc*)y_f, (Vc*)out, cdt);
+        return;
+    }
     if (fuse)
         dev::bnd_back<T, MODE, false, can_fuse><<<nbk, 128, 0, s>>>(ct, n_orb, s1, a_coef, hp, hf, (const Vc*)tr.t,
                                                                     tr.nsplit, tr.stride, c->sym_gather,
@@ -874,6 +879,30 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             dev::stencil_stage_x2z2<<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, (float)(1.0 / (g.h * g.h)),
                                                         (const float2*)w_phi, (const float2*)y_phi, (const float*)V,
                                                         (const float2*)bt, (float2*)o_phi, (float)cdt);
+        } else if (sizeof(T) == 4 && (g.nx & 1) == 0 && c->stencil_bps > 0 && ss != s) {
+            // beside the boundary chain: a bounded number of blocks per SM, grid-stride
+            dev::stencil_stage_x2_gs<<<(unsigned)(c->tc_sms_all * c->stencil_bps), 256, 0, ss>>>(
+                g.nx, g.ny, g.nz, n_orb, (float)(1.0 / (g.h * g.h)), (const float2*)w_phi, (const float2*)y_phi,
+                (const float*)V, (const float2*)bt, (float2*)o_phi, (float)cdt);
+        } else if (sizeof(T) == 4 && (g.nx & 1) == 0 && c->stencil_kz >= 2) {
+            // complex64, even rows: two nodes per thread marching through KZ planes
+            dim3 gp = stencil_grid(c, n_orb);
+            gp.x = (unsigned)(((g.nx / 2) * g.ny + 255) / 256);
+            gp.y = (unsigned)((g.nz + c->stencil_kz - 1) / c->stencil_kz);
+            const float ih2 = (float)(1.0 / (g.h * g.h));
+            const float2 *wp = (const float2*)w_phi, *yp = (const float2*)y_phi, *btp = (const float2*)bt;
+            if (c->stencil_kz == 2)
+                dev::stencil_stage_x2zk<2><<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, ih2, wp, yp, (const float*)V,
+                                                               btp, (float2*)o_phi, (float)cdt);
+            else if (c->stencil_kz == 4)
+                dev::stencil_stage_x2zk<4><<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, ih2, wp, yp, (const float*)V,
+                                                               btp, (float2*)o_phi, (float)cdt);
+            else if (c->stencil_kz == 8)
+                dev::stencil_stage_x2zk<8><<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, ih2, wp, yp, (const float*)V,
+                                                               btp, (float2*)o_phi, (float)cdt);
+            else
+                dev::stencil_stage_x2zk<16><<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, ih2, wp, yp,
+                                                                (const float*)V, btp, (float2*)o_phi, (float)cdt);
         } else if (sizeof(T) == 4 && (g.nx & 1) == 0) {       // complex64, even rows: two nodes per thread
             dim3 gp = stencil_grid(c, n_orb);
             gp.x = (unsigned)(((g.nx / 2) * g.ny + 255) / 256);
@@ -1180,6 +1209,7 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     st = compute_param_blocks(c->geo, *params, c->blocks, err);
     if (st) return fail(st, err);
     CUDA_TRY(cudaGetDevice(&c->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&c->tc_sms_all, cudaDevAttrMultiProcessorCount, c->device));
     if ((st = upload_tables(c.get()))) return st;
     if ((st = upload_matrices(c.get()))) return st;
     if ((st = ensure_workspace(c.get()))) return st;
@@ -1818,6 +1848,24 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         }
         return ABC_OK;
     }
+    if (key == ABC_TUNE_BACK_MULTI) {
+        ctx->back_multi = value != 0;
+        drop_graphs(ctx);
+        return ABC_OK;
+    }
+    if (key == ABC_TUNE_STENCIL_KZ) {
+        if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16)
+            return fail(ABC_ERR_ARG, "stencil planes per thread must be 0, 2, 4, 8 or 16");
+        ctx->stencil_kz = (int)value;
+        drop_graphs(ctx);
+        return ABC_OK;
+    }
+    if (key == ABC_TUNE_STENCIL_BPS) {
+        if (value < 0 || value > 8) return fail(ABC_ERR_ARG, "stencil blocks per SM must be 0..8");
+        ctx->stencil_bps = (int)value;
+        drop_graphs(ctx);
+        return ABC_OK;
+    }
     if (key == ABC_TUNE_FUSED) {
         if (value < -1 || value > 1) return fail(ABC_ERR_ARG, "fused stencil must be -1 (auto), 0 or 1");
         ctx->fused_mode = (int)value;
@@ -1836,6 +1884,9 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_STENCIL) { *value = ctx->stencil_mode; return ABC_OK; }
     if (key == ABC_TUNE_FUSED) { *value = ctx->fused_mode; return ABC_OK; }
     if (key == ABC_TUNE_GEMM_TILE) { *value = ctx->tc_wide ? 0 : 1; return ABC_OK; }
+    if (key == ABC_TUNE_STENCIL_BPS) { *value = ctx->stencil_bps; return ABC_OK; }
+    if (key == ABC_TUNE_STENCIL_KZ) { *value = ctx->stencil_kz; return ABC_OK; }
+    if (key == ABC_TUNE_BACK_MULTI) { *value = ctx->back_multi ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_GEMM_SPLIT) { *value = ctx->tc_split; return ABC_OK; }
     return fail(ABC_ERR_ARG, "unknown tuning key");
 }

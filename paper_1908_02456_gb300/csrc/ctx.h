@@ -84,6 +84,10 @@ struct abc_ctx {
     bool pdl = true;                 // the contraction is a programmatic dependent of the forward transform (tuning)
     bool chain = false;              // order-1 back transforms form the next stage's adapted inputs (tuning)
     int stencil_mode = 0;            // where the stencil runs in a stage (tuning, ABC_TUNE_STENCIL)
+    int stencil_bps = 0;             // side-stream stencil: blocks per SM of a grid-stride grid (0: one per pair)
+    int stencil_kz = 0;              // complex64 stencil: planes per thread (0: one; 2, 4, 8, 16: z march)
+    bool back_multi = false;         // order-1 back transform four orbitals per cell group (tuning)
+    int tc_sms_all = 0;              // SMs of the device
     abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
     abc::dev::SymGather sym_gather{};   // partial-sum view for the back transform
     // many-orbital complex64 contraction on the tensor cores (ABC_C64_3XTF32)

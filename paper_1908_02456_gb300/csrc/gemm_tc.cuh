@@ -68,6 +68,7 @@ constexpr int TC_B_PLANES = 6;
 constexpr uint32_t TC_B_PLANE = TC_NMAX * TC_KB * 4;
 constexpr uint32_t TC_B_BYTES = TC_B_PLANES * TC_B_PLANE;   // 36 KB: the packed X chunk stride in global memory
 constexpr int TC_MAX_SPLIT = 8;
+constexpr int TC_PACK_KB = 4;                      // K blocks packed per pack_x_tc block
 
 // Tile configurations of the persistent GEMM (chosen per shape by the autotuner):
 // NMX output columns at most per tile, STG ring stages, CPS resident CTAs per SM.
@@ -191,7 +192,8 @@ struct TcItem {
 // X -> packed TF32 planes of every K block of a column range, in the shared-memory
 // image the GEMM copies with one bulk copy per K block: hi planes (-Xi, Xr, Xi), then
 // lo planes in the same order (conj: (Xr, Xi, -Xr)).  Grid (column ranges, largest
-// nkb), 128 threads; x orbital-major (o * ng + j).  TC_F16: FP16 hi + lo of the
+// nkb / TC_PACK_KB), 128 threads, TC_PACK_KB consecutive K blocks per block; x
+// orbital-major (o * ng + j).  TC_F16: FP16 hi + lo of the
 // column scaled by 2^colexp[column], 8 elements per 16-byte core-matrix row.
 template <int KIND>
 __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCols* __restrict__ cols, int n_orb, int ng,
@@ -199,9 +201,11 @@ __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCols* __re
                                                  const int* __restrict__ colexp) {
     constexpr int EPR = 16 / TcKind<KIND>::EB;          // elements per 16-byte row
     const TcCols cr = cols[blockIdx.x];
-    const int c = cr.cls, kb = blockIdx.y;
-    if (kb >= info.nkb[c]) return;
+    const int c = cr.cls;
     const int m = info.m[c], N = cr.n;
+    for (int kbi = 0; kbi < TC_PACK_KB; ++kbi) {
+    const int kb = blockIdx.y * TC_PACK_KB + kbi;
+    if (kb >= info.nkb[c]) return;
     unsigned char* B = reinterpret_cast<unsigned char*>(bpack + (size_t)(cr.bchunk0 + kb) * (TC_B_BYTES / 4));
     for (int it = threadIdx.x; it < N * 4; it += blockDim.x) {
         const int cc = (it & 7) | ((it >> 5) << 3), q = (it >> 3) & 3;
@@ -262,6 +266,7 @@ __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCols* __re
 #pragma unroll
         for (int p = 0; p < 6; ++p)
             *reinterpret_cast<uint4*>(B + p * pb + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+    }
     }
 }
 

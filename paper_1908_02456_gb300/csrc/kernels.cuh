@@ -584,6 +584,78 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
     }
 }
 
+// bnd_back<T, 0, false> for FO consecutive orbitals per cell group (n_orb a multiple of
+// FO): the cell's tables and coefficients are read once per FO orbitals and each
+// thread has FO independent sets of loads in flight.  Same arithmetic and order as
+// bnd_back<T, 0, false>, orbital by orbital.
+template <typename T>
+__global__ void __launch_bounds__(128) bnd_back_multi(CellTab<T> ct, int n_orb, T s1, T a_coef,
+                                                      const typename C2<T>::t* __restrict__ hat_phi,
+                                                      const typename C2<T>::t* __restrict__ hat_f,
+                                                      const typename C2<T>::t* __restrict__ t_in, int nsplit,
+                                                      long long split_stride, const typename C2<T>::t* y_f,
+                                                      typename C2<T>::t* out, T cdt) {
+    typedef typename C2<T>::t V;
+    __shared__ V sx[2][FO][8][8];              // [group][orbital][output][parity]
+    const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const int nch = n_orb / FO;
+    const long long gidx = (long long)blockIdx.x * 2 + grp;
+    const bool live = gidx < (long long)ct.n_cells * nch;
+    const int j0 = live ? (int)(gidx % nch) * FO : 0;
+    const int cell = live ? (int)(gidx / nch) : 0;
+    const int s = t >> 3, g = t & 7;
+    const int jj = live ? ct.out[cell * 64 + t] : -1;
+    const int ty = live ? ct.type[cell * 8 + g] : 0;
+    const int wr = live ? ct.wr[cell * 64 + t] : -1;
+    const T c_cell = live ? (T)ct.cell_c[cell] : (T)0;
+    T cf[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) cf[o] = live ? ct.coef_bt[(long long)ty * 64 + s * 8 + o] : (T)0;
+    V yv[FO], x[FO];
+#pragma unroll
+    for (int o = 0; o < FO; ++o) {
+        yv[o] = wr >= 0 ? y_f[(long long)wr * n_orb + j0 + o] : mk<T>(0, 0);
+        x[o] = mk<T>(0, 0);
+    }
+    if (jj >= 0) {
+        V fv[FO], pv[FO], tv[FO];
+#pragma unroll
+        for (int o = 0; o < FO; ++o) {
+            const long long e = (long long)(j0 + o) * ct.ng + jj;
+            fv[o] = hat_f[e];
+            pv[o] = hat_phi[e];
+            tv[o] = t_in[e];
+        }
+        for (int q = 1; q < nsplit; ++q)
+#pragma unroll
+            for (int o = 0; o < FO; ++o) {
+                const V u = t_in[(long long)q * split_stride + (long long)(j0 + o) * ct.ng + jj];
+                tv[o].x += u.x;
+                tv[o].y += u.y;
+            }
+        const T a = a_coef * c_cell;
+#pragma unroll
+        for (int o = 0; o < FO; ++o) {
+            const T dr = pv[o].x - tv[o].x, di = pv[o].y - tv[o].y;
+            x[o] = mk<T>(s1 * fv[o].x + a * di, s1 * fv[o].y - a * dr);
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < FO; ++o) sx[grp][o][s][g] = x[o];
+    __syncthreads();
+#pragma unroll
+    for (int o = 0; o < FO; ++o) {
+        V v = mk<T>(0, 0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            v.x += cf[q] * sx[grp][o][q][g].x;
+            v.y += cf[q] * sx[grp][o][q][g].y;
+        }
+        v = wht8_lanes(v, g);
+        if (wr >= 0) out[(long long)wr * n_orb + j0 + o] = mk<T>(yv[o].x + cdt * v.x, yv[o].y + cdt * v.y);
+    }
+}
+
 // --------------------------------------------------------------------------
 // Boundary contraction, one orbital: t = S_p x_p for every parity block p
 // (GEMV; HBM-bound).  One warp per row; the row is streamed with 16-byte loads.
@@ -898,13 +970,12 @@ __global__ void stencil_stage(int nx, int ny, int nz, int n_orb, T inv_h2, const
 // thread, with 16-byte loads of the pair and of its y and z neighbours (nx even, so a
 // pair never crosses a row and every pair starts on a 16-byte boundary): 7 loads of w
 // for two nodes instead of 14.  Same neighbour order and formula as stencil_stage.
-static __global__ void stencil_stage_x2(int nx, int ny, int nz, int n_orb, float inv_h2, const float2* __restrict__ w,
-                                 const float2* y, const float* __restrict__ V, const float2* __restrict__ bterm,
-                                 float2* out, float cdt) {
+__device__ __forceinline__ void stencil_pair_x2(int nx, int ny, int nz, int n_orb, float inv_h2,
+                                                const float2* __restrict__ w, const float2* y,
+                                                const float* __restrict__ V, const float2* __restrict__ bterm,
+                                                float2* out, float cdt, int tp2, int k, int orb) {
     const long long nxy = (long long)nx * ny, nvox = nxy * nz;
-    const int tp2 = blockIdx.x * blockDim.x + threadIdx.x;         // pair in the z-plane
-    if (tp2 >= (nx >> 1) * ny) return;
-    const int jy = tp2 / (nx >> 1), i = 2 * (tp2 - jy * (nx >> 1)), k = blockIdx.y, orb = blockIdx.z;
+    const int jy = tp2 / (nx >> 1), i = 2 * (tp2 - jy * (nx >> 1));
     const long long n = (long long)k * nxy + (long long)jy * nx + i;
     const float2* wo = w + (long long)orb * nvox;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -954,6 +1025,123 @@ static __global__ void stencil_stage_x2(int nx, int ny, int nz, int n_orb, float
         }
     *reinterpret_cast<float4*>(out + idx) =
         make_float4(yv.x + cdt * hi[0], yv.y - cdt * hr[0], yv.z + cdt * hi[1], yv.w - cdt * hr[1]);
+}
+
+static __global__ void stencil_stage_x2(int nx, int ny, int nz, int n_orb, float inv_h2, const float2* __restrict__ w,
+                                        const float2* y, const float* __restrict__ V,
+                                        const float2* __restrict__ bterm, float2* out, float cdt) {
+    const int tp2 = blockIdx.x * blockDim.x + threadIdx.x;         // pair in the z-plane
+    if (tp2 >= (nx >> 1) * ny) return;
+    stencil_pair_x2(nx, ny, nz, n_orb, inv_h2, w, y, V, bterm, out, cdt, tp2, blockIdx.y, blockIdx.z);
+}
+
+// stencil_stage_x2 with each thread marching through KZ consecutive planes of its node
+// pair (grid y = groups of KZ planes): the pair's z column rolls through registers (the
+// centre of plane k + 1 is the z+ neighbour of plane k), and the loads of plane k + 1
+// are issued before plane k is computed, so two planes' loads are in flight per
+// thread.  Same neighbour order and formula as stencil_stage_x2, node by node.
+template <int KZ>
+__global__ void __launch_bounds__(256) stencil_stage_x2zk(int nx, int ny, int nz, int n_orb, float inv_h2,
+                                                          const float2* __restrict__ w, const float2* y,
+                                                          const float* __restrict__ V,
+                                                          const float2* __restrict__ bterm, float2* out, float cdt) {
+    const long long nxy = (long long)nx * ny, nvox = nxy * nz;
+    const int tp2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tp2 >= (nx >> 1) * ny) return;
+    const int jy = tp2 / (nx >> 1), i = 2 * (tp2 - jy * (nx >> 1)), orb = blockIdx.z;
+    const int k0 = blockIdx.y * KZ, k1 = min(nz, k0 + KZ);
+    const float2* wo = w + (long long)orb * nvox;
+    const float2* yo = y + (long long)orb * nvox;
+    float2* oo = out + (long long)orb * nvox;
+    const long long col = (long long)jy * nx + i;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 z2 = make_float2(0.f, 0.f);
+    auto ld4 = [&](const float2* p, long long n) { return *reinterpret_cast<const float4*>(p + n); };
+    // plane k0: its centre, in-plane neighbours, y and V; and the z- neighbour
+    long long n = (long long)k0 * nxy + col;
+    float4 zm = k0 >= 1 ? ld4(wo, n - nxy) : zero;
+    float4 c = ld4(wo, n);
+    float2 xm = i >= 1 ? wo[n - 1] : z2, xp = i + 2 < nx ? wo[n + 2] : z2;
+    float4 ym = jy >= 1 ? ld4(wo, n - nx) : zero, yp = jy + 1 < ny ? ld4(wo, n + nx) : zero;
+    float4 yv = ld4(yo, n);
+    float2 vv = *reinterpret_cast<const float2*>(V + n);
+#pragma unroll
+    for (int kk = 0; kk < KZ; ++kk) {
+        const int k = k0 + kk;
+        if (k >= k1) break;
+        // plane k + 1 (its centre is this plane's z+ neighbour)
+        const long long nn = n + nxy;
+        const bool more = k + 1 < nz;
+        const float4 zp = more ? ld4(wo, nn) : zero;
+        float2 xmn = z2, xpn = z2, vvn = z2;
+        float4 ymn = zero, ypn = zero, yvn = zero;
+        if (more && k + 1 < k1) {
+            xmn = i >= 1 ? wo[nn - 1] : z2;
+            xpn = i + 2 < nx ? wo[nn + 2] : z2;
+            ymn = jy >= 1 ? ld4(wo, nn - nx) : zero;
+            ypn = jy + 1 < ny ? ld4(wo, nn + nx) : zero;
+            yvn = ld4(yo, nn);
+            vvn = *reinterpret_cast<const float2*>(V + nn);
+        }
+        float hr[2], hi[2];
+        {
+            float sr = 0.f, si = 0.f;
+            sr += xm.x; si += xm.y;
+            sr += c.z; si += c.w;
+            sr += ym.x; si += ym.y;
+            sr += yp.x; si += yp.y;
+            sr += zm.x; si += zm.y;
+            sr += zp.x; si += zp.y;
+            const float dg = 3.f * inv_h2 + vv.x;
+            hr[0] = dg * c.x - 0.5f * inv_h2 * sr;
+            hi[0] = dg * c.y - 0.5f * inv_h2 * si;
+        }
+        {
+            float sr = 0.f, si = 0.f;
+            sr += c.x; si += c.y;
+            sr += xp.x; si += xp.y;
+            sr += ym.z; si += ym.w;
+            sr += yp.z; si += yp.w;
+            sr += zm.z; si += zm.w;
+            sr += zp.z; si += zp.w;
+            const float dg = 3.f * inv_h2 + vv.y;
+            hr[1] = dg * c.z - 0.5f * inv_h2 * sr;
+            hi[1] = dg * c.w - 0.5f * inv_h2 * si;
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            if (on_gamma<1>(i + q, jy, k, nx, ny, nz)) {
+                const float2 b = bterm[(long long)gamma_index<1>(i + q, jy, k, nx, ny, nz) * n_orb + orb];
+                hr[q] += b.x;
+                hi[q] += b.y;
+            }
+        *reinterpret_cast<float4*>(oo + n) =
+            make_float4(yv.x + cdt * hi[0], yv.y - cdt * hr[0], yv.z + cdt * hi[1], yv.w - cdt * hr[1]);
+        zm = c;
+        c = zp;
+        xm = xmn; xp = xpn; ym = ymn; yp = ypn; yv = yvn; vv = vvn;
+        n = nn;
+    }
+}
+
+// stencil_stage_x2 on a grid of a fixed number of blocks per SM that strides over
+// (orbital, plane, pair): launched at the start of a stage beside the boundary chain,
+// it leaves thread slots and registers on every SM for the chain's kernels (the
+// tensor-core GEMM keeps its one CTA per SM) instead of filling the GPU.
+static __global__ void __launch_bounds__(256) stencil_stage_x2_gs(int nx, int ny, int nz, int n_orb, float inv_h2,
+                                                                  const float2* __restrict__ w, const float2* y,
+                                                                  const float* __restrict__ V,
+                                                                  const float2* __restrict__ bterm, float2* out,
+                                                                  float cdt) {
+    const int pp = (nx >> 1) * ny;                                  // pairs per plane
+    const long long total = (long long)pp * nz * n_orb;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x) {
+        const long long pl = it / pp;
+        const int tp2 = (int)(it - pl * pp);
+        const int orb = (int)(pl / nz), k = (int)(pl - (long long)orb * nz);
+        stencil_pair_x2(nx, ny, nz, n_orb, inv_h2, w, y, V, bterm, out, cdt, tp2, k, orb);
+    }
 }
 
 // stencil_stage_x2 for two planes per thread as well (grid y = plane pairs): the pair's

@@ -9,7 +9,9 @@ precision and the device, so the library exposes its choices as tuning knobs
   (``TUNE_GEMM_SPLIT``: automatic, or 1, 2, 4 splits per output tile);
 * the interior stencil of an order-1 step: the four Horner stages fused in time
   (``TUNE_FUSED``) or stage by stage, and for the latter where the stencil runs
-  beside the boundary chain (``TUNE_STENCIL``);
+  beside the boundary chain (``TUNE_STENCIL``) and how many planes each of its threads
+  marches through (``TUNE_STENCIL_KZ``);
+* the order-1 back transform one or four orbitals per cell group (``TUNE_BACK_MULTI``);
 * for one complex64 orbital, the early start of the tiled contraction behind the
   forward transform (``TUNE_PDL``).
 
@@ -59,10 +61,14 @@ def knob_groups(ctx: abc.Context, n_orb: int):
         groups.append([{abc.TUNE_GEMM_TILE: t, abc.TUNE_GEMM_SPLIT: sp} for t in (0, 1) for sp in (0, 1, 2, 4)])
     if ctx.order == 1 and ctx.precision != abc.FP64:
         nx = ctx.shape[0]
-        stencil = [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: m} for m in (0, 2)]
+        stencil = [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: m, abc.TUNE_STENCIL_KZ: 0} for m in (0, 1, 2)]
+        if nx % 2 == 0 and ctx.radius == 1 and n_orb >= 2:
+            stencil += [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: 0, abc.TUNE_STENCIL_KZ: kz} for kz in (2, 4, 8, 16)]
         if nx % 2 == 0 and min(ctx.shape) >= 8 and ctx.radius == 1:
             stencil.append({abc.TUNE_FUSED: 1})
         groups.append(stencil)
+    if ctx.order == 1 and ctx.fit1 == abc.FIT1_LIMIT and n_orb >= 4 and n_orb % 4 == 0:
+        groups.append([{abc.TUNE_BACK_MULTI: 0}, {abc.TUNE_BACK_MULTI: 1}])
     if n_orb == 1 and ctx.precision != abc.FP64 and ctx.get_tuning(abc.TUNE_TILE_COUNT) > 0:
         groups.append([{abc.TUNE_PDL: 1}, {abc.TUNE_PDL: 0}])
     return groups
@@ -74,13 +80,19 @@ def _apply(ctx, setting):
 
 
 def tune(ctx: abc.Context, psi, aux, V, dt: float, meanfield=None, steps: int = 8, repeats: int = 2,
-         use_cache: bool = True, device_name: Optional[str] = None) -> dict:
+         use_cache: bool = True, device_name: Optional[str] = None, fresh: Optional[dict] = None) -> dict:
     """Pick the knobs for this context and orbital count; returns the chosen setting,
-    its step time and the sweep."""
+    its step time and the sweep.  With `fresh` (a result of an uncached call) the
+    result is only stored in the cache."""
     import torch
     n_orb = psi.shape[0]
     name = device_name or torch.cuda.get_device_name()
     key = _key(ctx, n_orb, name, meanfield)
+    if fresh is not None:
+        cache = _load()
+        cache[key] = {k: v for k, v in fresh.items() if k != "cached"}
+        _save(cache)
+        return fresh
     if use_cache:
         cache = _load()
         if key in cache:
@@ -107,7 +119,7 @@ def tune(ctx: abc.Context, psi, aux, V, dt: float, meanfield=None, steps: int = 
     for group in knob_groups(ctx, n_orb):
         times = []
         for cand in group:
-            setting = dict(chosen, **cand)
+            setting = {**chosen, **cand}
             t = time_setting(setting)
             sweep[json.dumps({str(k): v for k, v in sorted(setting.items())})] = round(t, 5)
             times.append((t, cand))
@@ -128,5 +140,8 @@ def describe(setting: dict) -> dict:
     """Readable names of a setting returned by tune()."""
     names = {abc.TUNE_GEMM_TILE: "gemm_tile(0=96 cols x 1 CTA/SM, 1=64 cols x 2 CTAs/SM)",
              abc.TUNE_GEMM_SPLIT: "gemm_split(0=auto)", abc.TUNE_FUSED: "fused_stencil",
-             abc.TUNE_STENCIL: "stencil_placement", abc.TUNE_PDL: "pdl"}
+             abc.TUNE_STENCIL: "stencil_placement(0=after contraction, 1=stage start, 2=serial)",
+             abc.TUNE_STENCIL_BPS: "stencil_blocks_per_sm(0=one thread per pair)",
+             abc.TUNE_STENCIL_KZ: "stencil_planes_per_thread(0=one)", abc.TUNE_BACK_MULTI: "back_transform_4_orbitals",
+             abc.TUNE_PDL: "pdl"}
     return {names.get(int(k), str(k)): v for k, v in setting.items()}

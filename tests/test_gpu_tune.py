@@ -82,3 +82,54 @@ def test_tuned_setting_matches_default(env, tmp_path, monkeypatch):
         ctx.close()
     assert rel(outs[1][0], outs[0][0]) < 2e-6
     assert rel(outs[1][1], outs[0][1]) < 2e-6
+
+
+@pytest.mark.parametrize("mode,bps", [(1, 3), (0, 4), (1, 0), (2, 0)])
+def test_stencil_placements_give_identical_steps(env, mode, bps):
+    """Where the stencil runs (second stream after the contraction, from the stage start,
+    or serially) and the grid-stride grid of a bounded number of blocks per SM change
+    only the schedule: every node is computed by the same expression, so the steps
+    agree bit for bit with the default."""
+    torch, abc = env
+    dims, h, dt, b = (20, 18, 16), 0.45, 0.005, 8
+    psi0 = inputs.orbital_set(dims, h, np.random.default_rng(4), b)
+    outs = []
+    for setting in ((0, 0), (mode, bps)):
+        ctx = abc.Context(dims, h, 1, 1.0, precision="fp16x3", max_orbitals=b)
+        ctx.set_tuning(abc.TUNE_STENCIL, setting[0])
+        ctx.set_tuning(abc.TUNE_STENCIL_BPS, setting[1])
+        psi = torch.from_numpy(psi0).to("cuda", torch.complex64).contiguous()
+        aux = ctx.new_aux(b)
+        V = torch.zeros(dims[::-1], dtype=torch.float32, device="cuda")
+        ctx.run(psi, aux, V, dt, 9, meanfield=(-1.0, 0.8, 1.0 / 6.0))
+        torch.cuda.synchronize()
+        outs.append((psi.cpu(), aux.cpu()))
+        ctx.close()
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("knob,value", [("STENCIL_KZ", 2), ("STENCIL_KZ", 4), ("STENCIL_KZ", 8), ("STENCIL_KZ", 16),
+                                        ("BACK_MULTI", 1)])
+@pytest.mark.parametrize("prec", ["fp16x3", "c64"])
+def test_kernel_forms_match_default(env, knob, value, prec):
+    """The z-marching stencil forms (2..16 planes per thread, the box's 13 planes leave a
+    ragged last group) and the four-orbital back transform evaluate the same
+    expressions as the default kernels."""
+    torch, abc = env
+    dims, h, dt, b = (18, 14, 13), 0.45, 0.005, 8
+    psi0 = inputs.orbital_set(dims, h, np.random.default_rng(6), b)
+    V0 = inputs.smooth_random(dims, h, np.random.default_rng(7))
+    outs = []
+    for setting in (0, value):
+        ctx = abc.Context(dims, h, 1, 1.0, precision=prec, max_orbitals=b)
+        ctx.set_tuning(getattr(abc, "TUNE_" + knob), setting)
+        psi = torch.from_numpy(psi0).to("cuda", torch.complex64).contiguous()
+        aux = ctx.new_aux(b)
+        V = torch.from_numpy(V0).to("cuda", torch.float32).contiguous()
+        ctx.run(psi, aux, V, dt, 7, meanfield=(-1.0, 0.8, 1.0 / 6.0))
+        torch.cuda.synchronize()
+        outs.append((psi.cpu().numpy().astype(np.complex128), aux.cpu().numpy().astype(np.complex128)))
+        ctx.close()
+    assert rel(outs[1][0], outs[0][0]) < 1e-6
+    assert rel(outs[1][1], outs[0][1]) < 1e-6
