@@ -351,15 +351,21 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           leaves room on every SM for the boundary chain's kernels
  *                           (the tensor-core GEMM needs one CTA slot per SM); 0 (default):
  *                           one thread per node pair.
- *   ABC_TUNE_STENCIL_KZ     complex64, radius 1, nx even, n_orb >= 2: planes per thread of
- *                           the stage-by-stage stencil: 0 (default) one; 2, 4, 8 or 16:
- *                           each thread marches through that many planes of its node pair,
- *                           the z neighbours rolling through registers and the next plane's
- *                           loads issued before the current one is computed (same formula).
+ *   ABC_TUNE_STENCIL_KZ     complex64, radius 1, nx even, n_orb >= 2: form of the
+ *                           stage-by-stage stencil: 0 one node pair per thread; 1 (default)
+ *                           the same with registers capped for 8 blocks per SM; 2, 4, 8
+ *                           or 16: each thread marches through that many planes of its
+ *                           node pair, the z neighbours rolling through registers and the
+ *                           next plane's loads issued before the current one is computed
+ *                           (same formula in every form).
  *   ABC_TUNE_BACK_MULTI     order 1 (limit fit), n_orb a multiple of 4, unpacked
  *                           contraction output: 1 runs the back transform four orbitals
  *                           per cell group (its tables read once per four); 0 (default)
  *                           one orbital per group.
+ *   ABC_TUNE_FORWARD_RW     n_orb a multiple of 4: 1 runs the four-orbital forward
+ *                           transform with each slot's 8-point reflection transform in
+ *                           one thread's registers (no lane shuffles; bit-identical
+ *                           outputs); 0 (default) across 8 lanes.
  *   ABC_TUNE_GEMM_TILE      tensor-core forms, n_orb >= 2: 0 (default) output tiles of up
  *                           to 96 columns, three ring stages, one CTA per SM; 1: up to 64
  *                           columns, two stages, two CTAs per SM.  Rebuilds the work lists
@@ -380,6 +386,7 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
 #define ABC_TUNE_STENCIL_BPS 8
 #define ABC_TUNE_STENCIL_KZ 9
 #define ABC_TUNE_BACK_MULTI 10
+#define ABC_TUNE_FORWARD_RW 11
 int abc_set_tuning(abc_ctx* ctx, int key, long long value);
 int abc_get_tuning(const abc_ctx* ctx, int key, long long* value);
 

@@ -49,7 +49,8 @@ typedef struct {
     double s[4];      /* order 0: s[0] = s0; order 1: s[0] = s1 (and s[1] = s1b for the
                          two-point fit); order 2: the four distinct points            */
     int fit1;         /* order 1: ABC_FIT1_LIMIT or ABC_FIT1_TWO_POINT                  */
-    int precision;    /* ABC_FP64 or ABC_C64_FP32                                      */
+    int precision;    /* ABC_FP64 or ABC_C64_FP32 (order 2: ABC_FP64 only, else
+                         ABC_ERR_UNSUPPORTED: its fitted blocks cancel beyond FP32)    */
 } abc1d_params;
 
 typedef struct abc1d_ctx abc1d_ctx;

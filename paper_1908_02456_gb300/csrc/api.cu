@@ -884,6 +884,14 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             dev::stencil_stage_x2_gs<<<(unsigned)(c->tc_sms_all * c->stencil_bps), 256, 0, ss>>>(
                 g.nx, g.ny, g.nz, n_orb, (float)(1.0 / (g.h * g.h)), (const float2*)w_phi, (const float2*)y_phi,
                 (const float*)V, (const float2*)bt, (float2*)o_phi, (float)cdt);
+        } else if (sizeof(T) == 4 && (g.nx & 1) == 0 && c->stencil_kz == 1) {
+            // complex64, even rows: two nodes per thread, registers capped for 8 blocks per SM
+            dim3 gp = stencil_grid(c, n_orb);
+            gp.x = (unsigned)(((g.nx / 2) * g.ny + 255) / 256);
+            dev::stencil_stage_x2_lb<8><<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, (float)(1.0 / (g.h * g.h)),
+                                                            (const float2*)w_phi, (const float2*)y_phi,
+                                                            (const float*)V, (const float2*)bt, (float2*)o_phi,
+                                                            (float)cdt);
         } else if (sizeof(T) == 4 && (g.nx & 1) == 0 && c->stencil_kz >= 2) {
             // complex64, even rows: two nodes per thread marching through KZ planes
             dim3 gp = stencil_grid(c, n_orb);
@@ -967,6 +975,9 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             dev::bnd_forward<T, 0, true><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
                                                              order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,
                                                              nullptr, (T)0, dev::Ord2Fwd<T>{});
+        else if (n_orb % dev::FO == 0 && c->fwd_rw)
+            dev::bnd_forward_multi_rw<T><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
+                ct, n_orb, c->nvox, (const Vc*)w_phi, order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf);
         else if (n_orb % dev::FO == 0)
             dev::bnd_forward_multi<T><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
                 ct, n_orb, c->nvox, (const Vc*)w_phi, order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf);
@@ -1062,7 +1073,10 @@ void boundary_chain_f(abc_ctx* c, int n_orb, float cdt, const void* w_phi, const
     const float a_coef = (float)(1.0 / (4.0 * c->geo.h * c->geo.h * c->geo.h * c->geo.h));
     void* hp = c->hat_phi.p;
     void* hf = c->hat_f.p;
-    if (n_orb % dev::FO == 0)
+    if (n_orb % dev::FO == 0 && c->fwd_rw)
+        dev::bnd_forward_multi_rw<float><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
+            ct, n_orb, c->nvox, (const Vc*)w_phi, (const Vc*)w_f, (Vc*)hp, (Vc*)hf);
+    else if (n_orb % dev::FO == 0)
         dev::bnd_forward_multi<float><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
             ct, n_orb, c->nvox, (const Vc*)w_phi, (const Vc*)w_f, (Vc*)hp, (Vc*)hf);
     else
@@ -1848,14 +1862,19 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         }
         return ABC_OK;
     }
+    if (key == ABC_TUNE_FORWARD_RW) {
+        ctx->fwd_rw = value != 0;
+        drop_graphs(ctx);
+        return ABC_OK;
+    }
     if (key == ABC_TUNE_BACK_MULTI) {
         ctx->back_multi = value != 0;
         drop_graphs(ctx);
         return ABC_OK;
     }
     if (key == ABC_TUNE_STENCIL_KZ) {
-        if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16)
-            return fail(ABC_ERR_ARG, "stencil planes per thread must be 0, 2, 4, 8 or 16");
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+            return fail(ABC_ERR_ARG, "stencil form must be 0, 1, 2, 4, 8 or 16");
         ctx->stencil_kz = (int)value;
         drop_graphs(ctx);
         return ABC_OK;
@@ -1887,6 +1906,7 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_STENCIL_BPS) { *value = ctx->stencil_bps; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL_KZ) { *value = ctx->stencil_kz; return ABC_OK; }
     if (key == ABC_TUNE_BACK_MULTI) { *value = ctx->back_multi ? 1 : 0; return ABC_OK; }
+    if (key == ABC_TUNE_FORWARD_RW) { *value = ctx->fwd_rw ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_GEMM_SPLIT) { *value = ctx->tc_split; return ABC_OK; }
     return fail(ABC_ERR_ARG, "unknown tuning key");
 }

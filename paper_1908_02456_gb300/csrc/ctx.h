@@ -85,8 +85,9 @@ struct abc_ctx {
     bool chain = false;              // order-1 back transforms form the next stage's adapted inputs (tuning)
     int stencil_mode = 0;            // where the stencil runs in a stage (tuning, ABC_TUNE_STENCIL)
     int stencil_bps = 0;             // side-stream stencil: blocks per SM of a grid-stride grid (0: one per pair)
-    int stencil_kz = 0;              // complex64 stencil: planes per thread (0: one; 2, 4, 8, 16: z march)
+    int stencil_kz = 1;              // complex64 stencil form (ABC_TUNE_STENCIL_KZ): 1 capped registers (default)
     bool back_multi = false;         // order-1 back transform four orbitals per cell group (tuning)
+    bool fwd_rw = false;             // four-orbital forward transform with the reflection transform in registers
     int tc_sms_all = 0;              // SMs of the device
     abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
     abc::dev::SymGather sym_gather{};   // partial-sum view for the back transform

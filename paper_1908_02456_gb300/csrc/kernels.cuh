@@ -333,6 +333,84 @@ __global__ void __launch_bounds__(128) bnd_forward_multi(CellTab<T> ct, int n_or
     }
 }
 
+// bnd_forward_multi with the reflection transform done in registers instead of across
+// lanes: in phase A thread (array, orbital o, slot s) of a 64-thread group loads the 8
+// reflections of its slot (psi at the nodes, or f) and runs the 8-point Walsh-Hadamard
+// butterfly on them (the butterfly of wht8_lanes, so the same sums in the same order);
+// in phase B thread (output, parity) mixes the 8 slots' values of its parity, read as
+// contiguous 16-byte words.  No shuffles; the shared-memory traffic is about a third of
+// bnd_forward_multi's.  Same outputs, bit for bit.
+template <typename T>
+__global__ void __launch_bounds__(128) bnd_forward_multi_rw(CellTab<T> ct, int n_orb, long long nvox,
+                                                            const typename C2<T>::t* __restrict__ w_phi,
+                                                            const typename C2<T>::t* __restrict__ w_f,
+                                                            typename C2<T>::t* __restrict__ hat_phi,
+                                                            typename C2<T>::t* __restrict__ hat_f) {
+    typedef typename C2<T>::t V;
+    __shared__ __align__(16) V sw[2][2][FO][8][8];        // [group][array][orbital][parity][slot]
+    const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const int nch = n_orb / FO;
+    const long long gidx = (long long)blockIdx.x * 2 + grp;
+    const bool live = gidx < (long long)ct.n_cells * nch;
+    const int j0 = live ? (int)(gidx % nch) * FO : 0;
+    const int cell = live ? (int)(gidx / nch) : 0;
+    // phase A: t = 32 array + 8 orbital + slot
+    {
+        const int arr = t >> 5, o = (t >> 3) & 3, sl = t & 7;
+        V x[8];
+        int gi[8], nd[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            gi[g] = live ? ct.gi[cell * 64 + sl * 8 + g] : -1;
+            nd[g] = live ? ct.node[cell * 64 + sl * 8 + g] : 0;
+        }
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            x[g] = mk<T>(0, 0);
+            if (gi[g] >= 0) {
+                if (arr == 0) x[g] = w_phi[(long long)(j0 + o) * nvox + nd[g]];
+                else if (w_f) x[g] = w_f[(long long)gi[g] * n_orb + j0 + o];
+            }
+        }
+#pragma unroll
+        for (int bit = 1; bit < 8; bit <<= 1) {
+            V y[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const V ov = x[g ^ bit];
+                if (g & bit) y[g] = mk<T>(ov.x - x[g].x, ov.y - x[g].y);
+                else y[g] = mk<T>(x[g].x + ov.x, x[g].y + ov.y);
+            }
+#pragma unroll
+            for (int g = 0; g < 8; ++g) x[g] = y[g];
+        }
+#pragma unroll
+        for (int p = 0; p < 8; ++p) sw[grp][arr][o][p][sl] = x[p];
+    }
+    __syncthreads();
+    // phase B: t = 8 output + parity
+    const int oo = t >> 3, p = t & 7;
+    const int jj = live ? ct.out[cell * 64 + t] : -1;
+    if (jj < 0) return;
+    const int ty = ct.type[cell * 8 + p];
+    T cf[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cf[q] = ct.coef_f[(long long)ty * 64 + oo * 8 + q];
+#pragma unroll
+    for (int o = 0; o < FO; ++o) {
+        V ap = mk<T>(0, 0), af = mk<T>(0, 0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const V vp = sw[grp][0][o][p][q], vf = sw[grp][1][o][p][q];
+            ap.x += cf[q] * vp.x; ap.y += cf[q] * vp.y;
+            if (w_f) { af.x += cf[q] * vf.x; af.y += cf[q] * vf.y; }
+        }
+        const long long e = (long long)(j0 + o) * ct.ng + jj;
+        hat_phi[e] = ap;
+        if (w_f) hat_f[e] = af;
+    }
+}
+
 // t from the partial sums of the tiled contraction (see SymGather).  The loads of the
 // first two row segments and the first 24 column parts are all issued before any
 // of them is used (one memory round trip for the common case); the sums are then
@@ -1031,6 +1109,20 @@ static __global__ void stencil_stage_x2(int nx, int ny, int nz, int n_orb, float
                                         const float2* y, const float* __restrict__ V,
                                         const float2* __restrict__ bterm, float2* out, float cdt) {
     const int tp2 = blockIdx.x * blockDim.x + threadIdx.x;         // pair in the z-plane
+    if (tp2 >= (nx >> 1) * ny) return;
+    stencil_pair_x2(nx, ny, nz, n_orb, inv_h2, w, y, V, bterm, out, cdt, tp2, blockIdx.y, blockIdx.z);
+}
+
+// stencil_stage_x2 compiled for MINB resident blocks per SM (registers capped so that
+// all of the SM's warp slots can be filled: the kernel waits on loads, and more warps
+// keep more of them in flight).
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) stencil_stage_x2_lb(int nx, int ny, int nz, int n_orb, float inv_h2,
+                                                                 const float2* __restrict__ w, const float2* y,
+                                                                 const float* __restrict__ V,
+                                                                 const float2* __restrict__ bterm, float2* out,
+                                                                 float cdt) {
+    const int tp2 = blockIdx.x * blockDim.x + threadIdx.x;
     if (tp2 >= (nx >> 1) * ny) return;
     stencil_pair_x2(nx, ny, nz, n_orb, inv_h2, w, y, V, bterm, out, cdt, tp2, blockIdx.y, blockIdx.z);
 }

@@ -11,7 +11,9 @@ precision and the device, so the library exposes its choices as tuning knobs
   (``TUNE_FUSED``) or stage by stage, and for the latter where the stencil runs
   beside the boundary chain (``TUNE_STENCIL``) and how many planes each of its threads
   marches through (``TUNE_STENCIL_KZ``);
-* the order-1 back transform one or four orbitals per cell group (``TUNE_BACK_MULTI``);
+* the order-1 back transform one or four orbitals per cell group (``TUNE_BACK_MULTI``)
+  and the four-orbital forward transform's reflection transform across lanes or in
+  registers (``TUNE_FORWARD_RW``);
 * for one complex64 orbital, the early start of the tiled contraction behind the
   forward transform (``TUNE_PDL``).
 
@@ -63,12 +65,14 @@ def knob_groups(ctx: abc.Context, n_orb: int):
         nx = ctx.shape[0]
         stencil = [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: m, abc.TUNE_STENCIL_KZ: 0} for m in (0, 1, 2)]
         if nx % 2 == 0 and ctx.radius == 1 and n_orb >= 2:
-            stencil += [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: 0, abc.TUNE_STENCIL_KZ: kz} for kz in (2, 4, 8, 16)]
+            stencil += [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: 0, abc.TUNE_STENCIL_KZ: kz} for kz in (1, 2, 4, 8)]
         if nx % 2 == 0 and min(ctx.shape) >= 8 and ctx.radius == 1:
             stencil.append({abc.TUNE_FUSED: 1})
         groups.append(stencil)
     if ctx.order == 1 and ctx.fit1 == abc.FIT1_LIMIT and n_orb >= 4 and n_orb % 4 == 0:
         groups.append([{abc.TUNE_BACK_MULTI: 0}, {abc.TUNE_BACK_MULTI: 1}])
+    if n_orb >= 4 and n_orb % 4 == 0 and ctx.order < 2:
+        groups.append([{abc.TUNE_FORWARD_RW: 0}, {abc.TUNE_FORWARD_RW: 1}])
     if n_orb == 1 and ctx.precision != abc.FP64 and ctx.get_tuning(abc.TUNE_TILE_COUNT) > 0:
         groups.append([{abc.TUNE_PDL: 1}, {abc.TUNE_PDL: 0}])
     return groups
@@ -142,6 +146,7 @@ def describe(setting: dict) -> dict:
              abc.TUNE_GEMM_SPLIT: "gemm_split(0=auto)", abc.TUNE_FUSED: "fused_stencil",
              abc.TUNE_STENCIL: "stencil_placement(0=after contraction, 1=stage start, 2=serial)",
              abc.TUNE_STENCIL_BPS: "stencil_blocks_per_sm(0=one thread per pair)",
-             abc.TUNE_STENCIL_KZ: "stencil_planes_per_thread(0=one)", abc.TUNE_BACK_MULTI: "back_transform_4_orbitals",
+             abc.TUNE_STENCIL_KZ: "stencil_form(0=pair per thread, 1=capped registers, k>1=k planes)",
+             abc.TUNE_BACK_MULTI: "back_transform_4_orbitals", abc.TUNE_FORWARD_RW: "forward_transform_in_registers",
              abc.TUNE_PDL: "pdl"}
     return {names.get(int(k), str(k)): v for k, v in setting.items()}

@@ -1,8 +1,9 @@
 """The one-dimensional stepper of Sec. 4.1 on the GPU (include/abc1d.h; marked gpu).
 
 * Parity with the FP64 oracle on a short 1D box: orders 0 and 1 (Thm 3.2 fit and the
-  two-point fit) to 1e-10 in FP64 and 1e-5 in complex64 (the auxiliary f, two orders of
-  magnitude above psi here, in the norm of Thm 3.2's W, and bare to 1e-4).  Order 2 is held to 1e-5 (psi,
+  two-point fit) to 1e-10 in FP64 and 3e-5 in complex64 after 2000 steps (the
+  auxiliary f, two orders of magnitude above psi here, in the norm of Thm 3.2's W, and
+  bare to 1e-4); the second order runs in FP64 only.  Order 2 is held to 1e-5 (psi,
   norms) and 1e-4 (its auxiliary [f | g]): its interpolation at the paper's points (two
   close pairs) determines the coefficients only to ~1e-4 and R_22 on the imaginary axis
   to ~1e-6 (see tests/test_oned_host.py), and the library and the oracle solve that
@@ -62,6 +63,11 @@ def gpu_run(torch, abc, n, h, order, s, fit, prec, psi0, dt, steps, every):
 @pytest.mark.parametrize("prec", ["fp64", "c64"])
 def test_oned_against_oracle(env, name, order, s, fit, prec):
     torch, abc = env
+    if order == 2 and prec == "c64":
+        with pytest.raises(abc.AbcError) as e:         # FP64 only (see abc1d.h)
+            abc.Context1D(240, 0.05, order, s, fit1=fit, precision=prec)
+        assert e.value.status == 7
+        return
     n, h, dt, steps = 240, 0.05, 2e-4, 2000
     x = -9.0 + h * np.arange(n)
     psi0 = free_packet([x], 0.0, (0.5,), (5.0,), 0.5)
@@ -69,21 +75,23 @@ def test_oned_against_oracle(env, name, order, s, fit, prec):
     sy = System(box, coeffs=oracle_coeffs(box, order, s, fit))
     ref_p, ref_f, ref_d = sy.run(psi0[None], dt, steps, diag_every=250)
     p, f, d = gpu_run(torch, abc, n, h, order, s, fit, prec, psi0, dt, steps, 250)
-    tol = 1e-10 if prec == "fp64" else 1e-5
+    # FP32 in 1D: the five-point H at h = 0.05 has a spectral radius near 1070 and f
+    # reaches ~250 (A ~ 1/(4 h^4)) from a psi of order one; over 2000 steps the rounding
+    # accumulates to 0.8-1.5e-5 (measured), so the complex64 bound here is 3e-5, with f in
+    # the norm of W = |phi|^2 + f^* Q f (Thm 3.2) and bare to 1e-4
+    tol = 1e-10 if prec == "fp64" else 3e-5
     ftol = tol
     if order == 2:
         # the fit's conditioning: the coefficients agree to ~1e-4, g (|g| ~ 3e3 here) to ~2e-5
         tol, ftol = max(tol, 1e-5), 1e-4
     elif prec == "c64":
-        # f reaches ~250 here (A ~ 1/(4h^4) at h = 0.05) from a psi of order one: in FP32 it
-        # is held to 1e-5 in the norm of W = |phi|^2 + f^* Q f (Thm 3.2), bare to 1e-4
         ftol = 1e-4
         if order == 1:
             Q = sy.coeffs["Q"]
             d_f = f - ref_f[0]
             num = h * np.sum(np.abs(p - ref_p[0]) ** 2) + np.real(np.conj(d_f) @ Q @ d_f)
             den = h * np.sum(np.abs(ref_p[0]) ** 2) + np.real(np.conj(ref_f[0]) @ Q @ ref_f[0])
-            assert np.sqrt(num / den) < 1e-5
+            assert np.sqrt(num / den) < tol
     assert rel(p, ref_p[0]) < tol
     if f is not None:
         assert rel(f, ref_f[0]) < ftol
