@@ -44,6 +44,7 @@ SINGLE_ORBITAL_WORKLOAD = 2
 L2_BYTES = 129 << 20
 L2_FLUSH_BYTES = 256 << 20          # written before every timed step when the state fits in L2
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tensor-core rates (TF32 / BF16)
+FP64_CUBLAS_TFLOPS = 1.10           # torch.matmul FP64 4096^3 on this GPU model (library probe)
 
 
 def parse():
@@ -477,9 +478,19 @@ def measure(args, w, rank, world, dev, extra_lines=True):
         s64 = f0.elapsed_time(f1) * 1e-3
         err = float(torch.linalg.norm(p32.to(torch.complex128) - p64) / torch.linalg.norm(p64))
         ferr = float(torch.linalg.norm(a32.to(torch.complex128) - a64) / torch.linalg.norm(a64))
+        # the FP64 contraction's own rate, against the cuBLAS FP64 GEMM of this part
+        ctx64.profile(True)
+        ctx64.run(p64, a64, V64, w.dt, 1, meanfield=mf)
+        ms64, n64c = ctx64.profile_read(abc.KERNEL_CONTRACTION)
+        ctx64.profile(False)
+        _, iss64 = ctx64.kernel_flops(abc.KERNEL_CONTRACTION, w.n_orb)
+        fp64_gemm = {"avg_launch_ms": round(ms64 / n64c, 3),
+                     "tflops": round(iss64 / (ms64 / n64c * 1e-3) / 1e12, 3),
+                     "frac_of_cublas_fp64": round(iss64 / (ms64 / n64c * 1e-3) / 1e12 / FP64_CUBLAS_TFLOPS, 3)}
         out["fp64_form"] = {"value": w.n_orb * np.prod(w.shape) * n64 / s64, "ms_per_step": s64 / n64 * 1e3,
                             "steps": n64 + 1, "psi_rel_l2_vs_fp64": err, "aux_rel_l2_vs_fp64": ferr, "dtype": "f64",
-                            "fp64_peak_note": "cuBLAS FP64 GEMM measured 1.10 TFLOP/s on this part"}
+                            "contraction": fp64_gemm,
+                            "fp64_peak_note": f"cuBLAS FP64 GEMM measured {FP64_CUBLAS_TFLOPS} TFLOP/s on this part"}
         ctx64.close()
     ctx.close()
     return out

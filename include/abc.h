@@ -282,8 +282,10 @@ int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, double* bytes);
  * must be ABC_KERNEL_CONTRACTION): useful = 8 real flops per complex multiply-add of
  * the class blocks with their right-hand sides, sum_k nseg R_k m_k^2 n_orb of them;
  * issued = what the arithmetic performs: 3 x useful on the tensor-core split forms
- * (three products per term), useful otherwise.  The paper has no counterpart
- * (measurement support). */
+ * (three products per term; 2.25 x with the Karatsuba GEMM form, three real products
+ * per complex term), 8 flops per entry of the stored blocks and orbital on the
+ * CUDA-core GEMM of n_orb >= 2 (FP64, ABC_C64_FP32), useful otherwise.  The paper has
+ * no counterpart (measurement support). */
 int abc_kernel_flops(const abc_ctx* ctx, int kernel, int n_orb, double* useful, double* issued);
 
 /* abc_step without any device allocation.  The paper has no counterpart: this
@@ -368,8 +370,13 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           outputs); 0 (default) across 8 lanes.
  *   ABC_TUNE_GEMM_TILE      tensor-core forms, n_orb >= 2: 0 (default) output tiles of up
  *                           to 96 columns, three ring stages, one CTA per SM; 1: up to 64
- *                           columns, two stages, two CTAs per SM.  Rebuilds the work lists
- *                           (synchronises the device).
+ *                           columns, two stages, two CTAs per SM; 2: the complex products
+ *                           by Karatsuba's three real products (P1 = Sr Xr, P2 = Si Xi,
+ *                           P3 = (Sr + Si)(Xr + Xi); Re = P1 - P2, Im = P3 - P1 - P2: a
+ *                           quarter less tensor work, a third more matrix bytes), 64
+ *                           columns, three stages, one CTA per SM (its matrix image is
+ *                           built on first use).  Rebuilds the work lists (synchronises
+ *                           the device).
  *   ABC_TUNE_GEMM_SPLIT     tensor-core forms: number of K splits of every output tile
  *                           (1..8), or 0 (default) for about two work items per CTA slot.
  *                           Rebuilds the work lists (synchronises the device).

@@ -18,7 +18,13 @@
  *            H_{II,Gamma}, B = s1 I - A K(s1)^{-1}) or ABC_FIT1_TWO_POINT
  *            ((s_j I - B) K(s_j) = A at s1 and s1b; Sec. 4.1 uses s = 10, 20)
  *   order 2 (eq:dynamics2): R_22(s) = (s^2 I - s B1 - B0)^{-1}(s A1 + A0) = K(s) at four
- *            points (Sec. 4.1 uses s = 10, 11, 20, 21); g(0) = A1 E phi(0)
+ *            points (Sec. 4.1 uses s = 10, 11, 20, 21); g(0) = A1 E phi(0).  For the
+ *            five-point scheme these conditions are singular: a fixed row combination
+ *            of K(s) obeys a first-degree identity at every s, so the solutions share
+ *            R_22 and differ in one hidden root of det(s^2 I - s B1 - B0) that rounding
+ *            excites (in the right half-plane the run diverges).  The library takes the
+ *            minimum-norm solution plus the shortest correction along the null
+ *            direction that puts that root at s = -min(s_j).
  *
  * One time step applies the degree-4 Taylor polynomial of exp(dt L) in Horner form
  * (eq:21 read as that series), the same integrator as the 3D library.  The whole run
@@ -49,8 +55,7 @@ typedef struct {
     double s[4];      /* order 0: s[0] = s0; order 1: s[0] = s1 (and s[1] = s1b for the
                          two-point fit); order 2: the four distinct points            */
     int fit1;         /* order 1: ABC_FIT1_LIMIT or ABC_FIT1_TWO_POINT                  */
-    int precision;    /* ABC_FP64 or ABC_C64_FP32 (order 2: ABC_FP64 only, else
-                         ABC_ERR_UNSUPPORTED: its fitted blocks cancel beyond FP32)    */
+    int precision;    /* ABC_FP64 or ABC_C64_FP32                                       */
 } abc1d_params;
 
 typedef struct abc1d_ctx abc1d_ctx;

@@ -21,6 +21,18 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 * Order 2 (Sec. 3.3, eq:dynamics2): R_22(s) = (s^2 I - s B1 - B0)^{-1} (s A1 + A0),
   fitted by interpolation at four points s_j (R_22(s_j) = K(s_j)); each condition
   s_j^2 K_j = s_j B1 K_j + B0 K_j + s_j A1 + A0 is linear in [B1, B0, A1, A0].
+* Order 2 in 1D (Sec. 4.1, five-point scheme): each end's 2 x 2 block is fitted on its
+  own (the ends see disjoint half-lines, so K is block diagonal).  There the 8 x 8
+  interpolation system has a one-dimensional null space: a fixed row combination of
+  K(s) obeys a first-degree identity (s b1 + b0) K(s) = -(s a1 + a0) for every s.  The
+  solutions [B1 B0 A1 A0] = X0 + w x (x the null row, w any 2-vector) share R_22(s)
+  for every s but differ in one hidden mode, a root of det(s^2 I - s B1 - B0) that R_22
+  does not show and that rounding excites; for some w it lies in the right half-plane
+  and the run diverges.  The paper does not address this; the reading taken here: X0 is
+  the minimum-norm solution (pseudo-inverse of rank 7) and w the shortest vector that
+  puts the hidden root at s = -min(s_j), a decaying mode.  By the determinant lemma
+  det(D0(l) - w r) = det D0(l) - r adj(D0(l)) w with D0(l) = l^2 I - l B1 - B0 of X0 and
+  r = l x_B1 + x_B0, so the condition is one linear equation in w.
 """
 from __future__ import annotations
 
@@ -92,6 +104,17 @@ def order2(box: Box, points=(1.0, 2.0, 3.0, 10.0), Ks=None) -> dict:
     if len(pts) != 4 or len(set(pts)) != 4 or min(pts) <= 0:
         raise ValueError("order 2 needs four distinct positive interpolation points")
     Ks = [dtn_eval(box, sj) for sj in pts] if Ks is None else list(Ks)
+    if box.d == 1:
+        return _order2_1d(pts, Ks)
+    n = Ks[0].shape[0]
+    M, Y = _interp2_system(pts, Ks)
+    X = np.linalg.solve(M.T, Y.T).T
+    B1, B0, A1, A0 = (X[:, k * n:(k + 1) * n] for k in range(4))
+    return {"order": 2, "points": tuple(pts), "B1": B1, "B0": B0, "A1": A1, "A0": A0, "Ks": Ks}
+
+
+def _interp2_system(pts, Ks):
+    """M and Y of the order-2 interpolation conditions X M = Y, X = [B1 B0 A1 A0]."""
     n = Ks[0].shape[0]
     I = np.eye(n)
     M = np.zeros((4 * n, 4 * n), dtype=np.complex128)
@@ -103,9 +126,34 @@ def order2(box: Box, points=(1.0, 2.0, 3.0, 10.0), Ks=None) -> dict:
         M[2 * n:3 * n, cols] = sj * I
         M[3 * n:4 * n, cols] = I
         Y[:, cols] = sj * sj * Kj
-    X = np.linalg.solve(M.T, Y.T).T
-    B1, B0, A1, A0 = (X[:, k * n:(k + 1) * n] for k in range(4))
-    return {"order": 2, "points": tuple(pts), "B1": B1, "B0": B0, "A1": A1, "A0": A0, "Ks": Ks}
+    return M, Y
+
+
+def order2_end(pts, Ks) -> np.ndarray:
+    """One end of the 1D box: X = [B1 B0 A1 A0] (2 x 8) for the 2 x 2 blocks Ks at the
+    four points, the null direction fixed by the hidden-root rule of the module doc."""
+    M, Y = _interp2_system(pts, Ks)
+    U, S, Vh = np.linalg.svd(M)
+    if S[-1] > 1e-6 * S[-2]:                        # full rank: the unique solution
+        return np.linalg.solve(M.T, Y.T).T
+    x = U[:, -1].conj()                             # x M = 0
+    X0 = Y @ (Vh[:-1].conj().T @ np.diag(1.0 / S[:-1]) @ U[:, :-1].conj().T)
+    lam = -min(pts)
+    D0 = lam * lam * np.eye(2) - lam * X0[:, 0:2] - X0[:, 2:4]
+    adj = np.array([[D0[1, 1], -D0[0, 1]], [-D0[1, 0], D0[0, 0]]])
+    c = (lam * x[0:2] + x[2:4]) @ adj
+    w = np.conj(c) * np.linalg.det(D0) / np.vdot(c, c)
+    return X0 + np.outer(w, x)
+
+
+def _order2_1d(pts, Ks) -> dict:
+    """Order 2 on a 1D box: Gamma = [0, 1, n-2, n-1], K block diagonal over the ends."""
+    out = {k: np.zeros((4, 4), dtype=np.complex128) for k in ("B1", "B0", "A1", "A0")}
+    for ends in (slice(0, 2), slice(2, 4)):
+        X = order2_end(pts, [K[ends, ends] for K in Ks])
+        for k, key in enumerate(("B1", "B0", "A1", "A0")):
+            out[key][ends, ends] = X[:, 2 * k:2 * k + 2]
+    return {"order": 2, "points": tuple(pts), **out, "Ks": Ks}
 
 
 def rational22(co: dict, s: float) -> np.ndarray:

@@ -489,14 +489,16 @@ float tf32_rna(float v) {
 
 // Output tiles and work lists of the persistent GEMM for every orbital count
 // 1..max_orbitals (largest classes first), for the context's tile configuration
-// (tc_wide: 96 columns, one CTA per SM; else 64 columns, two CTAs per SM) and split
+// (tc_cfg: 0 96 columns, one CTA per SM; 1 64 columns, two CTAs per SM; 2 the Karatsuba
+// form, 64 columns, one CTA per SM) and split
 // choice (tc_split = 0: about two items per CTA slot; else that many K splits).
 int build_tc_plans(abc_ctx* c) {
     using namespace abc::dev;
     const Geometry& g = c->geo;
     const TcInfo& info = c->tci;
-    const int nmax = c->tc_wide ? TcWide::nmax : TcNarrow::nmax;
-    const int slots = c->tc_sms * (c->tc_wide ? TcWide::cps : TcNarrow::cps);
+    const int nmax = c->tc_cfg == 0 ? TcWide::nmax : c->tc_cfg == 1 ? TcNarrow::nmax : TcKara::nmax;
+    const int slots = c->tc_sms * (c->tc_cfg == 0 ? TcWide::cps : c->tc_cfg == 1 ? TcNarrow::cps : TcKara::cps);
+    const double a_chunk = c->tc_cfg == 2 ? (double)TcKara::a_bytes : (double)TC_A_BYTES;
     std::vector<int> order(g.cls.size());
     for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return g.cls[a].m > g.cls[b].m; });
@@ -544,7 +546,7 @@ int build_tc_plans(abc_ctx* c) {
                 const TcTile& x = tiles[w.tile];
                 const int nkb = info.nkb[x.cls];
                 const int nk = (int)((long long)nkb * (w.split + 1) / pl.nsplit - (long long)nkb * w.split / pl.nsplit);
-                return (nk + 2.0) * (TC_A_BYTES + (double)x.n * 64 * TC_B_PLANES);
+                return (nk + 2.0) * (a_chunk + (double)x.n * 64 * TC_B_PLANES);
             };
             std::stable_sort(its.begin(), its.end(), [&](const TcItem& a, const TcItem& b2) {
                 const double ca = item_cost(a), cb = item_cost(b2);
@@ -592,6 +594,64 @@ int build_tc_plans(abc_ctx* c) {
     return ABC_OK;
 }
 
+// The GEMM's A operand image: every class block split into hi / lo planes (TF32, or
+// FP16 after the class scale 2^es) in the shared-memory image of gemm_tc, per (128-row
+// tile, K block): 4 planes (Re hi, Re lo, Im hi, Im lo), or for the Karatsuba form 6
+// (the same plus (Re + Im) hi, lo).
+int pack_a_image(abc_ctx* c, bool kara) {
+    using namespace abc::dev;
+    const Geometry& g = c->geo;
+    const TcInfo& info = c->tci;
+    const bool f16 = c->tc_f16;
+    const int KB = f16 ? TcKind<TC_F16>::KB : TcKind<TC_TF32>::KB;
+    const int nplanes = kara ? 6 : 4;
+    const size_t per = (size_t)nplanes * TC_A_PLANE / 4;
+    const long long chunks = c->tc_chunks;
+    std::vector<float> pack((size_t)chunks * per, 0.0f);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long ch = 0; ch < chunks; ++ch) {
+        int k = 0;
+        while (k + 1 < (int)g.cls.size() && ch >= info.abase[k + 1]) ++k;
+        const int m = info.m[k], nkb = info.nkb[k];
+        const long long loc = ch - info.abase[k];
+        const int mt = (int)(loc / nkb), kb = (int)(loc % nkb);
+        const std::vector<cd>& S = c->blocks.mat[k];
+        float* dst = pack.data() + (size_t)ch * per;
+        __half* dh = reinterpret_cast<__half*>(dst);
+        const double sc = std::ldexp(1.0, info.es[k]);
+        for (int r = 0; r < TC_M; ++r) {
+            const int row = mt * TC_M + r;
+            if (row >= m) break;
+            for (int q = 0; q < KB; ++q) {
+                const int col = kb * KB + q;
+                if (col >= m) break;
+                const cd v = S[(size_t)row * m + col];
+                const double parts[3] = {v.real(), v.imag(), v.real() + v.imag()};
+                for (int pp = 0; pp < nplanes / 2; ++pp) {
+                    if (f16) {
+                        const float x = (float)(parts[pp] * sc);
+                        const __half xh = __float2half_rn(x);
+                        const size_t o = tc_core_offset_f16(r, q) / 2;
+                        dh[(2 * pp) * (TC_A_PLANE / 2) + o] = xh;
+                        dh[(2 * pp + 1) * (TC_A_PLANE / 2) + o] = __float2half_rn(x - __half2float(xh));
+                    } else {
+                        const float x = (float)parts[pp];
+                        const float xh = tf32_rna(x);
+                        const size_t o = tc_core_offset(r, q) / 4;
+                        dst[(2 * pp) * (TC_A_PLANE / 4) + o] = xh;
+                        dst[(2 * pp + 1) * (TC_A_PLANE / 4) + o] = tf32_rna(x - xh);
+                    }
+                }
+            }
+        }
+    }
+    DevBuf& out = kara ? c->tc_apack_k : c->tc_apack;
+    int st;
+    if ((st = out.alloc(pack.size() * sizeof(float)))) return st;
+    CUDA_TRY(cudaMemcpy(out.p, pack.data(), pack.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return ABC_OK;
+}
+
 // Tensor-core form of the many-orbital contraction: every class block split into
 // hi / lo planes of its real and imaginary parts (TF32, or FP16 after scaling the
 // block by 2^es), packed per (128-row tile, K block) in the shared-memory image of
@@ -623,49 +683,11 @@ int build_tc(abc_ctx* c) {
         if (mx > 0) std::frexp(mx, &ex);                 // mx = f 2^ex, f in [0.5, 1)
         info.es[k] = f16 && mx > 0 ? std::min(60, std::max(-60, TC_TARGET_EXP - ex)) : 0;
     }
-    const size_t per = TC_A_BYTES / 4;
-    std::vector<float> pack((size_t)chunks * per, 0.0f);
-#pragma omp parallel for schedule(dynamic, 4)
-    for (long long ch = 0; ch < chunks; ++ch) {
-        int k = 0;
-        while (k + 1 < (int)g.cls.size() && ch >= info.abase[k + 1]) ++k;
-        const int m = info.m[k], nkb = info.nkb[k];
-        const long long loc = ch - info.abase[k];
-        const int mt = (int)(loc / nkb), kb = (int)(loc % nkb);
-        const std::vector<cd>& S = c->blocks.mat[k];
-        float* dst = pack.data() + (size_t)ch * per;
-        __half* dh = reinterpret_cast<__half*>(dst);
-        const double sc = std::ldexp(1.0, info.es[k]);
-        for (int r = 0; r < TC_M; ++r) {
-            const int row = mt * TC_M + r;
-            if (row >= m) break;
-            for (int q = 0; q < KB; ++q) {
-                const int col = kb * KB + q;
-                if (col >= m) break;
-                const cd v = S[(size_t)row * m + col];
-                if (f16) {
-                    const float re = (float)(v.real() * sc), im = (float)(v.imag() * sc);
-                    const __half rh = __float2half_rn(re), ih = __float2half_rn(im);
-                    const size_t o = tc_core_offset_f16(r, q) / 2;
-                    dh[0 * (TC_A_PLANE / 2) + o] = rh;
-                    dh[1 * (TC_A_PLANE / 2) + o] = __float2half_rn(re - __half2float(rh));
-                    dh[2 * (TC_A_PLANE / 2) + o] = ih;
-                    dh[3 * (TC_A_PLANE / 2) + o] = __float2half_rn(im - __half2float(ih));
-                } else {
-                    const float re = (float)v.real(), im = (float)v.imag();
-                    const float rh = tf32_rna(re), ih = tf32_rna(im);
-                    const size_t o = tc_core_offset(r, q) / 4;
-                    dst[0 * (TC_A_PLANE / 4) + o] = rh;
-                    dst[1 * (TC_A_PLANE / 4) + o] = tf32_rna(re - rh);
-                    dst[2 * (TC_A_PLANE / 4) + o] = ih;
-                    dst[3 * (TC_A_PLANE / 4) + o] = tf32_rna(im - ih);
-                }
-            }
-        }
-    }
+    c->tc_f16 = f16;
+    c->tci = info;
+    c->tc_chunks = chunks;
     int st;
-    if ((st = c->tc_apack.alloc(pack.size() * sizeof(float)))) return st;
-    CUDA_TRY(cudaMemcpy(c->tc_apack.p, pack.data(), pack.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if ((st = pack_a_image(c, false))) return st;
     int sms = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     if (!c->err_flag.p) {
@@ -678,6 +700,8 @@ int build_tc(abc_ctx* c) {
                                   (int)TcNarrow::smem));
     CUDA_TRY(cudaFuncSetAttribute(gemm_tc<TC_F16, TcNarrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)TcNarrow::smem));
+    CUDA_TRY(cudaFuncSetAttribute(gemm_tc<TC_TF32, TcKara>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcKara::smem));
+    CUDA_TRY(cudaFuncSetAttribute(gemm_tc<TC_F16, TcKara>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcKara::smem));
     if (f16 && (st = c->tc_colexp.alloc(sizeof(int) * (size_t)rsum * c->params.max_orbitals))) return st;
     c->tc_f16 = f16;
     c->tc_ncols = rsum;
@@ -731,7 +755,12 @@ template <int KIND>
 void launch_gemm_tc(abc_ctx* c, const abc_ctx::TcPlan& pl, int n_orb, float2* out, int conj, const int* colexp,
                     cudaStream_t s) {
     const long long n = c->geo.n_gamma;
-    if (c->tc_wide)
+    if (c->tc_cfg == 2)
+        dev::gemm_tc<KIND, dev::TcKara><<<(unsigned)pl.grid, dev::TC_THREADS, dev::TcKara::smem, s>>>(
+            c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
+            c->tc_apack_k.as<float>(), c->tc_bpack.as<float>(), n_orb, (int)n, pl.nsplit, n * n_orb, out, conj,
+            c->err_flag.as<int>(), colexp);
+    else if (c->tc_cfg == 0)
         dev::gemm_tc<KIND, dev::TcWide><<<(unsigned)pl.grid, dev::TC_THREADS, dev::TcWide::smem, s>>>(
             c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
             c->tc_apack.as<float>(), c->tc_bpack.as<float>(), n_orb, (int)n, pl.nsplit, n * n_orb, out, conj,
@@ -778,17 +807,27 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
             const int ncols = c->tc_ncols * n_orb;
             dev::tc_colexp<<<(unsigned)((ncols + 7) / 8), 256, 0, s>>>(c->tci, n_orb, n, (const float2*)x,
                                                                        c->tc_colexp.as<int>(), ncols);
-            dev::pack_x_tc<dev::TC_F16><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
-                                                               n_orb, n, (const float2*)x, conj,
-                                                               c->tc_bpack.as<float>(), colexp);
+            if (c->tc_cfg == 2)
+                dev::pack_x_tc<dev::TC_F16, 1><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
+                                                                      n_orb, n, (const float2*)x, conj,
+                                                                      c->tc_bpack.as<float>(), colexp);
+            else
+                dev::pack_x_tc<dev::TC_F16><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
+                                                                   n_orb, n, (const float2*)x, conj,
+                                                                   c->tc_bpack.as<float>(), colexp);
             prof_end(c, ABC_KERNEL_PACK, s);
             prof_begin(c, ABC_KERNEL_CONTRACTION, s);
             launch_gemm_tc<dev::TC_F16>(c, pl, n_orb, out, conj, colexp, s);
             c->launches += 2;
         } else {
-            dev::pack_x_tc<dev::TC_TF32><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
-                                                                n_orb, n, (const float2*)x, conj,
-                                                                c->tc_bpack.as<float>(), colexp);
+            if (c->tc_cfg == 2)
+                dev::pack_x_tc<dev::TC_TF32, 1><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
+                                                                       n_orb, n, (const float2*)x, conj,
+                                                                       c->tc_bpack.as<float>(), colexp);
+            else
+                dev::pack_x_tc<dev::TC_TF32><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
+                                                                    n_orb, n, (const float2*)x, conj,
+                                                                    c->tc_bpack.as<float>(), colexp);
             prof_end(c, ABC_KERNEL_PACK, s);
             prof_begin(c, ABC_KERNEL_CONTRACTION, s);
             launch_gemm_tc<dev::TC_TF32>(c, pl, n_orb, out, conj, colexp, s);
@@ -1786,7 +1825,7 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
             }
             const int ns = ctx->tc_b[n_orb].nsplit;
             const double eb = ctx->tc_f16 ? 2.0 : 4.0;        // bytes per split-plane element
-            *bytes = a * 4 * eb + x * 6 * eb + x * ns * 8;
+            *bytes = a * (ctx->tc_cfg == 2 ? 6 : 4) * eb + x * 6 * eb + x * ns * 8;
             return ABC_OK;
         } else {
             for (int p = 0; p < ctx->bi.n; ++p) entries += (double)ctx->bi.nseg * ctx->bi.m[p] * ctx->bi.m[p];
@@ -1815,7 +1854,17 @@ extern "C" int abc_kernel_flops(const abc_ctx* ctx, int kernel, int n_orb, doubl
     double u = 0;
     for (int k = 0; k < ctx->ci.n; ++k) u += 8.0 * ctx->bi.nseg * ctx->ci.R[k] * (double)ctx->ci.m[k] * ctx->ci.m[k];
     *useful = u * n_orb;
-    *issued = (ctx->tc && n_orb > 1) ? 3.0 * *useful : *useful;   // three products per split term
+    if (ctx->tc && n_orb > 1) {
+        *issued = (ctx->tc_cfg == 2 ? 2.25 : 3.0) * *useful;       // three products per split term (x 3/4: Karatsuba)
+    } else if (n_orb > 1) {
+        // the CUDA-core GEMM multiplies every entry of the stored blocks (bi) by each
+        // orbital's right-hand side
+        double e = 0;
+        for (int p = 0; p < ctx->bi.n; ++p) e += (double)ctx->bi.nseg * ctx->bi.m[p] * ctx->bi.m[p];
+        *issued = 8.0 * e * n_orb;
+    } else {
+        *issued = *useful;
+    }
     return ABC_OK;
 }
 
@@ -1851,16 +1900,16 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         return ABC_OK;
     }
     if (key == ABC_TUNE_GEMM_TILE || key == ABC_TUNE_GEMM_SPLIT) {
-        if (key == ABC_TUNE_GEMM_TILE && (value < 0 || value > 1)) return fail(ABC_ERR_ARG, "GEMM tile must be 0 or 1");
+        if (key == ABC_TUNE_GEMM_TILE && (value < 0 || value > 2)) return fail(ABC_ERR_ARG, "GEMM tile must be 0, 1 or 2");
         if (key == ABC_TUNE_GEMM_SPLIT && (value < 0 || value > 8)) return fail(ABC_ERR_ARG, "GEMM split must be 0..8");
-        if (key == ABC_TUNE_GEMM_TILE) ctx->tc_wide = value == 0;
-        else ctx->tc_split = (int)value;
         drop_graphs(ctx);
-        if (ctx->tc) {
-            CUDA_TRY(cudaDeviceSynchronize());       // the old work lists may be in use
-            return build_tc_plans(ctx);
-        }
-        return ABC_OK;
+        if (ctx->tc) CUDA_TRY(cudaDeviceSynchronize());   // the old work lists may be in use
+        if (key == ABC_TUNE_GEMM_TILE) ctx->tc_cfg = (int)value;
+        else ctx->tc_split = (int)value;
+        if (!ctx->tc) return ABC_OK;
+        int st;
+        if (ctx->tc_cfg == 2 && !ctx->tc_apack_k.p && (st = pack_a_image(ctx, true))) return st;
+        return build_tc_plans(ctx);
     }
     if (key == ABC_TUNE_FORWARD_RW) {
         ctx->fwd_rw = value != 0;
@@ -1902,7 +1951,7 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_CHAIN) { *value = ctx->chain ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL) { *value = ctx->stencil_mode; return ABC_OK; }
     if (key == ABC_TUNE_FUSED) { *value = ctx->fused_mode; return ABC_OK; }
-    if (key == ABC_TUNE_GEMM_TILE) { *value = ctx->tc_wide ? 0 : 1; return ABC_OK; }
+    if (key == ABC_TUNE_GEMM_TILE) { *value = ctx->tc_cfg; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL_BPS) { *value = ctx->stencil_bps; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL_KZ) { *value = ctx->stencil_kz; return ABC_OK; }
     if (key == ABC_TUNE_BACK_MULTI) { *value = ctx->back_multi ? 1 : 0; return ABC_OK; }

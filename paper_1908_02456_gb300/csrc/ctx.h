@@ -96,7 +96,9 @@ struct abc_ctx {
     abc::dev::TcInfo tci{};
     abc::DevBuf tc_apack, tc_tiles, tc_cols, tc_bpack, tc_part;
     bool tc_f16 = false;             // ABC_C64_SPLIT_FP16: kind::f16 operands with power-of-two scales
-    bool tc_wide = true;             // GEMM tiles: 96 columns, one CTA per SM (else 64, two per SM)
+    int tc_cfg = 0;                  // GEMM form (ABC_TUNE_GEMM_TILE): 0 96 columns x 1 CTA/SM, 1 64 x 2, 2 Karatsuba
+    long long tc_chunks = 0;         // (128-row tile, K block) chunks of the A image
+    abc::DevBuf tc_apack_k;          // the Karatsuba form's A image (built when first selected)
     int tc_split = 0;                // GEMM K splits: 0 = about two items per CTA slot
     int tc_ncols = 0;                // right-hand sides over all classes (column scales per orbital)
     abc::DevBuf tc_colexp;           // TC_F16: per-column scale exponents of the current contraction

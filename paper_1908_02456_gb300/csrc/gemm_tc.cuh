@@ -73,16 +73,23 @@ constexpr int TC_PACK_KB = 4;                      // K blocks packed per pack_x
 // Tile configurations of the persistent GEMM (chosen per shape by the autotuner):
 // NMX output columns at most per tile, STG ring stages, CPS resident CTAs per SM.
 // TMEM holds two accumulators of 2 NMX columns (rounded up to a power of two).
-template <int NMX, int STG, int CPS>
+// KARA = 1: the complex product by Karatsuba's three real products, P1 = Sr Xr,
+// P2 = Si Xi, P3 = (Sr + Si)(Xr + Xi), Re T = P1 - P2, Im T = P3 - P1 - P2: 9 MMAs of
+// width N per K step instead of 6 of width 2N (a quarter less tensor work), with a
+// third pair of A planes (Sr + Si, hi and lo) and three accumulators of N columns.
+template <int NMX, int STG, int CPS, int KARA = 0>
 struct TcCfg {
-    static constexpr int nmax = NMX, stages = STG, cps = CPS;
+    static constexpr int nmax = NMX, stages = STG, cps = CPS, kara = KARA;
+    static constexpr uint32_t a_bytes = (KARA ? 6u : 4u) * TC_A_PLANE;
     static constexpr uint32_t b_stage = (uint32_t)TC_B_PLANES * NMX * 64;
-    static constexpr uint32_t tmem_cols = 4 * NMX > 256 ? 512 : 4 * NMX > 128 ? 256 : 128;
+    static constexpr uint32_t acc_cols = (KARA ? 3 : 2) * NMX;     // one item's accumulators
+    static constexpr uint32_t tmem_cols = 2 * acc_cols > 256 ? 512 : 2 * acc_cols > 128 ? 256 : 128;
     static constexpr uint32_t buf_cols = tmem_cols / 2;
-    static constexpr size_t smem = (size_t)STG * (TC_A_BYTES + b_stage) + 256;
+    static constexpr size_t smem = (size_t)STG * (a_bytes + b_stage) + 256;
 };
 typedef TcCfg<96, 3, 1> TcWide;                    // 96 columns, one CTA per SM
 typedef TcCfg<64, 2, 2> TcNarrow;                  // 64 columns, two CTAs per SM
+typedef TcCfg<64, 3, 1, 1> TcKara;                 // Karatsuba, 64 columns, one CTA per SM
 constexpr long long TC_WAIT_LIMIT = 1ll << 24;
 
 // Byte offset of element (row r, k) inside a K-major no-swizzle plane of 16-deep
@@ -195,7 +202,7 @@ struct TcItem {
 // nkb / TC_PACK_KB), 128 threads, TC_PACK_KB consecutive K blocks per block; x
 // orbital-major (o * ng + j).  TC_F16: FP16 hi + lo of the
 // column scaled by 2^colexp[column], 8 elements per 16-byte core-matrix row.
-template <int KIND>
+template <int KIND, int KARA = 0>
 __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCols* __restrict__ cols, int n_orb, int ng,
                                                  const float2* __restrict__ x, int conj, float* __restrict__ bpack,
                                                  const int* __restrict__ colexp) {
@@ -223,9 +230,45 @@ __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCols* __re
             re[e] = v.x * sc;
             im[e] = v.y * sc;
         }
+        // Karatsuba planes: (Xr, Xi, Xr + Xi), conj: the same of conj(X)
+        if constexpr (KARA) {
+#pragma unroll
+            for (int e = 0; e < EPR; ++e) {
+                if (conj) im[e] = -im[e];
+            }
+        }
         // planes 0-2 (hi) and 3-5 (lo) of this 16-byte row
         uint32_t w[6][4];
-        if constexpr (KIND == TC_F16) {
+        if constexpr (KARA) {
+            float sm[EPR];
+#pragma unroll
+            for (int e = 0; e < EPR; ++e) sm[e] = re[e] + im[e];
+            if constexpr (KIND == TC_F16) {
+#pragma unroll
+                for (int e2 = 0; e2 < 4; ++e2) {
+                    const float* src[3] = {re, im, sm};
+#pragma unroll
+                    for (int pl = 0; pl < 3; ++pl) {
+                        const __half2 hh = __floats2half2_rn(src[pl][2 * e2], src[pl][2 * e2 + 1]);
+                        const float2 hf = __half22float2(hh);
+                        const __half2 ll = __floats2half2_rn(src[pl][2 * e2] - hf.x, src[pl][2 * e2 + 1] - hf.y);
+                        w[pl][e2] = *reinterpret_cast<const uint32_t*>(&hh);
+                        w[3 + pl][e2] = *reinterpret_cast<const uint32_t*>(&ll);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float* src[3] = {re, im, sm};
+#pragma unroll
+                    for (int pl = 0; pl < 3; ++pl) {
+                        const uint32_t hh = tf32_hi(src[pl][e]);
+                        w[pl][e] = hh;
+                        w[3 + pl][e] = tf32_hi(src[pl][e] - __uint_as_float(hh));
+                    }
+                }
+            }
+        } else if constexpr (KIND == TC_F16) {
             const uint32_t sgn = 0x80008000u;
 #pragma unroll
             for (int e2 = 0; e2 < 4; ++e2) {
@@ -320,11 +363,12 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
         int ng, int nsplit, long long split_stride, float2* __restrict__ out, int conj, int* __restrict__ err,
         const int* __restrict__ colexp) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    unsigned char* sA = tc_smem;                                       // [stage][4 planes]
+    unsigned char* sA = tc_smem;                                       // [stage][4 or 6 planes]
     constexpr int TC_STAGES = CFG::stages;
     constexpr uint32_t SB = CFG::b_stage;                              // smem bytes of one X stage
-    unsigned char* sB = tc_smem + (size_t)TC_STAGES * TC_A_BYTES;      // [stage][6 planes]
-    uint64_t* full = reinterpret_cast<uint64_t*>(tc_smem + (size_t)TC_STAGES * (TC_A_BYTES + SB));
+    constexpr uint32_t SA = CFG::a_bytes;                              // smem bytes of one A stage
+    unsigned char* sB = tc_smem + (size_t)TC_STAGES * SA;              // [stage][6 planes]
+    uint64_t* full = reinterpret_cast<uint64_t*>(tc_smem + (size_t)TC_STAGES * (SA + SB));
     uint64_t* empty = full + TC_STAGES;
     uint64_t* tfull = empty + TC_STAGES;                               // [2] accumulators ready
     uint64_t* tempty = tfull + 2;                                      // [2] accumulators drained
@@ -363,15 +407,14 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
             const TcTile tile = tiles[w.tile];
             const int c = tile.cls, nkb = info.nkb[c], N = tile.n;
             const int kb0 = (int)((long long)nkb * w.split / nsplit), kb1 = (int)((long long)nkb * (w.split + 1) / nsplit);
-            const float* achunk =
-                apack + (size_t)(info.abase[c] + (long long)(tile.row0 / TC_M) * nkb) * (TC_A_BYTES / 4);
+            const float* achunk = apack + (size_t)(info.abase[c] + (long long)(tile.row0 / TC_M) * nkb) * (SA / 4);
             const float* bchunk = bpack + (size_t)tile.bchunk0 * (TC_B_BYTES / 4);
             const uint32_t b_bytes = (uint32_t)N * 64 * TC_B_PLANES;
             for (int kb = kb0; kb < kb1 && ok; ++kb, ++issued) {
                 const int st = (int)(issued % TC_STAGES);
                 if (issued >= TC_STAGES) ok &= mbar_wait_bounded(&empty[st], (uint32_t)((issued / TC_STAGES - 1) & 1));
-                mbar_expect_tx(&full[st], TC_A_BYTES + b_bytes);
-                bulk_g2s(sA + (size_t)st * TC_A_BYTES, achunk + (size_t)kb * (TC_A_BYTES / 4), TC_A_BYTES, &full[st]);
+                mbar_expect_tx(&full[st], SA + b_bytes);
+                bulk_g2s(sA + (size_t)st * SA, achunk + (size_t)kb * (SA / 4), SA, &full[st]);
                 bulk_g2s(sB + (size_t)st * SB, bchunk + (size_t)kb * (TC_B_BYTES / 4), b_bytes, &full[st]);
             }
         }
@@ -388,8 +431,8 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
             const int buf = q & 1;
             if (q >= 2) ok &= mbar_wait_bounded(&tempty[buf], (uint32_t)((q / 2 - 1) & 1));
             tc_fence_after();
-            const uint32_t idesc = tc_idesc<KIND>(2 * N);
-            const uint32_t d = tmem + buf * CFG::buf_cols;                // [Re | Im], 2N columns
+            const uint32_t idesc = tc_idesc<KIND>(CFG::kara ? N : 2 * N);
+            const uint32_t d = tmem + buf * CFG::buf_cols;                // [Re | Im] (2N) or [P1 | P2 | P3] (3N)
             const uint32_t pb = (uint32_t)N * 64;                         // X plane stride in the chunk
             // windows of two planes: [Xr | Xi] and [-Xi | Xr] (conj: [Xr | Xi] and [Xi | -Xr])
             const uint32_t wr = conj ? 0u : pb, wi = conj ? pb : 0u, lo = 3 * pb;
@@ -397,7 +440,26 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
                 const int st = (int)(g % TC_STAGES);
                 ok &= mbar_wait_bounded(&full[st], (uint32_t)((g / TC_STAGES) & 1));
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(sA + (size_t)st * TC_A_BYTES), b0 = smem_u32(sB + (size_t)st * SB);
+                const uint32_t a0 = smem_u32(sA + (size_t)st * SA), b0 = smem_u32(sB + (size_t)st * SB);
+                if constexpr (CFG::kara) {
+#pragma unroll
+                    for (int ks = 0; ks < TC_KB / 8; ++ks) {
+                        const uint32_t ko = ks * 256;
+                        const uint32_t acc0 = (kb > kb0 || ks > 0) ? 1u : 0u;
+#pragma unroll
+                        for (int pr = 0; pr < 3; ++pr) {       // P1 = Sr Xr, P2 = Si Xi, P3 = Ss Xs
+                            const uint64_t ah = tc_desc(a0 + (2 * pr) * TC_A_PLANE + ko);
+                            const uint64_t al = tc_desc(a0 + (2 * pr + 1) * TC_A_PLANE + ko);
+                            const uint64_t bh = tc_desc(b0 + pr * pb + ko), bl = tc_desc(b0 + lo + pr * pb + ko);
+                            const uint32_t dp = d + pr * (uint32_t)N;
+                            tc_mma<KIND>(dp, ah, bh, idesc, acc0);
+                            tc_mma<KIND>(dp, ah, bl, idesc, 1u);
+                            tc_mma<KIND>(dp, al, bh, idesc, 1u);
+                        }
+                    }
+                    tc_commit(&empty[st]);
+                    continue;
+                }
 #pragma unroll
                 for (int ks = 0; ks < TC_KB / 8; ++ks) {
                     const uint32_t ko = ks * 256;      // two core matrices along K per MMA
@@ -445,7 +507,19 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
                 if (any) {
                     tc_ld16(lane_base + buf * CFG::buf_cols + c0, pr);
                     tc_ld16(lane_base + buf * CFG::buf_cols + N + c0, pi);
-                    tc_wait_ld();
+                    if constexpr (CFG::kara) {
+                        float p3[16];
+                        tc_ld16(lane_base + buf * CFG::buf_cols + 2 * N + c0, p3);
+                        tc_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {       // Re = P1 - P2, Im = P3 - P1 - P2 (conj: -Im)
+                            const float re = pr[i] - pi[i], im = p3[i] - pr[i] - pi[i];
+                            pr[i] = re;
+                            pi[i] = conj ? -im : im;
+                        }
+                    } else {
+                        tc_wait_ld();
+                    }
                 }
                 if (row < m) {
 #pragma unroll

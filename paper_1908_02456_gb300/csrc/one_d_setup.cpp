@@ -12,6 +12,7 @@
 // Then eq:eval, K = -(I - H_{Gamma,Sigma} G_{Sigma,Gamma})^{-1} H_{Gamma,Sigma}
 // G_{Sigma,Sigma} H_{Sigma,Gamma}, and the order-0/1/2 coefficients of the 3D library,
 // here as 2 x 2 blocks.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <string>
@@ -52,6 +53,114 @@ bool solve(std::vector<cd> A, std::vector<cd>& B, int n, int m) {
         }
     }
     return true;
+}
+
+// One-sided (Hestenes) Jacobi SVD of a square complex matrix B (row-major n x n):
+// unitary plane rotations from the right make the columns of B V mutually orthogonal.
+// On return B holds W = B V (column k has norm sigma_k), V the accumulated rotations
+// (row-major, column k the right singular vector k).  Each rotation first turns the
+// phase of column q so that the pair's Gram matrix is real, then applies the real
+// symmetric Schur rotation of that 2 x 2 Gram matrix (Golub and Van Loan, Sec. 8.6).
+void jacobi_svd(std::vector<cd>& B, std::vector<cd>& V, int n) {
+    V.assign((size_t)n * n, cd(0.0));
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        bool rotated = false;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double al = 0, be = 0;
+                cd ga = 0;
+                for (int i = 0; i < n; ++i) {
+                    const cd bp = B[(size_t)i * n + p], bq = B[(size_t)i * n + q];
+                    al += std::norm(bp);
+                    be += std::norm(bq);
+                    ga += std::conj(bp) * bq;
+                }
+                const double g = std::abs(ga);
+                if (g <= 1e-15 * std::sqrt(al * be) || g == 0.0) continue;
+                rotated = true;
+                const cd ph = std::conj(ga / g);
+                const double zeta = (be - al) / (2.0 * g);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+                for (std::vector<cd>* m : {&B, &V})
+                    for (int i = 0; i < n; ++i) {
+                        cd& xp = (*m)[(size_t)i * n + p];
+                        cd& xq = (*m)[(size_t)i * n + q];
+                        const cd a = xp, b = xq * ph;
+                        xp = c * a - sn * b;
+                        xq = sn * a + c * b;
+                    }
+            }
+        if (!rotated) break;
+    }
+}
+
+// The order-2 interpolation conditions of one end, X M = Y with X = [B1 B0 A1 A0]
+// (2 x 8), given as Mt = M^T and Yt = Y^T (row-major 8 x 8 and 8 x 2).  For the
+// five-point scheme M has a one-dimensional null space: a fixed row combination of
+// K(s) obeys a first-degree identity (s b1 + b0) K(s) = -(s a1 + a0) for every s, so
+// the solutions X0 + w x (x the null row, w any 2-vector) share R_22(s) for every s and
+// differ only in one hidden root of det(s^2 I - s B1 - B0), which rounding excites and
+// which for some w lies in the right half-plane.  Here X0 is the minimum-norm solution
+// (pseudo-inverse of rank 7) and w the shortest vector that puts the hidden root at
+// s = -min(s_j): by the determinant lemma det(D0(l) - w r) = det D0(l) - r adj(D0(l)) w
+// with D0(l) = l^2 I - l B1 - B0 of X0 and r = l x_B1 + x_B0, one linear condition.  A
+// system of full numerical rank is solved as it stands.
+int fit_order2_end(const std::vector<cd>& Mt, const std::vector<cd>& Yt, double lam, cd X[2][8],
+                   std::string& err) {
+    std::vector<cd> B(64), V;
+    for (int i = 0; i < 64; ++i) B[i] = std::conj(Mt[i]);          // B = M^H
+    jacobi_svd(B, V, 8);                                            // M = V diag(sigma) (B V / sigma)^H
+    double sig[8];
+    int order[8];
+    for (int k = 0; k < 8; ++k) {
+        double v = 0;
+        for (int i = 0; i < 8; ++i) v += std::norm(B[i * 8 + k]);
+        sig[k] = std::sqrt(v);
+        order[k] = k;
+    }
+    std::sort(order, order + 8, [&](int a, int b) { return sig[a] > sig[b]; });
+    const int kmin = order[7];
+    if (sig[kmin] > 1e-6 * sig[order[6]]) {
+        std::vector<cd> Y = Yt;
+        if (!solve(Mt, Y, 8, 2)) { err = "order-2 interpolation system singular"; return ABC_ERR_SINGULAR; }
+        for (int r = 0; r < 2; ++r)
+            for (int k = 0; k < 8; ++k) X[r][k] = Y[k * 2 + r];
+        return ABC_OK;
+    }
+    if (!(sig[order[6]] > 1e-14 * sig[order[0]])) {
+        err = "order-2 interpolation system has more than one null direction";
+        return ABC_ERR_SINGULAR;
+    }
+    cd x[8];
+    for (int k = 0; k < 8; ++k) x[k] = std::conj(V[k * 8 + kmin]);      // x M = 0
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 8; ++k) X[r][k] = 0.0;
+    for (int kk = 0; kk < 8; ++kk) {
+        if (kk == kmin) continue;
+        for (int r = 0; r < 2; ++r) {
+            cd yw = 0;                                                  // Y w_kk
+            for (int col = 0; col < 8; ++col) yw += Yt[col * 2 + r] * B[col * 8 + kk];
+            yw /= sig[kk] * sig[kk];
+            for (int k = 0; k < 8; ++k) X[r][k] += yw * std::conj(V[k * 8 + kk]);
+        }
+    }
+    cd D0[2][2];
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 2; ++k) D0[r][k] = (r == k ? lam * lam : 0.0) - lam * X[r][k] - X[r][2 + k];
+    const cd adj[2][2] = {{D0[1][1], -D0[0][1]}, {-D0[1][0], D0[0][0]}};
+    const cd det = D0[0][0] * D0[1][1] - D0[0][1] * D0[1][0];
+    const cd rv[2] = {lam * x[0] + x[2], lam * x[1] + x[3]};
+    cd c[2];
+    for (int j = 0; j < 2; ++j) c[j] = rv[0] * adj[0][j] + rv[1] * adj[1][j];
+    const double cn = std::norm(c[0]) + std::norm(c[1]);
+    if (!(cn > 0.0)) { err = "order-2 hidden root cannot be placed"; return ABC_ERR_SINGULAR; }
+    for (int r = 0; r < 2; ++r) {
+        const cd w = std::conj(c[r]) * det / cn;
+        for (int k = 0; k < 8; ++k) X[r][k] += w * x[k];
+    }
+    return ABC_OK;
 }
 
 Mat2 mul(const Mat2& a, const Mat2& b) {
@@ -204,13 +313,17 @@ int build_blocks(const abc1d_params& p, Blocks1D& out, std::string& err) {
             }
             for (int r = 0; r < 2; ++r) Y[col * 2 + r] = p.s[j] * p.s[j] * Ks[j].v[r][c];
         }
-    if (!solve(Mt, Y, 8, 2)) { err = "order-2 interpolation system singular"; return ABC_ERR_SINGULAR; }
+    double smin = p.s[0];
+    for (int j = 1; j < 4; ++j) smin = std::min(smin, p.s[j]);
+    cd X[2][8];
+    const int st = fit_order2_end(Mt, Y, -smin, X, err);
+    if (st != ABC_OK) return st;
     for (int r = 0; r < 2; ++r)
         for (int k = 0; k < 2; ++k) {
-            out.B1.v[r][k] = Y[(0 + k) * 2 + r];
-            out.B0.v[r][k] = Y[(2 + k) * 2 + r];
-            out.A1.v[r][k] = Y[(4 + k) * 2 + r];
-            out.A0.v[r][k] = Y[(6 + k) * 2 + r];
+            out.B1.v[r][k] = X[r][0 + k];
+            out.B0.v[r][k] = X[r][2 + k];
+            out.A1.v[r][k] = X[r][4 + k];
+            out.A0.v[r][k] = X[r][6 + k];
         }
     return ABC_OK;
 }
@@ -223,12 +336,6 @@ int check_params(const abc1d_params* p, std::string& err) {
     if (p->precision != ABC_FP64 && p->precision != ABC_C64_FP32) {
         err = "precision must be ABC_FP64 or ABC_C64_FP32";
         return ABC_ERR_ARG;
-    }
-    if (p->order == 2 && p->precision != ABC_FP64) {
-        // the second-order blocks at close interpolation points carry large, cancelling
-        // entries: FP32 loses the result (measured 6e-2 relative after 2000 steps)
-        err = "the 1D second-order ABC needs ABC_FP64";
-        return ABC_ERR_UNSUPPORTED;
     }
     const int npts = p->order == 2 ? 4 : (p->order == 1 && p->fit1 == ABC_FIT1_TWO_POINT) ? 2 : 1;
     if (p->order == 1 && p->fit1 != ABC_FIT1_LIMIT && p->fit1 != ABC_FIT1_TWO_POINT) {

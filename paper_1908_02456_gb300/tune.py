@@ -4,9 +4,9 @@ The fastest form of a time step depends on the grid, the orbital count, the
 precision and the device, so the library exposes its choices as tuning knobs
 (``abc_set_tuning``) and this module picks them by timing:
 
-* the tensor-core GEMM's tile configuration (``TUNE_GEMM_TILE``: 96-column tiles with
-  one CTA per SM, or 64-column tiles with two) and its K split count
-  (``TUNE_GEMM_SPLIT``: automatic, or 1, 2, 4 splits per output tile);
+* the tensor-core GEMM's form (``TUNE_GEMM_TILE``: 96-column tiles with one CTA per
+  SM, 64-column tiles with two, or the Karatsuba form with three real products) and its
+  K split count (``TUNE_GEMM_SPLIT``: automatic, or 1, 2 splits per output tile);
 * the interior stencil of an order-1 step: the four Horner stages fused in time
   (``TUNE_FUSED``) or stage by stage, and for the latter where the stencil runs
   beside the boundary chain (``TUNE_STENCIL``) and how many planes each of its threads
@@ -60,7 +60,7 @@ def knob_groups(ctx: abc.Context, n_orb: int):
     tc = ctx.precision in (abc.C64_3XTF32, abc.C64_SPLIT_FP16) and n_orb >= 2 and ctx.order < 2 \
         and ctx.fit1 == abc.FIT1_LIMIT
     if tc:
-        groups.append([{abc.TUNE_GEMM_TILE: t, abc.TUNE_GEMM_SPLIT: sp} for t in (0, 1) for sp in (0, 1, 2, 4)])
+        groups.append([{abc.TUNE_GEMM_TILE: t, abc.TUNE_GEMM_SPLIT: sp} for t in (0, 1, 2) for sp in (0, 1, 2)])
     if ctx.order == 1 and ctx.precision != abc.FP64:
         nx = ctx.shape[0]
         stencil = [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: m, abc.TUNE_STENCIL_KZ: 0} for m in (0, 1, 2)]
@@ -142,7 +142,7 @@ def tune(ctx: abc.Context, psi, aux, V, dt: float, meanfield=None, steps: int = 
 
 def describe(setting: dict) -> dict:
     """Readable names of a setting returned by tune()."""
-    names = {abc.TUNE_GEMM_TILE: "gemm_tile(0=96 cols x 1 CTA/SM, 1=64 cols x 2 CTAs/SM)",
+    names = {abc.TUNE_GEMM_TILE: "gemm_tile(0=96 cols x 1 CTA/SM, 1=64 cols x 2 CTAs/SM, 2=Karatsuba 64 cols)",
              abc.TUNE_GEMM_SPLIT: "gemm_split(0=auto)", abc.TUNE_FUSED: "fused_stencil",
              abc.TUNE_STENCIL: "stencil_placement(0=after contraction, 1=stage start, 2=serial)",
              abc.TUNE_STENCIL_BPS: "stencil_blocks_per_sm(0=one thread per pair)",

@@ -30,7 +30,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
-@pytest.mark.parametrize("tile,split", [(0, 0), (0, 1), (0, 4), (1, 0), (1, 2), (1, 8)])
+@pytest.mark.parametrize("tile,split", [(0, 0), (0, 1), (0, 4), (1, 0), (1, 2), (1, 8), (2, 0), (2, 1), (2, 3)])
 def test_gemm_settings_against_oracle(env, prec, tile, split):
     torch, abc = env
     dims, h, dt, b = (22, 22, 22), 0.45, 0.005, 40

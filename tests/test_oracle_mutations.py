@@ -134,3 +134,34 @@ def test_meanfield_energy_mistakes_are_caught():
     for bad in (_EnergyFullA, _EnergyWrongB, _EnergyPowerOnePlusAlpha):
         assert not energy_drift_ok(bad), bad.__name__
     assert not energy_scaling_ok(_EnergyPowerOnePlusAlpha)
+
+
+# ---- the second-order fit on a 1D box (hidden root at -min(s_j)) ----
+from order2_pins import end_blocks, fit_ok, system  # noqa: E402
+
+
+def _fit_copy(pts, Ks, sign=-1.0, place=True, ypow=2):
+    """A copy of the oracle's one-end order-2 fit with one slip selectable."""
+    M, Y = system(pts, Ks)
+    if ypow != 2:
+        Y = Y / np.repeat(np.asarray(pts), 2)[None, :] ** (2 - ypow)
+    U, S, Vh = np.linalg.svd(M)
+    x = U[:, -1].conj()
+    X0 = Y @ (Vh[:-1].conj().T @ np.diag(1.0 / S[:-1]) @ U[:, :-1].conj().T)
+    if not place:
+        return X0
+    lam = sign * min(pts)
+    D0 = lam * lam * np.eye(2) - lam * X0[:, 0:2] - X0[:, 2:4]
+    adj = np.array([[D0[1, 1], -D0[0, 1]], [-D0[1, 0], D0[0, 0]]])
+    c = (lam * x[0:2] + x[2:4]) @ adj
+    w = np.conj(c) * np.linalg.det(D0) / np.vdot(c, c)
+    return X0 + np.outer(w, x)
+
+
+def test_order2_1d_fit_mistakes_are_caught():
+    pts = (10.0, 11.0, 20.0, 21.0)
+    _, Ks = end_blocks(0.05, 240, pts)
+    assert fit_ok(pts, Ks, _fit_copy(pts, Ks))                    # the copy itself passes
+    assert not fit_ok(pts, Ks, _fit_copy(pts, Ks, sign=1.0))      # hidden root at +min(s_j)
+    assert not fit_ok(pts, Ks, _fit_copy(pts, Ks, place=False))   # hidden root left where it falls
+    assert not fit_ok(pts, Ks, _fit_copy(pts, Ks, ypow=1))        # s_j K_j for s_j^2 K_j
