@@ -368,6 +368,13 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           transform with each slot's 8-point reflection transform in
  *                           one thread's registers (no lane shuffles; bit-identical
  *                           outputs); 0 (default) across 8 lanes.
+ *   ABC_TUNE_GAMMA_COPY     complex64, radius 1, nx even, orders 0 and 1, n_orb a multiple
+ *                           of 4: 1 each stage's stencil also writes its output on Gamma in
+ *                           the natural boundary layout (two copies, 2 n_gamma max_orbitals
+ *                           complex values, allocated on first use), and the next stage's
+ *                           forward transform reads it there instead of gathering single
+ *                           values from the whole state; 0 (default) gathers from the
+ *                           state.  Bit-identical results either way.
  *   ABC_TUNE_GEMM_TILE      tensor-core forms, n_orb >= 2: 0 (default) output tiles of up
  *                           to 96 columns, three ring stages, one CTA per SM; 1: up to 64
  *                           columns, two stages, two CTAs per SM; 2: the complex products
@@ -394,6 +401,7 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
 #define ABC_TUNE_STENCIL_KZ 9
 #define ABC_TUNE_BACK_MULTI 10
 #define ABC_TUNE_FORWARD_RW 11
+#define ABC_TUNE_GAMMA_COPY 12
 int abc_set_tuning(abc_ctx* ctx, int key, long long value);
 int abc_get_tuning(const abc_ctx* ctx, int key, long long* value);
 

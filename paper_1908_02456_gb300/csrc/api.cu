@@ -172,6 +172,8 @@ int upload_matrices(abc_ctx* c) {
     return ABC_OK;
 }
 
+int ensure_gam(abc_ctx* c);
+
 int ensure_workspace(abc_ctx* c) {
     const size_t cb = cplx_bytes(c);
     const size_t b = (size_t)c->params.max_orbitals;
@@ -894,9 +896,12 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
 // the contraction: its CTAs each need a whole SM (shared memory), so stencil blocks
 // resident at its launch would hold back its start; forked after it, the stencil
 // overlaps the back transform instead.
+// g_in / g_out (complex64 stages with the Gamma copy, else NULL): the forward transform
+// reads w on Gamma from g_in, and the stencil writes the stage output on Gamma to g_out.
 template <typename T>
 void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, const void* y_phi, const void* y_f,
-           void* o_phi, void* o_f, const T* V, cudaStream_t s, int st = -1) {
+           void* o_phi, void* o_f, const T* V, cudaStream_t s, int st = -1, const void* g_in = nullptr,
+           void* g_out = nullptr) {
     typedef typename dev::C2<T>::t Vc;
     const Geometry& g = c->geo;
     const int order = c->params.order;
@@ -922,7 +927,7 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             // beside the boundary chain: a bounded number of blocks per SM, grid-stride
             dev::stencil_stage_x2_gs<<<(unsigned)(c->tc_sms_all * c->stencil_bps), 256, 0, ss>>>(
                 g.nx, g.ny, g.nz, n_orb, (float)(1.0 / (g.h * g.h)), (const float2*)w_phi, (const float2*)y_phi,
-                (const float*)V, (const float2*)bt, (float2*)o_phi, (float)cdt);
+                (const float*)V, (const float2*)bt, (float2*)o_phi, (float)cdt, (float2*)g_out);
         } else if (sizeof(T) == 4 && (g.nx & 1) == 0 && c->stencil_kz == 1) {
             // complex64, even rows: two nodes per thread, registers capped for 8 blocks per SM
             dim3 gp = stencil_grid(c, n_orb);
@@ -930,7 +935,7 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             dev::stencil_stage_x2_lb<8><<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, (float)(1.0 / (g.h * g.h)),
                                                             (const float2*)w_phi, (const float2*)y_phi,
                                                             (const float*)V, (const float2*)bt, (float2*)o_phi,
-                                                            (float)cdt);
+                                                            (float)cdt, (float2*)g_out);
         } else if (sizeof(T) == 4 && (g.nx & 1) == 0 && c->stencil_kz >= 2) {
             // complex64, even rows: two nodes per thread marching through KZ planes
             dim3 gp = stencil_grid(c, n_orb);
@@ -940,22 +945,23 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             const float2 *wp = (const float2*)w_phi, *yp = (const float2*)y_phi, *btp = (const float2*)bt;
             if (c->stencil_kz == 2)
                 dev::stencil_stage_x2zk<2><<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, ih2, wp, yp, (const float*)V,
-                                                               btp, (float2*)o_phi, (float)cdt);
+                                                               btp, (float2*)o_phi, (float)cdt, (float2*)g_out);
             else if (c->stencil_kz == 4)
                 dev::stencil_stage_x2zk<4><<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, ih2, wp, yp, (const float*)V,
-                                                               btp, (float2*)o_phi, (float)cdt);
+                                                               btp, (float2*)o_phi, (float)cdt, (float2*)g_out);
             else if (c->stencil_kz == 8)
                 dev::stencil_stage_x2zk<8><<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, ih2, wp, yp, (const float*)V,
-                                                               btp, (float2*)o_phi, (float)cdt);
+                                                               btp, (float2*)o_phi, (float)cdt, (float2*)g_out);
             else
                 dev::stencil_stage_x2zk<16><<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, ih2, wp, yp,
-                                                                (const float*)V, btp, (float2*)o_phi, (float)cdt);
+                                                                (const float*)V, btp, (float2*)o_phi, (float)cdt,
+                                                                (float2*)g_out);
         } else if (sizeof(T) == 4 && (g.nx & 1) == 0) {       // complex64, even rows: two nodes per thread
             dim3 gp = stencil_grid(c, n_orb);
             gp.x = (unsigned)(((g.nx / 2) * g.ny + 255) / 256);
             dev::stencil_stage_x2<<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, (float)(1.0 / (g.h * g.h)),
                                                       (const float2*)w_phi, (const float2*)y_phi, (const float*)V,
-                                                      (const float2*)bt, (float2*)o_phi, (float)cdt);
+                                                      (const float2*)bt, (float2*)o_phi, (float)cdt, (float2*)g_out);
         } else
             dev::stencil_stage<T, 1><<<stencil_grid(c, n_orb), 256, 0, ss>>>(
                 g.nx, g.ny, g.nz, n_orb, (T)(1.0 / (g.h * g.h)), (const Vc*)w_phi, (const Vc*)y_phi, V, bt,
@@ -1016,10 +1022,12 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
                                                              nullptr, (T)0, dev::Ord2Fwd<T>{});
         else if (n_orb % dev::FO == 0 && c->fwd_rw)
             dev::bnd_forward_multi_rw<T><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
-                ct, n_orb, c->nvox, (const Vc*)w_phi, order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf);
+                ct, n_orb, c->nvox, (const Vc*)w_phi, order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,
+                (const Vc*)g_in);
         else if (n_orb % dev::FO == 0)
             dev::bnd_forward_multi<T><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
-                ct, n_orb, c->nvox, (const Vc*)w_phi, order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf);
+                ct, n_orb, c->nvox, (const Vc*)w_phi, order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,
+                (const Vc*)g_in);
         else
             dev::bnd_forward<T, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
                                                        order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,
@@ -1049,10 +1057,41 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
     }
 }
 
-// One time step (4 Horner stages) in place on (psi, aux).
+// The Gamma copy (ABC_TUNE_GAMMA_COPY): complex64, radius 1, nx even, orders 0 and 1,
+// n_orb a multiple of 4 (the four-orbital forward transform), the stage-by-stage step.
+// Each stage's stencil also writes its output on Gamma, in the natural boundary layout,
+// to gam[(stage + 1) % 2]; the forward transform of the next stage reads it there
+// instead of gathering single values from the whole state (a quarter or less of each
+// 32-byte sector it fetches is Gamma).  The last stage writes gam[0], the next step's
+// input; gamma_prime fills gam[0] from psi before the first step of a call.
+bool gam_ok(const abc_ctx* c, int n_orb) {
+    return c->gam_mode && c->prec != ABC_FP64 && c->geo.R == 1 && (c->geo.nx & 1) == 0 && c->params.order <= 1 &&
+           n_orb >= 2 && n_orb % dev::FO == 0 && !c->chain && !(c->params.order == 1 && c->blocks.rows1) &&
+           c->gam[0].p && c->gam[1].p;
+}
+
+int ensure_gam(abc_ctx* c) {
+    if (!c->gam_mode || c->prec == ABC_FP64 || c->gam[0].p) return ABC_OK;
+    if (c->geo.R != 1 || (c->geo.nx & 1) || c->params.order > 1 || c->params.max_orbitals < dev::FO) return ABC_OK;
+    const size_t b = (size_t)c->geo.n_gamma * c->params.max_orbitals * cplx_bytes(c);
+    int st;
+    for (int i = 0; i < 2; ++i)
+        if ((st = c->gam[i].alloc(b))) return st;
+    return ABC_OK;
+}
+
+void gamma_prime(abc_ctx* c, const void* psi, int n_orb, cudaStream_t s) {
+    const long long n = (long long)c->geo.n_cells * 64 * n_orb;
+    dev::gamma_gather<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cell_tab<float>(c), n_orb, c->nvox,
+                                                                         (const float2*)psi, c->gam[0].as<float2>());
+    c->launches += 1;
+}
+
+// One time step (4 Horner stages) in place on (psi, aux); gam: the Gamma copy is in use
+// (gam[0] holds psi on Gamma).
 template <typename T>
 void step_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double dt, const abc_meanfield* mf,
-               cudaStream_t s) {
+               cudaStream_t s, bool gam = false) {
     const T* Vuse = (const T*)V;
     if (mf) {
         dev::density_potential<T><<<nblk(c->nvox, 256), 256, 0, s>>>(
@@ -1067,7 +1106,8 @@ void step_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, doubl
     for (int st = 0; st < 4; ++st) {
         void* op = st == 3 ? psi : c->Tp[st & 1].p;
         void* of = st == 3 ? aux : c->Tf[st & 1].p;
-        stage<T>(c, n_orb, (T)(cs[st] * dt), in_p, in_f, psi, aux, op, of, Vuse, s, st);
+        stage<T>(c, n_orb, (T)(cs[st] * dt), in_p, in_f, psi, aux, op, of, Vuse, s, st,
+                 gam ? c->gam[st & 1].p : nullptr, gam ? c->gam[(st + 1) & 1].p : nullptr);
         in_p = op;
         in_f = of;
     }
@@ -1114,10 +1154,10 @@ void boundary_chain_f(abc_ctx* c, int n_orb, float cdt, const void* w_phi, const
     void* hf = c->hat_f.p;
     if (n_orb % dev::FO == 0 && c->fwd_rw)
         dev::bnd_forward_multi_rw<float><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
-            ct, n_orb, c->nvox, (const Vc*)w_phi, (const Vc*)w_f, (Vc*)hp, (Vc*)hf);
+            ct, n_orb, c->nvox, (const Vc*)w_phi, (const Vc*)w_f, (Vc*)hp, (Vc*)hf, nullptr);
     else if (n_orb % dev::FO == 0)
         dev::bnd_forward_multi<float><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
-            ct, n_orb, c->nvox, (const Vc*)w_phi, (const Vc*)w_f, (Vc*)hp, (Vc*)hf);
+            ct, n_orb, c->nvox, (const Vc*)w_phi, (const Vc*)w_f, (Vc*)hp, (Vc*)hf, nullptr);
     else
         dev::bnd_forward<float, 0><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi, (const Vc*)w_f, (Vc*)hp,
                                                        (Vc*)hf, nullptr, 0.f, dev::Ord2Fwd<float>{});
@@ -1266,6 +1306,7 @@ extern "C" int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx
     if ((st = upload_tables(c.get()))) return st;
     if ((st = upload_matrices(c.get()))) return st;
     if ((st = ensure_workspace(c.get()))) return st;
+    if ((st = ensure_gam(c.get()))) return st;
     if ((st = c->diag.alloc(sizeof(double) * 3 * params->max_orbitals))) return st;
     if ((st = build_tiles(c.get()))) return st;
     // the packed symmetric tiles and the tensor-core image hold one symmetric m x m block
@@ -1301,7 +1342,11 @@ extern "C" int abc_step(abc_ctx* ctx, void* psi, void* aux, const void* V, int n
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (ctx->prec == ABC_FP64) step_impl<double>(ctx, psi, aux, V, n_orb, dt, nullptr, s);
-    else step_impl<float>(ctx, psi, aux, V, n_orb, dt, nullptr, s);
+    else {
+        const bool gam = gam_ok(ctx, n_orb);
+        if (gam) gamma_prime(ctx, psi, n_orb, s);
+        step_impl<float>(ctx, psi, aux, V, n_orb, dt, nullptr, s, gam);
+    }
     ctx->steps_done += 1;
     ctx->t_done += dt;
     return last_launch_status();
@@ -1329,6 +1374,7 @@ int run_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double 
     }
     const bool fused = fused_ok(c, n_orb);
     if (fused && (st = ensure_fused_workspace(c))) return st;
+    const bool gam = !fused && gam_ok(c, n_orb);
     // fused steps alternate between psi and the context's alternate buffer: step n (from
     // 1) reads psi and writes alt when n is odd, the reverse when n is even
     auto one_step = [&](cudaStream_t ss, int parity) {
@@ -1336,7 +1382,7 @@ int run_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double 
             if (parity) step_fused(c, psi, c->alt.p, aux, V, n_orb, dt, mf, ss);
             else step_fused(c, c->alt.p, psi, aux, V, n_orb, dt, mf, ss);
         } else if (c->prec == ABC_FP64) step_impl<double>(c, psi, aux, V, n_orb, dt, mf, ss);
-        else step_impl<float>(c, psi, aux, V, n_orb, dt, mf, ss);
+        else step_impl<float>(c, psi, aux, V, n_orb, dt, mf, ss, gam);
     };
     auto state_after = [&](long long n) -> const void* { return fused && (n & 1) ? c->alt.p : psi; };
     // divergence monitor (Thm 3.1 / Thm 3.2 give W as the quantity that may not grow):
@@ -1393,6 +1439,7 @@ int run_impl(abc_ctx* c, void* psi, void* aux, const void* V, int n_orb, double 
             c->key = k;
         }
     }
+    if (gam && nsteps >= 1) gamma_prime(c, psi, n_orb, s);
     for (long long n = 1; n <= nsteps; ++n) {
         const int par = (int)(n & 1) | (fused ? 0 : 1);
         if (use_graph) {
@@ -1916,6 +1963,11 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         drop_graphs(ctx);
         return ABC_OK;
     }
+    if (key == ABC_TUNE_GAMMA_COPY) {
+        ctx->gam_mode = value != 0;
+        drop_graphs(ctx);
+        return ensure_gam(ctx);
+    }
     if (key == ABC_TUNE_BACK_MULTI) {
         ctx->back_multi = value != 0;
         drop_graphs(ctx);
@@ -1956,6 +2008,7 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_STENCIL_KZ) { *value = ctx->stencil_kz; return ABC_OK; }
     if (key == ABC_TUNE_BACK_MULTI) { *value = ctx->back_multi ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_FORWARD_RW) { *value = ctx->fwd_rw ? 1 : 0; return ABC_OK; }
+    if (key == ABC_TUNE_GAMMA_COPY) { *value = ctx->gam_mode ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_GEMM_SPLIT) { *value = ctx->tc_split; return ABC_OK; }
     return fail(ABC_ERR_ARG, "unknown tuning key");
 }

@@ -88,6 +88,8 @@ struct abc_ctx {
     int stencil_kz = 1;              // complex64 stencil form (ABC_TUNE_STENCIL_KZ): 1 capped registers (default)
     bool back_multi = false;         // order-1 back transform four orbitals per cell group (tuning)
     bool fwd_rw = false;             // four-orbital forward transform with the reflection transform in registers
+    bool gam_mode = false;           // stencils write the next stage's w on Gamma for the forward transform (tuning)
+    abc::DevBuf gam[2];              // that Gamma copy, [n_gamma][max_orbitals], one per stage parity
     int tc_sms_all = 0;              // SMs of the device
     abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
     abc::dev::SymGather sym_gather{};   // partial-sum view for the back transform

@@ -284,12 +284,15 @@ __global__ void __launch_bounds__(128) bnd_forward(CellTab<T> ct, int n_orb, lon
 // coefficients are read once per FO orbitals and each thread has FO independent value
 // loads in flight.  Same arithmetic, order and outputs as bnd_forward<T, 0>.
 constexpr int FO = 4;
+// g_phi (optional): w on Gamma in the natural boundary layout [n_gamma][n_orb] (written
+// by the previous stage's stencil); read instead of gathering from w_phi.
 template <typename T>
 __global__ void __launch_bounds__(128) bnd_forward_multi(CellTab<T> ct, int n_orb, long long nvox,
                                                          const typename C2<T>::t* __restrict__ w_phi,
                                                          const typename C2<T>::t* __restrict__ w_f,
                                                          typename C2<T>::t* __restrict__ hat_phi,
-                                                         typename C2<T>::t* __restrict__ hat_f) {
+                                                         typename C2<T>::t* __restrict__ hat_f,
+                                                         const typename C2<T>::t* __restrict__ g_phi) {
     typedef typename C2<T>::t V;
     __shared__ V sp[2][FO][8][8], sf[2][FO][8][8];     // [group][orbital][slot][parity]
     const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
@@ -306,7 +309,8 @@ __global__ void __launch_bounds__(128) bnd_forward_multi(CellTab<T> ct, int n_or
     V xp[FO], xf[FO];
 #pragma unroll
     for (int o = 0; o < FO; ++o) {
-        xp[o] = gi >= 0 ? w_phi[(long long)(j0 + o) * nvox + node] : mk<T>(0, 0);
+        xp[o] = gi < 0 ? mk<T>(0, 0)
+                       : g_phi ? g_phi[(long long)gi * n_orb + j0 + o] : w_phi[(long long)(j0 + o) * nvox + node];
         xf[o] = (gi >= 0 && w_f) ? w_f[(long long)gi * n_orb + j0 + o] : mk<T>(0, 0);
     }
     T cf[8];
@@ -333,6 +337,21 @@ __global__ void __launch_bounds__(128) bnd_forward_multi(CellTab<T> ct, int n_or
     }
 }
 
+// w on Gamma in the natural boundary layout, g[gamma index][orbital], gathered from the
+// full state: one thread per (cell slot, orbital), orbitals fastest so the writes are
+// contiguous.  Fills the forward transform's Gamma copy before the first stage of a run.
+template <typename T>
+__global__ void gamma_gather(CellTab<T> ct, int n_orb, long long nvox, const typename C2<T>::t* __restrict__ w_phi,
+                             typename C2<T>::t* __restrict__ g) {
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)ct.n_cells * 64 * n_orb) return;
+    const int j = (int)(id % n_orb);
+    const long long cs = id / n_orb;                     // cell * 64 + slot
+    const int gi = ct.gi[cs];
+    if (gi < 0) return;
+    g[(long long)gi * n_orb + j] = w_phi[(long long)j * nvox + ct.node[cs]];
+}
+
 // bnd_forward_multi with the reflection transform done in registers instead of across
 // lanes: in phase A thread (array, orbital o, slot s) of a 64-thread group loads the 8
 // reflections of its slot (psi at the nodes, or f) and runs the 8-point Walsh-Hadamard
@@ -345,7 +364,8 @@ __global__ void __launch_bounds__(128) bnd_forward_multi_rw(CellTab<T> ct, int n
                                                             const typename C2<T>::t* __restrict__ w_phi,
                                                             const typename C2<T>::t* __restrict__ w_f,
                                                             typename C2<T>::t* __restrict__ hat_phi,
-                                                            typename C2<T>::t* __restrict__ hat_f) {
+                                                            typename C2<T>::t* __restrict__ hat_f,
+                                                            const typename C2<T>::t* __restrict__ g_phi) {
     typedef typename C2<T>::t V;
     __shared__ __align__(16) V sw[2][2][FO][8][8];        // [group][array][orbital][parity][slot]
     const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
@@ -368,7 +388,8 @@ __global__ void __launch_bounds__(128) bnd_forward_multi_rw(CellTab<T> ct, int n
         for (int g = 0; g < 8; ++g) {
             x[g] = mk<T>(0, 0);
             if (gi[g] >= 0) {
-                if (arr == 0) x[g] = w_phi[(long long)(j0 + o) * nvox + nd[g]];
+                if (arr == 0)
+                    x[g] = g_phi ? g_phi[(long long)gi[g] * n_orb + j0 + o] : w_phi[(long long)(j0 + o) * nvox + nd[g]];
                 else if (w_f) x[g] = w_f[(long long)gi[g] * n_orb + j0 + o];
             }
         }
@@ -1048,10 +1069,14 @@ __global__ void stencil_stage(int nx, int ny, int nz, int n_orb, T inv_h2, const
 // thread, with 16-byte loads of the pair and of its y and z neighbours (nx even, so a
 // pair never crosses a row and every pair starts on a 16-byte boundary): 7 loads of w
 // for two nodes instead of 14.  Same neighbour order and formula as stencil_stage.
+// gout (optional): the outputs on Gamma also go to gout[gamma_index * n_orb + orb], the
+// natural boundary layout the next stage's forward transform reads instead of gathering
+// them from the whole state.
 __device__ __forceinline__ void stencil_pair_x2(int nx, int ny, int nz, int n_orb, float inv_h2,
                                                 const float2* __restrict__ w, const float2* y,
                                                 const float* __restrict__ V, const float2* __restrict__ bterm,
-                                                float2* out, float cdt, int tp2, int k, int orb) {
+                                                float2* out, float cdt, int tp2, int k, int orb,
+                                                float2* __restrict__ gout) {
     const long long nxy = (long long)nx * ny, nvox = nxy * nz;
     const int jy = tp2 / (nx >> 1), i = 2 * (tp2 - jy * (nx >> 1));
     const long long n = (long long)k * nxy + (long long)jy * nx + i;
@@ -1094,23 +1119,30 @@ __device__ __forceinline__ void stencil_pair_x2(int nx, int ny, int nz, int n_or
         hr[1] = dg * c.z - 0.5f * inv_h2 * sr;
         hi[1] = dg * c.w - 0.5f * inv_h2 * si;
     }
+    long long gq[2] = {-1, -1};
 #pragma unroll
     for (int q = 0; q < 2; ++q)
         if (on_gamma<1>(i + q, jy, k, nx, ny, nz)) {
-            const float2 b = bterm[(long long)gamma_index<1>(i + q, jy, k, nx, ny, nz) * n_orb + orb];
+            gq[q] = (long long)gamma_index<1>(i + q, jy, k, nx, ny, nz) * n_orb + orb;
+            const float2 b = bterm[gq[q]];
             hr[q] += b.x;
             hi[q] += b.y;
         }
-    *reinterpret_cast<float4*>(out + idx) =
-        make_float4(yv.x + cdt * hi[0], yv.y - cdt * hr[0], yv.z + cdt * hi[1], yv.w - cdt * hr[1]);
+    const float4 o = make_float4(yv.x + cdt * hi[0], yv.y - cdt * hr[0], yv.z + cdt * hi[1], yv.w - cdt * hr[1]);
+    *reinterpret_cast<float4*>(out + idx) = o;
+    if (gout) {
+        if (gq[0] >= 0) gout[gq[0]] = make_float2(o.x, o.y);
+        if (gq[1] >= 0) gout[gq[1]] = make_float2(o.z, o.w);
+    }
 }
 
 static __global__ void stencil_stage_x2(int nx, int ny, int nz, int n_orb, float inv_h2, const float2* __restrict__ w,
                                         const float2* y, const float* __restrict__ V,
-                                        const float2* __restrict__ bterm, float2* out, float cdt) {
+                                        const float2* __restrict__ bterm, float2* out, float cdt,
+                                        float2* __restrict__ gout) {
     const int tp2 = blockIdx.x * blockDim.x + threadIdx.x;         // pair in the z-plane
     if (tp2 >= (nx >> 1) * ny) return;
-    stencil_pair_x2(nx, ny, nz, n_orb, inv_h2, w, y, V, bterm, out, cdt, tp2, blockIdx.y, blockIdx.z);
+    stencil_pair_x2(nx, ny, nz, n_orb, inv_h2, w, y, V, bterm, out, cdt, tp2, blockIdx.y, blockIdx.z, gout);
 }
 
 // stencil_stage_x2 compiled for MINB resident blocks per SM (registers capped so that
@@ -1121,10 +1153,10 @@ __global__ void __launch_bounds__(256, MINB) stencil_stage_x2_lb(int nx, int ny,
                                                                  const float2* __restrict__ w, const float2* y,
                                                                  const float* __restrict__ V,
                                                                  const float2* __restrict__ bterm, float2* out,
-                                                                 float cdt) {
+                                                                 float cdt, float2* __restrict__ gout) {
     const int tp2 = blockIdx.x * blockDim.x + threadIdx.x;
     if (tp2 >= (nx >> 1) * ny) return;
-    stencil_pair_x2(nx, ny, nz, n_orb, inv_h2, w, y, V, bterm, out, cdt, tp2, blockIdx.y, blockIdx.z);
+    stencil_pair_x2(nx, ny, nz, n_orb, inv_h2, w, y, V, bterm, out, cdt, tp2, blockIdx.y, blockIdx.z, gout);
 }
 
 // stencil_stage_x2 with each thread marching through KZ consecutive planes of its node
@@ -1136,7 +1168,8 @@ template <int KZ>
 __global__ void __launch_bounds__(256) stencil_stage_x2zk(int nx, int ny, int nz, int n_orb, float inv_h2,
                                                           const float2* __restrict__ w, const float2* y,
                                                           const float* __restrict__ V,
-                                                          const float2* __restrict__ bterm, float2* out, float cdt) {
+                                                          const float2* __restrict__ bterm, float2* out, float cdt,
+                                                          float2* __restrict__ gout) {
     const long long nxy = (long long)nx * ny, nvox = nxy * nz;
     const int tp2 = blockIdx.x * blockDim.x + threadIdx.x;
     if (tp2 >= (nx >> 1) * ny) return;
@@ -1200,15 +1233,21 @@ __global__ void __launch_bounds__(256) stencil_stage_x2zk(int nx, int ny, int nz
             hr[1] = dg * c.z - 0.5f * inv_h2 * sr;
             hi[1] = dg * c.w - 0.5f * inv_h2 * si;
         }
+        long long gq[2] = {-1, -1};
 #pragma unroll
         for (int q = 0; q < 2; ++q)
             if (on_gamma<1>(i + q, jy, k, nx, ny, nz)) {
-                const float2 b = bterm[(long long)gamma_index<1>(i + q, jy, k, nx, ny, nz) * n_orb + orb];
+                gq[q] = (long long)gamma_index<1>(i + q, jy, k, nx, ny, nz) * n_orb + orb;
+                const float2 b = bterm[gq[q]];
                 hr[q] += b.x;
                 hi[q] += b.y;
             }
-        *reinterpret_cast<float4*>(oo + n) =
-            make_float4(yv.x + cdt * hi[0], yv.y - cdt * hr[0], yv.z + cdt * hi[1], yv.w - cdt * hr[1]);
+        const float4 o = make_float4(yv.x + cdt * hi[0], yv.y - cdt * hr[0], yv.z + cdt * hi[1], yv.w - cdt * hr[1]);
+        *reinterpret_cast<float4*>(oo + n) = o;
+        if (gout) {
+            if (gq[0] >= 0) gout[gq[0]] = make_float2(o.x, o.y);
+            if (gq[1] >= 0) gout[gq[1]] = make_float2(o.z, o.w);
+        }
         zm = c;
         c = zp;
         xm = xmn; xp = xpn; ym = ymn; yp = ypn; yv = yvn; vv = vvn;
@@ -1224,7 +1263,7 @@ static __global__ void __launch_bounds__(256) stencil_stage_x2_gs(int nx, int ny
                                                                   const float2* __restrict__ w, const float2* y,
                                                                   const float* __restrict__ V,
                                                                   const float2* __restrict__ bterm, float2* out,
-                                                                  float cdt) {
+                                                                  float cdt, float2* __restrict__ gout) {
     const int pp = (nx >> 1) * ny;                                  // pairs per plane
     const long long total = (long long)pp * nz * n_orb;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < total;
@@ -1232,7 +1271,7 @@ static __global__ void __launch_bounds__(256) stencil_stage_x2_gs(int nx, int ny
         const long long pl = it / pp;
         const int tp2 = (int)(it - pl * pp);
         const int orb = (int)(pl / nz), k = (int)(pl - (long long)orb * nz);
-        stencil_pair_x2(nx, ny, nz, n_orb, inv_h2, w, y, V, bterm, out, cdt, tp2, k, orb);
+        stencil_pair_x2(nx, ny, nz, n_orb, inv_h2, w, y, V, bterm, out, cdt, tp2, k, orb, gout);
     }
 }
 

@@ -11,9 +11,10 @@ precision and the device, so the library exposes its choices as tuning knobs
   (``TUNE_FUSED``) or stage by stage, and for the latter where the stencil runs
   beside the boundary chain (``TUNE_STENCIL``) and how many planes each of its threads
   marches through (``TUNE_STENCIL_KZ``);
-* the order-1 back transform one or four orbitals per cell group (``TUNE_BACK_MULTI``)
-  and the four-orbital forward transform's reflection transform across lanes or in
-  registers (``TUNE_FORWARD_RW``);
+* the order-1 back transform one or four orbitals per cell group (``TUNE_BACK_MULTI``),
+  the four-orbital forward transform's reflection transform across lanes or in
+  registers (``TUNE_FORWARD_RW``) and whether it reads w on Gamma from the copy the
+  previous stage's stencil wrote (``TUNE_GAMMA_COPY``);
 * for one complex64 orbital, the early start of the tiled contraction behind the
   forward transform (``TUNE_PDL``).
 
@@ -72,7 +73,10 @@ def knob_groups(ctx: abc.Context, n_orb: int):
     if ctx.order == 1 and ctx.fit1 == abc.FIT1_LIMIT and n_orb >= 4 and n_orb % 4 == 0:
         groups.append([{abc.TUNE_BACK_MULTI: 0}, {abc.TUNE_BACK_MULTI: 1}])
     if n_orb >= 4 and n_orb % 4 == 0 and ctx.order < 2:
-        groups.append([{abc.TUNE_FORWARD_RW: 0}, {abc.TUNE_FORWARD_RW: 1}])
+        if ctx.precision != abc.FP64 and ctx.radius == 1 and ctx.shape[0] % 2 == 0:
+            groups.append([{abc.TUNE_FORWARD_RW: rw, abc.TUNE_GAMMA_COPY: gc} for gc in (0, 1) for rw in (0, 1)])
+        else:
+            groups.append([{abc.TUNE_FORWARD_RW: 0}, {abc.TUNE_FORWARD_RW: 1}])
     if n_orb == 1 and ctx.precision != abc.FP64 and ctx.get_tuning(abc.TUNE_TILE_COUNT) > 0:
         groups.append([{abc.TUNE_PDL: 1}, {abc.TUNE_PDL: 0}])
     return groups
@@ -148,5 +152,6 @@ def describe(setting: dict) -> dict:
              abc.TUNE_STENCIL_BPS: "stencil_blocks_per_sm(0=one thread per pair)",
              abc.TUNE_STENCIL_KZ: "stencil_form(0=pair per thread, 1=capped registers, k>1=k planes)",
              abc.TUNE_BACK_MULTI: "back_transform_4_orbitals", abc.TUNE_FORWARD_RW: "forward_transform_in_registers",
+             abc.TUNE_GAMMA_COPY: "forward_reads_gamma_copy",
              abc.TUNE_PDL: "pdl"}
     return {names.get(int(k), str(k)): v for k, v in setting.items()}

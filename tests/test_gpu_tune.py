@@ -134,3 +134,39 @@ def test_kernel_forms_match_default(env, knob, value, prec):
         ctx.close()
     assert rel(outs[1][0], outs[0][0]) < 1e-6
     assert rel(outs[1][1], outs[0][1]) < 1e-6
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("form", [(0, 1, 0), (1, 1, 0), (0, 0, 0), (0, 4, 0), (1, 0, 2)])
+@pytest.mark.parametrize("prec", ["fp16x3", "c64"])
+def test_gamma_copy_is_bit_identical(env, order, form, prec):
+    """The forward transform reading w on Gamma from the copy the previous stage's stencil
+    wrote (two alternating copies, the first filled from psi at the start of each call)
+    sees exactly the values it would gather from the state: abc_run and abc_step give
+    bit-identical results with the copy on and off, for every stencil form and placement
+    (form = stencil placement, planes per thread, blocks per SM of the grid-stride form;
+    placement 1 runs each stage's stencil beside its forward transform)."""
+    torch, abc = env
+    dims, h, dt, b = (18, 14, 13), 0.45, 0.005, 8
+    psi0 = inputs.orbital_set(dims, h, np.random.default_rng(16), b)
+    V0 = inputs.smooth_random(dims, h, np.random.default_rng(17))
+    outs = []
+    for gc in (0, 1):
+        ctx = abc.Context(dims, h, order, 1.0, precision=prec, max_orbitals=b)
+        ctx.set_tuning(abc.TUNE_GAMMA_COPY, gc)
+        ctx.set_tuning(abc.TUNE_STENCIL, form[0])
+        ctx.set_tuning(abc.TUNE_STENCIL_KZ, form[1])
+        ctx.set_tuning(abc.TUNE_STENCIL_BPS, form[2])
+        assert ctx.get_tuning(abc.TUNE_GAMMA_COPY) == gc
+        psi = torch.from_numpy(psi0).to("cuda", torch.complex64).contiguous()
+        aux = ctx.new_aux(b)
+        V = torch.from_numpy(V0).to("cuda", torch.float32).contiguous()
+        ctx.run(psi, aux, V, dt, 7, meanfield=(-1.0, 0.8, 1.0 / 6.0))
+        ctx.step(psi, aux, V, dt)
+        ctx.run(psi, aux, V, dt, 3)
+        torch.cuda.synchronize()
+        outs.append((psi.cpu(), None if aux is None else aux.cpu()))
+        ctx.close()
+    assert torch.equal(outs[0][0], outs[1][0])
+    if order == 1:
+        assert torch.equal(outs[0][1], outs[1][1])
