@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--reuse-tuning", action="store_true",
                     help="take the autotuner's cached choice when there is one (profiling runs)")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default knobs (profiling runs)")
+    ap.add_argument("--knob", action="append", default=[], metavar="NAME=VALUE",
+                    help="set a tuning knob (abc.TUNE_<NAME>) after tuning, e.g. BACK_MULTI=1 (profiling runs)")
     ap.add_argument("--workload", type=int, default=WORKLOAD_NUMBER,
                     help="5 (default) or 2 give a full line; 1, 3, 4, 6-9 a line of their own")
     return ap.parse_args()
@@ -283,7 +285,8 @@ def cublas_tf32_tflops(dev):
 
 
 # ----------------------------------------------------------------------
-# native arm: a full line for workload 5 (default) or 2
+# native arm: a full line for the 96^3 x 128-orbital mean-field workload (default) or the
+# 64^3 single-orbital one
 # ----------------------------------------------------------------------
 def measure(args, w, rank, world, dev, extra_lines=True):
     import torch
@@ -310,6 +313,8 @@ def measure(args, w, rank, world, dev, extra_lines=True):
     else:
         tuned = tune.tune(ctx, psi, aux, Vt, w.dt, meanfield=mf, use_cache=False)
         tune.tune(ctx, psi, aux, Vt, w.dt, meanfield=mf, use_cache=True, fresh=tuned)
+    if args.knob:
+        tuned = dict(tuned, knobs=apply_knobs(ctx, args.knob))
     # warm-up (also captures the CUDA graph)
     ctx.run(psi, aux, Vt, w.dt, max(args.warmup, 1), meanfield=mf)
     torch.cuda.synchronize()
@@ -342,7 +347,8 @@ def measure(args, w, rank, world, dev, extra_lines=True):
     tot_units, max_sec = aggregate(units, sec)
     out = {"value": tot_units / max_sec, "ms_per_step": max_sec / steps * 1e3, "steps": steps,
            "clocks": clk.summary(), "gpu_launches": gpu_launches,
-           "tuning": {"setting": tune.describe(tuned.get("setting", {})), "sweep_ms_per_step": tuned.get("sweep")}}
+           "tuning": {"setting": tune.describe(tuned.get("setting", {})), "sweep_ms_per_step": tuned.get("sweep"),
+                      "knobs": tuned.get("knobs")}}
 
     # dominant kernels: live CUDA-event timing of every launch over eager steps on the
     # launching stream (no graph), the same flush policy as the timed steps
@@ -514,6 +520,17 @@ def inputs_for(w):
     return inputs.make_inputs(w)
 
 
+def apply_knobs(ctx, knobs):
+    """Set the --knob NAME=VALUE tuning knobs on a context; returns them as a dict."""
+    from paper_1908_02456_gb300 import abc
+    out = {}
+    for kv in knobs:
+        name, value = kv.split("=")
+        ctx.set_tuning(getattr(abc, "TUNE_" + name.strip().upper()), int(value))
+        out[name.strip().upper()] = int(value)
+    return out
+
+
 def other_workload(args, w):
     """One line for a workload without a full line: K time steps (mean-field workloads:
     the potential is rebuilt from the density every step) or, for the adjoint workload,
@@ -530,6 +547,7 @@ def other_workload(args, w):
     psi = torch.from_numpy(psi0).to(dev, ctx.complex_dtype)
     aux = ctx.new_aux(w.n_orb) if w.order == 1 else ctx.init_aux(psi) if w.order == 2 else None
     Vt = torch.from_numpy(V).to(dev, ctx.real_dtype)
+    knobs = apply_knobs(ctx, args.knob)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -578,7 +596,7 @@ def other_workload(args, w):
                                            "precision": w.precision, "what": what},
             "contraction": {"avg_launch_us": round(ms_c / n_c * 1e3, 2), "bytes_per_launch": bytes_c,
                             "achieved_gbs": round(bytes_c / (ms_c / n_c * 1e-3) / 1e9, 1)},
-            "clocks": clk.summary(), "gpu_launches": launches}
+            "clocks": clk.summary(), "gpu_launches": launches, "knobs": knobs}
     print(json.dumps(line))
     ctx.close()
 
