@@ -426,6 +426,12 @@ def measure(args, w, rank, world, dev, extra_lines=True):
     psi_h = torch.from_numpy(psi0.astype(np.complex64)).pin_memory()
     aux_h = torch.zeros((ctx.n_gamma, w.n_orb), dtype=torch.complex64).pin_memory()
     V_h = torch.from_numpy(V.astype(np.float32)).pin_memory()
+    # warm-up call (untimed): the context's device copies of the state are allocated and
+    # the step graph for them captured on the first call, as for any caller that steps
+    # repeatedly; then the inputs are restored
+    ctx.run_host(psi_h, aux_h, V_h, w.dt, max(args.warmup, 1), meanfield=mf)
+    psi_h.copy_(torch.from_numpy(psi0.astype(np.complex64)))
+    aux_h.zero_()
     if flush is not None:
         flush.fill_(1.0)
     torch.cuda.synchronize()
