@@ -149,11 +149,15 @@ typedef struct {
 typedef struct abc_ctx abc_ctx;
 
 /* Builds the context: index sets, K(s) by eq:eval with the free lattice Green's
- * function (App. A, App. D), the order-0 / order-1 coefficients (Thm 3.1 / 3.2),
- * all in FP64 on the host (untimed setup, OpenMP), then converts them to the
- * device format of `precision` and uploads them to the current CUDA device.
- * *out receives the context (free with abc_destroy).  Errors: ABC_ERR_ARG for bad
- * sizes/order/precision, ABC_ERR_SINGULAR, ABC_ERR_ALLOC, ABC_ERR_CUDA. */
+ * function (App. A, App. D), the order-0 / order-1 coefficients (Thm 3.1 / 3.2) or
+ * the order-2 fit (Sec. 3.3: four interpolation conditions per irreducible class; at
+ * radius 3 the system is nearly singular and its basic solution by column-pivoted QR
+ * is taken, pivots below 1e-13 of the largest column norm dropped), all in FP64 on
+ * the host (untimed setup, OpenMP), then converts them to the device format of
+ * `precision` and uploads them to the current CUDA device.  *out receives the context
+ * (free with abc_destroy).  Errors: ABC_ERR_ARG for bad sizes/order/precision,
+ * ABC_ERR_UNSUPPORTED (order 2 at radius 3 in a reduced precision; ABC_C64_SPLIT_BF16),
+ * ABC_ERR_SINGULAR, ABC_ERR_ALLOC, ABC_ERR_CUDA. */
 int abc_setup(const abc_grid* grid, const abc_params* params, abc_ctx** out);
 
 /* n_gamma = |Gamma| = nx*ny*nz - (nx-2R)(ny-2R)(nz-2R) (eq:25, radius R). */

@@ -33,6 +33,14 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   puts the hidden root at s = -min(s_j), a decaying mode.  By the determinant lemma
   det(D0(l) - w r) = det D0(l) - r adj(D0(l)) w with D0(l) = l^2 I - l B1 - B0 of X0 and
   r = l x_B1 + x_B0, so the condition is one linear equation in w.
+* Order 2 with a wider stencil in 3D (radius R >= 2, Sec. 4.2's seven-point scheme per
+  axis): the 4 n x 4 n system has many near-null directions with no clear gap (131
+  singular values below 1e-11 sigma_1 at 7 x 8 x 7), and a plain LU solution puts roots
+  of det(s^2 I - s B1 - B0) deep in the right half-plane (real parts ~1e3 at 11^3,
+  h = 0.1: the fitted dynamics diverge).  Reading: the basic solution of a
+  column-pivoted QR at numerical rank, pivots below 1e-13 |R_11| dropped (the free
+  unknowns set to zero; Golub and Van Loan, Sec. 5.5).  It interpolates K to ~1e-9 and
+  keeps every root at Re <= ~1e-7 on the boxes checked.  Radius 1 keeps the plain solve.
 """
 from __future__ import annotations
 
@@ -108,7 +116,10 @@ def order2(box: Box, points=(1.0, 2.0, 3.0, 10.0), Ks=None) -> dict:
         return _order2_1d(pts, Ks)
     n = Ks[0].shape[0]
     M, Y = _interp2_system(pts, Ks)
-    X = np.linalg.solve(M.T, Y.T).T
+    if box.R >= 2:
+        X = _basic_solution(M.T, Y.T, 1e-13).T
+    else:
+        X = np.linalg.solve(M.T, Y.T).T
     B1, B0, A1, A0 = (X[:, k * n:(k + 1) * n] for k in range(4))
     return {"order": 2, "points": tuple(pts), "B1": B1, "B0": B0, "A1": A1, "A0": A0, "Ks": Ks}
 
@@ -127,6 +138,18 @@ def _interp2_system(pts, Ks):
         M[3 * n:4 * n, cols] = I
         Y[:, cols] = sj * sj * Kj
     return M, Y
+
+
+def _basic_solution(A, B, rtol):
+    """Z with A Z = B by column-pivoted QR, at the rank of the pivots above rtol |R_11|,
+    the remaining unknowns zero."""
+    import scipy.linalg as sla
+    Q, R, P = sla.qr(A, pivoting=True)
+    d = np.abs(np.diag(R))
+    r = int(np.sum(d > rtol * d[0]))
+    Z = np.zeros((A.shape[1], B.shape[1]), dtype=np.complex128)
+    Z[P[:r]] = sla.solve_triangular(R[:r, :r], (Q.conj().T @ B)[:r])
+    return Z
 
 
 def order2_end(pts, Ks) -> np.ndarray:

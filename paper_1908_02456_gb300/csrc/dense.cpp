@@ -228,4 +228,104 @@ void zgetrs(int n, int nrhs, const cd* A, int lda, const int* ipiv, cd* B, int l
     }
 }
 
+// Householder QR with column pivoting of a square A (column-major n x n, overwritten)
+// and the basic solution of A Z = B (B: n x nrhs, overwritten by Z).  Each step takes
+// the remaining column of largest norm (norms downdated after each reflection and
+// recomputed when cancellation has eaten half the digits), reflects it onto e_k with
+// H = I - tau v v^H (v_0 = 1, beta = R_kk real: the convention of LAPACK's zlarfg) and
+// applies H^H to the trailing columns.  The factorisation stops at the first pivot with
+// |R_kk| <= abs_tol (every remaining column is that small): the numerical rank r.  Then
+// Z = P [R_11^{-1} (Q^H B)_1 ; 0]: the free unknowns of a rank-deficient system are set
+// to zero (Golub and Van Loan, Sec. 5.5, the basic solution).  Returns 0; *rank = r.
+int zqrp_basic(int n, int nrhs, cd* A, int lda, cd* B, int ldb, double abs_tol, int* rank) {
+    std::vector<int> perm(n);
+    std::vector<double> cn(n), cn0(n);
+    std::vector<cd> tau(n, cd(0.0, 0.0));
+    const double tol3z = std::sqrt(2.220446049250313e-16);
+    for (int j = 0; j < n; ++j) {
+        perm[j] = j;
+        double s2 = 0;
+        const cd* c = A + (size_t)j * lda;
+        for (int i = 0; i < n; ++i) s2 += std::norm(c[i]);
+        cn[j] = cn0[j] = std::sqrt(s2);
+    }
+    int r = n;
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int j = k + 1; j < n; ++j)
+            if (cn[j] > cn[p]) p = j;
+        if (p != k) {
+            std::swap_ranges(A + (size_t)k * lda, A + (size_t)k * lda + n, A + (size_t)p * lda);
+            std::swap(cn[k], cn[p]);
+            std::swap(cn0[k], cn0[p]);
+            std::swap(perm[k], perm[p]);
+        }
+        cd* col = A + (size_t)k * lda;
+        const cd alpha = col[k];
+        double xn = 0;
+        for (int i = k + 1; i < n; ++i) xn += std::norm(col[i]);
+        xn = std::sqrt(xn);
+        double beta;
+        cd t(0.0, 0.0);
+        if (xn == 0.0 && alpha.imag() == 0.0) {
+            beta = alpha.real();
+        } else {
+            beta = -std::copysign(std::sqrt(std::norm(alpha) + xn * xn), alpha.real());
+            t = cd((beta - alpha.real()) / beta, -alpha.imag() / beta);
+            const cd sc = 1.0 / (alpha - beta);
+            for (int i = k + 1; i < n; ++i) col[i] *= sc;
+        }
+        col[k] = beta;
+        tau[k] = t;
+        if (std::fabs(beta) <= abs_tol) {
+            r = k;
+            break;
+        }
+        const cd ct = std::conj(t);
+#pragma omp parallel for schedule(static) if (n - k > 96)
+        for (int j = k + 1; j < n; ++j) {
+            cd* cj = A + (size_t)j * lda;
+            cd w = cj[k];
+            for (int i = k + 1; i < n; ++i) w += std::conj(col[i]) * cj[i];
+            w *= ct;
+            cj[k] -= w;
+            for (int i = k + 1; i < n; ++i) cj[i] -= col[i] * w;
+            if (cn[j] > 0.0) {
+                const double q = std::abs(cj[k]) / cn[j];
+                const double temp = std::max(0.0, (1.0 + q) * (1.0 - q));
+                const double ratio = cn[j] / cn0[j];
+                if (temp * ratio * ratio <= tol3z) {
+                    double s2 = 0;
+                    for (int i = k + 1; i < n; ++i) s2 += std::norm(cj[i]);
+                    cn[j] = cn0[j] = std::sqrt(s2);
+                } else {
+                    cn[j] *= std::sqrt(temp);
+                }
+            }
+        }
+    }
+    *rank = r;
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < nrhs; ++c) {
+        cd* b = B + (size_t)c * ldb;
+        for (int k = 0; k < r; ++k) {                  // b <- H_k^H b
+            const cd* v = A + (size_t)k * lda;
+            cd w = b[k];
+            for (int i = k + 1; i < n; ++i) w += std::conj(v[i]) * b[i];
+            w *= std::conj(tau[k]);
+            b[k] -= w;
+            for (int i = k + 1; i < n; ++i) b[i] -= v[i] * w;
+        }
+        std::vector<cd> y(r);
+        for (int i = r - 1; i >= 0; --i) {             // R_11 y = (Q^H b)_1
+            cd acc = b[i];
+            for (int j = i + 1; j < r; ++j) acc -= A[(size_t)j * lda + i] * y[j];
+            y[i] = acc / A[(size_t)i * lda + i];
+        }
+        for (int i = 0; i < n; ++i) b[i] = cd(0.0, 0.0);
+        for (int i = 0; i < r; ++i) b[perm[i]] = y[i];
+    }
+    return 0;
+}
+
 }  // namespace abc

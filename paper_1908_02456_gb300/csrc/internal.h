@@ -151,6 +151,10 @@ void free_green_table(const Geometry& g, double s, int dx, int dy, int dz, std::
 // right-hand sides.  Return 0, or k+1 if U(k,k) == 0.
 int zgetrf(int n, cd* A, int lda, int* ipiv);
 void zgetrs(int n, int nrhs, const cd* A, int lda, const int* ipiv, cd* B, int ldb);
+// Column-pivoted Householder QR of a square A (column-major, overwritten) and the basic
+// solution of A Z = B at numerical rank r = the number of pivots above abs_tol (the free
+// unknowns set to zero); Z overwrites B.  Returns 0.
+int zqrp_basic(int n, int nrhs, cd* A, int lda, cd* B, int ldb, double abs_tol, int* rank);
 // C -= A * B (column-major, m x k times k x n)
 void zgemm_sub(int m, int n, int k, const cd* A, int lda, const cd* B, int ldb, cd* C, int ldc);
 

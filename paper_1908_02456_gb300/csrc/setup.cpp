@@ -648,13 +648,14 @@ int compute_blocks2(const Geometry& g, const double s[4], Blocks& out, std::stri
     for (int j = 0; j < 4; ++j) out.s2[j] = s[j];
     const size_t nc = g.cls.size();
     for (int q = 0; q < 4; ++q) out.mat2[q].resize(nc);
-    for (size_t k = 0; k < nc; ++k) {
+    // M (4m x 4m) row-major: block column j = (s_j K_j; K_j; s_j I; I); Y (m x 4m)
+    // row-major: block j = s_j^2 K_j.  X M = Y  <=>  M^T X^T = Y^T, and a row-major
+    // array read column-major is the transpose, so the column-major solvers are applied
+    // to M's row-major buffer with Y's row-major buffer as right-hand sides.
+    auto assemble = [&](size_t k, std::vector<cd>& M, std::vector<cd>& Y) {
         const int m = g.cls[k].m, n4 = 4 * m;
-        // M (4m x 4m) row-major: block column j = (s_j K_j; K_j; s_j I; I); Y (m x 4m)
-        // row-major: block j = s_j^2 K_j.  X M = Y  <=>  M^T X^T = Y^T, and a row-major
-        // array read column-major is the transpose, so the column-major solver is
-        // applied to M's row-major buffer with Y's row-major buffer as right-hand sides.
-        std::vector<cd> M((size_t)n4 * n4, cd(0.0, 0.0)), Y((size_t)m * n4, cd(0.0, 0.0));
+        M.assign((size_t)n4 * n4, cd(0.0, 0.0));
+        Y.assign((size_t)m * n4, cd(0.0, 0.0));
         for (int j = 0; j < 4; ++j) {
             const std::vector<cd>& K = Kj[j].mat[k];
             for (int r = 0; r < m; ++r)
@@ -669,15 +670,46 @@ int compute_blocks2(const Geometry& g, const double s[4], Blocks& out, std::stri
                 M[(size_t)(3 * m + r) * n4 + j * m + r] = 1.0;
             }
         }
-        std::vector<int> piv(n4);
-        const int info = zgetrf(n4, M.data(), n4, piv.data());
-        if (info) {
-            char buf[128];
-            std::snprintf(buf, sizeof(buf), "order-2 interpolation system of class %zu singular at pivot %d", k, info);
-            err = buf;
-            return ABC_ERR_SINGULAR;
+    };
+    // Radius 3: the system is nearly singular (many near-null directions, no clear gap)
+    // and an LU solution puts roots of det(s^2 I - s B1 - B0) deep in the right
+    // half-plane (real parts ~1e3 at 11^3, h = 0.1), so the fit is the basic solution of
+    // a column-pivoted QR at numerical rank, pivots below 1e-13 times the largest column
+    // norm of all classes' systems dropped.  Radius 1: the LU solution (well conditioned).
+    double abs_tol = 0.0;
+    std::vector<cd> M, Y;
+    if (g.R > 1) {
+        double big = 0.0;
+        for (size_t k = 0; k < nc; ++k) {
+            assemble(k, M, Y);
+            const int n4 = 4 * g.cls[k].m;
+            for (int j = 0; j < n4; ++j) {                       // column j of M^T = row j of M
+                double s2 = 0.0;
+                for (int i = 0; i < n4; ++i) s2 += std::norm(M[(size_t)j * n4 + i]);
+                big = std::max(big, std::sqrt(s2));
+            }
         }
-        zgetrs(n4, m, M.data(), n4, piv.data(), Y.data(), n4);     // Y now holds X row-major (m x 4m)
+        abs_tol = 1e-13 * big;
+    }
+    for (size_t k = 0; k < nc; ++k) {
+        const int m = g.cls[k].m, n4 = 4 * m;
+        assemble(k, M, Y);
+        if (g.R > 1) {
+            int rank = 0;
+            zqrp_basic(n4, m, M.data(), n4, Y.data(), n4, abs_tol, &rank);
+        } else {
+            std::vector<int> piv(n4);
+            const int info = zgetrf(n4, M.data(), n4, piv.data());
+            if (info) {
+                char buf[128];
+                std::snprintf(buf, sizeof(buf), "order-2 interpolation system of class %zu singular at pivot %d", k,
+                              info);
+                err = buf;
+                return ABC_ERR_SINGULAR;
+            }
+            zgetrs(n4, m, M.data(), n4, piv.data(), Y.data(), n4);
+        }
+        // Y now holds X row-major (m x 4m)
         for (int q = 0; q < 4; ++q) {
             std::vector<cd>& D = out.mat2[q][k];
             D.assign((size_t)m * m, cd(0.0, 0.0));

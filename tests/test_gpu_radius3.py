@@ -3,7 +3,8 @@ FP64 oracle (marked gpu): a Gamma three nodes deep, the 19-point interior stenci
 order 0 (packed symmetric tiles for one complex64 orbital) and order 1 (Thm 3.2's fit
 and the two-point fit, both as dense class rows [B | A], since A = -i H_{Gamma,II}
 H_{II,Gamma} is not diagonal), a cube (irreducible classes) and a box with unequal odd
-axes, one and three orbitals, element by element."""
+axes, one and three orbitals, element by element; order 2 in FP64; and the paper's 31^3
+experiment with orders 0, 1 and 2."""
 import numpy as np
 import pytest
 
@@ -75,11 +76,16 @@ def test_radius3_run_matches_oracle(torch_cuda, dims, b, prec, order, fit):
 @pytest.mark.parametrize("prec", ["fp64"])
 def test_radius3_order2_matches_oracle(torch_cuda, prec):
     """The second-order ABC (s = 1, 2, 3, 10 as in Sec. 4.2) with the radius-3 stencil, in
-    FP64 (the library refuses complex64 here: the interpolation system is nearly
-    singular and B1, B0 carry entries near 1e7 that cancel to eigenvalues near 1e2).  Two
-    FP64 setups agree only to cond * eps: the library's and the oracle's coefficient sets
-    differ elementwise by ~1e-3 while both interpolate K to ~1e-8 at the four points, so
-    phi is compared at 1e-7 and the auxiliary state [f | g] they drive at 1e-5."""
+    FP64 (the library refuses complex64 here: its fitted entries near 1e5 cancel and
+    FP32 drifts by ~1e-4).  The four-point system is nearly singular, so its solution is
+    a family; both sides take the basic solution of a column-pivoted QR, the oracle on
+    the natural-order system, the library per irreducible class, i.e. in another basis,
+    so they pick different members (coefficients differing O(1)) that both interpolate K
+    to ~1e-9 with every root of det(s^2 I - s B1 - B0) at Re <= ~1e-13 here
+    (`tests/test_library_host.py`, `tests/test_oracle_order2.py`).  The trajectories they
+    drive differ by 3e-7 (phi) and 2e-4 ([f | g]) after 40 steps (measured with both
+    coefficient sets in the oracle's stepper), so phi is held to 1e-6 and the auxiliary
+    state to 1e-3."""
     torch = torch_cuda
     from paper_1908_02456_gb300 import abc
     dims, h, dt, steps, b = (9, 8, 9), 0.5, 0.005, 40, 2
@@ -97,9 +103,9 @@ def test_radius3_order2_matches_oracle(torch_cuda, prec):
     ref_p, ref_a, _ = sy.run(psi0.reshape(b, -1), dt, steps, f0=sy.initial_aux(psi0.reshape(b, -1)))
     ctx.run(psi, aux, Vt, dt, steps)
     torch.cuda.synchronize()
-    assert rel(psi.cpu().numpy().reshape(b, -1), ref_p) < 1e-7
+    assert rel(psi.cpu().numpy().reshape(b, -1), ref_p) < 1e-6
     a = aux.cpu().numpy().astype(np.complex128)
-    assert rel(a.transpose(2, 0, 1).reshape(b, -1), ref_a) < 1e-5
+    assert rel(a.transpose(2, 0, 1).reshape(b, -1), ref_a) < 1e-3
 
 
 def test_radius3_refuses_adjoint_and_noalloc(torch_cuda):
@@ -129,9 +135,10 @@ def test_paper_3d_experiment_replay(torch_cuda):
     with the first-order ABC fitted at s = 1, 2; read here as the norm left in the box
     minus the closed form's norm in the box at t = 0.6.  Before the packet reaches the
     faces (t = 0.1) the run follows eq:15 up to the discretisation and the first
-    absorption (< 7 %).  The zeroth order (s0 = 1) reflects more.  (The second order at
-    s = 1, 2, 3, 10 is not replayed: with this stencil and spacing its four-point fit is
-    nearly singular and the fitted dynamics diverge, in the oracle as in the library.)"""
+    absorption (< 7 %).  The zeroth order (s0 = 1) reflects more.  The second order at
+    s = 1, 2, 3, 10 (FP64; its nearly singular four-point fit taken as the basic solution
+    of a column-pivoted QR) reflects far less, as the paper reports (measured 0.011
+    against 0.198), and stays stable: the norm keeps falling over 2400 further steps."""
     torch = torch_cuda
     from oracle.exact import free_packet
     from paper_1908_02456_gb300 import abc
@@ -143,15 +150,20 @@ def test_paper_3d_experiment_replay(torch_cuda):
     ex0 = free_packet([X, Y, Z], 0.0, (0, 0, 0), (5.0, 0, 0), 0.5)
     scale = psi0[0][0, 0, 0] / ex0[0, 0, 0]             # the inputs are h^3-normalised
     res = {}
-    for name, order, kw in [("order0", 0, {}), ("order1", 1, dict(fit1="two_point", s1b=2.0))]:
-        ctx = abc.Context(dims, h, order, 1.0, precision="c64", radius=3, **kw)
+    runs = [("order0", 0, 1.0, "c64", {}), ("order1", 1, 1.0, "c64", dict(fit1="two_point", s1b=2.0)),
+            ("order2", 2, (1.0, 2.0, 3.0, 10.0), "fp64", {})]
+    later = None
+    for name, order, s, prec, kw in runs:
+        ctx = abc.Context(dims, h, order, s, precision=prec, radius=3, **kw)
         assert ctx.n_gamma == 14166
         psi = torch.from_numpy(psi0).to("cuda", ctx.complex_dtype).contiguous()
         Vt = torch.from_numpy(V).to("cuda", ctx.real_dtype).contiguous()
-        aux = ctx.new_aux(1) if order == 1 else None
+        aux = ctx.init_aux(psi) if order == 2 else ctx.new_aux(1) if order == 1 else None
         d1 = ctx.run(psi, aux, Vt, dt, 100, diag_every=100)
         p1 = psi.cpu().numpy()[0].astype(np.complex128)
         d = ctx.run(psi, aux, Vt, dt, 500, diag_every=100)
+        if order == 2:
+            later = ctx.run(psi, aux, Vt, dt, 2400, diag_every=600)[:, 0, 0]
         torch.cuda.synchronize()
         norms = np.concatenate([d1[:, 0, 0], d[:, 0, 0]])
         ex1 = scale * free_packet([X, Y, Z], 0.1, (0, 0, 0), (5.0, 0, 0), 0.5)
@@ -164,3 +176,5 @@ def test_paper_3d_experiment_replay(torch_cuda):
     assert np.all(np.diff(res["order1"][0][:4]) < 0), res["order1"][0]
     assert 0.1 < refl["order1"] < 0.3, refl
     assert refl["order0"] > refl["order1"], refl
+    assert 0 < refl["order2"] < 0.05 and refl["order2"] < refl["order1"] / 5, refl
+    assert np.all(np.diff(np.concatenate([res["order2"][0], later])) < 0), later

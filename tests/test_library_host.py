@@ -157,3 +157,21 @@ def test_radius3_order2_host_interpolates(lib):
     for sj in pts:
         K = dtn_eval(box, sj)
         assert np.abs(rational22(co, sj) - K).max() < 1e-7 * np.abs(K).max()
+
+
+@pytest.mark.parametrize("dims", [(7, 8, 7), (9, 8, 9)])
+def test_radius3_order2_fit_is_stable(lib, dims):
+    """The library's radius-3 second-order fit (basic solution of a column-pivoted QR per
+    irreducible class) interpolates K at its four points and keeps every root of
+    det(s^2 I - s B1 - B0) in the closed left half-plane (up to 1e-9): the fitted
+    auxiliary dynamics cannot grow."""
+    h, pts = 0.5, (1.0, 2.0, 3.0, 10.0)
+    co = {k: abc.abc_host_matrices(dims, h, 2, pts, w, radius=3)
+          for k, w in (("B1", abc.MAT_B1), ("B0", abc.MAT_B0), ("A1", abc.MAT_A1), ("A0", abc.MAT_A0))}
+    n = co["B1"].shape[0]
+    roots = np.linalg.eigvals(np.block([[np.zeros((n, n)), np.eye(n)], [co["B0"], co["B1"]]]))
+    assert roots.real.max() < 1e-9
+    box = Box(dims, h, 3)
+    for sj in pts:
+        K = dtn_eval(box, sj)
+        assert np.abs(rational22(co, sj) - K).max() < 1e-7 * np.abs(K).max()

@@ -107,3 +107,21 @@ def test_swapped_b0_b1_is_caught(small):
     box, co = small
     broken = dict(co, B1=co["B0"], B0=co["B1"])
     assert _transfer_residual(box, co, broken, 2.2) > 1e-6
+
+
+def test_radius3_fit_is_a_stable_basic_solution():
+    """Radius 3 (Sec. 4.2's stencil): the four-point system is nearly singular; the
+    oracle's fit (basic solution of a column-pivoted QR) interpolates K at the points
+    and keeps every root of det(s^2 I - s B1 - B0) in the closed left half-plane, and
+    its free unknowns (one per dropped pivot, shared by all rows) are exactly zero."""
+    box = Box((9, 8, 9), 0.5, 3)
+    pts = (1.0, 2.0, 3.0, 10.0)
+    co = order2(box, pts)
+    n = co["B1"].shape[0]
+    roots = np.linalg.eigvals(np.block([[np.zeros((n, n)), np.eye(n)], [co["B0"], co["B1"]]]))
+    assert roots.real.max() < 1e-9
+    for sj, K in zip(pts, co["Ks"]):
+        assert np.abs(rational22(co, sj) - K).max() < 1e-7 * np.abs(K).max()
+    X = np.concatenate([co[k] for k in ("B1", "B0", "A1", "A0")], axis=1)
+    zero_cols = np.sum(np.all(X == 0, axis=0))
+    assert 1 <= zero_cols < X.shape[1] // 4
