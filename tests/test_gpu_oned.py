@@ -121,3 +121,27 @@ def test_paper_1d_experiment_on_gpu(env):
     assert err["order0"].max() > err["order1_2pt"].max() > err["order2"].max()
     _, _, d32 = gpu_run(torch, abc, n, h, 2, CASES[3][2], "limit", "c64", psi0, dt, nsteps, every)
     assert np.abs(d32 - n_exact).max() < 3e-3            # the same bound in complex64 (measured 8.1e-4)
+
+
+def test_paper_1d_solutions_on_gpu(env):
+    """The GPU's solutions of Sec. 4.1 at t = 1.6 (the packet crossing x = 3), FP64:
+    each order's psi equals the oracle's (1e-9 for orders 0 and 1, 1e-7 for order 2,
+    whose two fits agree to ~1e-7 at this h) and the error against the exact solution
+    falls with the order, as the paper's figure of the wave functions shows."""
+    torch, abc = env
+    h, n, k0, xc = 0.01, 1501, 5.0, -6.0
+    x = -12.0 + h * np.arange(n)
+    psi0 = free_packet([x], 0.0, (xc,), (k0,), 0.5)
+    T, dt = 1.6, 8e-5
+    nsteps = int(round(T / dt))
+    ex = free_packet([x], T, (xc,), (k0,), 0.5)
+    box = Box((n,), h, 2)
+    err = {}
+    for name, order, s, fit in CASES:
+        if name == "order1":
+            continue
+        p, _, _ = gpu_run(torch, abc, n, h, order, s, fit, "fp64", psi0, dt, nsteps, 0)
+        ref, _, _ = System(box, coeffs=oracle_coeffs(box, order, s, fit)).run(psi0[None], dt, nsteps)
+        assert rel(p, ref[0]) < (1e-9 if order < 2 else 1e-7), name
+        err[name] = rel(p, ex)
+    assert err["order0"] > 2 * err["order1_2pt"] > 4 * err["order2"], err
