@@ -364,6 +364,15 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           node pair, the z neighbours rolling through registers and the
  *                           next plane's loads issued before the current one is computed
  *                           (same formula in every form).
+ *   ABC_TUNE_STENCIL_STAGED complex64, radius 1, nx even and <= 256, n_orb >= 2: 1 runs the
+ *                           stage-by-stage stencil with each CTA marching through 24 planes
+ *                           of an 8-row tile of one orbital, the planes of w (with their y
+ *                           halo) and of y staged in six shared-memory slots by 1D bulk
+ *                           copies (cp.async.bulk, two per plane) on mbarriers, so that
+ *                           planes z + 2 .. z + 4 are in flight while plane z is computed;
+ *                           bit-identical to the other forms; 0 (default) direct loads.
+ *                           Takes precedence
+ *                           over ABC_TUNE_STENCIL_KZ and ABC_TUNE_STENCIL_BPS.
  *   ABC_TUNE_BACK_MULTI     order 1 (limit fit), n_orb a multiple of 4, unpacked
  *                           contraction output: 1 runs the back transform four orbitals
  *                           per cell group (its tables read once per four); 0 (default)
@@ -406,6 +415,7 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
 #define ABC_TUNE_BACK_MULTI 10
 #define ABC_TUNE_FORWARD_RW 11
 #define ABC_TUNE_GAMMA_COPY 12
+#define ABC_TUNE_STENCIL_STAGED 13
 int abc_set_tuning(abc_ctx* ctx, int key, long long value);
 int abc_get_tuning(const abc_ctx* ctx, int key, long long* value);
 

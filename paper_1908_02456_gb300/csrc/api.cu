@@ -15,6 +15,7 @@
 
 #include "ctx.h"
 #include "stencil_fused.cuh"
+#include "stencil_bulk.cuh"
 
 namespace abc {
 int fail(int status, const std::string& msg);
@@ -896,6 +897,14 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
 // the contraction: its CTAs each need a whole SM (shared memory), so stencil blocks
 // resident at its launch would hold back its start; forked after it, the stencil
 // overlaps the back transform instead.
+// The staged stencil form applies to radius 1, nx even and at most 256 (a tile row of
+// pairs per thread), several orbitals and 16-byte aligned state arrays (bulk copies).
+bool staged_ok(const abc_ctx* c, const void* w, const void* y, const void* o) {
+    const Geometry& g = c->geo;
+    const uintptr_t a = (uintptr_t)w | (uintptr_t)y | (uintptr_t)o;
+    return g.R == 1 && (g.nx & 1) == 0 && g.nx <= 256 && c->staged_attr && (a & 15) == 0;
+}
+
 // g_in / g_out (complex64 stages with the Gamma copy, else NULL): the forward transform
 // reads w on Gamma from g_in, and the stencil writes the stage output on Gamma to g_out.
 template <typename T>
@@ -923,6 +932,13 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             dev::stencil_stage_x2z2<<<gp, 256, 0, ss>>>(g.nx, g.ny, g.nz, n_orb, (float)(1.0 / (g.h * g.h)),
                                                         (const float2*)w_phi, (const float2*)y_phi, (const float*)V,
                                                         (const float2*)bt, (float2*)o_phi, (float)cdt);
+        } else if (sizeof(T) == 4 && c->stencil_staged && staged_ok(c, w_phi, y_phi, o_phi)) {
+            // complex64: planes staged in shared memory by bulk copies, marching through z
+            const dim3 gb((unsigned)((g.ny + dev::SB_TY - 1) / dev::SB_TY), (unsigned)((g.nz + dev::SB_KZ - 1) / dev::SB_KZ),
+                          (unsigned)n_orb);
+            dev::stencil_stage_x2_bulk<<<gb, (g.nx / 2) * dev::SB_TY, dev::stencil_bulk_smem(g.nx), ss>>>(
+                g.nx, g.ny, g.nz, n_orb, (float)(1.0 / (g.h * g.h)), (const float2*)w_phi, (const float2*)y_phi,
+                (const float*)V, (const float2*)bt, (float2*)o_phi, (float)cdt, (float2*)g_out, c->err_flag.as<int>());
         } else if (sizeof(T) == 4 && (g.nx & 1) == 0 && c->stencil_bps > 0 && ss != s) {
             // beside the boundary chain: a bounded number of blocks per SM, grid-stride
             dev::stencil_stage_x2_gs<<<(unsigned)(c->tc_sms_all * c->stencil_bps), 256, 0, ss>>>(
@@ -1968,6 +1984,16 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         drop_graphs(ctx);
         return ensure_gam(ctx);
     }
+    if (key == ABC_TUNE_STENCIL_STAGED) {
+        ctx->stencil_staged = value != 0;
+        drop_graphs(ctx);
+        if (ctx->stencil_staged && !ctx->staged_attr && ctx->geo.nx <= 256) {
+            CUDA_TRY(cudaFuncSetAttribute(abc::dev::stencil_stage_x2_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)abc::dev::stencil_bulk_smem(ctx->geo.nx)));
+            ctx->staged_attr = true;
+        }
+        return ABC_OK;
+    }
     if (key == ABC_TUNE_BACK_MULTI) {
         ctx->back_multi = value != 0;
         drop_graphs(ctx);
@@ -2009,6 +2035,7 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_BACK_MULTI) { *value = ctx->back_multi ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_FORWARD_RW) { *value = ctx->fwd_rw ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_GAMMA_COPY) { *value = ctx->gam_mode ? 1 : 0; return ABC_OK; }
+    if (key == ABC_TUNE_STENCIL_STAGED) { *value = ctx->stencil_staged ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_GEMM_SPLIT) { *value = ctx->tc_split; return ABC_OK; }
     return fail(ABC_ERR_ARG, "unknown tuning key");
 }

@@ -86,6 +86,8 @@ struct abc_ctx {
     int stencil_mode = 0;            // where the stencil runs in a stage (tuning, ABC_TUNE_STENCIL)
     int stencil_bps = 0;             // side-stream stencil: blocks per SM of a grid-stride grid (0: one per pair)
     int stencil_kz = 1;              // complex64 stencil form (ABC_TUNE_STENCIL_KZ): 1 capped registers (default)
+    bool stencil_staged = false;     // complex64 stencil with planes staged by bulk copies (ABC_TUNE_STENCIL_STAGED)
+    bool staged_attr = false;        // its shared-memory size attribute has been set
     bool back_multi = false;         // order-1 back transform four orbitals per cell group (tuning)
     bool fwd_rw = false;             // four-orbital forward transform with the reflection transform in registers
     bool gam_mode = false;           // stencils write the next stage's w on Gamma for the forward transform (tuning)

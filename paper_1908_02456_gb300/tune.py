@@ -9,8 +9,9 @@ precision and the device, so the library exposes its choices as tuning knobs
   K split count (``TUNE_GEMM_SPLIT``: automatic, or 1, 2 splits per output tile);
 * the interior stencil of an order-1 step: the four Horner stages fused in time
   (``TUNE_FUSED``) or stage by stage, and for the latter where the stencil runs
-  beside the boundary chain (``TUNE_STENCIL``) and how many planes each of its threads
-  marches through (``TUNE_STENCIL_KZ``);
+  beside the boundary chain (``TUNE_STENCIL``), how many planes each of its threads
+  marches through (``TUNE_STENCIL_KZ``) and whether its planes are staged in shared
+  memory by bulk copies (``TUNE_STENCIL_STAGED``);
 * the order-1 back transform one or four orbitals per cell group (``TUNE_BACK_MULTI``),
   the four-orbital forward transform's reflection transform across lanes or in
   registers (``TUNE_FORWARD_RW``) and whether it reads w on Gamma from the copy the
@@ -64,11 +65,15 @@ def knob_groups(ctx: abc.Context, n_orb: int):
         groups.append([{abc.TUNE_GEMM_TILE: t, abc.TUNE_GEMM_SPLIT: sp} for t in (0, 1, 2) for sp in (0, 1, 2)])
     if ctx.order == 1 and ctx.precision != abc.FP64:
         nx = ctx.shape[0]
-        stencil = [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: m, abc.TUNE_STENCIL_KZ: 0} for m in (0, 1, 2)]
+        st = {abc.TUNE_STENCIL_STAGED: 0}
+        stencil = [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: m, abc.TUNE_STENCIL_KZ: 0, **st} for m in (0, 1, 2)]
         if nx % 2 == 0 and ctx.radius == 1 and n_orb >= 2:
-            stencil += [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: 0, abc.TUNE_STENCIL_KZ: kz} for kz in (1, 2, 4, 8)]
+            stencil += [{abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: 0, abc.TUNE_STENCIL_KZ: kz, **st} for kz in (1, 2, 4, 8)]
+            if nx <= 256:
+                stencil.append({abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: 0, abc.TUNE_STENCIL_KZ: 1,
+                                abc.TUNE_STENCIL_STAGED: 1})
         if nx % 2 == 0 and min(ctx.shape) >= 8 and ctx.radius == 1:
-            stencil.append({abc.TUNE_FUSED: 1})
+            stencil.append({abc.TUNE_FUSED: 1, **st})
         groups.append(stencil)
     if ctx.order == 1 and ctx.fit1 == abc.FIT1_LIMIT and n_orb >= 4 and n_orb % 4 == 0:
         groups.append([{abc.TUNE_BACK_MULTI: 0}, {abc.TUNE_BACK_MULTI: 1}])
@@ -152,6 +157,6 @@ def describe(setting: dict) -> dict:
              abc.TUNE_STENCIL_BPS: "stencil_blocks_per_sm(0=one thread per pair)",
              abc.TUNE_STENCIL_KZ: "stencil_form(0=pair per thread, 1=capped registers, k>1=k planes)",
              abc.TUNE_BACK_MULTI: "back_transform_4_orbitals", abc.TUNE_FORWARD_RW: "forward_transform_in_registers",
-             abc.TUNE_GAMMA_COPY: "forward_reads_gamma_copy",
+             abc.TUNE_GAMMA_COPY: "forward_reads_gamma_copy", abc.TUNE_STENCIL_STAGED: "stencil_planes_staged_by_bulk_copies",
              abc.TUNE_PDL: "pdl"}
     return {names.get(int(k), str(k)): v for k, v in setting.items()}

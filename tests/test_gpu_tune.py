@@ -170,3 +170,36 @@ def test_gamma_copy_is_bit_identical(env, order, form, prec):
     assert torch.equal(outs[0][0], outs[1][0])
     if order == 1:
         assert torch.equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("dims", [(18, 14, 13), (10, 17, 50), (96, 9, 26)])
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("placement,gc", [(0, 0), (1, 1)])
+def test_staged_stencil_is_bit_identical(env, dims, order, placement, gc):
+    """The stencil with its planes staged in shared memory by bulk copies evaluates the
+    same expressions in the same order as the direct-load forms, so whole runs are bit
+    for bit the same: ragged row tiles (14 = 8 + 6 rows, 17 = 8 + 8 + 1) and plane runs
+    (13 < 24, 50 = 24 + 24 + 2, 26 = 24 + 2), a full-width row of 96, orders 0 and 1,
+    the stencil beside the forward transform, the Gamma copy written by it."""
+    torch, abc = env
+    h, dt, b = 0.45, 0.005, 4
+    psi0 = inputs.orbital_set(dims, h, np.random.default_rng(36), b)
+    V0 = inputs.smooth_random(dims, h, np.random.default_rng(37))
+    outs = []
+    for staged in (0, 1):
+        ctx = abc.Context(dims, h, order, 1.0, precision="c64", max_orbitals=b)
+        ctx.set_tuning(abc.TUNE_STENCIL, placement)
+        ctx.set_tuning(abc.TUNE_GAMMA_COPY, gc)
+        ctx.set_tuning(abc.TUNE_STENCIL_STAGED, staged)
+        assert ctx.get_tuning(abc.TUNE_STENCIL_STAGED) == staged
+        psi = torch.from_numpy(psi0).to("cuda", torch.complex64).contiguous()
+        aux = ctx.new_aux(b)
+        V = torch.from_numpy(V0).to("cuda", torch.float32).contiguous()
+        ctx.run(psi, aux, V, dt, 6, meanfield=(-1.0, 0.8, 1.0 / 6.0))
+        ctx.step(psi, aux, V, dt)
+        torch.cuda.synchronize()
+        outs.append((psi.cpu(), aux.cpu()))
+        ctx.close()
+    assert torch.equal(outs[0][0], outs[1][0])
+    if order == 1:
+        assert torch.equal(outs[0][1], outs[1][1])
