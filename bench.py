@@ -379,8 +379,9 @@ def measure(args, w, rank, world, dev, extra_lines=True):
     ach_s = bytes_s / avg_s / 1e9
     fused = ctx.get_tuning(abc.TUNE_FUSED) == 1 or (ctx.get_tuning(abc.TUNE_FUSED) == -1 and w.n_orb >= 2)
     kz = ctx.get_tuning(abc.TUNE_STENCIL_KZ)
-    form = ("stencil_stage_x2z2" if w.n_orb == 1 else "stencil_stage_x2_lb<8>" if kz == 1 else
-            "stencil_stage_x2" if kz == 0 else f"stencil_stage_x2zk<{kz}>")
+    form = ("stencil_stage_x2z2" if w.n_orb == 1 else
+            "stencil_stage_x2_bulk" if ctx.get_tuning(abc.TUNE_STENCIL_STAGED) == 1 else
+            "stencil_stage_x2_lb<8>" if kz == 1 else "stencil_stage_x2" if kz == 0 else f"stencil_stage_x2zk<{kz}>")
     sname = ("stencil_bulk4 (the four Horner stages' interior fused in time)" if fused else
              f"{form} (fused stencil + potential + Horner stage)")
     stencil = {"bound": "hbm", "kernel": sname,
