@@ -373,10 +373,10 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           bit-identical to the other forms; 0 (default) direct loads.
  *                           Takes precedence
  *                           over ABC_TUNE_STENCIL_KZ and ABC_TUNE_STENCIL_BPS.
- *   ABC_TUNE_BACK_MULTI     order 1 (limit fit), n_orb a multiple of 4, unpacked
- *                           contraction output: 1 runs the back transform four orbitals
- *                           per cell group (its tables read once per four); 0 (default)
- *                           one orbital per group.
+ *   ABC_TUNE_BACK_MULTI     order 1 (limit fit), unpacked contraction output: 1 runs the
+ *                           back transform four orbitals per cell group (n_orb a multiple
+ *                           of 4; its tables read once per four), 2 two orbitals per group
+ *                           (n_orb even); 0 (default) one orbital per group.
  *   ABC_TUNE_FORWARD_RW     n_orb a multiple of 4: 1 runs the four-orbital forward
  *                           transform with each slot's 8-point reflection transform in
  *                           one thread's registers (no lane shuffles; bit-identical

@@ -875,8 +875,13 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
             return;
         }
     }
-    if (MODE == 0 && !fuse && c->back_multi && n_orb % dev::FO == 0) {
-        dev::bnd_back_multi<T><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
+    if (MODE == 0 && !fuse && c->back_multi == 1 && n_orb % 4 == 0) {
+        dev::bnd_back_multi<T, 4><<<cell_blocks(c, n_orb / 4), 128, 0, s>>>(
+            ct, n_orb, s1, a_coef, hp, hf, (const Vc*)tr.t, tr.nsplit, tr.stride, (const Vc*)y_f, (Vc*)out, cdt);
+        return;
+    }
+    if (MODE == 0 && !fuse && c->back_multi == 2 && n_orb % 2 == 0) {
+        dev::bnd_back_multi<T, 2><<<cell_blocks(c, n_orb / 2), 128, 0, s>>>(
             ct, n_orb, s1, a_coef, hp, hf, (const Vc*)tr.t, tr.nsplit, tr.stride, (const Vc*)y_f, (Vc*)out, cdt);
         return;
     }
@@ -1995,7 +2000,8 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         return ABC_OK;
     }
     if (key == ABC_TUNE_BACK_MULTI) {
-        ctx->back_multi = value != 0;
+        if (value < 0 || value > 2) return fail(ABC_ERR_ARG, "ABC_TUNE_BACK_MULTI takes 0, 1 or 2");
+        ctx->back_multi = (int)value;
         drop_graphs(ctx);
         return ABC_OK;
     }
@@ -2032,7 +2038,7 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_GEMM_TILE) { *value = ctx->tc_cfg; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL_BPS) { *value = ctx->stencil_bps; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL_KZ) { *value = ctx->stencil_kz; return ABC_OK; }
-    if (key == ABC_TUNE_BACK_MULTI) { *value = ctx->back_multi ? 1 : 0; return ABC_OK; }
+    if (key == ABC_TUNE_BACK_MULTI) { *value = ctx->back_multi; return ABC_OK; }
     if (key == ABC_TUNE_FORWARD_RW) { *value = ctx->fwd_rw ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_GAMMA_COPY) { *value = ctx->gam_mode ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL_STAGED) { *value = ctx->stencil_staged ? 1 : 0; return ABC_OK; }

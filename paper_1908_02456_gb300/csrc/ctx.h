@@ -88,7 +88,7 @@ struct abc_ctx {
     int stencil_kz = 1;              // complex64 stencil form (ABC_TUNE_STENCIL_KZ): 1 capped registers (default)
     bool stencil_staged = false;     // complex64 stencil with planes staged by bulk copies (ABC_TUNE_STENCIL_STAGED)
     bool staged_attr = false;        // its shared-memory size attribute has been set
-    bool back_multi = false;         // order-1 back transform four orbitals per cell group (tuning)
+    int back_multi = 0;              // order-1 back transform: 0 one orbital per cell group, 1 four, 2 two (tuning)
     bool fwd_rw = false;             // four-orbital forward transform with the reflection transform in registers
     bool gam_mode = false;           // stencils write the next stage's w on Gamma for the forward transform (tuning)
     abc::DevBuf gam[2];              // that Gamma copy, [n_gamma][max_orbitals], one per stage parity

@@ -684,10 +684,10 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
 }
 
 // bnd_back<T, 0, false> for FO consecutive orbitals per cell group (n_orb a multiple of
-// FO): the cell's tables and coefficients are read once per FO orbitals and each
-// thread has FO independent sets of loads in flight.  Same arithmetic and order as
+// FO, 2 or 4): the cell's tables and coefficients are read once per FO orbitals and
+// each thread has FO independent sets of loads in flight.  Same arithmetic and order as
 // bnd_back<T, 0, false>, orbital by orbital.
-template <typename T>
+template <typename T, int FO = dev::FO>
 __global__ void __launch_bounds__(128) bnd_back_multi(CellTab<T> ct, int n_orb, T s1, T a_coef,
                                                       const typename C2<T>::t* __restrict__ hat_phi,
                                                       const typename C2<T>::t* __restrict__ hat_f,

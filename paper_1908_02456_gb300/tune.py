@@ -75,8 +75,8 @@ def knob_groups(ctx: abc.Context, n_orb: int):
         if nx % 2 == 0 and min(ctx.shape) >= 8 and ctx.radius == 1:
             stencil.append({abc.TUNE_FUSED: 1, **st})
         groups.append(stencil)
-    if ctx.order == 1 and ctx.fit1 == abc.FIT1_LIMIT and n_orb >= 4 and n_orb % 4 == 0:
-        groups.append([{abc.TUNE_BACK_MULTI: 0}, {abc.TUNE_BACK_MULTI: 1}])
+    if ctx.order == 1 and ctx.fit1 == abc.FIT1_LIMIT and n_orb >= 2 and n_orb % 2 == 0:
+        groups.append([{abc.TUNE_BACK_MULTI: m} for m in ((0, 1, 2) if n_orb % 4 == 0 else (0, 2))])
     if n_orb >= 4 and n_orb % 4 == 0 and ctx.order < 2:
         if ctx.precision != abc.FP64 and ctx.radius == 1 and ctx.shape[0] % 2 == 0:
             groups.append([{abc.TUNE_FORWARD_RW: rw, abc.TUNE_GAMMA_COPY: gc} for gc in (0, 1) for rw in (0, 1)])
@@ -156,7 +156,7 @@ def describe(setting: dict) -> dict:
              abc.TUNE_STENCIL: "stencil_placement(0=after contraction, 1=stage start, 2=serial)",
              abc.TUNE_STENCIL_BPS: "stencil_blocks_per_sm(0=one thread per pair)",
              abc.TUNE_STENCIL_KZ: "stencil_form(0=pair per thread, 1=capped registers, k>1=k planes)",
-             abc.TUNE_BACK_MULTI: "back_transform_4_orbitals", abc.TUNE_FORWARD_RW: "forward_transform_in_registers",
+             abc.TUNE_BACK_MULTI: "back_transform_orbitals_per_group(0=1, 1=4, 2=2)", abc.TUNE_FORWARD_RW: "forward_transform_in_registers",
              abc.TUNE_GAMMA_COPY: "forward_reads_gamma_copy", abc.TUNE_STENCIL_STAGED: "stencil_planes_staged_by_bulk_copies",
              abc.TUNE_PDL: "pdl"}
     return {names.get(int(k), str(k)): v for k, v in setting.items()}

@@ -111,7 +111,7 @@ def test_stencil_placements_give_identical_steps(env, mode, bps):
 
 @pytest.mark.parametrize("knob,value", [("STENCIL_KZ", 1), ("STENCIL_KZ", 2), ("STENCIL_KZ", 4), ("STENCIL_KZ", 8),
                                         ("STENCIL_KZ", 16),
-                                        ("BACK_MULTI", 1), ("FORWARD_RW", 1)])
+                                        ("BACK_MULTI", 1), ("BACK_MULTI", 2), ("FORWARD_RW", 1)])
 @pytest.mark.parametrize("prec", ["fp16x3", "c64"])
 def test_kernel_forms_match_default(env, knob, value, prec):
     """The z-marching stencil forms (2..16 planes per thread, the box's 13 planes leave a
