@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--knob", action="append", default=[], metavar="NAME=VALUE",
                     help="set a tuning knob (abc.TUNE_<NAME>) after tuning, e.g. BACK_MULTI=1 (profiling runs)")
     ap.add_argument("--workload", type=int, default=WORKLOAD_NUMBER,
-                    help="5 (default) or 2 give a full line; 1, 3, 4, 6-9 a line of their own")
+                    help="5 (default) or 2 give a full line; 1, 3, 4, 6-10 a line of their own")
     return ap.parse_args()
 
 

@@ -83,6 +83,10 @@ WORKLOADS = {
     # first order fitted at s = 1, 2
     9: Workload(9, "paper-free-31cube-r3-order1-twopoint", 31, 0.1, 1, 1, 1.0, 0.001, 600,
                 "zero", precision="c64", fit1="two_point", s1b=2.0, radius=3),
+    # the same experiment with the second order at s = 1, 2, 3, 10 (FP64: the fit at
+    # radius 3 needs it)
+    10: Workload(10, "paper-free-31cube-r3-order2", 31, 0.1, 1, 2, 1.0, 0.001, 600,
+                 "zero", precision="fp64", points=(1.0, 2.0, 3.0, 10.0), radius=3),
 }
 
 
@@ -182,7 +186,7 @@ def make_inputs(w: Workload, n: Optional[int] = None, n_orb: Optional[int] = Non
         V = smooth_random(shape, w.h, rng)
     else:
         raise ValueError(w.potential)
-    if w.number == 9:
+    if w.number in (9, 10):
         # the paper's packet: eq:15 at t = 0 with k0 = 5 (sigma^2 = 1/2, centre 0)
         psi = gaussian_packet(shape, w.h, (0.0, 0.0, 0.0), (5.0, 0.0, 0.0), 1.0)[None]
     elif w.number == 1:
