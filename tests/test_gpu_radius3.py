@@ -73,8 +73,8 @@ def test_radius3_run_matches_oracle(torch_cuda, dims, b, prec, order, fit):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64"])
-def test_radius3_order2_matches_oracle(torch_cuda, prec):
+@pytest.mark.parametrize("dims,b", [((9, 8, 9), 2), ((8, 8, 8), 1)])
+def test_radius3_order2_matches_oracle(torch_cuda, dims, b):
     """The second-order ABC (s = 1, 2, 3, 10 as in Sec. 4.2) with the radius-3 stencil, in
     FP64 (the library refuses complex64 here: its fitted entries near 1e5 cancel and
     FP32 drifts by ~1e-4).  The four-point system is nearly singular, so its solution is
@@ -83,12 +83,13 @@ def test_radius3_order2_matches_oracle(torch_cuda, prec):
     so they pick different members (coefficients differing O(1)) that both interpolate K
     to ~1e-9 with every root of det(s^2 I - s B1 - B0) at Re <= ~1e-13 here
     (`tests/test_library_host.py`, `tests/test_oracle_order2.py`).  The trajectories they
-    drive differ by 3e-7 (phi) and 2e-4 ([f | g]) after 40 steps (measured with both
-    coefficient sets in the oracle's stepper), so phi is held to 1e-6 and the auxiliary
-    state to 1e-3."""
+    drive differ by 3e-7 to 7e-7 (phi) and 2e-4 to 3e-4 ([f | g]) after 40 steps on these
+    boxes (measured with both coefficient sets in the oracle's stepper), so phi is held
+    to 3e-6 and the auxiliary state to 1e-3."""
     torch = torch_cuda
     from paper_1908_02456_gb300 import abc
-    dims, h, dt, steps, b = (9, 8, 9), 0.5, 0.005, 40, 2
+    prec = "fp64"
+    h, dt, steps = 0.5, 0.005, 40
     pts = (1.0, 2.0, 3.0, 10.0)
     rng = np.random.default_rng(95)
     V = inputs.smooth_random(dims, h, rng)
@@ -103,7 +104,7 @@ def test_radius3_order2_matches_oracle(torch_cuda, prec):
     ref_p, ref_a, _ = sy.run(psi0.reshape(b, -1), dt, steps, f0=sy.initial_aux(psi0.reshape(b, -1)))
     ctx.run(psi, aux, Vt, dt, steps)
     torch.cuda.synchronize()
-    assert rel(psi.cpu().numpy().reshape(b, -1), ref_p) < 1e-6
+    assert rel(psi.cpu().numpy().reshape(b, -1), ref_p) < 3e-6
     a = aux.cpu().numpy().astype(np.complex128)
     assert rel(a.transpose(2, 0, 1).reshape(b, -1), ref_a) < 1e-3
 

@@ -175,3 +175,15 @@ def test_radius3_order2_fit_is_stable(lib, dims):
     for sj in pts:
         K = dtn_eval(box, sj)
         assert np.abs(rational22(co, sj) - K).max() < 1e-7 * np.abs(K).max()
+
+
+def test_radius3_order2_fit_is_stable_at_the_paper_spacing(lib):
+    """At h = 0.1 (Sec. 4.2's spacing) the near-singular four-point system is where a plain
+    LU solution put roots of det(s^2 I - s B1 - B0) at real parts ~1.6e3 (11^3); the
+    library's pivoted-QR fit keeps them at Re <= 1e-6."""
+    dims, h, pts = (11, 11, 11), 0.1, (1.0, 2.0, 3.0, 10.0)
+    B1 = abc.abc_host_matrices(dims, h, 2, pts, abc.MAT_B1, radius=3)
+    B0 = abc.abc_host_matrices(dims, h, 2, pts, abc.MAT_B0, radius=3)
+    n = B1.shape[0]
+    roots = np.linalg.eigvals(np.block([[np.zeros((n, n)), np.eye(n)], [B0, B1]]))
+    assert roots.real.max() < 1e-6
