@@ -388,6 +388,15 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           forward transform reads it there instead of gathering single
  *                           values from the whole state; 0 (default) gathers from the
  *                           state.  Bit-identical results either way.
+ *   ABC_TUNE_LANES          order 1 (limit fit), tensor-core forms, n_orb a multiple of 32:
+ *                           1 holds the adapted vectors and the contraction output
+ *                           node-major ([adapted index][orbital]) inside a stage, and runs
+ *                           the forward and back transforms one warp per cell and 32
+ *                           orbitals, lane = orbital, the cell's transform in registers;
+ *                           every access of a warp is then 256 contiguous bytes (except
+ *                           the gather of w at Gamma from the state).  Bit-identical
+ *                           results; takes precedence over ABC_TUNE_FORWARD_RW and
+ *                           ABC_TUNE_BACK_MULTI.  0 (default) orbital-major.
  *   ABC_TUNE_GEMM_TILE      tensor-core forms, n_orb >= 2: 0 (default) output tiles of up
  *                           to 96 columns, three ring stages, one CTA per SM; 1: up to 64
  *                           columns, two stages, two CTAs per SM; 2: the complex products
@@ -416,6 +425,7 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
 #define ABC_TUNE_FORWARD_RW 11
 #define ABC_TUNE_GAMMA_COPY 12
 #define ABC_TUNE_STENCIL_STAGED 13
+#define ABC_TUNE_LANES 14
 int abc_set_tuning(abc_ctx* ctx, int key, long long value);
 int abc_get_tuning(const abc_ctx* ctx, int key, long long* value);
 

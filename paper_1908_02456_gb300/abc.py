@@ -20,7 +20,7 @@ MAT_B1, MAT_B0, MAT_A1, MAT_A0 = 5, 6, 7, 8
 KERNEL_CONTRACTION, KERNEL_STENCIL, KERNEL_PACK = 0, 1, 2
 TUNE_L2_KEEP_TILES, TUNE_TILE_COUNT, TUNE_PDL, TUNE_CHAIN, TUNE_STENCIL, TUNE_FUSED = 0, 1, 2, 3, 4, 5
 TUNE_GEMM_TILE, TUNE_GEMM_SPLIT, TUNE_STENCIL_BPS, TUNE_STENCIL_KZ, TUNE_BACK_MULTI = 6, 7, 8, 9, 10
-TUNE_FORWARD_RW, TUNE_GAMMA_COPY, TUNE_STENCIL_STAGED = 11, 12, 13
+TUNE_FORWARD_RW, TUNE_GAMMA_COPY, TUNE_STENCIL_STAGED, TUNE_LANES = 11, 12, 13, 14
 PRECISIONS = {"fp64": FP64, "c64": C64_FP32, "bf16x3": C64_SPLIT_BF16, "tf32x3": C64_3XTF32,
               "fp16x3": C64_SPLIT_FP16}
 FIT1_LIMIT, FIT1_TWO_POINT, FIT1_HERMITE = 0, 1, 2

@@ -15,6 +15,7 @@
 
 #include "ctx.h"
 #include "stencil_fused.cuh"
+#include "cell_lanes.cuh"
 #include "stencil_bulk.cuh"
 
 namespace abc {
@@ -756,29 +757,30 @@ struct TRes {
 // The persistent tensor-core GEMM in the context's tile configuration.
 template <int KIND>
 void launch_gemm_tc(abc_ctx* c, const abc_ctx::TcPlan& pl, int n_orb, float2* out, int conj, const int* colexp,
-                    cudaStream_t s) {
+                    cudaStream_t s, int nm = 0) {
     const long long n = c->geo.n_gamma;
     if (c->tc_cfg == 2)
         dev::gemm_tc<KIND, dev::TcKara><<<(unsigned)pl.grid, dev::TC_THREADS, dev::TcKara::smem, s>>>(
             c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
             c->tc_apack_k.as<float>(), c->tc_bpack.as<float>(), n_orb, (int)n, pl.nsplit, n * n_orb, out, conj,
-            c->err_flag.as<int>(), colexp);
+            c->err_flag.as<int>(), colexp, nm);
     else if (c->tc_cfg == 0)
         dev::gemm_tc<KIND, dev::TcWide><<<(unsigned)pl.grid, dev::TC_THREADS, dev::TcWide::smem, s>>>(
             c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
             c->tc_apack.as<float>(), c->tc_bpack.as<float>(), n_orb, (int)n, pl.nsplit, n * n_orb, out, conj,
-            c->err_flag.as<int>(), colexp);
+            c->err_flag.as<int>(), colexp, nm);
     else
         dev::gemm_tc<KIND, dev::TcNarrow><<<(unsigned)pl.grid, dev::TC_THREADS, dev::TcNarrow::smem, s>>>(
             c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
             c->tc_apack.as<float>(), c->tc_bpack.as<float>(), n_orb, (int)n, pl.nsplit, n * n_orb, out, conj,
-            c->err_flag.as<int>(), colexp);
+            c->err_flag.as<int>(), colexp, nm);
 }
 
-// The boundary contraction t = S x (conj: conj(S) x).
+// The boundary contraction t = S x (conj: conj(S) x).  nm: x and t node-major
+// (tensor-core path, n_orb a multiple of 32).
 template <typename T>
 TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaStream_t s,
-                 const void* const* x4 = nullptr) {
+                 const void* const* x4 = nullptr, bool nm = false) {
     typedef typename dev::C2<T>::t V;
     dev::XSeg<V> xs{{(const V*)x, nullptr, nullptr, nullptr}};
     if (x4)
@@ -808,32 +810,36 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
         const int* colexp = c->tc_colexp.as<int>();
         if (c->tc_f16) {
             const int ncols = c->tc_ncols * n_orb;
-            dev::tc_colexp<<<(unsigned)((ncols + 7) / 8), 256, 0, s>>>(c->tci, n_orb, n, (const float2*)x,
-                                                                       c->tc_colexp.as<int>(), ncols);
+            if (nm)
+                dev::tc_colexp_nm<<<(unsigned)(ncols / 32), 32 * dev::CX_WARPS, 0, s>>>(c->tci, n_orb, (const float2*)x,
+                                                                       c->tc_colexp.as<int>());
+            else
+                dev::tc_colexp<<<(unsigned)((ncols + 7) / 8), 256, 0, s>>>(c->tci, n_orb, n, (const float2*)x,
+                                                                           c->tc_colexp.as<int>(), ncols);
             if (c->tc_cfg == 2)
                 dev::pack_x_tc<dev::TC_F16, 1><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
                                                                       n_orb, n, (const float2*)x, conj,
-                                                                      c->tc_bpack.as<float>(), colexp);
+                                                                      c->tc_bpack.as<float>(), colexp, (int)nm);
             else
                 dev::pack_x_tc<dev::TC_F16><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
                                                                    n_orb, n, (const float2*)x, conj,
-                                                                   c->tc_bpack.as<float>(), colexp);
+                                                                   c->tc_bpack.as<float>(), colexp, (int)nm);
             prof_end(c, ABC_KERNEL_PACK, s);
             prof_begin(c, ABC_KERNEL_CONTRACTION, s);
-            launch_gemm_tc<dev::TC_F16>(c, pl, n_orb, out, conj, colexp, s);
+            launch_gemm_tc<dev::TC_F16>(c, pl, n_orb, out, conj, colexp, s, (int)nm);
             c->launches += 2;
         } else {
             if (c->tc_cfg == 2)
                 dev::pack_x_tc<dev::TC_TF32, 1><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
                                                                        n_orb, n, (const float2*)x, conj,
-                                                                       c->tc_bpack.as<float>(), colexp);
+                                                                       c->tc_bpack.as<float>(), colexp, (int)nm);
             else
                 dev::pack_x_tc<dev::TC_TF32><<<pgrid, 128, 0, s>>>(c->tci, c->tc_cols.as<dev::TcCols>() + pl.cols_off,
                                                                     n_orb, n, (const float2*)x, conj,
-                                                                    c->tc_bpack.as<float>(), colexp);
+                                                                    c->tc_bpack.as<float>(), colexp, (int)nm);
             prof_end(c, ABC_KERNEL_PACK, s);
             prof_begin(c, ABC_KERNEL_CONTRACTION, s);
-            launch_gemm_tc<dev::TC_TF32>(c, pl, n_orb, out, conj, colexp, s);
+            launch_gemm_tc<dev::TC_TF32>(c, pl, n_orb, out, conj, colexp, s, (int)nm);
             c->launches += 1;
         }
         res.t = out;
@@ -854,7 +860,7 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
 template <typename T, int MODE>
 void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f, void* out, void* acc, T cdt,
           cudaStream_t s, const void* hat_phi = nullptr, const void* hat_f = nullptr,
-          dev::FwdNext<T> fn = dev::FwdNext<T>{}) {
+          dev::FwdNext<T> fn = dev::FwdNext<T>{}, bool nm = false) {
     typedef typename dev::C2<T>::t Vc;
     const dev::CellTab<T> ct = cell_tab<T>(c);
     const unsigned nbk = cell_blocks(c, n_orb);
@@ -872,6 +878,13 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
                 dev::bnd_back<T, MODE, true><<<nbk, 128, 0, s>>>(ct, n_orb, s1, a_coef, hp, hf, (const Vc*)nullptr, 1,
                                                                  0LL, c->sym_gather, (const Vc*)y_f, (Vc*)out,
                                                                  (Vc*)acc, cdt, fn);
+            return;
+        }
+    }
+    if constexpr (sizeof(T) == 4 && MODE == 0) {
+        if (nm) {                            // node-major adapted vectors and t (lanes_ok)
+            dev::bnd_back_lanes<<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, dev::LANES_SMEM, s>>>(
+                ct, n_orb, s1, a_coef, hp, hf, (const Vc*)tr.t, tr.nsplit, tr.stride, (const Vc*)y_f, (Vc*)out, cdt);
             return;
         }
     }
@@ -904,6 +917,12 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
 // overlaps the back transform instead.
 // The staged stencil form applies to radius 1, nx even and at most 256 (a tile row of
 // pairs per thread), several orbitals and 16-byte aligned state arrays (bulk copies).
+// The node-major order-1 chain (ABC_TUNE_LANES): complex64 on the tensor cores, the
+// limit fit (diagonal A), n_orb a multiple of 32.
+bool lanes_ok(const abc_ctx* c, int n_orb) {
+    return c->lanes && c->lanes_attr && c->prec != ABC_FP64 && c->tc && c->params.order == 1 && !c->blocks.rows1 && n_orb % 32 == 0;
+}
+
 bool staged_ok(const abc_ctx* c, const void* w, const void* y, const void* o) {
     const Geometry& g = c->geo;
     const uintptr_t a = (uintptr_t)w | (uintptr_t)y | (uintptr_t)o;
@@ -1026,6 +1045,7 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
     // the next stage's adapted inputs (two alternating sets), so stages 1-3 skip the
     // forward transform.
     const bool chain = st >= 0 && order == 1 && c->chain;
+    const bool nm = sizeof(T) == 4 && lanes_ok(c, n_orb) && !chain;
     if (order >= 1) stencil_at(1);
     void* hp = chain && (st & 1) ? c->hat2_phi.p : c->hat_phi.p;
     void* hf = chain && (st & 1) ? c->hat2_f.p : c->hat_f.p;
@@ -1041,6 +1061,10 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             dev::bnd_forward<T, 0, true><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
                                                              order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,
                                                              nullptr, (T)0, dev::Ord2Fwd<T>{});
+        else if (nm)
+            dev::bnd_forward_lanes<<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
+                cell_tab<float>(c), n_orb, c->nvox, (const float2*)w_phi, (const float2*)w_f, (float2*)hp, (float2*)hf,
+                (const float2*)g_in);
         else if (n_orb % dev::FO == 0 && c->fwd_rw)
             dev::bnd_forward_multi_rw<T><<<cell_blocks(c, n_orb / dev::FO), 128, 0, s>>>(
                 ct, n_orb, c->nvox, (const Vc*)w_phi, order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,
@@ -1066,10 +1090,10 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
         join();
         return;
     }
-    const TRes gathered = contraction<T>(c, order == 1 ? hf : hp, c->tvec.p, n_orb, 0, s);
+    const TRes gathered = contraction<T>(c, order == 1 ? hf : hp, c->tvec.p, n_orb, 0, s, nullptr, nm);
     if (order == 1) {
         stencil_at(0);
-        back<T, 0>(c, gathered, n_orb, (T)c->blocks.s, a_coef, y_f, o_f, nullptr, cdt, s, hp, hf, fn);
+        back<T, 0>(c, gathered, n_orb, (T)c->blocks.s, a_coef, y_f, o_f, nullptr, cdt, s, hp, hf, fn, nm);
         stencil_at(2);
         join();
     } else {
@@ -1999,6 +2023,16 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         }
         return ABC_OK;
     }
+    if (key == ABC_TUNE_LANES) {
+        ctx->lanes = value != 0;
+        drop_graphs(ctx);
+        if (ctx->lanes && !ctx->lanes_attr) {
+            CUDA_TRY(cudaFuncSetAttribute(abc::dev::bnd_back_lanes, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)abc::dev::LANES_SMEM));
+            ctx->lanes_attr = true;
+        }
+        return ABC_OK;
+    }
     if (key == ABC_TUNE_BACK_MULTI) {
         if (value < 0 || value > 2) return fail(ABC_ERR_ARG, "ABC_TUNE_BACK_MULTI takes 0, 1 or 2");
         ctx->back_multi = (int)value;
@@ -2041,6 +2075,7 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_BACK_MULTI) { *value = ctx->back_multi; return ABC_OK; }
     if (key == ABC_TUNE_FORWARD_RW) { *value = ctx->fwd_rw ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_GAMMA_COPY) { *value = ctx->gam_mode ? 1 : 0; return ABC_OK; }
+    if (key == ABC_TUNE_LANES) { *value = ctx->lanes ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL_STAGED) { *value = ctx->stencil_staged ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_GEMM_SPLIT) { *value = ctx->tc_split; return ABC_OK; }
     return fail(ABC_ERR_ARG, "unknown tuning key");

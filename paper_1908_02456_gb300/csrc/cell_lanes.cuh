@@ -1,0 +1,248 @@
+// Boundary transforms of an order-1 stage with the orbitals across the lanes (complex64,
+// n_orb a multiple of 32, the many-orbital tensor-core contraction between them).
+//
+// The adapted vectors (hat_phi, hat_f) and the contraction output t are held node-major,
+// [adapted index][orbital] (orbitals fastest), instead of orbital-major.  A warp takes
+// one cell and 32 consecutive orbitals, lane = orbital, and does the cell's whole
+// transform for its orbital in registers: the 8-point reflection butterflies of every
+// slot and the per-parity 8 x 8 slot mixing (no lane shuffles, no shared memory).  The
+// cell's tables and coefficients are the same for every lane of the warp (broadcast
+// loads, uniform branches), and every array access of a warp instruction is 32
+// consecutive orbitals of one node: 256 contiguous bytes, whether the array is
+// node-major or in the natural boundary layout [n_gamma][orbital].  Only the gather of
+// w at Gamma from the full state is still one 8-byte value per orbital plane.
+//
+// The sums are those of bnd_forward_multi / bnd_back_multi, in the same order, so the
+// results are bit for bit the same as the orbital-major chain's.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gemm_tc.cuh"
+#include "kernels.cuh"
+
+namespace abc {
+namespace dev {
+
+constexpr int LANES_W = 4;          // warps per block
+
+// The 8-point Walsh-Hadamard butterflies of wht8_lanes on eight values in registers
+// (element g plays lane g): the same sums in the same order.
+__device__ __forceinline__ void wht8_regs(float2 (&x)[8]) {
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1) {
+        float2 y[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const float2 o = x[g ^ bit];
+            y[g] = (g & bit) ? make_float2(o.x - x[g].x, o.y - x[g].y) : make_float2(x[g].x + o.x, x[g].y + o.y);
+        }
+#pragma unroll
+        for (int g = 0; g < 8; ++g) x[g] = y[g];
+    }
+}
+
+__device__ __forceinline__ void ld_int8(const int* p, int (&v)[8]) {
+    const int4 a = __ldg(reinterpret_cast<const int4*>(p)), b = __ldg(reinterpret_cast<const int4*>(p + 4));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+__device__ __forceinline__ void ld_float8(const float* p, float (&v)[8]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p + 4));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// Warp -> (cell, first orbital), chunks of 32 orbitals fastest; false for the idle
+// warps of the last block.
+__device__ __forceinline__ bool lanes_item(const CellTab<float>& ct, int n_orb, int& cell, int& j) {
+    const int nch = n_orb >> 5;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= (long long)ct.n_cells * nch) return false;
+    cell = (int)(wid / nch);
+    j = (int)(wid - (long long)cell * nch) * 32 + (threadIdx.x & 31);
+    return true;
+}
+
+// Forward transform (bnd_forward_multi's outputs, node-major): hat_phi[jj][j] from w at
+// Gamma (gathered from the state w_phi [n_orb][nvox], or read from g_phi in the natural
+// boundary layout), hat_f[jj][j] from w_f (natural layout; nullptr: none).  Grid
+// ceil(n_cells * n_orb / 32 / LANES_W) blocks of 32 LANES_W threads.
+__global__ void __launch_bounds__(32 * LANES_W, 3) bnd_forward_lanes(CellTab<float> ct, int n_orb, long long nvox,
+                                                                     const float2* __restrict__ w_phi,
+                                                                     const float2* __restrict__ w_f,
+                                                                     float2* __restrict__ hat_phi,
+                                                                     float2* __restrict__ hat_f,
+                                                                     const float2* __restrict__ g_phi) {
+    int cell, j;
+    if (!lanes_item(ct, n_orb, cell, j)) return;
+    const int* gic = ct.gi + (size_t)cell * 64;
+    const int* ndc = ct.node + (size_t)cell * 64;
+    const int* outc = ct.out + (size_t)cell * 64;
+    const int* tyc = ct.type + (size_t)cell * 8;
+#pragma unroll 1
+    for (int arr = 0; arr < 2; ++arr) {
+        if (arr == 1 && !w_f) break;
+        const bool gather = arr == 0 && !g_phi;          // w from the full state
+        const float2* nat = arr == 0 ? g_phi : w_f;      // natural boundary layout
+        float2 x[8][8];                                  // [slot][reflection, then parity]
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            int gis[8], nds[8];
+            ld_int8(gic + s * 8, gis);
+            if (gather) ld_int8(ndc + s * 8, nds);
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                float2 v = make_float2(0.f, 0.f);
+                if (gis[g] >= 0) v = gather ? w_phi[(long long)j * nvox + nds[g]] : nat[(size_t)gis[g] * n_orb + j];
+                x[s][g] = v;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 8; ++s) wht8_regs(x[s]);
+        float2* hat = arr == 0 ? hat_phi : hat_f;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const float* cf = ct.coef_f + (size_t)__ldg(tyc + p) * 64;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int jj = __ldg(outc + o * 8 + p);
+                if (jj < 0) continue;
+                float c[8];
+                ld_float8(cf + o * 8, c);
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    a.x += c[q] * x[q][p].x;
+                    a.y += c[q] * x[q][p].y;
+                }
+                hat[(size_t)jj * n_orb + j] = a;
+            }
+        }
+    }
+}
+
+// Back transform of an order-1 stage (bnd_back_multi's formula, node-major inputs):
+// x = s1 f_hat + (-i a)(phi_hat - t) at the cell's outputs, a = a_coef c, t the sum of
+// the nsplit arrays t_in + q split_stride; mixed back per parity and transformed back
+// per slot; out[e][j] = y_f[e][j] + cdt v at each Gamma index e the cell writes (y_f and
+// out natural; out may be y_f: each element is read and written by one lane).
+// The 64 values of a lane pass through its own column of shared memory (LANES_SMEM
+// bytes per block, [warp][output o * 8 + parity p][lane]): first x at every output (all
+// loads independent of each other, so many are in flight), then the per-parity mixing
+// in place (v[s][p] over x[.][p]), then per slot the butterflies and the writes.
+constexpr size_t LANES_SMEM = (size_t)LANES_W * 64 * 32 * sizeof(float2);
+__global__ void __launch_bounds__(32 * LANES_W, 3) bnd_back_lanes(CellTab<float> ct, int n_orb, float s1, float a_coef,
+                                                                  const float2* __restrict__ hat_phi,
+                                                                  const float2* __restrict__ hat_f,
+                                                                  const float2* __restrict__ t_in, int nsplit,
+                                                                  long long split_stride, const float2* y_f,
+                                                                  float2* out, float cdt) {
+    extern __shared__ float2 lsm[];
+    int cell, j;
+    if (!lanes_item(ct, n_orb, cell, j)) return;
+    const int lane = threadIdx.x & 31;
+    float2* xs = lsm + (size_t)(threadIdx.x >> 5) * 64 * 32 + lane;   // this lane's column, stride 32
+    const int* outc = ct.out + (size_t)cell * 64;
+    const int* tyc = ct.type + (size_t)cell * 8;
+    const int* wrc = ct.wr + (size_t)cell * 64;
+    const float a = a_coef * (float)__ldg(ct.cell_c + cell);
+#pragma unroll 16
+    for (int t = 0; t < 64; ++t) {                       // t = o * 8 + p
+        const int jj = __ldg(outc + t);
+        float2 x = make_float2(0.f, 0.f);
+        if (jj >= 0) {
+            const size_t e = (size_t)jj * n_orb + j;
+            const float2 fv = hat_f[e], pv = hat_phi[e];
+            float2 tv = t_in[e];
+            for (int q = 1; q < nsplit; ++q) {
+                const float2 u = t_in[(long long)q * split_stride + e];
+                tv.x += u.x;
+                tv.y += u.y;
+            }
+            const float dr = pv.x - tv.x, di = pv.y - tv.y;
+            x = make_float2(s1 * fv.x + a * di, s1 * fv.y - a * dr);
+        }
+        xs[t * 32] = x;
+    }
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        float2 x[8];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) x[o] = xs[(o * 8 + p) * 32];
+        const float* cb = ct.coef_bt + (size_t)__ldg(tyc + p) * 64;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            float c[8];
+            ld_float8(cb + s * 8, c);
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                acc.x += c[q] * x[q].x;
+                acc.y += c[q] * x[q].y;
+            }
+            xs[(s * 8 + p) * 32] = acc;                  // v[s][p] over x[s][p] (column p read above)
+        }
+    }
+#pragma unroll 2
+    for (int s = 0; s < 8; ++s) {
+        int wr[8];
+        ld_int8(wrc + s * 8, wr);
+        float2 y[8], v[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) y[g] = wr[g] >= 0 ? y_f[(size_t)wr[g] * n_orb + j] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) v[p] = xs[(s * 8 + p) * 32];
+        wht8_regs(v);
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            if (wr[g] >= 0) out[(size_t)wr[g] * n_orb + j] = make_float2(y[g].x + cdt * v[g].x, y[g].y + cdt * v[g].y);
+    }
+}
+
+// tc_colexp for a node-major x ((moff + row) * n_orb + o): one block per (class member,
+// 32 consecutive orbitals), lane = orbital, the 32 warps taking every 32nd row with 16
+// loads in flight each; the same exponents as tc_colexp.  Grid tc_ncols * n_orb / 32
+// blocks of 1024 threads.
+constexpr int CX_WARPS = 32, CX_DEPTH = 16;
+static __global__ void __launch_bounds__(32 * CX_WARPS) tc_colexp_nm(TcInfo info, int n_orb, const float2* __restrict__ x,
+                                                                   int* __restrict__ colexp) {
+    __shared__ uint32_t red[CX_WARPS][32];
+    const int nog = n_orb >> 5;
+    const int rm = blockIdx.x / nog, og = blockIdx.x - rm * nog;      // class member (rsum index), orbital group
+    int c = 0;
+    while (c + 1 < info.ncls && rm >= info.rsum[c + 1]) ++c;
+    const int k = rm - info.rsum[c], m = info.m[c];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int o = og * 32 + lane;
+    const float2* p = x + (size_t)info.moff[c][k] * n_orb + o;
+    uint32_t mx = 0;
+    for (int r0 = w; r0 < m; r0 += CX_WARPS * CX_DEPTH) {
+        float2 v[CX_DEPTH];
+#pragma unroll
+        for (int u = 0; u < CX_DEPTH; ++u) {
+            const int r = r0 + CX_WARPS * u;
+            v[u] = r < m ? __ldg(p + (size_t)r * n_orb) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < CX_DEPTH; ++u)
+            mx = max(mx, max(__float_as_uint(v[u].x) & 0x7fffffffu, __float_as_uint(v[u].y) & 0x7fffffffu));
+    }
+    red[w][lane] = mx;
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 1; q < CX_WARPS; ++q) mx = max(mx, red[q][lane]);
+        int e = 0;
+        if (mx != 0) {
+            const int E = (int)(mx >> 23) - 127;
+            e = min(TC_COLEXP_MAX, max(-TC_COLEXP_MAX, TC_TARGET_EXP - 1 - E));
+        }
+        colexp[rm * n_orb + o] = e;
+    }
+}
+
+}  // namespace dev
+}  // namespace abc

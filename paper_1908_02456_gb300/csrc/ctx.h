@@ -91,6 +91,8 @@ struct abc_ctx {
     int back_multi = 0;              // order-1 back transform: 0 one orbital per cell group, 1 four, 2 two (tuning)
     bool fwd_rw = false;             // four-orbital forward transform with the reflection transform in registers
     bool gam_mode = false;           // stencils write the next stage's w on Gamma for the forward transform (tuning)
+    bool lanes = false;              // order-1 tensor-core chain with node-major adapted vectors (tuning)
+    bool lanes_attr = false;         // bnd_back_lanes's shared-memory size set
     abc::DevBuf gam[2];              // that Gamma copy, [n_gamma][max_orbitals], one per stage parity
     int tc_sms_all = 0;              // SMs of the device
     abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
@@ -146,6 +148,11 @@ inline dev::CellTab<T> cell_tab(const abc_ctx* c) {
 // Blocks (of 128 threads) of the boundary transforms for n_orb orbitals.
 inline unsigned cell_blocks(const abc_ctx* c, int n_orb) {
     return (unsigned)(((long long)c->geo.n_cells * n_orb + 1) / 2);
+}
+// Blocks of the lane-per-orbital transforms (one warp per cell and 32 orbitals, four
+// warps per block; n_orb a multiple of 32).
+inline unsigned lanes_blocks(const abc_ctx* c, int n_orb) {
+    return (unsigned)(((long long)c->geo.n_cells * (n_orb / 32) + 3) / 4);
 }
 }  // namespace abc
 

@@ -200,12 +200,13 @@ struct TcItem {
 // image the GEMM copies with one bulk copy per K block: hi planes (-Xi, Xr, Xi), then
 // lo planes in the same order (conj: (Xr, Xi, -Xr)).  Grid (column ranges, largest
 // nkb / TC_PACK_KB), 128 threads, TC_PACK_KB consecutive K blocks per block; x
-// orbital-major (o * ng + j).  TC_F16: FP16 hi + lo of the
-// column scaled by 2^colexp[column], 8 elements per 16-byte core-matrix row.
+// orbital-major (o * ng + j), or node-major (j * n_orb + o) when nm is set.  TC_F16:
+// FP16 hi + lo of the column scaled by 2^colexp[column], 8 elements per 16-byte
+// core-matrix row.
 template <int KIND, int KARA = 0>
 __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCols* __restrict__ cols, int n_orb, int ng,
                                                  const float2* __restrict__ x, int conj, float* __restrict__ bpack,
-                                                 const int* __restrict__ colexp) {
+                                                 const int* __restrict__ colexp, int nm = 0) {
     constexpr int EPR = 16 / TcKind<KIND>::EB;          // elements per 16-byte row
     const TcCols cr = cols[blockIdx.x];
     const int c = cr.cls;
@@ -226,7 +227,8 @@ __global__ void __launch_bounds__(128) pack_x_tc(TcInfo info, const TcCols* __re
         for (int e = 0; e < EPR; ++e) {
             const int row = kb * TcKind<KIND>::KB + EPR * q + e;
             float2 v = make_float2(0.f, 0.f);
-            if (k < info.R[c] && row < m) v = __ldg(x + (size_t)o * ng + info.moff[c][k] + row);
+            if (k < info.R[c] && row < m)
+                v = __ldg(nm ? x + (size_t)(info.moff[c][k] + row) * n_orb + o : x + (size_t)o * ng + info.moff[c][k] + row);
             re[e] = v.x * sc;
             im[e] = v.y * sc;
         }
@@ -354,14 +356,16 @@ static __global__ void __launch_bounds__(256) tc_colexp(TcInfo info, int n_orb, 
 }
 
 // One CTA per SM over the items item_off[blockIdx.x] .. item_off[blockIdx.x + 1] of
-// items[]; out + split * split_stride receives each item's (split's) partial product
-// (x, out orbital-major).
+// items[]; out + split * split_stride receives each item's (split's) partial product,
+// orbital-major (o * ng + j), or node-major (j * n_orb + o) when nm is set (n_orb a
+// multiple of 16: each 16-column group of a tile is then 16 consecutive orbitals of one
+// right-hand side, stored as 128 contiguous bytes).
 template <int KIND, typename CFG>
 __global__ void __launch_bounds__(TC_THREADS, CFG::cps)
 gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict__ items,
         const int* __restrict__ item_off, const float* __restrict__ apack, const float* __restrict__ bpack, int n_orb,
         int ng, int nsplit, long long split_stride, float2* __restrict__ out, int conj, int* __restrict__ err,
-        const int* __restrict__ colexp) {
+        const int* __restrict__ colexp, int nm = 0) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char* sA = tc_smem;                                       // [stage][4 or 6 planes]
     constexpr int TC_STAGES = CFG::stages;
@@ -521,7 +525,26 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
                         tc_wait_ld();
                     }
                 }
-                if (row < m) {
+                if (row < m && nm) {
+                    const int col = tile.col0 + c0;
+                    const int k = col / n_orb, o = col - k * n_orb;
+                    if (c0 < N && k < info.R[c]) {
+                        float4* d4 = reinterpret_cast<float4*>(dst + (size_t)(info.moff[c][k] + row) * n_orb + o);
+#pragma unroll
+                        for (int i = 0; i < 16; i += 2) {
+                            float2 v0 = any ? make_float2(pr[i], pi[i]) : make_float2(0.f, 0.f);
+                            float2 v1 = any ? make_float2(pr[i + 1], pi[i + 1]) : make_float2(0.f, 0.f);
+                            if constexpr (KIND == TC_F16) {      // as below, element by element
+                                const float sc = tc_exp2i(-info.es[c]);
+                                const float s0 = tc_exp2i(-colexp[info.rsum[c] * n_orb + col + i]);
+                                const float s1 = tc_exp2i(-colexp[info.rsum[c] * n_orb + col + i + 1]);
+                                v0 = make_float2(v0.x * sc * s0, v0.y * sc * s0);
+                                v1 = make_float2(v1.x * sc * s1, v1.y * sc * s1);
+                            }
+                            d4[i >> 1] = make_float4(v0.x, v0.y, v1.x, v1.y);
+                        }
+                    }
+                } else if (row < m) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const int col = tile.col0 + c0 + i;

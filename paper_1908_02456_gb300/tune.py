@@ -12,10 +12,12 @@ precision and the device, so the library exposes its choices as tuning knobs
   beside the boundary chain (``TUNE_STENCIL``), how many planes each of its threads
   marches through (``TUNE_STENCIL_KZ``) and whether its planes are staged in shared
   memory by bulk copies (``TUNE_STENCIL_STAGED``);
-* the order-1 back transform one or four orbitals per cell group (``TUNE_BACK_MULTI``),
-  the four-orbital forward transform's reflection transform across lanes or in
-  registers (``TUNE_FORWARD_RW``) and whether it reads w on Gamma from the copy the
-  previous stage's stencil wrote (``TUNE_GAMMA_COPY``);
+* the order-1 back transform one, two or four orbitals per cell group
+  (``TUNE_BACK_MULTI``), the four-orbital forward transform's reflection transform
+  across lanes or in registers (``TUNE_FORWARD_RW``), whether it reads w on Gamma from
+  the copy the previous stage's stencil wrote (``TUNE_GAMMA_COPY``), and, on the
+  tensor-core path with a multiple of 32 orbitals, the node-major chain with both
+  transforms one warp per cell and 32 orbitals (``TUNE_LANES``);
 * for one complex64 orbital, the early start of the tiled contraction behind the
   forward transform (``TUNE_PDL``).
 
@@ -78,10 +80,17 @@ def knob_groups(ctx: abc.Context, n_orb: int):
     if ctx.order == 1 and ctx.fit1 == abc.FIT1_LIMIT and n_orb >= 2 and n_orb % 2 == 0:
         groups.append([{abc.TUNE_BACK_MULTI: m} for m in ((0, 1, 2) if n_orb % 4 == 0 else (0, 2))])
     if n_orb >= 4 and n_orb % 4 == 0 and ctx.order < 2:
+        lanes = tc and ctx.order == 1 and n_orb % 32 == 0
+        ln = {abc.TUNE_LANES: 0} if lanes else {}
         if ctx.precision != abc.FP64 and ctx.radius == 1 and ctx.shape[0] % 2 == 0:
-            groups.append([{abc.TUNE_FORWARD_RW: rw, abc.TUNE_GAMMA_COPY: gc} for gc in (0, 1) for rw in (0, 1)])
+            fwd = [{abc.TUNE_FORWARD_RW: rw, abc.TUNE_GAMMA_COPY: gc, **ln} for gc in (0, 1) for rw in (0, 1)]
+            if lanes:
+                fwd += [{abc.TUNE_FORWARD_RW: 0, abc.TUNE_GAMMA_COPY: gc, abc.TUNE_LANES: 1} for gc in (0, 1)]
         else:
-            groups.append([{abc.TUNE_FORWARD_RW: 0}, {abc.TUNE_FORWARD_RW: 1}])
+            fwd = [{abc.TUNE_FORWARD_RW: 0, **ln}, {abc.TUNE_FORWARD_RW: 1, **ln}]
+            if lanes:
+                fwd.append({abc.TUNE_FORWARD_RW: 0, abc.TUNE_LANES: 1})
+        groups.append(fwd)
     if n_orb == 1 and ctx.precision != abc.FP64 and ctx.get_tuning(abc.TUNE_TILE_COUNT) > 0:
         groups.append([{abc.TUNE_PDL: 1}, {abc.TUNE_PDL: 0}])
     return groups
@@ -158,5 +167,5 @@ def describe(setting: dict) -> dict:
              abc.TUNE_STENCIL_KZ: "stencil_form(0=pair per thread, 1=capped registers, k>1=k planes)",
              abc.TUNE_BACK_MULTI: "back_transform_orbitals_per_group(0=1, 1=4, 2=2)", abc.TUNE_FORWARD_RW: "forward_transform_in_registers",
              abc.TUNE_GAMMA_COPY: "forward_reads_gamma_copy", abc.TUNE_STENCIL_STAGED: "stencil_planes_staged_by_bulk_copies",
-             abc.TUNE_PDL: "pdl"}
+             abc.TUNE_LANES: "node_major_chain_warp_per_cell", abc.TUNE_PDL: "pdl"}
     return {names.get(int(k), str(k)): v for k, v in setting.items()}
