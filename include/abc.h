@@ -394,9 +394,12 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           the forward and back transforms one warp per cell and 32
  *                           orbitals, lane = orbital, the cell's transform in registers;
  *                           every access of a warp is then 256 contiguous bytes (except
- *                           the gather of w at Gamma from the state).  Bit-identical
- *                           results; takes precedence over ABC_TUNE_FORWARD_RW and
- *                           ABC_TUNE_BACK_MULTI.  0 (default) orbital-major.
+ *                           the gather of w at Gamma from the state).  With one K split
+ *                           the GEMM epilogue also forms the back transform's input
+ *                           x = s1 f_hat + (-i a)(phi_hat - t), so the back transform
+ *                           reads one array.  Bit-identical results; takes precedence over
+ *                           ABC_TUNE_FORWARD_RW and ABC_TUNE_BACK_MULTI.  0 (default)
+ *                           orbital-major.
  *   ABC_TUNE_GEMM_TILE      tensor-core forms, n_orb >= 2: 0 (default) output tiles of up
  *                           to 96 columns, three ring stages, one CTA per SM; 1: up to 64
  *                           columns, two stages, two CTAs per SM; 2: the complex products

@@ -749,6 +749,7 @@ int check_device_flag(abc_ctx* c, cudaStream_t s) {
 // cores), or plain t (nsplit = 1).
 struct TRes {
     bool gathered = false;
+    bool xform = false;        // t holds the order-1 back transform's x (XEpi), node-major
     const void* t = nullptr;
     int nsplit = 1;
     long long stride = 0;
@@ -757,30 +758,30 @@ struct TRes {
 // The persistent tensor-core GEMM in the context's tile configuration.
 template <int KIND>
 void launch_gemm_tc(abc_ctx* c, const abc_ctx::TcPlan& pl, int n_orb, float2* out, int conj, const int* colexp,
-                    cudaStream_t s, int nm = 0) {
+                    cudaStream_t s, int nm = 0, dev::XEpi xe = dev::XEpi{}) {
     const long long n = c->geo.n_gamma;
     if (c->tc_cfg == 2)
         dev::gemm_tc<KIND, dev::TcKara><<<(unsigned)pl.grid, dev::TC_THREADS, dev::TcKara::smem, s>>>(
             c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
             c->tc_apack_k.as<float>(), c->tc_bpack.as<float>(), n_orb, (int)n, pl.nsplit, n * n_orb, out, conj,
-            c->err_flag.as<int>(), colexp, nm);
+            c->err_flag.as<int>(), colexp, nm, xe);
     else if (c->tc_cfg == 0)
         dev::gemm_tc<KIND, dev::TcWide><<<(unsigned)pl.grid, dev::TC_THREADS, dev::TcWide::smem, s>>>(
             c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
             c->tc_apack.as<float>(), c->tc_bpack.as<float>(), n_orb, (int)n, pl.nsplit, n * n_orb, out, conj,
-            c->err_flag.as<int>(), colexp, nm);
+            c->err_flag.as<int>(), colexp, nm, xe);
     else
         dev::gemm_tc<KIND, dev::TcNarrow><<<(unsigned)pl.grid, dev::TC_THREADS, dev::TcNarrow::smem, s>>>(
             c->tci, c->tc_tiles.as<dev::TcTile>(), c->tc_items.as<dev::TcItem>(), c->tc_item_off.as<int>() + pl.off_base,
             c->tc_apack.as<float>(), c->tc_bpack.as<float>(), n_orb, (int)n, pl.nsplit, n * n_orb, out, conj,
-            c->err_flag.as<int>(), colexp, nm);
+            c->err_flag.as<int>(), colexp, nm, xe);
 }
 
 // The boundary contraction t = S x (conj: conj(S) x).  nm: x and t node-major
 // (tensor-core path, n_orb a multiple of 32).
 template <typename T>
 TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaStream_t s,
-                 const void* const* x4 = nullptr, bool nm = false) {
+                 const void* const* x4 = nullptr, bool nm = false, const dev::XEpi* xe = nullptr) {
     typedef typename dev::C2<T>::t V;
     dev::XSeg<V> xs{{(const V*)x, nullptr, nullptr, nullptr}};
     if (x4)
@@ -808,6 +809,9 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
         const dim3 pgrid((unsigned)pl.cols_cnt, (unsigned)((pl.max_nkb + dev::TC_PACK_KB - 1) / dev::TC_PACK_KB));
         float2* out = pl.nsplit > 1 ? c->tc_part.as<float2>() : (float2*)t;
         const int* colexp = c->tc_colexp.as<int>();
+        // the epilogue forms the back transform's x when the whole sum is in one item
+        const dev::XEpi xep = nm && xe && pl.nsplit == 1 ? *xe : dev::XEpi{};
+        res.xform = xep.ac != nullptr;
         if (c->tc_f16) {
             const int ncols = c->tc_ncols * n_orb;
             if (nm)
@@ -826,7 +830,7 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
                                                                    c->tc_bpack.as<float>(), colexp, (int)nm);
             prof_end(c, ABC_KERNEL_PACK, s);
             prof_begin(c, ABC_KERNEL_CONTRACTION, s);
-            launch_gemm_tc<dev::TC_F16>(c, pl, n_orb, out, conj, colexp, s, (int)nm);
+            launch_gemm_tc<dev::TC_F16>(c, pl, n_orb, out, conj, colexp, s, (int)nm, xep);
             c->launches += 2;
         } else {
             if (c->tc_cfg == 2)
@@ -839,7 +843,7 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
                                                                     c->tc_bpack.as<float>(), colexp, (int)nm);
             prof_end(c, ABC_KERNEL_PACK, s);
             prof_begin(c, ABC_KERNEL_CONTRACTION, s);
-            launch_gemm_tc<dev::TC_TF32>(c, pl, n_orb, out, conj, colexp, s, (int)nm);
+            launch_gemm_tc<dev::TC_TF32>(c, pl, n_orb, out, conj, colexp, s, (int)nm, xep);
             c->launches += 1;
         }
         res.t = out;
@@ -882,6 +886,11 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
         }
     }
     if constexpr (sizeof(T) == 4 && MODE == 0) {
+        if (nm && tr.xform) {                // x formed by the contraction epilogue
+            dev::bnd_back_lanes_x<<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, dev::LANES_SMEM, s>>>(
+                ct, n_orb, (const Vc*)tr.t, (const Vc*)y_f, (Vc*)out, cdt);
+            return;
+        }
         if (nm) {                            // node-major adapted vectors and t (lanes_ok)
             dev::bnd_back_lanes<<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, dev::LANES_SMEM, s>>>(
                 ct, n_orb, s1, a_coef, hp, hf, (const Vc*)tr.t, tr.nsplit, tr.stride, (const Vc*)y_f, (Vc*)out, cdt);
@@ -1090,7 +1099,9 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
         join();
         return;
     }
-    const TRes gathered = contraction<T>(c, order == 1 ? hf : hp, c->tvec.p, n_orb, 0, s, nullptr, nm);
+    const dev::XEpi xe{(const float2*)hf, (const float2*)hp, c->lanes_ac.as<float>(), (float)c->blocks.s};
+    const TRes gathered = contraction<T>(c, order == 1 ? hf : hp, c->tvec.p, n_orb, 0, s, nullptr, nm,
+                                         nm && order == 1 ? &xe : nullptr);
     if (order == 1) {
         stencil_at(0);
         back<T, 0>(c, gathered, n_orb, (T)c->blocks.s, a_coef, y_f, o_f, nullptr, cdt, s, hp, hf, fn, nm);
@@ -2029,6 +2040,21 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         if (ctx->lanes && !ctx->lanes_attr) {
             CUDA_TRY(cudaFuncSetAttribute(abc::dev::bnd_back_lanes, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)abc::dev::LANES_SMEM));
+            CUDA_TRY(cudaFuncSetAttribute(abc::dev::bnd_back_lanes_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)abc::dev::LANES_SMEM));
+            // a_coef c per adapted index for the contraction epilogue's x (the back
+            // transform's a = a_coef * c, in the same float arithmetic)
+            const Geometry& g = ctx->geo;
+            const float af = (float)(1.0 / (4.0 * g.h * g.h * g.h * g.h));
+            std::vector<float> ac((size_t)g.n_gamma, 0.f);
+            for (int cell = 0; cell < g.n_cells; ++cell)
+                for (int t = 0; t < 64; ++t) {
+                    const int jj = g.cell_out[(size_t)cell * 64 + t];
+                    if (jj >= 0) ac[(size_t)jj] = af * (float)g.cell_c[cell];
+                }
+            int st;
+            if ((st = ctx->lanes_ac.alloc(ac.size() * sizeof(float)))) return st;
+            CUDA_TRY(cudaMemcpy(ctx->lanes_ac.p, ac.data(), ac.size() * sizeof(float), cudaMemcpyHostToDevice));
             ctx->lanes_attr = true;
         }
         return ABC_OK;

@@ -128,7 +128,9 @@ __global__ void __launch_bounds__(32 * LANES_W, 3) bnd_forward_lanes(CellTab<flo
 // x = s1 f_hat + (-i a)(phi_hat - t) at the cell's outputs, a = a_coef c, t the sum of
 // the nsplit arrays t_in + q split_stride; mixed back per parity and transformed back
 // per slot; out[e][j] = y_f[e][j] + cdt v at each Gamma index e the cell writes (y_f and
-// out natural; out may be y_f: each element is read and written by one lane).
+// out natural; out may be y_f: each element is read, then written, by one lane and by
+// no other thread, so y_f is read through the read-only path, which leaves the compiler
+// free to issue the next loads before the earlier stores).
 // The 64 values of a lane pass through its own column of shared memory (LANES_SMEM
 // bytes per block, [warp][output o * 8 + parity p][lane]): first x at every output (all
 // loads independent of each other, so many are in flight), then the per-parity mixing
@@ -162,8 +164,7 @@ __global__ void __launch_bounds__(32 * LANES_W, 3) bnd_back_lanes(CellTab<float>
                 tv.x += u.x;
                 tv.y += u.y;
             }
-            const float dr = pv.x - tv.x, di = pv.y - tv.y;
-            x = make_float2(s1 * fv.x + a * di, s1 * fv.y - a * dr);
+            x = back_x1(s1, a, fv, pv, tv);
         }
         xs[t * 32] = x;
     }
@@ -192,7 +193,73 @@ __global__ void __launch_bounds__(32 * LANES_W, 3) bnd_back_lanes(CellTab<float>
         ld_int8(wrc + s * 8, wr);
         float2 y[8], v[8];
 #pragma unroll
-        for (int g = 0; g < 8; ++g) y[g] = wr[g] >= 0 ? y_f[(size_t)wr[g] * n_orb + j] : make_float2(0.f, 0.f);
+        for (int g = 0; g < 8; ++g) y[g] = wr[g] >= 0 ? __ldg(y_f + (size_t)wr[g] * n_orb + j) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) v[p] = xs[(s * 8 + p) * 32];
+        wht8_regs(v);
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            if (wr[g] >= 0) out[(size_t)wr[g] * n_orb + j] = make_float2(y[g].x + cdt * v[g].x, y[g].y + cdt * v[g].y);
+    }
+}
+
+// Back transform from x formed by the contraction epilogue (XEpi; node-major): a lane
+// loads the cell's 64 values of x in one round into registers and mixes them back per
+// parity in place; the results go to the lane's shared-memory column (LANES_SMEM bytes
+// per block), which frees the registers for all y_f loads of the cell at once; then per
+// slot the butterflies and out[e][j] = y_f[e][j] + cdt v (the same bits as
+// bnd_back_lanes; y_f through the read-only path, as there).
+__global__ void __launch_bounds__(32 * LANES_W, 3) bnd_back_lanes_x(CellTab<float> ct, int n_orb,
+                                                                    const float2* __restrict__ x_in,
+                                                                    const float2* y_f, float2* out, float cdt) {
+    extern __shared__ float2 lsm[];
+    int cell, j;
+    if (!lanes_item(ct, n_orb, cell, j)) return;
+    float2* xs = lsm + (size_t)(threadIdx.x >> 5) * 64 * 32 + (threadIdx.x & 31);
+    const int* outc = ct.out + (size_t)cell * 64;
+    const int* tyc = ct.type + (size_t)cell * 8;
+    const int* wrc = ct.wr + (size_t)cell * 64;
+    {
+        float2 v[8][8];                                  // x[o][p], then v[s][p]
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            int jj[8];
+            ld_int8(outc + o * 8, jj);
+#pragma unroll
+            for (int p = 0; p < 8; ++p) v[o][p] = jj[p] >= 0 ? x_in[(size_t)jj[p] * n_orb + j] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            float2 x[8];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) x[o] = v[o][p];
+            const float* cb = ct.coef_bt + (size_t)__ldg(tyc + p) * 64;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                float c[8];
+                ld_float8(cb + s * 8, c);
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    acc.x += c[q] * x[q].x;
+                    acc.y += c[q] * x[q].y;
+                }
+                v[s][p] = acc;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+#pragma unroll
+            for (int p = 0; p < 8; ++p) xs[(s * 8 + p) * 32] = v[s][p];
+    }
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        int wr[8];
+        ld_int8(wrc + s * 8, wr);
+        float2 y[8], v[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) y[g] = wr[g] >= 0 ? __ldg(y_f + (size_t)wr[g] * n_orb + j) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int p = 0; p < 8; ++p) v[p] = xs[(s * 8 + p) * 32];
         wht8_regs(v);

@@ -92,7 +92,8 @@ struct abc_ctx {
     bool fwd_rw = false;             // four-orbital forward transform with the reflection transform in registers
     bool gam_mode = false;           // stencils write the next stage's w on Gamma for the forward transform (tuning)
     bool lanes = false;              // order-1 tensor-core chain with node-major adapted vectors (tuning)
-    bool lanes_attr = false;         // bnd_back_lanes's shared-memory size set
+    bool lanes_attr = false;         // bnd_back_lanes's shared-memory size set, lanes_ac filled
+    abc::DevBuf lanes_ac;            // [n_gamma] a_coef * c per adapted index (node-major chain)
     abc::DevBuf gam[2];              // that Gamma copy, [n_gamma][max_orbitals], one per stage parity
     int tc_sms_all = 0;              // SMs of the device
     abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;

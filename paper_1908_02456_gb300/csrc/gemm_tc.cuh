@@ -360,12 +360,21 @@ static __global__ void __launch_bounds__(256) tc_colexp(TcInfo info, int n_orb, 
 // orbital-major (o * ng + j), or node-major (j * n_orb + o) when nm is set (n_orb a
 // multiple of 16: each 16-column group of a tile is then 16 consecutive orbitals of one
 // right-hand side, stored as 128 contiguous bytes).
+// Order-1 back-transform input (xe.ac set; node-major, one split): instead of t the
+// epilogue stores x = s1 f_hat + (-i a)(phi_hat - t) (back_x1), a = xe.ac[j] per adapted
+// index, f_hat and phi_hat node-major.
+struct XEpi {
+    const float2* hf;
+    const float2* hp;
+    const float* ac;
+    float s1;
+};
 template <int KIND, typename CFG>
 __global__ void __launch_bounds__(TC_THREADS, CFG::cps)
 gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict__ items,
         const int* __restrict__ item_off, const float* __restrict__ apack, const float* __restrict__ bpack, int n_orb,
         int ng, int nsplit, long long split_stride, float2* __restrict__ out, int conj, int* __restrict__ err,
-        const int* __restrict__ colexp, int nm = 0) {
+        const int* __restrict__ colexp, int nm = 0, XEpi xe = XEpi{}) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char* sA = tc_smem;                                       // [stage][4 or 6 planes]
     constexpr int TC_STAGES = CFG::stages;
@@ -508,6 +517,21 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
             float2* dst = out + (size_t)w.split * split_stride;
             for (int c0 = 0; c0 < N; c0 += 16) {
                 float pr[16], pi[16];
+                // x form: this row's f_hat and phi_hat over the 16 columns, loaded before
+                // the accumulator is read
+                float4 fh[8], ph[8];
+                float ar = 0.f;
+                const int colx = tile.col0 + c0, kx = colx / n_orb;
+                const bool xrow = xe.ac && row < m && c0 < N && kx < info.R[c];
+                if (xrow) {
+                    const size_t rb = (size_t)(info.moff[c][kx] + row) * n_orb + (colx - kx * n_orb);
+                    ar = __ldg(xe.ac + info.moff[c][kx] + row);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        fh[i] = __ldg(reinterpret_cast<const float4*>(xe.hf + rb) + i);
+                        ph[i] = __ldg(reinterpret_cast<const float4*>(xe.hp + rb) + i);
+                    }
+                }
                 if (any) {
                     tc_ld16(lane_base + buf * CFG::buf_cols + c0, pr);
                     tc_ld16(lane_base + buf * CFG::buf_cols + N + c0, pi);
@@ -540,6 +564,11 @@ gemm_tc(TcInfo info, const TcTile* __restrict__ tiles, const TcItem* __restrict_
                                 const float s1 = tc_exp2i(-colexp[info.rsum[c] * n_orb + col + i + 1]);
                                 v0 = make_float2(v0.x * sc * s0, v0.y * sc * s0);
                                 v1 = make_float2(v1.x * sc * s1, v1.y * sc * s1);
+                            }
+                            if (xrow) {
+                                const float4 f4 = fh[i >> 1], p4 = ph[i >> 1];
+                                v0 = back_x1(xe.s1, ar, make_float2(f4.x, f4.y), make_float2(p4.x, p4.y), v0);
+                                v1 = back_x1(xe.s1, ar, make_float2(f4.z, f4.w), make_float2(p4.z, p4.w), v1);
                             }
                             d4[i >> 1] = make_float4(v0.x, v0.y, v1.x, v1.y);
                         }

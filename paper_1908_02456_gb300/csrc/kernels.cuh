@@ -23,6 +23,19 @@ template <typename T> __device__ __forceinline__ typename C2<T>::t mk(T re, T im
     typename C2<T>::t v; v.x = re; v.y = im; return v;
 }
 
+// The adapted input of an order-1 back transform, x = s1 f + (-i a)(p - t), with one
+// fixed rounding order (every form of the back transform and the contraction epilogue
+// that can form it give the same bits): re = fma(s1, f.re, a di), im = fma(s1, f.im,
+// -(a dr)), d = p - t.
+__device__ __forceinline__ float2 back_x1(float s1, float a, float2 f, float2 p, float2 t) {
+    const float dr = __fsub_rn(p.x, t.x), di = __fsub_rn(p.y, t.y);
+    return make_float2(__fmaf_rn(s1, f.x, __fmul_rn(a, di)), __fmaf_rn(s1, f.y, -__fmul_rn(a, dr)));
+}
+__device__ __forceinline__ double2 back_x1(double s1, double a, double2 f, double2 p, double2 t) {
+    const double dr = __dsub_rn(p.x, t.x), di = __dsub_rn(p.y, t.y);
+    return make_double2(__fma_rn(s1, f.x, __dmul_rn(a, di)), __fma_rn(s1, f.y, -__dmul_rn(a, dr)));
+}
+
 // Block structure of the symmetry-adapted boundary matrices (kernel parameter).
 // Entry e is one right-hand side of one irreducible class: the class's matrix
 // (m x m at mat_off, row stride ld) maps adapted indices [off, off + m) to the same
@@ -625,9 +638,7 @@ __global__ void __launch_bounds__(128) bnd_back(CellTab<T> ct, int n_orb, T s1, 
             }
         }
         if (MODE == 0) {
-            const T a = a_coef * c_cell;
-            const T dr = pv.x - tv.x, di = pv.y - tv.y;
-            x = mk<T>(s1 * fv.x + a * di, s1 * fv.y - a * dr);
+            x = back_x1(s1, a_coef * c_cell, fv, pv, tv);
         } else if (MODE == 1 || MODE == 3 || MODE == 4) {
             x = tv;
         } else {
@@ -734,10 +745,7 @@ __global__ void __launch_bounds__(128) bnd_back_multi(CellTab<T> ct, int n_orb, 
             }
         const T a = a_coef * c_cell;
 #pragma unroll
-        for (int o = 0; o < FO; ++o) {
-            const T dr = pv[o].x - tv[o].x, di = pv[o].y - tv[o].y;
-            x[o] = mk<T>(s1 * fv[o].x + a * di, s1 * fv[o].y - a * dr);
-        }
+        for (int o = 0; o < FO; ++o) x[o] = back_x1(s1, a, fv[o], pv[o], tv[o]);
     }
 #pragma unroll
     for (int o = 0; o < FO; ++o) sx[grp][o][s][g] = x[o];
