@@ -397,9 +397,12 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           the gather of w at Gamma from the state).  With one K split
  *                           the GEMM epilogue also forms the back transform's input
  *                           x = s1 f_hat + (-i a)(phi_hat - t), so the back transform
- *                           reads one array.  Bit-identical results; takes precedence over
- *                           ABC_TUNE_FORWARD_RW and ABC_TUNE_BACK_MULTI.  0 (default)
- *                           orbital-major.
+ *                           reads one array.  2 and 3: the same chain with each cell split
+ *                           between two lanes (a warp per cell and 16 orbitals, half the
+ *                           values per lane, the halves exchanged by lane shuffles;
+ *                           registers capped for 4 or 5 blocks per SM).  Bit-identical
+ *                           results; takes precedence over ABC_TUNE_FORWARD_RW and
+ *                           ABC_TUNE_BACK_MULTI.  0 (default) orbital-major.
  *   ABC_TUNE_GEMM_TILE      tensor-core forms, n_orb >= 2: 0 (default) output tiles of up
  *                           to 96 columns, three ring stages, one CTA per SM; 1: up to 64
  *                           columns, two stages, two CTAs per SM; 2: the complex products

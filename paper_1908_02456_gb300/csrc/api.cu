@@ -886,13 +886,23 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
         }
     }
     if constexpr (sizeof(T) == 4 && MODE == 0) {
-        if (nm && tr.xform) {                // x formed by the contraction epilogue
+        if (nm && tr.xform && c->lanes >= 2) {   // x formed by the contraction epilogue
+            if (c->lanes == 3)
+                dev::bnd_back_pairs_x<5><<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
+                    ct, n_orb, (const Vc*)tr.t, (const Vc*)y_f, (Vc*)out, cdt);
+            else
+                dev::bnd_back_pairs_x<4><<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
+                    ct, n_orb, (const Vc*)tr.t, (const Vc*)y_f, (Vc*)out, cdt);
+            return;
+        }
+        if (nm && tr.xform) {
             dev::bnd_back_lanes_x<<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, dev::LANES_SMEM, s>>>(
                 ct, n_orb, (const Vc*)tr.t, (const Vc*)y_f, (Vc*)out, cdt);
             return;
         }
         if (nm) {                            // node-major adapted vectors and t (lanes_ok)
-            dev::bnd_back_lanes<<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, dev::LANES_SMEM, s>>>(
+            dev::bnd_back_lanes<<<(unsigned)(((long long)c->geo.n_cells * (n_orb / 32) + 3) / 4), 32 * dev::LANES_W,
+                                  dev::LANES_SMEM, s>>>(
                 ct, n_orb, s1, a_coef, hp, hf, (const Vc*)tr.t, tr.nsplit, tr.stride, (const Vc*)y_f, (Vc*)out, cdt);
             return;
         }
@@ -1070,6 +1080,14 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             dev::bnd_forward<T, 0, true><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
                                                              order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,
                                                              nullptr, (T)0, dev::Ord2Fwd<T>{});
+        else if (nm && c->lanes == 3)
+            dev::bnd_forward_pairs<5><<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
+                cell_tab<float>(c), n_orb, c->nvox, (const float2*)w_phi, (const float2*)w_f, (float2*)hp, (float2*)hf,
+                (const float2*)g_in);
+        else if (nm && c->lanes == 2)
+            dev::bnd_forward_pairs<4><<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
+                cell_tab<float>(c), n_orb, c->nvox, (const float2*)w_phi, (const float2*)w_f, (float2*)hp, (float2*)hf,
+                (const float2*)g_in);
         else if (nm)
             dev::bnd_forward_lanes<<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
                 cell_tab<float>(c), n_orb, c->nvox, (const float2*)w_phi, (const float2*)w_f, (float2*)hp, (float2*)hf,
@@ -2035,7 +2053,8 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         return ABC_OK;
     }
     if (key == ABC_TUNE_LANES) {
-        ctx->lanes = value != 0;
+        if (value < 0 || value > 3) return fail(ABC_ERR_ARG, "ABC_TUNE_LANES takes 0, 1, 2 or 3");
+        ctx->lanes = (int)value;
         drop_graphs(ctx);
         if (ctx->lanes && !ctx->lanes_attr) {
             CUDA_TRY(cudaFuncSetAttribute(abc::dev::bnd_back_lanes, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2101,7 +2120,7 @@ extern "C" int abc_get_tuning(const abc_ctx* ctx, int key, long long* value) {
     if (key == ABC_TUNE_BACK_MULTI) { *value = ctx->back_multi; return ABC_OK; }
     if (key == ABC_TUNE_FORWARD_RW) { *value = ctx->fwd_rw ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_GAMMA_COPY) { *value = ctx->gam_mode ? 1 : 0; return ABC_OK; }
-    if (key == ABC_TUNE_LANES) { *value = ctx->lanes ? 1 : 0; return ABC_OK; }
+    if (key == ABC_TUNE_LANES) { *value = ctx->lanes; return ABC_OK; }
     if (key == ABC_TUNE_STENCIL_STAGED) { *value = ctx->stencil_staged ? 1 : 0; return ABC_OK; }
     if (key == ABC_TUNE_GEMM_SPLIT) { *value = ctx->tc_split; return ABC_OK; }
     return fail(ABC_ERR_ARG, "unknown tuning key");

@@ -269,6 +269,170 @@ __global__ void __launch_bounds__(32 * LANES_W, 3) bnd_back_lanes_x(CellTab<floa
     }
 }
 
+// ---------------------------------------------------------------------------------
+// The same transforms with a cell split between two lanes (ABC_TUNE_LANES 2): a warp
+// takes one cell and 16 consecutive orbitals; lanes l and l + 16 share orbital l and
+// each holds half of the cell's 64 values, so a lane needs half the registers and twice
+// as many warps stay resident.  The halves swap 16 values through one lane shuffle each
+// between the reflection butterflies (per slot) and the mixing (per parity).  Every
+// access of a warp instruction is two runs of 16 orbitals (128 contiguous bytes each).
+// Same sums in the same order as the forms above.  MINB: blocks per SM the registers
+// are capped for (4: 128 registers; 5: 96, with a few spilled).
+// ---------------------------------------------------------------------------------
+
+__device__ __forceinline__ bool pairs_item(const CellTab<float>& ct, int n_orb, int& cell, int& j, int& h) {
+    const int nch = n_orb >> 4;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= (long long)ct.n_cells * nch) return false;
+    cell = (int)(wid / nch);
+    j = (int)(wid - (long long)cell * nch) * 16 + (threadIdx.x & 15);
+    h = (threadIdx.x >> 4) & 1;
+    return true;
+}
+
+__device__ __forceinline__ float2 shfl16(float2 v) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, 16), __shfl_xor_sync(0xffffffffu, v.y, 16));
+}
+
+// Forward (bnd_forward_lanes's outputs): half h loads and transforms slots 4h .. 4h + 3,
+// then mixes parities 4h .. 4h + 3 over all eight slots.  Grid ceil(n_cells * n_orb / 16
+// / LANES_W) blocks of 32 LANES_W threads.
+template <int MINB>
+__global__ void __launch_bounds__(32 * LANES_W, MINB) bnd_forward_pairs(CellTab<float> ct, int n_orb, long long nvox,
+                                                                  const float2* __restrict__ w_phi,
+                                                                  const float2* __restrict__ w_f,
+                                                                  float2* __restrict__ hat_phi,
+                                                                  float2* __restrict__ hat_f,
+                                                                  const float2* __restrict__ g_phi) {
+    int cell, j, h;
+    const bool live = pairs_item(ct, n_orb, cell, j, h);
+    if (!__any_sync(0xffffffffu, live)) return;      // whole warps only (the shuffles)
+    if (!live) return;
+    const int* gic = ct.gi + (size_t)cell * 64 + 32 * h;     // this half's slots
+    const int* ndc = ct.node + (size_t)cell * 64 + 32 * h;
+    const int* outc = ct.out + (size_t)cell * 64;
+    const int* tyc = ct.type + (size_t)cell * 8;
+#pragma unroll 1
+    for (int arr = 0; arr < 2; ++arr) {
+        if (arr == 1 && !w_f) break;
+        const bool gather = arr == 0 && !g_phi;
+        const float2* nat = arr == 0 ? g_phi : w_f;
+        float2 x[4][8];                                  // [slot 4h + s][reflection, then parity]
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            int gis[8], nds[8];
+            ld_int8(gic + s * 8, gis);
+            if (gather) ld_int8(ndc + s * 8, nds);
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                float2 v = make_float2(0.f, 0.f);
+                if (gis[g] >= 0) v = gather ? w_phi[(long long)j * nvox + nds[g]] : nat[(size_t)gis[g] * n_orb + j];
+                x[s][g] = v;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) wht8_regs(x[s]);
+        // y[S][q]: slot S (0..7), parity 4h + q; own slots from x, the partner's by shuffle
+        float2 y[8][4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 keep = h ? x[s][4 + q] : x[s][q];
+                const float2 got = shfl16(h ? x[s][q] : x[s][4 + q]);
+                y[s][q] = h ? got : keep;                // slots 0..3
+                y[4 + s][q] = h ? keep : got;            // slots 4..7
+            }
+        float2* hat = arr == 0 ? hat_phi : hat_f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int p = 4 * h + q;
+            const float* cf = ct.coef_f + (size_t)__ldg(tyc + p) * 64;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int jj = __ldg(outc + o * 8 + p);
+                if (jj < 0) continue;
+                float c[8];
+                ld_float8(cf + o * 8, c);
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int S = 0; S < 8; ++S) {
+                    a.x += c[S] * y[S][q].x;
+                    a.y += c[S] * y[S][q].y;
+                }
+                hat[(size_t)jj * n_orb + j] = a;
+            }
+        }
+    }
+}
+
+// Back from the epilogue's x (bnd_back_lanes_x's outputs): half h loads and mixes
+// parities 4h .. 4h + 3, then transforms back slots 4h .. 4h + 3 over all eight
+// parities and writes their nodes.
+template <int MINB>
+__global__ void __launch_bounds__(32 * LANES_W, MINB) bnd_back_pairs_x(CellTab<float> ct, int n_orb,
+                                                                 const float2* __restrict__ x_in, const float2* y_f,
+                                                                 float2* out, float cdt) {
+    int cell, j, h;
+    const bool live = pairs_item(ct, n_orb, cell, j, h);
+    if (!__any_sync(0xffffffffu, live)) return;
+    if (!live) return;
+    const int* outc = ct.out + (size_t)cell * 64;
+    const int* tyc = ct.type + (size_t)cell * 8;
+    const int* wrc = ct.wr + (size_t)cell * 64 + 32 * h;
+    float2 v[8][4];                                      // x[o][q], then v[s][q] (parity 4h + q)
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const int4 jq = __ldg(reinterpret_cast<const int4*>(outc + o * 8 + 4 * h));
+        const int jj[4] = {jq.x, jq.y, jq.z, jq.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[o][q] = jj[q] >= 0 ? x_in[(size_t)jj[q] * n_orb + j] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float2 x[8];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) x[o] = v[o][q];
+        const float* cb = ct.coef_bt + (size_t)__ldg(tyc + 4 * h + q) * 64;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            float c[8];
+            ld_float8(cb + s * 8, c);
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                acc.x += c[o] * x[o].x;
+                acc.y += c[o] * x[o].y;
+            }
+            v[s][q] = acc;
+        }
+    }
+    // u[s][p]: slot 4h + s, parity p (0..7); own parities from v, the partner's by shuffle
+    float2 u[4][8];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 keep = h ? v[4 + s][q] : v[s][q];
+            const float2 got = shfl16(h ? v[s][q] : v[4 + s][q]);
+            u[s][q] = h ? got : keep;                    // parities 0..3
+            u[s][4 + q] = h ? keep : got;                // parities 4..7
+        }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) wht8_regs(u[s]);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        int wr[8];
+        ld_int8(wrc + s * 8, wr);
+        float2 y[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) y[g] = wr[g] >= 0 ? __ldg(y_f + (size_t)wr[g] * n_orb + j) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            if (wr[g] >= 0) out[(size_t)wr[g] * n_orb + j] = make_float2(y[g].x + cdt * u[s][g].x, y[g].y + cdt * u[s][g].y);
+    }
+}
+
 // tc_colexp for a node-major x ((moff + row) * n_orb + o): one block per (class member,
 // 32 consecutive orbitals), lane = orbital, the 32 warps taking every 32nd row with 16
 // loads in flight each; the same exponents as tc_colexp.  Grid tc_ncols * n_orb / 32

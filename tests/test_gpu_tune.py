@@ -205,26 +205,29 @@ def test_staged_stencil_is_bit_identical(env, dims, order, placement, gc):
         assert torch.equal(outs[0][1], outs[1][1])
 
 
+@pytest.mark.parametrize("lanes", [1, 2, 3])
 @pytest.mark.parametrize("prec,b,tile,split,gc", [("fp16x3", 32, 0, 0, 0), ("fp16x3", 64, 1, 2, 1),
                                                   ("fp16x3", 96, 0, 1, 0), ("tf32x3", 32, 2, 3, 0),
                                                   ("tf32x3", 64, 0, 1, 1), ("fp16x3", 40, 0, 0, 0),
                                                   ("c64", 32, 0, 0, 0)])
-def test_node_major_chain_is_bit_identical(env, prec, b, tile, split, gc):
+def test_node_major_chain_is_bit_identical(env, lanes, prec, b, tile, split, gc):
     """The order-1 chain with node-major adapted vectors (ABC_TUNE_LANES: warp per cell
     and 32 orbitals; the column scales, the operand packing and the GEMM epilogue in that
     layout) forms the same sums in the same order as the orbital-major chain: runs and
     single steps are bit for bit the same, for each GEMM form, split count and the Gamma
-    copy, on a box whose classes span several 128-row tiles and K blocks.  Orbital counts
-    that are not a multiple of 32, and plain complex64, keep the orbital-major chain."""
+    copy, on a box whose classes span several 128-row tiles and K blocks, with a warp per
+    cell (lanes 1) or each cell split between lane pairs (lanes 2 and 3, two register
+    caps).  Orbital counts that are not a multiple of 32, and plain complex64, keep the
+    orbital-major chain."""
     torch, abc = env
     dims, h, dt = (22, 20, 18), 0.45, 0.005
     psi0 = inputs.orbital_set(dims, h, np.random.default_rng(46), b)
     V0 = inputs.smooth_random(dims, h, np.random.default_rng(47))
     outs = []
-    for lanes in (0, 1):
+    for setting in (0, lanes):
         ctx = abc.Context(dims, h, 1, 1.0, precision=prec, max_orbitals=b)
-        ctx.set_tuning(abc.TUNE_LANES, lanes)
-        assert ctx.get_tuning(abc.TUNE_LANES) == lanes
+        ctx.set_tuning(abc.TUNE_LANES, setting)
+        assert ctx.get_tuning(abc.TUNE_LANES) == setting
         if prec != "c64":
             ctx.set_tuning(abc.TUNE_GEMM_TILE, tile)
             ctx.set_tuning(abc.TUNE_GEMM_SPLIT, split)
@@ -242,8 +245,9 @@ def test_node_major_chain_is_bit_identical(env, prec, b, tile, split, gc):
     assert torch.equal(outs[0][1], outs[1][1])
 
 
+@pytest.mark.parametrize("lanes", [1, 2])
 @pytest.mark.parametrize("prec", ["fp16x3", "tf32x3"])
-def test_node_major_chain_against_oracle(env, prec):
+def test_node_major_chain_against_oracle(env, prec, lanes):
     """One step of the node-major chain against the FP64 oracle (64 orbitals, random
     auxiliary state): the same 1e-6 as every other tensor-core setting."""
     torch, abc = env
@@ -256,7 +260,8 @@ def test_node_major_chain_against_oracle(env, prec):
     f0 = rng.normal(size=(b, len(sy.G))) + 1j * rng.normal(size=(b, len(sy.G)))
     ref_p, ref_f = sy.step(psi0, f0, dt)
     ctx = abc.Context(dims, h, 1, 1.0, precision=prec, max_orbitals=b)
-    ctx.set_tuning(abc.TUNE_LANES, 1)
+    ctx.set_tuning(abc.TUNE_LANES, lanes)
+    ctx.set_tuning(abc.TUNE_GEMM_SPLIT, 1)               # the epilogue forms x
     psi = torch.from_numpy(psi0.reshape(b, *dims[::-1])).to("cuda", torch.complex64).contiguous()
     aux = torch.from_numpy(f0.T.copy()).to("cuda", torch.complex64).contiguous()
     Vt = torch.from_numpy(V).to("cuda", torch.float32).contiguous()
