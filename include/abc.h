@@ -400,7 +400,10 @@ int abc_wait_selftest(abc_ctx* ctx, long long polls, void* stream);
  *                           reads one array.  2 and 3: the same chain with each cell split
  *                           between two lanes (a warp per cell and 16 orbitals, half the
  *                           values per lane, the halves exchanged by lane shuffles;
- *                           registers capped for 4 or 5 blocks per SM).  Bit-identical
+ *                           registers capped for 4 or 5 blocks per SM); 4 and 5: each
+ *                           cell split between four lanes (a warp per cell and 8
+ *                           orbitals, the quarters exchanged through the warp's own
+ *                           shared-memory tile; 6 or 8 blocks per SM).  Bit-identical
  *                           results; takes precedence over ABC_TUNE_FORWARD_RW and
  *                           ABC_TUNE_BACK_MULTI.  0 (default) orbital-major.
  *   ABC_TUNE_GEMM_TILE      tensor-core forms, n_orb >= 2: 0 (default) output tiles of up

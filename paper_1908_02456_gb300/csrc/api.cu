@@ -886,7 +886,16 @@ void back(abc_ctx* c, const TRes& tr, int n_orb, T s1, T a_coef, const void* y_f
         }
     }
     if constexpr (sizeof(T) == 4 && MODE == 0) {
-        if (nm && tr.xform && c->lanes >= 2) {   // x formed by the contraction epilogue
+        if (nm && tr.xform && c->lanes >= 4) {   // x formed by the contraction epilogue
+            if (c->lanes == 5)
+                dev::bnd_back_quads_x<8><<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
+                    ct, n_orb, (const Vc*)tr.t, (const Vc*)y_f, (Vc*)out, cdt);
+            else
+                dev::bnd_back_quads_x<6><<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
+                    ct, n_orb, (const Vc*)tr.t, (const Vc*)y_f, (Vc*)out, cdt);
+            return;
+        }
+        if (nm && tr.xform && c->lanes >= 2) {
             if (c->lanes == 3)
                 dev::bnd_back_pairs_x<5><<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
                     ct, n_orb, (const Vc*)tr.t, (const Vc*)y_f, (Vc*)out, cdt);
@@ -1080,7 +1089,16 @@ void stage(abc_ctx* c, int n_orb, T cdt, const void* w_phi, const void* w_f, con
             dev::bnd_forward<T, 0, true><<<nbk, 128, 0, s>>>(ct, n_orb, c->nvox, (const Vc*)w_phi,
                                                              order == 1 ? (const Vc*)w_f : nullptr, (Vc*)hp, (Vc*)hf,
                                                              nullptr, (T)0, dev::Ord2Fwd<T>{});
-        else if (nm && c->lanes == 3)
+        else if (nm && c->lanes >= 4) {
+            if (c->lanes == 5)
+                dev::bnd_forward_quads<8><<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
+                    cell_tab<float>(c), n_orb, c->nvox, (const float2*)w_phi, (const float2*)w_f, (float2*)hp,
+                    (float2*)hf, (const float2*)g_in);
+            else
+                dev::bnd_forward_quads<6><<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
+                    cell_tab<float>(c), n_orb, c->nvox, (const float2*)w_phi, (const float2*)w_f, (float2*)hp,
+                    (float2*)hf, (const float2*)g_in);
+        } else if (nm && c->lanes == 3)
             dev::bnd_forward_pairs<5><<<lanes_blocks(c, n_orb), 32 * dev::LANES_W, 0, s>>>(
                 cell_tab<float>(c), n_orb, c->nvox, (const float2*)w_phi, (const float2*)w_f, (float2*)hp, (float2*)hf,
                 (const float2*)g_in);
@@ -2053,7 +2071,7 @@ extern "C" int abc_set_tuning(abc_ctx* ctx, int key, long long value) {
         return ABC_OK;
     }
     if (key == ABC_TUNE_LANES) {
-        if (value < 0 || value > 3) return fail(ABC_ERR_ARG, "ABC_TUNE_LANES takes 0, 1, 2 or 3");
+        if (value < 0 || value > 5) return fail(ABC_ERR_ARG, "ABC_TUNE_LANES takes 0 .. 5");
         ctx->lanes = (int)value;
         drop_graphs(ctx);
         if (ctx->lanes && !ctx->lanes_attr) {

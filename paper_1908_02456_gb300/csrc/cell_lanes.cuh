@@ -433,6 +433,165 @@ __global__ void __launch_bounds__(32 * LANES_W, MINB) bnd_back_pairs_x(CellTab<f
     }
 }
 
+// ---------------------------------------------------------------------------------
+// A cell split between four lanes (ABC_TUNE_LANES 4 and 5): a warp takes one cell and 8
+// consecutive orbitals; lanes l, l + 8, l + 16, l + 24 share orbital l & 7 and each holds
+// a quarter of the cell's values (two slots, then two parities).  The quarters swap
+// their values through the warp's own tile of shared memory, laid out so that both the
+// writes (one parity of two slots per quarter) and the reads (one slot of two parities
+// per quarter) take the two wavefronts 32 eight-byte values need.  Every access of a
+// warp instruction is four runs of 8 orbitals (64 contiguous bytes).  Same sums in the
+// same order as the forms above.  MINB: blocks per SM the registers are capped for.
+// ---------------------------------------------------------------------------------
+constexpr int QS_P = 12, QS_S = 8 * QS_P + 4;         // float2 strides of a parity and a slot
+constexpr int QS_WARP = 8 * QS_S;                       // float2 per warp
+
+__device__ __forceinline__ bool quads_item(const CellTab<float>& ct, int n_orb, int& cell, int& j, int& r) {
+    const int nch = n_orb >> 3;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= (long long)ct.n_cells * nch) return false;
+    cell = (int)(wid / nch);
+    j = (int)(wid - (long long)cell * nch) * 8 + (threadIdx.x & 7);
+    r = (threadIdx.x >> 3) & 3;
+    return true;
+}
+
+// Forward: quarter r loads and transforms slots 2r, 2r + 1, then mixes parities 2r,
+// 2r + 1 over all eight slots.
+template <int MINB>
+__global__ void __launch_bounds__(32 * LANES_W, MINB) bnd_forward_quads(CellTab<float> ct, int n_orb, long long nvox,
+                                                                        const float2* __restrict__ w_phi,
+                                                                        const float2* __restrict__ w_f,
+                                                                        float2* __restrict__ hat_phi,
+                                                                        float2* __restrict__ hat_f,
+                                                                        const float2* __restrict__ g_phi) {
+    __shared__ float2 qs[LANES_W][QS_WARP];
+    int cell, j, r;
+    if (!quads_item(ct, n_orb, cell, j, r)) return;    // whole warps (the item is per warp)
+    float2* sm = qs[threadIdx.x >> 5] + (threadIdx.x & 7);
+    const int* gic = ct.gi + (size_t)cell * 64 + 16 * r;     // slots 2r, 2r + 1
+    const int* ndc = ct.node + (size_t)cell * 64 + 16 * r;
+    const int* outc = ct.out + (size_t)cell * 64;
+    const int* tyc = ct.type + (size_t)cell * 8;
+#pragma unroll 1
+    for (int arr = 0; arr < 2; ++arr) {
+        if (arr == 1 && !w_f) break;
+        const bool gather = arr == 0 && !g_phi;
+        const float2* nat = arr == 0 ? g_phi : w_f;
+        float2 x[2][8];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            int gis[8], nds[8];
+            ld_int8(gic + a * 8, gis);
+            if (gather) ld_int8(ndc + a * 8, nds);
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                float2 v = make_float2(0.f, 0.f);
+                if (gis[g] >= 0) v = gather ? w_phi[(long long)j * nvox + nds[g]] : nat[(size_t)gis[g] * n_orb + j];
+                x[a][g] = v;
+            }
+            wht8_regs(x[a]);
+        }
+        __syncwarp();                                    // the previous array's reads are done
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int p = 0; p < 8; ++p) sm[(2 * r + a) * QS_S + p * QS_P] = x[a][p];
+        __syncwarp();
+        float2 y[8][2];                                  // slot S, parity 2r + b
+#pragma unroll
+        for (int S = 0; S < 8; ++S)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) y[S][b] = sm[S * QS_S + (2 * r + b) * QS_P];
+        float2* hat = arr == 0 ? hat_phi : hat_f;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int p = 2 * r + b;
+            const float* cf = ct.coef_f + (size_t)__ldg(tyc + p) * 64;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int jj = __ldg(outc + o * 8 + p);
+                if (jj < 0) continue;
+                float c[8];
+                ld_float8(cf + o * 8, c);
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int S = 0; S < 8; ++S) {
+                    acc.x += c[S] * y[S][b].x;
+                    acc.y += c[S] * y[S][b].y;
+                }
+                hat[(size_t)jj * n_orb + j] = acc;
+            }
+        }
+    }
+}
+
+// Back from the epilogue's x: quarter r loads and mixes parities 2r, 2r + 1, then
+// transforms back slots 2r, 2r + 1 over all eight parities and writes their nodes.
+template <int MINB>
+__global__ void __launch_bounds__(32 * LANES_W, MINB) bnd_back_quads_x(CellTab<float> ct, int n_orb,
+                                                                       const float2* __restrict__ x_in,
+                                                                       const float2* y_f, float2* out, float cdt) {
+    __shared__ float2 qs[LANES_W][QS_WARP];
+    int cell, j, r;
+    if (!quads_item(ct, n_orb, cell, j, r)) return;
+    float2* sm = qs[threadIdx.x >> 5] + (threadIdx.x & 7);
+    const int* outc = ct.out + (size_t)cell * 64;
+    const int* tyc = ct.type + (size_t)cell * 8;
+    const int* wrc = ct.wr + (size_t)cell * 64 + 16 * r;
+    float2 v[8][2];                                      // x[o][b], then v[s][b] (parity 2r + b)
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const int2 jq = __ldg(reinterpret_cast<const int2*>(outc + o * 8 + 2 * r));
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int jj = b ? jq.y : jq.x;
+            v[o][b] = jj >= 0 ? x_in[(size_t)jj * n_orb + j] : make_float2(0.f, 0.f);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        float2 x[8];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) x[o] = v[o][b];
+        const float* cb = ct.coef_bt + (size_t)__ldg(tyc + 2 * r + b) * 64;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            float c[8];
+            ld_float8(cb + s * 8, c);
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                acc.x += c[o] * x[o].x;
+                acc.y += c[o] * x[o].y;
+            }
+            v[s][b] = acc;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) sm[s * QS_S + (2 * r + b) * QS_P] = v[s][b];
+    __syncwarp();
+    float2 u[2][8];                                      // slot 2r + a, parity p
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int p = 0; p < 8; ++p) u[a][p] = sm[(2 * r + a) * QS_S + p * QS_P];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        wht8_regs(u[a]);
+        int wr[8];
+        ld_int8(wrc + a * 8, wr);
+        float2 y[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) y[g] = wr[g] >= 0 ? __ldg(y_f + (size_t)wr[g] * n_orb + j) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            if (wr[g] >= 0) out[(size_t)wr[g] * n_orb + j] = make_float2(y[g].x + cdt * u[a][g].x, y[g].y + cdt * u[a][g].y);
+    }
+}
+
 // tc_colexp for a node-major x ((moff + row) * n_orb + o): one block per (class member,
 // 32 consecutive orbitals), lane = orbital, the 32 warps taking every 32nd row with 16
 // loads in flight each; the same exponents as tc_colexp.  Grid tc_ncols * n_orb / 32

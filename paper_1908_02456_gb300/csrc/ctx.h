@@ -93,7 +93,8 @@ struct abc_ctx {
     bool gam_mode = false;           // stencils write the next stage's w on Gamma for the forward transform (tuning)
     int lanes = 0;                   // order-1 tensor-core chain with node-major adapted vectors (tuning):
                                      // 1 warp per cell and 32 orbitals, 2 / 3 cell split between lane
-                                     // pairs (registers for 4 / 5 blocks per SM)
+                                     // pairs (registers for 4 / 5 blocks per SM), 4 / 5 between four
+                                     // lanes (6 / 8 blocks per SM)
     bool lanes_attr = false;         // bnd_back_lanes's shared-memory size set, lanes_ac filled
     abc::DevBuf lanes_ac;            // [n_gamma] a_coef * c per adapted index (node-major chain)
     abc::DevBuf gam[2];              // that Gamma copy, [n_gamma][max_orbitals], one per stage parity
@@ -155,7 +156,7 @@ inline unsigned cell_blocks(const abc_ctx* c, int n_orb) {
 // Blocks of the lane-per-orbital transforms (one warp per cell and 32 orbitals, four
 // warps per block; n_orb a multiple of 32).
 inline unsigned lanes_blocks(const abc_ctx* c, int n_orb) {
-    const int per = c->lanes >= 2 ? 16 : 32;         // orbitals per warp
+    const int per = c->lanes >= 4 ? 8 : c->lanes >= 2 ? 16 : 32;   // orbitals per warp
     return (unsigned)(((long long)c->geo.n_cells * (n_orb / per) + 3) / 4);
 }
 }  // namespace abc

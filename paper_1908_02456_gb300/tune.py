@@ -86,11 +86,11 @@ def knob_groups(ctx: abc.Context, n_orb: int):
             fwd = [{abc.TUNE_FORWARD_RW: rw, abc.TUNE_GAMMA_COPY: gc, **ln} for gc in (0, 1) for rw in (0, 1)]
             if lanes:
                 fwd += [{abc.TUNE_FORWARD_RW: 0, abc.TUNE_GAMMA_COPY: gc, abc.TUNE_LANES: ln}
-                        for gc in (0, 1) for ln in (1, 2, 3)]
+                        for gc in (0, 1) for ln in (1, 2, 3, 4, 5)]
         else:
             fwd = [{abc.TUNE_FORWARD_RW: 0, **ln}, {abc.TUNE_FORWARD_RW: 1, **ln}]
             if lanes:
-                fwd += [{abc.TUNE_FORWARD_RW: 0, abc.TUNE_LANES: ln} for ln in (1, 2, 3)]
+                fwd += [{abc.TUNE_FORWARD_RW: 0, abc.TUNE_LANES: ln} for ln in (1, 2, 3, 4, 5)]
         groups.append(fwd)
     if n_orb == 1 and ctx.precision != abc.FP64 and ctx.get_tuning(abc.TUNE_TILE_COUNT) > 0:
         groups.append([{abc.TUNE_PDL: 1}, {abc.TUNE_PDL: 0}])
@@ -168,5 +168,5 @@ def describe(setting: dict) -> dict:
              abc.TUNE_STENCIL_KZ: "stencil_form(0=pair per thread, 1=capped registers, k>1=k planes)",
              abc.TUNE_BACK_MULTI: "back_transform_orbitals_per_group(0=1, 1=4, 2=2)", abc.TUNE_FORWARD_RW: "forward_transform_in_registers",
              abc.TUNE_GAMMA_COPY: "forward_reads_gamma_copy", abc.TUNE_STENCIL_STAGED: "stencil_planes_staged_by_bulk_copies",
-             abc.TUNE_LANES: "node_major_chain(1=warp per cell, 2/3=cell split between lane pairs)", abc.TUNE_PDL: "pdl"}
+             abc.TUNE_LANES: "node_major_chain(1=warp per cell, 2/3=cell split between 2 lanes, 4/5=between 4)", abc.TUNE_PDL: "pdl"}
     return {names.get(int(k), str(k)): v for k, v in setting.items()}

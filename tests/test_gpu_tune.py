@@ -205,7 +205,7 @@ def test_staged_stencil_is_bit_identical(env, dims, order, placement, gc):
         assert torch.equal(outs[0][1], outs[1][1])
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 3])
+@pytest.mark.parametrize("lanes", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("prec,b,tile,split,gc", [("fp16x3", 32, 0, 0, 0), ("fp16x3", 64, 1, 2, 1),
                                                   ("fp16x3", 96, 0, 1, 0), ("tf32x3", 32, 2, 3, 0),
                                                   ("tf32x3", 64, 0, 1, 1), ("fp16x3", 40, 0, 0, 0),
@@ -216,8 +216,8 @@ def test_node_major_chain_is_bit_identical(env, lanes, prec, b, tile, split, gc)
     layout) forms the same sums in the same order as the orbital-major chain: runs and
     single steps are bit for bit the same, for each GEMM form, split count and the Gamma
     copy, on a box whose classes span several 128-row tiles and K blocks, with a warp per
-    cell (lanes 1) or each cell split between lane pairs (lanes 2 and 3, two register
-    caps).  Orbital counts that are not a multiple of 32, and plain complex64, keep the
+    cell (lanes 1) or each cell split between two lanes (lanes 2 and 3, two register caps)
+    or four (lanes 4 and 5).  Orbital counts that are not a multiple of 32, and plain complex64, keep the
     orbital-major chain."""
     torch, abc = env
     dims, h, dt = (22, 20, 18), 0.45, 0.005
@@ -245,7 +245,7 @@ def test_node_major_chain_is_bit_identical(env, lanes, prec, b, tile, split, gc)
     assert torch.equal(outs[0][1], outs[1][1])
 
 
-@pytest.mark.parametrize("lanes", [1, 2])
+@pytest.mark.parametrize("lanes", [1, 2, 4])
 @pytest.mark.parametrize("prec", ["fp16x3", "tf32x3"])
 def test_node_major_chain_against_oracle(env, prec, lanes):
     """One step of the node-major chain against the FP64 oracle (64 orbitals, random
