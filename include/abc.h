@@ -276,8 +276,10 @@ int abc_profile_durations(abc_ctx* ctx, int kernel, float* ms_out, long long max
 /* Algorithmic bytes of one launch of a kernel for n_orb orbitals (the roofline
  * numerator): boundary matrix bytes + vectors for the contraction (for the
  * tensor-core GEMM: its split operand planes of every class block once, the packed
- * right-hand sides and the partial outputs); for the stencil 3 complex values per
- * point and orbital plus V per point, or, when abc_run fuses the stages in time
+ * right-hand sides and the partial outputs, plus f_hat and phi_hat when its epilogue
+ * forms the back transform's input, ABC_TUNE_LANES); for the stencil 3 complex values
+ * per point and orbital plus V per point (plus the output on Gamma with
+ * ABC_TUNE_GAMMA_COPY), or, when abc_run fuses the stages in time
  * (ABC_TUNE_FUSED), the fused pass's 2 complex values per point and orbital plus V
  * plus the band values it stores. */
 int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, double* bytes);

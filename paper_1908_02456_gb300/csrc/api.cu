@@ -1964,7 +1964,9 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
             }
             const int ns = ctx->tc_b[n_orb].nsplit;
             const double eb = ctx->tc_f16 ? 2.0 : 4.0;        // bytes per split-plane element
-            *bytes = a * (ctx->tc_cfg == 2 ? 6 : 4) * eb + x * 6 * eb + x * ns * 8;
+            // the node-major chain's epilogue forming x also reads f_hat and phi_hat
+            const bool xf = lanes_ok(ctx, n_orb) && ns == 1;
+            *bytes = a * (ctx->tc_cfg == 2 ? 6 : 4) * eb + x * 6 * eb + x * ns * 8 + (xf ? 2.0 * x * 8 : 0.0);
             return ABC_OK;
         } else {
             for (int p = 0; p < ctx->bi.n; ++p) entries += (double)ctx->bi.nseg * ctx->bi.m[p] * ctx->bi.m[p];
@@ -1978,8 +1980,9 @@ extern "C" int abc_kernel_bytes(const abc_ctx* ctx, int kernel, int n_orb, doubl
                           (dev::band_nodes(ctx->geo.nx, ctx->geo.ny, ctx->geo.nz, 2) - ctx->geo.n_gamma) +
                           (dev::band_nodes(ctx->geo.nx, ctx->geo.ny, ctx->geo.nz, 3) -
                            dev::band_nodes(ctx->geo.nx, ctx->geo.ny, ctx->geo.nz, 1)));
-        else
-            *bytes = (double)ctx->nvox * (3.0 * n_orb * cb + ctx->real_bytes);
+        else    // w, y in, out, V; with the Gamma copy also the output on Gamma
+            *bytes = (double)ctx->nvox * (3.0 * n_orb * cb + ctx->real_bytes) +
+                     (gam_ok(ctx, n_orb) ? (double)ctx->geo.n_gamma * n_orb * cb : 0.0);
     } else {
         return fail(ABC_ERR_ARG, "unknown kernel");
     }
