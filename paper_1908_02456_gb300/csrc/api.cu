@@ -707,6 +707,11 @@ int build_tc(abc_ctx* c) {
     CUDA_TRY(cudaFuncSetAttribute(gemm_tc<TC_TF32, TcKara>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcKara::smem));
     CUDA_TRY(cudaFuncSetAttribute(gemm_tc<TC_F16, TcKara>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcKara::smem));
     if (f16 && (st = c->tc_colexp.alloc(sizeof(int) * (size_t)rsum * c->params.max_orbitals))) return st;
+    if (f16) {   // tc_colexp_nm's column maxima and completion counters (zero between calls)
+        const size_t n = (size_t)rsum * c->params.max_orbitals;
+        if ((st = c->tc_colmax.alloc(sizeof(unsigned) * (n + n / 32 + 1)))) return st;
+        CUDA_TRY(cudaMemset(c->tc_colmax.p, 0, sizeof(unsigned) * (n + n / 32 + 1)));
+    }
     c->tc_f16 = f16;
     c->tc_ncols = rsum;
     c->tc_sms = sms;
@@ -815,8 +820,9 @@ TRes contraction(abc_ctx* c, const void* x, void* t, int n_orb, int conj, cudaSt
         if (c->tc_f16) {
             const int ncols = c->tc_ncols * n_orb;
             if (nm)
-                dev::tc_colexp_nm<<<(unsigned)(ncols / 32), 32 * dev::CX_WARPS, 0, s>>>(c->tci, n_orb, (const float2*)x,
-                                                                       c->tc_colexp.as<int>());
+                dev::tc_colexp_nm<<<(unsigned)(ncols / 32 * dev::CX_PARTS), 32 * dev::CX_WARPS, 0, s>>>(
+                    c->tci, n_orb, (const float2*)x, c->tc_colexp.as<int>(), c->tc_colmax.as<unsigned>(),
+                    c->tc_colmax.as<unsigned>() + (size_t)c->tc_ncols * c->params.max_orbitals);
             else
                 dev::tc_colexp<<<(unsigned)((ncols + 7) / 8), 256, 0, s>>>(c->tci, n_orb, n, (const float2*)x,
                                                                            c->tc_colexp.as<int>(), ncols);

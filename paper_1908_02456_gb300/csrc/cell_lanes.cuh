@@ -592,29 +592,36 @@ __global__ void __launch_bounds__(32 * LANES_W, MINB) bnd_back_quads_x(CellTab<f
     }
 }
 
-// tc_colexp for a node-major x ((moff + row) * n_orb + o): one block per (class member,
-// 32 consecutive orbitals), lane = orbital, the 32 warps taking every 32nd row with 16
-// loads in flight each; the same exponents as tc_colexp.  Grid tc_ncols * n_orb / 32
-// blocks of 1024 threads.
-constexpr int CX_WARPS = 32, CX_DEPTH = 16;
+// tc_colexp for a node-major x ((moff + row) * n_orb + o): block (class member rm,
+// 32 consecutive orbitals, row part) with lane = orbital and its 16 warps taking every
+// 16th row of the part; the parts' maxima meet in colmax by atomicMax, and the block
+// that completes a column group last (counter) turns them into the exponents and resets
+// colmax and the counter for the next call (no block waits for another).  The same
+// exponents as tc_colexp.  Grid tc_ncols * n_orb / 32 * CX_PARTS blocks of 512 threads;
+// colmax [tc_ncols * n_orb] and count [tc_ncols * n_orb / 32] zero before the first call.
+constexpr int CX_WARPS = 16, CX_DEPTH = 8, CX_PARTS = 8;
 static __global__ void __launch_bounds__(32 * CX_WARPS) tc_colexp_nm(TcInfo info, int n_orb, const float2* __restrict__ x,
-                                                                   int* __restrict__ colexp) {
+                                                                   int* __restrict__ colexp, unsigned* colmax,
+                                                                   unsigned* count) {
     __shared__ uint32_t red[CX_WARPS][32];
+    __shared__ bool last;
     const int nog = n_orb >> 5;
-    const int rm = blockIdx.x / nog, og = blockIdx.x - rm * nog;      // class member (rsum index), orbital group
+    const int part = blockIdx.x % CX_PARTS, grp = blockIdx.x / CX_PARTS;
+    const int rm = grp / nog, og = grp - rm * nog;                  // class member (rsum index), orbital group
     int c = 0;
     while (c + 1 < info.ncls && rm >= info.rsum[c + 1]) ++c;
     const int k = rm - info.rsum[c], m = info.m[c];
+    const int r_lo = (int)((long long)m * part / CX_PARTS), r_hi = (int)((long long)m * (part + 1) / CX_PARTS);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int o = og * 32 + lane;
     const float2* p = x + (size_t)info.moff[c][k] * n_orb + o;
     uint32_t mx = 0;
-    for (int r0 = w; r0 < m; r0 += CX_WARPS * CX_DEPTH) {
+    for (int r0 = r_lo + w; r0 < r_hi; r0 += CX_WARPS * CX_DEPTH) {
         float2 v[CX_DEPTH];
 #pragma unroll
         for (int u = 0; u < CX_DEPTH; ++u) {
             const int r = r0 + CX_WARPS * u;
-            v[u] = r < m ? __ldg(p + (size_t)r * n_orb) : make_float2(0.f, 0.f);
+            v[u] = r < r_hi ? __ldg(p + (size_t)r * n_orb) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < CX_DEPTH; ++u)
@@ -625,12 +632,25 @@ static __global__ void __launch_bounds__(32 * CX_WARPS) tc_colexp_nm(TcInfo info
     if (w == 0) {
 #pragma unroll
         for (int q = 1; q < CX_WARPS; ++q) mx = max(mx, red[q][lane]);
+        atomicMax(colmax + rm * n_orb + o, mx);
+        __threadfence();
+        __syncwarp();                                    // every lane's maximum before the count
+        unsigned done = 0;
+        if (lane == 0) done = atomicAdd(count + grp, 1u);
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (lane == 0) last = done == CX_PARTS - 1;
+    }
+    __syncthreads();
+    if (w == 0 && last) {
+        __threadfence();
+        const uint32_t all = atomicExch(colmax + rm * n_orb + o, 0u);     // the final maximum; reset
         int e = 0;
-        if (mx != 0) {
-            const int E = (int)(mx >> 23) - 127;
+        if (all != 0) {
+            const int E = (int)(all >> 23) - 127;
             e = min(TC_COLEXP_MAX, max(-TC_COLEXP_MAX, TC_TARGET_EXP - 1 - E));
         }
         colexp[rm * n_orb + o] = e;
+        if (lane == 0) count[grp] = 0u;
     }
 }
 

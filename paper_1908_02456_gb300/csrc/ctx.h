@@ -97,6 +97,7 @@ struct abc_ctx {
                                      // lanes (6 / 8 blocks per SM)
     bool lanes_attr = false;         // bnd_back_lanes's shared-memory size set, lanes_ac filled
     abc::DevBuf lanes_ac;            // [n_gamma] a_coef * c per adapted index (node-major chain)
+    abc::DevBuf tc_colmax;           // tc_colexp_nm: column maxima [tc_ncols * max_orbitals], then counters
     abc::DevBuf gam[2];              // that Gamma copy, [n_gamma][max_orbitals], one per stage parity
     int tc_sms_all = 0;              // SMs of the device
     abc::DevBuf sym_tiles, sym_seg, sym_cta, sym_rowseg, sym_rowpart, sym_colpart, sym_gdesc, err_flag;
