@@ -75,7 +75,9 @@ def knob_groups(ctx: abc.Context, n_orb: int):
                 stencil.append({abc.TUNE_FUSED: 0, abc.TUNE_STENCIL: 0, abc.TUNE_STENCIL_KZ: 1,
                                 abc.TUNE_STENCIL_STAGED: 1})
         if nx % 2 == 0 and min(ctx.shape) >= 8 and ctx.radius == 1:
-            stencil.append({abc.TUNE_FUSED: 1, **st})
+            # abc_step and the adjoint still step stage by stage: the library's default form
+            stencil.append({abc.TUNE_FUSED: 1, abc.TUNE_STENCIL: 0,
+                            abc.TUNE_STENCIL_KZ: 1 if n_orb >= 2 else 0, **st})
         groups.append(stencil)
     if ctx.order == 1 and ctx.fit1 == abc.FIT1_LIMIT and n_orb >= 2 and n_orb % 2 == 0:
         groups.append([{abc.TUNE_BACK_MULTI: m} for m in ((0, 1, 2) if n_orb % 4 == 0 else (0, 2))])
