@@ -204,11 +204,11 @@ __global__ void __launch_bounds__(32 * LANES_W, 3) bnd_back_lanes(CellTab<float>
 }
 
 // Back transform from x formed by the contraction epilogue (XEpi; node-major): a lane
-// loads the cell's 64 values of x in one round into registers and mixes them back per
-// parity in place; the results go to the lane's shared-memory column (LANES_SMEM bytes
-// per block), which frees the registers for all y_f loads of the cell at once; then per
-// slot the butterflies and out[e][j] = y_f[e][j] + cdt v (the same bits as
-// bnd_back_lanes; y_f through the read-only path, as there).
+// loads the cell's 64 values of x into registers (all loads issued together) and mixes
+// them back per parity in place; the results go to the lane's shared-memory column
+// (LANES_SMEM bytes per block), which frees the registers for all y_f loads of the cell
+// at once; then per slot the butterflies and out[e][j] = y_f[e][j] + cdt v (the same
+// bits as bnd_back_lanes; y_f through the read-only path, as there).
 __global__ void __launch_bounds__(32 * LANES_W, 3) bnd_back_lanes_x(CellTab<float> ct, int n_orb,
                                                                     const float2* __restrict__ x_in,
                                                                     const float2* y_f, float2* out, float cdt) {
