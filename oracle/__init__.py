@@ -26,8 +26,13 @@ order, in float64 / complex128:
                      the norm / Lyapunov / energy diagnostics.
 * ``adjoint``     -- reverse-mode gradient of the absorbed probability with
                      respect to the potential, written from the same Taylor form.
+* ``exact``       -- the free Gaussian packet of eq:15 (the reference solution of
+                     the paper's 3D experiment).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
 closed forms, invariants proved in the paper, brute force on tiny inputs or the
-paper's printed values.  No function here is "parity unpinned".
+paper's printed values; the internal building blocks (names with a leading
+underscore, and small pieces such as ``Box.diag_weight``, ``order2_end`` or
+``all_offsets``) through the pinned functions that call them.  No function here
+is "parity unpinned".
 """
